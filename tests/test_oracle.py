@@ -1,0 +1,205 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: fixtures come from the paper's
+worked examples (tests/golden, each cited), the structural-analysis trace of
+Fig. 3, lattice laws, invariants of the dataflow, and brute force (a GCN
+interpreter running the assembly against an evaluator running the decompiled
+OpenCL on random buffers)."""
+import os
+
+import numpy as np
+import pytest
+
+import brute
+import gcngen
+import ocl_eval
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return f.read()
+
+
+# ---- "The body extraction", Listing 1 -------------------------------------
+def test_listing1_dims_and_workgroup():
+    r = oracle.decompile(gold("listing1_body.s"), with_ir=True)
+    h = np.frombuffer(r.ir[0][oracle.IR_HEADER], np.uint32)
+    dims, c0, c1, c2 = (int(x) for x in h[:4])
+    assert dims == 3 and (c0, c1, c2) == (8, 8, 2) and c0 * c1 * c2 == 128
+
+
+# ---- "Data type recovery", Listing 3 and its signature ---------------------
+def test_listing3_signature():
+    r = oracle.decompile(gold("listing3_copy.s"))
+    assert r.status == [0]
+    assert r.text.split("\n")[0] == "__kernel void copy(__global int *data, int x)"
+
+
+# ---- "Search for memory accesses": system values ---------------------------
+@pytest.mark.parametrize("name", ["p194_global_offset", "idiom_noofs", "gid_offset"])
+def test_system_values(name):
+    r = oracle.decompile(gold(name + ".s"))
+    assert r.status == [0]
+    assert r.text == gold(name + ".cl")
+
+
+# ---- "Data type recovery": suffix typing -----------------------------------
+def test_suffix_u32_is_unsigned_addition():
+    r = oracle.decompile(gold("suffix_uint_add.s"))
+    assert r.text == gold("suffix_uint_add.cl")
+
+
+# ---- "Search for control structures", Fig. 3 --------------------------------
+def test_fig3_region_trace():
+    lines = [l.split() for l in gold("fig3_trace.txt").split("\n") if l and not l.startswith("#")]
+    edges = [tuple(int(x) for x in e.split(">")) for e in lines[0][1:]]
+    n = 6
+    succ = {b: [] for b in range(1, n + 1)}
+    for a, b in edges:
+        succ[a].append(b)
+    s0 = [succ[b][0] - 1 if succ[b] else -1 for b in range(1, n + 1)]
+    s1 = [succ[b][1] - 1 if len(succ[b]) > 1 else -1 for b in range(1, n + 1)]
+    log = oracle.reduce_graph(s0, s1)
+    want = [(int(l[1]), sorted(int(x) for x in l[3:])) for l in lines[1:]]
+    got = [(nid + 1, sorted(m + 1 for m in members)) for nid, members in log]
+    assert got == want
+
+
+def test_fig3_unstructured_graph_does_not_reduce():
+    # two blocks jumping into each other's middle: an irreducible loop
+    assert oracle.reduce_graph([1, 2, 1], [2, -1, -1]) is None
+
+
+# ---- exec-mask if-else forms (Fig. 4, Fig. 5) --------------------------------
+@pytest.mark.parametrize("form", [1, 2, 3])
+def test_ifelse_forms_reduce_to_standard_form(form):
+    r = oracle.decompile(gold(f"ifelse_form{form}.s"))
+    assert r.status == [0]
+    assert r.text == gold("ifelse.cl")
+
+
+# ---- the type lattice: a join semilattice -----------------------------------
+def test_type_join_is_a_semilattice():
+    ts = range(9)
+    j = oracle.type_join
+    for a in ts:
+        assert j(0, a) == a and j(a, 0) == a and j(a, a) == a
+        for b in ts:
+            assert j(a, b) == j(b, a)
+            for c in ts:
+                assert j(j(a, b), c) == j(a, j(b, c))
+    # monotone: a <= b  =>  join(a, c) <= join(b, c), with x <= y iff join(x, y) == y
+    for a in ts:
+        for b in ts:
+            if j(a, b) != b:
+                continue
+            for c in ts:
+                assert j(j(a, c), j(b, c)) == j(b, c)
+
+
+# ---- dataflow invariants on generated kernels --------------------------------
+def _batch(cfg, n, **over):
+    p = gcngen.preset(cfg, **over)
+    return gcngen.generate(p, n, seed=gcngen.SEED_BASE + 7 + cfg)
+
+
+def test_every_read_has_a_reaching_definition():
+    b = _batch(1, 40, max_len=600)
+    for i in range(len(b)):
+        r = oracle.decompile(b.kernel(i), with_ir=True)
+        stats = np.frombuffer(r.ir[0][oracle.IR_STATS], np.uint32)
+        assert r.status == [0]
+        assert stats[1] == 0, f"kernel {i}: {stats[1]} reads without a reaching definition"
+
+
+def test_join_versions_are_minimal():
+    # every used join version merges at least two different values (no trivial joins)
+    b = _batch(1, 60, max_len=1500)
+    used = 0
+    for i in range(len(b)):
+        r = oracle.decompile(b.kernel(i), with_ir=True)
+        stats = np.frombuffer(r.ir[0][oracle.IR_STATS], np.uint32)
+        used += int(stats[3])
+        assert stats[4] == 0, f"kernel {i}: {stats[4]} trivial join versions"
+    assert used > 0
+
+
+def test_output_is_wellformed_opencl():
+    b = _batch(1, 60, max_len=900)
+    out, oo, st = oracle.decompile_batch(b.text, b.offsets)
+    assert (st == 0).all()
+    for i in range(len(b)):
+        txt = out[oo[i]:oo[i + 1]].tobytes().decode()
+        ks = ocl_eval.parse(txt)
+        assert len(ks) == 1
+        assert txt.count("{") == txt.count("}") and txt.count("(") == txt.count(")")
+
+
+# ---- brute force: assembly vs decompiled OpenCL on random buffers -----------
+@pytest.mark.parametrize("cfg,n,maxlen", [(0, 4, 0), (1, 40, 400), (4, 6, 1500)])
+def test_brute_force_semantics(cfg, n, maxlen):
+    over = dict(cws0=8, cws1=4)
+    if maxlen:
+        over["max_len"] = maxlen
+    b = _batch(cfg, n, **over)
+    for i in range(len(b)):
+        txt = b.kernel(i).decode()
+        r = oracle.decompile(txt)
+        assert r.status == [0]
+        assert brute.check(txt, r.text, seed=i) is None, f"kernel {i}"
+
+
+def test_brute_force_large_cfg_style():
+    # the large-CFG workload's instruction mix (int/long, spills, deep loops) at a small size
+    # a low VGPR budget forces locals into scratch slots
+    b = _batch(3, 4, min_len=600, max_len=600, trip_max=2, max_depth=4, cws0=8, cws1=4,
+               vgpr_budget=40, max_locals=40)
+    spilled = 0
+    for i in range(len(b)):
+        txt = b.kernel(i).decode()
+        spilled += "buffer_store_dword" in txt
+        r = oracle.decompile(txt)
+        assert r.status == [0]
+        assert brute.check(txt, r.text, seed=i) is None, f"kernel {i}"
+    assert spilled > 0
+
+
+def test_brute_force_catches_planted_mistake():
+    b = _batch(0, 1, cws0=8, cws1=4)
+    txt = b.kernel(0).decode()
+    good = oracle.decompile(txt).text
+    bad = good.replace("get_global_id(0)", "get_local_id(0)", 1)
+    assert bad != good and brute.check(txt, bad) is not None
+
+
+# ---- files, kernels and failure statuses (Listing 2) --------------------------
+def test_multi_kernel_file_equals_single_files():
+    b = _batch(1, 5, max_len=300)
+    whole = "junk before the first kernel\n" + "".join(b.kernel(i).decode() for i in range(5))
+    r = oracle.decompile(whole)
+    assert r.status == [0] * 5
+    assert r.text == "\n".join(oracle.decompile(b.kernel(i)).text for i in range(5))
+
+
+def test_kernel_with_empty_text_is_not_lost():
+    src = ".kernel a\n    .config\n        .dims x\n.kernel b\n    .config\n        .dims x\n    .text\n        s_endpgm\n"
+    r = oracle.decompile(src)
+    assert r.text == "__kernel void a(void)\n{\n}\n\n__kernel void b(void)\n{\n}\n"
+
+
+def test_unknown_instruction_is_inline_asm_and_partial():
+    txt = gold("p194_global_offset.s").replace("        s_endpgm", "        v_frobnicate_b32 v7, v6\n        s_endpgm")
+    r = oracle.decompile(txt)
+    assert r.status == [1]
+    assert '__asm__("v_frobnicate_b32 v7, v6");' in r.text
+
+
+@pytest.mark.parametrize("mut", ["v_mov_b32 v6, s2x", "s_branch .Lnowhere", "v_mov_b32 v99, v0"])
+def test_parse_errors(mut):
+    txt = gold("p194_global_offset.s").replace("        v_mov_b32 v6, s2", "        " + mut)
+    r = oracle.decompile(txt)
+    assert r.status == [2]
+    assert "not decompiled" in r.text
