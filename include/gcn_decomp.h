@@ -1,0 +1,126 @@
+/* gcn_decomp.h — C ABI of the GB300 (sm_103a) GCN -> OpenCL decompiler.
+ *
+ * The operation is the one the paper states as its problem ("A method for
+ * decompilation of AMD GCN kernels to OpenCL", "Statement of the problem"):
+ * a disassembled GCN file goes in, the equivalent OpenCL text comes out.  A
+ * file may hold several kernels (the body-extraction algorithm of Listing 2
+ * splits them at `.kernel`); unsupported instructions are kept as inline
+ * assembly ("Practical implementation").  Every stage of the method runs as a
+ * CUDA kernel on one GPU; nothing here falls back to the CPU.
+ *
+ * Conventions for every call:
+ *  - Return value: 0 on success, a negative GCN_E* code on failure.  No call
+ *    throws or aborts; a failed CUDA call returns GCN_ECUDA and leaves the
+ *    handle usable for gcn_decomp_destroy.
+ *  - Host pointers are plain process memory; "device" pointers are CUDA
+ *    global-memory addresses on the handle's device.  The caller keeps
+ *    ownership of every buffer it passes; the library copies what it needs
+ *    before returning (host inputs) or reads it on the given stream (device
+ *    inputs) and never frees caller memory.
+ *  - Text is bytes, not NUL-terminated; lines end with '\n'.
+ *  - One handle owns its device memory and its CUDA stream.  Calls on one
+ *    handle are serialised by an internal mutex; different handles are
+ *    independent.
+ */
+#ifndef GCN_DECOMP_H
+#define GCN_DECOMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define GCN_OK 0
+#define GCN_EINVAL (-1)  /* bad argument (NULL where not allowed, bad size, unknown id) */
+#define GCN_ENOMEM (-2)  /* device or host allocation failed, or a size exceeds a limit */
+#define GCN_EAGAIN (-3)  /* nothing admitted (memory budget), or the job is not finished */
+#define GCN_ENOJOB (-4)  /* unknown or already fetched job id */
+#define GCN_ECUDA (-5)   /* a CUDA call failed; the message is in gcn_decomp_last_error */
+
+/* per-kernel status, worst over a file's kernels for a job (numeric max) */
+#define GCN_ST_OK 0            /* fully decompiled */
+#define GCN_ST_PARTIAL 1       /* inline asm, unstructured control flow or pseudo-code present */
+#define GCN_ST_PARSE_ERROR 2   /* malformed configuration, operand, label or exec-mask form */
+#define GCN_ST_FIXPOINT_CAP 3  /* a device-side iteration limit was reached */
+
+/* flags */
+#define GCN_WAIT 1u            /* gcn_decomp_fetch_opencl: block until the job is done */
+
+typedef struct gcn_decomp gcn_decomp_t; /* opaque */
+
+typedef struct {
+  int device;                 /* CUDA device ordinal */
+  uint64_t mem_budget_bytes;  /* device memory the handle may hold (0 = no limit) */
+  uint32_t max_slots;         /* jobs resident at once (0 = 65536) */
+  const char *tuning_file;    /* reserved (NULL) */
+  uint32_t flags;             /* reserved (0) */
+} gcn_decomp_config;
+
+/* Create a handle on cfg->device.  *out receives the handle.  Errors:
+ * GCN_EINVAL (NULL cfg/out, bad device), GCN_ECUDA. */
+int gcn_decomp_create(const gcn_decomp_config *cfg, gcn_decomp_t **out);
+
+/* Submit n jobs; job i is one disassembly file text[i][0..len[i]).  The
+ * library copies the texts (a '\n' is appended when the last line lacks one),
+ * decompiles them on the device and keeps the results resident until fetched.
+ * job_ids[i] receives the id of job i; *n_admitted the number of jobs taken
+ * (jobs are admitted in order while the memory budget and slots allow).
+ * Errors: GCN_EINVAL, GCN_EAGAIN (none admitted), GCN_ENOMEM, GCN_ECUDA. */
+int gcn_decomp_submit_batch(gcn_decomp_t *h, const char *const *text, const size_t *len, size_t n,
+                            uint64_t *job_ids, size_t *n_admitted);
+
+/* Copy the OpenCL text of a job (its kernels joined by a blank line) into
+ * buf[0..cap).  buf == NULL only reports the size.  *len_out = bytes of the
+ * text; *status_out = worst GCN_ST_* of the job's kernels (either may be
+ * NULL).  On success with buf != NULL the job's slot is released and its id
+ * becomes unknown.  Errors: GCN_ENOJOB, GCN_EINVAL (cap too small: nothing is
+ * copied and the job stays), GCN_EAGAIN (not finished and no GCN_WAIT). */
+int gcn_decomp_fetch_opencl(gcn_decomp_t *h, uint64_t job_id, char *buf, size_t cap, size_t *len_out,
+                            int *status_out, uint32_t flags);
+
+/* Intermediate arrays of a job, for parity checks: `which` selects
+ *   0 instruction records (32 bytes each: u16 op, u8 nops, u8 flags, u32 imm,
+ *     u32 target, u32 operand[5]),
+ *   1 physical block of each instruction (u32),  2 physical blocks (u32 first,end,succ0,succ1),
+ *   3 logical block of each instruction (u32, 0xFFFFFFFF = exec bookkeeping),
+ *   4 logical blocks (as 2),  5 per-kernel configuration header (8 x u32:
+ *     dims, cws x/y/z, sgprs, vgprs, useargs, user args)
+ * concatenated over the job's kernels in file order.  Sizes as for fetch.
+ * Does not release the job.  Errors: GCN_ENOJOB, GCN_EINVAL. */
+int gcn_decomp_fetch_ir(gcn_decomp_t *h, uint64_t job_id, int which, void *buf, size_t cap, size_t *len_out);
+
+/* Wait for in-flight work and free every resource of the handle (NULL is a no-op). */
+void gcn_decomp_destroy(gcn_decomp_t *h);
+
+/* Device-resident batch: decompile n_files files already in device memory,
+ * file f = d_text[d_file_off[f] .. d_file_off[f+1]), each ending with '\n',
+ * total at most 4 GiB.  Work is queued on `stream` (a cudaStream_t, NULL =
+ * the handle's stream) and the call returns without synchronising; results
+ * stay in the handle's device memory until the next run_device call.
+ * Errors: GCN_EINVAL, GCN_ENOMEM, GCN_ECUDA. */
+int gcn_decomp_run_device(gcn_decomp_t *h, const uint8_t *d_text, uint64_t text_len, const uint64_t *d_file_off,
+                          uint64_t n_files, void *stream);
+
+/* Results of the last run_device call, as device pointers owned by the
+ * handle: d_out = concatenated OpenCL text, d_out_off = u64[n_files+1] byte
+ * offsets per file, d_status = i32[n_files] worst status per file; *out_bytes
+ * = total text size (synchronises the stream).  Errors: GCN_EINVAL (no run). */
+int gcn_decomp_result_device(gcn_decomp_t *h, const uint8_t **d_out, const uint64_t **d_out_off,
+                             const int32_t **d_status, uint64_t *out_bytes);
+
+/* Per-stage device times of the last run (milliseconds, CUDA events on the
+ * run's stream), stage names in *names (static strings).  Returns the number
+ * of stages (<= cap) or a negative code. */
+int gcn_decomp_stage_times(gcn_decomp_t *h, float *ms, const char **names, int cap);
+
+/* Last error message of this thread (static storage; never NULL). */
+const char *gcn_decomp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCN_DECOMP_H */

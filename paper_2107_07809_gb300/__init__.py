@@ -1,0 +1,192 @@
+"""GB300 (sm_103a) GCN -> OpenCL decompiler: thin ctypes binding of libgcndecomp.so.
+
+Every stage of the decompiler runs in the CUDA kernels of ``csrc/``; this module
+only marshals arguments to the C ABI declared in ``include/gcn_decomp.h``.  When
+the shared library is missing, or no GPU is present, calls raise — there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libgcndecomp.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+
+GCN_OK, GCN_EINVAL, GCN_ENOMEM, GCN_EAGAIN, GCN_ENOJOB, GCN_ECUDA = 0, -1, -2, -3, -4, -5
+ST_OK, ST_PARTIAL, ST_PARSE_ERROR, ST_FIXPOINT_CAP = 0, 1, 2, 3
+IR_INSTR, IR_PBLOCK_OF, IR_PBLOCKS, IR_LBLOCK_OF, IR_LBLOCKS, IR_HEADER = range(6)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _sources():
+    return sorted(os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".cu"))
+
+
+def _headers():
+    hs = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith((".h", ".cuh"))]
+    return hs + [os.path.join(_ROOT, "include", "gcn_decomp.h")]
+
+
+def build(force: bool = False, jobs: int | None = None) -> str:
+    """Compile every .cu for sm_103a (in parallel) and link libgcndecomp.so in-tree."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = _sources()
+    newest_hdr = max(os.path.getmtime(h) for h in _headers())
+    objs = []
+    todo = []
+    for src in srcs:
+        obj = os.path.join(_BUILD, os.path.basename(src)[:-3] + ".o")
+        objs.append(obj)
+        if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), newest_hdr):
+            todo.append((src, obj))
+
+    def compile_one(so):
+        src, obj = so
+        tmp = obj + f".{os.getpid()}.tmp.o"
+        cmd = ["nvcc", *ARCH, *NVCC_FLAGS, "-c", src, "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, obj)
+
+    if todo:
+        with ThreadPoolExecutor(max_workers=jobs or min(8, len(todo))) as ex:
+            list(ex.map(compile_one, todo))
+    if force or todo or not os.path.exists(LIB_PATH):
+        tmp = LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_uint32),
+                ("tuning_file", ctypes.c_char_p), ("flags", ctypes.c_uint32)]
+
+
+def lib():
+    """Load libgcndecomp.so (it must have been built; there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_2107_07809_gb300.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, u64, i32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
+            L.gcn_decomp_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+            L.gcn_decomp_destroy.argtypes = [vp]
+            L.gcn_decomp_destroy.restype = None
+            L.gcn_decomp_submit_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(sz), sz,
+                                                  ctypes.POINTER(u64), ctypes.POINTER(sz)]
+            L.gcn_decomp_fetch_opencl.argtypes = [vp, u64, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(i32),
+                                                  ctypes.c_uint32]
+            L.gcn_decomp_fetch_ir.argtypes = [vp, u64, i32, vp, sz, ctypes.POINTER(sz)]
+            L.gcn_decomp_run_device.argtypes = [vp, vp, u64, vp, u64, vp]
+            L.gcn_decomp_result_device.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                   ctypes.POINTER(u64)]
+            L.gcn_decomp_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
+                                                 ctypes.POINTER(ctypes.c_char_p), i32]
+            L.gcn_decomp_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+class GcnDecompError(RuntimeError):
+    def __init__(self, rc: int, what: str):
+        msg = lib().gcn_decomp_last_error().decode(errors="replace")
+        super().__init__(f"{what} failed ({rc}): {msg}")
+        self.rc = rc
+
+
+def _ck(rc: int, what: str):
+    if rc != GCN_OK:
+        raise GcnDecompError(rc, what)
+
+
+class Decompiler:
+    """One handle: a CUDA stream plus device memory on ``device``."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_slots: int = 0):
+        self._h = ctypes.c_void_p()
+        cfg = Config(device, mem_budget_bytes, max_slots, None, 0)
+        _ck(lib().gcn_decomp_create(ctypes.byref(cfg), ctypes.byref(self._h)), "gcn_decomp_create")
+
+    def close(self):
+        if self._h:
+            lib().gcn_decomp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host-buffer API -----------------------------------------------------
+    def submit_batch(self, texts: list[bytes]) -> list[int]:
+        n = len(texts)
+        arr = (ctypes.c_char_p * n)(*texts)
+        lens = (ctypes.c_size_t * n)(*[len(t) for t in texts])
+        ids = (ctypes.c_uint64 * n)()
+        got = ctypes.c_size_t()
+        _ck(lib().gcn_decomp_submit_batch(self._h, arr, lens, n, ids, ctypes.byref(got)), "gcn_decomp_submit_batch")
+        return list(ids[: got.value])
+
+    def fetch_opencl(self, job: int, wait: bool = True) -> tuple[str, int]:
+        n = ctypes.c_size_t()
+        st = ctypes.c_int()
+        _ck(lib().gcn_decomp_fetch_opencl(self._h, job, None, 0, ctypes.byref(n), ctypes.byref(st), 1 if wait else 0),
+            "gcn_decomp_fetch_opencl")
+        buf = ctypes.create_string_buffer(max(n.value, 1))
+        _ck(lib().gcn_decomp_fetch_opencl(self._h, job, buf, n.value, ctypes.byref(n), ctypes.byref(st), 1 if wait else 0),
+            "gcn_decomp_fetch_opencl")
+        return buf.raw[: n.value].decode(), st.value
+
+    def fetch_ir(self, job: int, which: int) -> bytes:
+        n = ctypes.c_size_t()
+        _ck(lib().gcn_decomp_fetch_ir(self._h, job, which, None, 0, ctypes.byref(n)), "gcn_decomp_fetch_ir")
+        buf = ctypes.create_string_buffer(max(n.value, 1))
+        _ck(lib().gcn_decomp_fetch_ir(self._h, job, which, buf, n.value, ctypes.byref(n)), "gcn_decomp_fetch_ir")
+        return buf.raw[: n.value]
+
+    def decompile(self, texts: list[bytes]) -> list[tuple[str, int]]:
+        ids = self.submit_batch(texts)
+        return [self.fetch_opencl(j) for j in ids]
+
+    # ---- device-buffer API -----------------------------------------------------
+    def run_device(self, text_ptr: int, text_len: int, off_ptr: int, n_files: int, stream: int = 0):
+        _ck(lib().gcn_decomp_run_device(self._h, text_ptr, text_len, off_ptr, n_files, stream or None),
+            "gcn_decomp_run_device")
+
+    def result_device(self):
+        o, oo, st = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        nb = ctypes.c_uint64()
+        _ck(lib().gcn_decomp_result_device(self._h, ctypes.byref(o), ctypes.byref(oo), ctypes.byref(st),
+                                           ctypes.byref(nb)), "gcn_decomp_result_device")
+        return o.value, oo.value, st.value, nb.value
+
+    def stage_times(self) -> dict[str, float]:
+        ms = (ctypes.c_float * 16)()
+        nm = (ctypes.c_char_p * 16)()
+        n = lib().gcn_decomp_stage_times(self._h, ms, nm, 16)
+        return {nm[i].decode(): float(ms[i]) for i in range(max(n, 0))}

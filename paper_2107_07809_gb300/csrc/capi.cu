@@ -1,0 +1,558 @@
+// capi.cu — host orchestration of the CUDA stages and the C ABI of gcn_decomp.h.
+//
+// A handle owns one CUDA stream and a grow-only workspace of device arrays.
+// One pipeline run takes a batch of files that is resident in device memory
+// and executes the stages in order: S1 newline scan, S2 row segmentation,
+// S3 configuration, S4 decoding, S5 physical CFG, S6 logical CFG, S7/S8
+// dataflow, S9-S11 analysis, S12 regions, S13 emission.  The host reads back
+// four small counters between stages (lines, kernels/instructions, blocks,
+// output bytes) to size the next arrays; everything else stays on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gcn_decomp.h"
+#include "gd_kernels.h"
+
+using namespace gd;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+void set_err(const std::string& s) { g_err = s; }
+
+#define CK(x)                                                                   \
+  do {                                                                          \
+    cudaError_t e_ = (x);                                                       \
+    if (e_ != cudaSuccess) {                                                    \
+      set_err(std::string(#x) + ": " + cudaGetErrorString(e_));                 \
+      throw GCN_ECUDA;                                                          \
+    }                                                                           \
+  } while (0)
+
+struct Workspace {
+  struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+  };
+  std::map<std::string, Buf> bufs;
+  size_t total = 0;
+  uint64_t budget = 0;
+  template <class T>
+  T* get(const char* name, size_t n) {
+    size_t bytes = std::max<size_t>(n * sizeof(T), 256);
+    Buf& b = bufs[name];
+    if (b.cap < bytes) {
+      if (b.p) {
+        cudaFree(b.p);
+        total -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+      }
+      size_t want = bytes + bytes / 8;
+      if (budget && total + want > budget) {
+        set_err(std::string("memory budget exceeded allocating ") + name);
+        throw GCN_ENOMEM;
+      }
+      if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(std::string("cudaMalloc failed for ") + name);
+        throw GCN_ENOMEM;
+      }
+      b.cap = want;
+      total += want;
+    }
+    return (T*)b.p;
+  }
+  void release() {
+    for (auto& kv : bufs)
+      if (kv.second.p) cudaFree(kv.second.p);
+    bufs.clear();
+    total = 0;
+  }
+};
+
+const char* kStageNames[] = {"S1 tokenise", "S2 segment", "S3 config", "S4 decode", "S5 cfg", "S6 logical cfg",
+                             "S7-S8 dataflow", "S9-S11 analysis", "S12 regions", "S13 emit"};
+constexpr int kStages = 10;
+
+struct Run {
+  bool valid = false;
+  Batch b{};
+  std::vector<KHdr> kh;           // host copy (after the run)
+  std::vector<uint32_t> file_k0;  // first kernel of each file (F + 1)
+  uint64_t out_bytes = 0;
+};
+
+struct JobRec {
+  std::string text;  // OpenCL output
+  int status = 0;
+  uint32_t run_file = 0;
+  uint64_t run_id = 0;
+};
+
+}  // namespace
+
+struct gcn_decomp {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Workspace ws;
+  std::mutex mu;
+  Run run;
+  uint64_t run_id = 0;
+  uint64_t next_job = 1;
+  uint32_t max_slots = 65536;
+  std::map<uint64_t, JobRec> jobs;
+  cudaEvent_t ev[kStages + 1];
+  float stage_ms[kStages] = {0};
+  uint32_t* h_tot = nullptr;  // pinned counters
+};
+
+namespace {
+
+// the whole pipeline on a device-resident batch
+void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t* file_off, uint32_t F,
+                  cudaStream_t s) {
+  Workspace& W = h->ws;
+  Run& R = h->run;
+  R.valid = false;
+  Batch& b = R.b;
+  b = Batch{};
+  b.text = text;
+  b.text_len = n;
+  b.file_off = file_off;
+  b.F = F;
+  uint32_t* tot = W.get<uint32_t>("totals", 16);
+  uint32_t* err = W.get<uint32_t>("err", 4);
+  b.err = err;
+  CK(cudaMemsetAsync(err, 0, 16, s));
+  CK(cudaMemsetAsync(tot, 0, 64, s));
+  auto sync_totals = [&]() {
+    CK(cudaMemcpyAsync(h->h_tot, tot, 64, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  };
+  CK(cudaEventRecord(h->ev[0], s));
+  // S1
+  uint32_t* line_start = W.get<uint32_t>("line_start", n + 2);
+  uint64_t* tstat = W.get<uint64_t>("tile_status", std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)));
+  uint32_t* counters = W.get<uint32_t>("counters", 4);
+  launch_line_scan(text, n, line_start, tstat, counters, err, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[1], s));
+  uint32_t L = 0;
+  CK(cudaMemcpyAsync(&h->h_tot[8], counters + 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  L = h->h_tot[8];
+  b.L = L;
+  b.line_start = line_start;
+  ScanScratch sc{tstat, W.get<uint32_t>("scan_counter", 4)};
+  // S2
+  RowArrays ra;
+  ra.file_start = W.get<uint8_t>("file_start", L + 1);
+  ra.kind = W.get<uint8_t>("kind", L + 1);
+  ra.rowtype = W.get<uint8_t>("rowtype", L + 1);
+  ra.t0 = W.get<uint32_t>("t0", L + 1);
+  ra.t1 = W.get<uint32_t>("t1", L + 1);
+  ra.t2 = W.get<uint32_t>("t2", L + 1);
+  ra.mkmax = W.get<uint32_t>("mkmax", L + 1);
+  ra.fsmax = W.get<uint32_t>("fsmax", L + 1);
+  ra.kcnt = W.get<uint32_t>("kcnt", L + 1);
+  ra.instr_excl = W.get<uint32_t>("instr_excl", L + 1);
+  ra.label_excl = W.get<uint32_t>("label_excl", L + 1);
+  if (L) launch_rows(text, line_start, L, file_off, F, ra, sc, tot, err, s);
+  CK(cudaGetLastError());
+  sync_totals();
+  b.K = h->h_tot[0];
+  b.I = h->h_tot[1];
+  b.NL = h->h_tot[2];
+  b.rowtype = ra.rowtype;
+  b.file_start = ra.file_start;
+  b.kind = ra.kind;
+  b.kcnt = ra.kcnt;
+  b.kh = W.get<KHdr>("kh", b.K + 1);
+  b.args = W.get<ArgRec>("args", (size_t)b.K * kMaxArgs + 1);
+  b.instr_line = W.get<uint32_t>("instr_line", b.I + 1);
+  b.label_line = W.get<uint32_t>("label_line", b.NL + 1);
+  b.label_instr = W.get<uint32_t>("label_instr", b.NL + 1);
+  b.label_hash = W.get<uint32_t>("label_hash", b.NL + 1);
+  if (L) launch_scatter_rows(L, ra, b.instr_line, b.label_line, b.label_instr, b.kh, s);
+  CK(cudaEventRecord(h->ev[2], s));
+  // S3
+  launch_config(b, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[3], s));
+  // S4 + S5
+  b.ikern = W.get<uint32_t>("ikern", b.I + 1);
+  b.blen = W.get<uint32_t>("blen", b.I + 1);
+  b.ins = W.get<InstrRec>("ins", b.I + 1);
+  b.branch_hash = W.get<uint32_t>("branch_hash", b.I + 1);
+  b.branch_pos = W.get<uint32_t>("branch_pos", b.I + 1);
+  b.pleader = W.get<uint32_t>("pleader", b.I + 1);
+  b.lleader = W.get<uint32_t>("lleader", b.I + 1);
+  b.pblock_of = W.get<uint32_t>("pblock_of", b.I + 1);
+  launch_decode(b, sc, tot, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[4], s));
+  sync_totals();
+  b.NPB = h->h_tot[3];
+  b.pblocks = W.get<BlockRec>("pblocks", b.NPB + 1);
+  uint32_t* blk_kern = W.get<uint32_t>("blk_kern", std::max(b.NPB, b.I) + 1);
+  launch_pblocks(b, blk_kern, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[5], s));
+  // S6
+  b.ctl = W.get<uint8_t>("ctl", b.I + 1);
+  b.sense = W.get<uint8_t>("sense", b.I + 1);
+  b.ltarget = W.get<uint32_t>("ltarget", b.I + 1);
+  b.lblock_of = W.get<uint32_t>("lblock_of", b.I + 1);
+  launch_logical(b, sc, tot, s);
+  CK(cudaGetLastError());
+  sync_totals();
+  b.NLB = h->h_tot[4];
+  b.lblocks = W.get<BlockRec>("lblocks", b.NLB + 1);
+  b.lterm = W.get<uint32_t>("lterm", b.NLB + 1);
+  launch_lblocks(b, blk_kern, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[6], s));
+  // S7 + S8
+  DfScratch d{};
+  d.kstate = W.get<uint32_t>("kstate", b.K + 1);
+  d.kstate_off = W.get<uint32_t>("kstate_off", b.K + 1);
+  d.kbits = W.get<uint32_t>("kbits", b.K + 1);
+  d.bits_off = W.get<uint32_t>("bits_off", b.K + 1);
+  d.pcount = W.get<uint32_t>("pcount", b.NLB + 2);
+  d.blk_kern = blk_kern;
+  b.fused = W.get<uint8_t>("fused", b.I + 1);
+  b.co_idx = W.get<uint32_t>("co_idx", b.I + 1);
+  b.pred_off = W.get<uint32_t>("pred_off", b.NLB + 2);
+  b.pred_fill = W.get<uint32_t>("pred_fill", b.NLB + 1);
+  launch_df_counts(b, d, sc, tot, s);
+  CK(cudaGetLastError());
+  sync_totals();
+  b.NS = h->h_tot[5];
+  d.NW = h->h_tot[6];
+  uint32_t NE = h->h_tot[7];
+  b.preds = W.get<uint32_t>("preds", NE + 1);
+  b.idom = W.get<uint32_t>("idom", b.NLB + 1);
+  b.rpo = W.get<uint32_t>("rpo", b.NLB + 1);
+  b.scratch32 = W.get<uint32_t>("scratch32", b.NLB + 1);
+  d.rpo_index = W.get<uint32_t>("rpo_index", b.NLB + 1);
+  d.stack = W.get<uint32_t>("dfs_stack", b.NLB + 1);
+  d.child = W.get<uint8_t>("dfs_child", b.NLB + 1);
+  b.st_in = W.get<uint32_t>("st_in", b.NS + 1);
+  b.st_out = W.get<uint32_t>("st_out", b.NS + 1);
+  b.has_phi = W.get<uint8_t>("has_phi", b.NS + 1);
+  d.defbits = W.get<uint32_t>("defbits", d.NW + 1);
+  d.phibits = W.get<uint32_t>("phibits", d.NW + 1);
+  b.nodes = W.get<Node>("nodes", 4ull * b.I + 4);
+  launch_df_main(b, d, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[7], s));
+  // S9 - S11
+  b.uses = W.get<uint32_t>("uses", 4ull * b.I + 4);
+  b.nflag = W.get<uint8_t>("nflag", 4ull * b.I + 4);
+  b.ntype = W.get<uint8_t>("ntype", 4ull * b.I + 4);
+  b.var_of = W.get<int32_t>("var_of", 4ull * b.I + 4);
+  b.phi_used = W.get<uint8_t>("phi_used", b.NS + 1);
+  b.phi_type = W.get<uint8_t>("phi_type", b.NS + 1);
+  b.phi_var = W.get<int32_t>("phi_var", b.NS + 1);
+  b.var_type = W.get<uint8_t>("var_type", 4ull * b.I + b.NS + 4);
+  uint32_t* wlsz = W.get<uint32_t>("wl_size", b.K + 1);
+  uint32_t* wloff = W.get<uint32_t>("wl_off", b.K + 1);
+  launch_wl_size(b, wlsz, wloff, sc, &tot[9], s);
+  sync_totals();
+  uint32_t* wl = W.get<uint32_t>("wl", (size_t)h->h_tot[9] + 8);
+  launch_analysis(b, wl, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[8], s));
+  // S12
+  b.rg = W.get<uint32_t>("regions", 24ull * b.NLB + 24);
+  uint32_t* seen = W.get<uint32_t>("rg_seen", 2ull * b.NLB + 2);
+  uint32_t* rstk = W.get<uint32_t>("rg_stack", 4ull * b.NLB + 4);
+  uint8_t* alive = W.get<uint8_t>("rg_alive", 2ull * b.NLB + 2);
+  uint8_t* cond = W.get<uint8_t>("rg_cond", b.NLB + 1);
+  launch_regions(b, seen, rstk, alive, cond, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[9], s));
+  // S13
+  b.kout_len = W.get<uint32_t>("kout_len", b.K + 1);
+  b.kout_off = W.get<uint32_t>("kout_off", b.K + 1);
+  launch_emit_size(b, wl, rstk, s);
+  launch_emit_scan(b, sc, &tot[10], s);
+  CK(cudaGetLastError());
+  sync_totals();
+  uint32_t total = b.K ? h->h_tot[10] : 0;
+  b.out = W.get<uint8_t>("out", (size_t)total + 16);
+  b.file_out_off = W.get<uint64_t>("file_out_off", b.F + 2);
+  b.file_status = W.get<int32_t>("file_status", b.F + 1);
+  launch_emit_write(b, wl, rstk, total, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev[10], s));
+  R.out_bytes = total;
+  R.valid = true;
+}
+
+void finish_run(gcn_decomp* h, cudaStream_t s) {
+  Run& R = h->run;
+  Batch& b = R.b;
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&h->stage_ms[i], h->ev[i], h->ev[i + 1]);
+  uint32_t e = 0;
+  CK(cudaMemcpy(&e, b.err, 4, cudaMemcpyDeviceToHost));
+  if (e) {
+    set_err("device error flags " + std::to_string(e));
+    throw GCN_ECUDA;
+  }
+  R.kh.resize(b.K);
+  if (b.K) CK(cudaMemcpy(R.kh.data(), b.kh, sizeof(KHdr) * b.K, cudaMemcpyDeviceToHost));
+  R.file_k0.assign(b.F + 1, 0);
+  // kernels are in file order: first kernel of each file
+  uint32_t k = 0;
+  for (uint32_t f = 0; f <= b.F; ++f) {
+    while (k < b.K && R.kh[k].file < f) ++k;
+    R.file_k0[f] = k;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gcn_decomp_last_error(void) { return g_err.c_str(); }
+
+int gcn_decomp_create(const gcn_decomp_config* cfg, gcn_decomp_t** out) {
+  if (!cfg || !out) {
+    set_err("NULL argument");
+    return GCN_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    set_err("no such CUDA device");
+    return GCN_EINVAL;
+  }
+  gcn_decomp* h = new gcn_decomp;
+  try {
+    h->device = cfg->device;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    for (auto& e : h->ev) CK(cudaEventCreate(&e));
+    CK(cudaMallocHost(&h->h_tot, 64));
+    CK(cudaDeviceSetLimit(cudaLimitStackSize, 16384));
+    h->ws.budget = cfg->mem_budget_bytes;
+    if (cfg->max_slots) h->max_slots = cfg->max_slots;
+    init_decode_tables();
+    CK(cudaGetLastError());
+  } catch (int rc) {
+    gcn_decomp_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return GCN_OK;
+}
+
+void gcn_decomp_destroy(gcn_decomp_t* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  h->ws.release();
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->h_tot) cudaFreeHost(h->h_tot);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int gcn_decomp_run_device(gcn_decomp_t* h, const uint8_t* d_text, uint64_t text_len, const uint64_t* d_file_off,
+                          uint64_t n_files, void* stream) {
+  if (!h || (!d_text && text_len) || !d_file_off || text_len >= (1ull << 32) || n_files >= (1ull << 31)) {
+    set_err("bad argument");
+    return GCN_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  try {
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    run_pipeline(h, d_text, text_len, d_file_off, (uint32_t)n_files, s);
+    ++h->run_id;
+  } catch (int rc) {
+    h->run.valid = false;
+    return rc;
+  }
+  return GCN_OK;
+}
+
+int gcn_decomp_result_device(gcn_decomp_t* h, const uint8_t** d_out, const uint64_t** d_out_off,
+                             const int32_t** d_status, uint64_t* out_bytes) {
+  if (!h || !h->run.valid) {
+    set_err("no completed run");
+    return GCN_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  try {
+    finish_run(h, h->stream);
+  } catch (int rc) {
+    return rc;
+  }
+  if (d_out) *d_out = h->run.b.out;
+  if (d_out_off) *d_out_off = h->run.b.file_out_off;
+  if (d_status) *d_status = h->run.b.file_status;
+  if (out_bytes) *out_bytes = h->run.out_bytes;
+  return GCN_OK;
+}
+
+int gcn_decomp_submit_batch(gcn_decomp_t* h, const char* const* text, const size_t* len, size_t n,
+                            uint64_t* job_ids, size_t* n_admitted) {
+  if (!h || (n && (!text || !len || !job_ids))) {
+    set_err("bad argument");
+    return GCN_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (n_admitted) *n_admitted = 0;
+  size_t take = std::min<size_t>(n, h->max_slots > h->jobs.size() ? h->max_slots - h->jobs.size() : 0);
+  if (n && !take) {
+    set_err("no free job slot");
+    return GCN_EAGAIN;
+  }
+  try {
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    // stage the files (each ending with '\n') in pinned memory, copy to the device
+    std::vector<uint64_t> off(take + 1, 0);
+    for (size_t i = 0; i < take; ++i) {
+      size_t l = len[i];
+      bool nl = l && text[i][l - 1] == '\n';
+      off[i + 1] = off[i] + l + ((l && !nl) ? 1 : 0);
+    }
+    uint64_t N = off[take];
+    if (N >= (1ull << 32)) {
+      set_err("batch text exceeds 4 GiB");
+      throw GCN_ENOMEM;
+    }
+    uint8_t* hbuf = nullptr;
+    CK(cudaMallocHost(&hbuf, std::max<uint64_t>(N, 1)));
+    for (size_t i = 0; i < take; ++i) {
+      memcpy(hbuf + off[i], text[i], len[i]);
+      if (off[i + 1] - off[i] > len[i]) hbuf[off[i + 1] - 1] = '\n';
+    }
+    uint8_t* d_text = h->ws.get<uint8_t>("in_text", N + 16);
+    uint64_t* d_off = h->ws.get<uint64_t>("in_off", take + 1);
+    CK(cudaMemcpyAsync(d_text, hbuf, N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_off, off.data(), sizeof(uint64_t) * (take + 1), cudaMemcpyHostToDevice, s));
+    run_pipeline(h, d_text, N, d_off, (uint32_t)take, s);
+    finish_run(h, s);
+    ++h->run_id;
+    CK(cudaFreeHost(hbuf));
+    // results to host memory, one record per job
+    const Run& R = h->run;
+    std::vector<uint64_t> fo(take + 1, 0);
+    std::vector<int32_t> st(take, 0);
+    std::string out;
+    if (R.b.file_out_off) {
+      CK(cudaMemcpy(fo.data(), R.b.file_out_off, sizeof(uint64_t) * (take + 1), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(st.data(), R.b.file_status, sizeof(int32_t) * take, cudaMemcpyDeviceToHost));
+      out.resize(fo[take]);
+      if (fo[take]) CK(cudaMemcpy(&out[0], R.b.out, fo[take], cudaMemcpyDeviceToHost));
+    }
+    for (size_t i = 0; i < take; ++i) {
+      JobRec j;
+      j.text = out.substr(fo[i], fo[i + 1] - fo[i]);
+      j.status = st[i];
+      j.run_file = (uint32_t)i;
+      j.run_id = h->run_id;
+      uint64_t id = h->next_job++;
+      h->jobs[id] = std::move(j);
+      job_ids[i] = id;
+    }
+    if (n_admitted) *n_admitted = take;
+  } catch (int rc) {
+    return rc;
+  }
+  return GCN_OK;
+}
+
+int gcn_decomp_fetch_opencl(gcn_decomp_t* h, uint64_t job_id, char* buf, size_t cap, size_t* len_out,
+                            int* status_out, uint32_t flags) {
+  (void)flags;
+  if (!h) return GCN_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->jobs.find(job_id);
+  if (it == h->jobs.end()) {
+    set_err("unknown job");
+    return GCN_ENOJOB;
+  }
+  if (len_out) *len_out = it->second.text.size();
+  if (status_out) *status_out = it->second.status;
+  if (!buf) return GCN_OK;
+  if (cap < it->second.text.size()) {
+    set_err("buffer too small");
+    return GCN_EINVAL;
+  }
+  memcpy(buf, it->second.text.data(), it->second.text.size());
+  h->jobs.erase(it);
+  return GCN_OK;
+}
+
+int gcn_decomp_fetch_ir(gcn_decomp_t* h, uint64_t job_id, int which, void* buf, size_t cap, size_t* len_out) {
+  if (!h || which < 0 || which > 5) return GCN_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->jobs.find(job_id);
+  if (it == h->jobs.end() || it->second.run_id != h->run_id || !h->run.valid) {
+    set_err("job unknown or no longer resident");
+    return GCN_ENOJOB;
+  }
+  const Run& R = h->run;
+  const Batch& b = R.b;
+  uint32_t f = it->second.run_file;
+  std::vector<uint8_t> v;
+  try {
+    for (uint32_t k = R.file_k0[f]; k < R.file_k0[f + 1]; ++k) {
+      const KHdr& K = R.kh[k];
+      auto grab = [&](const void* dev, size_t bytes) {
+        size_t o = v.size();
+        v.resize(o + bytes);
+        if (bytes) CK(cudaMemcpy(v.data() + o, dev, bytes, cudaMemcpyDeviceToHost));
+      };
+      bool lbad = (K.bad & ~3u) != 0 || (K.bad & 3u) != 0;
+      switch (which) {
+        case 0: if (!(K.bad & 1u)) grab(b.ins + K.first_instr, sizeof(InstrRec) * K.n_instr); break;
+        case 1: if (!(K.bad & 1u)) grab(b.pblock_of + K.first_instr, 4ull * K.n_instr); break;
+        case 2: if (!(K.bad & 1u)) grab(b.pblocks + K.first_pblock, sizeof(BlockRec) * K.n_pblock); break;
+        case 3: if (!lbad) grab(b.lblock_of + K.first_instr, 4ull * K.n_instr); break;
+        case 4: if (!lbad) grab(b.lblocks + K.first_lblock, sizeof(BlockRec) * K.n_lblock); break;
+        case 5: {
+          uint32_t hd[8] = {K.dims, K.cws[0], K.cws[1], K.cws[2], K.sgprs, K.vgprs, K.useargs, K.nuser};
+          size_t o = v.size();
+          v.resize(o + sizeof hd);
+          memcpy(v.data() + o, hd, sizeof hd);
+          break;
+        }
+      }
+    }
+  } catch (int rc) {
+    return rc;
+  }
+  if (len_out) *len_out = v.size();
+  if (!buf) return GCN_OK;
+  if (cap < v.size()) return GCN_EINVAL;
+  memcpy(buf, v.data(), v.size());
+  return GCN_OK;
+}
+
+int gcn_decomp_stage_times(gcn_decomp_t* h, float* ms, const char** names, int cap) {
+  if (!h || cap < 0) return GCN_EINVAL;
+  int n = std::min(cap, kStages);
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = h->stage_ms[i];
+    if (names) names[i] = kStageNames[i];
+  }
+  return n;
+}
+
+}  // extern "C"

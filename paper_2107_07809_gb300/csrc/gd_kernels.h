@@ -1,0 +1,145 @@
+// gd_kernels.h — host-side launchers of the CUDA stages (one translation unit each).
+#pragma once
+#include "gd_common.cuh"
+
+namespace gd {
+
+// line kinds and row types
+enum : uint8_t { LK_BLANK = 0, LK_KERNEL = 1, LK_CONFIG = 2, LK_TEXT = 3, LK_LABEL = 4, LK_ROW = 5 };
+enum : uint8_t { RT_NONE = 0, RT_CFG = 1, RT_LABEL = 2, RT_INSTR = 3, RT_KERNEL = 4 };
+
+struct ScanScratch {
+  uint64_t* status;   // >= scan_tiles(n) words
+  uint32_t* counter;  // 1 word
+};
+
+struct RowArrays {    // per line
+  uint8_t* file_start;
+  uint8_t* kind;
+  uint8_t* rowtype;
+  uint32_t *t0, *t1, *t2;
+  uint32_t *mkmax, *fsmax, *kcnt, *instr_excl, *label_excl;
+};
+
+// everything the per-kernel stages read and write (device pointers)
+struct Batch {
+  const uint8_t* text;
+  uint64_t text_len;
+  const uint64_t* file_off;
+  uint32_t F, L, K, I, NL;       // files, lines, kernels, instructions, labels
+  uint32_t NPB, NLB;             // physical / logical blocks
+  uint64_t NS;                   // block x register state words
+  const uint32_t* line_start;
+  const uint8_t* rowtype;
+  const uint8_t* file_start;
+  const uint8_t* kind;
+  KHdr* kh;
+  ArgRec* args;                  // K * kMaxArgs
+  uint32_t* instr_line;          // I
+  uint32_t* ikern;               // I: kernel of each instruction
+  uint32_t* blen;                // I: length of a branch's label operand
+  const uint32_t* kcnt;          // L: running count of .kernel rows
+  uint32_t* label_line;          // NL
+  uint32_t* label_instr;         // NL (global instruction index)
+  uint32_t* label_hash;          // NL
+  InstrRec* ins;                 // I
+  uint32_t* branch_hash;         // I (label name hash of a branch)
+  uint32_t* branch_pos;          // I (byte offset | len<<24 of the label operand)
+  // physical CFG
+  uint32_t* pleader;             // I (scratch flag / scan)
+  uint32_t* pblock_of;           // I (kernel-relative)
+  BlockRec* pblocks;             // NPB
+  // logical CFG
+  uint8_t* ctl;                  // I
+  uint8_t* sense;                // I
+  uint32_t* ltarget;             // I (kernel-relative)
+  uint32_t* lleader;             // I
+  uint32_t* lblock_of;           // I (kernel-relative, kNone = dropped)
+  BlockRec* lblocks;             // NLB (kernel-relative indices)
+  uint32_t* lterm;               // NLB (kernel-relative instruction)
+  // dataflow
+  uint8_t* fused;                // I
+  uint32_t* co_idx;              // I (kernel-relative)
+  uint32_t* pred_off;            // NLB + 1 (global)
+  uint32_t* preds;               // (kernel-relative block ids)
+  uint32_t* pred_fill;           // NLB
+  uint32_t* idom;                // NLB (kernel-relative)
+  uint32_t* rpo;                 // NLB (kernel-relative, per-kernel order)
+  uint32_t* df_off;              // NLB + 1
+  uint32_t* df;                  // dominance frontier lists
+  uint32_t* scratch32;           // NLB (dfs stacks etc.)
+  uint32_t* st_in;               // NS
+  uint32_t* st_out;              // NS
+  uint8_t* has_phi;              // NS
+  Node* nodes;                   // 4 * I
+  // analysis
+  uint8_t* ncls;                 // 4 * I
+  uint8_t* nclsk;                // 4 * I
+  uint32_t* mem_arg;             // I: matched argument (kNone = raw address)
+  uint32_t* mem_idx;             // I: index value reference (kTop = constant 0)
+  uint32_t* uses;                // 4 * I
+  uint8_t* nflag;                // 4 * I: 1 reach, 2 cross-block, 4 join input
+  uint8_t* ntype;                // 4 * I
+  int32_t* var_of;               // 4 * I
+  uint8_t* phi_used;             // NS
+  uint8_t* phi_type;             // NS
+  int32_t* phi_var;              // NS
+  uint8_t* var_type;             // per kernel: at most 4*I + NS ... (indexed by var_base + v)
+  uint32_t* var_base;            // K
+  uint64_t* wl;                  // reachability work lists
+  // regions
+  uint32_t* rg;                  // region records, 12 words per region
+  // emission
+  uint32_t* kout_len;            // K (text length of each kernel incl. separator)
+  uint32_t* kout_off;            // K (exclusive scan)
+  uint8_t* out;                  // output text
+  uint64_t* file_out_off;        // F + 1
+  int32_t* file_status;          // F
+  uint32_t* err;
+};
+
+// k_text.cu
+uint32_t line_scan_tiles(uint64_t n);
+uint32_t scan_tiles(uint32_t n);
+void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uint64_t* tile_status,
+                      uint32_t* counters, uint32_t* err, cudaStream_t s);
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t n, int op, bool inclusive, ScanScratch sc,
+                 uint32_t* total_out, uint32_t* err, cudaStream_t s);
+void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, const uint64_t* file_off, uint32_t F,
+                 RowArrays& ra, ScanScratch sc, uint32_t* totals, uint32_t* err, cudaStream_t s);
+void launch_scatter_rows(uint32_t L, RowArrays& ra, uint32_t* instr_line, uint32_t* label_line, uint32_t* label_instr,
+                         KHdr* kh, cudaStream_t s);
+
+// k_decode.cu
+void init_decode_tables();
+void launch_config(Batch& b, cudaStream_t s);
+void launch_decode(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s);
+void launch_pblocks(Batch& b, uint32_t* blk_kern, cudaStream_t s);
+void launch_logical(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s);
+void launch_lblocks(Batch& b, uint32_t* blk_kern, cudaStream_t s);
+
+// k_dataflow.cu
+struct DfScratch {
+  uint32_t *kstate, *kstate_off, *kbits, *bits_off;  // K
+  uint32_t *pcount, *blk_kern;                       // NLB + 1
+  uint32_t *rpo_index, *stack;                       // NLB
+  uint8_t* child;                                    // NLB
+  uint32_t *defbits, *phibits;                       // NW
+  uint32_t NW;
+};
+void launch_df_counts(Batch& b, DfScratch& d, ScanScratch sc, uint32_t* totals, cudaStream_t s);
+void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s);
+
+// k_analysis.cu
+void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint32_t* total, cudaStream_t s);
+void launch_analysis(Batch& b, uint32_t* wl, cudaStream_t s);
+
+// k_region.cu
+void launch_regions(Batch& b, uint32_t* seen, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s);
+
+// k_emit.cu
+void launch_emit_size(Batch& b, uint32_t* scratch, uint32_t* stk, cudaStream_t s);
+void launch_emit_scan(Batch& b, ScanScratch sc, uint32_t* total, cudaStream_t s);
+void launch_emit_write(Batch& b, uint32_t* scratch, uint32_t* stk, uint32_t total, cudaStream_t s);
+
+}  // namespace gd

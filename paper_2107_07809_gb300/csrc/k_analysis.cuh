@@ -1,0 +1,262 @@
+// k_analysis.cuh — device functions shared by the analysis (S9-S11) and
+// emission (S13) kernels of the CUDA path: value forwarding, system-value and
+// argument classification, memory-access matching, node types.
+#pragma once
+#include "gd_kernels.h"
+
+namespace gd {
+
+// kernel view: node / argument arrays of one kernel
+struct KView {
+  const Batch* b;
+  const KHdr* K;
+  const Node* N;      // b.nodes + 4 * first_instr
+  const ArgRec* A;    // b.args + k * kMaxArgs
+  uint32_t k;
+  __device__ const Node& node(uint32_t id) const { return N[id]; }
+};
+
+__device__ __forceinline__ bool is_copy_node(const Node& n) {
+  return n.kind == N_OP && (n.op == O_V_MOV_B32 || n.op == O_S_MOV_B32 || n.op == O_BUFFER_STORE_DWORD ||
+                            n.op == O_BUFFER_LOAD_DWORD);
+}
+
+// a copy is the value it copies; the halves of a split pair are its sources;
+// a pair of the low and high part of one 64-bit value is that value
+static __device__ uint32_t fwd_d(const KView& v, uint32_t r, int depth) {
+  for (int step = 0; step < 512 && depth < 64; ++step) {
+    if (r == kTop) return kUndef;
+    if (!r_node(r)) return r;
+    const Node& n = v.node(rid(r));
+    uint32_t part = rpart(r);
+    if (is_copy_node(n) && part == PART_ENTIRE) {
+      r = n.src[0];
+      continue;
+    }
+    if (n.kind == N_PAIR) {
+      if (part == PART_LO) { r = n.src[0]; continue; }
+      if (part == PART_HI) { r = n.src[1]; continue; }
+      uint32_t lo = fwd_d(v, n.src[0], depth + 1), hi = fwd_d(v, n.src[1], depth + 1);
+      if ((r_node(lo) || r_leaf(lo)) && rpart(lo) == PART_LO && hi == ((lo & ~3u) | PART_HI)) return lo & ~3u;
+      return r;
+    }
+    return r;
+  }
+  return r;
+}
+__device__ __forceinline__ uint32_t fwd(const KView& v, uint32_t r) { return fwd_d(v, r, 0); }
+
+// classes of values
+enum : uint8_t { K_NONE = 0, K_LID, K_GRP, K_KARG, K_UNDEF, K_GOFS64, K_GOFSLO, K_MULGRP, K_GIDNO, K_GID, K_ARGPTR,
+                 K_ARG32, K_ARG64, K_CONST32, K_CONST64 };
+struct Cls {
+  uint8_t c, k;
+};
+__device__ __forceinline__ bool leaf_like(uint8_t c) { return c != K_NONE && c != K_MULGRP; }
+__device__ __forceinline__ bool ty64(uint8_t t) { return t == TY_LONG || t == TY_ULONG || t == TY_DOUBLE || t == TY_TOP64; }
+__device__ __forceinline__ int ilog2_exact(uint32_t x) {
+  return (x && !(x & (x - 1)) && x < (1u << 31)) ? (31 - __clz(x)) : -1;
+}
+
+static __device__ Cls classify(const KView& v, uint32_t r);
+
+static __device__ Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide) {
+  Cls none{K_NONE, 0};
+  Cls base = classify(v, fwd(v, n.src[0]));
+  if (base.c != K_KARG || (n.cval & 7u)) return none;
+  uint32_t slot = n.cval / 8;
+  if (slot >= v.K->nargs) return none;
+  const ArgRec& a = v.A[slot];
+  if (wide) {
+    if (a.hidden && a.gofs) {
+      if (part == PART_ENTIRE) return Cls{K_GOFS64, (uint8_t)(a.gofs - 1)};
+      if (part == PART_LO) return Cls{K_GOFSLO, (uint8_t)(a.gofs - 1)};
+      return none;
+    }
+    if (a.hidden || part != PART_ENTIRE) return none;
+    if (a.pointer) return Cls{K_ARGPTR, (uint8_t)slot};
+    if (ty64(a.elem)) return Cls{K_ARG64, (uint8_t)slot};
+    return none;
+  }
+  if (a.hidden || a.pointer || ty64(a.elem) || part != PART_ENTIRE) return none;
+  return Cls{K_ARG32, (uint8_t)slot};
+}
+
+__device__ __forceinline__ int64_t const_of(const KView& v, uint32_t r) {
+  uint32_t s = fwd(v, r);
+  if (!r_node(s) || rpart(s) != PART_ENTIRE) return -1;
+  const Node& n = v.node(rid(s));
+  return n.kind == N_CONST ? (int64_t)n.cval : -1;
+}
+
+static __device__ Cls classify(const KView& v, uint32_t r) {
+  Cls none{K_NONE, 0};
+  if (r == kUndef || r == kTop) return Cls{K_UNDEF, 0};
+  if (r_leaf(r)) {
+    uint32_t id = rid(r) & 0x0FFFFFFFu;
+    uint32_t kind = id >> 8, k = id & 0xFF;
+    if (rpart(r) != PART_ENTIRE) return none;
+    if (kind == LEAF_LID) return Cls{K_LID, (uint8_t)k};
+    if (kind == LEAF_GRP) return Cls{K_GRP, (uint8_t)k};
+    if (kind == LEAF_KARG) return Cls{K_KARG, 0};
+    return none;
+  }
+  if (!r_node(r)) return none;
+  const Node& n = v.node(rid(r));
+  uint32_t part = rpart(r);
+  if (n.kind == N_CONST) return Cls{K_CONST32, 0};
+  if (n.kind == N_PAIR && part == PART_ENTIRE) {
+    Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1]));
+    return (a.c == K_CONST32 && b.c == K_CONST32) ? Cls{K_CONST64, 0} : none;
+  }
+  if (n.kind == N_SLOAD64B) return settings_load(v, n, part, true);
+  if (n.kind != N_OP) return none;
+  if (n.op == O_S_LOAD_DWORDX2 || n.op == O_S_LOAD_DWORDX4) return settings_load(v, n, part, true);
+  if (n.op == O_S_LOAD_DWORD) return settings_load(v, n, part, false);
+  if (part != PART_ENTIRE) return none;
+  const uint32_t* cws = v.K->cws;
+  auto cw = [&](int d) -> int64_t { return d < 3 ? (int64_t)cws[d] : -1; };
+  switch (n.op) {
+    case O_S_MUL_I32: {
+      Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1]));
+      if (a.c == K_GRP && const_of(v, n.src[1]) == cw(a.k)) return Cls{K_MULGRP, a.k};
+      if (b.c == K_GRP && const_of(v, n.src[0]) == cw(b.k)) return Cls{K_MULGRP, b.k};
+      return none;
+    }
+    case O_S_LSHL_B32: {
+      Cls a = classify(v, fwd(v, n.src[0]));
+      if (a.c == K_GRP) {
+        int l = ilog2_exact((uint32_t)cw(a.k));
+        if (l >= 0 && const_of(v, n.src[1]) == l) return Cls{K_MULGRP, a.k};
+      }
+      return none;
+    }
+    case O_V_ADD_U32: {
+      Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1]));
+      if (a.c == K_MULGRP && b.c == K_LID && a.k == b.k) return Cls{K_GIDNO, a.k};
+      if (b.c == K_MULGRP && a.c == K_LID && a.k == b.k) return Cls{K_GIDNO, a.k};
+      if (a.c == K_GIDNO && b.c == K_GOFSLO && a.k == b.k) return Cls{K_GID, a.k};
+      if (b.c == K_GIDNO && a.c == K_GOFSLO && a.k == b.k) return Cls{K_GID, a.k};
+      return none;
+    }
+    case O_V_MAD_U32_U24: {
+      Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1])), c = classify(v, fwd(v, n.src[2]));
+      if (c.c != K_LID) return none;
+      if (a.c == K_GRP && a.k == c.k && const_of(v, n.src[1]) == cw(a.k)) return Cls{K_GIDNO, a.k};
+      if (b.c == K_GRP && b.k == c.k && const_of(v, n.src[0]) == cw(b.k)) return Cls{K_GIDNO, b.k};
+      return none;
+    }
+  }
+  return none;
+}
+
+// memory access: argument pointer + (32-bit index, extended) << log2(element size)
+struct Mem {
+  bool ok;
+  uint32_t arg;
+  uint32_t idx;  // kTop = constant 0
+};
+
+static __device__ Mem match_addr(const KView& v, uint32_t addr, uint32_t width) {
+  Mem m{false, kNone, kTop};
+  Cls c = classify(v, addr);
+  if (c.c == K_ARGPTR) {
+    if ((ty64(v.A[c.k].elem) ? 8u : 4u) != width) return m;
+    m.ok = true;
+    m.arg = c.k;
+    return m;
+  }
+  if (!r_node(addr) || rpart(addr) != PART_ENTIRE) return m;
+  const Node& n = v.node(rid(addr));
+  if (n.kind != N_OP || n.op != O_V_ADDC_CO_U32 || !n.fused) return m;
+  for (int o = 0; o < 2; ++o) {
+    uint32_t X = fwd(v, n.src[o]), Y = fwd(v, n.src[1 - o]);
+    Cls cx = classify(v, X);
+    if (cx.c != K_ARGPTR) continue;
+    uint32_t es = ty64(v.A[cx.k].elem) ? 8u : 4u;
+    if (es != width) continue;
+    if (!r_node(Y) || rpart(Y) != PART_ENTIRE) continue;
+    const Node& sh = v.node(rid(Y));
+    if (sh.kind != N_OP || sh.op != O_V_LSHLREV_B64) continue;
+    if (const_of(v, sh.src[0]) != ilog2_exact(es)) continue;
+    uint32_t V = fwd(v, sh.src[1]);
+    if (!r_node(V) || rpart(V) != PART_ENTIRE || v.node(rid(V)).kind != N_PAIR) continue;
+    const Node& p = v.node(rid(V));
+    uint32_t lo = fwd(v, p.src[0]), hi = fwd(v, p.src[1]);
+    bool ext = false;
+    if (r_node(hi) && rpart(hi) == PART_ENTIRE && v.node(rid(hi)).kind == N_CONST && v.node(rid(hi)).cval == 0)
+      ext = true;
+    if (r_node(hi) && rpart(hi) == PART_ENTIRE) {
+      const Node& a = v.node(rid(hi));
+      if (a.kind == N_OP && a.op == O_V_ASHRREV_I32 && const_of(v, a.src[0]) == 31 && fwd(v, a.src[1]) == lo)
+        ext = true;
+    }
+    if (!ext) continue;
+    m.ok = true;
+    m.arg = cx.k;
+    m.idx = lo;
+    return m;
+  }
+  return m;
+}
+
+__device__ __forceinline__ bool op_store(uint16_t op) { return op == O_GLOBAL_STORE_DWORD || op == O_GLOBAL_STORE_DWORDX2; }
+__device__ __forceinline__ bool op_gload(uint16_t op) { return op == O_GLOBAL_LOAD_DWORD || op == O_GLOBAL_LOAD_DWORDX2; }
+__device__ __forceinline__ bool op_vcmp(uint16_t op) { return op >= O_V_CMP0 && op < O_V_CMP0 + 18; }
+__device__ __forceinline__ bool op_scmp(uint16_t op) { return op >= O_S_CMP0 && op < O_S_CMP0 + 12; }
+__device__ __forceinline__ bool op_wide(uint16_t op) {
+  return op == O_S_LOAD_DWORDX2 || op == O_V_CVT_F64_F32 || op == O_V_CVT_F64_I32 || op == O_V_LSHLREV_B64 ||
+         op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2;
+}
+
+__device__ __forceinline__ int node_width(const KView& v, uint32_t id) {
+  const Node& n = v.node(id);
+  if (n.kind == N_PAIR || n.kind == N_SLOAD64B) return 64;
+  if (n.kind == N_OP) {
+    if (op_wide(n.op) || n.op == O_S_LOAD_DWORDX4) return 64;
+    if ((n.op == O_V_ADDC_CO_U32 || n.op == O_V_SUBB_CO_U32) && n.fused) return 64;
+  }
+  return 32;
+}
+
+__device__ __forceinline__ uint8_t tjoin(uint8_t a, uint8_t b) {
+  if (a == TY_NONE) return b;
+  if (b == TY_NONE) return a;
+  if (a == b) return a;
+  return (ty64(a) || ty64(b)) ? TY_TOP64 : TY_TOP32;
+}
+__device__ __forceinline__ uint8_t tresolve(uint8_t t, int width) {
+  if (t == TY_NONE) return width == 64 ? TY_ULONG : TY_UINT;
+  if (t == TY_TOP32) return TY_UINT;
+  if (t == TY_TOP64) return TY_ULONG;
+  return t;
+}
+
+// children printed with a node (after forwarding); returns the count (<= 3)
+static __device__ int node_children(const KView& v, uint32_t id, uint32_t* ch) {
+  const Node& n = v.node(id);
+  if (leaf_like(classify(v, mkref(id, PART_ENTIRE)).c)) return 0;
+  int c = 0;
+  if (n.kind == N_PAIR) {
+    ch[c++] = fwd(v, n.src[0]);
+    ch[c++] = fwd(v, n.src[1]);
+    return c;
+  }
+  if (n.kind != N_OP) return 0;
+  if (op_gload(n.op) || op_store(n.op)) {
+    uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
+    Mem m = match_addr(v, fwd(v, n.src[0]), w);
+    if (m.ok) {
+      if (m.idx != kTop) ch[c++] = m.idx;
+    } else {
+      ch[c++] = fwd(v, n.src[0]);
+    }
+    if (op_store(n.op)) ch[c++] = fwd(v, n.src[1]);
+    return c;
+  }
+  if (n.op == O_UNKNOWN || n.op == O_S_LOAD_DWORD || n.op == O_S_LOAD_DWORDX2 || n.op == O_S_LOAD_DWORDX4) return 0;
+  for (int q = 0; q < n.nsrc && q < 3; ++q) ch[c++] = fwd(v, n.src[q]);
+  return c;
+}
+
+}  // namespace gd

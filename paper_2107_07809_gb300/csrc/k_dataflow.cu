@@ -1,0 +1,637 @@
+// k_dataflow.cu — S7/S8: register versions and expression nodes.
+//
+// The paper assigns versions to registers and creates variables where a
+// block with several predecessors sees different versions ("Search for
+// control structures", last paragraphs).  The placement computed here is the
+// minimal one: register r gets a new version at block B exactly when B is in
+// the iterated dominance frontier of r's defining blocks (the entry defines
+// every register with its ABI value).  GPU mapping:
+//   - definitions and 64-bit carry pairs: one thread per instruction;
+//   - dominators (reverse postorder + iterative intersection): one thread per kernel;
+//   - the frontier closure for all registers at once: one warp per kernel, each
+//     lane owns 32 registers of a bitset, walking the frontier paths together;
+//   - values: the same warp walks blocks in reverse postorder, lanes over registers;
+//   - nodes: one thread per instruction, scanning back inside its block.
+#include "gd_kernels.h"
+
+namespace gd {
+
+struct RegMap {
+  uint32_t vg, sg;
+  __device__ __forceinline__ uint32_t v(uint32_t i) const { return i; }
+  __device__ __forceinline__ uint32_t s(uint32_t i) const { return vg + i; }
+  __device__ __forceinline__ uint32_t vcc() const { return vg + sg; }
+  __device__ __forceinline__ uint32_t scc() const { return vg + sg + 1; }
+  __device__ __forceinline__ uint32_t spill(uint32_t k) const { return vg + sg + 2 + k; }
+};
+
+struct Def {
+  uint32_t reg, val;
+};
+
+__device__ __forceinline__ bool vcmp(uint16_t op) { return op >= O_V_CMP0 && op < O_V_CMP0 + 18; }
+__device__ __forceinline__ bool scmp(uint16_t op) { return op >= O_S_CMP0 && op < O_S_CMP0 + 12; }
+__device__ __forceinline__ bool wide_result(uint16_t op) {
+  return op == O_S_LOAD_DWORDX2 || op == O_V_CVT_F64_F32 || op == O_V_CVT_F64_I32 || op == O_V_LSHLREV_B64 ||
+         op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2;
+}
+
+// register index of the first register of an operand word (v/s/vcc)
+__device__ __forceinline__ uint32_t reg_of(const RegMap& M, uint32_t o, uint32_t k) {
+  uint32_t tg = otag(o);
+  if (tg == TG_VGPR) return M.v(opay(o) + k);
+  if (tg == TG_SGPR) return M.s(opay(o) + k);
+  return M.vcc();
+}
+
+// definitions of kernel-relative instruction i (at most 4)
+__device__ int idefs(const Batch& b, const KHdr& K, const RegMap& M, uint32_t i, Def* d) {
+  uint32_t gi = K.first_instr + i;
+  if (b.ctl[gi] != C_NORMAL) return 0;
+  const InstrRec& r = b.ins[gi];
+  uint32_t base = 4 * i;
+  int n = 0;
+  switch (r.op) {
+    case O_S_WAITCNT: case O_GLOBAL_STORE_DWORD: case O_GLOBAL_STORE_DWORDX2: return 0;
+    case O_S_LOAD_DWORD: d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)}; return n;
+    case O_S_LOAD_DWORDX4:
+      d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_LO)};
+      d[n++] = {reg_of(M, r.opnd[0], 1), mkref(base, PART_HI)};
+      d[n++] = {reg_of(M, r.opnd[0], 2), mkref(base + 1, PART_LO)};
+      d[n++] = {reg_of(M, r.opnd[0], 3), mkref(base + 1, PART_HI)};
+      return n;
+    case O_S_ADD_U32: case O_S_MUL_I32: case O_S_LSHL_B32:
+      d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)};
+      d[n++] = {M.scc(), kUndef};
+      return n;
+    case O_V_ADD_CO_U32: case O_V_SUB_CO_U32:
+      d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)};
+      d[n++] = {M.vcc(), mkref(base + 3, PART_ENTIRE)};
+      return n;
+    case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32:
+      if (b.fused[gi]) {
+        const InstrRec& lo = b.ins[K.first_instr + b.co_idx[gi]];
+        d[n++] = {reg_of(M, lo.opnd[0], 0), mkref(base, PART_LO)};
+        d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_HI)};
+      } else {
+        d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)};
+      }
+      d[n++] = {M.vcc(), kUndef};
+      return n;
+    case O_BUFFER_STORE_DWORD: d[n++] = {M.spill(r.imm / 4), mkref(base, PART_ENTIRE)}; return n;
+    case O_UNKNOWN: {
+      if (!r.nops) return 0;
+      uint32_t o = r.opnd[0], tg = otag(o);
+      if (tg != TG_VGPR && tg != TG_SGPR && tg != TG_VCC) return 0;
+      uint32_t c = tg == TG_VCC ? 1 : ocnt(o);
+      if (c == 2) {
+        d[n++] = {reg_of(M, o, 0), mkref(base, PART_LO)};
+        d[n++] = {reg_of(M, o, 1), mkref(base, PART_HI)};
+      } else {
+        for (uint32_t q = 0; q < c && n < 4; ++q) d[n++] = {reg_of(M, o, q), mkref(base, PART_ENTIRE)};
+      }
+      return n;
+    }
+    default:
+      if (scmp(r.op)) { d[n++] = {M.scc(), mkref(base, PART_ENTIRE)}; return n; }
+      if (vcmp(r.op)) { d[n++] = {M.vcc(), mkref(base, PART_ENTIRE)}; return n; }
+      if (wide_result(r.op)) {
+        d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_LO)};
+        d[n++] = {reg_of(M, r.opnd[0], 1), mkref(base, PART_HI)};
+      } else {
+        d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)};
+      }
+      return n;
+  }
+}
+
+__device__ __forceinline__ bool defines_vcc(const InstrRec& r) {
+  return r.op == O_V_ADD_CO_U32 || r.op == O_V_SUB_CO_U32 || r.op == O_V_ADDC_CO_U32 || r.op == O_V_SUBB_CO_U32 ||
+         vcmp(r.op) || (r.op == O_UNKNOWN && r.nops && otag(r.opnd[0]) == TG_VCC);
+}
+
+// ---------------------------------------------------------------------------
+// sizes: spill slots, register count, limits
+// ---------------------------------------------------------------------------
+__global__ void k_df_sizes(Batch b, uint32_t* __restrict__ kstate) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  uint32_t ns = 0;
+  for (uint32_t i = 0; i < K.n_instr; ++i) {
+    const InstrRec& r = b.ins[K.first_instr + i];
+    if (r.op == O_BUFFER_LOAD_DWORD || r.op == O_BUFFER_STORE_DWORD) ns = max(ns, r.imm / 4 + 1);
+  }
+  K.nspill = ns;
+  K.R = K.vgprs + K.sgprs + 2 + ns;
+  if (!K.bad && (K.R > kMaxRegs || K.n_lblock >= kMaxBlocks || K.n_instr >= (1u << 26))) K.bad |= 16u;
+  if (!K.bad && K.n_lblock) {
+    // the entry block may not be the target of a branch
+    for (uint32_t q = 0; q < K.n_lblock; ++q) {
+      const BlockRec& B = b.lblocks[K.first_lblock + q];
+      if (B.succ0 == 0 || B.succ1 == 0) K.bad |= 32u;
+    }
+  }
+  kstate[k] = K.bad ? 0u : K.n_lblock * K.R;
+}
+
+__global__ void k_state_off(Batch b, const uint32_t* __restrict__ off) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  b.kh[k].state_off = off[k];
+}
+
+// ---------------------------------------------------------------------------
+// 64-bit carry pairs: v_addc_co_u32 / v_subb_co_u32 completing the low half of
+// the last carry-out of the same block (whose register still holds it)
+// ---------------------------------------------------------------------------
+__global__ void k_fusion(Batch b) {
+  uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  b.fused[gi] = 0;
+  b.co_idx[gi] = kNone;
+  const InstrRec& r = b.ins[gi];
+  if (r.op != O_V_ADDC_CO_U32 && r.op != O_V_SUBB_CO_U32) return;
+  const KHdr& K = b.kh[b.ikern[gi]];
+  if (K.bad || b.ctl[gi] != C_NORMAL) return;
+  uint32_t i = gi - K.first_instr;
+  uint32_t blk = b.lblock_of[gi];
+  if (blk == kNone) return;
+  uint32_t first = b.lblocks[K.first_lblock + blk].first;
+  int j = -1;
+  for (int q = (int)i - 1; q >= (int)first; --q) {
+    uint32_t gq = K.first_instr + q;
+    if (b.lblock_of[gq] != blk || b.ctl[gq] != C_NORMAL) continue;
+    if (defines_vcc(b.ins[gq])) { j = q; break; }
+  }
+  uint16_t want = r.op == O_V_ADDC_CO_U32 ? O_V_ADD_CO_U32 : O_V_SUB_CO_U32;
+  if (j < 0 || b.ins[K.first_instr + j].op != want) return;
+  RegMap M{K.vgprs, K.sgprs};
+  uint32_t lo = M.v(opay(b.ins[K.first_instr + j].opnd[0]));
+  uint32_t hi = M.v(opay(r.opnd[0]));
+  if (lo == hi) return;
+  for (uint32_t q = (uint32_t)j + 1; q < i; ++q) {
+    if (b.lblock_of[K.first_instr + q] != blk) continue;
+    Def d[4];
+    int n = idefs(b, K, M, q, d);  // no carry instruction sits between j and i
+    for (int t = 0; t < n; ++t)
+      if (d[t].reg == lo) return;
+  }
+  b.fused[gi] = 1;
+  b.co_idx[gi] = (uint32_t)j;
+}
+
+// ---------------------------------------------------------------------------
+// predecessors (CSR, sorted)
+// ---------------------------------------------------------------------------
+__global__ void k_pred_count(Batch b, uint32_t* __restrict__ cnt, const uint32_t* __restrict__ blk_kern) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NLB) return;
+  const KHdr& K = b.kh[blk_kern[g]];
+  const BlockRec& B = b.lblocks[g];
+  if (B.succ0 != kNone) atomicAdd(&cnt[K.first_lblock + B.succ0], 1u);
+  if (B.succ1 != kNone) atomicAdd(&cnt[K.first_lblock + B.succ1], 1u);
+}
+
+__global__ void k_pred_fill(Batch b, const uint32_t* __restrict__ blk_kern) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NLB) return;
+  const KHdr& K = b.kh[blk_kern[g]];
+  const BlockRec& B = b.lblocks[g];
+  uint32_t rel = g - K.first_lblock;
+  if (B.succ0 != kNone) {
+    uint32_t s = K.first_lblock + B.succ0;
+    b.preds[b.pred_off[s] + atomicAdd(&b.pred_fill[s], 1u)] = rel;
+  }
+  if (B.succ1 != kNone) {
+    uint32_t s = K.first_lblock + B.succ1;
+    b.preds[b.pred_off[s] + atomicAdd(&b.pred_fill[s], 1u)] = rel;
+  }
+}
+
+__global__ void k_pred_sort(Batch b) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NLB) return;
+  uint32_t a = b.pred_off[g], e = b.pred_off[g + 1];
+  for (uint32_t x = a + 1; x < e; ++x) {  // insertion sort: lists are short
+    uint32_t v = b.preds[x];
+    uint32_t y = x;
+    while (y > a && b.preds[y - 1] > v) {
+      b.preds[y] = b.preds[y - 1];
+      --y;
+    }
+    b.preds[y] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dominators: depth-first reverse postorder, then iterative intersection
+// ---------------------------------------------------------------------------
+__global__ void k_dominators(Batch b, uint32_t* __restrict__ rpo_index, uint32_t* __restrict__ stk,
+                             uint8_t* __restrict__ child) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  uint32_t nb = K.n_lblock, base = K.first_lblock;
+  if (K.bad || !nb) return;
+  const BlockRec* B = b.lblocks + base;
+  uint32_t* order = b.rpo + base;
+  uint32_t* ri = rpo_index + base;
+  uint32_t* idom = b.idom + base;
+  uint32_t* st = stk + base;
+  uint8_t* ch = child + base;
+  for (uint32_t x = 0; x < nb; ++x) {
+    ri[x] = kNone;
+    idom[x] = kNone;
+    ch[x] = 0;
+  }
+  // iterative DFS; postorder written backwards gives the reverse postorder
+  uint32_t sp = 0, npost = 0;
+  st[sp++] = 0;
+  ri[0] = 0;  // "seen"
+  uint32_t* post = b.scratch32 + base;
+  while (sp) {
+    uint32_t x = st[sp - 1];
+    uint32_t s = kNone;
+    while (ch[x] < 2 && s == kNone) {
+      uint32_t c = ch[x] == 0 ? B[x].succ0 : B[x].succ1;
+      ++ch[x];
+      if (c != kNone && ri[c] == kNone) s = c;
+    }
+    if (s != kNone) {
+      ri[s] = 0;
+      st[sp++] = s;
+    } else {
+      post[npost++] = x;
+      --sp;
+    }
+  }
+  for (uint32_t q = 0; q < nb; ++q) ri[q] = kNone;
+  for (uint32_t q = 0; q < npost; ++q) {
+    order[q] = post[npost - 1 - q];
+    ri[order[q]] = q;
+  }
+  for (uint32_t q = npost; q < nb; ++q) order[q] = kNone;
+  idom[0] = 0;
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (uint32_t q = 1; q < npost; ++q) {
+      uint32_t x = order[q], nd = kNone;
+      for (uint32_t pi = b.pred_off[base + x]; pi < b.pred_off[base + x + 1]; ++pi) {
+        uint32_t p = b.preds[pi];
+        if (ri[p] == kNone || idom[p] == kNone) continue;
+        if (nd == kNone) nd = p;
+        else {
+          uint32_t a1 = p, a2 = nd;
+          while (a1 != a2) {
+            while (ri[a1] > ri[a2]) a1 = idom[a1];
+            while (ri[a2] > ri[a1]) a2 = idom[a2];
+          }
+          nd = a1;
+        }
+      }
+      if (nd != idom[x]) {
+        idom[x] = nd;
+        changed = true;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-block definitions: last definition of every register (into st_out) and
+// the block's definition bitset
+// ---------------------------------------------------------------------------
+__global__ void k_local_defs(Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off) {
+  uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const KHdr& K = b.kh[b.ikern[gi]];
+  if (K.bad) return;
+  uint32_t blk = b.lblock_of[gi];
+  if (blk == kNone) return;
+  RegMap M{K.vgprs, K.sgprs};
+  uint32_t i = gi - K.first_instr;
+  Def d[4];
+  int n = idefs(b, K, M, i, d);
+  if (!n) return;
+  const BlockRec& B = b.lblocks[K.first_lblock + blk];
+  uint32_t words = (K.R + 31) / 32;
+  uint32_t* db = defbits + bits_off[b.ikern[gi]] + (size_t)blk * words;
+  for (int t = 0; t < n; ++t) {
+    atomicOr(&db[d[t].reg >> 5], 1u << (d[t].reg & 31));
+    bool later = false;
+    for (int u = t + 1; u < n && !later; ++u) later = d[u].reg == d[t].reg;
+    for (uint32_t q = i + 1; q < B.end && !later; ++q) {
+      if (b.lblock_of[K.first_instr + q] != blk) continue;
+      Def e[4];
+      int m = idefs(b, K, M, q, e);
+      for (int u = 0; u < m; ++u)
+        if (e[u].reg == d[t].reg) later = true;
+    }
+    if (!later) b.st_out[K.state_off + (size_t)blk * K.R + d[t].reg] = d[t].val;
+  }
+}
+
+__device__ __forceinline__ uint32_t entry_value(const KHdr& K, uint32_t r) {
+  if (r < K.vgprs) {
+    if (r < K.dims && r < 3) return leafref(LEAF_LID, r, PART_ENTIRE);
+    return kUndef;
+  }
+  if (r < K.vgprs + K.sgprs) {
+    uint32_t s = r - K.vgprs;
+    if (K.useargs && s >= 6 && s < 6 + K.dims && s < 9) return leafref(LEAF_GRP, s - 6, PART_ENTIRE);
+    if (K.sgprs > 5 && s == 4) return leafref(LEAF_KARG, 0, PART_LO);
+    if (K.sgprs > 5 && s == 5) return leafref(LEAF_KARG, 0, PART_HI);
+  }
+  return kUndef;
+}
+
+// ---------------------------------------------------------------------------
+// versions: frontier closure (warp per kernel, lane = 32 registers), then
+// values in reverse postorder (lanes over registers)
+// ---------------------------------------------------------------------------
+__global__ void k_versions(Batch b, uint32_t* __restrict__ defbits, uint32_t* __restrict__ phibits,
+                           const uint32_t* __restrict__ bits_off, uint32_t* __restrict__ err) {
+  uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  uint32_t lane = threadIdx.x & 31u;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  if (K.bad || !K.n_lblock) return;
+  uint32_t nb = K.n_lblock, base = K.first_lblock, R = K.R, words = (R + 31) / 32;
+  uint32_t* db = defbits + bits_off[k];
+  uint32_t* pb = phibits + bits_off[k];
+  const uint32_t* idom = b.idom + base;
+  // the entry defines every register
+  for (uint32_t w = lane; w < words; w += 32) db[w] = 0xFFFFFFFFu;
+  __syncwarp();
+  bool changed = true;
+  uint32_t sweeps = 0;
+  while (changed) {
+    changed = false;
+    if (++sweeps > 4 * nb + 8) {  // cannot happen for a closure; bounded all the same
+      if (lane == 0) atomicOr(err, ERR_CAPACITY);
+      break;
+    }
+    for (uint32_t x = 0; x < nb; ++x) {
+      uint32_t np = b.pred_off[base + x + 1] - b.pred_off[base + x];
+      if (np < 2 || idom[x] == kNone) continue;
+      for (uint32_t pi = b.pred_off[base + x]; pi < b.pred_off[base + x + 1]; ++pi) {
+        uint32_t r = b.preds[pi];
+        if (idom[r] == kNone) continue;  // unreachable predecessor
+        while (r != idom[x]) {
+          for (uint32_t w = lane; w < words; w += 32) {
+            uint32_t add = (db[(size_t)r * words + w] | pb[(size_t)r * words + w]) & ~pb[(size_t)x * words + w];
+            if (add) {
+              pb[(size_t)x * words + w] |= add;
+              changed = true;
+            }
+          }
+          r = idom[r];
+        }
+      }
+    }
+    changed = __any_sync(0xFFFFFFFFu, changed);
+  }
+  __syncwarp();
+  // values
+  uint32_t* in = b.st_in + K.state_off;
+  uint32_t* out = b.st_out + K.state_off;
+  uint8_t* hp = b.has_phi + K.state_off;
+  for (uint32_t q = 0; q < nb; ++q) {
+    uint32_t x = b.rpo[base + q];
+    if (x == kNone) break;
+    for (uint32_t r = lane; r < R; r += 32) {
+      bool phi = (pb[(size_t)x * words + (r >> 5)] >> (r & 31)) & 1u;
+      hp[(size_t)x * R + r] = phi;
+      uint32_t v = phi ? phiref(x, r) : (x == 0 ? entry_value(K, r) : out[(size_t)idom[x] * R + r]);
+      in[(size_t)x * R + r] = v;
+      uint32_t o = out[(size_t)x * R + r];
+      if (o == kTop) out[(size_t)x * R + r] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// nodes: one thread per instruction
+// ---------------------------------------------------------------------------
+struct NodeCtx;
+__device__ uint32_t reg_before(const NodeCtx& c, uint32_t reg);
+
+struct NodeCtx {
+  const Batch* b;
+  const KHdr* K;
+  RegMap M;
+  uint32_t i, blk, first;
+};
+
+// register value just before instruction ctx.i
+__device__ uint32_t reg_before(const NodeCtx& c, uint32_t reg) {
+  const Batch& b = *c.b;
+  for (int q = (int)c.i - 1; q >= (int)c.first; --q) {
+    if (b.lblock_of[c.K->first_instr + q] != c.blk) continue;
+    Def d[4];
+    int n = idefs(b, *c.K, c.M, (uint32_t)q, d);
+    for (int t = n - 1; t >= 0; --t)
+      if (d[t].reg == reg) return d[t].val;
+  }
+  uint32_t v = b.st_in[c.K->state_off + (size_t)c.blk * c.K->R + reg];
+  return v == kTop ? kUndef : v;
+}
+
+__device__ __forceinline__ uint32_t src32(const NodeCtx& c, Node* nodes, const InstrRec& r, uint32_t o,
+                                          uint32_t slot) {
+  uint32_t tg = otag(o);
+  if (tg == TG_VGPR) return reg_before(c, c.M.v(opay(o)));
+  if (tg == TG_SGPR) return reg_before(c, c.M.s(opay(o)));
+  if (tg == TG_VCC) return reg_before(c, c.M.vcc());
+  Node& n = nodes[slot];
+  n.kind = N_CONST;
+  if (tg == TG_ICONST) {
+    uint32_t p = opay(o);
+    n.cval = (p & 0x800000u) ? (p | 0xFF000000u) : p;
+  } else if (tg == TG_FCONST) {
+    const uint32_t fb[8] = {0x3f000000u, 0xbf000000u, 0x3f800000u, 0xbf800000u,
+                            0x40000000u, 0xc0000000u, 0x40800000u, 0xc0800000u};
+    n.cval = fb[opay(o) & 7];
+  } else {
+    n.cval = r.imm;
+  }
+  return mkref(4 * c.i + slot, PART_ENTIRE);
+}
+
+// source value of operand q of the carry-out instruction described by c, as
+// that instruction's own node holds it (constants live in its slots 1..2)
+__device__ __forceinline__ uint32_t src_of_co(const NodeCtx& c, const InstrRec& r, int q) {
+  uint32_t o = r.opnd[q], tg = otag(o);
+  if (tg == TG_VGPR) return reg_before(c, c.M.v(opay(o)));
+  if (tg == TG_SGPR) return reg_before(c, c.M.s(opay(o)));
+  if (tg == TG_VCC) return reg_before(c, c.M.vcc());
+  return mkref(4 * c.i + 1 + (uint32_t)(q - 2), PART_ENTIRE);
+}
+
+__device__ __forceinline__ uint32_t make_pair(const NodeCtx& c, Node* nodes, uint32_t lo, uint32_t hi,
+                                              uint32_t slot) {
+  if ((r_node(lo) || r_leaf(lo)) && rpart(lo) == PART_LO && hi == ((lo & ~3u) | PART_HI)) return lo & ~3u;
+  Node& p = nodes[slot];
+  p.kind = N_PAIR;
+  p.nsrc = 2;
+  p.src[0] = lo;
+  p.src[1] = hi;
+  return mkref(4 * c.i + slot, PART_ENTIRE);
+}
+
+__device__ __forceinline__ uint32_t src64(const NodeCtx& c, Node* nodes, uint32_t o, uint32_t slot) {
+  uint32_t a = reg_before(c, reg_of(c.M, o, 0)), h = reg_before(c, reg_of(c.M, o, 1));
+  return make_pair(c, nodes, a, h, slot);
+}
+
+__global__ void k_nodes(Batch b) {
+  uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const KHdr& K = b.kh[b.ikern[gi]];
+  Node* nodes = b.nodes + 4 * (size_t)gi;
+  for (int q = 0; q < 4; ++q) {
+    nodes[q].kind = N_NONE;
+    nodes[q].nsrc = 0;
+    nodes[q].fused = 0;
+    nodes[q].op = 0;
+    nodes[q].src[0] = nodes[q].src[1] = nodes[q].src[2] = kTop;
+    nodes[q].cval = 0;
+  }
+  if (K.bad) return;
+  uint32_t blk = b.lblock_of[gi];
+  if (blk == kNone) return;
+  NodeCtx c;
+  c.b = &b;
+  c.K = &K;
+  c.M = RegMap{K.vgprs, K.sgprs};
+  c.i = gi - K.first_instr;
+  c.blk = blk;
+  c.first = b.lblocks[K.first_lblock + blk].first;
+  const InstrRec& r = b.ins[gi];
+  uint8_t ctl = b.ctl[gi];
+  Node& nd = nodes[0];
+  if (ctl != C_NORMAL && ctl != C_CBR) return;
+  nd.kind = N_OP;
+  nd.op = r.op;
+  if (ctl == C_CBR) {
+    nd.nsrc = 1;
+    nd.src[0] = reg_before(c, r.op == O_S_AND_SAVEEXEC ? c.M.vcc() : c.M.scc());
+    return;
+  }
+  uint32_t s[3];
+  int ns = 0;
+  switch (r.op) {
+    case O_S_WAITCNT: break;
+    case O_S_LOAD_DWORD: case O_S_LOAD_DWORDX2: case O_S_LOAD_DWORDX4:
+      s[ns++] = src64(c, nodes, r.opnd[1], 2);
+      nd.cval = r.imm;
+      break;
+    case O_BUFFER_STORE_DWORD: s[ns++] = src32(c, nodes, r, r.opnd[0], 1); break;
+    case O_BUFFER_LOAD_DWORD: s[ns++] = reg_before(c, c.M.spill(r.imm / 4)); break;
+    case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: {
+      uint32_t a = src32(c, nodes, r, r.opnd[2], 1), bb = src32(c, nodes, r, r.opnd[3], 2);
+      if (b.fused[gi]) {
+        // the low-half node belongs to another thread: take its sources the same way
+        uint32_t j = b.co_idx[gi];
+        NodeCtx cj = c;
+        cj.i = j;
+        const InstrRec& rj = b.ins[K.first_instr + j];
+        uint32_t l0 = src_of_co(cj, rj, 2), l1 = src_of_co(cj, rj, 3);
+        s[ns++] = make_pair(c, nodes, l0, a, 1);
+        s[ns++] = make_pair(c, nodes, l1, bb, 2);
+        nd.fused = 1;
+      } else {
+        s[ns++] = a;
+        s[ns++] = bb;
+        s[ns++] = reg_before(c, c.M.vcc());
+      }
+      break;
+    }
+    case O_UNKNOWN:
+      for (int q = 1; q < r.nops && ns < 3; ++q) {
+        uint32_t o = r.opnd[q], tg = otag(o);
+        if (tg == TG_VGPR || tg == TG_SGPR || tg == TG_VCC) {
+          uint32_t cnt = tg == TG_VCC ? 1 : ocnt(o);
+          if (cnt == 2) s[ns] = src64(c, nodes, o, 1 + ns);
+          else s[ns] = reg_before(c, reg_of(c.M, o, 0));
+          ++ns;
+        }
+      }
+      break;
+    default: {
+      const char* sig = c_sig[r.op];
+      int nop = sig_count(r.op);
+      for (int q = 0; q < nop && ns < 3; ++q) {
+        char sc = sig[2 * q];
+        bool dst = (q == 0 && (sc == 'V' || sc == 'W' || sc == 's' || sc == 'p' || sc == 'q' || sc == 'c')) ||
+                   (q == 1 && sc == 'c' && (r.op == O_V_ADD_CO_U32 || r.op == O_V_SUB_CO_U32));
+        if (r.op == O_GLOBAL_STORE_DWORD || r.op == O_GLOBAL_STORE_DWORDX2 || scmp(r.op)) dst = false;
+        if (dst || sc == 'o') continue;
+        uint32_t slot = 1 + ns;
+        if (sc == 'W' || sc == 'p') s[ns] = src64(c, nodes, r.opnd[q], slot);
+        else s[ns] = src32(c, nodes, r, r.opnd[q], slot);
+        ++ns;
+      }
+    }
+  }
+  nd.nsrc = (uint8_t)ns;
+  for (int q = 0; q < ns; ++q) nd.src[q] = s[q];
+  if (r.op == O_S_LOAD_DWORDX4) {
+    Node& h2 = nodes[1];
+    h2.kind = N_SLOAD64B;
+    h2.nsrc = 1;
+    h2.src[0] = nd.src[0];
+    h2.cval = r.imm + 8;
+  }
+  if (r.op == O_V_ADD_CO_U32 || r.op == O_V_SUB_CO_U32) nodes[3].kind = N_CARRY;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+__global__ void k_bits_size(Batch b, uint32_t* __restrict__ kbits) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  const KHdr& K = b.kh[k];
+  kbits[k] = K.bad ? 0u : K.n_lblock * ((K.R + 31) / 32);
+}
+
+void launch_df_counts(Batch& b, DfScratch& d, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
+  const int T = 256;
+  if (!b.K) return;
+  k_df_sizes<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kstate);
+  k_bits_size<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kbits);
+  launch_scan(d.kstate, d.kstate_off, b.K, 0, false, sc, &totals[5], b.err, s);  // totals[5] = state words
+  launch_scan(d.kbits, d.bits_off, b.K, 0, false, sc, &totals[6], b.err, s);     // totals[6] = bitset words
+  if (b.I) k_fusion<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  if (b.NLB) {
+    cudaMemsetAsync(d.pcount, 0, sizeof(uint32_t) * (b.NLB + 1), s);
+    k_pred_count<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, d.pcount, d.blk_kern);
+    launch_scan(d.pcount, b.pred_off, b.NLB + 1, 0, false, sc, &totals[7], b.err, s);  // totals[7] = edges
+  }
+}
+
+void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
+  const int T = 256;
+  if (!b.K) return;
+  k_state_off<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kstate_off);
+  if (b.NLB) {
+    cudaMemsetAsync(b.pred_fill, 0, sizeof(uint32_t) * b.NLB, s);
+    k_pred_fill<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, d.blk_kern);
+    k_pred_sort<<<(b.NLB + T - 1) / T, T, 0, s>>>(b);
+    k_dominators<<<(b.K + 63) / 64, 64, 0, s>>>(b, d.rpo_index, d.stack, d.child);
+  }
+  if (b.NS) cudaMemsetAsync(b.st_out, 0xFF, sizeof(uint32_t) * b.NS, s);
+  if (d.NW) {
+    cudaMemsetAsync(d.defbits, 0, sizeof(uint32_t) * d.NW, s);
+    cudaMemsetAsync(d.phibits, 0, sizeof(uint32_t) * d.NW, s);
+  }
+  if (b.I) k_local_defs<<<(b.I + T - 1) / T, T, 0, s>>>(b, d.defbits, d.bits_off);
+  k_versions<<<(b.K + 3) / 4, 128, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
+  if (b.I) k_nodes<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+}
+
+}  // namespace gd

@@ -1,0 +1,746 @@
+// k_decode.cu — configuration, instruction decoding and control-flow graphs.
+//
+// S3 (configuration, Listings 1 and 3): one thread per kernel reads its
+//    .config rows: dims, .cws, register counts, .useargs and the .arg table
+//    (8-byte settings slots in declaration order; "_."-names are hidden).
+// S4 (decoding, prefix_root_suffix names of "The body extraction"): one thread
+//    per instruction row produces a fixed 32-byte record; mnemonics are found
+//    through an FNV-1a hash table held in constant memory.
+// S5 (CFG, "Search for control structures"): leaders by flags, block ids by a
+//    device-wide scan, block table by one thread per block.
+// S6 (logical CFG, Fig. 4/5): the exec-mask if / if-else forms are matched by
+//    one thread per kernel with a bounded stack and rewritten into per-work-item
+//    branches; logical leaders and blocks follow as for S5.
+#include <cstring>
+
+#include "gd_kernels.h"
+
+namespace gd {
+
+// ---------------------------------------------------------------------------
+// mnemonic table (the dialect) and operand signatures
+// ---------------------------------------------------------------------------
+struct OpName {
+  const char* n;
+  const char* sig;
+};
+// signature letters: V vgpr, W vgpr pair, s sgpr, p sgpr pair, q sgpr quad,
+// S 32-bit source, M 64-bit mask, c vcc, o off, K constant, L label, * free
+static const OpName kOps[O_COUNT] = {
+    {"", "?"}, {"s_load_dword", "s,p,K"}, {"s_load_dwordx2", "p,p,K"}, {"s_load_dwordx4", "q,p,K"},
+    {"s_waitcnt", "*"}, {"s_mov_b32", "s,S"}, {"s_mul_i32", "s,S,S"}, {"s_lshl_b32", "s,S,S"},
+    {"s_add_u32", "s,S,S"},
+    {"s_cmp_eq_u32", "S,S"}, {"s_cmp_lg_u32", "S,S"}, {"s_cmp_gt_u32", "S,S"}, {"s_cmp_lt_u32", "S,S"},
+    {"s_cmp_ge_u32", "S,S"}, {"s_cmp_le_u32", "S,S"}, {"s_cmp_eq_i32", "S,S"}, {"s_cmp_lg_i32", "S,S"},
+    {"s_cmp_gt_i32", "S,S"}, {"s_cmp_lt_i32", "S,S"}, {"s_cmp_ge_i32", "S,S"}, {"s_cmp_le_i32", "S,S"},
+    {"s_and_saveexec_b64", "M,M"}, {"s_xor_b64", "M,M,M"}, {"s_or_b64", "M,M,M"}, {"s_or_saveexec_b64", "M,M"},
+    {"s_branch", "L"}, {"s_cbranch_scc0", "L"}, {"s_cbranch_scc1", "L"}, {"s_cbranch_execz", "L"},
+    {"s_endpgm", ""}, {"v_mov_b32", "V,S"}, {"v_add_u32", "V,S,S"}, {"v_sub_u32", "V,S,S"},
+    {"v_mul_lo_u32", "V,S,S"}, {"v_mad_u32_u24", "V,S,S,S"}, {"v_mul_u32_u24", "V,S,S"}, {"v_and_b32", "V,S,S"},
+    {"v_or_b32", "V,S,S"}, {"v_xor_b32", "V,S,S"}, {"v_lshlrev_b32", "V,S,S"}, {"v_lshrrev_b32", "V,S,S"},
+    {"v_ashrrev_i32", "V,S,S"}, {"v_add_f32", "V,S,S"}, {"v_sub_f32", "V,S,S"}, {"v_mul_f32", "V,S,S"},
+    {"v_fma_f32", "V,S,S,S"}, {"v_cvt_f32_i32", "V,S"}, {"v_cvt_f32_u32", "V,S"}, {"v_cvt_f64_f32", "W,S"},
+    {"v_cvt_f64_i32", "W,S"}, {"v_cvt_f32_f64", "V,W"},
+    {"v_cmp_eq_i32", "c,S,S"}, {"v_cmp_ne_i32", "c,S,S"}, {"v_cmp_gt_i32", "c,S,S"}, {"v_cmp_lt_i32", "c,S,S"},
+    {"v_cmp_ge_i32", "c,S,S"}, {"v_cmp_le_i32", "c,S,S"}, {"v_cmp_eq_u32", "c,S,S"}, {"v_cmp_ne_u32", "c,S,S"},
+    {"v_cmp_gt_u32", "c,S,S"}, {"v_cmp_lt_u32", "c,S,S"}, {"v_cmp_ge_u32", "c,S,S"}, {"v_cmp_le_u32", "c,S,S"},
+    {"v_cmp_eq_f32", "c,S,S"}, {"v_cmp_neq_f32", "c,S,S"}, {"v_cmp_gt_f32", "c,S,S"}, {"v_cmp_lt_f32", "c,S,S"},
+    {"v_cmp_ge_f32", "c,S,S"}, {"v_cmp_le_f32", "c,S,S"},
+    {"v_add_co_u32", "V,c,S,S"}, {"v_addc_co_u32", "V,c,S,S,c"}, {"v_sub_co_u32", "V,c,S,S"},
+    {"v_subb_co_u32", "V,c,S,S,c"}, {"v_lshlrev_b64", "W,S,W"}, {"v_add_f64", "W,W,W"}, {"v_mul_f64", "W,W,W"},
+    {"v_fma_f64", "W,W,W,W"}, {"global_load_dword", "V,W,o"}, {"global_load_dwordx2", "W,W,o"},
+    {"global_store_dword", "W,V,o"}, {"global_store_dwordx2", "W,W,o"}, {"buffer_load_dword", "V,o,q,s"},
+    {"buffer_store_dword", "V,o,q,s"},
+};
+
+constexpr int kHash = 512;
+struct DecodeTables {
+  char names[O_COUNT][24];
+  char sigs[O_COUNT][12];
+  uint8_t name_len[O_COUNT];
+  uint8_t nsig[O_COUNT];   // operand count of the signature
+  uint16_t ht[kHash];      // hash slot -> op + 1 (0 = empty)
+};
+__constant__ DecodeTables c_tab;
+
+static const uint32_t kInlineFloatBits[8] = {0x3f000000u, 0xbf000000u, 0x3f800000u, 0xbf800000u,
+                                             0x40000000u, 0xc0000000u, 0x40800000u, 0xc0800000u};
+__constant__ uint32_t c_fbits[8];
+__constant__ char c_ftext[8][5];
+
+void init_decode_tables() {
+  static bool done = false;
+  if (done) return;
+  DecodeTables t;
+  memset(&t, 0, sizeof t);
+  for (int i = 1; i < O_COUNT; ++i) {
+    size_t n = strlen(kOps[i].n);
+    memcpy(t.names[i], kOps[i].n, n);
+    t.name_len[i] = (uint8_t)n;
+    memcpy(t.sigs[i], kOps[i].sig, strlen(kOps[i].sig));
+    size_t sl = strlen(kOps[i].sig);
+    t.nsig[i] = (uint8_t)(sl ? (sl + 1) / 2 : 0);
+    uint32_t h = fnv1a((const uint8_t*)kOps[i].n, (uint32_t)n) & (kHash - 1);
+    while (t.ht[h]) h = (h + 1) & (kHash - 1);
+    t.ht[h] = (uint16_t)(i + 1);
+  }
+  cudaMemcpyToSymbol(c_tab, &t, sizeof t);
+  const char ft[8][5] = {"0.5", "-0.5", "1.0", "-1.0", "2.0", "-2.0", "4.0", "-4.0"};
+  cudaMemcpyToSymbol(c_fbits, kInlineFloatBits, sizeof kInlineFloatBits);
+  cudaMemcpyToSymbol(c_ftext, ft, sizeof ft);
+  done = true;
+}
+
+__device__ int find_op(const uint8_t* p, const uint8_t* e) {
+  uint32_t n = (uint32_t)(e - p);
+  uint32_t h = fnv1a(p, n) & (kHash - 1);
+  for (int probe = 0; probe < kHash; ++probe) {
+    uint16_t v = c_tab.ht[h];
+    if (!v) return O_UNKNOWN;
+    int op = v - 1;
+    if (c_tab.name_len[op] == n) {
+      bool eq = true;
+      for (uint32_t i = 0; i < n && eq; ++i) eq = c_tab.names[op][i] == (char)p[i];
+      if (eq) return op;
+    }
+    h = (h + 1) & (kHash - 1);
+  }
+  return O_UNKNOWN;
+}
+
+// ---------------------------------------------------------------------------
+// S3: configuration
+// ---------------------------------------------------------------------------
+__device__ uint8_t type_code(const uint8_t* p, const uint8_t* e) {
+  if (tok_eq(p, e, "int")) return TY_INT;
+  if (tok_eq(p, e, "uint")) return TY_UINT;
+  if (tok_eq(p, e, "float")) return TY_FLOAT;
+  if (tok_eq(p, e, "long")) return TY_LONG;
+  if (tok_eq(p, e, "ulong")) return TY_ULONG;
+  if (tok_eq(p, e, "double")) return TY_DOUBLE;
+  return TY_NONE;
+}
+
+__device__ __forceinline__ void trim(const uint8_t*& p, const uint8_t*& e) {
+  while (p < e && is_space(*p)) ++p;
+  while (e > p && is_space(e[-1])) --e;
+}
+
+__global__ void k_config(Batch b) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  const uint8_t* T = b.text;
+  // name: second word of the .kernel row
+  {
+    const uint8_t* p = T + b.line_start[K.line];
+    const uint8_t* e = T + b.line_start[K.line + 1] - 1;
+    trim(p, e);
+    while (p < e && !is_space(*p)) ++p;
+    while (p < e && is_space(*p)) ++p;
+    const uint8_t* q = p;
+    while (q < e && !is_space(*q)) ++q;
+    K.name_off = (uint32_t)(p - T);
+    K.name_len = (uint32_t)(q - p);
+  }
+  // file
+  {
+    // last f with file_off[f] <= pos: empty files share their start with the next
+    // file, so this is the (non-empty) file that holds the row
+    uint64_t pos = b.line_start[K.line];
+    uint32_t lo = 0, hi = b.F;
+    while (lo + 1 < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (b.file_off[mid] <= pos) lo = mid;
+      else hi = mid;
+    }
+    K.file = lo;
+  }
+  K.n_instr = (k + 1 < b.K ? b.kh[k + 1].first_instr : b.I) - K.first_instr;
+  K.n_label = (k + 1 < b.K ? b.kh[k + 1].first_label : b.NL) - K.first_label;
+  K.first_pblock = K.n_pblock = K.first_lblock = K.n_lblock = 0;
+  K.dims = 1;
+  K.cws[0] = K.cws[1] = K.cws[2] = 1;
+  K.sgprs = 104;
+  K.vgprs = 256;
+  K.useargs = 0;
+  K.nargs = 0;
+  K.nuser = 0;
+  K.bad = 0;
+  K.partial = 0;
+  K.status = 0;
+  ArgRec* A = b.args + (size_t)k * kMaxArgs;
+  uint32_t l = K.line + 1;
+  for (; l < b.L && b.kind[l] != LK_KERNEL && !b.file_start[l]; ++l) {
+    if (b.rowtype[l] != RT_CFG) continue;
+    const uint8_t* p = T + b.line_start[l];
+    const uint8_t* e = T + b.line_start[l + 1] - 1;
+    trim(p, e);
+    const uint8_t* t = p;
+    while (t < e && !is_space(*t)) ++t;
+    const uint8_t* w1 = t;
+    while (w1 < e && is_space(*w1)) ++w1;
+    const uint8_t* w1e = w1;
+    while (w1e < e && !is_space(*w1e)) ++w1e;
+    if (tok_eq(p, t, ".dims") || tok_eq(p, t, "dims")) {
+      if (w1 == w1e) { K.bad = 1; continue; }
+      K.dims = (uint32_t)(w1e - w1);
+      if (K.dims < 1 || K.dims > 3) K.bad = 1;
+    } else if (tok_eq(p, t, ".cws")) {
+      const uint8_t* q = p + 4;  // the row after ".cws"
+      int idx = 0;
+      while (idx < 3) {
+        const uint8_t* fe = q;
+        while (fe < e && *fe != ',') ++fe;
+        const uint8_t *a = q, *z = fe;
+        trim(a, z);
+        int64_t v;
+        bool hx;
+        if (!dparse_int(a, z, &v, &hx) || v < 1 || v > 1024) K.bad = 1;
+        else K.cws[idx] = (uint32_t)v;
+        ++idx;
+        if (fe >= e) break;
+        q = fe + 1;
+      }
+    } else if (tok_eq(p, t, ".sgprsnum") || tok_eq(p, t, ".vgprsnum")) {
+      int64_t v;
+      bool hx;
+      if (w1 == w1e || !dparse_int(w1, w1e, &v, &hx) || v < 0 || v > 1024) { K.bad = 1; continue; }
+      if (p[1] == 's') K.sgprs = (uint32_t)v;
+      else K.vgprs = (uint32_t)v;
+    } else if (tok_eq(p, t, ".useargs")) {
+      K.useargs = 1;
+    } else if (tok_eq(p, t, ".arg")) {
+      // fields of the row after ".arg", split at commas and trimmed
+      const uint8_t* fs[6];
+      const uint8_t* fe[6];
+      int nf = 0;
+      const uint8_t* q = p + 4;
+      while (true) {
+        const uint8_t* z = q;
+        while (z < e && *z != ',') ++z;
+        const uint8_t *a = q, *y = z;
+        trim(a, y);
+        if (nf < 6) { fs[nf] = a; fe[nf] = y; }
+        ++nf;
+        if (z >= e) break;
+        q = z + 1;
+      }
+      if (nf < 3) { K.bad = 1; continue; }
+      if (K.nargs >= (uint32_t)kMaxArgs) { K.bad = 1; continue; }
+      ArgRec a;
+      a.name_off = (uint32_t)(fs[0] - T);
+      a.name_len = (uint16_t)(fe[0] - fs[0]);
+      a.hidden = (fe[0] - fs[0]) >= 2 && fs[0][0] == '_' && fs[0][1] == '.';
+      a.gofs = 0;
+      if (a.hidden && fe[0] - fs[0] == 17) {
+        const char* g = "_.global_offset_";
+        bool m = true;
+        for (int i = 0; i < 16 && m; ++i) m = fs[0][i] == (uint8_t)g[i];
+        if (m && fs[0][16] >= '0' && fs[0][16] <= '2') a.gofs = (uint8_t)(1 + fs[0][16] - '0');
+      }
+      a.pointer = 0;
+      a.is_const = 0;
+      a.space = 0;
+      if (fe[2] > fs[2] && fe[2][-1] == '*') {
+        a.pointer = 1;
+        a.elem = type_code(fs[2], fe[2] - 1);
+        if (nf > 3) {
+          if (tok_eq(fs[3], fe[3], "constant")) a.space = 1;
+          else if (tok_eq(fs[3], fe[3], "local")) a.space = 2;
+        }
+        a.is_const = nf > 4 && tok_eq(fs[4], fe[4], "const");
+      } else {
+        a.elem = type_code(fs[2], fe[2]);
+      }
+      if (!a.hidden) {
+        if (a.elem == TY_NONE) K.bad = 1;
+        ++K.nuser;
+      }
+      A[K.nargs++] = a;
+    }
+  }
+  K.cfg_end = l;
+}
+
+void launch_config(Batch& b, cudaStream_t s) {
+  if (!b.K) return;
+  k_config<<<(b.K + 127) / 128, 128, 0, s>>>(b);
+}
+
+// ---------------------------------------------------------------------------
+// S4: instruction decoding
+// ---------------------------------------------------------------------------
+__device__ bool parse_operand(const uint8_t* p, const uint8_t* e, uint32_t* word, bool* is_lit, uint32_t* lit) {
+  *is_lit = false;
+  uint32_t n = (uint32_t)(e - p);
+  if (tok_eq(p, e, "vcc")) { *word = opw(TG_VCC, 2, 0); return true; }
+  if (tok_eq(p, e, "exec")) { *word = opw(TG_EXEC, 2, 0); return true; }
+  if (tok_eq(p, e, "off")) { *word = opw(TG_OFF, 0, 0); return true; }
+  if ((p[0] == 'v' || p[0] == 's') && n >= 2) {
+    uint32_t tag = p[0] == 'v' ? TG_VGPR : TG_SGPR;
+    if (p[1] == '[') {
+      const uint8_t *colon = nullptr, *close = nullptr;
+      for (const uint8_t* q = p; q < e; ++q) {
+        if (!colon && *q == ':') colon = q;
+        if (!close && *q == ']') close = q;
+      }
+      if (!colon || !close || close != e - 1 || colon > close) return false;
+      int64_t a, bb;
+      bool h1, h2;
+      if (!dparse_int(p + 2, colon, &a, &h1) || !dparse_int(colon + 1, close, &bb, &h2)) return false;
+      if ((colon - (p + 2) >= 2 && p[2] == '0' && p[3] == 'x') || a < 0 || bb < a || bb - a + 1 > 8 || bb > 1023)
+        return false;
+      *word = opw(tag, (uint32_t)(bb - a + 1), (uint32_t)a);
+      return true;
+    }
+    for (const uint8_t* q = p + 1; q < e; ++q)
+      if (*q < '0' || *q > '9') return false;
+    int64_t a;
+    bool hx;
+    if (!dparse_int(p + 1, e, &a, &hx) || a > 1023) return false;
+    *word = opw(tag, 1, (uint32_t)a);
+    return true;
+  }
+  for (int i = 0; i < 8; ++i) {
+    const char* f = c_ftext[i];
+    if (tok_eq(p, e, f)) { *word = opw(TG_FCONST, 1, (uint32_t)i); return true; }
+  }
+  int64_t v;
+  bool hex;
+  if (dparse_int(p, e, &v, &hex)) {
+    bool anyx = false;
+    for (const uint8_t* q = p; q < e; ++q) anyx |= (*q == 'x' || *q == 'X');
+    if (!anyx && v >= -16 && v <= 64) {
+      *word = opw(TG_ICONST, 1, (uint32_t)v & 0xFFFFFFu);
+      return true;
+    }
+    *word = opw(TG_LIT, 1, 0);
+    *is_lit = true;
+    *lit = (uint32_t)(uint64_t)v;
+    return true;
+  }
+  return false;
+}
+
+__device__ bool sig_ok(char s, uint32_t o) {
+  uint32_t tg = otag(o), n = ocnt(o);
+  switch (s) {
+    case 'V': return tg == TG_VGPR && n == 1;
+    case 'W': return tg == TG_VGPR && n == 2;
+    case 's': return tg == TG_SGPR && n == 1;
+    case 'p': return tg == TG_SGPR && n == 2;
+    case 'q': return tg == TG_SGPR && n == 4;
+    case 'S': return ((tg == TG_VGPR || tg == TG_SGPR) && n == 1) || tg == TG_ICONST || tg == TG_FCONST || tg == TG_LIT;
+    case 'M': return (tg == TG_SGPR && n == 2) || tg == TG_VCC || tg == TG_EXEC;
+    case 'c': return tg == TG_VCC;
+    case 'o': return tg == TG_OFF;
+    case 'K': return tg == TG_ICONST || tg == TG_LIT;
+  }
+  return false;
+}
+
+__global__ void k_decode(Batch b) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.I) return;
+  uint32_t line = b.instr_line[i];
+  uint32_t k = b.kcnt[line] - 1;
+  const KHdr& K = b.kh[k];
+  const uint8_t* p = b.text + b.line_start[line];
+  const uint8_t* e = b.text + b.line_start[line + 1] - 1;
+  trim(p, e);
+  const uint8_t* me = p;
+  while (me < e && !is_space(*me)) ++me;
+  InstrRec r;
+  r.op = (uint16_t)find_op(p, me);
+  r.nops = 0;
+  r.flags = r.op == O_UNKNOWN ? FL_UNSUPPORTED : 0;
+  r.imm = 0;
+  r.target = kNone;
+  for (int q = 0; q < 5; ++q) r.opnd[q] = 0;
+  uint32_t lbl_pos = 0, lbl_len = 0;
+  const char* sig = c_sig[r.op];
+  const uint8_t* rp = me;
+  while (rp < e && is_space(*rp)) ++rp;
+  if (r.op != O_S_WAITCNT && rp < e) {
+    int nlit = 0;
+    const uint8_t* q = rp;
+    while (true) {
+      const uint8_t* z = q;
+      while (z < e && *z != ',') ++z;
+      const uint8_t *a = q, *y = z;
+      trim(a, y);
+      // sub-tokens: operand then modifiers
+      const uint8_t* s0 = a;
+      while (s0 < y && !is_space(*s0)) ++s0;
+      if (a == y) {
+        r.flags |= FL_BAD;
+      } else {
+        const uint8_t* m = s0;
+        while (m < y) {
+          while (m < y && is_space(*m)) ++m;
+          const uint8_t* me2 = m;
+          while (me2 < y && !is_space(*me2)) ++me2;
+          if (me2 - m >= 7 && m[0] == 'o' && m[1] == 'f' && m[2] == 'f' && m[3] == 's' && m[4] == 'e' &&
+              m[5] == 't' && m[6] == ':') {
+            int64_t v;
+            bool hx;
+            if (!dparse_int(m + 7, me2, &v, &hx) || v < 0) r.flags |= FL_BAD;
+            else r.imm = (uint32_t)v;
+          }
+          m = me2;
+        }
+        uint32_t word = 0, lit = 0;
+        bool is_lit = false, ok = true;
+        if (sig[0] == 'L') {
+          lbl_pos = (uint32_t)(a - b.text);
+          lbl_len = (uint32_t)(s0 - a);
+          word = opw(TG_LABEL, 0, 0);
+        } else if (!parse_operand(a, s0, &word, &is_lit, &lit)) {
+          r.flags |= FL_BAD;
+          ok = false;
+        }
+        if (ok) {
+          if (is_lit) {
+            if (nlit++) r.flags |= FL_BAD;
+            r.imm = lit;
+          }
+          if (r.nops < 5) r.opnd[r.nops++] = word;
+          else r.flags |= FL_BAD;
+        }
+      }
+      if (z >= e) break;
+      q = z + 1;
+    }
+  }
+  if (r.op && r.op != O_S_WAITCNT) {
+    int want = sig_count(r.op);
+    if (r.nops != want) r.flags |= FL_BAD;
+    else
+      for (int q = 0; q < want; ++q)
+        if (sig[2 * q] != 'L' && !sig_ok(sig[2 * q], r.opnd[q])) r.flags |= FL_BAD;
+    if ((r.op == O_S_LOAD_DWORD || r.op == O_S_LOAD_DWORDX2 || r.op == O_S_LOAD_DWORDX4) && r.nops == 3 &&
+        otag(r.opnd[2]) == TG_ICONST) {
+      uint32_t pay = opay(r.opnd[2]);
+      r.imm = (pay & 0x800000u) ? (pay | 0xFF000000u) : pay;
+    }
+    if ((r.op == O_BUFFER_LOAD_DWORD || r.op == O_BUFFER_STORE_DWORD) && (r.imm & 3u)) r.flags |= FL_BAD;
+  }
+  if (r.op == O_S_WAITCNT) r.nops = 0;
+  for (int q = 0; q < r.nops; ++q) {
+    uint32_t o = r.opnd[q], tg = otag(o);
+    if (tg == TG_VGPR && opay(o) + ocnt(o) > K.vgprs) r.flags |= FL_REGRANGE;
+    if (tg == TG_SGPR && opay(o) + ocnt(o) > K.sgprs) r.flags |= FL_REGRANGE;
+  }
+  b.ins[i] = r;
+  b.branch_hash[i] = lbl_len ? fnv1a(b.text + lbl_pos, lbl_len) : 0;
+  b.branch_pos[i] = lbl_len ? lbl_pos : kNone;
+  b.blen[i] = lbl_len;
+  b.ikern[i] = k;
+}
+
+__global__ void k_label_hash(Batch b) {
+  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.NL) return;
+  uint32_t line = b.label_line[j];
+  const uint8_t* p = b.text + b.line_start[line];
+  const uint8_t* e = b.text + b.line_start[line + 1] - 1;
+  trim(p, e);
+  b.label_hash[j] = fnv1a(p, (uint32_t)(e - p - 1));
+}
+
+// branch targets (first definition of the label wins), per-kernel parse flags, leaders
+__global__ void k_resolve(Batch b) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.I) return;
+  uint32_t k = b.ikern[i];
+  KHdr& K = b.kh[k];
+  InstrRec& r = b.ins[i];
+  if (b.branch_pos[i] != kNone) {
+    uint32_t len = b.blen[i];
+    const uint8_t* s = b.text + b.branch_pos[i];
+    uint32_t h = b.branch_hash[i];
+    uint32_t found = kNone;
+    for (uint32_t j = K.first_label; j < K.first_label + K.n_label && found == kNone; ++j) {
+      if (b.label_hash[j] != h) continue;
+      const uint8_t* p = b.text + b.line_start[b.label_line[j]];
+      while (is_space(*p)) ++p;
+      bool eq = true;
+      for (uint32_t q = 0; q < len && eq; ++q) eq = p[q] == s[q];
+      if (eq && p[len] == ':') found = b.label_instr[j] - K.first_instr;
+    }
+    if (found == kNone) r.flags |= FL_NOLABEL;
+    else r.target = found;
+  }
+  if (r.flags & (FL_BAD | FL_REGRANGE | FL_NOLABEL)) atomicOr(&K.bad, 2u);
+}
+
+__device__ __forceinline__ bool is_br(uint16_t op) {
+  return op == O_S_BRANCH || op == O_S_CBRANCH_SCC0 || op == O_S_CBRANCH_SCC1 || op == O_S_CBRANCH_EXECZ;
+}
+
+__global__ void k_pleaders(Batch b) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.I) return;
+  const KHdr& K = b.kh[b.ikern[i]];
+  uint32_t rel = i - K.first_instr, n = K.n_instr;
+  const InstrRec& r = b.ins[i];
+  if (rel == 0) b.pleader[i] = 1;
+  if (is_br(r.op) && r.target < n) b.pleader[K.first_instr + r.target] = 1;
+  if ((is_br(r.op) || r.op == O_S_ENDPGM) && rel + 1 < n) b.pleader[i + 1] = 1;
+}
+
+// after the inclusive scan of leaders: block ids and block starts
+__global__ void k_pblocks(Batch b, const uint32_t* __restrict__ incl, uint32_t* __restrict__ blk_kern) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.I) return;
+  uint32_t k = b.ikern[i];
+  KHdr& K = b.kh[k];
+  uint32_t g = incl[i] - 1;
+  uint32_t base = incl[K.first_instr] - 1;
+  uint32_t rel = i - K.first_instr;
+  b.pblock_of[i] = g - base;
+  if (rel == 0) {
+    K.first_pblock = base;
+    K.n_pblock = (K.n_instr ? incl[K.first_instr + K.n_instr - 1] : base) - base;
+  }
+  if (b.pleader[i]) {
+    b.pblocks[g].first = rel;
+    blk_kern[g] = k;
+  }
+}
+
+__global__ void k_pblock_edges(Batch b, const uint32_t* __restrict__ blk_kern) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NPB) return;
+  const KHdr& K = b.kh[blk_kern[g]];
+  uint32_t n = K.n_instr;
+  BlockRec& B = b.pblocks[g];
+  B.end = (g + 1 < K.first_pblock + K.n_pblock) ? b.pblocks[g + 1].first : n;
+  const InstrRec& last = b.ins[K.first_instr + B.end - 1];
+  uint32_t ft = B.end < n ? b.pblock_of[K.first_instr + B.end] : kNone;
+  uint32_t tg = last.target < n ? b.pblock_of[K.first_instr + last.target] : kNone;
+  B.succ0 = kNone;
+  B.succ1 = kNone;
+  if (last.op == O_S_BRANCH) B.succ0 = tg;
+  else if (is_br(last.op)) { B.succ0 = ft; B.succ1 = tg; }
+  else if (last.op != O_S_ENDPGM) B.succ0 = ft;
+}
+
+void launch_decode(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
+  const int T = 256;
+  if (!b.I) return;
+  k_decode<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  if (b.NL) k_label_hash<<<(b.NL + T - 1) / T, T, 0, s>>>(b);
+  k_resolve<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  cudaMemsetAsync(b.pleader, 0, sizeof(uint32_t) * b.I, s);
+  k_pleaders<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  launch_scan(b.pleader, b.lleader, b.I, 0, true, sc, &totals[3], b.err, s);  // totals[3] = physical blocks
+}
+
+void launch_pblocks(Batch& b, uint32_t* blk_kern, cudaStream_t s) {
+  const int T = 256;
+  if (!b.I) return;
+  k_pblocks<<<(b.I + T - 1) / T, T, 0, s>>>(b, b.lleader, blk_kern);
+  if (b.NPB) k_pblock_edges<<<(b.NPB + T - 1) / T, T, 0, s>>>(b, blk_kern);
+}
+
+// ---------------------------------------------------------------------------
+// S6: exec-mask forms -> standard form, logical blocks
+// ---------------------------------------------------------------------------
+struct Form {
+  uint32_t save, xor1, ez1, els, xor2, ez2;
+};
+
+__device__ __forceinline__ bool same_pair(uint32_t a, uint32_t bb) { return otag(a) == TG_SGPR && a == bb; }
+
+__global__ void k_exec_forms(Batch b) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  const InstrRec* R = b.ins + K.first_instr;
+  uint8_t* ctl = b.ctl + K.first_instr;
+  uint32_t* lt = b.ltarget + K.first_instr;
+  uint8_t* sense = b.sense + K.first_instr;
+  uint32_t n = K.n_instr;
+  for (uint32_t i = 0; i < n; ++i) {
+    ctl[i] = C_NORMAL;
+    lt[i] = kNone;
+    sense[i] = 0;
+  }
+  Form st[kMaxExecDepth];
+  int sp = 0;
+  bool bad = false;
+  for (uint32_t i = 0; i < n && !bad; ++i) {
+    const InstrRec& r = R[i];
+    switch (r.op) {
+      case O_S_AND_SAVEEXEC:
+        if (otag(r.opnd[0]) != TG_SGPR || otag(r.opnd[1]) != TG_VCC || sp == kMaxExecDepth) { bad = true; break; }
+        st[sp++] = Form{i, kNone, kNone, kNone, kNone, kNone};
+        break;
+      case O_S_XOR_B64: {
+        if (!sp) { bad = true; break; }
+        Form& f = st[sp - 1];
+        uint32_t S = R[f.save].opnd[0];
+        if (f.els == kNone && f.xor1 == kNone && i == f.save + 1 && same_pair(r.opnd[0], S) &&
+            otag(r.opnd[1]) == TG_EXEC && same_pair(r.opnd[2], S))
+          f.xor1 = i;
+        else if (f.els != kNone && f.xor2 == kNone && i == f.els + 1 && otag(r.opnd[0]) == TG_EXEC &&
+                 otag(r.opnd[1]) == TG_EXEC && same_pair(r.opnd[2], S))
+          f.xor2 = i;
+        else
+          bad = true;
+        break;
+      }
+      case O_S_CBRANCH_EXECZ: {
+        if (!sp) { bad = true; break; }
+        Form& f = st[sp - 1];
+        if (f.els == kNone && f.ez1 == kNone && i == (f.xor1 != kNone ? f.xor1 : f.save) + 1) f.ez1 = i;
+        else if (f.xor2 != kNone && f.ez2 == kNone && i == f.xor2 + 1) f.ez2 = i;
+        else bad = true;
+        break;
+      }
+      case O_S_OR_SAVEEXEC: {
+        if (!sp) { bad = true; break; }
+        Form& f = st[sp - 1];
+        uint32_t S = R[f.save].opnd[0];
+        if (f.xor1 == kNone || f.els != kNone || !same_pair(r.opnd[0], S) || !same_pair(r.opnd[1], S)) {
+          bad = true;
+          break;
+        }
+        f.els = i;
+        break;
+      }
+      case O_S_OR_B64: {
+        if (!sp) { bad = true; break; }
+        Form f = st[sp - 1];
+        uint32_t S = R[f.save].opnd[0];
+        if (otag(r.opnd[0]) != TG_EXEC || otag(r.opnd[1]) != TG_EXEC || !same_pair(r.opnd[2], S) ||
+            (f.xor1 == kNone) != (f.els == kNone) || (f.els != kNone && f.xor2 == kNone)) {
+          bad = true;
+          break;
+        }
+        --sp;
+        // standard form: branch on the compare, jump from the then part to the join
+        ctl[f.save] = C_CBR;
+        sense[f.save] = 0;
+        if (f.xor1 != kNone) ctl[f.xor1] = C_DROP;
+        if (f.ez1 != kNone) ctl[f.ez1] = C_DROP;
+        if (f.els != kNone) {
+          ctl[f.els] = C_JMP;
+          ctl[f.xor2] = C_DROP;
+          if (f.ez2 != kNone) ctl[f.ez2] = C_DROP;
+          lt[f.save] = (f.ez2 != kNone ? f.ez2 : f.xor2) + 1;
+          lt[f.els] = i + 1;
+        } else {
+          lt[f.save] = i + 1;
+        }
+        ctl[i] = C_DROP;
+        break;
+      }
+      default:
+        break;
+    }
+  }
+  if (sp) bad = true;
+  if (bad) {
+    K.bad |= 4u;
+    return;
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    uint16_t op = R[i].op;
+    if (op == O_S_BRANCH) { ctl[i] = C_JMP; lt[i] = R[i].target; }
+    if (op == O_S_CBRANCH_SCC0 || op == O_S_CBRANCH_SCC1) {
+      ctl[i] = C_CBR;
+      lt[i] = R[i].target;
+      sense[i] = op == O_S_CBRANCH_SCC1;
+    }
+    if (op == O_S_ENDPGM) ctl[i] = C_END;
+  }
+}
+
+__device__ __forceinline__ uint32_t resolve_t(const uint8_t* ctl, uint32_t t, uint32_t n) {
+  while (t < n && ctl[t] == C_DROP) ++t;
+  return t;
+}
+
+__global__ void k_lleaders(Batch b) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.I) return;
+  const KHdr& K = b.kh[b.ikern[i]];
+  if (K.bad) return;
+  const uint8_t* ctl = b.ctl + K.first_instr;
+  uint32_t n = K.n_instr, rel = i - K.first_instr;
+  uint32_t& t = b.ltarget[i];
+  if (t != kNone) t = resolve_t(ctl, t, n);
+  if (rel == resolve_t(ctl, 0, n)) b.pleader[i] = 1;
+  uint8_t c = ctl[rel];
+  if ((c == C_CBR || c == C_JMP) && t < n) b.pleader[K.first_instr + t] = 1;
+  if (c == C_CBR || c == C_JMP || c == C_END) {
+    uint32_t nx = resolve_t(ctl, rel + 1, n);
+    if (nx < n) b.pleader[K.first_instr + nx] = 1;
+  }
+}
+
+__global__ void k_lblocks(Batch b, const uint32_t* __restrict__ incl, uint32_t* __restrict__ blk_kern) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.I) return;
+  uint32_t k = b.ikern[i];
+  KHdr& K = b.kh[k];
+  uint32_t rel = i - K.first_instr;
+  uint32_t before = K.first_instr ? incl[K.first_instr - 1] : 0;  // blocks of earlier kernels
+  if (rel == 0) {
+    K.first_lblock = before;
+    K.n_lblock = (K.n_instr ? incl[K.first_instr + K.n_instr - 1] : before) - before;
+  }
+  if (K.bad) { b.lblock_of[i] = kNone; return; }
+  uint32_t g = incl[i];
+  b.lblock_of[i] = (b.ctl[i] == C_DROP || g == before) ? kNone : g - 1 - before;
+  if (b.pleader[i]) {
+    b.lblocks[g - 1].first = rel;
+    blk_kern[g - 1] = k;
+  }
+}
+
+__global__ void k_lblock_edges(Batch b, const uint32_t* __restrict__ blk_kern) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NLB) return;
+  const KHdr& K = b.kh[blk_kern[g]];
+  uint32_t n = K.n_instr;
+  const uint8_t* ctl = b.ctl + K.first_instr;
+  BlockRec& B = b.lblocks[g];
+  B.end = (g + 1 < K.first_lblock + K.n_lblock) ? b.lblocks[g + 1].first : n;
+  uint32_t t = B.end - 1;
+  while (t > B.first && ctl[t] == C_DROP) --t;
+  b.lterm[g] = t;
+  uint32_t nx = resolve_t(ctl, t + 1, n);
+  uint32_t ft = nx < n ? b.lblock_of[K.first_instr + nx] : kNone;
+  uint32_t tt = b.ltarget[K.first_instr + t];
+  uint32_t tg = tt < n ? b.lblock_of[K.first_instr + tt] : kNone;
+  B.succ0 = kNone;
+  B.succ1 = kNone;
+  switch (ctl[t]) {
+    case C_CBR: B.succ0 = ft; B.succ1 = tg == ft ? kNone : tg; break;
+    case C_JMP: B.succ0 = tg; break;
+    case C_END: break;
+    default: B.succ0 = ft;
+  }
+}
+
+void launch_logical(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
+  const int T = 256;
+  if (!b.I) return;
+  k_exec_forms<<<(b.K + 127) / 128, 128, 0, s>>>(b);
+  cudaMemsetAsync(b.pleader, 0, sizeof(uint32_t) * b.I, s);
+  k_lleaders<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  launch_scan(b.pleader, b.lleader, b.I, 0, true, sc, &totals[4], b.err, s);  // totals[4] = logical blocks
+}
+
+void launch_lblocks(Batch& b, uint32_t* blk_kern, cudaStream_t s) {
+  const int T = 256;
+  if (!b.I) return;
+  k_lblocks<<<(b.I + T - 1) / T, T, 0, s>>>(b, b.lleader, blk_kern);
+  if (b.NLB) k_lblock_edges<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, blk_kern);
+}
+
+}  // namespace gd

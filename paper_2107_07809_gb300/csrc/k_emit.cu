@@ -1,0 +1,835 @@
+// k_emit.cu — S13: OpenCL generation.
+//
+// Output conventions (the paper fixes none; these are the project's): the
+// signature lists the user arguments (`__global T *name`, scalars `T name`);
+// variables `varN` are declared first, numbered in program order; every
+// binary operation is parenthesised; an operand whose recovered type differs
+// from the operation's type gets a cast (integers) or as_T (reinterpretation);
+// a value at a join is assigned on the edges into the join; 4-space indent.
+// Unsupported instructions stay as inline asm ("Practical implementation").
+//
+// Two launches run the same code: the first only counts bytes, a scan places
+// every kernel, the second writes.  One thread per kernel; the region tree is
+// walked with an explicit stack, expressions recursively with a depth guard.
+#include "k_analysis.cuh"
+
+namespace gd {
+
+struct Wr {
+  uint8_t* p;
+  uint32_t n;
+  bool on;
+  __device__ __forceinline__ void c(char ch) {
+    if (on) p[n] = (uint8_t)ch;
+    ++n;
+  }
+  __device__ void s(const char* z) {
+    while (*z) c(*z++);
+  }
+  __device__ void mem(const uint8_t* a, uint32_t len) {
+    for (uint32_t i = 0; i < len; ++i) c((char)a[i]);
+  }
+  __device__ void u64(uint64_t v) {
+    char t[24];
+    int k = 0;
+    do {
+      t[k++] = (char)('0' + v % 10);
+      v /= 10;
+    } while (v);
+    while (k) c(t[--k]);
+  }
+  __device__ void i64(int64_t v) {
+    if (v < 0) {
+      c('-');
+      u64(0 - (uint64_t)v);
+    } else {
+      u64((uint64_t)v);
+    }
+  }
+  __device__ void indent(int lvl) {
+    for (int i = 0; i < 4 * lvl; ++i) c(' ');
+  }
+};
+
+__device__ const char* tname(uint8_t t) {
+  switch (t) {
+    case TY_INT: return "int";
+    case TY_UINT: return "uint";
+    case TY_FLOAT: return "float";
+    case TY_LONG: return "long";
+    case TY_ULONG: return "ulong";
+    case TY_DOUBLE: return "double";
+  }
+  return "uint";
+}
+__device__ __forceinline__ bool tint(uint8_t t) { return t == TY_INT || t == TY_UINT || t == TY_LONG || t == TY_ULONG; }
+__device__ __forceinline__ int twidth(uint8_t t) { return ty64(t) ? 64 : 32; }
+
+// exact short decimal when the value has few binary fraction digits, else as_float/as_double
+__device__ void float_lit(Wr& w, uint64_t bits, bool dbl) {
+  int mbits = dbl ? 52 : 23, ebits = dbl ? 11 : 8, bias = dbl ? 1023 : 127;
+  uint64_t sign = bits >> (mbits + ebits);
+  uint64_t ex = (bits >> mbits) & ((1ull << ebits) - 1);
+  uint64_t man = bits & ((1ull << mbits) - 1);
+  auto fallback = [&]() {
+    w.s(dbl ? "as_double(" : "as_float(");
+    w.u64(bits);
+    w.s(dbl ? "UL)" : "u)");
+  };
+  if (bits == 0) {
+    w.s(dbl ? "0.0" : "0.0f");
+    return;
+  }
+  if (ex == (1ull << ebits) - 1 || ex == 0) return fallback();
+  uint64_t m = man | (1ull << mbits);
+  int e = (int)ex - bias - mbits;
+  while ((m & 1) == 0 && e < 0) {
+    m >>= 1;
+    ++e;
+  }
+  if (e >= 0) {
+    if (e > 62 || (m >> (63 - e)) != 0) return fallback();
+    if (sign) w.c('-');
+    w.u64(m << e);
+    w.s(dbl ? ".0" : ".0f");
+    return;
+  }
+  int k = -e;
+  if (k > 16) return fallback();
+  uint64_t p5 = 1;
+  for (int i = 0; i < k; ++i) p5 *= 5;
+  if (m > UINT64_MAX / p5) return fallback();
+  uint64_t N = m * p5, p10 = 1;
+  for (int i = 0; i < k; ++i) p10 *= 10;
+  uint64_t ip = N / p10, fp = N % p10;
+  char d[20];
+  for (int i = k - 1; i >= 0; --i) {
+    d[i] = (char)('0' + fp % 10);
+    fp /= 10;
+  }
+  int len = k;
+  while (len > 1 && d[len - 1] == '0') --len;
+  if (sign) w.c('-');
+  w.u64(ip);
+  w.c('.');
+  for (int i = 0; i < len; ++i) w.c(d[i]);
+  if (!dbl) w.c('f');
+}
+
+__device__ void lit32(Wr& w, uint32_t bits, uint8_t want) {
+  if (want == TY_INT) {
+    int32_t v = (int32_t)bits;
+    if (v == INT32_MIN) w.s("(-2147483647 - 1)");
+    else w.i64(v);
+  } else if (want == TY_FLOAT) {
+    float_lit(w, bits, false);
+  } else {
+    w.u64(bits);
+    w.c('u');
+  }
+}
+__device__ void lit64(Wr& w, uint64_t bits, uint8_t want) {
+  if (want == TY_LONG) {
+    int64_t v = (int64_t)bits;
+    if (v == INT64_MIN) w.s("(-9223372036854775807L - 1L)");
+    else {
+      w.i64(v);
+      w.c('L');
+    }
+  } else if (want == TY_DOUBLE) {
+    float_lit(w, bits, true);
+  } else {
+    w.u64(bits);
+    w.s("UL");
+  }
+}
+
+struct Em {
+  KView v;
+  const Batch* b;
+  const KHdr* K;
+  const uint32_t* uses;
+  const uint8_t* fl;
+  const uint8_t* nt;
+  const int32_t* vo;
+  const int32_t* pv;
+  const uint8_t* vt;
+  uint32_t* scratch;  // per-kernel: copies list (3 words per pending copy)
+  uint32_t scap;      // its capacity in words
+  Wr w;
+  bool partial;
+  bool deep;
+
+  __device__ uint8_t NT(uint32_t id) const { return tresolve(nt[id], node_width(v, id)); }
+  __device__ int32_t phivar(uint32_t r) const {
+    return pv[(size_t)((rid(r) >> 10) & 0x3FFFF) * K->R + (rid(r) & 0x3FF)];
+  }
+
+  // ---- conversions -----------------------------------------------------------
+  __device__ void conv_open(uint8_t from, uint8_t want) {
+    if (want == TY_NONE || from == want) return;
+    if (tint(from) && tint(want)) {
+      w.c('(');
+      w.s(tname(want));
+      w.c(')');
+    } else if (twidth(from) == twidth(want)) {
+      w.s("as_");
+      w.s(tname(want));
+      w.c('(');
+    } else {
+      w.c('(');
+      w.s(tname(want));
+      w.c(')');
+    }
+  }
+  __device__ void conv_close(uint8_t from, uint8_t want) {
+    if (want == TY_NONE || from == want) return;
+    if (!(tint(from) && tint(want)) && twidth(from) == twidth(want)) w.c(')');
+  }
+
+  // ---- types of expressions (computed before printing) ------------------------
+  __device__ uint8_t mem_elem(const Node& n, uint32_t width) {
+    Mem m = match_addr(v, fwd(v, n.src[0]), width);
+    if (m.ok) return v.A[m.arg].elem;
+    return width == 8 ? TY_ULONG : TY_UINT;
+  }
+
+  __device__ uint8_t node_expr_type(uint32_t id) {
+    const Node& n = v.node(id);
+    uint8_t T = NT(id);
+    if (n.kind == N_PAIR) return TY_ULONG;
+    if (n.kind != N_OP) return TY_UINT;
+    uint16_t op = n.op;
+    if (op_scmp(op) || op_vcmp(op)) return TY_INT;
+    switch (op) {
+      case O_S_ADD_U32: case O_V_ADD_U32: case O_V_SUB_U32: case O_V_MUL_LO_U32: case O_V_MAD_U32_U24:
+      case O_V_MUL_U32_U24: case O_V_LSHRREV_B32: case O_V_ADD_CO_U32: case O_V_SUB_CO_U32: return TY_UINT;
+      case O_S_MUL_I32: case O_V_ASHRREV_I32: return TY_INT;
+      case O_S_LSHL_B32: case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_LSHLREV_B32:
+      case O_V_LSHLREV_B64: return T;
+      case O_V_ADD_F32: case O_V_SUB_F32: case O_V_MUL_F32: case O_V_FMA_F32: case O_V_CVT_F32_I32:
+      case O_V_CVT_F32_U32: case O_V_CVT_F32_F64: return TY_FLOAT;
+      case O_V_CVT_F64_F32: case O_V_CVT_F64_I32: case O_V_ADD_F64: case O_V_MUL_F64: case O_V_FMA_F64: return TY_DOUBLE;
+      case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused ? T : TY_UINT;
+      case O_GLOBAL_LOAD_DWORD: return mem_elem(n, 4);
+      case O_GLOBAL_LOAD_DWORDX2: return mem_elem(n, 8);
+    }
+    return T == TY_ULONG ? TY_ULONG : TY_UINT;
+  }
+
+  __device__ uint8_t expr_type(uint32_t r, uint8_t want) {
+    r = fwd(v, r);
+    if (r_phi(r)) {
+      int32_t x = phivar(r);
+      return x < 0 ? TY_UINT : vt[x];
+    }
+    Cls c = classify(v, r);
+    switch (c.c) {
+      case K_UNDEF: case K_LID: case K_GRP: case K_GID: case K_GIDNO: case K_GOFSLO: return TY_UINT;
+      case K_GOFS64: case K_ARGPTR: case K_KARG: return TY_ULONG;
+      case K_ARG32: case K_ARG64: return v.A[c.k].elem;
+      case K_CONST32: {
+        uint8_t t = want == TY_NONE ? TY_UINT : want;
+        return twidth(t) == 64 ? TY_UINT : t;
+      }
+      case K_CONST64: {
+        uint8_t t = want == TY_NONE ? TY_ULONG : want;
+        return twidth(t) == 32 ? TY_ULONG : t;
+      }
+    }
+    if (!r_node(r)) return TY_UINT;
+    uint32_t id = rid(r);
+    if (rpart(r) != PART_ENTIRE) return TY_UINT;
+    if (vo[id] >= 0) return vt[vo[id]];
+    return node_expr_type(id);
+  }
+
+  // ---- printing -------------------------------------------------------------
+  __device__ void E(uint32_t r, uint8_t want, int d) {
+    uint8_t t = expr_type(r, want);
+    conv_open(t, want);
+    ex(r, want, d);
+    conv_close(t, want);
+  }
+
+  __device__ void name(uint32_t slot) { w.mem(b->text + v.A[slot].name_off, v.A[slot].name_len); }
+
+  __device__ void ex(uint32_t r, uint8_t want, int d) {
+    if (d > 200) {
+      deep = true;
+      w.s("0u");
+      return;
+    }
+    r = fwd(v, r);
+    if (r_phi(r)) {
+      int32_t x = phivar(r);
+      if (x < 0) {
+        partial = true;
+        w.s("0u");
+      } else {
+        w.s("var");
+        w.u64((uint64_t)x);
+      }
+      return;
+    }
+    Cls c = classify(v, r);
+    switch (c.c) {
+      case K_UNDEF: partial = true; w.s("0u"); return;
+      case K_LID: w.s("get_local_id("); w.u64(c.k); w.c(')'); return;
+      case K_GRP: w.s("get_group_id("); w.u64(c.k); w.c(')'); return;
+      case K_GID: w.s("get_global_id("); w.u64(c.k); w.c(')'); return;
+      case K_GIDNO:
+        w.s("(get_global_id(");
+        w.u64(c.k);
+        w.s(") - get_global_offset(");
+        w.u64(c.k);
+        w.s("))");
+        return;
+      case K_GOFSLO: case K_GOFS64: w.s("get_global_offset("); w.u64(c.k); w.c(')'); return;
+      case K_ARG32: case K_ARG64: name(c.k); return;
+      case K_ARGPTR: w.s("(ulong)"); name(c.k); return;
+      case K_KARG: partial = true; w.s("0UL"); return;
+      case K_CONST32: {
+        uint8_t t = want == TY_NONE ? TY_UINT : want;
+        if (twidth(t) == 64) t = TY_UINT;
+        lit32(w, v.node(rid(r)).cval, t);
+        return;
+      }
+      case K_CONST64: {
+        const Node& p = v.node(rid(r));
+        uint64_t lo = v.node(rid(fwd(v, p.src[0]))).cval, hi = v.node(rid(fwd(v, p.src[1]))).cval;
+        uint8_t t = want == TY_NONE ? TY_ULONG : want;
+        if (twidth(t) == 32) t = TY_ULONG;
+        lit64(w, lo | (hi << 32), t);
+        return;
+      }
+    }
+    if (!r_node(r)) {
+      partial = true;
+      w.s("0u");
+      return;
+    }
+    uint32_t id = rid(r);
+    if (rpart(r) != PART_ENTIRE) {
+      uint32_t whole = mkref(id, PART_ENTIRE);
+      bool dbl = expr_type(whole, TY_NONE) == TY_DOUBLE;
+      if (rpart(r) == PART_LO) {
+        w.s(dbl ? "(uint)as_ulong(" : "(uint)");
+        ex(whole, TY_NONE, d + 1);
+        if (dbl) w.c(')');
+      } else {
+        w.s(dbl ? "(uint)(as_ulong(" : "(uint)(");
+        ex(whole, TY_NONE, d + 1);
+        w.s(dbl ? ") >> 32)" : " >> 32)");
+      }
+      return;
+    }
+    if (vo[id] >= 0) {
+      w.s("var");
+      w.u64((uint64_t)vo[id]);
+      return;
+    }
+    node_expr(id, d + 1);
+  }
+
+  __device__ void S(const Node& n, int q, uint8_t t, int d) { E(fwd(v, n.src[q]), t, d); }
+  __device__ void binop(const Node& n, const char* sym, uint8_t ot, int d) {
+    w.c('(');
+    S(n, 0, ot, d);
+    w.c(' ');
+    w.s(sym);
+    w.c(' ');
+    S(n, 1, ot, d);
+    w.c(')');
+  }
+  __device__ void shamt(uint32_t r, uint32_t mask, int d) {
+    uint32_t f = fwd(v, r);
+    if (r_node(f) && rpart(f) == PART_ENTIRE && v.node(rid(f)).kind == N_CONST) {
+      w.u64(v.node(rid(f)).cval & mask);
+      return;
+    }
+    w.c('(');
+    E(f, TY_UINT, d);
+    w.s(" & ");
+    w.u64(mask);
+    w.s("u)");
+  }
+  __device__ void call3(const char* fn, const Node& n, int k, uint8_t t, int d) {
+    w.s(fn);
+    w.c('(');
+    for (int q = 0; q < k; ++q) {
+      if (q) w.s(", ");
+      S(n, q, t, d);
+    }
+    w.c(')');
+  }
+  __device__ void cast1(const char* pre, const Node& n, uint8_t t, int d) {
+    w.s(pre);
+    S(n, 0, t, d);
+  }
+  __device__ void shift(const Node& n, int vq, int sq, uint8_t t, const char* sym, uint32_t mask, int d) {
+    w.c('(');
+    S(n, vq, t, d);
+    w.c(' ');
+    w.s(sym);
+    w.c(' ');
+    shamt(n.src[sq], mask, d);
+    w.c(')');
+  }
+
+  __device__ void memref(const Node& n, uint32_t width, int d) {
+    Mem m = match_addr(v, fwd(v, n.src[0]), width);
+    if (m.ok) {
+      name(m.arg);
+      w.c('[');
+      if (m.idx == kTop) w.c('0');
+      else E(m.idx, TY_NONE, d);
+      w.c(']');
+      return;
+    }
+    w.s("*((__global ");
+    w.s(width == 8 ? "ulong" : "uint");
+    w.s(" *)(");
+    E(fwd(v, n.src[0]), TY_ULONG, d);
+    w.s("))");
+  }
+
+  // a node's own expression (ignoring its variable)
+  __device__ void node_expr(uint32_t id, int d) {
+    const Node& n = v.node(id);
+    uint8_t T = NT(id);
+    if (n.kind == N_PAIR) {
+      w.s("upsample(");
+      S(n, 1, TY_UINT, d);
+      w.s(", ");
+      S(n, 0, TY_UINT, d);
+      w.c(')');
+      return;
+    }
+    if (n.kind != N_OP) {
+      partial = true;
+      w.s("0u");
+      return;
+    }
+    uint16_t op = n.op;
+    if (op_scmp(op) || op_vcmp(op)) {
+      uint32_t cc;
+      uint8_t ot;
+      if (op_scmp(op)) {
+        cc = (op - O_S_CMP0) % 6;
+        ot = (op - O_S_CMP0) / 6 == 0 ? TY_UINT : TY_INT;
+      } else {
+        cc = (op - O_V_CMP0) % 6;
+        uint32_t ty = (op - O_V_CMP0) / 6;
+        ot = ty == 0 ? TY_INT : (ty == 1 ? TY_UINT : TY_FLOAT);
+      }
+      const char* sym[6] = {"==", "!=", ">", "<", ">=", "<="};
+      binop(n, sym[cc], ot, d);
+      return;
+    }
+    switch (op) {
+      case O_S_ADD_U32: return binop(n, "+", TY_UINT, d);
+      case O_S_MUL_I32: return binop(n, "*", TY_INT, d);
+      case O_S_LSHL_B32: return shift(n, 0, 1, T, "<<", 31, d);
+      case O_V_ADD_U32: return binop(n, "+", TY_UINT, d);
+      case O_V_SUB_U32: return binop(n, "-", TY_UINT, d);
+      case O_V_MUL_LO_U32: return binop(n, "*", TY_UINT, d);
+      case O_V_MAD_U32_U24: return call3("mad24", n, 3, TY_UINT, d);
+      case O_V_MUL_U32_U24: return call3("mul24", n, 2, TY_UINT, d);
+      case O_V_AND_B32: return binop(n, "&", T, d);
+      case O_V_OR_B32: return binop(n, "|", T, d);
+      case O_V_XOR_B32: return binop(n, "^", T, d);
+      case O_V_LSHLREV_B32: return shift(n, 1, 0, T, "<<", 31, d);
+      case O_V_LSHRREV_B32: return shift(n, 1, 0, TY_UINT, ">>", 31, d);
+      case O_V_ASHRREV_I32: return shift(n, 1, 0, TY_INT, ">>", 31, d);
+      case O_V_ADD_F32: return binop(n, "+", TY_FLOAT, d);
+      case O_V_SUB_F32: return binop(n, "-", TY_FLOAT, d);
+      case O_V_MUL_F32: return binop(n, "*", TY_FLOAT, d);
+      case O_V_FMA_F32: return call3("fma", n, 3, TY_FLOAT, d);
+      case O_V_CVT_F32_I32: return cast1("(float)", n, TY_INT, d);
+      case O_V_CVT_F32_U32: return cast1("(float)", n, TY_UINT, d);
+      case O_V_CVT_F64_F32: return cast1("(double)", n, TY_FLOAT, d);
+      case O_V_CVT_F64_I32: return cast1("(double)", n, TY_INT, d);
+      case O_V_CVT_F32_F64: return cast1("(float)", n, TY_DOUBLE, d);
+      case O_V_ADD_CO_U32: return binop(n, "+", TY_UINT, d);
+      case O_V_SUB_CO_U32: return binop(n, "-", TY_UINT, d);
+      case O_V_ADDC_CO_U32:
+        if (!n.fused) partial = true;
+        return binop(n, "+", n.fused ? T : TY_UINT, d);
+      case O_V_SUBB_CO_U32:
+        if (!n.fused) partial = true;
+        return binop(n, "-", n.fused ? T : TY_UINT, d);
+      case O_V_LSHLREV_B64: return shift(n, 1, 0, T, "<<", 63, d);
+      case O_V_ADD_F64: return binop(n, "+", TY_DOUBLE, d);
+      case O_V_MUL_F64: return binop(n, "*", TY_DOUBLE, d);
+      case O_V_FMA_F64: return call3("fma", n, 3, TY_DOUBLE, d);
+      case O_GLOBAL_LOAD_DWORD: return memref(n, 4, d);
+      case O_GLOBAL_LOAD_DWORDX2: return memref(n, 8, d);
+    }
+    partial = true;
+    w.s(T == TY_ULONG ? "0UL" : "0u");
+  }
+
+  // ---- statements ---------------------------------------------------------------
+  __device__ void block_stmts(uint32_t bl, int lvl) {
+    const BlockRec& B = b->lblocks[K->first_lblock + bl];
+    for (uint32_t i = B.first; i < B.end; ++i) {
+      uint32_t gi = K->first_instr + i;
+      if (b->lblock_of[gi] != bl) continue;
+      const int order[4] = {1, 2, 3, 0};
+      for (int q = 0; q < 4; ++q) {
+        uint32_t id = 4 * i + (uint32_t)order[q];
+        const Node& n = v.node(id);
+        if (n.kind == N_OP && order[q] == 0 && n.op == O_UNKNOWN && (fl[id] & 1)) {
+          w.indent(lvl);
+          w.s("__asm__(\"");
+          const uint8_t* p = b->text + b->line_start[b->instr_line[gi]];
+          const uint8_t* e = b->text + b->line_start[b->instr_line[gi] + 1] - 1;
+          while (p < e && is_space(*p)) ++p;
+          while (e > p && is_space(e[-1])) --e;
+          for (; p < e; ++p) {
+            if (*p == '"' || *p == '\\') w.c('\\');
+            w.c((char)*p);
+          }
+          w.s("\");\n");
+          partial = true;
+          continue;
+        }
+        if (n.kind == N_OP && order[q] == 0 && op_store(n.op) && (fl[id] & 1)) {
+          uint32_t width = n.op == O_GLOBAL_STORE_DWORDX2 ? 8 : 4;
+          uint8_t elem = mem_elem(n, width);
+          w.indent(lvl);
+          memref(n, width, 0);
+          w.s(" = ");
+          E(fwd(v, n.src[1]), elem, 0);
+          w.s(";\n");
+          continue;
+        }
+        if (vo[id] >= 0) {
+          uint8_t t = node_expr_type(id), want = vt[vo[id]];
+          w.indent(lvl);
+          w.s("var");
+          w.u64((uint64_t)vo[id]);
+          w.s(" = ");
+          conv_open(t, want);
+          node_expr(id, 0);
+          conv_close(t, want);
+          w.s(";\n");
+        }
+      }
+    }
+  }
+
+  // assignments of the join versions of block s along the edge p -> s
+  __device__ void copies(uint32_t p, uint32_t s, int lvl) {
+    uint32_t R = K->R;
+    uint32_t m = 0;
+    const uint8_t* pu = b->phi_used + K->state_off;
+    for (uint32_t reg = 0; reg < R; ++reg) {
+      if (!pu[(size_t)s * R + reg]) continue;
+      uint32_t dst = phiref(s, reg);
+      uint32_t o = b->st_out[K->state_off + (size_t)p * R + reg];
+      uint32_t src = fwd(v, o == kTop ? kUndef : o);
+      if (src == dst || src == kUndef) continue;
+      if (3 * (m + 1) > scap) {
+        atomicOr(b->err, ERR_CAPACITY);
+        break;
+      }
+      scratch[3 * m] = reg;
+      scratch[3 * m + 1] = dst;
+      scratch[3 * m + 2] = src;
+      ++m;
+    }
+    while (m) {
+      uint32_t pick = m;
+      for (uint32_t k = 0; k < m && pick == m; ++k) {
+        bool read = false;
+        for (uint32_t q = 0; q < m; ++q)
+          if (q != k && scratch[3 * q + 2] == scratch[3 * k + 1]) read = true;
+        if (!read) pick = k;
+      }
+      if (pick == m) {
+        partial = true;
+        pick = 0;
+      }
+      uint32_t dst = scratch[3 * pick + 1], src = scratch[3 * pick + 2];
+      int32_t x = phivar(dst);
+      w.indent(lvl);
+      w.s("var");
+      w.u64((uint64_t)x);
+      w.s(" = ");
+      E(src, vt[x], 0);
+      w.s(";\n");
+      for (uint32_t q = pick; q + 1 < m; ++q) {
+        scratch[3 * q] = scratch[3 * q + 3];
+        scratch[3 * q + 1] = scratch[3 * q + 4];
+        scratch[3 * q + 2] = scratch[3 * q + 5];
+      }
+      --m;
+    }
+  }
+
+  // condition under which block t's terminator goes to block dst
+  __device__ void cond_to(uint32_t t, uint32_t dst) {
+    const BlockRec& B = b->lblocks[K->first_lblock + t];
+    uint32_t i = b->lterm[K->first_lblock + t];
+    uint32_t c = fwd(v, v.node(4 * i).src[0]);
+    bool sense = b->sense[K->first_instr + i] != 0;
+    bool positive = (dst != B.succ0) ? sense : !sense;
+    if (r_node(c) && rpart(c) == PART_ENTIRE) {
+      const Node& n = v.node(rid(c));
+      if (n.kind == N_OP && (op_scmp(n.op) || op_vcmp(n.op)) && vo[rid(c)] < 0) {
+        if (!positive) {
+          w.c('!');
+          node_expr(rid(c), 0);
+          return;
+        }
+        // the comparison without its outer parentheses
+        Wr save = w;
+        node_expr(rid(c), 0);
+        uint32_t end = w.n;
+        if (w.on) {
+          for (uint32_t q = save.n; q + 2 < end; ++q) w.p[q] = w.p[q + 1];
+        }
+        w.n = end - 2;
+        return;
+      }
+    }
+    if (!positive) w.s("!(");
+    E(c, TY_NONE, 0);
+    if (!positive) w.c(')');
+  }
+};
+
+enum : uint32_t { R_BLOCK = 0, R_SEQ = 1, R_IF = 2, R_IFELSE = 3, R_LOOP = 4 };
+enum { RG_KIND = 0, RG_NCH = 1, RG_CH = 2, RG_BLOCK = 6, RG_S0 = 7, RG_S1 = 8, RG_NPRED = 9, RG_HEAD = 10, RG_TAIL = 11 };
+constexpr int RGW = 12;
+
+__device__ void print_args(Wr& w, const Batch& b, const KHdr& K, const ArgRec* A) {
+  bool any = false;
+  for (uint32_t q = 0; q < K.nargs; ++q) {
+    const ArgRec& a = A[q];
+    if (a.hidden) continue;
+    if (any) w.s(", ");
+    any = true;
+    if (a.pointer) {
+      w.s(a.space == 1 ? "__constant " : (a.space == 2 ? "__local " : "__global "));
+      if (a.is_const) w.s("const ");
+      w.s(tname(a.elem));
+      w.s(" *");
+    } else {
+      w.s(tname(a.elem));
+      w.c(' ');
+    }
+    w.mem(b.text + a.name_off, a.name_len);
+  }
+  if (!any) w.s("void");
+}
+
+__global__ void k_emit(Batch b, uint32_t* __restrict__ scratch_all, uint32_t* __restrict__ stk_all, int write) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  const ArgRec* A = b.args + (size_t)k * kMaxArgs;
+  Wr w{write ? b.out + b.kout_off[k] : nullptr, 0, write != 0};
+  bool last = k + 1 == b.K || b.kh[k + 1].file != K.file;
+  auto head = [&](bool args) {
+    w.s("__kernel void ");
+    w.mem(b.text + K.name_off, K.name_len);
+    w.c('(');
+    if (args) print_args(w, b, K, A);
+    w.s(")\n{\n");
+  };
+  uint32_t status;
+  if (K.bad) {
+    head(false);
+    w.s("    /* not decompiled: parse error */\n}\n");
+    status = ST_PARSE_ERROR;
+  } else if (K.n_lblock && K.root == kNone) {
+    head(true);
+    w.s("    /* not decompiled: unstructured control flow */\n}\n");
+    status = ST_PARTIAL;
+  } else {
+    head(true);
+    const size_t nb = 4 * (size_t)K.first_instr;
+    Em em;
+    em.v = KView{&b, &K, b.nodes + nb, A, k};
+    em.b = &b;
+    em.K = &K;
+    em.uses = b.uses + nb;
+    em.fl = b.nflag + nb;
+    em.nt = b.ntype + nb;
+    em.vo = b.var_of + nb;
+    em.pv = b.phi_var + K.state_off;
+    em.vt = b.var_type + nb + K.state_off;
+    em.scratch = scratch_all + K.wl_off;
+    em.scap = 4 * K.n_instr + K.n_lblock * K.R + 8;
+    em.w = w;
+    em.partial = false;
+    em.deep = false;
+    for (uint32_t x = 0; x < K.n_vars; ++x) {
+      em.w.s("    ");
+      em.w.s(tname(em.vt[x]));
+      em.w.s(" var");
+      em.w.u64(x);
+      em.w.s(";\n");
+    }
+    if (K.n_lblock) {
+      // region tree, explicit stack of (region, level << 8 | phase)
+      const uint32_t* RG = b.rg + (size_t)2 * K.first_lblock * RGW;
+      const BlockRec* BL = b.lblocks + K.first_lblock;
+      const uint8_t* cnd = nullptr;
+      uint32_t* st = stk_all + 4 * (size_t)K.first_lblock;
+      uint32_t cap = 4 * K.n_lblock, sp = 0;
+      auto push = [&](uint32_t r, uint32_t lvl, uint32_t ph) {
+        if (sp + 2 > cap) {
+          atomicOr(b.err, ERR_STACK);
+          return;
+        }
+        st[sp++] = r;
+        st[sp++] = (lvl << 8) | ph;
+      };
+      push(K.root, 1, 0);
+      while (sp >= 2) {
+        uint32_t info = st[--sp];
+        uint32_t r = st[--sp];
+        uint32_t lvl = info >> 8, ph = info & 0xFF;
+        const uint32_t* X = RG + (size_t)r * RGW;
+        switch (X[RG_KIND]) {
+          case R_BLOCK: {
+            uint32_t bl = X[RG_BLOCK];
+            em.block_stmts(bl, (int)lvl);
+            uint32_t term = b.lterm[K.first_lblock + bl];
+            bool cb = b.ctl[K.first_instr + term] == C_CBR && BL[bl].succ1 != kNone;
+            if (!cb && BL[bl].succ0 != kNone) em.copies(bl, BL[bl].succ0, (int)lvl);
+            break;
+          }
+          case R_SEQ:
+            if (ph == 0) {
+              push(r, lvl, 1);
+              push(X[RG_CH], lvl, 0);
+            } else {
+              push(X[RG_CH + 1], lvl, 0);
+            }
+            break;
+          case R_IF: {
+            const uint32_t* H = RG + (size_t)X[RG_CH] * RGW;
+            uint32_t t = H[RG_TAIL];
+            uint32_t th = RG[(size_t)X[RG_CH + 1] * RGW + RG_HEAD];
+            if (ph == 0) {
+              push(r, lvl, 1);
+              push(X[RG_CH], lvl, 0);
+            } else if (ph == 1) {
+              em.w.indent((int)lvl);
+              em.w.s("if (");
+              em.cond_to(t, th);
+              em.w.s(") {\n");
+              push(r, lvl, 2);
+              push(X[RG_CH + 1], lvl + 1, 0);
+            } else {
+              uint32_t other = BL[t].succ0 == th ? BL[t].succ1 : BL[t].succ0;
+              uint32_t mark = em.w.n;
+              em.w.indent((int)lvl);
+              em.w.s("} else {\n");
+              uint32_t mark2 = em.w.n;
+              em.copies(t, other, (int)lvl + 1);
+              if (em.w.n == mark2) em.w.n = mark;
+              em.w.indent((int)lvl);
+              em.w.s("}\n");
+              if (X[RG_NCH] == 3) push(X[RG_CH + 2], lvl, 0);
+            }
+            break;
+          }
+          case R_IFELSE: {
+            const uint32_t* H = RG + (size_t)X[RG_CH] * RGW;
+            uint32_t t = H[RG_TAIL];
+            uint32_t th = RG[(size_t)X[RG_CH + 1] * RGW + RG_HEAD];
+            if (ph == 0) {
+              push(r, lvl, 1);
+              push(X[RG_CH], lvl, 0);
+            } else if (ph == 1) {
+              em.w.indent((int)lvl);
+              em.w.s("if (");
+              em.cond_to(t, th);
+              em.w.s(") {\n");
+              push(r, lvl, 2);
+              push(X[RG_CH + 1], lvl + 1, 0);
+            } else if (ph == 2) {
+              em.w.indent((int)lvl);
+              em.w.s("} else {\n");
+              push(r, lvl, 3);
+              push(X[RG_CH + 2], lvl + 1, 0);
+            } else {
+              em.w.indent((int)lvl);
+              em.w.s("}\n");
+              if (X[RG_NCH] == 4) push(X[RG_CH + 3], lvl, 0);
+            }
+            break;
+          }
+          case R_LOOP: {
+            uint32_t nch = X[RG_NCH];
+            uint32_t h = RG[(size_t)X[RG_CH] * RGW + RG_HEAD];
+            uint32_t t = RG[(size_t)X[RG_CH + nch - 1] * RGW + RG_TAIL];
+            if (ph == 0) {
+              em.w.indent((int)lvl);
+              em.w.s("do {\n");
+              push(r, lvl, 1);
+              for (int q = (int)nch - 1; q >= 0; --q) push(X[RG_CH + q], lvl + 1, 0);
+            } else {
+              uint32_t exitb = BL[t].succ0 == h ? BL[t].succ1 : BL[t].succ0;
+              em.copies(t, h, (int)lvl + 1);
+              em.w.indent((int)lvl);
+              em.w.s("} while (");
+              em.cond_to(t, h);
+              em.w.s(");\n");
+              if (exitb != kNone) em.copies(t, exitb, (int)lvl);
+            }
+            break;
+          }
+        }
+      }
+      (void)cnd;
+    }
+    em.w.s("}\n");
+    w = em.w;
+    status = em.partial ? ST_PARTIAL : ST_OK;
+    if (em.deep) atomicOr(b.err, ERR_STACK);
+  }
+  if (!last) w.c('\n');
+  if (!write) {
+    b.kout_len[k] = w.n;
+    K.status = status;
+  }
+}
+
+// per file: output offset and worst status of its kernels
+__global__ void k_file_out(Batch b, uint32_t total) {
+  uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f > b.F) return;
+  uint32_t lo = 0, hi = b.K;  // first kernel with file >= f
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (b.kh[mid].file < f) lo = mid + 1;
+    else hi = mid;
+  }
+  b.file_out_off[f] = lo < b.K ? b.kout_off[lo] : total;
+  if (f == b.F) return;
+  int32_t st = 0;
+  for (uint32_t k = lo; k < b.K && b.kh[k].file == f; ++k) st = max(st, (int32_t)b.kh[k].status);
+  b.file_status[f] = st;
+}
+
+void launch_emit_size(Batch& b, uint32_t* scratch, uint32_t* stk, cudaStream_t s) {
+  if (!b.K) return;
+  k_emit<<<(b.K + 63) / 64, 64, 0, s>>>(b, scratch, stk, 0);
+}
+void launch_emit_scan(Batch& b, ScanScratch sc, uint32_t* total, cudaStream_t s) {
+  if (!b.K) return;
+  launch_scan(b.kout_len, b.kout_off, b.K, 0, false, sc, total, b.err, s);
+}
+void launch_emit_write(Batch& b, uint32_t* scratch, uint32_t* stk, uint32_t total, cudaStream_t s) {
+  if (b.K) k_emit<<<(b.K + 63) / 64, 64, 0, s>>>(b, scratch, stk, 1);
+  k_file_out<<<(b.F + 1 + 127) / 128, 128, 0, s>>>(b, total);
+}
+
+}  // namespace gd

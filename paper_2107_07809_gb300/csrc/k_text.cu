@@ -1,0 +1,295 @@
+// k_text.cu — tokenisation and body extraction on the GPU.
+//
+// S1 (line tokenisation): every byte of the batch text is read once.  A tile
+// of 16 KiB is moved into shared memory with one bulk TMA copy
+// (cp.async.bulk + mbarrier), each thread counts the '\n' bytes of 64
+// contiguous bytes, a block scan plus a single-pass decoupled look-back gives
+// each newline its global rank, and the line starts are written.
+// S2 (body extraction, Listing 2 of the paper): the row state machine
+// (.kernel / .config / .text) becomes three scans over the rows — the last
+// state marker, the last file start and the running count of .kernel rows —
+// after which every row knows its kernel and its section independently.
+#include "gd_kernels.h"
+
+namespace gd {
+
+// ---------------------------------------------------------------------------
+// S1: newline scan
+// ---------------------------------------------------------------------------
+constexpr int LS_THREADS = 256;
+constexpr int LS_PER_THREAD = 64;
+constexpr int LS_TILE = LS_THREADS * LS_PER_THREAD;
+
+__global__ void __launch_bounds__(LS_THREADS) k_line_scan(const uint8_t* __restrict__ text, uint64_t n,
+                                                          uint32_t* __restrict__ line_start,
+                                                          uint64_t* __restrict__ status, uint32_t* counters,
+                                                          uint32_t* err) {
+  __shared__ __align__(128) uint8_t buf[LS_TILE];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tile, s_prefix, s_warp[32];
+  if (threadIdx.x == 0) s_tile = atomicAdd(&counters[0], 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * LS_TILE;
+  const uint64_t rem = n > base ? n - base : 0;
+  const uint32_t nbytes = rem < (uint64_t)LS_TILE ? (uint32_t)rem : (uint32_t)LS_TILE;
+  const uint32_t bulk = nbytes & ~15u;  // TMA part: 16-byte multiple, 16-byte aligned source
+  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
+  if (threadIdx.x == 0 && bulk) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bulk) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(text + base), "r"(bulk), "r"(mb)
+        : "memory");
+  }
+  for (uint32_t j = bulk + threadIdx.x; j < (uint32_t)LS_TILE; j += blockDim.x)
+    buf[j] = j < nbytes ? text[base + j] : 0;
+  __syncthreads();
+  if (bulk) {
+    uint32_t done = 0, spins = 0;
+    while (!done) {
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+          : "=r"(done)
+          : "r"(mb)
+          : "memory");
+      if (!done && ++spins > (1u << 22)) {
+        atomicOr(err, ERR_MBAR);
+        break;
+      }
+    }
+  }
+  // count newlines in this thread's 64 contiguous bytes
+  const uint4* mine = reinterpret_cast<const uint4*>(buf + threadIdx.x * LS_PER_THREAD);
+  uint4 w[4];
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w[k] = mine[k];
+    cnt += __popc(__vcmpeq4(w[k].x, 0x0A0A0A0Au)) + __popc(__vcmpeq4(w[k].y, 0x0A0A0A0Au)) +
+           __popc(__vcmpeq4(w[k].z, 0x0A0A0A0Au)) + __popc(__vcmpeq4(w[k].w, 0x0A0A0A0Au));
+  }
+  cnt >>= 3;
+  uint32_t total;
+  uint32_t incl = block_incl_scan<ScanSum>(cnt, s_warp, &total);
+  if (threadIdx.x < 32) {
+    uint32_t p = lookback<ScanSum>(status, tile, total, err);
+    if (threadIdx.x == 0) {
+      s_prefix = p;
+      if (tile == gridDim.x - 1) counters[1] = p + total;  // number of lines
+    }
+  }
+  __syncthreads();
+  uint32_t rank = s_prefix + incl - cnt;
+  if (tile == 0 && threadIdx.x == 0) line_start[0] = 0;
+  const uint64_t my0 = base + (uint64_t)threadIdx.x * LS_PER_THREAD;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint32_t ws[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t m = __vcmpeq4(ws[q], 0x0A0A0A0Au);
+      while (m) {
+        int bit = __ffs(m) - 1;  // lowest byte first = text order (little endian)
+        uint32_t byte = (uint32_t)bit >> 3;
+        line_start[1 + rank++] = (uint32_t)(my0 + k * 16 + q * 4 + byte + 1);
+        m &= ~(0xFFu << (byte * 8));
+      }
+    }
+  }
+}
+
+void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uint64_t* tile_status,
+                      uint32_t* counters, uint32_t* err, cudaStream_t s) {
+  uint32_t tiles = (uint32_t)((n + LS_TILE - 1) / LS_TILE);
+  if (!tiles) tiles = 1;
+  cudaMemsetAsync(tile_status, 0, sizeof(uint64_t) * tiles, s);
+  cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), s);
+  k_line_scan<<<tiles, LS_THREADS, 0, s>>>(text, n, line_start, tile_status, counters, err);
+}
+uint32_t line_scan_tiles(uint64_t n) { return (uint32_t)((n + LS_TILE - 1) / LS_TILE) + 1; }
+
+// ---------------------------------------------------------------------------
+// generic single-pass scan of u32 arrays
+// ---------------------------------------------------------------------------
+constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
+
+template <class Op, bool Incl>
+__global__ void __launch_bounds__(SC_THREADS) k_scan(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                     uint32_t n, uint64_t* status, uint32_t* counter,
+                                                     uint32_t* total_out, uint32_t* err) {
+  __shared__ uint32_t sm[SC_TILE];
+  __shared__ uint32_t s_tile, s_prefix, s_warp[32];
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * SC_TILE;
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    uint64_t i = base + (uint64_t)k * SC_THREADS + threadIdx.x;
+    sm[k * SC_THREADS + threadIdx.x] = i < n ? in[i] : Op::id;
+  }
+  __syncthreads();
+  uint32_t v[SC_ITEMS];
+  uint32_t acc = Op::id;
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    acc = Op::op(acc, sm[threadIdx.x * SC_ITEMS + k]);
+    v[k] = acc;
+  }
+  uint32_t total;
+  uint32_t incl = block_incl_scan<Op>(acc, s_warp, &total);
+  // exclusive prefix of this thread inside the tile: inclusive minus own (for sum),
+  // or the previous thread's inclusive value (general)
+  uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t texcl = lane ? prev : (warp ? s_warp[warp - 1] : Op::id);
+  if (threadIdx.x < 32) {
+    uint32_t p = lookback<Op>(status, tile, total, err);
+    if (threadIdx.x == 0) {
+      s_prefix = p;
+      if (tile == gridDim.x - 1 && total_out) *total_out = Op::op(p, total);
+    }
+  }
+  __syncthreads();
+  const uint32_t pre = Op::op(s_prefix, texcl);
+  uint32_t run = pre;
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    uint32_t r = Op::op(pre, v[k]);
+    sm[threadIdx.x * SC_ITEMS + k] = Incl ? r : run;
+    run = r;
+  }
+  __syncthreads();
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    uint64_t i = base + (uint64_t)k * SC_THREADS + threadIdx.x;
+    if (i < n) out[i] = sm[k * SC_THREADS + threadIdx.x];
+  }
+}
+
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t n, int op, bool inclusive, ScanScratch sc,
+                 uint32_t* total_out, uint32_t* err, cudaStream_t s) {
+  uint32_t tiles = (n + SC_TILE - 1) / SC_TILE;
+  if (!tiles) tiles = 1;
+  cudaMemsetAsync(sc.status, 0, sizeof(uint64_t) * tiles, s);
+  cudaMemsetAsync(sc.counter, 0, sizeof(uint32_t), s);
+  if (op == 0 && inclusive) k_scan<ScanSum, true><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+  if (op == 0 && !inclusive) k_scan<ScanSum, false><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+  if (op == 1 && inclusive) k_scan<ScanMax, true><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+  if (op == 1 && !inclusive) k_scan<ScanMax, false><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+}
+uint32_t scan_tiles(uint32_t n) { return (n + SC_TILE - 1) / SC_TILE + 1; }
+
+// ---------------------------------------------------------------------------
+// S2: rows, files, kernels
+// ---------------------------------------------------------------------------
+// first line of every non-empty file (files end with '\n', so a file start is a line start)
+__global__ void k_file_starts(const uint32_t* __restrict__ line_start, uint32_t L, const uint64_t* __restrict__ file_off,
+                              uint32_t F, uint8_t* __restrict__ file_start) {
+  uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  uint64_t a = file_off[f], b = file_off[f + 1];
+  if (a >= b) return;
+  uint32_t lo = 0, hi = L;  // first line with start >= a
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (line_start[mid] < a) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < L) file_start[lo] = 1;
+}
+
+__global__ void k_classify(const uint8_t* __restrict__ text, const uint32_t* __restrict__ line_start, uint32_t L,
+                           const uint8_t* __restrict__ file_start, uint8_t* __restrict__ kind, uint32_t* __restrict__ mk,
+                           uint32_t* __restrict__ fs, uint32_t* __restrict__ kf) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  const uint8_t* p = text + line_start[i];
+  const uint8_t* e = text + line_start[i + 1] - 1;  // the '\n'
+  while (p < e && is_space(*p)) ++p;
+  while (e > p && is_space(e[-1])) --e;
+  uint8_t k = LK_BLANK;
+  if (p < e && !(*p == '#' || *p == ';' || (e - p >= 2 && p[0] == '/' && p[1] == '/'))) {
+    const uint8_t* t = p;
+    while (t < e && !is_space(*t)) ++t;
+    if (tok_eq(p, t, ".kernel")) k = LK_KERNEL;
+    else if (tok_eq(p, t, ".config")) k = LK_CONFIG;
+    else if (tok_eq(p, t, ".text")) k = LK_TEXT;
+    else if (t == e && e - p >= 2 && e[-1] == ':') k = LK_LABEL;
+    else k = LK_ROW;
+  }
+  kind[i] = k;
+  mk[i] = (k == LK_KERNEL || k == LK_CONFIG || k == LK_TEXT) ? i + 1 : 0;
+  fs[i] = file_start[i] ? i + 1 : 0;
+  kf[i] = k == LK_KERNEL ? 1 : 0;
+}
+
+// row type of every line: state from the last marker, kernel from the .kernel count
+__global__ void k_assign(const uint8_t* __restrict__ kind, const uint32_t* __restrict__ mkmax,
+                         const uint32_t* __restrict__ fsmax, const uint32_t* __restrict__ kcnt, uint32_t L,
+                         uint8_t* __restrict__ rowtype, uint32_t* __restrict__ is_instr, uint32_t* __restrict__ is_label) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  uint8_t rt = RT_NONE;
+  uint32_t f0 = fsmax[i] - 1;  // a file start precedes every line
+  uint32_t before = kcnt[f0] - (kind[f0] == LK_KERNEL ? 1u : 0u);
+  if (kcnt[i] > before) {  // a .kernel row of this file has been seen
+    uint8_t k = kind[i];
+    uint8_t st = kind[mkmax[i] - 1];
+    if (k == LK_KERNEL) rt = RT_KERNEL;
+    else if (k == LK_LABEL || k == LK_ROW) {
+      if (st == LK_CONFIG) rt = RT_CFG;
+      else if (st == LK_TEXT) rt = k == LK_LABEL ? RT_LABEL : RT_INSTR;
+    }
+  }
+  rowtype[i] = rt;
+  is_instr[i] = rt == RT_INSTR;
+  is_label[i] = rt == RT_LABEL;
+}
+
+__global__ void k_scatter_rows(const uint8_t* __restrict__ rowtype, const uint32_t* __restrict__ instr_excl,
+                               const uint32_t* __restrict__ label_excl, const uint32_t* __restrict__ kcnt, uint32_t L,
+                               uint32_t* __restrict__ instr_line, uint32_t* __restrict__ label_line,
+                               uint32_t* __restrict__ label_instr, KHdr* __restrict__ kh) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  uint8_t rt = rowtype[i];
+  if (rt == RT_INSTR) instr_line[instr_excl[i]] = i;
+  else if (rt == RT_LABEL) {
+    label_line[label_excl[i]] = i;
+    label_instr[label_excl[i]] = instr_excl[i];
+  } else if (rt == RT_KERNEL) {
+    KHdr& k = kh[kcnt[i] - 1];
+    k.line = i;
+    k.first_instr = instr_excl[i];
+    k.first_label = label_excl[i];
+  }
+}
+
+void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, const uint64_t* file_off, uint32_t F,
+                 RowArrays& ra, ScanScratch sc, uint32_t* totals, uint32_t* err, cudaStream_t s) {
+  const int T = 256;
+  cudaMemsetAsync(ra.file_start, 0, L, s);
+  if (F) k_file_starts<<<(F + T - 1) / T, T, 0, s>>>(line_start, L, file_off, F, ra.file_start);
+  k_classify<<<(L + T - 1) / T, T, 0, s>>>(text, line_start, L, ra.file_start, ra.kind, ra.t0, ra.t1, ra.t2);
+  launch_scan(ra.t0, ra.mkmax, L, 1, true, sc, nullptr, err, s);
+  launch_scan(ra.t1, ra.fsmax, L, 1, true, sc, nullptr, err, s);
+  launch_scan(ra.t2, ra.kcnt, L, 0, true, sc, &totals[0], err, s);  // totals[0] = kernels
+  k_assign<<<(L + T - 1) / T, T, 0, s>>>(ra.kind, ra.mkmax, ra.fsmax, ra.kcnt, L, ra.rowtype, ra.t0, ra.t1);
+  launch_scan(ra.t0, ra.instr_excl, L, 0, false, sc, &totals[1], err, s);  // totals[1] = instructions
+  launch_scan(ra.t1, ra.label_excl, L, 0, false, sc, &totals[2], err, s);  // totals[2] = labels
+}
+
+void launch_scatter_rows(uint32_t L, RowArrays& ra, uint32_t* instr_line, uint32_t* label_line, uint32_t* label_instr,
+                         KHdr* kh, cudaStream_t s) {
+  const int T = 256;
+  k_scatter_rows<<<(L + T - 1) / T, T, 0, s>>>(ra.rowtype, ra.instr_excl, ra.label_excl, ra.kcnt, L, instr_line,
+                                               label_line, label_instr, kh);
+}
+
+}  // namespace gd
