@@ -272,10 +272,10 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[8], s));
   // S12
-  b.rg = W.get<uint32_t>("regions", 24ull * b.NLB + 24);
-  uint32_t* seen = W.get<uint32_t>("rg_seen", 2ull * b.NLB + 2);
-  uint32_t* rstk = W.get<uint32_t>("rg_stack", 4ull * b.NLB + 4);
-  uint8_t* alive = W.get<uint8_t>("rg_alive", 2ull * b.NLB + 2);
+  b.rg = W.get<uint32_t>("regions", 12ull * kRegionsPerBlock * b.NLB + 24);
+  uint32_t* seen = W.get<uint32_t>("rg_seen", (size_t)kRegionsPerBlock * b.NLB + 2);
+  uint32_t* rstk = W.get<uint32_t>("rg_stack", (size_t)kStackPerBlock * b.NLB + 4);
+  uint8_t* alive = W.get<uint8_t>("rg_alive", (size_t)kRegionsPerBlock * b.NLB + 2);
   uint8_t* cond = W.get<uint8_t>("rg_cond", b.NLB + 1);
   launch_regions(b, seen, rstk, alive, cond, s);
   CK(cudaGetLastError());

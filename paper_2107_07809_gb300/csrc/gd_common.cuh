@@ -15,6 +15,14 @@ constexpr int kMaxArgs = 32;        // .arg rows per kernel
 constexpr int kMaxExecDepth = 64;   // nested exec-mask forms per kernel
 constexpr uint32_t kMaxRegs = 1024; // tracked registers per kernel (join ids use 10 bits)
 constexpr uint32_t kMaxBlocks = 1u << 18;
+// regions per logical block: every merge makes one region; merges that do not
+// shrink the graph are the self-loop ones (at most one per block), so a kernel
+// of n blocks ends with fewer than 3n regions
+constexpr uint32_t kRegionsPerBlock = 3;
+// stack words per logical block: the reduction's search (< 2 pushes per live
+// region) and the printer's frames (2 words, at most 2 per level of a tree of
+// fewer than 3n regions)
+constexpr uint32_t kStackPerBlock = 12;
 
 // ---- error bits (kernel-wide `err` word) ----------------------------------------
 enum : uint32_t { ERR_LOOKBACK = 1, ERR_MBAR = 2, ERR_CAPACITY = 4, ERR_STACK = 8 };

@@ -676,11 +676,11 @@ __global__ void k_emit(Batch b, uint32_t* __restrict__ scratch_all, uint32_t* __
     }
     if (K.n_lblock) {
       // region tree, explicit stack of (region, level << 8 | phase)
-      const uint32_t* RG = b.rg + (size_t)2 * K.first_lblock * RGW;
+      const uint32_t* RG = b.rg + (size_t)kRegionsPerBlock * K.first_lblock * RGW;
       const BlockRec* BL = b.lblocks + K.first_lblock;
       const uint8_t* cnd = nullptr;
-      uint32_t* st = stk_all + 4 * (size_t)K.first_lblock;
-      uint32_t cap = 4 * K.n_lblock, sp = 0;
+      uint32_t* st = stk_all + kStackPerBlock * (size_t)K.first_lblock;
+      uint32_t cap = kStackPerBlock * K.n_lblock, sp = 0;
       auto push = [&](uint32_t r, uint32_t lvl, uint32_t ph) {
         if (sp + 2 > cap) {
           atomicOr(b.err, ERR_STACK);

@@ -23,7 +23,7 @@ enum { RG_KIND = 0, RG_NCH = 1, RG_CH = 2, RG_BLOCK = 6, RG_S0 = 7, RG_S1 = 8, R
 constexpr int RGW = 12;
 
 struct Red {
-  uint32_t* rg;        // 2n regions of this kernel
+  uint32_t* rg;        // 3n regions of this kernel
   uint32_t* seen;      // epoch per region
   uint32_t* stk;
   uint8_t* alive;
@@ -194,10 +194,10 @@ __global__ void k_regions(Batch b, uint32_t* __restrict__ seen_all, uint32_t* __
   if (K.bad || !K.n_lblock) return;
   uint32_t n = K.n_lblock, base = K.first_lblock;
   Red rd;
-  rd.rg = b.rg + (size_t)2 * base * RGW;
-  rd.seen = seen_all + 2 * (size_t)base;
-  rd.stk = stk_all + 4 * (size_t)base;
-  rd.alive = alive_all + 2 * (size_t)base;
+  rd.rg = b.rg + (size_t)kRegionsPerBlock * base * RGW;
+  rd.seen = seen_all + kRegionsPerBlock * (size_t)base;
+  rd.stk = stk_all + kStackPerBlock * (size_t)base;
+  rd.alive = alive_all + kRegionsPerBlock * (size_t)base;
   rd.B = b.lblocks + base;
   rd.cond = cond_all + base;
   rd.n = n;
@@ -206,7 +206,7 @@ __global__ void k_regions(Batch b, uint32_t* __restrict__ seen_all, uint32_t* __
   rd.epoch = 0;
   uint8_t* cnd = cond_all + base;
   // reachable blocks from the entry (the stack doubles as the DFS stack)
-  for (uint32_t x = 0; x < 2 * n; ++x) {
+  for (uint32_t x = 0; x < kRegionsPerBlock * n; ++x) {
     rd.alive[x] = 0;
     rd.seen[x] = 0;
   }
@@ -246,6 +246,7 @@ __global__ void k_regions(Batch b, uint32_t* __restrict__ seen_all, uint32_t* __
   uint32_t nalive = 0;
   for (uint32_t x = 0; x < n; ++x) nalive += rd.alive[x];
   while (nalive > 1) {
+    if (rd.nreg >= kRegionsPerBlock * n) { atomicOr(b.err, ERR_CAPACITY); return; }  // cannot happen: < 3n
     ++rd.epoch;
     sp = 0;
     rd.stk[sp++] = rd.entry;
@@ -262,16 +263,15 @@ __global__ void k_regions(Batch b, uint32_t* __restrict__ seen_all, uint32_t* __
       }
       uint32_t* X = rd.R(x);
       if (X[RG_S1] != kNone && rd.seen[X[RG_S1]] != rd.epoch) {
-        if (sp >= 4 * n) { atomicOr(b.err, ERR_CAPACITY); return; }
+        if (sp >= kStackPerBlock * n) { atomicOr(b.err, ERR_CAPACITY); return; }
         rd.stk[sp++] = X[RG_S1];
       }
       if (X[RG_S0] != kNone && rd.seen[X[RG_S0]] != rd.epoch) {
-        if (sp >= 4 * n) { atomicOr(b.err, ERR_CAPACITY); return; }
+        if (sp >= kStackPerBlock * n) { atomicOr(b.err, ERR_CAPACITY); return; }
         rd.stk[sp++] = X[RG_S0];
       }
     }
     if (!merged) return;  // does not reduce: unstructured
-    if (rd.nreg >= 2 * n) { atomicOr(b.err, ERR_CAPACITY); return; }
   }
   K.root = rd.entry;
 }

@@ -57,3 +57,58 @@ def test_ir_parity_golden_fixtures(dec):
     g = os.path.join(os.path.dirname(__file__), "golden")
     files = [open(os.path.join(g, f), "rb").read() for f in sorted(os.listdir(g)) if f.endswith(".s")]
     _check_ir(dec, files)
+
+
+# ---- OpenCL text: byte-identical to the oracle -------------------------------
+def _check_text(dec, files):
+    ids = dec.submit_batch(files)
+    assert len(ids) == len(files)
+    for n, (f, j) in enumerate(zip(files, ids)):
+        want = oracle.decompile(f)
+        got, status = dec.fetch_opencl(j)
+        assert got == want.text, f"file {n}: OpenCL text differs"
+        assert status == want.worst, f"file {n}: status {status} vs {want.worst}"
+
+
+def test_text_parity_config0(dec):
+    _check_text(dec, _files(0, 1))
+
+
+def test_text_parity_golden(dec):
+    import os
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    _check_text(dec, [open(os.path.join(g, f), "rb").read() for f in sorted(os.listdir(g)) if f.endswith(".s")])
+
+
+def test_text_parity_config1(dec):
+    _check_text(dec, _files(1, 2000))
+
+
+def test_text_parity_multi_kernel_files(dec):
+    ks = _files(1, 30, max_len=600)
+    files = [b"".join(ks[0:10]), b"junk\n.text\n" + b"".join(ks[10:20]), b"", b"".join(ks[20:30])]
+    _check_text(dec, files)
+
+
+def test_text_parity_serving_sizes(dec):
+    _check_text(dec, _files(4, 40))
+
+
+def test_text_parity_large_cfg(dec):
+    _check_text(dec, _files(3, 2))
+
+
+def test_text_parity_edge_cases(dec):
+    import os
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    base = open(os.path.join(g, "p194_global_offset.s"), "rb").read()
+    files = [
+        base.replace(b"        s_endpgm", b"        v_frobnicate_b32 v7, v6\n        s_endpgm"),
+        base.replace(b"        v_mov_b32 v6, s2", b"        v_mov_b32 v6, s2x"),
+        base.replace(b"        v_mov_b32 v6, s2", b"        s_branch .Lnowhere"),
+        base.replace(b"        v_mov_b32 v6, s2", b"        v_mov_b32 v99, v0"),
+        base.replace(b".cws 64, 1, 1", b".cws 64, x, 1"),
+        b".kernel empty\n    .config\n        .dims x\n",
+        b"no kernel here\n",
+    ]
+    _check_text(dec, files)
