@@ -1,0 +1,302 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: GCN instructions decompiled per second on GB300.
+
+One step decompiles the whole workload batch (every stage S1..S13 of the
+method) through the C ABI.  Default workload: 10,000 seeded synthetic kernels
+with log-uniform lengths 50..2000 (the plain-method-at-scale configuration),
+one kernel per file, text resident in HBM when the timed region starts
+(`value`).  `e2e` measures the same through the host-buffer entry points
+(submit_batch + fetch_opencl), host<->device copies inside the timed region.
+
+--impl reference times the CPU oracle (single-threaded) on bounded samples of
+the same workload, the comparison arm.  Multi-GPU (torchrun): every rank
+decompiles its own kernels (weak scaling); there is no collective.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gcngen  # noqa: E402
+
+WORKLOADS = {
+    # name: (preset, kernels)
+    "config1": (1, 10_000),
+    "config3": (3, 64),
+}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name, rank, kernels=None):
+    cfg, n = WORKLOADS[name]
+    if kernels:
+        n = kernels
+    params = gcngen.preset(cfg)
+    batch = gcngen.generate(params, n, seed=gcngen.SEED_BASE + cfg, first=rank * n)
+    return cfg, batch
+
+
+def oracle_rate(batch, budget_s, start=0):
+    """Single-threaded oracle over consecutive kernels until `budget_s` elapses."""
+    import oracle
+
+    done_instr, t0, k = 0, time.perf_counter(), start
+    n = len(batch)
+    while time.perf_counter() - t0 < budget_s and k < start + n:
+        hi = min(k + 50, start + n)
+        lo_, hi_ = k % n, (hi - 1) % n + 1
+        oracle.decompile_batch(batch.text, batch.offsets[lo_:hi_ + 1] if hi_ > lo_ else batch.offsets[lo_:lo_ + 2], 1)
+        done_instr += int(batch.ninstr[lo_:hi_].sum())
+        k = hi
+    dt = time.perf_counter() - t0
+    return done_instr / dt, done_instr, k - start, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg, batch = make_workload(args.workload, 0, args.kernels)
+    per_step = 6.0
+    for _ in range(args.warmup):
+        oracle_rate(batch, 1.0)
+    rates, instrs, kern = [], 0, 0
+    pos = 0
+    for _ in range(args.steps):
+        r, ni, nk, dt = oracle_rate(batch, per_step, start=pos)
+        pos = (pos + nk) % len(batch)
+        rates.append(r)
+        instrs += ni
+        kern += nk
+    value = float(statistics.mean(rates))
+    sample = f"{kern} kernels ({instrs} instrs) over {args.steps} steps of ~{per_step:.0f} s, single thread"
+    line = {
+        "impl": "reference", "metric": "GCN instrs decompiled/sec", "value": value, "unit": "instr/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {len(batch)} seeded synthetic kernels (preset {cfg})"},
+        "cpu_baseline": {"value": value, "unit": "instr/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "instr/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic_bytes(st):
+    """Contract bytes of one pass: text in + OpenCL out + the IR arrays the
+    parity tests compare (instruction records, block ids, block tables, headers)."""
+    return {
+        "text_in": st["text_bytes"],
+        "text_out": st["out_bytes"],
+        "ir": 32 * st["instrs"] + 4 * st["instrs"] + 4 * st["instrs"] + 16 * st["pblocks"] + 16 * st["lblocks"]
+        + 32 * st["kernels"],
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config1", choices=sorted(WORKLOADS))
+    ap.add_argument("--kernels", type=int, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2107_07809_gb300 as pkg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.build()
+    cfg, batch = make_workload(args.workload, rank, args.kernels)
+    n_files = len(batch)
+    total_instr = batch.total_instr
+    d_text = torch.from_numpy(batch.text).to(f"cuda:{local}")
+    d_off = torch.from_numpy(batch.offsets.view(np.int64)).to(f"cuda:{local}")
+    dec = pkg.Decompiler(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dec.run_device(d_text.data_ptr(), int(batch.text.nbytes), d_off.data_ptr(), n_files, stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    out_ptr, off_ptr, st_ptr, out_bytes = dec.result_device()
+
+    # byte-exact parity on a sample of the benchmarked batch (outside the timed region)
+    parity = {"checked": 0, "mismatches": 0}
+    if rank == 0:
+        import oracle
+
+        n_check = min(200, n_files)
+        texts, statuses = dec.result_copy(0, n_check)
+        for f in range(n_check):
+            want = oracle.decompile(batch.kernel(f))
+            parity["checked"] += 1
+            parity["mismatches"] += int(texts[f] != want.text or statuses[f] != want.worst)
+
+    stats = dec.run_stats()
+    stats["text_bytes"] = int(batch.text.nbytes)
+    launches = dec.launches()
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    stage_ms = dec.stage_times()
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = total_instr * world / (ms / 1e3)
+
+    # end to end through the host-buffer API
+    files = [batch.kernel(i) for i in range(n_files)]
+    h2d = int(batch.text.nbytes) + 8 * (n_files + 1)
+    e2e_ms = []
+    d2h = 0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = dec.submit_batch(files)
+        outs = [dec.fetch_opencl(j) for j in ids]
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        d2h = sum(len(o[0]) for o in outs) + 12 * n_files
+    e2e_val = total_instr * world / (statistics.median(e2e_ms) / 1e3) if e2e_ms else None
+
+    peaks, src = measured_peaks()
+    ab = algorithmic_bytes(stats)
+    bytes_per_pass = ab["text_in"] + ab["text_out"] + ab["ir"]
+    dom = max(stage_ms, key=stage_ms.get)
+    dom_ms = stage_ms[dom]
+    achieved = bytes_per_pass / (dom_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "bytes_per_instr": bytes_per_pass / total_instr,
+                "path_frac": bytes_per_pass / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, ni, nk, dt = oracle_rate(batch, 12.0)
+        cpu = {"value": r, "unit": "instr/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {nk} kernels of the workload ({ni} instrs, {dt:.1f} s), single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": "GCN instrs decompiled/sec", "value": value, "unit": "instr/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {n_files} seeded synthetic kernels (preset {cfg}), "
+                                   f"{total_instr} instrs, {stats['text_bytes']} text bytes per GPU",
+                       "kernels": n_files, "instrs": total_instr, "text_bytes": stats["text_bytes"],
+                       "l2": "inputs larger than L2 (text > 129 MB); no flush between steps",
+                       "form": "batched: one pipeline pass over all kernels per step"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "instr/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.median(e2e_ms) if e2e_ms else None},
+            "gpu_launches": launches * args.steps, "clocks": clk.summary(), "stage_ms": stage_ms,
+            "parity": parity, "run_stats": stats,
+        }
+        print(json.dumps(line), flush=True)
+    dec.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

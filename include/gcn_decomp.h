@@ -111,10 +111,28 @@ int gcn_decomp_run_device(gcn_decomp_t *h, const uint8_t *d_text, uint64_t text_
 int gcn_decomp_result_device(gcn_decomp_t *h, const uint8_t **d_out, const uint64_t **d_out_off,
                              const int32_t **d_status, uint64_t *out_bytes);
 
+/* Copy files [f0, f1) of the last run_device result to host memory:
+ * buf[0..cap) receives their OpenCL text back to back, off_out[0..f1-f0]
+ * (u64, relative to buf) their boundaries, status_out[0..f1-f0) (i32) their
+ * worst status; either array may be NULL.  buf == NULL only fills off_out.
+ * Synchronises the handle's stream.  Errors: GCN_EINVAL (no run, bad range,
+ * cap too small), GCN_ECUDA. */
+int gcn_decomp_result_copy(gcn_decomp_t *h, uint64_t f0, uint64_t f1, void *buf, size_t cap, uint64_t *off_out,
+                           int32_t *status_out);
+
 /* Per-stage device times of the last run (milliseconds, CUDA events on the
  * run's stream), stage names in *names (static strings).  Returns the number
  * of stages (<= cap) or a negative code. */
 int gcn_decomp_stage_times(gcn_decomp_t *h, float *ms, const char **names, int cap);
+
+/* Sizes of the last pipeline run: out[0..7] = lines, kernels, instructions,
+ * labels, physical blocks, logical blocks, register-state words, output bytes.
+ * Returns the number of values written (<= cap) or a negative code. */
+int gcn_decomp_run_stats(gcn_decomp_t *h, uint64_t *out, int cap);
+
+/* Number of CUDA kernels the library launched for the last pipeline run
+ * (run_device or submit_batch); 0 before the first run. */
+uint64_t gcn_decomp_launches(gcn_decomp_t *h);
 
 /* Last error message of this thread (static storage; never NULL). */
 const char *gcn_decomp_last_error(void);

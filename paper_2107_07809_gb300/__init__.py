@@ -101,6 +101,10 @@ def lib():
             L.gcn_decomp_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
                                                  ctypes.POINTER(ctypes.c_char_p), i32]
             L.gcn_decomp_last_error.restype = ctypes.c_char_p
+            L.gcn_decomp_result_copy.argtypes = [vp, u64, u64, vp, sz, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_int32)]
+            L.gcn_decomp_run_stats.argtypes = [vp, ctypes.POINTER(u64), i32]
+            L.gcn_decomp_launches.argtypes = [vp]
+            L.gcn_decomp_launches.restype = u64
             _lib = L
     return _lib
 
@@ -184,6 +188,28 @@ class Decompiler:
         _ck(lib().gcn_decomp_result_device(self._h, ctypes.byref(o), ctypes.byref(oo), ctypes.byref(st),
                                            ctypes.byref(nb)), "gcn_decomp_result_device")
         return o.value, oo.value, st.value, nb.value
+
+    def run_stats(self) -> dict[str, int]:
+        """Sizes of the last run (lines, kernels, instructions, labels, blocks, state words, output bytes)."""
+        v = (ctypes.c_uint64 * 8)()
+        n = lib().gcn_decomp_run_stats(self._h, v, 8)
+        keys = ["lines", "kernels", "instrs", "labels", "pblocks", "lblocks", "state_words", "out_bytes"]
+        return {keys[i]: int(v[i]) for i in range(max(n, 0))}
+
+    def launches(self) -> int:
+        """CUDA kernels launched by the last pipeline run."""
+        return int(lib().gcn_decomp_launches(self._h))
+
+    def result_copy(self, f0: int, f1: int) -> tuple[list[str], list[int]]:
+        """Texts and statuses of files [f0, f1) of the last device-resident run."""
+        n = f1 - f0
+        offs = (ctypes.c_uint64 * (n + 1))()
+        st = (ctypes.c_int32 * max(n, 1))()
+        _ck(lib().gcn_decomp_result_copy(self._h, f0, f1, None, 0, offs, st), "gcn_decomp_result_copy")
+        buf = ctypes.create_string_buffer(max(int(offs[n]), 1))
+        _ck(lib().gcn_decomp_result_copy(self._h, f0, f1, buf, int(offs[n]), offs, st), "gcn_decomp_result_copy")
+        raw = buf.raw
+        return [raw[offs[i]:offs[i + 1]].decode() for i in range(n)], [int(st[i]) for i in range(n)]
 
     def stage_times(self) -> dict[str, float]:
         ms = (ctypes.c_float * 16)()

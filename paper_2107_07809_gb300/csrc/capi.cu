@@ -111,6 +111,7 @@ struct gcn_decomp {
   std::map<uint64_t, JobRec> jobs;
   cudaEvent_t ev[kStages + 1];
   float stage_ms[kStages] = {0};
+  uint64_t launches = 0;
   uint32_t* h_tot = nullptr;  // pinned counters
 };
 
@@ -122,6 +123,7 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   Workspace& W = h->ws;
   Run& R = h->run;
   R.valid = false;
+  const uint64_t launches0 = launch_counter();
   Batch& b = R.b;
   b = Batch{};
   b.text = text;
@@ -296,6 +298,7 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   CK(cudaEventRecord(h->ev[10], s));
   R.out_bytes = total;
   R.valid = true;
+  h->launches = launch_counter() - launches0;
 }
 
 void finish_run(gcn_decomp* h, cudaStream_t s) {
@@ -404,6 +407,36 @@ int gcn_decomp_result_device(gcn_decomp_t* h, const uint8_t** d_out, const uint6
   if (d_out_off) *d_out_off = h->run.b.file_out_off;
   if (d_status) *d_status = h->run.b.file_status;
   if (out_bytes) *out_bytes = h->run.out_bytes;
+  return GCN_OK;
+}
+
+int gcn_decomp_result_copy(gcn_decomp_t* h, uint64_t f0, uint64_t f1, void* buf, size_t cap, uint64_t* off_out,
+                           int32_t* status_out) {
+  if (!h || !h->run.valid || f0 > f1 || f1 > h->run.b.F) {
+    set_err("no run or bad file range");
+    return GCN_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  try {
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    const Batch& b = h->run.b;
+    std::vector<uint64_t> o(f1 - f0 + 1);
+    CK(cudaMemcpy(o.data(), b.file_out_off + f0, 8 * o.size(), cudaMemcpyDeviceToHost));
+    uint64_t bytes = o.back() - o.front();
+    if (off_out)
+      for (size_t i = 0; i < o.size(); ++i) off_out[i] = o[i] - o[0];
+    if (status_out && f1 > f0) CK(cudaMemcpy(status_out, b.file_status + f0, 4 * (f1 - f0), cudaMemcpyDeviceToHost));
+    if (buf) {
+      if (cap < bytes) {
+        set_err("buffer too small");
+        return GCN_EINVAL;
+      }
+      if (bytes) CK(cudaMemcpy(buf, b.out + o[0], bytes, cudaMemcpyDeviceToHost));
+    }
+  } catch (int rc) {
+    return rc;
+  }
   return GCN_OK;
 }
 
@@ -543,6 +576,17 @@ int gcn_decomp_fetch_ir(gcn_decomp_t* h, uint64_t job_id, int which, void* buf, 
   if (cap < v.size()) return GCN_EINVAL;
   memcpy(buf, v.data(), v.size());
   return GCN_OK;
+}
+
+uint64_t gcn_decomp_launches(gcn_decomp_t* h) { return h ? h->launches : 0; }
+
+int gcn_decomp_run_stats(gcn_decomp_t* h, uint64_t* out, int cap) {
+  if (!h || !out || cap < 0) return GCN_EINVAL;
+  const Batch& b = h->run.b;
+  uint64_t v[8] = {b.L, b.K, b.I, b.NL, b.NPB, b.NLB, b.NS, h->run.out_bytes};
+  int n = cap < 8 ? cap : 8;
+  for (int i = 0; i < n; ++i) out[i] = v[i];
+  return n;
 }
 
 int gcn_decomp_stage_times(gcn_decomp_t* h, float* ms, const char** names, int cap) {

@@ -4,6 +4,12 @@
 
 namespace gd {
 
+// kernels launched by this process (host-side count; one instance across units)
+inline uint64_t& launch_counter() {
+  static uint64_t c = 0;
+  return c;
+}
+
 // line kinds and row types
 enum : uint8_t { LK_BLANK = 0, LK_KERNEL = 1, LK_CONFIG = 2, LK_TEXT = 3, LK_LABEL = 4, LK_ROW = 5 };
 enum : uint8_t { RT_NONE = 0, RT_CFG = 1, RT_LABEL = 2, RT_INSTR = 3, RT_KERNEL = 4 };

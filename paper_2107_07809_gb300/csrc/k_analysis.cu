@@ -260,16 +260,21 @@ __global__ void k_wl_off(Batch b, const uint32_t* __restrict__ off) {
 void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint32_t* total, cudaStream_t s) {
   if (!b.K) return;
   k_wl_size<<<(b.K + 127) / 128, 128, 0, s>>>(b, sz);
+  ++launch_counter();
   launch_scan(sz, off, b.K, 0, false, sc, total, b.err, s);
   k_wl_off<<<(b.K + 127) / 128, 128, 0, s>>>(b, off);
+  ++launch_counter();
 }
 
 void launch_analysis(Batch& b, uint32_t* wl, cudaStream_t s) {
   if (!b.K) return;
   const int T = 64;
   k_reach<<<(b.K + T - 1) / T, T, 0, s>>>(b, wl);
+  ++launch_counter();
   k_types<<<(b.K + T - 1) / T, T, 0, s>>>(b);
+  ++launch_counter();
   k_vars<<<(b.K + T - 1) / T, T, 0, s>>>(b);
+  ++launch_counter();
 }
 
 }  // namespace gd

@@ -603,13 +603,19 @@ void launch_df_counts(Batch& b, DfScratch& d, ScanScratch sc, uint32_t* totals, 
   const int T = 256;
   if (!b.K) return;
   k_df_sizes<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kstate);
+  ++launch_counter();
   k_bits_size<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kbits);
+  ++launch_counter();
   launch_scan(d.kstate, d.kstate_off, b.K, 0, false, sc, &totals[5], b.err, s);  // totals[5] = state words
   launch_scan(d.kbits, d.bits_off, b.K, 0, false, sc, &totals[6], b.err, s);     // totals[6] = bitset words
-  if (b.I) k_fusion<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  if (b.I) {
+    k_fusion<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+    ++launch_counter();
+  }
   if (b.NLB) {
     cudaMemsetAsync(d.pcount, 0, sizeof(uint32_t) * (b.NLB + 1), s);
     k_pred_count<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, d.pcount, d.blk_kern);
+    ++launch_counter();
     launch_scan(d.pcount, b.pred_off, b.NLB + 1, 0, false, sc, &totals[7], b.err, s);  // totals[7] = edges
   }
 }
@@ -618,20 +624,31 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
   const int T = 256;
   if (!b.K) return;
   k_state_off<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kstate_off);
+  ++launch_counter();
   if (b.NLB) {
     cudaMemsetAsync(b.pred_fill, 0, sizeof(uint32_t) * b.NLB, s);
     k_pred_fill<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, d.blk_kern);
+    ++launch_counter();
     k_pred_sort<<<(b.NLB + T - 1) / T, T, 0, s>>>(b);
+    ++launch_counter();
     k_dominators<<<(b.K + 63) / 64, 64, 0, s>>>(b, d.rpo_index, d.stack, d.child);
+    ++launch_counter();
   }
   if (b.NS) cudaMemsetAsync(b.st_out, 0xFF, sizeof(uint32_t) * b.NS, s);
   if (d.NW) {
     cudaMemsetAsync(d.defbits, 0, sizeof(uint32_t) * d.NW, s);
     cudaMemsetAsync(d.phibits, 0, sizeof(uint32_t) * d.NW, s);
   }
-  if (b.I) k_local_defs<<<(b.I + T - 1) / T, T, 0, s>>>(b, d.defbits, d.bits_off);
+  if (b.I) {
+    k_local_defs<<<(b.I + T - 1) / T, T, 0, s>>>(b, d.defbits, d.bits_off);
+    ++launch_counter();
+  }
   k_versions<<<(b.K + 3) / 4, 128, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
-  if (b.I) k_nodes<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  ++launch_counter();
+  if (b.I) {
+    k_nodes<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+    ++launch_counter();
+  }
 }
 
 }  // namespace gd

@@ -266,6 +266,7 @@ __global__ void k_config(Batch b) {
 void launch_config(Batch& b, cudaStream_t s) {
   if (!b.K) return;
   k_config<<<(b.K + 127) / 128, 128, 0, s>>>(b);
+  ++launch_counter();
 }
 
 // ---------------------------------------------------------------------------
@@ -531,10 +532,16 @@ void launch_decode(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
   const int T = 256;
   if (!b.I) return;
   k_decode<<<(b.I + T - 1) / T, T, 0, s>>>(b);
-  if (b.NL) k_label_hash<<<(b.NL + T - 1) / T, T, 0, s>>>(b);
+  ++launch_counter();
+  if (b.NL) {
+    k_label_hash<<<(b.NL + T - 1) / T, T, 0, s>>>(b);
+    ++launch_counter();
+  }
   k_resolve<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  ++launch_counter();
   cudaMemsetAsync(b.pleader, 0, sizeof(uint32_t) * b.I, s);
   k_pleaders<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  ++launch_counter();
   launch_scan(b.pleader, b.lleader, b.I, 0, true, sc, &totals[3], b.err, s);  // totals[3] = physical blocks
 }
 
@@ -542,7 +549,11 @@ void launch_pblocks(Batch& b, uint32_t* blk_kern, cudaStream_t s) {
   const int T = 256;
   if (!b.I) return;
   k_pblocks<<<(b.I + T - 1) / T, T, 0, s>>>(b, b.lleader, blk_kern);
-  if (b.NPB) k_pblock_edges<<<(b.NPB + T - 1) / T, T, 0, s>>>(b, blk_kern);
+  ++launch_counter();
+  if (b.NPB) {
+    k_pblock_edges<<<(b.NPB + T - 1) / T, T, 0, s>>>(b, blk_kern);
+    ++launch_counter();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -731,8 +742,10 @@ void launch_logical(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) 
   const int T = 256;
   if (!b.I) return;
   k_exec_forms<<<(b.K + 127) / 128, 128, 0, s>>>(b);
+  ++launch_counter();
   cudaMemsetAsync(b.pleader, 0, sizeof(uint32_t) * b.I, s);
   k_lleaders<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  ++launch_counter();
   launch_scan(b.pleader, b.lleader, b.I, 0, true, sc, &totals[4], b.err, s);  // totals[4] = logical blocks
 }
 
@@ -740,7 +753,11 @@ void launch_lblocks(Batch& b, uint32_t* blk_kern, cudaStream_t s) {
   const int T = 256;
   if (!b.I) return;
   k_lblocks<<<(b.I + T - 1) / T, T, 0, s>>>(b, b.lleader, blk_kern);
-  if (b.NLB) k_lblock_edges<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, blk_kern);
+  ++launch_counter();
+  if (b.NLB) {
+    k_lblock_edges<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, blk_kern);
+    ++launch_counter();
+  }
 }
 
 }  // namespace gd

@@ -822,14 +822,19 @@ __global__ void k_file_out(Batch b, uint32_t total) {
 void launch_emit_size(Batch& b, uint32_t* scratch, uint32_t* stk, cudaStream_t s) {
   if (!b.K) return;
   k_emit<<<(b.K + 63) / 64, 64, 0, s>>>(b, scratch, stk, 0);
+  ++launch_counter();
 }
 void launch_emit_scan(Batch& b, ScanScratch sc, uint32_t* total, cudaStream_t s) {
   if (!b.K) return;
   launch_scan(b.kout_len, b.kout_off, b.K, 0, false, sc, total, b.err, s);
 }
 void launch_emit_write(Batch& b, uint32_t* scratch, uint32_t* stk, uint32_t total, cudaStream_t s) {
-  if (b.K) k_emit<<<(b.K + 63) / 64, 64, 0, s>>>(b, scratch, stk, 1);
+  if (b.K) {
+    k_emit<<<(b.K + 63) / 64, 64, 0, s>>>(b, scratch, stk, 1);
+    ++launch_counter();
+  }
   k_file_out<<<(b.F + 1 + 127) / 128, 128, 0, s>>>(b, total);
+  ++launch_counter();
 }
 
 }  // namespace gd

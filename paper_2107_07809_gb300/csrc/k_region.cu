@@ -279,6 +279,7 @@ __global__ void k_regions(Batch b, uint32_t* __restrict__ seen_all, uint32_t* __
 void launch_regions(Batch& b, uint32_t* seen, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s) {
   if (!b.K) return;
   k_regions<<<(b.K + 63) / 64, 64, 0, s>>>(b, seen, stk, alive, cond);
+  ++launch_counter();
 }
 
 }  // namespace gd

@@ -109,6 +109,7 @@ void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uin
   cudaMemsetAsync(tile_status, 0, sizeof(uint64_t) * tiles, s);
   cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), s);
   k_line_scan<<<tiles, LS_THREADS, 0, s>>>(text, n, line_start, tile_status, counters, err);
+  ++launch_counter();
 }
 uint32_t line_scan_tiles(uint64_t n) { return (uint32_t)((n + LS_TILE - 1) / LS_TILE) + 1; }
 
@@ -178,10 +179,22 @@ void launch_scan(const uint32_t* in, uint32_t* out, uint32_t n, int op, bool inc
   if (!tiles) tiles = 1;
   cudaMemsetAsync(sc.status, 0, sizeof(uint64_t) * tiles, s);
   cudaMemsetAsync(sc.counter, 0, sizeof(uint32_t), s);
-  if (op == 0 && inclusive) k_scan<ScanSum, true><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
-  if (op == 0 && !inclusive) k_scan<ScanSum, false><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
-  if (op == 1 && inclusive) k_scan<ScanMax, true><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
-  if (op == 1 && !inclusive) k_scan<ScanMax, false><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+  if (op == 0 && inclusive) {
+    k_scan<ScanSum, true><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+    ++launch_counter();
+  }
+  if (op == 0 && !inclusive) {
+    k_scan<ScanSum, false><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+    ++launch_counter();
+  }
+  if (op == 1 && inclusive) {
+    k_scan<ScanMax, true><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+    ++launch_counter();
+  }
+  if (op == 1 && !inclusive) {
+    k_scan<ScanMax, false><<<tiles, SC_THREADS, 0, s>>>(in, out, n, sc.status, sc.counter, total_out, err);
+    ++launch_counter();
+  }
 }
 uint32_t scan_tiles(uint32_t n) { return (n + SC_TILE - 1) / SC_TILE + 1; }
 
@@ -275,12 +288,17 @@ void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, co
                  RowArrays& ra, ScanScratch sc, uint32_t* totals, uint32_t* err, cudaStream_t s) {
   const int T = 256;
   cudaMemsetAsync(ra.file_start, 0, L, s);
-  if (F) k_file_starts<<<(F + T - 1) / T, T, 0, s>>>(line_start, L, file_off, F, ra.file_start);
+  if (F) {
+    k_file_starts<<<(F + T - 1) / T, T, 0, s>>>(line_start, L, file_off, F, ra.file_start);
+    ++launch_counter();
+  }
   k_classify<<<(L + T - 1) / T, T, 0, s>>>(text, line_start, L, ra.file_start, ra.kind, ra.t0, ra.t1, ra.t2);
+  ++launch_counter();
   launch_scan(ra.t0, ra.mkmax, L, 1, true, sc, nullptr, err, s);
   launch_scan(ra.t1, ra.fsmax, L, 1, true, sc, nullptr, err, s);
   launch_scan(ra.t2, ra.kcnt, L, 0, true, sc, &totals[0], err, s);  // totals[0] = kernels
   k_assign<<<(L + T - 1) / T, T, 0, s>>>(ra.kind, ra.mkmax, ra.fsmax, ra.kcnt, L, ra.rowtype, ra.t0, ra.t1);
+  ++launch_counter();
   launch_scan(ra.t0, ra.instr_excl, L, 0, false, sc, &totals[1], err, s);  // totals[1] = instructions
   launch_scan(ra.t1, ra.label_excl, L, 0, false, sc, &totals[2], err, s);  // totals[2] = labels
 }
