@@ -142,7 +142,7 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   CK(cudaEventRecord(h->ev[0], s));
   // S1
   uint32_t* line_start = W.get<uint32_t>("line_start", n + 2);
-  uint64_t* tstat = W.get<uint64_t>("tile_status", std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)));
+  uint64_t* tstat = W.get<uint64_t>("tile_status", std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)) + 64);
   uint32_t* counters = W.get<uint32_t>("counters", 4);
   launch_line_scan(text, n, line_start, tstat, counters, err, s);
   CK(cudaGetLastError());
@@ -257,6 +257,12 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[7], s));
   // S9 - S11
+  b.ncls = W.get<uint8_t>("ncls", 4ull * b.I + 4);
+  b.nclsk = W.get<uint8_t>("nclsk", 4ull * b.I + 4);
+  b.nsrcf = W.get<uint32_t>("nsrcf", 12ull * b.I + 12);
+  b.mem_arg = W.get<uint32_t>("mem_arg", b.I + 1);
+  b.mem_idx = W.get<uint32_t>("mem_idx", b.I + 1);
+  launch_node_cache(b, s);
   b.uses = W.get<uint32_t>("uses", 4ull * b.I + 4);
   b.nflag = W.get<uint8_t>("nflag", 4ull * b.I + 4);
   b.ntype = W.get<uint8_t>("ntype", 4ull * b.I + 4);
@@ -282,18 +288,29 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   launch_regions(b, seen, rstk, alive, cond, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[9], s));
-  // S13
-  b.kout_len = W.get<uint32_t>("kout_len", b.K + 1);
+  // S13: layout (count, scan, write), item sizes, scan, item text
   b.kout_off = W.get<uint32_t>("kout_off", b.K + 1);
-  launch_emit_size(b, wl, rstk, s);
-  launch_emit_scan(b, sc, &tot[10], s);
+  uint32_t* icnt = W.get<uint32_t>("item_cnt", b.K + 1);
+  uint32_t* ibase = W.get<uint32_t>("item_base", b.K + 1);
+  launch_layout(b, nullptr, nullptr, icnt, wl, rstk, 0, s);
+  if (b.K) launch_scan(icnt, ibase, b.K, 0, false, sc, &tot[10], b.err, s);
   CK(cudaGetLastError());
   sync_totals();
-  uint32_t total = b.K ? h->h_tot[10] : 0;
+  uint32_t NI = b.K ? h->h_tot[10] : 0;
+  Item* items = W.get<Item>("items", (size_t)NI + 1);
+  uint32_t* ilen = W.get<uint32_t>("item_len", (size_t)NI + 1);
+  uint32_t* ioff = W.get<uint32_t>("item_off", (size_t)NI + 1);
+  launch_layout(b, items, ibase, icnt, wl, rstk, 1, s);
+  launch_items(b, items, NI, ilen, ioff, 0, s);
+  if (NI) launch_scan(ilen, ioff, NI, 0, false, sc, &tot[11], b.err, s);
+  CK(cudaGetLastError());
+  sync_totals();
+  uint32_t total = NI ? h->h_tot[11] : 0;
   b.out = W.get<uint8_t>("out", (size_t)total + 16);
   b.file_out_off = W.get<uint64_t>("file_out_off", b.F + 2);
   b.file_status = W.get<int32_t>("file_status", b.F + 1);
-  launch_emit_write(b, wl, rstk, total, s);
+  launch_items(b, items, NI, ilen, ioff, 1, s);
+  launch_finish(b, ibase, ioff, total, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[10], s));
   R.out_bytes = total;

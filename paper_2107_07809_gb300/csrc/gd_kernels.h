@@ -79,8 +79,9 @@ struct Batch {
   uint8_t* has_phi;              // NS
   Node* nodes;                   // 4 * I
   // analysis
-  uint8_t* ncls;                 // 4 * I
+  uint8_t* ncls;                 // 4 * I: class of each node (null until cached)
   uint8_t* nclsk;                // 4 * I
+  uint32_t* nsrcf;               // 12 * I: forwarded sources of each node
   uint32_t* mem_arg;             // I: matched argument (kNone = raw address)
   uint32_t* mem_idx;             // I: index value reference (kTop = constant 0)
   uint32_t* uses;                // 4 * I
@@ -138,14 +139,22 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s);
 
 // k_analysis.cu
 void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint32_t* total, cudaStream_t s);
+void launch_node_cache(Batch& b, cudaStream_t s);
 void launch_analysis(Batch& b, uint32_t* wl, cudaStream_t s);
 
 // k_region.cu
 void launch_regions(Batch& b, uint32_t* seen, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s);
 
 // k_emit.cu
-void launch_emit_size(Batch& b, uint32_t* scratch, uint32_t* stk, cudaStream_t s);
-void launch_emit_scan(Batch& b, ScanScratch sc, uint32_t* total, cudaStream_t s);
-void launch_emit_write(Batch& b, uint32_t* scratch, uint32_t* stk, uint32_t total, cudaStream_t s);
+struct Item {
+  uint32_t kl;  // kind | level << 8
+  uint32_t k;   // kernel
+  uint32_t a, b;
+};
+void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* item_cnt, uint32_t* scratch,
+                   uint32_t* stk, int write, cudaStream_t s);
+void launch_items(Batch& b, const Item* items, uint32_t NI, uint32_t* item_len, const uint32_t* item_off, int write,
+                  cudaStream_t s);
+void launch_finish(Batch& b, const uint32_t* item_base, const uint32_t* item_off, uint32_t total, cudaStream_t s);
 
 }  // namespace gd

@@ -24,7 +24,7 @@ __global__ void k_reach(Batch b, uint32_t* __restrict__ wl_all) {
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) return;
-  KView v{&b, &K, b.nodes + 4 * (size_t)K.first_instr, b.args + (size_t)k * kMaxArgs, k};
+  KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint32_t* uses = b.uses + nb;
   uint8_t* fl = b.nflag + nb;
@@ -67,7 +67,7 @@ __global__ void k_reach(Batch b, uint32_t* __restrict__ wl_all) {
       const Node& n = v.node(4 * i);
       if (n.kind != N_OP) continue;
       if (b.ctl[gi] == C_CBR) {
-        if (B.succ1 != kNone) use(fwd(v, n.src[0]), bl);
+        if (B.succ1 != kNone) use(nsrc(v, n, 0), bl);
         continue;
       }
       if (op_store(n.op) || op_gload(n.op) || n.op == O_UNKNOWN) {
@@ -123,7 +123,7 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
     case K_ARG32: case K_ARG64: return v.A[c.k].elem;
     case K_CONST32: case K_CONST64: case K_UNDEF: return TY_NONE;
   }
-  auto st = [&](int q) { return ref_type(v, nt, pt, fwd(v, n.src[q])); };
+  auto st = [&](int q) { return ref_type(v, nt, pt, nsrc(v, n, q)); };
   if (n.kind == N_PAIR || n.kind == N_SLOAD64B) return TY_ULONG;
   if (n.kind == N_CARRY) return TY_UINT;
   if (n.kind != N_OP) return TY_NONE;
@@ -143,10 +143,9 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
     case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused ? tjoin(st(0), st(1)) : TY_UINT;
     case O_V_LSHLREV_B64: return st(1);
     case O_GLOBAL_LOAD_DWORD: case O_GLOBAL_LOAD_DWORDX2: {
-      uint32_t w = n.op == O_GLOBAL_LOAD_DWORDX2 ? 8 : 4;
-      Mem m = match_addr(v, fwd(v, n.src[0]), w);
+      Mem m = mem_of(v, id);
       if (m.ok) return v.A[m.arg].elem;
-      return w == 8 ? TY_ULONG : TY_UINT;
+      return n.op == O_GLOBAL_LOAD_DWORDX2 ? TY_ULONG : TY_UINT;
     }
     case O_S_LOAD_DWORD: return TY_UINT;
     case O_S_LOAD_DWORDX2: case O_S_LOAD_DWORDX4: return TY_ULONG;
@@ -161,7 +160,7 @@ __global__ void k_types(Batch b) {
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) return;
-  KView v{&b, &K, b.nodes + 4 * (size_t)K.first_instr, b.args + (size_t)k * kMaxArgs, k};
+  KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint8_t* nt = b.ntype + nb;
   const uint8_t* fl = b.nflag + nb;
@@ -208,7 +207,7 @@ __global__ void k_vars(Batch b) {
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) return;
-  KView v{&b, &K, b.nodes + 4 * (size_t)K.first_instr, b.args + (size_t)k * kMaxArgs, k};
+  KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   int32_t* vo = b.var_of + nb;
   const uint32_t* uses = b.uses + nb;
@@ -249,7 +248,7 @@ __global__ void k_wl_size(Batch b, uint32_t* __restrict__ sz) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   const KHdr& K = b.kh[k];
-  sz[k] = K.bad ? 0u : 4 * K.n_instr + K.n_lblock * K.R + 8;
+  sz[k] = K.bad ? 0u : 4 * K.n_instr + K.n_lblock * K.R + 3 * K.R + 8;
 }
 __global__ void k_wl_off(Batch b, const uint32_t* __restrict__ off) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -263,6 +262,47 @@ void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint3
   ++launch_counter();
   launch_scan(sz, off, b.K, 0, false, sc, total, b.err, s);
   k_wl_off<<<(b.K + 127) / 128, 128, 0, s>>>(b, off);
+  ++launch_counter();
+}
+
+// one thread per node: its class, its forwarded sources and, for a load or
+// store, its memory match; later stages read these instead of recomputing
+__global__ void k_node_cache(Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck, uint32_t* __restrict__ sf,
+                             uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
+  uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 4ull * b.I) return;
+  uint32_t gi = (uint32_t)(g / 4);
+  uint32_t k = b.ikern[gi];
+  const KHdr& K = b.kh[k];
+  KView v = make_view(b, K, k);  // b carries no caches here
+  uint32_t id = (uint32_t)(g - 4ull * K.first_instr);
+  const Node& n = v.node(id);
+  Cls c{K_NONE, 0};
+  if (!K.bad && n.kind != N_NONE) c = classify(v, mkref(id, PART_ENTIRE));
+  cc[g] = c.c;
+  ck[g] = c.k;
+  for (int q = 0; q < 3; ++q) sf[3 * g + q] = (!K.bad && q < n.nsrc) ? fwd(v, n.src[q]) : kTop;
+  if ((g & 3) == 0) {
+    uint32_t a = kNone, x = kTop;
+    if (!K.bad && n.kind == N_OP && (op_gload(n.op) || op_store(n.op))) {
+      uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
+      Mem m = match_addr(v, fwd(v, n.src[0]), w);
+      if (m.ok) {
+        a = m.arg;
+        x = m.idx;
+      }
+    }
+    marg[gi] = a;
+    midx[gi] = x;
+  }
+}
+
+void launch_node_cache(Batch& b, cudaStream_t s) {
+  if (!b.I) return;
+  Batch raw = b;
+  raw.ncls = nullptr;
+  uint64_t n = 4ull * b.I;
+  k_node_cache<<<(uint32_t)((n + 255) / 256), 256, 0, s>>>(raw, b.ncls, b.nclsk, b.nsrcf, b.mem_arg, b.mem_idx);
   ++launch_counter();
 }
 

@@ -13,8 +13,29 @@ struct KView {
   const Node* N;      // b.nodes + 4 * first_instr
   const ArgRec* A;    // b.args + k * kMaxArgs
   uint32_t k;
+  // caches filled by k_node_cache (null while it runs): class of each node,
+  // forwarded sources of each node, memory match of each load/store
+  const uint8_t* cc;
+  const uint8_t* ck;
+  const uint32_t* sf;
+  const uint32_t* marg;
+  const uint32_t* midx;
   __device__ const Node& node(uint32_t id) const { return N[id]; }
 };
+
+// a kernel view with the caches of the batch
+__device__ __forceinline__ KView make_view(const Batch& b, const KHdr& K, uint32_t k) {
+  const size_t nb = 4 * (size_t)K.first_instr;
+  KView v{&b, &K, b.nodes + nb, b.args + (size_t)k * kMaxArgs, k, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (b.ncls) {
+    v.cc = b.ncls + nb;
+    v.ck = b.nclsk + nb;
+    v.sf = b.nsrcf + 3 * nb;
+    v.marg = b.mem_arg + K.first_instr;
+    v.midx = b.mem_idx + K.first_instr;
+  }
+  return v;
+}
 
 __device__ __forceinline__ bool is_copy_node(const Node& n) {
   return n.kind == N_OP && (n.op == O_V_MOV_B32 || n.op == O_S_MOV_B32 || n.op == O_BUFFER_STORE_DWORD ||
@@ -45,6 +66,10 @@ static __device__ uint32_t fwd_d(const KView& v, uint32_t r, int depth) {
   return r;
 }
 __device__ __forceinline__ uint32_t fwd(const KView& v, uint32_t r) { return fwd_d(v, r, 0); }
+// forwarded source q of node n (n must live in v.N)
+__device__ __forceinline__ uint32_t nsrc(const KView& v, const Node& n, int q) {
+  return v.sf ? v.sf[3 * (size_t)(&n - v.N) + q] : fwd_d(v, n.src[q], 0);
+}
 
 // classes of values
 enum : uint8_t { K_NONE = 0, K_LID, K_GRP, K_KARG, K_UNDEF, K_GOFS64, K_GOFSLO, K_MULGRP, K_GIDNO, K_GID, K_ARGPTR,
@@ -62,7 +87,7 @@ static __device__ Cls classify(const KView& v, uint32_t r);
 
 static __device__ Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide) {
   Cls none{K_NONE, 0};
-  Cls base = classify(v, fwd(v, n.src[0]));
+  Cls base = classify(v, nsrc(v, n, 0));
   if (base.c != K_KARG || (n.cval & 7u)) return none;
   uint32_t slot = n.cval / 8;
   if (slot >= v.K->nargs) return none;
@@ -82,16 +107,20 @@ static __device__ Cls settings_load(const KView& v, const Node& n, uint32_t part
   return Cls{K_ARG32, (uint8_t)slot};
 }
 
-__device__ __forceinline__ int64_t const_of(const KView& v, uint32_t r) {
-  uint32_t s = fwd(v, r);
+__device__ __forceinline__ int64_t const_of_f(const KView& v, uint32_t s) {
   if (!r_node(s) || rpart(s) != PART_ENTIRE) return -1;
   const Node& n = v.node(rid(s));
   return n.kind == N_CONST ? (int64_t)n.cval : -1;
+}
+// constant value of forwarded source q of node n, -1 if not a constant
+__device__ __forceinline__ int64_t const_src(const KView& v, const Node& n, int q) {
+  return const_of_f(v, nsrc(v, n, q));
 }
 
 static __device__ Cls classify(const KView& v, uint32_t r) {
   Cls none{K_NONE, 0};
   if (r == kUndef || r == kTop) return Cls{K_UNDEF, 0};
+  if (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) return Cls{v.cc[rid(r)], v.ck[rid(r)]};
   if (r_leaf(r)) {
     uint32_t id = rid(r) & 0x0FFFFFFFu;
     uint32_t kind = id >> 8, k = id & 0xFF;
@@ -106,7 +135,7 @@ static __device__ Cls classify(const KView& v, uint32_t r) {
   uint32_t part = rpart(r);
   if (n.kind == N_CONST) return Cls{K_CONST32, 0};
   if (n.kind == N_PAIR && part == PART_ENTIRE) {
-    Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1]));
+    Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1));
     return (a.c == K_CONST32 && b.c == K_CONST32) ? Cls{K_CONST64, 0} : none;
   }
   if (n.kind == N_SLOAD64B) return settings_load(v, n, part, true);
@@ -118,21 +147,21 @@ static __device__ Cls classify(const KView& v, uint32_t r) {
   auto cw = [&](int d) -> int64_t { return d < 3 ? (int64_t)cws[d] : -1; };
   switch (n.op) {
     case O_S_MUL_I32: {
-      Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1]));
-      if (a.c == K_GRP && const_of(v, n.src[1]) == cw(a.k)) return Cls{K_MULGRP, a.k};
-      if (b.c == K_GRP && const_of(v, n.src[0]) == cw(b.k)) return Cls{K_MULGRP, b.k};
+      Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1));
+      if (a.c == K_GRP && const_src(v, n, 1) == cw(a.k)) return Cls{K_MULGRP, a.k};
+      if (b.c == K_GRP && const_src(v, n, 0) == cw(b.k)) return Cls{K_MULGRP, b.k};
       return none;
     }
     case O_S_LSHL_B32: {
-      Cls a = classify(v, fwd(v, n.src[0]));
+      Cls a = classify(v, nsrc(v, n, 0));
       if (a.c == K_GRP) {
         int l = ilog2_exact((uint32_t)cw(a.k));
-        if (l >= 0 && const_of(v, n.src[1]) == l) return Cls{K_MULGRP, a.k};
+        if (l >= 0 && const_src(v, n, 1) == l) return Cls{K_MULGRP, a.k};
       }
       return none;
     }
     case O_V_ADD_U32: {
-      Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1]));
+      Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1));
       if (a.c == K_MULGRP && b.c == K_LID && a.k == b.k) return Cls{K_GIDNO, a.k};
       if (b.c == K_MULGRP && a.c == K_LID && a.k == b.k) return Cls{K_GIDNO, a.k};
       if (a.c == K_GIDNO && b.c == K_GOFSLO && a.k == b.k) return Cls{K_GID, a.k};
@@ -140,10 +169,10 @@ static __device__ Cls classify(const KView& v, uint32_t r) {
       return none;
     }
     case O_V_MAD_U32_U24: {
-      Cls a = classify(v, fwd(v, n.src[0])), b = classify(v, fwd(v, n.src[1])), c = classify(v, fwd(v, n.src[2]));
+      Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1)), c = classify(v, nsrc(v, n, 2));
       if (c.c != K_LID) return none;
-      if (a.c == K_GRP && a.k == c.k && const_of(v, n.src[1]) == cw(a.k)) return Cls{K_GIDNO, a.k};
-      if (b.c == K_GRP && b.k == c.k && const_of(v, n.src[0]) == cw(b.k)) return Cls{K_GIDNO, b.k};
+      if (a.c == K_GRP && a.k == c.k && const_src(v, n, 1) == cw(a.k)) return Cls{K_GIDNO, a.k};
+      if (b.c == K_GRP && b.k == c.k && const_src(v, n, 0) == cw(b.k)) return Cls{K_GIDNO, b.k};
       return none;
     }
   }
@@ -170,7 +199,7 @@ static __device__ Mem match_addr(const KView& v, uint32_t addr, uint32_t width) 
   const Node& n = v.node(rid(addr));
   if (n.kind != N_OP || n.op != O_V_ADDC_CO_U32 || !n.fused) return m;
   for (int o = 0; o < 2; ++o) {
-    uint32_t X = fwd(v, n.src[o]), Y = fwd(v, n.src[1 - o]);
+    uint32_t X = nsrc(v, n, o), Y = nsrc(v, n, 1 - o);
     Cls cx = classify(v, X);
     if (cx.c != K_ARGPTR) continue;
     uint32_t es = ty64(v.A[cx.k].elem) ? 8u : 4u;
@@ -178,17 +207,17 @@ static __device__ Mem match_addr(const KView& v, uint32_t addr, uint32_t width) 
     if (!r_node(Y) || rpart(Y) != PART_ENTIRE) continue;
     const Node& sh = v.node(rid(Y));
     if (sh.kind != N_OP || sh.op != O_V_LSHLREV_B64) continue;
-    if (const_of(v, sh.src[0]) != ilog2_exact(es)) continue;
-    uint32_t V = fwd(v, sh.src[1]);
+    if (const_src(v, sh, 0) != ilog2_exact(es)) continue;
+    uint32_t V = nsrc(v, sh, 1);
     if (!r_node(V) || rpart(V) != PART_ENTIRE || v.node(rid(V)).kind != N_PAIR) continue;
     const Node& p = v.node(rid(V));
-    uint32_t lo = fwd(v, p.src[0]), hi = fwd(v, p.src[1]);
+    uint32_t lo = nsrc(v, p, 0), hi = nsrc(v, p, 1);
     bool ext = false;
     if (r_node(hi) && rpart(hi) == PART_ENTIRE && v.node(rid(hi)).kind == N_CONST && v.node(rid(hi)).cval == 0)
       ext = true;
     if (r_node(hi) && rpart(hi) == PART_ENTIRE) {
       const Node& a = v.node(rid(hi));
-      if (a.kind == N_OP && a.op == O_V_ASHRREV_I32 && const_of(v, a.src[0]) == 31 && fwd(v, a.src[1]) == lo)
+      if (a.kind == N_OP && a.op == O_V_ASHRREV_I32 && const_src(v, a, 0) == 31 && nsrc(v, a, 1) == lo)
         ext = true;
     }
     if (!ext) continue;
@@ -233,29 +262,36 @@ __device__ __forceinline__ uint8_t tresolve(uint8_t t, int width) {
 }
 
 // children printed with a node (after forwarding); returns the count (<= 3)
+// memory match of load/store node `id` (slot 0 of its instruction)
+__device__ __forceinline__ Mem mem_of(const KView& v, uint32_t id) {
+  if (v.marg) return Mem{v.marg[id / 4] != kNone, v.marg[id / 4], v.midx[id / 4]};
+  const Node& n = v.node(id);
+  uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
+  return match_addr(v, nsrc(v, n, 0), w);
+}
+
 static __device__ int node_children(const KView& v, uint32_t id, uint32_t* ch) {
   const Node& n = v.node(id);
   if (leaf_like(classify(v, mkref(id, PART_ENTIRE)).c)) return 0;
   int c = 0;
   if (n.kind == N_PAIR) {
-    ch[c++] = fwd(v, n.src[0]);
-    ch[c++] = fwd(v, n.src[1]);
+    ch[c++] = nsrc(v, n, 0);
+    ch[c++] = nsrc(v, n, 1);
     return c;
   }
   if (n.kind != N_OP) return 0;
   if (op_gload(n.op) || op_store(n.op)) {
-    uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
-    Mem m = match_addr(v, fwd(v, n.src[0]), w);
+    Mem m = mem_of(v, id);
     if (m.ok) {
       if (m.idx != kTop) ch[c++] = m.idx;
     } else {
-      ch[c++] = fwd(v, n.src[0]);
+      ch[c++] = nsrc(v, n, 0);
     }
-    if (op_store(n.op)) ch[c++] = fwd(v, n.src[1]);
+    if (op_store(n.op)) ch[c++] = nsrc(v, n, 1);
     return c;
   }
   if (n.op == O_UNKNOWN || n.op == O_S_LOAD_DWORD || n.op == O_S_LOAD_DWORDX2 || n.op == O_S_LOAD_DWORDX4) return 0;
-  for (int q = 0; q < n.nsrc && q < 3; ++q) ch[c++] = fwd(v, n.src[q]);
+  for (int q = 0; q < n.nsrc && q < 3; ++q) ch[c++] = nsrc(v, n, q);
   return c;
 }
 

@@ -189,7 +189,7 @@ struct Em {
 
   // ---- types of expressions (computed before printing) ------------------------
   __device__ uint8_t mem_elem(const Node& n, uint32_t width) {
-    Mem m = match_addr(v, fwd(v, n.src[0]), width);
+    Mem m = mem_of(v, (uint32_t)(&n - v.N));
     if (m.ok) return v.A[m.arg].elem;
     return width == 8 ? TY_ULONG : TY_UINT;
   }
@@ -297,7 +297,7 @@ struct Em {
       }
       case K_CONST64: {
         const Node& p = v.node(rid(r));
-        uint64_t lo = v.node(rid(fwd(v, p.src[0]))).cval, hi = v.node(rid(fwd(v, p.src[1]))).cval;
+        uint64_t lo = v.node(rid(nsrc(v, p, 0))).cval, hi = v.node(rid(nsrc(v, p, 1))).cval;
         uint8_t t = want == TY_NONE ? TY_ULONG : want;
         if (twidth(t) == 32) t = TY_ULONG;
         lit64(w, lo | (hi << 32), t);
@@ -332,7 +332,7 @@ struct Em {
     node_expr(id, d + 1);
   }
 
-  __device__ void S(const Node& n, int q, uint8_t t, int d) { E(fwd(v, n.src[q]), t, d); }
+  __device__ void S(const Node& n, int q, uint8_t t, int d) { E(nsrc(v, n, q), t, d); }
   __device__ void binop(const Node& n, const char* sym, uint8_t ot, int d) {
     w.c('(');
     S(n, 0, ot, d);
@@ -342,8 +342,7 @@ struct Em {
     S(n, 1, ot, d);
     w.c(')');
   }
-  __device__ void shamt(uint32_t r, uint32_t mask, int d) {
-    uint32_t f = fwd(v, r);
+  __device__ void shamt(uint32_t f, uint32_t mask, int d) {
     if (r_node(f) && rpart(f) == PART_ENTIRE && v.node(rid(f)).kind == N_CONST) {
       w.u64(v.node(rid(f)).cval & mask);
       return;
@@ -373,12 +372,12 @@ struct Em {
     w.c(' ');
     w.s(sym);
     w.c(' ');
-    shamt(n.src[sq], mask, d);
+    shamt(nsrc(v, n, sq), mask, d);
     w.c(')');
   }
 
   __device__ void memref(const Node& n, uint32_t width, int d) {
-    Mem m = match_addr(v, fwd(v, n.src[0]), width);
+    Mem m = mem_of(v, (uint32_t)(&n - v.N));
     if (m.ok) {
       name(m.arg);
       w.c('[');
@@ -390,7 +389,7 @@ struct Em {
     w.s("*((__global ");
     w.s(width == 8 ? "ulong" : "uint");
     w.s(" *)(");
-    E(fwd(v, n.src[0]), TY_ULONG, d);
+    E(nsrc(v, n, 0), TY_ULONG, d);
     w.s("))");
   }
 
@@ -471,11 +470,10 @@ struct Em {
   }
 
   // ---- statements ---------------------------------------------------------------
-  __device__ void block_stmts(uint32_t bl, int lvl) {
-    const BlockRec& B = b->lblocks[K->first_lblock + bl];
-    for (uint32_t i = B.first; i < B.end; ++i) {
+  // statements of instruction i: its operand-slot variables, then its result
+  __device__ void instr_stmts(uint32_t i, int lvl) {
+    {
       uint32_t gi = K->first_instr + i;
-      if (b->lblock_of[gi] != bl) continue;
       const int order[4] = {1, 2, 3, 0};
       for (int q = 0; q < 4; ++q) {
         uint32_t id = 4 * i + (uint32_t)order[q];
@@ -501,7 +499,7 @@ struct Em {
           w.indent(lvl);
           memref(n, width, 0);
           w.s(" = ");
-          E(fwd(v, n.src[1]), elem, 0);
+          E(nsrc(v, n, 1), elem, 0);
           w.s(";\n");
           continue;
         }
@@ -518,6 +516,20 @@ struct Em {
         }
       }
     }
+  }
+
+  // one assignment of the join version of register reg at block s along p -> s
+  __device__ void one_copy(uint32_t s, uint32_t reg, uint32_t p, int lvl) {
+    uint32_t dst = phiref(s, reg);
+    uint32_t o = b->st_out[K->state_off + (size_t)p * K->R + reg];
+    uint32_t src = fwd(v, o == kTop ? kUndef : o);
+    int32_t x = phivar(dst);
+    w.indent(lvl);
+    w.s("var");
+    w.u64((uint64_t)x);
+    w.s(" = ");
+    E(src, vt[x], 0);
+    w.s(";\n");
   }
 
   // assignments of the join versions of block s along the edge p -> s
@@ -573,7 +585,7 @@ struct Em {
   __device__ void cond_to(uint32_t t, uint32_t dst) {
     const BlockRec& B = b->lblocks[K->first_lblock + t];
     uint32_t i = b->lterm[K->first_lblock + t];
-    uint32_t c = fwd(v, v.node(4 * i).src[0]);
+    uint32_t c = nsrc(v, v.node(4 * i), 0);
     bool sense = b->sense[K->first_instr + i] != 0;
     bool positive = (dst != B.succ0) ? sense : !sense;
     if (r_node(c) && rpart(c) == PART_ENTIRE) {
@@ -626,59 +638,120 @@ __device__ void print_args(Wr& w, const Batch& b, const KHdr& K, const ArgRec* A
   if (!any) w.s("void");
 }
 
-__global__ void k_emit(Batch b, uint32_t* __restrict__ scratch_all, uint32_t* __restrict__ stk_all, int write) {
+// ---------------------------------------------------------------------------
+// output items: a per-kernel walk lays them out in output order (count, then
+// write at scanned offsets); one thread per item sizes it and, after a scan,
+// writes it
+// ---------------------------------------------------------------------------
+enum : uint32_t { IT_NONE = 0, IT_HEAD, IT_DECLS, IT_INSTR, IT_COPY, IT_IF, IT_ELSE, IT_CLOSE, IT_DO, IT_WHILE,
+                  IT_TAIL, IT_FAIL };
+constexpr uint32_t kDeclChunk = 64;
+
+struct LayoutCtx {
+  const Batch* b;
+  KHdr* K;
+  KView v;
+  Item* items;
+  uint32_t base, n;
+  bool write;
+  uint32_t* scratch;
+  uint32_t scap;
+  __device__ void put(uint32_t kind, uint32_t lvl, uint32_t a, uint32_t bb) {
+    if (write) items[base + n] = Item{kind | (lvl << 8), v.k, a, bb};
+    ++n;
+  }
+  // the copies along p -> s, in an order where no copy overwrites a version
+  // that a later copy still reads (a cycle marks the kernel partial)
+  __device__ void copies(uint32_t p, uint32_t s, uint32_t lvl) {
+    const KHdr& Kr = *K;
+    const uint8_t* pu = b->phi_used + Kr.state_off;
+    uint32_t R = Kr.R, m = 0;
+    for (uint32_t reg = 0; reg < R; ++reg) {
+      if (!pu[(size_t)s * R + reg]) continue;
+      uint32_t dst = phiref(s, reg);
+      uint32_t o = b->st_out[Kr.state_off + (size_t)p * R + reg];
+      uint32_t src = fwd(v, o == kTop ? kUndef : o);
+      if (src == dst || src == kUndef) continue;
+      if (!write) {
+        ++m;
+        continue;
+      }
+      if (2 * (m + 1) > scap) {
+        atomicOr(b->err, ERR_CAPACITY);
+        break;
+      }
+      scratch[2 * m] = reg;
+      scratch[2 * m + 1] = src;
+      ++m;
+    }
+    if (!write) {
+      n += m;
+      return;
+    }
+    while (m) {
+      uint32_t pick = m;
+      for (uint32_t k = 0; k < m && pick == m; ++k) {
+        uint32_t dk = phiref(s, scratch[2 * k]);
+        bool read = false;
+        for (uint32_t q = 0; q < m && !read; ++q)
+          if (q != k && scratch[2 * q + 1] == dk) read = true;
+        if (!read) pick = k;
+      }
+      if (pick == m) {
+        atomicOr(&K->partial, 1u);
+        pick = 0;
+      }
+      put(IT_COPY, lvl, (s << 10) | scratch[2 * pick], p);
+      for (uint32_t q = pick; q + 1 < m; ++q) {
+        scratch[2 * q] = scratch[2 * q + 2];
+        scratch[2 * q + 1] = scratch[2 * q + 3];
+      }
+      --m;
+    }
+  }
+  __device__ uint32_t ncopies(uint32_t p, uint32_t s) {
+    const KHdr& Kr = *K;
+    const uint8_t* pu = b->phi_used + Kr.state_off;
+    uint32_t c = 0;
+    for (uint32_t reg = 0; reg < Kr.R; ++reg) {
+      if (!pu[(size_t)s * Kr.R + reg]) continue;
+      uint32_t o = b->st_out[Kr.state_off + (size_t)p * Kr.R + reg];
+      uint32_t src = fwd(v, o == kTop ? kUndef : o);
+      if (src != phiref(s, reg) && src != kUndef) ++c;
+    }
+    return c;
+  }
+};
+
+__global__ void k_layout(Batch b, Item* __restrict__ items, const uint32_t* __restrict__ item_base,
+                         uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ scratch_all,
+                         uint32_t* __restrict__ stk_all, int write) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
-  const ArgRec* A = b.args + (size_t)k * kMaxArgs;
-  Wr w{write ? b.out + b.kout_off[k] : nullptr, 0, write != 0};
-  bool last = k + 1 == b.K || b.kh[k + 1].file != K.file;
-  auto head = [&](bool args) {
-    w.s("__kernel void ");
-    w.mem(b.text + K.name_off, K.name_len);
-    w.c('(');
-    if (args) print_args(w, b, K, A);
-    w.s(")\n{\n");
-  };
-  uint32_t status;
+  LayoutCtx L;
+  L.b = &b;
+  L.K = &K;
+  L.v = make_view(b, K, k);
+  L.items = items;
+  L.base = write ? item_base[k] : 0;
+  L.n = 0;
+  L.write = write != 0;
+  L.scratch = scratch_all + K.wl_off;
+  L.scap = 4 * K.n_instr + K.n_lblock * K.R + 3 * K.R + 8;
+  if (!write) K.partial = 0;
   if (K.bad) {
-    head(false);
-    w.s("    /* not decompiled: parse error */\n}\n");
-    status = ST_PARSE_ERROR;
+    L.put(IT_FAIL, 0, 0, 0);
+    L.put(IT_TAIL, 0, 1, 0);
   } else if (K.n_lblock && K.root == kNone) {
-    head(true);
-    w.s("    /* not decompiled: unstructured control flow */\n}\n");
-    status = ST_PARTIAL;
+    L.put(IT_FAIL, 0, 1, 0);
+    L.put(IT_TAIL, 0, 1, 0);
   } else {
-    head(true);
-    const size_t nb = 4 * (size_t)K.first_instr;
-    Em em;
-    em.v = KView{&b, &K, b.nodes + nb, A, k};
-    em.b = &b;
-    em.K = &K;
-    em.uses = b.uses + nb;
-    em.fl = b.nflag + nb;
-    em.nt = b.ntype + nb;
-    em.vo = b.var_of + nb;
-    em.pv = b.phi_var + K.state_off;
-    em.vt = b.var_type + nb + K.state_off;
-    em.scratch = scratch_all + K.wl_off;
-    em.scap = 4 * K.n_instr + K.n_lblock * K.R + 8;
-    em.w = w;
-    em.partial = false;
-    em.deep = false;
-    for (uint32_t x = 0; x < K.n_vars; ++x) {
-      em.w.s("    ");
-      em.w.s(tname(em.vt[x]));
-      em.w.s(" var");
-      em.w.u64(x);
-      em.w.s(";\n");
-    }
+    L.put(IT_HEAD, 0, 0, 0);
+    for (uint32_t x = 0; x < K.n_vars; x += kDeclChunk) L.put(IT_DECLS, 1, x, min(kDeclChunk, K.n_vars - x));
     if (K.n_lblock) {
-      // region tree, explicit stack of (region, level << 8 | phase)
       const uint32_t* RG = b.rg + (size_t)kRegionsPerBlock * K.first_lblock * RGW;
       const BlockRec* BL = b.lblocks + K.first_lblock;
-      const uint8_t* cnd = nullptr;
       uint32_t* st = stk_all + kStackPerBlock * (size_t)K.first_lblock;
       uint32_t cap = kStackPerBlock * K.n_lblock, sp = 0;
       auto push = [&](uint32_t r, uint32_t lvl, uint32_t ph) {
@@ -698,10 +771,12 @@ __global__ void k_emit(Batch b, uint32_t* __restrict__ scratch_all, uint32_t* __
         switch (X[RG_KIND]) {
           case R_BLOCK: {
             uint32_t bl = X[RG_BLOCK];
-            em.block_stmts(bl, (int)lvl);
+            const BlockRec& B = BL[bl];
+            for (uint32_t i = B.first; i < B.end; ++i)
+              if (b.lblock_of[K.first_instr + i] == bl) L.put(IT_INSTR, lvl, i, 0);
             uint32_t term = b.lterm[K.first_lblock + bl];
-            bool cb = b.ctl[K.first_instr + term] == C_CBR && BL[bl].succ1 != kNone;
-            if (!cb && BL[bl].succ0 != kNone) em.copies(bl, BL[bl].succ0, (int)lvl);
+            bool cb = b.ctl[K.first_instr + term] == C_CBR && B.succ1 != kNone;
+            if (!cb && B.succ0 != kNone) L.copies(bl, B.succ0, lvl);
             break;
           }
           case R_SEQ:
@@ -713,55 +788,42 @@ __global__ void k_emit(Batch b, uint32_t* __restrict__ scratch_all, uint32_t* __
             }
             break;
           case R_IF: {
-            const uint32_t* H = RG + (size_t)X[RG_CH] * RGW;
-            uint32_t t = H[RG_TAIL];
+            uint32_t t = RG[(size_t)X[RG_CH] * RGW + RG_TAIL];
             uint32_t th = RG[(size_t)X[RG_CH + 1] * RGW + RG_HEAD];
             if (ph == 0) {
               push(r, lvl, 1);
               push(X[RG_CH], lvl, 0);
             } else if (ph == 1) {
-              em.w.indent((int)lvl);
-              em.w.s("if (");
-              em.cond_to(t, th);
-              em.w.s(") {\n");
+              L.put(IT_IF, lvl, t, th);
               push(r, lvl, 2);
               push(X[RG_CH + 1], lvl + 1, 0);
             } else {
               uint32_t other = BL[t].succ0 == th ? BL[t].succ1 : BL[t].succ0;
-              uint32_t mark = em.w.n;
-              em.w.indent((int)lvl);
-              em.w.s("} else {\n");
-              uint32_t mark2 = em.w.n;
-              em.copies(t, other, (int)lvl + 1);
-              if (em.w.n == mark2) em.w.n = mark;
-              em.w.indent((int)lvl);
-              em.w.s("}\n");
+              if (L.ncopies(t, other)) {
+                L.put(IT_ELSE, lvl, 0, 0);
+                L.copies(t, other, lvl + 1);
+              }
+              L.put(IT_CLOSE, lvl, 0, 0);
               if (X[RG_NCH] == 3) push(X[RG_CH + 2], lvl, 0);
             }
             break;
           }
           case R_IFELSE: {
-            const uint32_t* H = RG + (size_t)X[RG_CH] * RGW;
-            uint32_t t = H[RG_TAIL];
+            uint32_t t = RG[(size_t)X[RG_CH] * RGW + RG_TAIL];
             uint32_t th = RG[(size_t)X[RG_CH + 1] * RGW + RG_HEAD];
             if (ph == 0) {
               push(r, lvl, 1);
               push(X[RG_CH], lvl, 0);
             } else if (ph == 1) {
-              em.w.indent((int)lvl);
-              em.w.s("if (");
-              em.cond_to(t, th);
-              em.w.s(") {\n");
+              L.put(IT_IF, lvl, t, th);
               push(r, lvl, 2);
               push(X[RG_CH + 1], lvl + 1, 0);
             } else if (ph == 2) {
-              em.w.indent((int)lvl);
-              em.w.s("} else {\n");
+              L.put(IT_ELSE, lvl, 0, 0);
               push(r, lvl, 3);
               push(X[RG_CH + 2], lvl + 1, 0);
             } else {
-              em.w.indent((int)lvl);
-              em.w.s("}\n");
+              L.put(IT_CLOSE, lvl, 0, 0);
               if (X[RG_NCH] == 4) push(X[RG_CH + 3], lvl, 0);
             }
             break;
@@ -771,35 +833,113 @@ __global__ void k_emit(Batch b, uint32_t* __restrict__ scratch_all, uint32_t* __
             uint32_t h = RG[(size_t)X[RG_CH] * RGW + RG_HEAD];
             uint32_t t = RG[(size_t)X[RG_CH + nch - 1] * RGW + RG_TAIL];
             if (ph == 0) {
-              em.w.indent((int)lvl);
-              em.w.s("do {\n");
+              L.put(IT_DO, lvl, 0, 0);
               push(r, lvl, 1);
               for (int q = (int)nch - 1; q >= 0; --q) push(X[RG_CH + q], lvl + 1, 0);
             } else {
               uint32_t exitb = BL[t].succ0 == h ? BL[t].succ1 : BL[t].succ0;
-              em.copies(t, h, (int)lvl + 1);
-              em.w.indent((int)lvl);
-              em.w.s("} while (");
-              em.cond_to(t, h);
-              em.w.s(");\n");
-              if (exitb != kNone) em.copies(t, exitb, (int)lvl);
+              L.copies(t, h, lvl + 1);
+              L.put(IT_WHILE, lvl, t, h);
+              if (exitb != kNone) L.copies(t, exitb, lvl);
             }
             break;
           }
         }
       }
-      (void)cnd;
     }
-    em.w.s("}\n");
-    w = em.w;
-    status = em.partial ? ST_PARTIAL : ST_OK;
-    if (em.deep) atomicOr(b.err, ERR_STACK);
+    L.put(IT_TAIL, 0, 0, 0);
   }
-  if (!last) w.c('\n');
+  if (!write) item_cnt[k] = L.n;
+}
+
+__global__ void k_items(Batch b, const Item* __restrict__ items, uint32_t NI, uint32_t* __restrict__ item_len,
+                        const uint32_t* __restrict__ item_off, int write) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NI) return;
+  Item it = items[i];
+  uint32_t kind = it.kl & 0xFF, lvl = it.kl >> 8;
+  uint32_t k = it.k;
+  KHdr& K = b.kh[k];
+  const ArgRec* A = b.args + (size_t)k * kMaxArgs;
+  Em em;
+  em.v = make_view(b, K, k);
+  em.b = &b;
+  em.K = &K;
+  const size_t nb = 4 * (size_t)K.first_instr;
+  em.uses = b.uses + nb;
+  em.fl = b.nflag + nb;
+  em.nt = b.ntype + nb;
+  em.vo = b.var_of + nb;
+  em.pv = b.phi_var + K.state_off;
+  em.vt = b.var_type + nb + K.state_off;
+  em.scratch = nullptr;
+  em.scap = 0;
+  em.w = Wr{write ? b.out + item_off[i] : nullptr, 0, write != 0};
+  em.partial = false;
+  em.deep = false;
+  Wr& w = em.w;
+  switch (kind) {
+    case IT_HEAD:
+    case IT_FAIL:
+      w.s("__kernel void ");
+      w.mem(b.text + K.name_off, K.name_len);
+      w.c('(');
+      if (kind == IT_HEAD || it.a) print_args(w, b, K, A);
+      w.s(")\n{\n");
+      if (kind == IT_FAIL) {
+        w.s("    /* not decompiled: ");
+        w.s(K.bad ? "parse error" : "unstructured control flow");
+        w.s(" */\n}\n");
+      }
+      break;
+    case IT_DECLS:
+      for (uint32_t x = it.a; x < it.a + it.b; ++x) {
+        w.s("    ");
+        w.s(tname(em.vt[x]));
+        w.s(" var");
+        w.u64(x);
+        w.s(";\n");
+      }
+      break;
+    case IT_INSTR: em.instr_stmts(it.a, (int)lvl); break;
+    case IT_COPY: em.one_copy(it.a >> 10, it.a & 0x3FF, it.b, (int)lvl); break;
+    case IT_IF:
+      w.indent((int)lvl);
+      w.s("if (");
+      em.cond_to(it.a, it.b);
+      w.s(") {\n");
+      break;
+    case IT_ELSE: w.indent((int)lvl); w.s("} else {\n"); break;
+    case IT_CLOSE: w.indent((int)lvl); w.s("}\n"); break;
+    case IT_DO: w.indent((int)lvl); w.s("do {\n"); break;
+    case IT_WHILE:
+      w.indent((int)lvl);
+      w.s("} while (");
+      em.cond_to(it.a, it.b);
+      w.s(");\n");
+      break;
+    case IT_TAIL: {
+      if (!it.a) w.s("}\n");
+      bool last = k + 1 == b.K || b.kh[k + 1].file != K.file;
+      if (!last) w.c('\n');
+      break;
+    }
+  }
   if (!write) {
-    b.kout_len[k] = w.n;
-    K.status = status;
+    item_len[i] = w.n;
+    if (em.partial) atomicOr(&K.partial, 1u);
   }
+  if (em.deep) atomicOr(b.err, ERR_STACK);
+}
+
+__global__ void k_kernel_status(Batch b, const uint32_t* __restrict__ item_base, const uint32_t* __restrict__ item_off) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  if (K.bad) K.status = ST_PARSE_ERROR;
+  else if (K.n_lblock && K.root == kNone) K.status = ST_PARTIAL;
+  else K.status = K.partial ? ST_PARTIAL : ST_OK;
+  b.kout_off[k] = item_off[item_base[k]];
 }
 
 // per file: output offset and worst status of its kernels
@@ -819,18 +959,23 @@ __global__ void k_file_out(Batch b, uint32_t total) {
   b.file_status[f] = st;
 }
 
-void launch_emit_size(Batch& b, uint32_t* scratch, uint32_t* stk, cudaStream_t s) {
+void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* item_cnt, uint32_t* scratch,
+                   uint32_t* stk, int write, cudaStream_t s) {
   if (!b.K) return;
-  k_emit<<<(b.K + 63) / 64, 64, 0, s>>>(b, scratch, stk, 0);
+  k_layout<<<(b.K + 63) / 64, 64, 0, s>>>(b, items, item_base, item_cnt, scratch, stk, write);
   ++launch_counter();
 }
-void launch_emit_scan(Batch& b, ScanScratch sc, uint32_t* total, cudaStream_t s) {
-  if (!b.K) return;
-  launch_scan(b.kout_len, b.kout_off, b.K, 0, false, sc, total, b.err, s);
+
+void launch_items(Batch& b, const Item* items, uint32_t NI, uint32_t* item_len, const uint32_t* item_off, int write,
+                  cudaStream_t s) {
+  if (!NI) return;
+  k_items<<<(NI + 127) / 128, 128, 0, s>>>(b, items, NI, item_len, item_off, write);
+  ++launch_counter();
 }
-void launch_emit_write(Batch& b, uint32_t* scratch, uint32_t* stk, uint32_t total, cudaStream_t s) {
+
+void launch_finish(Batch& b, const uint32_t* item_base, const uint32_t* item_off, uint32_t total, cudaStream_t s) {
   if (b.K) {
-    k_emit<<<(b.K + 63) / 64, 64, 0, s>>>(b, scratch, stk, 1);
+    k_kernel_status<<<(b.K + 127) / 128, 128, 0, s>>>(b, item_base, item_off);
     ++launch_counter();
   }
   k_file_out<<<(b.F + 1 + 127) / 128, 128, 0, s>>>(b, total);
