@@ -252,6 +252,7 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   b.has_phi = W.get<uint8_t>("has_phi", b.NS + 1);
   d.defbits = W.get<uint32_t>("defbits", d.NW + 1);
   d.phibits = W.get<uint32_t>("phibits", d.NW + 1);
+  d.rows = W.get<uint32_t>("rows", b.NS + 1);
   b.nodes = W.get<Node>("nodes", 4ull * b.I + 4);
   launch_df_main(b, d, s);
   CK(cudaGetLastError());
@@ -268,6 +269,7 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   b.ntype = W.get<uint8_t>("ntype", 4ull * b.I + 4);
   b.var_of = W.get<int32_t>("var_of", 4ull * b.I + 4);
   b.phi_used = W.get<uint8_t>("phi_used", b.NS + 1);
+  b.plist = d.rows;  // the dataflow rows are dead once the nodes exist
   b.phi_type = W.get<uint8_t>("phi_type", b.NS + 1);
   b.phi_var = W.get<int32_t>("phi_var", b.NS + 1);
   b.var_type = W.get<uint8_t>("var_type", 4ull * b.I + b.NS + 4);
@@ -276,7 +278,9 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   launch_wl_size(b, wlsz, wloff, sc, &tot[9], s);
   sync_totals();
   uint32_t* wl = W.get<uint32_t>("wl", (size_t)h->h_tot[9] + 8);
-  launch_analysis(b, wl, s);
+  uint64_t nbw = 3 * ((4ull * b.I + 63) / 32) + (b.NS + 63) / 32 + 4;
+  uint32_t* bits = W.get<uint32_t>("reach_bits", nbw);
+  launch_analysis(b, wl, bits, nbw, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[8], s));
   // S12
@@ -292,7 +296,8 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   b.kout_off = W.get<uint32_t>("kout_off", b.K + 1);
   uint32_t* icnt = W.get<uint32_t>("item_cnt", b.K + 1);
   uint32_t* ibase = W.get<uint32_t>("item_base", b.K + 1);
-  launch_layout(b, nullptr, nullptr, icnt, wl, rstk, 0, s);
+  const uint32_t* pbits = bits + 3 * ((4ull * b.I + 63) / 32);  // used join versions (reachability)
+  launch_layout(b, nullptr, nullptr, icnt, wl, rstk, pbits, 0, s);
   if (b.K) launch_scan(icnt, ibase, b.K, 0, false, sc, &tot[10], b.err, s);
   CK(cudaGetLastError());
   sync_totals();
@@ -300,7 +305,7 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   Item* items = W.get<Item>("items", (size_t)NI + 1);
   uint32_t* ilen = W.get<uint32_t>("item_len", (size_t)NI + 1);
   uint32_t* ioff = W.get<uint32_t>("item_off", (size_t)NI + 1);
-  launch_layout(b, items, ibase, icnt, wl, rstk, 1, s);
+  launch_layout(b, items, ibase, icnt, wl, rstk, pbits, 1, s);
   launch_items(b, items, NI, ilen, ioff, 0, s);
   if (NI) launch_scan(ilen, ioff, NI, 0, false, sc, &tot[11], b.err, s);
   CK(cudaGetLastError());

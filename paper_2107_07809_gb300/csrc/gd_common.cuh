@@ -120,6 +120,7 @@ struct KHdr {
   uint32_t bad;                   // parse/config failure
   uint32_t partial;
   uint32_t n_vars;
+  uint32_t n_phis;                // used join versions (listed by the reachability walk)
   uint32_t out_len;
   uint32_t root;                  // root region (kernel-relative) or kNone
 };

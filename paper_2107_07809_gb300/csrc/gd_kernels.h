@@ -89,6 +89,7 @@ struct Batch {
   uint8_t* ntype;                // 4 * I
   int32_t* var_of;               // 4 * I
   uint8_t* phi_used;             // NS
+  uint32_t* plist;               // NS: used join versions of each kernel (block << 10 | reg)
   uint8_t* phi_type;             // NS
   int32_t* phi_var;              // NS
   uint8_t* var_type;             // per kernel: at most 4*I + NS ... (indexed by var_base + v)
@@ -132,6 +133,7 @@ struct DfScratch {
   uint32_t *rpo_index, *stack;                       // NLB
   uint8_t* child;                                    // NLB
   uint32_t *defbits, *phibits;                       // NW
+  uint32_t* rows;                                    // NS: working register rows
   uint32_t NW;
 };
 void launch_df_counts(Batch& b, DfScratch& d, ScanScratch sc, uint32_t* totals, cudaStream_t s);
@@ -140,7 +142,7 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s);
 // k_analysis.cu
 void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint32_t* total, cudaStream_t s);
 void launch_node_cache(Batch& b, cudaStream_t s);
-void launch_analysis(Batch& b, uint32_t* wl, cudaStream_t s);
+void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, cudaStream_t s);
 
 // k_region.cu
 void launch_regions(Batch& b, uint32_t* seen, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s);
@@ -152,7 +154,7 @@ struct Item {
   uint32_t a, b;
 };
 void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* item_cnt, uint32_t* scratch,
-                   uint32_t* stk, int write, cudaStream_t s);
+                   uint32_t* stk, const uint32_t* pbits, int write, cudaStream_t s);
 void launch_items(Batch& b, const Item* items, uint32_t NI, uint32_t* item_len, const uint32_t* item_off, int write,
                   cudaStream_t s);
 void launch_finish(Batch& b, const uint32_t* item_base, const uint32_t* item_off, uint32_t total, cudaStream_t s);

@@ -19,8 +19,20 @@ __device__ __forceinline__ uint32_t out_val(const Batch& b, const KHdr& K, uint3
 __device__ __forceinline__ uint32_t phi_blk(uint32_t r) { return (rid(r) >> 10) & 0x3FFFF; }
 __device__ __forceinline__ uint32_t phi_reg(uint32_t r) { return rid(r) & 0x3FF; }
 
-__global__ void k_reach(Batch b, uint32_t* __restrict__ wl_all) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+// Reachability and use counts, one warp per kernel.  Lanes pop up to 32
+// entries of the kernel's stack at a time; the first visit of a node or join
+// version is claimed with an atomic bit, use counts are atomic adds, so the
+// result does not depend on the order the lanes happen to take.
+__device__ __forceinline__ bool claim(uint32_t* bits, uint64_t g) {
+  uint32_t m = 1u << (g & 31);
+  return !(atomicOr(&bits[g >> 5], m) & m);
+}
+
+__global__ void k_reach(Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
+                        uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits) {
+  __shared__ uint32_t s_top[4], s_npl[4];
+  const uint32_t wid = threadIdx.x / 32, lane = threadIdx.x & 31u;
+  uint32_t k = blockIdx.x * (blockDim.x / 32) + wid;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) return;
@@ -30,74 +42,88 @@ __global__ void k_reach(Batch b, uint32_t* __restrict__ wl_all) {
   uint8_t* fl = b.nflag + nb;
   uint8_t* pu = b.phi_used + K.state_off;
   uint32_t* wl = wl_all + K.wl_off;
-  uint32_t cap = 4 * K.n_instr + K.n_lblock * K.R + 8, sp = 0;
-  uint32_t nn = 4 * K.n_instr;
-  for (uint32_t q = 0; q < nn; ++q) {
-    uses[q] = 0;
-    fl[q] = 0;
+  uint32_t* pl = b.plist + K.state_off;
+  const uint32_t nn = 4 * K.n_instr;
+  const uint32_t cap = nn + K.n_lblock * K.R + 8;
+  for (uint32_t q = lane; q < nn; q += 32) uses[q] = 0;
+  for (size_t q = lane; q < (size_t)K.n_lblock * K.R; q += 32) pu[q] = 0;
+  if (lane == 0) {
+    s_top[wid] = 0;
+    s_npl[wid] = 0;
   }
-  for (size_t q = 0; q < (size_t)K.n_lblock * K.R; ++q) pu[q] = 0;
-  // a reference from block `blk`: count it; queue first visits for expansion
+  __syncwarp();
+  auto push = [&](uint32_t r) {
+    uint32_t at = atomicAdd(&s_top[wid], 1u);
+    if (at < cap) wl[at] = r;
+    else atomicOr(b.err, ERR_CAPACITY);
+  };
   auto use = [&](uint32_t r, uint32_t blk) {
     if (r_phi(r)) {
-      uint32_t B = phi_blk(r), reg = phi_reg(r);
-      uint8_t& u = pu[(size_t)B * K.R + reg];
-      if (!u) {
-        u = 1;
-        if (sp < cap) wl[sp++] = r;
-        else atomicOr(b.err, ERR_CAPACITY);
+      uint32_t B = (rid(r) >> 10) & 0x3FFFF, reg = rid(r) & 0x3FF;
+      size_t slot = (size_t)B * K.R + reg;
+      if (claim(pbits, K.state_off + slot)) {
+        pu[slot] = 1;
+        pl[atomicAdd(&s_npl[wid], 1u)] = (B << 10) | reg;
+        push(r);
       }
       return;
     }
     if (!r_node(r)) return;
     uint32_t id = rid(r);
-    uses[id]++;
-    if (b.lblock_of[K.first_instr + id / 4] != blk) fl[id] |= 2;
-    if (!(fl[id] & 1)) {
-      fl[id] |= 1;
-      if (sp < cap) wl[sp++] = r & ~3u;
-      else atomicOr(b.err, ERR_CAPACITY);
-    }
+    atomicAdd(&uses[id], 1u);
+    if (b.lblock_of[K.first_instr + id / 4] != blk) claim(cbits, nb + id);
+    if (claim(rbits, nb + id)) push(r & ~3u);
   };
-  for (uint32_t bl = 0; bl < K.n_lblock; ++bl) {
-    const BlockRec& B = b.lblocks[K.first_lblock + bl];
-    for (uint32_t i = B.first; i < B.end; ++i) {
-      uint32_t gi = K.first_instr + i;
-      if (b.lblock_of[gi] != bl) continue;
-      const Node& n = v.node(4 * i);
-      if (n.kind != N_OP) continue;
-      if (b.ctl[gi] == C_CBR) {
-        if (B.succ1 != kNone) use(nsrc(v, n, 0), bl);
-        continue;
-      }
-      if (op_store(n.op) || op_gload(n.op) || n.op == O_UNKNOWN) {
-        if (!(fl[4 * i] & 1)) {
-          fl[4 * i] |= 1;
-          uint32_t ch[3];
-          int c = node_children(v, 4 * i, ch);
-          for (int q = 0; q < c; ++q) use(ch[q], bl);
-        }
-      }
-    }
-  }
-  while (sp) {
-    uint32_t r = wl[--sp];
-    if (r_phi(r)) {
-      uint32_t B = phi_blk(r), reg = phi_reg(r);
-      for (uint32_t pi = b.pred_off[K.first_lblock + B]; pi < b.pred_off[K.first_lblock + B + 1]; ++pi) {
-        uint32_t p = b.preds[pi];
-        uint32_t x = fwd(v, out_val(b, K, p, reg));
-        if (r_node(x)) fl[rid(x)] |= 4;
-        use(x, p);
-      }
+  // roots: stores, loads, unsupported instructions (expanded), branch conditions (used)
+  for (uint32_t i = lane; i < K.n_instr; i += 32) {
+    uint32_t gi = K.first_instr + i;
+    uint32_t bl = b.lblock_of[gi];
+    if (bl == kNone) continue;
+    const Node& n = v.node(4 * i);
+    if (n.kind != N_OP) continue;
+    if (b.ctl[gi] == C_CBR) {
+      if (b.lblocks[K.first_lblock + bl].succ1 != kNone) use(nsrc(v, n, 0), bl);
       continue;
     }
-    uint32_t id = rid(r);
-    uint32_t blk = b.lblock_of[K.first_instr + id / 4];
-    uint32_t ch[3];
-    int c = node_children(v, id, ch);
-    for (int q = 0; q < c; ++q) use(ch[q], blk);
+    if ((op_store(n.op) || op_gload(n.op) || n.op == O_UNKNOWN) && claim(rbits, nb + 4 * i)) push(mkref(4 * i, 0));
   }
+  __syncwarp();
+  for (;;) {
+    uint32_t top = s_top[wid];
+    if (top > cap) top = cap;
+    uint32_t take = top < 32 ? top : 32;
+    if (!take) break;
+    uint32_t r = lane < take ? wl[top - 1 - lane] : kTop;
+    __syncwarp();
+    if (lane == 0) s_top[wid] = top - take;
+    __syncwarp();
+    if (r != kTop) {
+      if (r_phi(r)) {
+        uint32_t B = (rid(r) >> 10) & 0x3FFFF, reg = rid(r) & 0x3FF;
+        for (uint32_t pi = b.pred_off[K.first_lblock + B]; pi < b.pred_off[K.first_lblock + B + 1]; ++pi) {
+          uint32_t p = b.preds[pi];
+          uint32_t x = fwd(v, out_val(b, K, p, reg));
+          if (r_node(x)) claim(ibits, nb + rid(x));
+          use(x, p);
+        }
+      } else {
+        uint32_t id = rid(r);
+        uint32_t blk = b.lblock_of[K.first_instr + id / 4];
+        uint32_t ch[3];
+        int c = node_children(v, id, ch);
+        for (int q = 0; q < c; ++q) use(ch[q], blk);
+      }
+    }
+    __syncwarp();
+  }
+  __syncwarp();
+  for (uint32_t q = lane; q < nn; q += 32) {
+    uint64_t g = nb + q;
+    uint32_t f = ((rbits[g >> 5] >> (g & 31)) & 1u) | (((cbits[g >> 5] >> (g & 31)) & 1u) << 1) |
+                 (((ibits[g >> 5] >> (g & 31)) & 1u) << 2);
+    fl[q] = (uint8_t)f;
+  }
+  if (lane == 0) K.n_phis = s_npl[wid];
 }
 
 // ---------------------------------------------------------------------------
@@ -155,8 +181,12 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
   return TY_NONE;
 }
 
+// least fixed point of the type equations: one warp per kernel, lanes update
+// nodes and used join versions concurrently until a vote finds no change (the
+// equations are monotone, so every such iteration reaches the same solution)
 __global__ void k_types(Batch b) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  uint32_t lane = threadIdx.x & 31u;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) return;
@@ -165,30 +195,43 @@ __global__ void k_types(Batch b) {
   uint8_t* nt = b.ntype + nb;
   const uint8_t* fl = b.nflag + nb;
   uint8_t* pt = b.phi_type + K.state_off;
-  const uint8_t* pu = b.phi_used + K.state_off;
+  const uint32_t* pl = b.plist + K.state_off;
   uint32_t nn = 4 * K.n_instr;
-  size_t np = (size_t)K.n_lblock * K.R;
-  for (uint32_t q = 0; q < nn; ++q) nt[q] = TY_NONE;
-  for (size_t q = 0; q < np; ++q) pt[q] = TY_NONE;
+  for (uint32_t q = lane; q < nn; q += 32) nt[q] = TY_NONE;
+  for (uint32_t q = lane; q < K.n_phis; q += 32) {
+    uint32_t e = pl[q];
+    pt[(size_t)(e >> 10) * K.R + (e & 0x3FF)] = TY_NONE;
+  }
+  __syncwarp();
   bool changed = true;
   int guard = 0;
   while (changed && guard++ < 100000) {
-    changed = false;
-    for (uint32_t id = 0; id < nn; ++id) {
+    bool ch = false;
+    for (uint32_t id = lane; id < nn; id += 32) {
       if (!(fl[id] & 1)) continue;
       uint8_t t = tjoin(nt[id], node_type(v, nt, pt, id));
-      if (t != nt[id]) { nt[id] = t; changed = true; }
+      if (t != nt[id]) {
+        nt[id] = t;
+        ch = true;
+      }
     }
-    for (size_t q = 0; q < np; ++q) {
-      if (!pu[q]) continue;
-      uint32_t B = (uint32_t)(q / K.R), reg = (uint32_t)(q % K.R);
-      uint8_t t = pt[q];
+    __syncwarp();
+    for (uint32_t q = lane; q < K.n_phis; q += 32) {
+      uint32_t e = pl[q];
+      uint32_t B = e >> 10, reg = e & 0x3FF;
+      size_t slot = (size_t)B * K.R + reg;
+      uint8_t t = pt[slot];
       for (uint32_t pi = b.pred_off[K.first_lblock + B]; pi < b.pred_off[K.first_lblock + B + 1]; ++pi)
         t = tjoin(t, ref_type(v, nt, pt, fwd(v, out_val(b, K, b.preds[pi], reg))));
-      if (t != pt[q]) { pt[q] = t; changed = true; }
+      if (t != pt[slot]) {
+        pt[slot] = t;
+        ch = true;
+      }
     }
+    __syncwarp();
+    changed = __any_sync(0xFFFFFFFFu, ch);
   }
-  if (changed) atomicOr(b.err, ERR_CAPACITY);
+  if (changed && lane == 0) atomicOr(b.err, ERR_CAPACITY);
 }
 
 __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses, const uint8_t* fl, uint32_t id) {
@@ -201,9 +244,11 @@ __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses
 }
 
 // variable numbers: per block its join versions (by register), then its nodes
-// by (instruction, slot); this is the order of their program points
+// by (instruction, slot); this is the order of their program points.  One warp
+// per kernel: lanes test 32 candidates at a time, a ballot numbers them in order.
 __global__ void k_vars(Batch b) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  uint32_t lane = threadIdx.x & 31u;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) return;
@@ -217,31 +262,50 @@ __global__ void k_vars(Batch b) {
   const uint8_t* pu = b.phi_used + K.state_off;
   const uint8_t* pt = b.phi_type + K.state_off;
   uint8_t* vt = b.var_type + nb + K.state_off;
-  for (uint32_t q = 0; q < 4 * K.n_instr; ++q) vo[q] = -1;
+  for (uint32_t q = lane; q < 4 * K.n_instr; q += 32) vo[q] = -1;
+  __syncwarp();
   int32_t n = 0;
+  const unsigned below = (1u << lane) - 1u;
   for (uint32_t bl = 0; bl < K.n_lblock; ++bl) {
-    for (uint32_t r = 0; r < K.R; ++r) {
+    for (uint32_t r0 = 0; r0 < K.R; r0 += 32) {
+      uint32_t r = r0 + lane;
       size_t q = (size_t)bl * K.R + r;
-      if (pu[q]) {
-        pv[q] = n;
-        vt[n++] = tresolve(pt[q], 32);
-      } else {
-        pv[q] = -1;
-      }
-    }
-    const BlockRec& B = b.lblocks[K.first_lblock + bl];
-    for (uint32_t i = B.first; i < B.end; ++i) {
-      if (b.lblock_of[K.first_instr + i] != bl) continue;
-      for (uint32_t s = 0; s < 4; ++s) {
-        uint32_t id = 4 * i + s;
-        if (is_var_node(v, uses, fl, id)) {
-          vo[id] = n;
-          vt[n++] = tresolve(nt[id], node_width(v, id));
+      bool used = r < K.R && pu[q];
+      unsigned m = __ballot_sync(0xFFFFFFFFu, used);
+      if (r < K.R) {
+        if (used) {
+          int32_t x = n + __popc(m & below);
+          pv[q] = x;
+          vt[x] = tresolve(pt[q], 32);
+        } else {
+          pv[q] = -1;
         }
       }
+      n += __popc(m);
+    }
+    const BlockRec& B = b.lblocks[K.first_lblock + bl];
+    for (uint32_t i0 = B.first; i0 < B.end; i0 += 8) {  // 8 instructions = 32 slots
+      uint32_t i = i0 + lane / 4, s = lane & 3u;
+      uint32_t id = 4 * i + s;
+      bool inb = i < B.end;
+      bool mine = inb && b.lblock_of[K.first_instr + i] == bl;
+      bool isv = mine && is_var_node(v, uses, fl, id);
+      unsigned m = __ballot_sync(0xFFFFFFFFu, isv);
+      if (mine) {
+        if (isv) {
+          int32_t x = n + __popc(m & below);
+          vo[id] = x;
+          vt[x] = tresolve(nt[id], node_width(v, id));
+        } else {
+          vo[id] = -1;
+        }
+      } else if (inb) {
+        vo[id] = -1;
+      }
+      n += __popc(m);
     }
   }
-  K.n_vars = (uint32_t)n;
+  if (lane == 0) K.n_vars = (uint32_t)n;
 }
 
 __global__ void k_wl_size(Batch b, uint32_t* __restrict__ sz) {
@@ -306,14 +370,17 @@ void launch_node_cache(Batch& b, cudaStream_t s) {
   ++launch_counter();
 }
 
-void launch_analysis(Batch& b, uint32_t* wl, cudaStream_t s) {
+void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, cudaStream_t s) {
   if (!b.K) return;
-  const int T = 64;
-  k_reach<<<(b.K + T - 1) / T, T, 0, s>>>(b, wl);
+  // four bitmaps: reached nodes, cross-block uses, join inputs (4I bits each), used joins (NS bits)
+  uint64_t wn = (4ull * b.I + 63) / 32;
+  uint32_t *rb = bits, *cb = bits + wn, *ib = bits + 2 * wn, *pb = bits + 3 * wn;
+  cudaMemsetAsync(bits, 0, sizeof(uint32_t) * nbits_words, s);
+  k_reach<<<(b.K + 3) / 4, 128, 0, s>>>(b, wl, rb, cb, ib, pb);
   ++launch_counter();
-  k_types<<<(b.K + T - 1) / T, T, 0, s>>>(b);
+  k_types<<<(b.K + 3) / 4, 128, 0, s>>>(b);
   ++launch_counter();
-  k_vars<<<(b.K + T - 1) / T, T, 0, s>>>(b);
+  k_vars<<<(b.K + 3) / 4, 128, 0, s>>>(b);
   ++launch_counter();
 }
 

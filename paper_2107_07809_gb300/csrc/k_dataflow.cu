@@ -303,33 +303,27 @@ __global__ void k_dominators(Batch b, uint32_t* __restrict__ rpo_index, uint32_t
 // per-block definitions: last definition of every register (into st_out) and
 // the block's definition bitset
 // ---------------------------------------------------------------------------
-__global__ void k_local_defs(Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off) {
-  uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= b.I) return;
-  const KHdr& K = b.kh[b.ikern[gi]];
+__global__ void k_local_defs(Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off,
+                             const uint32_t* __restrict__ blk_kern) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NLB) return;
+  uint32_t k = blk_kern[g];
+  const KHdr& K = b.kh[k];
   if (K.bad) return;
-  uint32_t blk = b.lblock_of[gi];
-  if (blk == kNone) return;
+  uint32_t bl = g - K.first_lblock;
+  const BlockRec& B = b.lblocks[g];
   RegMap M{K.vgprs, K.sgprs};
-  uint32_t i = gi - K.first_instr;
-  Def d[4];
-  int n = idefs(b, K, M, i, d);
-  if (!n) return;
-  const BlockRec& B = b.lblocks[K.first_lblock + blk];
   uint32_t words = (K.R + 31) / 32;
-  uint32_t* db = defbits + bits_off[b.ikern[gi]] + (size_t)blk * words;
-  for (int t = 0; t < n; ++t) {
-    atomicOr(&db[d[t].reg >> 5], 1u << (d[t].reg & 31));
-    bool later = false;
-    for (int u = t + 1; u < n && !later; ++u) later = d[u].reg == d[t].reg;
-    for (uint32_t q = i + 1; q < B.end && !later; ++q) {
-      if (b.lblock_of[K.first_instr + q] != blk) continue;
-      Def e[4];
-      int m = idefs(b, K, M, q, e);
-      for (int u = 0; u < m; ++u)
-        if (e[u].reg == d[t].reg) later = true;
+  uint32_t* db = defbits + bits_off[k] + (size_t)bl * words;
+  uint32_t* out = b.st_out + K.state_off + (size_t)bl * K.R;
+  for (uint32_t i = B.first; i < B.end; ++i) {
+    if (b.lblock_of[K.first_instr + i] != bl) continue;
+    Def d[4];
+    int n = idefs(b, K, M, i, d);
+    for (int t = 0; t < n; ++t) {  // later definitions overwrite: the row ends as the last ones
+      db[d[t].reg >> 5] |= 1u << (d[t].reg & 31);
+      out[d[t].reg] = d[t].val;
     }
-    if (!later) b.st_out[K.state_off + (size_t)blk * K.R + d[t].reg] = d[t].val;
   }
 }
 
@@ -416,36 +410,25 @@ __global__ void k_versions(Batch b, uint32_t* __restrict__ defbits, uint32_t* __
 // ---------------------------------------------------------------------------
 // nodes: one thread per instruction
 // ---------------------------------------------------------------------------
-struct NodeCtx;
-__device__ uint32_t reg_before(const NodeCtx& c, uint32_t reg);
-
 struct NodeCtx {
   const Batch* b;
   const KHdr* K;
   RegMap M;
-  uint32_t i, blk, first;
+  uint32_t i;
+  uint32_t* row;  // current register values of the block (its in-state, then updated)
 };
 
-// register value just before instruction ctx.i
-__device__ uint32_t reg_before(const NodeCtx& c, uint32_t reg) {
-  const Batch& b = *c.b;
-  for (int q = (int)c.i - 1; q >= (int)c.first; --q) {
-    if (b.lblock_of[c.K->first_instr + q] != c.blk) continue;
-    Def d[4];
-    int n = idefs(b, *c.K, c.M, (uint32_t)q, d);
-    for (int t = n - 1; t >= 0; --t)
-      if (d[t].reg == reg) return d[t].val;
-  }
-  uint32_t v = b.st_in[c.K->state_off + (size_t)c.blk * c.K->R + reg];
+__device__ __forceinline__ uint32_t reg_now(const NodeCtx& c, uint32_t reg) {
+  uint32_t v = c.row[reg];
   return v == kTop ? kUndef : v;
 }
 
 __device__ __forceinline__ uint32_t src32(const NodeCtx& c, Node* nodes, const InstrRec& r, uint32_t o,
                                           uint32_t slot) {
   uint32_t tg = otag(o);
-  if (tg == TG_VGPR) return reg_before(c, c.M.v(opay(o)));
-  if (tg == TG_SGPR) return reg_before(c, c.M.s(opay(o)));
-  if (tg == TG_VCC) return reg_before(c, c.M.vcc());
+  if (tg == TG_VGPR) return reg_now(c, c.M.v(opay(o)));
+  if (tg == TG_SGPR) return reg_now(c, c.M.s(opay(o)));
+  if (tg == TG_VCC) return reg_now(c, c.M.vcc());
   Node& n = nodes[slot];
   n.kind = N_CONST;
   if (tg == TG_ICONST) {
@@ -461,16 +444,6 @@ __device__ __forceinline__ uint32_t src32(const NodeCtx& c, Node* nodes, const I
   return mkref(4 * c.i + slot, PART_ENTIRE);
 }
 
-// source value of operand q of the carry-out instruction described by c, as
-// that instruction's own node holds it (constants live in its slots 1..2)
-__device__ __forceinline__ uint32_t src_of_co(const NodeCtx& c, const InstrRec& r, int q) {
-  uint32_t o = r.opnd[q], tg = otag(o);
-  if (tg == TG_VGPR) return reg_before(c, c.M.v(opay(o)));
-  if (tg == TG_SGPR) return reg_before(c, c.M.s(opay(o)));
-  if (tg == TG_VCC) return reg_before(c, c.M.vcc());
-  return mkref(4 * c.i + 1 + (uint32_t)(q - 2), PART_ENTIRE);
-}
-
 __device__ __forceinline__ uint32_t make_pair(const NodeCtx& c, Node* nodes, uint32_t lo, uint32_t hi,
                                               uint32_t slot) {
   if ((r_node(lo) || r_leaf(lo)) && rpart(lo) == PART_LO && hi == ((lo & ~3u) | PART_HI)) return lo & ~3u;
@@ -483,33 +456,14 @@ __device__ __forceinline__ uint32_t make_pair(const NodeCtx& c, Node* nodes, uin
 }
 
 __device__ __forceinline__ uint32_t src64(const NodeCtx& c, Node* nodes, uint32_t o, uint32_t slot) {
-  uint32_t a = reg_before(c, reg_of(c.M, o, 0)), h = reg_before(c, reg_of(c.M, o, 1));
+  uint32_t a = reg_now(c, reg_of(c.M, o, 0)), h = reg_now(c, reg_of(c.M, o, 1));
   return make_pair(c, nodes, a, h, slot);
 }
 
-__global__ void k_nodes(Batch b) {
-  uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= b.I) return;
-  const KHdr& K = b.kh[b.ikern[gi]];
-  Node* nodes = b.nodes + 4 * (size_t)gi;
-  for (int q = 0; q < 4; ++q) {
-    nodes[q].kind = N_NONE;
-    nodes[q].nsrc = 0;
-    nodes[q].fused = 0;
-    nodes[q].op = 0;
-    nodes[q].src[0] = nodes[q].src[1] = nodes[q].src[2] = kTop;
-    nodes[q].cval = 0;
-  }
-  if (K.bad) return;
-  uint32_t blk = b.lblock_of[gi];
-  if (blk == kNone) return;
-  NodeCtx c;
-  c.b = &b;
-  c.K = &K;
-  c.M = RegMap{K.vgprs, K.sgprs};
-  c.i = gi - K.first_instr;
-  c.blk = blk;
-  c.first = b.lblocks[K.first_lblock + blk].first;
+// nodes of instruction c.i (kernel-relative); `knodes` = the kernel's nodes
+__device__ void build_instr_nodes(const Batch& b, const KHdr& K, NodeCtx& c, Node* knodes) {
+  uint32_t gi = K.first_instr + c.i;
+  Node* nodes = knodes + 4 * (size_t)c.i;
   const InstrRec& r = b.ins[gi];
   uint8_t ctl = b.ctl[gi];
   Node& nd = nodes[0];
@@ -518,7 +472,7 @@ __global__ void k_nodes(Batch b) {
   nd.op = r.op;
   if (ctl == C_CBR) {
     nd.nsrc = 1;
-    nd.src[0] = reg_before(c, r.op == O_S_AND_SAVEEXEC ? c.M.vcc() : c.M.scc());
+    nd.src[0] = reg_now(c, r.op == O_S_AND_SAVEEXEC ? c.M.vcc() : c.M.scc());
     return;
   }
   uint32_t s[3];
@@ -530,23 +484,19 @@ __global__ void k_nodes(Batch b) {
       nd.cval = r.imm;
       break;
     case O_BUFFER_STORE_DWORD: s[ns++] = src32(c, nodes, r, r.opnd[0], 1); break;
-    case O_BUFFER_LOAD_DWORD: s[ns++] = reg_before(c, c.M.spill(r.imm / 4)); break;
+    case O_BUFFER_LOAD_DWORD: s[ns++] = reg_now(c, c.M.spill(r.imm / 4)); break;
     case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: {
       uint32_t a = src32(c, nodes, r, r.opnd[2], 1), bb = src32(c, nodes, r, r.opnd[3], 2);
       if (b.fused[gi]) {
-        // the low-half node belongs to another thread: take its sources the same way
-        uint32_t j = b.co_idx[gi];
-        NodeCtx cj = c;
-        cj.i = j;
-        const InstrRec& rj = b.ins[K.first_instr + j];
-        uint32_t l0 = src_of_co(cj, rj, 2), l1 = src_of_co(cj, rj, 3);
-        s[ns++] = make_pair(c, nodes, l0, a, 1);
-        s[ns++] = make_pair(c, nodes, l1, bb, 2);
+        // the low half's sources, as its node (built earlier in this walk) holds them
+        const Node& lo = knodes[4 * (size_t)b.co_idx[gi]];
+        s[ns++] = make_pair(c, nodes, lo.src[0], a, 1);
+        s[ns++] = make_pair(c, nodes, lo.src[1], bb, 2);
         nd.fused = 1;
       } else {
         s[ns++] = a;
         s[ns++] = bb;
-        s[ns++] = reg_before(c, c.M.vcc());
+        s[ns++] = reg_now(c, c.M.vcc());
       }
       break;
     }
@@ -556,7 +506,7 @@ __global__ void k_nodes(Batch b) {
         if (tg == TG_VGPR || tg == TG_SGPR || tg == TG_VCC) {
           uint32_t cnt = tg == TG_VCC ? 1 : ocnt(o);
           if (cnt == 2) s[ns] = src64(c, nodes, o, 1 + ns);
-          else s[ns] = reg_before(c, reg_of(c.M, o, 0));
+          else s[ns] = reg_now(c, reg_of(c.M, o, 0));
           ++ns;
         }
       }
@@ -587,6 +537,47 @@ __global__ void k_nodes(Batch b) {
     h2.cval = r.imm + 8;
   }
   if (r.op == O_V_ADD_CO_U32 || r.op == O_V_SUB_CO_U32) nodes[3].kind = N_CARRY;
+}
+
+__global__ void k_clear_nodes(Batch b) {
+  uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 4ull * b.I) return;
+  Node& n = b.nodes[g];
+  n.kind = N_NONE;
+  n.nsrc = 0;
+  n.fused = 0;
+  n.op = 0;
+  n.src[0] = n.src[1] = n.src[2] = kTop;
+  n.cval = 0;
+}
+
+// one thread per logical block: copy the block's in-state into a working row,
+// then build each instruction's nodes and apply its definitions in order
+__global__ void k_nodes(Batch b, uint32_t* __restrict__ rows, const uint32_t* __restrict__ blk_kern) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NLB) return;
+  uint32_t k = blk_kern[g];
+  const KHdr& K = b.kh[k];
+  if (K.bad) return;
+  uint32_t bl = g - K.first_lblock;
+  const BlockRec& B = b.lblocks[g];
+  uint32_t* row = rows + K.state_off + (size_t)bl * K.R;
+  const uint32_t* in = b.st_in + K.state_off + (size_t)bl * K.R;
+  for (uint32_t r = 0; r < K.R; ++r) row[r] = in[r];
+  NodeCtx c;
+  c.b = &b;
+  c.K = &K;
+  c.M = RegMap{K.vgprs, K.sgprs};
+  c.row = row;
+  Node* knodes = b.nodes + 4 * (size_t)K.first_instr;
+  for (uint32_t i = B.first; i < B.end; ++i) {
+    if (b.lblock_of[K.first_instr + i] != bl) continue;
+    c.i = i;
+    build_instr_nodes(b, K, c, knodes);
+    Def d[4];
+    int n = idefs(b, K, c.M, i, d);
+    for (int t = 0; t < n; ++t) row[d[t].reg] = d[t].val;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -639,14 +630,19 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
     cudaMemsetAsync(d.defbits, 0, sizeof(uint32_t) * d.NW, s);
     cudaMemsetAsync(d.phibits, 0, sizeof(uint32_t) * d.NW, s);
   }
-  if (b.I) {
-    k_local_defs<<<(b.I + T - 1) / T, T, 0, s>>>(b, d.defbits, d.bits_off);
+  if (b.NLB) {
+    k_local_defs<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, d.defbits, d.bits_off, d.blk_kern);
     ++launch_counter();
   }
   k_versions<<<(b.K + 3) / 4, 128, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
   ++launch_counter();
   if (b.I) {
-    k_nodes<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+    uint64_t nn = 4ull * b.I;
+    k_clear_nodes<<<(uint32_t)((nn + T - 1) / T), T, 0, s>>>(b);
+    ++launch_counter();
+  }
+  if (b.NLB) {
+    k_nodes<<<(b.NLB + 63) / 64, 64, 0, s>>>(b, d.rows, d.blk_kern);
     ++launch_counter();
   }
 }

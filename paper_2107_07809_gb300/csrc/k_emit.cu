@@ -643,7 +643,7 @@ __device__ void print_args(Wr& w, const Batch& b, const KHdr& K, const ArgRec* A
 // write at scanned offsets); one thread per item sizes it and, after a scan,
 // writes it
 // ---------------------------------------------------------------------------
-enum : uint32_t { IT_NONE = 0, IT_HEAD, IT_DECLS, IT_INSTR, IT_COPY, IT_IF, IT_ELSE, IT_CLOSE, IT_DO, IT_WHILE,
+enum : uint32_t { IT_NONE = 0, IT_HEAD, IT_DECLS, IT_BLOCK, IT_COPY, IT_IF, IT_ELSE, IT_CLOSE, IT_DO, IT_WHILE,
                   IT_TAIL, IT_FAIL };
 constexpr uint32_t kDeclChunk = 64;
 
@@ -662,12 +662,26 @@ struct LayoutCtx {
   }
   // the copies along p -> s, in an order where no copy overwrites a version
   // that a later copy still reads (a cycle marks the kernel partial)
+  const uint32_t* pbits;  // used join versions, bit (state_off + block * R + reg)
+  // next used join version of block s at a register >= reg (or R)
+  __device__ uint32_t next_used(uint32_t s, uint32_t reg) const {
+    const KHdr& Kr = *K;
+    uint64_t base = (uint64_t)Kr.state_off + (uint64_t)s * Kr.R;
+    while (reg < Kr.R) {
+      uint64_t g = base + reg;
+      uint32_t w = pbits[g >> 5] >> (g & 31);
+      if (w) {
+        uint32_t r = reg + (uint32_t)(__ffs(w) - 1);
+        return r < Kr.R ? r : Kr.R;
+      }
+      reg += 32 - (uint32_t)(g & 31);
+    }
+    return Kr.R;
+  }
   __device__ void copies(uint32_t p, uint32_t s, uint32_t lvl) {
     const KHdr& Kr = *K;
-    const uint8_t* pu = b->phi_used + Kr.state_off;
     uint32_t R = Kr.R, m = 0;
-    for (uint32_t reg = 0; reg < R; ++reg) {
-      if (!pu[(size_t)s * R + reg]) continue;
+    for (uint32_t reg = next_used(s, 0); reg < R; reg = next_used(s, reg + 1)) {
       uint32_t dst = phiref(s, reg);
       uint32_t o = b->st_out[Kr.state_off + (size_t)p * R + reg];
       uint32_t src = fwd(v, o == kTop ? kUndef : o);
@@ -711,10 +725,8 @@ struct LayoutCtx {
   }
   __device__ uint32_t ncopies(uint32_t p, uint32_t s) {
     const KHdr& Kr = *K;
-    const uint8_t* pu = b->phi_used + Kr.state_off;
     uint32_t c = 0;
-    for (uint32_t reg = 0; reg < Kr.R; ++reg) {
-      if (!pu[(size_t)s * Kr.R + reg]) continue;
+    for (uint32_t reg = next_used(s, 0); reg < Kr.R; reg = next_used(s, reg + 1)) {
       uint32_t o = b->st_out[Kr.state_off + (size_t)p * Kr.R + reg];
       uint32_t src = fwd(v, o == kTop ? kUndef : o);
       if (src != phiref(s, reg) && src != kUndef) ++c;
@@ -725,7 +737,7 @@ struct LayoutCtx {
 
 __global__ void k_layout(Batch b, Item* __restrict__ items, const uint32_t* __restrict__ item_base,
                          uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ scratch_all,
-                         uint32_t* __restrict__ stk_all, int write) {
+                         uint32_t* __restrict__ stk_all, const uint32_t* __restrict__ pbits, int write) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
@@ -739,6 +751,7 @@ __global__ void k_layout(Batch b, Item* __restrict__ items, const uint32_t* __re
   L.write = write != 0;
   L.scratch = scratch_all + K.wl_off;
   L.scap = 4 * K.n_instr + K.n_lblock * K.R + 3 * K.R + 8;
+  L.pbits = pbits;
   if (!write) K.partial = 0;
   if (K.bad) {
     L.put(IT_FAIL, 0, 0, 0);
@@ -772,8 +785,7 @@ __global__ void k_layout(Batch b, Item* __restrict__ items, const uint32_t* __re
           case R_BLOCK: {
             uint32_t bl = X[RG_BLOCK];
             const BlockRec& B = BL[bl];
-            for (uint32_t i = B.first; i < B.end; ++i)
-              if (b.lblock_of[K.first_instr + i] == bl) L.put(IT_INSTR, lvl, i, 0);
+            L.put(IT_BLOCK, lvl, bl, 0);
             uint32_t term = b.lterm[K.first_lblock + bl];
             bool cb = b.ctl[K.first_instr + term] == C_CBR && B.succ1 != kNone;
             if (!cb && B.succ0 != kNone) L.copies(bl, B.succ0, lvl);
@@ -901,7 +913,12 @@ __global__ void k_items(Batch b, const Item* __restrict__ items, uint32_t NI, ui
         w.s(";\n");
       }
       break;
-    case IT_INSTR: em.instr_stmts(it.a, (int)lvl); break;
+    case IT_BLOCK: {
+      const BlockRec& B = b.lblocks[K.first_lblock + it.a];
+      for (uint32_t q = B.first; q < B.end; ++q)
+        if (b.lblock_of[K.first_instr + q] == it.a) em.instr_stmts(q, (int)lvl);
+      break;
+    }
     case IT_COPY: em.one_copy(it.a >> 10, it.a & 0x3FF, it.b, (int)lvl); break;
     case IT_IF:
       w.indent((int)lvl);
@@ -960,9 +977,9 @@ __global__ void k_file_out(Batch b, uint32_t total) {
 }
 
 void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* item_cnt, uint32_t* scratch,
-                   uint32_t* stk, int write, cudaStream_t s) {
+                   uint32_t* stk, const uint32_t* pbits, int write, cudaStream_t s) {
   if (!b.K) return;
-  k_layout<<<(b.K + 63) / 64, 64, 0, s>>>(b, items, item_base, item_cnt, scratch, stk, write);
+  k_layout<<<(b.K + 63) / 64, 64, 0, s>>>(b, items, item_base, item_cnt, scratch, stk, pbits, write);
   ++launch_counter();
 }
 
