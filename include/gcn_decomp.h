@@ -134,6 +134,46 @@ int gcn_decomp_run_stats(gcn_decomp_t *h, uint64_t *out, int cap);
  * (run_device or submit_batch); 0 before the first run. */
 uint64_t gcn_decomp_launches(gcn_decomp_t *h);
 
+/* Line tokenisation without any allocation (the paper has no counterpart:
+ * this is a service for callers, not a step of the method).
+ *
+ * For callers that cannot let a library allocate device memory (code running
+ * while their own CUDA graph is being captured, where cudaMalloc is not
+ * allowed; a process whose memory pool owns all device memory; a real-time
+ * path that must not block on the allocator).  It runs the S1 newline scan of
+ * the batch pipeline on a text already in device memory, with its scratch in
+ * a fixed 512 KiB array compiled into the library instead of handle memory.
+ * No handle is needed; nothing is allocated by the CUDA runtime or any
+ * library.
+ *
+ *  d_text[0..text_len)   device bytes of the current device (any alignment;
+ *                        16-byte aligned is faster), at most 1 GiB.
+ *  d_line_start[0..line_cap)  device u32, receives the byte offset of every
+ *                        line start: [0] = 0, [k] = 1 + offset of the k-th
+ *                        '
+' (so a text ending with '
+' yields lines+1
+ *                        entries).  Needs line_cap >= 1 + number of '
+'.
+ *  d_result[0..2)        device u32: [0] = number of '
+' bytes, [1] = error
+ *                        bits (0 = ok; 4 = line_cap too small, the offsets
+ *                        past it were not written; 1 or 2 = a bounded
+ *                        device-side wait gave up, the output is invalid).
+ *  stream                cudaStream_t (NULL = legacy default stream).
+ *
+ * Work is queued on `stream` and the call returns without synchronising;
+ * read d_result after the stream has finished.  Runs on the calling thread's
+ * current device.  The first call on a device looks the scratch address up
+ * once (that may load the module): make it before any stream capture starts.
+ * The scratch is shared by all calls on a device, so calls whose device work
+ * could overlap (other streams, other threads) must be serialised by the
+ * caller; overlapping calls race and give wrong results.
+ * Errors: GCN_EINVAL (NULL pointer, line_cap 0), GCN_ENOMEM (text longer
+ * than 1 GiB: rejected before anything is queued), GCN_ECUDA. */
+int gcn_decomp_line_starts_noalloc(const uint8_t *d_text, uint64_t text_len, uint32_t *d_line_start,
+                                   uint64_t line_cap, uint32_t *d_result, void *stream);
+
 /* Last error message of this thread (static storage; never NULL). */
 const char *gcn_decomp_last_error(void);
 

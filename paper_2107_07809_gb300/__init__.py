@@ -105,6 +105,7 @@ def lib():
             L.gcn_decomp_run_stats.argtypes = [vp, ctypes.POINTER(u64), i32]
             L.gcn_decomp_launches.argtypes = [vp]
             L.gcn_decomp_launches.restype = u64
+            L.gcn_decomp_line_starts_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             _lib = L
     return _lib
 
@@ -216,3 +217,13 @@ class Decompiler:
         nm = (ctypes.c_char_p * 16)()
         n = lib().gcn_decomp_stage_times(self._h, ms, nm, 16)
         return {nm[i].decode(): float(ms[i]) for i in range(max(n, 0))}
+
+
+def line_starts_noalloc(d_text: int, text_len: int, d_line_start: int, line_cap: int, d_result: int,
+                        stream: int = 0) -> None:
+    """gcn_decomp_line_starts_noalloc: newline scan into caller device buffers, no allocation.
+
+    ``d_result`` (2 x u32 on the device) receives the newline count and error bits
+    once the stream has run the work."""
+    _ck(lib().gcn_decomp_line_starts_noalloc(d_text, text_len, d_line_start, line_cap, d_result, stream or None),
+        "gcn_decomp_line_starts_noalloc")

@@ -347,6 +347,9 @@ void finish_run(gcn_decomp* h, cudaStream_t s) {
 
 }  // namespace
 
+// error text for entry points defined in other translation units
+void gd::set_api_error(const char* msg) { set_err(msg); }
+
 extern "C" {
 
 const char* gcn_decomp_last_error(void) { return g_err.c_str(); }

@@ -4,6 +4,9 @@
 
 namespace gd {
 
+// sets the text gcn_decomp_last_error returns on this thread
+void set_api_error(const char* msg);
+
 // kernels launched by this process (host-side count; one instance across units)
 inline uint64_t& launch_counter() {
   static uint64_t c = 0;

@@ -36,3 +36,15 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(pkg.GcnDecompError) as e:
         pkg.Decompiler(0)
     assert e.value.rc == pkg.GCN_EINVAL
+
+
+def test_noalloc_rejects_on_the_host():
+    """Argument and size checks of gcn_decomp_line_starts_noalloc happen before
+    any CUDA call, so they answer the same without a GPU."""
+    pkg.build()
+    L = pkg.lib()
+    fake = 1 << 20  # never dereferenced: both calls are rejected first
+    assert L.gcn_decomp_line_starts_noalloc(fake, (1 << 30) + 1, fake, 16, fake, None) == pkg.GCN_ENOMEM
+    assert L.gcn_decomp_line_starts_noalloc(fake, 100, fake, 0, fake, None) == pkg.GCN_EINVAL
+    assert L.gcn_decomp_line_starts_noalloc(None, 100, fake, 16, fake, None) == pkg.GCN_EINVAL
+    assert L.gcn_decomp_line_starts_noalloc(fake, 100, None, 16, fake, None) == pkg.GCN_EINVAL
