@@ -303,19 +303,46 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   sync_totals();
   uint32_t NI = b.K ? h->h_tot[10] : 0;
   Item* items = W.get<Item>("items", (size_t)NI + 1);
-  uint32_t* ilen = W.get<uint32_t>("item_len", (size_t)NI + 1);
-  uint32_t* ioff = W.get<uint32_t>("item_off", (size_t)NI + 1);
+  uint32_t* iw = W.get<uint32_t>("item_weight", (size_t)NI + 1);
+  uint32_t* sub0 = W.get<uint32_t>("item_sub0", (size_t)NI + 1);
+  uint32_t* pflag = W.get<uint32_t>("print_flag", (size_t)b.I + 1);
+  uint32_t* prank = W.get<uint32_t>("print_rank", (size_t)b.I + 1);
+  uint32_t* plist = W.get<uint32_t>("print_instr", (size_t)b.I + 1);
   launch_layout(b, items, ibase, icnt, wl, rstk, pbits, 1, s);
-  launch_items(b, items, NI, ilen, ioff, 0, s);
-  if (NI) launch_scan(ilen, ioff, NI, 0, false, sc, &tot[11], b.err, s);
+  launch_print_list(b, pflag, nullptr, nullptr, 0, s);
+  launch_scan(pflag, prank, b.I + 1, 0, false, sc, nullptr, b.err, s);
+  launch_print_list(b, pflag, prank, plist, 1, s);
+  launch_subitems(b, items, NI, prank, iw, nullptr, nullptr, 0, 0, s);
+  if (NI) launch_scan(iw, sub0, NI, 0, false, sc, &tot[12], b.err, s);
   CK(cudaGetLastError());
   sync_totals();
-  uint32_t total = NI ? h->h_tot[11] : 0;
+  const uint32_t NS2 = NI ? h->h_tot[12] : 0;
+  CK(cudaMemcpyAsync(sub0 + NI, &tot[12], 4, cudaMemcpyDeviceToDevice, s));
+  ScanScratch sc2 = sc;
+  if (scan_tiles(NS2 + 1) + 64 > std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)) + 64)
+    sc2.status = W.get<uint64_t>("tile_status_sub", scan_tiles(NS2 + 1) + 64);
+  uint32_t* sitem = W.get<uint32_t>("sub_item", (size_t)NS2 + 1);
+  uint32_t* ilen = W.get<uint32_t>("sub_len", (size_t)NS2 + 1);
+  uint32_t* ioff = W.get<uint32_t>("sub_off", (size_t)NS2 + 1);
+  launch_subitems(b, items, NI, prank, nullptr, sub0, sitem, NS2, 1, s);
+  if (NS2) launch_scan(sitem, sitem, NS2, 1, true, sc2, nullptr, b.err, s);
+  uint8_t* stage = W.get<uint8_t>("emit_stage", (size_t)NS2 * kEmitSlot + 16);
+  uint32_t* ovl = W.get<uint32_t>("emit_overflow", (size_t)NS2 + 1);
+  CK(cudaMemsetAsync(&tot[13], 0, 4, s));
+  // one thread per statement while staging (measured faster than a warp per
+  // statement); one warp per statement for the few long ones redone in place
+  launch_items(b, items, sitem, sub0, prank, plist, NS2, nullptr, ilen, ioff, stage, ovl, &tot[13], 0, s);
+  if (NS2) launch_scan(ilen, ioff, NS2, 0, false, sc2, &tot[11], b.err, s);
+  CK(cudaGetLastError());
+  sync_totals();
+  uint32_t total = NS2 ? h->h_tot[11] : 0;
+  const uint32_t novf = NS2 ? h->h_tot[13] : 0;
   b.out = W.get<uint8_t>("out", (size_t)total + 16);
   b.file_out_off = W.get<uint64_t>("file_out_off", b.F + 2);
   b.file_status = W.get<int32_t>("file_status", b.F + 1);
-  launch_items(b, items, NI, ilen, ioff, 1, s);
-  launch_finish(b, ibase, ioff, total, s);
+  launch_compact(stage, ilen, ioff, NS2, b.out, s);
+  launch_items(b, items, sitem, sub0, prank, plist, novf, ovl, ilen, ioff, nullptr, nullptr, nullptr, 5, s);
+  launch_finish(b, ibase, sub0, ioff, total, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[10], s));
   R.out_bytes = total;

@@ -158,8 +158,17 @@ struct Item {
 };
 void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* item_cnt, uint32_t* scratch,
                    uint32_t* stk, const uint32_t* pbits, int write, cudaStream_t s);
-void launch_items(Batch& b, const Item* items, uint32_t NI, uint32_t* item_len, const uint32_t* item_off, int write,
-                  cudaStream_t s);
-void launch_finish(Batch& b, const uint32_t* item_base, const uint32_t* item_off, uint32_t total, cudaStream_t s);
+constexpr uint32_t kEmitSlot = 256;  // staging bytes per emission sub-item
+void launch_print_list(Batch& b, uint32_t* flag, const uint32_t* rank, uint32_t* list, int phase, cudaStream_t s);
+void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* prank, uint32_t* weight,
+                     const uint32_t* sub0, uint32_t* sub_item, uint32_t NS2, int phase, cudaStream_t s);
+void launch_items(Batch& b, const Item* items, const uint32_t* sub_item, const uint32_t* sub0, const uint32_t* prank,
+                  const uint32_t* pinstr, uint32_t N, const uint32_t* list, uint32_t* item_len,
+                  const uint32_t* item_off, uint8_t* stage, uint32_t* ovf_list, uint32_t* ovf_count,
+                  uint32_t lane_shift, cudaStream_t s);
+void launch_compact(const uint8_t* stage, const uint32_t* item_len, const uint32_t* item_off, uint32_t N,
+                    uint8_t* out, cudaStream_t s);
+void launch_finish(Batch& b, const uint32_t* item_base, const uint32_t* sub0, const uint32_t* item_off,
+                   uint32_t total, cudaStream_t s);
 
 }  // namespace gd

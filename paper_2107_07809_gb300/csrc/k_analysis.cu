@@ -28,7 +28,7 @@ __device__ __forceinline__ bool claim(uint32_t* bits, uint64_t g) {
   return !(atomicOr(&bits[g >> 5], m) & m);
 }
 
-__global__ void k_reach(Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
+__global__ void k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
                         uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits) {
   __shared__ uint32_t s_top[4], s_npl[4];
   const uint32_t wid = threadIdx.x / 32, lane = threadIdx.x & 31u;
@@ -184,7 +184,7 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
 // least fixed point of the type equations: one warp per kernel, lanes update
 // nodes and used join versions concurrently until a vote finds no change (the
 // equations are monotone, so every such iteration reaches the same solution)
-__global__ void k_types(Batch b) {
+__global__ void k_types(const __grid_constant__ Batch b) {
   uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   uint32_t lane = threadIdx.x & 31u;
   if (k >= b.K) return;
@@ -246,7 +246,7 @@ __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses
 // variable numbers: per block its join versions (by register), then its nodes
 // by (instruction, slot); this is the order of their program points.  One warp
 // per kernel: lanes test 32 candidates at a time, a ballot numbers them in order.
-__global__ void k_vars(Batch b) {
+__global__ void k_vars(const __grid_constant__ Batch b) {
   uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   uint32_t lane = threadIdx.x & 31u;
   if (k >= b.K) return;
@@ -308,13 +308,13 @@ __global__ void k_vars(Batch b) {
   if (lane == 0) K.n_vars = (uint32_t)n;
 }
 
-__global__ void k_wl_size(Batch b, uint32_t* __restrict__ sz) {
+__global__ void k_wl_size(const __grid_constant__ Batch b, uint32_t* __restrict__ sz) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   const KHdr& K = b.kh[k];
   sz[k] = K.bad ? 0u : 4 * K.n_instr + K.n_lblock * K.R + 3 * K.R + 8;
 }
-__global__ void k_wl_off(Batch b, const uint32_t* __restrict__ off) {
+__global__ void k_wl_off(const __grid_constant__ Batch b, const uint32_t* __restrict__ off) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   b.kh[k].wl_off = off[k];
@@ -331,7 +331,7 @@ void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint3
 
 // one thread per node: its class, its forwarded sources and, for a load or
 // store, its memory match; later stages read these instead of recomputing
-__global__ void k_node_cache(Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck, uint32_t* __restrict__ sf,
+__global__ void k_node_cache(const __grid_constant__ Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck, uint32_t* __restrict__ sf,
                              uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
   uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= 4ull * b.I) return;

@@ -113,7 +113,7 @@ __device__ __forceinline__ bool defines_vcc(const InstrRec& r) {
 // ---------------------------------------------------------------------------
 // sizes: spill slots, register count, limits
 // ---------------------------------------------------------------------------
-__global__ void k_df_sizes(Batch b, uint32_t* __restrict__ kstate) {
+__global__ void k_df_sizes(const __grid_constant__ Batch b, uint32_t* __restrict__ kstate) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
@@ -135,7 +135,7 @@ __global__ void k_df_sizes(Batch b, uint32_t* __restrict__ kstate) {
   kstate[k] = K.bad ? 0u : K.n_lblock * K.R;
 }
 
-__global__ void k_state_off(Batch b, const uint32_t* __restrict__ off) {
+__global__ void k_state_off(const __grid_constant__ Batch b, const uint32_t* __restrict__ off) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   b.kh[k].state_off = off[k];
@@ -145,7 +145,7 @@ __global__ void k_state_off(Batch b, const uint32_t* __restrict__ off) {
 // 64-bit carry pairs: v_addc_co_u32 / v_subb_co_u32 completing the low half of
 // the last carry-out of the same block (whose register still holds it)
 // ---------------------------------------------------------------------------
-__global__ void k_fusion(Batch b) {
+__global__ void k_fusion(const __grid_constant__ Batch b) {
   uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= b.I) return;
   b.fused[gi] = 0;
@@ -184,7 +184,7 @@ __global__ void k_fusion(Batch b) {
 // ---------------------------------------------------------------------------
 // predecessors (CSR, sorted)
 // ---------------------------------------------------------------------------
-__global__ void k_pred_count(Batch b, uint32_t* __restrict__ cnt, const uint32_t* __restrict__ blk_kern) {
+__global__ void k_pred_count(const __grid_constant__ Batch b, uint32_t* __restrict__ cnt, const uint32_t* __restrict__ blk_kern) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.NLB) return;
   const KHdr& K = b.kh[blk_kern[g]];
@@ -193,7 +193,7 @@ __global__ void k_pred_count(Batch b, uint32_t* __restrict__ cnt, const uint32_t
   if (B.succ1 != kNone) atomicAdd(&cnt[K.first_lblock + B.succ1], 1u);
 }
 
-__global__ void k_pred_fill(Batch b, const uint32_t* __restrict__ blk_kern) {
+__global__ void k_pred_fill(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.NLB) return;
   const KHdr& K = b.kh[blk_kern[g]];
@@ -209,7 +209,7 @@ __global__ void k_pred_fill(Batch b, const uint32_t* __restrict__ blk_kern) {
   }
 }
 
-__global__ void k_pred_sort(Batch b) {
+__global__ void k_pred_sort(const __grid_constant__ Batch b) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.NLB) return;
   uint32_t a = b.pred_off[g], e = b.pred_off[g + 1];
@@ -227,7 +227,7 @@ __global__ void k_pred_sort(Batch b) {
 // ---------------------------------------------------------------------------
 // dominators: depth-first reverse postorder, then iterative intersection
 // ---------------------------------------------------------------------------
-__global__ void k_dominators(Batch b, uint32_t* __restrict__ rpo_index, uint32_t* __restrict__ stk,
+__global__ void k_dominators(const __grid_constant__ Batch b, uint32_t* __restrict__ rpo_index, uint32_t* __restrict__ stk,
                              uint8_t* __restrict__ child) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
@@ -303,7 +303,7 @@ __global__ void k_dominators(Batch b, uint32_t* __restrict__ rpo_index, uint32_t
 // per-block definitions: last definition of every register (into st_out) and
 // the block's definition bitset
 // ---------------------------------------------------------------------------
-__global__ void k_local_defs(Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off,
+__global__ void k_local_defs(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off,
                              const uint32_t* __restrict__ blk_kern) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.NLB) return;
@@ -345,7 +345,7 @@ __device__ __forceinline__ uint32_t entry_value(const KHdr& K, uint32_t r) {
 // versions: frontier closure (warp per kernel, lane = 32 registers), then
 // values in reverse postorder (lanes over registers)
 // ---------------------------------------------------------------------------
-__global__ void k_versions(Batch b, uint32_t* __restrict__ defbits, uint32_t* __restrict__ phibits,
+__global__ void k_versions(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, uint32_t* __restrict__ phibits,
                            const uint32_t* __restrict__ bits_off, uint32_t* __restrict__ err) {
   uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   uint32_t lane = threadIdx.x & 31u;
@@ -539,7 +539,7 @@ __device__ void build_instr_nodes(const Batch& b, const KHdr& K, NodeCtx& c, Nod
   if (r.op == O_V_ADD_CO_U32 || r.op == O_V_SUB_CO_U32) nodes[3].kind = N_CARRY;
 }
 
-__global__ void k_clear_nodes(Batch b) {
+__global__ void k_clear_nodes(const __grid_constant__ Batch b) {
   uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= 4ull * b.I) return;
   Node& n = b.nodes[g];
@@ -553,7 +553,7 @@ __global__ void k_clear_nodes(Batch b) {
 
 // one thread per logical block: copy the block's in-state into a working row,
 // then build each instruction's nodes and apply its definitions in order
-__global__ void k_nodes(Batch b, uint32_t* __restrict__ rows, const uint32_t* __restrict__ blk_kern) {
+__global__ void k_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ rows, const uint32_t* __restrict__ blk_kern) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.NLB) return;
   uint32_t k = blk_kern[g];
@@ -583,7 +583,7 @@ __global__ void k_nodes(Batch b, uint32_t* __restrict__ rows, const uint32_t* __
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-__global__ void k_bits_size(Batch b, uint32_t* __restrict__ kbits) {
+__global__ void k_bits_size(const __grid_constant__ Batch b, uint32_t* __restrict__ kbits) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   const KHdr& K = b.kh[k];

@@ -126,7 +126,7 @@ __device__ __forceinline__ void trim(const uint8_t*& p, const uint8_t*& e) {
   while (e > p && is_space(e[-1])) --e;
 }
 
-__global__ void k_config(Batch b) {
+__global__ void k_config(const __grid_constant__ Batch b) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
@@ -341,7 +341,7 @@ __device__ bool sig_ok(char s, uint32_t o) {
   return false;
 }
 
-__global__ void k_decode(Batch b) {
+__global__ void k_decode(const __grid_constant__ Batch b) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= b.I) return;
   uint32_t line = b.instr_line[i];
@@ -440,7 +440,7 @@ __global__ void k_decode(Batch b) {
   b.ikern[i] = k;
 }
 
-__global__ void k_label_hash(Batch b) {
+__global__ void k_label_hash(const __grid_constant__ Batch b) {
   uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= b.NL) return;
   uint32_t line = b.label_line[j];
@@ -451,7 +451,7 @@ __global__ void k_label_hash(Batch b) {
 }
 
 // branch targets (first definition of the label wins), per-kernel parse flags, leaders
-__global__ void k_resolve(Batch b) {
+__global__ void k_resolve(const __grid_constant__ Batch b) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= b.I) return;
   uint32_t k = b.ikern[i];
@@ -480,7 +480,7 @@ __device__ __forceinline__ bool is_br(uint16_t op) {
   return op == O_S_BRANCH || op == O_S_CBRANCH_SCC0 || op == O_S_CBRANCH_SCC1 || op == O_S_CBRANCH_EXECZ;
 }
 
-__global__ void k_pleaders(Batch b) {
+__global__ void k_pleaders(const __grid_constant__ Batch b) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= b.I) return;
   const KHdr& K = b.kh[b.ikern[i]];
@@ -492,7 +492,7 @@ __global__ void k_pleaders(Batch b) {
 }
 
 // after the inclusive scan of leaders: block ids and block starts
-__global__ void k_pblocks(Batch b, const uint32_t* __restrict__ incl, uint32_t* __restrict__ blk_kern) {
+__global__ void k_pblocks(const __grid_constant__ Batch b, const uint32_t* __restrict__ incl, uint32_t* __restrict__ blk_kern) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= b.I) return;
   uint32_t k = b.ikern[i];
@@ -511,7 +511,7 @@ __global__ void k_pblocks(Batch b, const uint32_t* __restrict__ incl, uint32_t* 
   }
 }
 
-__global__ void k_pblock_edges(Batch b, const uint32_t* __restrict__ blk_kern) {
+__global__ void k_pblock_edges(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.NPB) return;
   const KHdr& K = b.kh[blk_kern[g]];
@@ -565,7 +565,7 @@ struct Form {
 
 __device__ __forceinline__ bool same_pair(uint32_t a, uint32_t bb) { return otag(a) == TG_SGPR && a == bb; }
 
-__global__ void k_exec_forms(Batch b) {
+__global__ void k_exec_forms(const __grid_constant__ Batch b) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
@@ -675,7 +675,7 @@ __device__ __forceinline__ uint32_t resolve_t(const uint8_t* ctl, uint32_t t, ui
   return t;
 }
 
-__global__ void k_lleaders(Batch b) {
+__global__ void k_lleaders(const __grid_constant__ Batch b) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= b.I) return;
   const KHdr& K = b.kh[b.ikern[i]];
@@ -693,7 +693,7 @@ __global__ void k_lleaders(Batch b) {
   }
 }
 
-__global__ void k_lblocks(Batch b, const uint32_t* __restrict__ incl, uint32_t* __restrict__ blk_kern) {
+__global__ void k_lblocks(const __grid_constant__ Batch b, const uint32_t* __restrict__ incl, uint32_t* __restrict__ blk_kern) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= b.I) return;
   uint32_t k = b.ikern[i];
@@ -713,7 +713,7 @@ __global__ void k_lblocks(Batch b, const uint32_t* __restrict__ incl, uint32_t* 
   }
 }
 
-__global__ void k_lblock_edges(Batch b, const uint32_t* __restrict__ blk_kern) {
+__global__ void k_lblock_edges(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.NLB) return;
   const KHdr& K = b.kh[blk_kern[g]];

@@ -8,35 +8,75 @@
 // a value at a join is assigned on the edges into the join; 4-space indent.
 // Unsupported instructions stay as inline asm ("Practical implementation").
 //
-// Two launches run the same code: the first only counts bytes, a scan places
-// every kernel, the second writes.  One thread per kernel; the region tree is
-// walked with an explicit stack, expressions recursively with a depth guard.
+// Layout: one thread per kernel walks the region tree (explicit stack) and
+// lays out items: the head, declaration chunks, the statements of a block,
+// join copies and control lines.  Printing: the statements of blocks become
+// one sub-item per printing instruction, every other item one sub-item; one
+// thread per sub-item prints into a fixed staging slot (expressions
+// recursively, with a depth guard) and records the exact length, a scan
+// places every sub-item, a warp-per-32 copy moves the staged bytes, and the
+// few sub-items longer than a slot are printed again straight into place.
 #include "k_analysis.cuh"
 
 namespace gd {
 
+// Byte writer.  Bytes go out through an inline-asm store the compiler does
+// not treat as a memory access: a plain byte store may alias anything, which
+// made every character reload and store the cursor of a stack-resident
+// writer.  The output buffer is never read back through C++ accesses (only
+// through ld_u8 below), so hiding the stores is safe.
+__device__ __forceinline__ void st_u8(uint8_t* a, char ch) {
+  asm volatile("st.u8 [%0], %1;" ::"l"(a), "h"((unsigned short)(uint8_t)ch));
+}
+__device__ __forceinline__ uint8_t ld_u8(const uint8_t* a) {
+  unsigned short v;
+  asm volatile("ld.u8 %0, [%1];" : "=h"(v) : "l"(a));
+  return (uint8_t)v;
+}
+
 struct Wr {
   uint8_t* p;
-  uint32_t n;
-  bool on;
+  uint32_t n;    // bytes produced so far (also those beyond cap)
+  uint32_t cap;  // bytes that may be stored at p
+  bool ovf;      // some byte fell beyond cap
   __device__ __forceinline__ void c(char ch) {
-    if (on) p[n] = (uint8_t)ch;
+    if (n < cap) st_u8(p + n, ch);
+    else ovf = true;
     ++n;
   }
   __device__ void s(const char* z) {
-    while (*z) c(*z++);
+    uint32_t m = n;
+    for (; *z; ++z, ++m) {
+      if (m < cap) st_u8(p + m, *z);
+      else ovf = true;
+    }
+    n = m;
   }
   __device__ void mem(const uint8_t* a, uint32_t len) {
-    for (uint32_t i = 0; i < len; ++i) c((char)a[i]);
+    uint32_t m = n;
+    for (uint32_t i = 0; i < len; ++i, ++m) {
+      if (m < cap) st_u8(p + m, (char)a[i]);
+      else ovf = true;
+    }
+    n = m;
   }
   __device__ void u64(uint64_t v) {
-    char t[24];
+    char t[20];
     int k = 0;
     do {
       t[k++] = (char)('0' + v % 10);
       v /= 10;
     } while (v);
-    while (k) c(t[--k]);
+    uint32_t m = n;
+    while (k) {
+      if (m < cap) st_u8(p + m, t[--k]);
+      else {
+        ovf = true;
+        --k;
+      }
+      ++m;
+    }
+    n = m;
   }
   __device__ void i64(int64_t v) {
     if (v < 0) {
@@ -47,7 +87,12 @@ struct Wr {
     }
   }
   __device__ void indent(int lvl) {
-    for (int i = 0; i < 4 * lvl; ++i) c(' ');
+    uint32_t m = n;
+    for (int i = 0; i < 4 * lvl; ++i, ++m) {
+      if (m < cap) st_u8(p + m, ' ');
+      else ovf = true;
+    }
+    n = m;
   }
 };
 
@@ -597,11 +642,13 @@ struct Em {
           return;
         }
         // the comparison without its outer parentheses
-        Wr save = w;
+        const uint32_t start = w.n;
         node_expr(rid(c), 0);
-        uint32_t end = w.n;
-        if (w.on) {
-          for (uint32_t q = save.n; q + 2 < end; ++q) w.p[q] = w.p[q + 1];
+        const uint32_t end = w.n;
+        if (end <= w.cap) {
+          for (uint32_t q = start; q + 2 < end; ++q) st_u8(w.p + q, (char)ld_u8(w.p + q + 1));
+        } else {
+          w.ovf = true;  // the text is redone with room for all of it
         }
         w.n = end - 2;
         return;
@@ -735,7 +782,7 @@ struct LayoutCtx {
   }
 };
 
-__global__ void k_layout(Batch b, Item* __restrict__ items, const uint32_t* __restrict__ item_base,
+__global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ items, const uint32_t* __restrict__ item_base,
                          uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ scratch_all,
                          uint32_t* __restrict__ stk_all, const uint32_t* __restrict__ pbits, int write) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -864,14 +911,87 @@ __global__ void k_layout(Batch b, Item* __restrict__ items, const uint32_t* __re
   if (!write) item_cnt[k] = L.n;
 }
 
-__global__ void k_items(Batch b, const Item* __restrict__ items, uint32_t NI, uint32_t* __restrict__ item_len,
-                        const uint32_t* __restrict__ item_off, int write) {
+// Sub-items.  Every instruction that may print a statement (a variable
+// assignment of one of its four node slots, a store, inline asm) gets a rank
+// among such instructions of the batch; a block item is split into one
+// sub-item per such instruction of its range, every other item is one
+// sub-item, so that a long block is printed by many threads instead of one.
+__global__ void k_print_flag(const __grid_constant__ Batch b, uint32_t* __restrict__ flag) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi > b.I) return;
+  uint32_t f = 0;
+  if (gi < b.I && b.lblock_of[gi] != kNone) {
+    const size_t id = 4 * (size_t)gi;
+    const Node& n = b.nodes[id];
+    if (n.kind == N_OP && (n.op == O_UNKNOWN || op_store(n.op)) && (b.nflag[id] & 1)) f = 1;
+    for (int q = 0; q < 4; ++q)
+      if (b.var_of[id + q] >= 0) f = 1;
+  }
+  flag[gi] = f;
+}
+
+__global__ void k_print_list(uint32_t I, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ rank,
+                             uint32_t* __restrict__ list) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi < I && flag[gi]) list[rank[gi]] = gi;
+}
+
+__global__ void k_item_weight(const __grid_constant__ Batch b, const Item* __restrict__ items, uint32_t NI,
+                              const uint32_t* __restrict__ prank, uint32_t* __restrict__ weight) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NI) return;
+  Item it = items[i];
+  uint32_t w = 1;
+  if ((it.kl & 0xFF) == IT_BLOCK) {
+    const KHdr& K = b.kh[it.k];
+    const BlockRec& B = b.lblocks[K.first_lblock + it.a];
+    w = prank[K.first_instr + B.end] - prank[K.first_instr + B.first];
+  }
+  weight[i] = w;
+}
+
+// head of each non-empty item's sub-item range (the array is zeroed first; a
+// max scan then gives every sub-item its item)
+__global__ void k_sub_heads(const uint32_t* __restrict__ sub0, uint32_t NI, uint32_t* __restrict__ sub_item) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NI) return;
+  if (sub0[i + 1] > sub0[i]) sub_item[sub0[i]] = i;
+}
+
+// Emission of sub-items.  Staging mode (stage != null): sub-item t prints into
+// its own kEmitSlot-byte slot of `stage`, records its exact length, and
+// appends itself to ovf_list when the text did not fit.  Direct mode
+// (stage == null): sub-item list[t] prints straight into its final place in
+// the output (used for the sub-items that overflowed their slot).
+__global__ void __launch_bounds__(128)
+    k_items(const __grid_constant__ Batch b, const Item* __restrict__ items, const uint32_t* __restrict__ sub_item,
+            const uint32_t* __restrict__ sub0, const uint32_t* __restrict__ prank, const uint32_t* __restrict__ pinstr,
+            uint32_t N, const uint32_t* __restrict__ list, uint32_t* __restrict__ item_len,
+            const uint32_t* __restrict__ item_off, uint8_t* stage, uint32_t* __restrict__ ovf_list,
+            uint32_t* ovf_count, uint32_t lane_shift) {
+  // with lane_shift 5 one warp handles one sub-item (lane 0 works): no
+  // divergence between statements inside a warp
+  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt & ((1u << lane_shift) - 1u)) return;
+  const uint32_t t = gt >> lane_shift;
+  if (t >= N) return;
+  const uint32_t sidx = list ? list[t] : t;
+  const uint32_t i = sub_item[sidx];
+  const uint32_t j = sidx - sub0[i];  // position inside the item
   Item it = items[i];
   uint32_t kind = it.kl & 0xFF, lvl = it.kl >> 8;
   uint32_t k = it.k;
   KHdr& K = b.kh[k];
+  uint32_t q_stmt = 0;
+  if (kind == IT_BLOCK) {
+    const BlockRec& B = b.lblocks[K.first_lblock + it.a];
+    const uint32_t gi = pinstr[prank[K.first_instr + B.first] + j];
+    q_stmt = gi - K.first_instr;
+    if (b.lblock_of[gi] != it.a) {
+      if (stage) item_len[sidx] = 0;
+      return;
+    }
+  }
   const ArgRec* A = b.args + (size_t)k * kMaxArgs;
   Em em;
   em.v = make_view(b, K, k);
@@ -886,7 +1006,8 @@ __global__ void k_items(Batch b, const Item* __restrict__ items, uint32_t NI, ui
   em.vt = b.var_type + nb + K.state_off;
   em.scratch = nullptr;
   em.scap = 0;
-  em.w = Wr{write ? b.out + item_off[i] : nullptr, 0, write != 0};
+  if (stage) em.w = Wr{stage + (size_t)sidx * kEmitSlot, 0, kEmitSlot, false};
+  else em.w = Wr{b.out + item_off[sidx], 0, item_len[sidx], false};
   em.partial = false;
   em.deep = false;
   Wr& w = em.w;
@@ -913,12 +1034,7 @@ __global__ void k_items(Batch b, const Item* __restrict__ items, uint32_t NI, ui
         w.s(";\n");
       }
       break;
-    case IT_BLOCK: {
-      const BlockRec& B = b.lblocks[K.first_lblock + it.a];
-      for (uint32_t q = B.first; q < B.end; ++q)
-        if (b.lblock_of[K.first_instr + q] == it.a) em.instr_stmts(q, (int)lvl);
-      break;
-    }
+    case IT_BLOCK: em.instr_stmts(q_stmt, (int)lvl); break;
     case IT_COPY: em.one_copy(it.a >> 10, it.a & 0x3FF, it.b, (int)lvl); break;
     case IT_IF:
       w.indent((int)lvl);
@@ -942,25 +1058,27 @@ __global__ void k_items(Batch b, const Item* __restrict__ items, uint32_t NI, ui
       break;
     }
   }
-  if (!write) {
-    item_len[i] = w.n;
+  if (stage) {
+    item_len[sidx] = w.n;
+    if (w.ovf) ovf_list[atomicAdd(ovf_count, 1u)] = sidx;
     if (em.partial) atomicOr(&K.partial, 1u);
   }
   if (em.deep) atomicOr(b.err, ERR_STACK);
 }
 
-__global__ void k_kernel_status(Batch b, const uint32_t* __restrict__ item_base, const uint32_t* __restrict__ item_off) {
+__global__ void k_kernel_status(const __grid_constant__ Batch b, const uint32_t* __restrict__ item_base, const uint32_t* __restrict__ sub0,
+                                const uint32_t* __restrict__ item_off) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) K.status = ST_PARSE_ERROR;
   else if (K.n_lblock && K.root == kNone) K.status = ST_PARTIAL;
   else K.status = K.partial ? ST_PARTIAL : ST_OK;
-  b.kout_off[k] = item_off[item_base[k]];
+  b.kout_off[k] = item_off[sub0[item_base[k]]];
 }
 
 // per file: output offset and worst status of its kernels
-__global__ void k_file_out(Batch b, uint32_t total) {
+__global__ void k_file_out(const __grid_constant__ Batch b, uint32_t total) {
   uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f > b.F) return;
   uint32_t lo = 0, hi = b.K;  // first kernel with file >= f
@@ -983,16 +1101,73 @@ void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* i
   ++launch_counter();
 }
 
-void launch_items(Batch& b, const Item* items, uint32_t NI, uint32_t* item_len, const uint32_t* item_off, int write,
-                  cudaStream_t s) {
-  if (!NI) return;
-  k_items<<<(NI + 127) / 128, 128, 0, s>>>(b, items, NI, item_len, item_off, write);
+void launch_print_list(Batch& b, uint32_t* flag, const uint32_t* rank, uint32_t* list, int phase, cudaStream_t s) {
+  if (phase == 0) {
+    k_print_flag<<<(b.I + 1 + 255) / 256, 256, 0, s>>>(b, flag);
+  } else {
+    if (!b.I) return;
+    k_print_list<<<(b.I + 255) / 256, 256, 0, s>>>(b.I, flag, rank, list);
+  }
   ++launch_counter();
 }
 
-void launch_finish(Batch& b, const uint32_t* item_base, const uint32_t* item_off, uint32_t total, cudaStream_t s) {
+void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* prank, uint32_t* weight,
+                     const uint32_t* sub0, uint32_t* sub_item, uint32_t NS2, int phase, cudaStream_t s) {
+  if (!NI) return;
+  if (phase == 0) {
+    k_item_weight<<<(NI + 255) / 256, 256, 0, s>>>(b, items, NI, prank, weight);
+    ++launch_counter();
+  } else {
+    cudaMemsetAsync(sub_item, 0, sizeof(uint32_t) * ((size_t)NS2 + 1), s);
+    k_sub_heads<<<(NI + 255) / 256, 256, 0, s>>>(sub0, NI, sub_item);
+    ++launch_counter();
+  }
+}
+
+// staged sub-item texts that fit their slot -> final place; a warp moves 32
+// consecutive sub-items, its lanes copying the bytes of one sub-item at a time
+__global__ void __launch_bounds__(256)
+    k_compact(const uint8_t* __restrict__ stage, const uint32_t* __restrict__ item_len,
+              const uint32_t* __restrict__ item_off, uint32_t N, uint8_t* __restrict__ out) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t s0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+  if (s0 >= N) return;
+  const uint32_t mine = s0 + lane;
+  const uint32_t len = mine < N ? item_len[mine] : 0;
+  const uint32_t off = mine < N ? item_off[mine] : 0;
+  unsigned todo = __ballot_sync(0xFFFFFFFFu, len > 0 && len <= kEmitSlot);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const uint32_t l = __shfl_sync(0xFFFFFFFFu, len, src);
+    const uint32_t o = __shfl_sync(0xFFFFFFFFu, off, src);
+    const uint8_t* from = stage + (size_t)(s0 + src) * kEmitSlot;
+    for (uint32_t q = lane; q < l; q += 32) out[o + q] = from[q];
+  }
+}
+
+void launch_items(Batch& b, const Item* items, const uint32_t* sub_item, const uint32_t* sub0, const uint32_t* prank,
+                  const uint32_t* pinstr, uint32_t N, const uint32_t* list, uint32_t* item_len,
+                  const uint32_t* item_off, uint8_t* stage, uint32_t* ovf_list, uint32_t* ovf_count,
+                  uint32_t lane_shift, cudaStream_t s) {
+  if (!N) return;
+  const uint64_t threads = (uint64_t)N << lane_shift;
+  k_items<<<(uint32_t)((threads + 127) / 128), 128, 0, s>>>(b, items, sub_item, sub0, prank, pinstr, N, list, item_len,
+                                                          item_off, stage, ovf_list, ovf_count, lane_shift);
+  ++launch_counter();
+}
+
+void launch_compact(const uint8_t* stage, const uint32_t* item_len, const uint32_t* item_off, uint32_t N,
+                    uint8_t* out, cudaStream_t s) {
+  if (!N) return;
+  k_compact<<<(N + 255) / 256, 256, 0, s>>>(stage, item_len, item_off, N, out);
+  ++launch_counter();
+}
+
+void launch_finish(Batch& b, const uint32_t* item_base, const uint32_t* sub0, const uint32_t* item_off,
+                   uint32_t total, cudaStream_t s) {
   if (b.K) {
-    k_kernel_status<<<(b.K + 127) / 128, 128, 0, s>>>(b, item_base, item_off);
+    k_kernel_status<<<(b.K + 127) / 128, 128, 0, s>>>(b, item_base, sub0, item_off);
     ++launch_counter();
   }
   k_file_out<<<(b.F + 1 + 127) / 128, 128, 0, s>>>(b, total);

@@ -185,7 +185,7 @@ struct Red {
   }
 };
 
-__global__ void k_regions(Batch b, uint32_t* __restrict__ seen_all, uint32_t* __restrict__ stk_all,
+__global__ void k_regions(const __grid_constant__ Batch b, uint32_t* __restrict__ seen_all, uint32_t* __restrict__ stk_all,
                           uint8_t* __restrict__ alive_all, uint8_t* __restrict__ cond_all) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
