@@ -7,6 +7,13 @@
 namespace gd {
 
 // kernel view: node / argument arrays of one kernel
+// Inlining of the recursive pattern matchers: left to the compiler by
+// default; a translation unit that calls them from many places (the printer)
+// defines GD_MATCH_INLINE as __noinline__ before including this header.
+#ifndef GD_MATCH_INLINE
+#define GD_MATCH_INLINE
+#endif
+
 struct KView {
   const Batch* b;
   const KHdr* K;
@@ -44,7 +51,7 @@ __device__ __forceinline__ bool is_copy_node(const Node& n) {
 
 // a copy is the value it copies; the halves of a split pair are its sources;
 // a pair of the low and high part of one 64-bit value is that value
-static __device__ uint32_t fwd_d(const KView& v, uint32_t r, int depth) {
+static __device__ GD_MATCH_INLINE uint32_t fwd_d(const KView& v, uint32_t r, int depth) {
   for (int step = 0; step < 512 && depth < 64; ++step) {
     if (r == kTop) return kUndef;
     if (!r_node(r)) return r;
@@ -85,7 +92,7 @@ __device__ __forceinline__ int ilog2_exact(uint32_t x) {
 
 static __device__ Cls classify(const KView& v, uint32_t r);
 
-static __device__ Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide) {
+static __device__ GD_MATCH_INLINE Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide) {
   Cls none{K_NONE, 0};
   Cls base = classify(v, nsrc(v, n, 0));
   if (base.c != K_KARG || (n.cval & 7u)) return none;
@@ -117,7 +124,7 @@ __device__ __forceinline__ int64_t const_src(const KView& v, const Node& n, int 
   return const_of_f(v, nsrc(v, n, q));
 }
 
-static __device__ Cls classify(const KView& v, uint32_t r) {
+static __device__ GD_MATCH_INLINE Cls classify(const KView& v, uint32_t r) {
   Cls none{K_NONE, 0};
   if (r == kUndef || r == kTop) return Cls{K_UNDEF, 0};
   if (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) return Cls{v.cc[rid(r)], v.ck[rid(r)]};
@@ -186,7 +193,7 @@ struct Mem {
   uint32_t idx;  // kTop = constant 0
 };
 
-static __device__ Mem match_addr(const KView& v, uint32_t addr, uint32_t width) {
+static __device__ GD_MATCH_INLINE Mem match_addr(const KView& v, uint32_t addr, uint32_t width) {
   Mem m{false, kNone, kTop};
   Cls c = classify(v, addr);
   if (c.c == K_ARGPTR) {

@@ -16,6 +16,9 @@
 // recursively, with a depth guard) and records the exact length, a scan
 // places every sub-item, a warp-per-32 copy moves the staged bytes, and the
 // few sub-items longer than a slot are printed again straight into place.
+// The printer calls the pattern matchers from many places; inlining them
+// there made the emission kernel megabytes long (instruction-cache bound).
+#define GD_MATCH_INLINE __noinline__
 #include "k_analysis.cuh"
 
 namespace gd {
@@ -44,7 +47,7 @@ struct Wr {
     else ovf = true;
     ++n;
   }
-  __device__ void s(const char* z) {
+  __device__ __noinline__ void s(const char* z) {
     uint32_t m = n;
     for (; *z; ++z, ++m) {
       if (m < cap) st_u8(p + m, *z);
@@ -52,7 +55,7 @@ struct Wr {
     }
     n = m;
   }
-  __device__ void mem(const uint8_t* a, uint32_t len) {
+  __device__ __noinline__ void mem(const uint8_t* a, uint32_t len) {
     uint32_t m = n;
     for (uint32_t i = 0; i < len; ++i, ++m) {
       if (m < cap) st_u8(p + m, (char)a[i]);
@@ -60,7 +63,7 @@ struct Wr {
     }
     n = m;
   }
-  __device__ void u64(uint64_t v) {
+  __device__ __noinline__ void u64(uint64_t v) {
     char t[20];
     int k = 0;
     do {
@@ -86,7 +89,7 @@ struct Wr {
       u64((uint64_t)v);
     }
   }
-  __device__ void indent(int lvl) {
+  __device__ __noinline__ void indent(int lvl) {
     uint32_t m = n;
     for (int i = 0; i < 4 * lvl; ++i, ++m) {
       if (m < cap) st_u8(p + m, ' ');
@@ -111,7 +114,7 @@ __device__ __forceinline__ bool tint(uint8_t t) { return t == TY_INT || t == TY_
 __device__ __forceinline__ int twidth(uint8_t t) { return ty64(t) ? 64 : 32; }
 
 // exact short decimal when the value has few binary fraction digits, else as_float/as_double
-__device__ void float_lit(Wr& w, uint64_t bits, bool dbl) {
+__device__ __noinline__ void float_lit(Wr& w, uint64_t bits, bool dbl) {
   int mbits = dbl ? 52 : 23, ebits = dbl ? 11 : 8, bias = dbl ? 1023 : 127;
   uint64_t sign = bits >> (mbits + ebits);
   uint64_t ex = (bits >> mbits) & ((1ull << ebits) - 1);
@@ -161,7 +164,7 @@ __device__ void float_lit(Wr& w, uint64_t bits, bool dbl) {
   if (!dbl) w.c('f');
 }
 
-__device__ void lit32(Wr& w, uint32_t bits, uint8_t want) {
+__device__ __noinline__ void lit32(Wr& w, uint32_t bits, uint8_t want) {
   if (want == TY_INT) {
     int32_t v = (int32_t)bits;
     if (v == INT32_MIN) w.s("(-2147483647 - 1)");
@@ -173,7 +176,7 @@ __device__ void lit32(Wr& w, uint32_t bits, uint8_t want) {
     w.c('u');
   }
 }
-__device__ void lit64(Wr& w, uint64_t bits, uint8_t want) {
+__device__ __noinline__ void lit64(Wr& w, uint64_t bits, uint8_t want) {
   if (want == TY_LONG) {
     int64_t v = (int64_t)bits;
     if (v == INT64_MIN) w.s("(-9223372036854775807L - 1L)");
@@ -211,7 +214,7 @@ struct Em {
   }
 
   // ---- conversions -----------------------------------------------------------
-  __device__ void conv_open(uint8_t from, uint8_t want) {
+  __device__ __noinline__ void conv_open(uint8_t from, uint8_t want) {
     if (want == TY_NONE || from == want) return;
     if (tint(from) && tint(want)) {
       w.c('(');
@@ -227,19 +230,19 @@ struct Em {
       w.c(')');
     }
   }
-  __device__ void conv_close(uint8_t from, uint8_t want) {
+  __device__ __noinline__ void conv_close(uint8_t from, uint8_t want) {
     if (want == TY_NONE || from == want) return;
     if (!(tint(from) && tint(want)) && twidth(from) == twidth(want)) w.c(')');
   }
 
   // ---- types of expressions (computed before printing) ------------------------
-  __device__ uint8_t mem_elem(const Node& n, uint32_t width) {
+  __device__ __noinline__ uint8_t mem_elem(const Node& n, uint32_t width) {
     Mem m = mem_of(v, (uint32_t)(&n - v.N));
     if (m.ok) return v.A[m.arg].elem;
     return width == 8 ? TY_ULONG : TY_UINT;
   }
 
-  __device__ uint8_t node_expr_type(uint32_t id) {
+  __device__ __noinline__ uint8_t node_expr_type(uint32_t id) {
     const Node& n = v.node(id);
     uint8_t T = NT(id);
     if (n.kind == N_PAIR) return TY_ULONG;
@@ -262,7 +265,7 @@ struct Em {
     return T == TY_ULONG ? TY_ULONG : TY_UINT;
   }
 
-  __device__ uint8_t expr_type(uint32_t r, uint8_t want) {
+  __device__ __noinline__ uint8_t expr_type(uint32_t r, uint8_t want) {
     r = fwd(v, r);
     if (r_phi(r)) {
       int32_t x = phivar(r);
@@ -290,7 +293,7 @@ struct Em {
   }
 
   // ---- printing -------------------------------------------------------------
-  __device__ void E(uint32_t r, uint8_t want, int d) {
+  __device__ __noinline__ void E(uint32_t r, uint8_t want, int d) {
     uint8_t t = expr_type(r, want);
     conv_open(t, want);
     ex(r, want, d);
@@ -299,7 +302,7 @@ struct Em {
 
   __device__ void name(uint32_t slot) { w.mem(b->text + v.A[slot].name_off, v.A[slot].name_len); }
 
-  __device__ void ex(uint32_t r, uint8_t want, int d) {
+  __device__ __noinline__ void ex(uint32_t r, uint8_t want, int d) {
     if (d > 200) {
       deep = true;
       w.s("0u");
@@ -378,7 +381,7 @@ struct Em {
   }
 
   __device__ void S(const Node& n, int q, uint8_t t, int d) { E(nsrc(v, n, q), t, d); }
-  __device__ void binop(const Node& n, const char* sym, uint8_t ot, int d) {
+  __device__ __noinline__ void binop(const Node& n, const char* sym, uint8_t ot, int d) {
     w.c('(');
     S(n, 0, ot, d);
     w.c(' ');
@@ -387,7 +390,7 @@ struct Em {
     S(n, 1, ot, d);
     w.c(')');
   }
-  __device__ void shamt(uint32_t f, uint32_t mask, int d) {
+  __device__ __noinline__ void shamt(uint32_t f, uint32_t mask, int d) {
     if (r_node(f) && rpart(f) == PART_ENTIRE && v.node(rid(f)).kind == N_CONST) {
       w.u64(v.node(rid(f)).cval & mask);
       return;
@@ -398,7 +401,7 @@ struct Em {
     w.u64(mask);
     w.s("u)");
   }
-  __device__ void call3(const char* fn, const Node& n, int k, uint8_t t, int d) {
+  __device__ __noinline__ void call3(const char* fn, const Node& n, int k, uint8_t t, int d) {
     w.s(fn);
     w.c('(');
     for (int q = 0; q < k; ++q) {
@@ -407,11 +410,11 @@ struct Em {
     }
     w.c(')');
   }
-  __device__ void cast1(const char* pre, const Node& n, uint8_t t, int d) {
+  __device__ __noinline__ void cast1(const char* pre, const Node& n, uint8_t t, int d) {
     w.s(pre);
     S(n, 0, t, d);
   }
-  __device__ void shift(const Node& n, int vq, int sq, uint8_t t, const char* sym, uint32_t mask, int d) {
+  __device__ __noinline__ void shift(const Node& n, int vq, int sq, uint8_t t, const char* sym, uint32_t mask, int d) {
     w.c('(');
     S(n, vq, t, d);
     w.c(' ');
@@ -421,7 +424,7 @@ struct Em {
     w.c(')');
   }
 
-  __device__ void memref(const Node& n, uint32_t width, int d) {
+  __device__ __noinline__ void memref(const Node& n, uint32_t width, int d) {
     Mem m = mem_of(v, (uint32_t)(&n - v.N));
     if (m.ok) {
       name(m.arg);
@@ -439,7 +442,7 @@ struct Em {
   }
 
   // a node's own expression (ignoring its variable)
-  __device__ void node_expr(uint32_t id, int d) {
+  __device__ __noinline__ void node_expr(uint32_t id, int d) {
     const Node& n = v.node(id);
     uint8_t T = NT(id);
     if (n.kind == N_PAIR) {
@@ -516,7 +519,7 @@ struct Em {
 
   // ---- statements ---------------------------------------------------------------
   // statements of instruction i: its operand-slot variables, then its result
-  __device__ void instr_stmts(uint32_t i, int lvl) {
+  __device__ __noinline__ void instr_stmts(uint32_t i, int lvl) {
     {
       uint32_t gi = K->first_instr + i;
       const int order[4] = {1, 2, 3, 0};
@@ -564,7 +567,7 @@ struct Em {
   }
 
   // one assignment of the join version of register reg at block s along p -> s
-  __device__ void one_copy(uint32_t s, uint32_t reg, uint32_t p, int lvl) {
+  __device__ __noinline__ void one_copy(uint32_t s, uint32_t reg, uint32_t p, int lvl) {
     uint32_t dst = phiref(s, reg);
     uint32_t o = b->st_out[K->state_off + (size_t)p * K->R + reg];
     uint32_t src = fwd(v, o == kTop ? kUndef : o);
@@ -627,7 +630,7 @@ struct Em {
   }
 
   // condition under which block t's terminator goes to block dst
-  __device__ void cond_to(uint32_t t, uint32_t dst) {
+  __device__ __noinline__ void cond_to(uint32_t t, uint32_t dst) {
     const BlockRec& B = b->lblocks[K->first_lblock + t];
     uint32_t i = b->lterm[K->first_lblock + t];
     uint32_t c = nsrc(v, v.node(4 * i), 0);
