@@ -253,10 +253,10 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ids = dec.submit_batch(files)
-        outs = [dec.fetch_opencl(j) for j in ids]
+        raw, offs, sts = dec.fetch_batch_raw(ids)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        d2h = sum(len(o[0]) for o in outs) + 12 * n_files
+        d2h = len(raw) + 12 * n_files
     e2e_val = total_instr * world / (statistics.median(e2e_ms) / 1e3) if e2e_ms else None
 
     peaks, src = measured_peaks()

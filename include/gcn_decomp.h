@@ -18,9 +18,16 @@
  *    before returning (host inputs) or reads it on the given stream (device
  *    inputs) and never frees caller memory.
  *  - Text is bytes, not NUL-terminated; lines end with '\n'.
- *  - One handle owns its device memory and its CUDA stream.  Calls on one
- *    handle are serialised by an internal mutex; different handles are
- *    independent.
+ *  - One handle owns its device memory, its CUDA streams and its worker
+ *    threads.  Every call is thread-safe; different handles are independent.
+ *
+ * Jobs (submit_batch / fetch_*) are served by continuous batching: admitted
+ * jobs queue on the host; each of the handle's worker lanes (a host thread
+ * with its own CUDA stream) takes everything queued when it becomes free, up
+ * to 64 MiB of text, and runs it as one batch, so jobs that arrive while
+ * others are on the GPU start as soon as a lane frees up, and the batches of
+ * different lanes overlap on the device.  A job's result does not depend on
+ * which jobs share its batch.
  */
 #ifndef GCN_DECOMP_H
 #define GCN_DECOMP_H
@@ -64,22 +71,51 @@ typedef struct {
 int gcn_decomp_create(const gcn_decomp_config *cfg, gcn_decomp_t **out);
 
 /* Submit n jobs; job i is one disassembly file text[i][0..len[i]).  The
- * library copies the texts (a '\n' is appended when the last line lacks one),
- * decompiles them on the device and keeps the results resident until fetched.
- * job_ids[i] receives the id of job i; *n_admitted the number of jobs taken
- * (jobs are admitted in order while the memory budget and slots allow).
- * Errors: GCN_EINVAL, GCN_EAGAIN (none admitted), GCN_ENOMEM, GCN_ECUDA. */
+ * library copies the texts before returning (a '\n' is appended when the last
+ * line lacks one) and queues them; the call does not wait for the GPU.
+ * job_ids[i] receives the id of job i; *n_admitted the number of jobs taken:
+ * jobs are admitted in order while a job slot is free (max_slots) and the
+ * estimated device memory of admitted, unfetched jobs (48 bytes per input
+ * byte + 1 MiB each) stays within mem_budget_bytes; the first job is always
+ * admitted when nothing else is.  A job's slot and budget share are given
+ * back when it is fetched.
+ * Errors: GCN_EINVAL, GCN_EAGAIN (none admitted: no slot or budget). */
 int gcn_decomp_submit_batch(gcn_decomp_t *h, const char *const *text, const size_t *len, size_t n,
                             uint64_t *job_ids, size_t *n_admitted);
 
 /* Copy the OpenCL text of a job (its kernels joined by a blank line) into
  * buf[0..cap).  buf == NULL only reports the size.  *len_out = bytes of the
  * text; *status_out = worst GCN_ST_* of the job's kernels (either may be
- * NULL).  On success with buf != NULL the job's slot is released and its id
- * becomes unknown.  Errors: GCN_ENOJOB, GCN_EINVAL (cap too small: nothing is
- * copied and the job stays), GCN_EAGAIN (not finished and no GCN_WAIT). */
+ * NULL).  With GCN_WAIT the call blocks until the job is done.  On success
+ * with buf != NULL the job's slot is released and its id becomes unknown.
+ * Errors: GCN_ENOJOB, GCN_EINVAL (cap too small: nothing is copied and the
+ * job stays), GCN_EAGAIN (not finished and no GCN_WAIT), or the error of the
+ * batch that ran the job (GCN_ENOMEM, GCN_ECUDA; the job is released). */
 int gcn_decomp_fetch_opencl(gcn_decomp_t *h, uint64_t job_id, char *buf, size_t cap, size_t *len_out,
                             int *status_out, uint32_t flags);
+
+/* Results of n jobs at once: off_out[0..n] (u64) receives the boundaries
+ * of their texts placed back to back in job_ids order, status_out[0..n) (i32,
+ * may be NULL) their worst status.  buf == NULL only fills off_out and
+ * status_out; otherwise buf[0..cap) receives the texts and all n jobs are
+ * released.  With GCN_WAIT the call blocks until every job is done.
+ * Errors: as gcn_decomp_fetch_opencl for the first job that has one (nothing
+ * is copied or released then). */
+int gcn_decomp_fetch_batch(gcn_decomp_t *h, const uint64_t *job_ids, size_t n, char *buf, size_t cap,
+                           uint64_t *off_out, int32_t *status_out, uint32_t flags);
+
+/* Ids of finished jobs not yet reported by an earlier poll (and not yet
+ * fetched), in completion order: up to cap of them into job_ids, their
+ * number into *n_out.  When none is ready the call waits up to timeout_ms
+ * (0 = do not wait, negative = no limit).  Errors: GCN_EINVAL. */
+int gcn_decomp_poll(gcn_decomp_t *h, uint64_t *job_ids, size_t cap, size_t *n_out, int timeout_ms);
+
+/* State and timestamps of a job not yet fetched: info[0..4] = state (0
+ * queued, 1 running, 2 done), submit time, batch start time, finish time
+ * (CLOCK_MONOTONIC nanoseconds, 0 = not yet), and 1 when its IR is still
+ * resident on the device.  Returns the number of values written (<= cap).
+ * Errors: GCN_ENOJOB, GCN_EINVAL. */
+int gcn_decomp_job_info(gcn_decomp_t *h, uint64_t job_id, uint64_t *info, int cap);
 
 /* Intermediate arrays of a job, for parity checks: `which` selects
  *   0 instruction records (32 bytes each: u16 op, u8 nops, u8 flags, u32 imm,
@@ -89,10 +125,14 @@ int gcn_decomp_fetch_opencl(gcn_decomp_t *h, uint64_t job_id, char *buf, size_t 
  *   4 logical blocks (as 2),  5 per-kernel configuration header (8 x u32:
  *     dims, cws x/y/z, sgprs, vgprs, useargs, user args)
  * concatenated over the job's kernels in file order.  Sizes as for fetch.
- * Does not release the job.  Errors: GCN_ENOJOB, GCN_EINVAL. */
+ * Waits for the job; does not release it.  The IR stays on the device until
+ * the job is fetched, unless the engine holding it is needed for a newer
+ * batch (then GCN_ENOJOB).  Errors: GCN_ENOJOB, GCN_EINVAL. */
 int gcn_decomp_fetch_ir(gcn_decomp_t *h, uint64_t job_id, int which, void *buf, size_t cap, size_t *len_out);
 
-/* Wait for in-flight work and free every resource of the handle (NULL is a no-op). */
+/* Stop the worker lanes (a batch already on the GPU finishes; queued jobs are
+ * dropped), wait for in-flight work and free every resource of the handle
+ * (NULL is a no-op). */
 void gcn_decomp_destroy(gcn_decomp_t *h);
 
 /* Device-resident batch: decompile n_files files already in device memory,
@@ -120,18 +160,19 @@ int gcn_decomp_result_device(gcn_decomp_t *h, const uint8_t **d_out, const uint6
 int gcn_decomp_result_copy(gcn_decomp_t *h, uint64_t f0, uint64_t f1, void *buf, size_t cap, uint64_t *off_out,
                            int32_t *status_out);
 
-/* Per-stage device times of the last run (milliseconds, CUDA events on the
- * run's stream), stage names in *names (static strings).  Returns the number
+/* Per-stage device times of the last run of either form (milliseconds, CUDA
+ * events on the run's stream), stage names in *names (static strings).  Returns the number
  * of stages (<= cap) or a negative code. */
 int gcn_decomp_stage_times(gcn_decomp_t *h, float *ms, const char **names, int cap);
 
-/* Sizes of the last pipeline run: out[0..7] = lines, kernels, instructions,
- * labels, physical blocks, logical blocks, register-state words, output bytes.
+/* Sizes of the last pipeline run (either form): out[0..8] = lines, kernels,
+ * instructions, labels, physical blocks, logical blocks, register-state
+ * words, output bytes, device bytes held by the engine that ran it.
  * Returns the number of values written (<= cap) or a negative code. */
 int gcn_decomp_run_stats(gcn_decomp_t *h, uint64_t *out, int cap);
 
 /* Number of CUDA kernels the library launched for the last pipeline run
- * (run_device or submit_batch); 0 before the first run. */
+ * (either form); 0 before the first run. */
 uint64_t gcn_decomp_launches(gcn_decomp_t *h);
 
 /* Line tokenisation without any allocation (the paper has no counterpart:

@@ -106,6 +106,10 @@ def lib():
             L.gcn_decomp_launches.argtypes = [vp]
             L.gcn_decomp_launches.restype = u64
             L.gcn_decomp_line_starts_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
+            L.gcn_decomp_fetch_batch.argtypes = [vp, ctypes.POINTER(u64), sz, vp, sz, ctypes.POINTER(u64),
+                                                 ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32]
+            L.gcn_decomp_poll.argtypes = [vp, ctypes.POINTER(u64), sz, ctypes.POINTER(sz), i32]
+            L.gcn_decomp_job_info.argtypes = [vp, u64, ctypes.POINTER(u64), i32]
             _lib = L
     return _lib
 
@@ -123,7 +127,7 @@ def _ck(rc: int, what: str):
 
 
 class Decompiler:
-    """One handle: a CUDA stream plus device memory on ``device``."""
+    """One handle on ``device``: device memory, CUDA streams and the worker lanes of the job service."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_slots: int = 0):
         self._h = ctypes.c_void_p()
@@ -174,9 +178,50 @@ class Decompiler:
         _ck(lib().gcn_decomp_fetch_ir(self._h, job, which, buf, n.value, ctypes.byref(n)), "gcn_decomp_fetch_ir")
         return buf.raw[: n.value]
 
+    def fetch_batch(self, ids: list[int], wait: bool = True) -> tuple[list[str], list[int]]:
+        """Texts and statuses of jobs `ids` (one call; the jobs are released)."""
+        n = len(ids)
+        arr = (ctypes.c_uint64 * max(n, 1))(*ids)
+        offs = (ctypes.c_uint64 * (n + 1))()
+        st = (ctypes.c_int32 * max(n, 1))()
+        fl = 1 if wait else 0
+        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, None, 0, offs, st, fl), "gcn_decomp_fetch_batch")
+        buf = ctypes.create_string_buffer(max(int(offs[n]), 1))
+        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, buf, int(offs[n]), offs, st, fl), "gcn_decomp_fetch_batch")
+        raw = buf.raw
+        return [raw[offs[i]:offs[i + 1]].decode() for i in range(n)], [int(st[i]) for i in range(n)]
+
+    def fetch_batch_raw(self, ids: list[int]) -> tuple[bytes, list[int], list[int]]:
+        """Like fetch_batch, without splitting: (texts back to back, offsets, statuses)."""
+        n = len(ids)
+        arr = (ctypes.c_uint64 * max(n, 1))(*ids)
+        offs = (ctypes.c_uint64 * (n + 1))()
+        st = (ctypes.c_int32 * max(n, 1))()
+        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, None, 0, offs, st, 1), "gcn_decomp_fetch_batch")
+        buf = ctypes.create_string_buffer(max(int(offs[n]), 1))
+        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, buf, int(offs[n]), offs, st, 1), "gcn_decomp_fetch_batch")
+        return buf.raw[: int(offs[n])], list(offs), list(st)
+
+    def poll(self, cap: int = 4096, timeout_ms: int = 0) -> list[int]:
+        """Finished jobs not reported before (waits up to timeout_ms for one)."""
+        ids = (ctypes.c_uint64 * cap)()
+        got = ctypes.c_size_t()
+        _ck(lib().gcn_decomp_poll(self._h, ids, cap, ctypes.byref(got), timeout_ms), "gcn_decomp_poll")
+        return list(ids[: got.value])
+
+    def job_info(self, job: int) -> dict[str, int]:
+        """State (0 queued, 1 running, 2 done), CLOCK_MONOTONIC ns timestamps, IR residency."""
+        v = (ctypes.c_uint64 * 5)()
+        n = lib().gcn_decomp_job_info(self._h, job, v, 5)
+        if n < 0:
+            raise GcnDecompError(n, "gcn_decomp_job_info")
+        keys = ["state", "t_submit", "t_start", "t_done", "ir_resident"]
+        return {keys[i]: int(v[i]) for i in range(n)}
+
     def decompile(self, texts: list[bytes]) -> list[tuple[str, int]]:
         ids = self.submit_batch(texts)
-        return [self.fetch_opencl(j) for j in ids]
+        outs, st = self.fetch_batch(ids)
+        return list(zip(outs, st))
 
     # ---- device-buffer API -----------------------------------------------------
     def run_device(self, text_ptr: int, text_len: int, off_ptr: int, n_files: int, stream: int = 0):
@@ -191,10 +236,12 @@ class Decompiler:
         return o.value, oo.value, st.value, nb.value
 
     def run_stats(self) -> dict[str, int]:
-        """Sizes of the last run (lines, kernels, instructions, labels, blocks, state words, output bytes)."""
-        v = (ctypes.c_uint64 * 8)()
-        n = lib().gcn_decomp_run_stats(self._h, v, 8)
-        keys = ["lines", "kernels", "instrs", "labels", "pblocks", "lblocks", "state_words", "out_bytes"]
+        """Sizes of the last run (lines, kernels, instructions, labels, blocks, state words, output and
+        device bytes)."""
+        v = (ctypes.c_uint64 * 9)()
+        n = lib().gcn_decomp_run_stats(self._h, v, 9)
+        keys = ["lines", "kernels", "instrs", "labels", "pblocks", "lblocks", "state_words", "out_bytes",
+                "device_bytes"]
         return {keys[i]: int(v[i]) for i in range(max(n, 0))}
 
     def launches(self) -> int:

@@ -1,20 +1,41 @@
-// capi.cu — host orchestration of the CUDA stages and the C ABI of gcn_decomp.h.
+// capi.cu — host runtime of the CUDA stages and the C ABI of gcn_decomp.h.
 //
-// A handle owns one CUDA stream and a grow-only workspace of device arrays.
-// One pipeline run takes a batch of files that is resident in device memory
-// and executes the stages in order: S1 newline scan, S2 row segmentation,
-// S3 configuration, S4 decoding, S5 physical CFG, S6 logical CFG, S7/S8
-// dataflow, S9-S11 analysis, S12 regions, S13 emission.  The host reads back
-// four small counters between stages (lines, kernels/instructions, blocks,
-// output bytes) to size the next arrays; everything else stays on the device.
+// An Engine is one execution context of the pipeline: a grow-only workspace of
+// device arrays, stage events and pinned counters.  One pipeline run takes a
+// batch of files resident in device memory and executes the stages in order:
+// S1 newline scan, S2 row segmentation, S3 configuration, S4 decoding, S5
+// physical CFG, S6 logical CFG, S7/S8 dataflow, S9-S11 analysis, S12 regions,
+// S13 emission.  The host reads back a few counters between stages (lines,
+// kernels/instructions, blocks, output bytes) to size the next arrays;
+// everything else stays on the device.
+//
+// A handle runs two kinds of work:
+//  - the device-resident form (run_device): one engine on the handle's
+//    stream, input and output in device memory;
+//  - jobs (submit_batch / fetch_*): a continuous-batching service.  Jobs are
+//    admitted under the slot limit and the device-memory budget and queued;
+//    each worker lane (a host thread with its own CUDA stream and pinned
+//    staging buffers) takes everything queued when it becomes free (up to a
+//    batch limit), stages it, runs the pipeline on an engine of a small pool
+//    and publishes the results, so batches of different lanes overlap on the
+//    device.  A finished batch keeps its engine (and so its IR) until all its
+//    jobs are fetched, unless the pool needs the engine back, in which case
+//    the IR of the oldest finished batch is dropped (its texts stay
+//    fetchable).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/gcn_decomp.h"
@@ -43,7 +64,8 @@ struct Workspace {
   };
   std::map<std::string, Buf> bufs;
   size_t total = 0;
-  uint64_t budget = 0;
+  uint64_t budget = 0;                         // device bytes all workspaces of a handle may hold (0 = no limit)
+  std::atomic<uint64_t>* pool = nullptr;       // bytes held by all workspaces of the handle
   template <class T>
   T* get(const char* name, size_t n) {
     size_t bytes = std::max<size_t>(n * sizeof(T), 256);
@@ -52,11 +74,12 @@ struct Workspace {
       if (b.p) {
         cudaFree(b.p);
         total -= b.cap;
+        if (pool) *pool -= b.cap;
         b.p = nullptr;
         b.cap = 0;
       }
       size_t want = bytes + bytes / 8;
-      if (budget && total + want > budget) {
+      if (budget && pool && *pool + want > budget) {
         set_err(std::string("memory budget exceeded allocating ") + name);
         throw GCN_ENOMEM;
       }
@@ -67,6 +90,7 @@ struct Workspace {
       }
       b.cap = want;
       total += want;
+      if (pool) *pool += want;
     }
     return (T*)b.p;
   }
@@ -74,6 +98,7 @@ struct Workspace {
     for (auto& kv : bufs)
       if (kv.second.p) cudaFree(kv.second.p);
     bufs.clear();
+    if (pool) *pool -= total;
     total = 0;
   }
 };
@@ -90,35 +115,96 @@ struct Run {
   uint64_t out_bytes = 0;
 };
 
+// one execution context of the pipeline
+struct Engine {
+  Workspace ws;
+  Run run;
+  cudaEvent_t ev[kStages + 1] = {};
+  float stage_ms[kStages] = {0};
+  uint64_t launches = 0;
+  uint32_t* h_tot = nullptr;  // pinned counters
+  // job service: the batch whose IR the workspace holds and its unfetched jobs
+  uint64_t batch = 0;
+  uint32_t live = 0;
+  bool busy = false;
+};
+
+enum JobState : int { JOB_PENDING = 0, JOB_RUNNING = 1, JOB_DONE = 2 };
+
 struct JobRec {
+  std::string in;    // input file text (ends with '\n'); dropped once run
   std::string text;  // OpenCL output
   int status = 0;
+  int rc = GCN_OK;   // a batch failure reported at fetch
+  int state = JOB_PENDING;
+  uint64_t est = 0;  // device bytes charged to the budget at admission
+  uint64_t t_submit = 0, t_start = 0, t_done = 0;
+  Engine* eng = nullptr;  // engine holding the job's IR (null = not resident)
+  uint64_t batch = 0;
   uint32_t run_file = 0;
-  uint64_t run_id = 0;
 };
+
+// a worker: host thread, CUDA stream, pinned staging buffers
+struct Lane {
+  std::thread th;
+  cudaStream_t stream = nullptr;
+  uint8_t* h_in = nullptr;
+  size_t h_in_cap = 0;
+  uint8_t* h_out = nullptr;
+  size_t h_out_cap = 0;
+  uint64_t* h_off = nullptr;  // file offsets in, then file output offsets out
+  size_t h_off_cap = 0;
+  int32_t* h_st = nullptr;
+  size_t h_st_cap = 0;
+};
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+constexpr int kLanes = 2;                      // worker lanes per handle
+constexpr int kPoolEngines = kLanes + 2;       // engines of the job service
+constexpr uint64_t kMaxBatchText = 64ull << 20;  // text bytes one lane takes at once
+constexpr uint64_t kEstPerTextByte = 48;       // device bytes per input byte (admission estimate)
+constexpr uint64_t kEstPerJob = 1ull << 20;
 
 }  // namespace
 
 struct gcn_decomp {
   int device = 0;
   cudaStream_t stream = nullptr;
-  Workspace ws;
-  std::mutex mu;
-  Run run;
+  // device-resident form
+  std::mutex dmu;
+  Engine direct;
+  cudaStream_t direct_stream = nullptr;  // stream of the last run_device call
   uint64_t run_id = 0;
-  uint64_t next_job = 1;
-  uint32_t max_slots = 65536;
+  // job service
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
   std::map<uint64_t, JobRec> jobs;
-  cudaEvent_t ev[kStages + 1];
-  float stage_ms[kStages] = {0};
-  uint64_t launches = 0;
-  uint32_t* h_tot = nullptr;  // pinned counters
+  std::deque<uint64_t> pending;
+  std::deque<uint64_t> done_q;  // finished jobs not yet reported by poll
+  std::vector<std::unique_ptr<Engine>> engines;
+  std::vector<std::unique_ptr<Lane>> lanes;
+  bool stop = false;
+  uint64_t next_job = 1, next_batch = 1;
+  uint32_t max_slots = 65536;
+  uint64_t budget = 0;
+  uint64_t admitted = 0;  // estimated device bytes of admitted, unfetched jobs
+  std::atomic<uint64_t> pool{0};
+  // most recent completed pipeline run (either form)
+  std::mutex smu;
+  float last_ms[kStages] = {0};
+  uint64_t last_stats[9] = {0};
+  uint64_t last_launches = 0;
 };
 
 namespace {
 
 // the whole pipeline on a device-resident batch
-void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t* file_off, uint32_t F,
+void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* file_off, uint32_t F,
                   cudaStream_t s) {
   Workspace& W = h->ws;
   Run& R = h->run;
@@ -350,19 +436,18 @@ void run_pipeline(gcn_decomp* h, const uint8_t* text, uint64_t n, const uint64_t
   h->launches = launch_counter() - launches0;
 }
 
-void finish_run(gcn_decomp* h, cudaStream_t s) {
+void finish_run(Engine* h, cudaStream_t s) {
   Run& R = h->run;
   Batch& b = R.b;
+  CK(cudaMemcpyAsync(&h->h_tot[15], b.err, 4, cudaMemcpyDeviceToHost, s));
+  R.kh.resize(b.K);
+  if (b.K) CK(cudaMemcpyAsync(R.kh.data(), b.kh, sizeof(KHdr) * b.K, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&h->stage_ms[i], h->ev[i], h->ev[i + 1]);
-  uint32_t e = 0;
-  CK(cudaMemcpy(&e, b.err, 4, cudaMemcpyDeviceToHost));
-  if (e) {
+  if (uint32_t e = h->h_tot[15]) {
     set_err("device error flags " + std::to_string(e));
     throw GCN_ECUDA;
   }
-  R.kh.resize(b.K);
-  if (b.K) CK(cudaMemcpy(R.kh.data(), b.kh, sizeof(KHdr) * b.K, cudaMemcpyDeviceToHost));
   R.file_k0.assign(b.F + 1, 0);
   // kernels are in file order: first kernel of each file
   uint32_t k = 0;
@@ -370,6 +455,263 @@ void finish_run(gcn_decomp* h, cudaStream_t s) {
     while (k < b.K && R.kh[k].file < f) ++k;
     R.file_k0[f] = k;
   }
+}
+
+void engine_init(gcn_decomp* h, Engine* E) {
+  E->ws.budget = h->budget;
+  E->ws.pool = &h->pool;
+  for (auto& e : E->ev) CK(cudaEventCreate(&e));
+  CK(cudaMallocHost(&E->h_tot, 64));
+}
+
+void engine_free(Engine* E) {
+  E->ws.release();
+  for (auto& e : E->ev)
+    if (e) cudaEventDestroy(e);
+  if (E->h_tot) cudaFreeHost(E->h_tot);
+  E->h_tot = nullptr;
+}
+
+void note_run(gcn_decomp* h, const Engine* E) {
+  std::lock_guard<std::mutex> g(h->smu);
+  const Batch& b = E->run.b;
+  const uint64_t v[9] = {b.L, b.K, b.I, b.NL, b.NPB, b.NLB, b.NS, E->run.out_bytes, E->ws.total};
+  for (int i = 0; i < 9; ++i) h->last_stats[i] = v[i];
+  for (int i = 0; i < kStages; ++i) h->last_ms[i] = E->stage_ms[i];
+  h->last_launches = E->launches;
+}
+
+template <class T>
+void grow_pinned(T*& p, size_t& cap, size_t n) {
+  if (cap >= n) return;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  cap = 0;
+  size_t want = n + n / 4 + 64;
+  CK(cudaMallocHost((void**)&p, want * sizeof(T)));
+  cap = want;
+}
+
+// drop the IR of every job whose batch lives on engine E (their texts stay)
+void drop_ir(gcn_decomp* h, Engine* E) {
+  if (!E->live) return;
+  for (auto& kv : h->jobs)
+    if (kv.second.eng == E) kv.second.eng = nullptr;
+  E->live = 0;
+}
+
+// an engine for a new batch (called with h->mu held)
+Engine* acquire_engine(gcn_decomp* h) {
+  Engine* pick = nullptr;
+  for (auto& e : h->engines)
+    if (!e->busy && !e->live && (!pick || e->ws.total > pick->ws.total)) pick = e.get();
+  if (!pick && (int)h->engines.size() < kPoolEngines) {
+    h->engines.emplace_back(new Engine);
+    pick = h->engines.back().get();
+    engine_init(h, pick);
+  }
+  if (!pick) {  // the finished batch that is oldest gives its engine back
+    for (auto& e : h->engines)
+      if (!e->busy && (!pick || e->batch < pick->batch)) pick = e.get();
+    drop_ir(h, pick);
+  }
+  pick->busy = true;
+  return pick;
+}
+
+// free the workspaces of idle engines (called with h->mu held)
+void shrink_pool(gcn_decomp* h) {
+  for (auto& e : h->engines)
+    if (!e->busy) {
+      drop_ir(h, e.get());
+      e->ws.release();
+    }
+}
+
+// one batch of jobs on engine E through lane L; fills the jobs' results
+void run_jobs(gcn_decomp* h, Lane* L, Engine* E, const std::vector<JobRec*>& js) {
+  cudaStream_t s = L->stream;
+  const size_t n = js.size();
+  grow_pinned(L->h_off, L->h_off_cap, n + 1);
+  grow_pinned(L->h_st, L->h_st_cap, n + 1);
+  uint64_t N = 0;
+  for (size_t i = 0; i < n; ++i) {
+    L->h_off[i] = N;
+    N += js[i]->in.size();
+  }
+  L->h_off[n] = N;
+  if (N >= (1ull << 32)) {
+    set_err("batch text exceeds 4 GiB");
+    throw GCN_ENOMEM;
+  }
+  grow_pinned(L->h_in, L->h_in_cap, N + 1);
+  for (size_t i = 0; i < n; ++i) memcpy(L->h_in + L->h_off[i], js[i]->in.data(), js[i]->in.size());
+  uint8_t* d_text = E->ws.get<uint8_t>("in_text", N + 16);
+  uint64_t* d_off = E->ws.get<uint64_t>("in_off", n + 1);
+  CK(cudaMemcpyAsync(d_text, L->h_in, N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_off, L->h_off, sizeof(uint64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+  run_pipeline(E, d_text, N, d_off, (uint32_t)n, s);
+  const Batch& b = E->run.b;
+  const uint64_t T = E->run.out_bytes;
+  grow_pinned(L->h_out, L->h_out_cap, T + 1);
+  if (b.file_out_off) {
+    CK(cudaMemcpyAsync(L->h_off, b.file_out_off, sizeof(uint64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(L->h_st, b.file_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    if (T) CK(cudaMemcpyAsync(L->h_out, b.out, T, cudaMemcpyDeviceToHost, s));
+  }
+  finish_run(E, s);
+  for (size_t i = 0; i < n; ++i) {
+    JobRec& j = *js[i];
+    j.text.assign((const char*)L->h_out + L->h_off[i], L->h_off[i + 1] - L->h_off[i]);
+    j.status = L->h_st[i];
+    j.run_file = (uint32_t)i;
+  }
+}
+
+void finish_jobs(gcn_decomp* h, const std::vector<uint64_t>& ids, Engine* E, uint64_t batch, int rc) {
+  const uint64_t t = now_ns();
+  for (uint64_t id : ids) {
+    JobRec& j = h->jobs[id];
+    j.state = JOB_DONE;
+    j.rc = rc;
+    j.t_done = t;
+    std::string().swap(j.in);
+    j.eng = rc == GCN_OK ? E : nullptr;
+    j.batch = batch;
+    h->done_q.push_back(id);
+  }
+  while (h->done_q.size() > 2ull * h->max_slots + 1024) h->done_q.pop_front();  // never polled
+  if (rc == GCN_OK) {
+    E->batch = batch;
+    E->live = (uint32_t)ids.size();
+  }
+  E->busy = false;
+}
+
+void lane_main(gcn_decomp* h, Lane* L) {
+  cudaSetDevice(h->device);
+  std::unique_lock<std::mutex> lk(h->mu);
+  while (true) {
+    h->cv_work.wait(lk, [&] { return h->stop || !h->pending.empty(); });
+    if (h->stop) break;
+    // continuous batching: everything queued now, up to the batch limit
+    std::vector<uint64_t> ids;
+    std::vector<JobRec*> js;
+    uint64_t bytes = 0;
+    const uint64_t t = now_ns();
+    while (!h->pending.empty()) {
+      JobRec& j = h->jobs[h->pending.front()];
+      if (!ids.empty() && bytes + j.in.size() > kMaxBatchText) break;
+      ids.push_back(h->pending.front());
+      js.push_back(&j);
+      h->pending.pop_front();
+      bytes += j.in.size();
+      j.state = JOB_RUNNING;
+      j.t_start = t;
+    }
+    if (!h->pending.empty()) h->cv_work.notify_one();
+    Engine* E = acquire_engine(h);
+    const uint64_t batch = h->next_batch++;
+    lk.unlock();
+    int rc = GCN_OK;
+    bool shrunk = false;
+    while (true) {
+      try {
+        run_jobs(h, L, E, js);
+        rc = GCN_OK;
+      } catch (int e) {
+        rc = e;
+      }
+      if (rc != GCN_ENOMEM || (shrunk && js.size() == 1)) break;
+      // out of the memory budget: first give back the memory of idle engines
+      // (and start this engine afresh), then run half of the batch and queue
+      // the other half again
+      lk.lock();
+      shrink_pool(h);
+      E->ws.release();
+      if (shrunk) {
+        const size_t keep = js.size() / 2;
+        for (size_t q = js.size(); q-- > keep;) {
+          js[q]->state = JOB_PENDING;
+          h->pending.push_front(ids[q]);
+        }
+        ids.resize(keep);
+        js.resize(keep);
+        h->cv_work.notify_one();
+      }
+      shrunk = true;
+      lk.unlock();
+    }
+    lk.lock();
+    if (rc == GCN_OK) note_run(h, E);
+    finish_jobs(h, ids, E, batch, rc);
+    h->cv_done.notify_all();
+  }
+}
+
+void start_lanes(gcn_decomp* h) {
+  for (int i = 0; i < kLanes; ++i) {
+    h->lanes.emplace_back(new Lane);
+    Lane* L = h->lanes.back().get();
+    CK(cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking));
+  }
+  for (auto& L : h->lanes) L->th = std::thread(lane_main, h, L.get());
+}
+
+void stop_lanes(gcn_decomp* h) {
+  {
+    std::lock_guard<std::mutex> g(h->mu);
+    h->stop = true;
+  }
+  h->cv_work.notify_all();
+  h->cv_done.notify_all();
+  for (auto& L : h->lanes) {
+    if (L->th.joinable()) L->th.join();
+    if (L->stream) {
+      cudaStreamSynchronize(L->stream);
+      cudaStreamDestroy(L->stream);
+    }
+    if (L->h_in) cudaFreeHost(L->h_in);
+    if (L->h_out) cudaFreeHost(L->h_out);
+    if (L->h_off) cudaFreeHost(L->h_off);
+    if (L->h_st) cudaFreeHost(L->h_st);
+  }
+  h->lanes.clear();
+}
+
+// release a fetched job (called with h->mu held)
+void release_job(gcn_decomp* h, std::map<uint64_t, JobRec>::iterator it) {
+  JobRec& j = it->second;
+  h->admitted -= std::min(h->admitted, j.est);
+  if (j.eng && j.eng->batch == j.batch && j.eng->live) --j.eng->live;
+  h->jobs.erase(it);
+}
+
+// wait until job `id` is done (or report why not); called with the lock held
+int wait_job(gcn_decomp* h, std::unique_lock<std::mutex>& lk, uint64_t id, bool wait,
+             std::map<uint64_t, JobRec>::iterator* out) {
+  auto it = h->jobs.find(id);
+  if (it == h->jobs.end()) {
+    set_err("unknown job");
+    return GCN_ENOJOB;
+  }
+  if (it->second.state != JOB_DONE) {
+    if (!wait) {
+      set_err("job not finished");
+      return GCN_EAGAIN;
+    }
+    h->cv_done.wait(lk, [&] {
+      auto q = h->jobs.find(id);
+      return h->stop || q == h->jobs.end() || q->second.state == JOB_DONE;
+    });
+    it = h->jobs.find(id);
+    if (it == h->jobs.end() || it->second.state != JOB_DONE) {
+      set_err("job no longer known");
+      return GCN_ENOJOB;
+    }
+  }
+  *out = it;
+  return GCN_OK;
 }
 
 }  // namespace
@@ -395,15 +737,15 @@ int gcn_decomp_create(const gcn_decomp_config* cfg, gcn_decomp_t** out) {
   gcn_decomp* h = new gcn_decomp;
   try {
     h->device = cfg->device;
+    h->budget = cfg->mem_budget_bytes;
+    if (cfg->max_slots) h->max_slots = cfg->max_slots;
     CK(cudaSetDevice(h->device));
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
-    for (auto& e : h->ev) CK(cudaEventCreate(&e));
-    CK(cudaMallocHost(&h->h_tot, 64));
     CK(cudaDeviceSetLimit(cudaLimitStackSize, 16384));
-    h->ws.budget = cfg->mem_budget_bytes;
-    if (cfg->max_slots) h->max_slots = cfg->max_slots;
+    engine_init(h, &h->direct);
     init_decode_tables();
     CK(cudaGetLastError());
+    start_lanes(h);
   } catch (int rc) {
     gcn_decomp_destroy(h);
     return rc;
@@ -415,11 +757,11 @@ int gcn_decomp_create(const gcn_decomp_config* cfg, gcn_decomp_t** out) {
 void gcn_decomp_destroy(gcn_decomp_t* h) {
   if (!h) return;
   cudaSetDevice(h->device);
+  stop_lanes(h);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  h->ws.release();
-  for (auto& e : h->ev)
-    if (e) cudaEventDestroy(e);
-  if (h->h_tot) cudaFreeHost(h->h_tot);
+  for (auto& e : h->engines) engine_free(e.get());
+  h->engines.clear();
+  engine_free(&h->direct);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -430,14 +772,16 @@ int gcn_decomp_run_device(gcn_decomp_t* h, const uint8_t* d_text, uint64_t text_
     set_err("bad argument");
     return GCN_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(h->mu);
+  std::lock_guard<std::mutex> lk(h->dmu);
   try {
     CK(cudaSetDevice(h->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
-    run_pipeline(h, d_text, text_len, d_file_off, (uint32_t)n_files, s);
+    h->direct_stream = s;
+    run_pipeline(&h->direct, d_text, text_len, d_file_off, (uint32_t)n_files, s);
     ++h->run_id;
+    note_run(h, &h->direct);
   } catch (int rc) {
-    h->run.valid = false;
+    h->direct.run.valid = false;
     return rc;
   }
   return GCN_OK;
@@ -445,34 +789,39 @@ int gcn_decomp_run_device(gcn_decomp_t* h, const uint8_t* d_text, uint64_t text_
 
 int gcn_decomp_result_device(gcn_decomp_t* h, const uint8_t** d_out, const uint64_t** d_out_off,
                              const int32_t** d_status, uint64_t* out_bytes) {
-  if (!h || !h->run.valid) {
+  if (!h) return GCN_EINVAL;
+  std::lock_guard<std::mutex> lk(h->dmu);
+  if (!h->direct.run.valid) {
     set_err("no completed run");
     return GCN_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(h->mu);
   try {
-    finish_run(h, h->stream);
+    CK(cudaSetDevice(h->device));
+    finish_run(&h->direct, h->direct_stream);
   } catch (int rc) {
     return rc;
   }
-  if (d_out) *d_out = h->run.b.out;
-  if (d_out_off) *d_out_off = h->run.b.file_out_off;
-  if (d_status) *d_status = h->run.b.file_status;
-  if (out_bytes) *out_bytes = h->run.out_bytes;
+  note_run(h, &h->direct);
+  const Run& R = h->direct.run;
+  if (d_out) *d_out = R.b.out;
+  if (d_out_off) *d_out_off = R.b.file_out_off;
+  if (d_status) *d_status = R.b.file_status;
+  if (out_bytes) *out_bytes = R.out_bytes;
   return GCN_OK;
 }
 
 int gcn_decomp_result_copy(gcn_decomp_t* h, uint64_t f0, uint64_t f1, void* buf, size_t cap, uint64_t* off_out,
                            int32_t* status_out) {
-  if (!h || !h->run.valid || f0 > f1 || f1 > h->run.b.F) {
+  if (!h) return GCN_EINVAL;
+  std::lock_guard<std::mutex> lk(h->dmu);
+  if (!h->direct.run.valid || f0 > f1 || f1 > h->direct.run.b.F) {
     set_err("no run or bad file range");
     return GCN_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(h->mu);
   try {
     CK(cudaSetDevice(h->device));
-    CK(cudaStreamSynchronize(h->stream));
-    const Batch& b = h->run.b;
+    CK(cudaStreamSynchronize(h->direct_stream));
+    const Batch& b = h->direct.run.b;
     std::vector<uint64_t> o(f1 - f0 + 1);
     CK(cudaMemcpy(o.data(), b.file_out_off + f0, 8 * o.size(), cudaMemcpyDeviceToHost));
     uint64_t bytes = o.back() - o.front();
@@ -498,105 +847,160 @@ int gcn_decomp_submit_batch(gcn_decomp_t* h, const char* const* text, const size
     set_err("bad argument");
     return GCN_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(h->mu);
   if (n_admitted) *n_admitted = 0;
-  size_t take = std::min<size_t>(n, h->max_slots > h->jobs.size() ? h->max_slots - h->jobs.size() : 0);
-  if (n && !take) {
-    set_err("no free job slot");
-    return GCN_EAGAIN;
+  std::unique_lock<std::mutex> lk(h->mu);
+  size_t take = 0;
+  const uint64_t t = now_ns();
+  for (; take < n; ++take) {
+    if (h->jobs.size() >= h->max_slots) break;
+    const size_t l = len[take];
+    if (l && !text[take]) break;
+    const uint64_t est = kEstPerTextByte * (uint64_t)l + kEstPerJob;
+    if (h->budget && h->admitted && h->admitted + est > h->budget) break;
+    const uint64_t id = h->next_job++;
+    JobRec& j = h->jobs[id];
+    const bool nl = l && text[take][l - 1] == '\n';
+    j.in.reserve(l + 1);
+    j.in.assign(text[take], l);
+    if (l && !nl) j.in.push_back('\n');
+    j.est = est;
+    j.t_submit = t;
+    h->admitted += est;
+    h->pending.push_back(id);
+    job_ids[take] = id;
   }
-  try {
-    CK(cudaSetDevice(h->device));
-    cudaStream_t s = h->stream;
-    // stage the files (each ending with '\n') in pinned memory, copy to the device
-    std::vector<uint64_t> off(take + 1, 0);
-    for (size_t i = 0; i < take; ++i) {
-      size_t l = len[i];
-      bool nl = l && text[i][l - 1] == '\n';
-      off[i + 1] = off[i] + l + ((l && !nl) ? 1 : 0);
-    }
-    uint64_t N = off[take];
-    if (N >= (1ull << 32)) {
-      set_err("batch text exceeds 4 GiB");
-      throw GCN_ENOMEM;
-    }
-    uint8_t* hbuf = nullptr;
-    CK(cudaMallocHost(&hbuf, std::max<uint64_t>(N, 1)));
-    for (size_t i = 0; i < take; ++i) {
-      memcpy(hbuf + off[i], text[i], len[i]);
-      if (off[i + 1] - off[i] > len[i]) hbuf[off[i + 1] - 1] = '\n';
-    }
-    uint8_t* d_text = h->ws.get<uint8_t>("in_text", N + 16);
-    uint64_t* d_off = h->ws.get<uint64_t>("in_off", take + 1);
-    CK(cudaMemcpyAsync(d_text, hbuf, N, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_off, off.data(), sizeof(uint64_t) * (take + 1), cudaMemcpyHostToDevice, s));
-    run_pipeline(h, d_text, N, d_off, (uint32_t)take, s);
-    finish_run(h, s);
-    ++h->run_id;
-    CK(cudaFreeHost(hbuf));
-    // results to host memory, one record per job
-    const Run& R = h->run;
-    std::vector<uint64_t> fo(take + 1, 0);
-    std::vector<int32_t> st(take, 0);
-    std::string out;
-    if (R.b.file_out_off) {
-      CK(cudaMemcpy(fo.data(), R.b.file_out_off, sizeof(uint64_t) * (take + 1), cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(st.data(), R.b.file_status, sizeof(int32_t) * take, cudaMemcpyDeviceToHost));
-      out.resize(fo[take]);
-      if (fo[take]) CK(cudaMemcpy(&out[0], R.b.out, fo[take], cudaMemcpyDeviceToHost));
-    }
-    for (size_t i = 0; i < take; ++i) {
-      JobRec j;
-      j.text = out.substr(fo[i], fo[i + 1] - fo[i]);
-      j.status = st[i];
-      j.run_file = (uint32_t)i;
-      j.run_id = h->run_id;
-      uint64_t id = h->next_job++;
-      h->jobs[id] = std::move(j);
-      job_ids[i] = id;
-    }
-    if (n_admitted) *n_admitted = take;
-  } catch (int rc) {
-    return rc;
+  if (n_admitted) *n_admitted = take;
+  lk.unlock();
+  if (take) h->cv_work.notify_all();
+  if (n && !take) {
+    set_err("nothing admitted: no free job slot or memory budget");
+    return GCN_EAGAIN;
   }
   return GCN_OK;
 }
 
 int gcn_decomp_fetch_opencl(gcn_decomp_t* h, uint64_t job_id, char* buf, size_t cap, size_t* len_out,
                             int* status_out, uint32_t flags) {
-  (void)flags;
   if (!h) return GCN_EINVAL;
+  std::unique_lock<std::mutex> lk(h->mu);
+  std::map<uint64_t, JobRec>::iterator it;
+  int rc = wait_job(h, lk, job_id, (flags & GCN_WAIT) != 0, &it);
+  if (rc != GCN_OK) return rc;
+  JobRec& j = it->second;
+  if (j.rc != GCN_OK) {
+    rc = j.rc;
+    set_err("the batch of this job failed");
+    release_job(h, it);
+    return rc;
+  }
+  if (len_out) *len_out = j.text.size();
+  if (status_out) *status_out = j.status;
+  if (!buf) return GCN_OK;
+  if (cap < j.text.size()) {
+    set_err("buffer too small");
+    return GCN_EINVAL;
+  }
+  memcpy(buf, j.text.data(), j.text.size());
+  release_job(h, it);
+  return GCN_OK;
+}
+
+int gcn_decomp_fetch_batch(gcn_decomp_t* h, const uint64_t* job_ids, size_t n, char* buf, size_t cap,
+                           uint64_t* off_out, int32_t* status_out, uint32_t flags) {
+  if (!h || (n && (!job_ids || !off_out))) {
+    set_err("bad argument");
+    return GCN_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(h->mu);
+  std::vector<std::map<uint64_t, JobRec>::iterator> its(n);
+  for (size_t i = 0; i < n; ++i) {
+    int rc = wait_job(h, lk, job_ids[i], (flags & GCN_WAIT) != 0, &its[i]);
+    if (rc != GCN_OK) return rc;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    its[i] = h->jobs.find(job_ids[i]);  // re-find: waiting released the lock
+    if (its[i] == h->jobs.end()) {
+      set_err("job no longer known");
+      return GCN_ENOJOB;
+    }
+    if (its[i]->second.rc != GCN_OK) {
+      set_err("the batch of a job failed");
+      return its[i]->second.rc;
+    }
+  }
+  uint64_t o = 0;
+  for (size_t i = 0; i < n; ++i) {
+    off_out[i] = o;
+    o += its[i]->second.text.size();
+    if (status_out) status_out[i] = its[i]->second.status;
+  }
+  off_out[n] = o;
+  if (!buf) return GCN_OK;
+  if (cap < o) {
+    set_err("buffer too small");
+    return GCN_EINVAL;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    const std::string& t = its[i]->second.text;
+    if (!t.empty()) memcpy(buf + off_out[i], t.data(), t.size());
+  }
+  for (size_t i = 0; i < n; ++i) release_job(h, its[i]);
+  return GCN_OK;
+}
+
+int gcn_decomp_poll(gcn_decomp_t* h, uint64_t* job_ids, size_t cap, size_t* n_out, int timeout_ms) {
+  if (!h || !n_out || (cap && !job_ids)) {
+    set_err("bad argument");
+    return GCN_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(h->mu);
+  if (h->done_q.empty() && timeout_ms != 0) {
+    auto ready = [&] { return h->stop || !h->done_q.empty(); };
+    if (timeout_ms < 0) h->cv_done.wait(lk, ready);
+    else h->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  }
+  size_t k = 0;
+  while (k < cap && !h->done_q.empty()) {
+    const uint64_t id = h->done_q.front();
+    h->done_q.pop_front();
+    if (h->jobs.count(id)) job_ids[k++] = id;
+  }
+  *n_out = k;
+  return GCN_OK;
+}
+
+int gcn_decomp_job_info(gcn_decomp_t* h, uint64_t job_id, uint64_t* info, int cap) {
+  if (!h || !info || cap < 0) return GCN_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
   auto it = h->jobs.find(job_id);
   if (it == h->jobs.end()) {
     set_err("unknown job");
     return GCN_ENOJOB;
   }
-  if (len_out) *len_out = it->second.text.size();
-  if (status_out) *status_out = it->second.status;
-  if (!buf) return GCN_OK;
-  if (cap < it->second.text.size()) {
-    set_err("buffer too small");
-    return GCN_EINVAL;
-  }
-  memcpy(buf, it->second.text.data(), it->second.text.size());
-  h->jobs.erase(it);
-  return GCN_OK;
+  const JobRec& j = it->second;
+  const uint64_t v[5] = {(uint64_t)j.state, j.t_submit, j.t_start, j.t_done, j.eng != nullptr};
+  int n = cap < 5 ? cap : 5;
+  for (int i = 0; i < n; ++i) info[i] = v[i];
+  return n;
 }
 
 int gcn_decomp_fetch_ir(gcn_decomp_t* h, uint64_t job_id, int which, void* buf, size_t cap, size_t* len_out) {
   if (!h || which < 0 || which > 5) return GCN_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
-  auto it = h->jobs.find(job_id);
-  if (it == h->jobs.end() || it->second.run_id != h->run_id || !h->run.valid) {
-    set_err("job unknown or no longer resident");
+  std::unique_lock<std::mutex> lk(h->mu);
+  std::map<uint64_t, JobRec>::iterator it;
+  int rc = wait_job(h, lk, job_id, true, &it);
+  if (rc != GCN_OK) return rc;
+  const JobRec& j = it->second;
+  if (j.rc != GCN_OK || !j.eng || j.eng->batch != j.batch || !j.eng->run.valid) {
+    set_err("job IR no longer resident");
     return GCN_ENOJOB;
   }
-  const Run& R = h->run;
+  const Run& R = j.eng->run;
   const Batch& b = R.b;
-  uint32_t f = it->second.run_file;
+  uint32_t f = j.run_file;
   std::vector<uint8_t> v;
   try {
+    CK(cudaSetDevice(h->device));
     for (uint32_t k = R.file_k0[f]; k < R.file_k0[f + 1]; ++k) {
       const KHdr& K = R.kh[k];
       auto grab = [&](const void* dev, size_t bytes) {
@@ -620,8 +1024,8 @@ int gcn_decomp_fetch_ir(gcn_decomp_t* h, uint64_t job_id, int which, void* buf, 
         }
       }
     }
-  } catch (int rc) {
-    return rc;
+  } catch (int e) {
+    return e;
   }
   if (len_out) *len_out = v.size();
   if (!buf) return GCN_OK;
@@ -630,22 +1034,26 @@ int gcn_decomp_fetch_ir(gcn_decomp_t* h, uint64_t job_id, int which, void* buf, 
   return GCN_OK;
 }
 
-uint64_t gcn_decomp_launches(gcn_decomp_t* h) { return h ? h->launches : 0; }
+uint64_t gcn_decomp_launches(gcn_decomp_t* h) {
+  if (!h) return 0;
+  std::lock_guard<std::mutex> g(h->smu);
+  return h->last_launches;
+}
 
 int gcn_decomp_run_stats(gcn_decomp_t* h, uint64_t* out, int cap) {
   if (!h || !out || cap < 0) return GCN_EINVAL;
-  const Batch& b = h->run.b;
-  uint64_t v[8] = {b.L, b.K, b.I, b.NL, b.NPB, b.NLB, b.NS, h->run.out_bytes};
-  int n = cap < 8 ? cap : 8;
-  for (int i = 0; i < n; ++i) out[i] = v[i];
+  std::lock_guard<std::mutex> g(h->smu);
+  int n = cap < 9 ? cap : 9;
+  for (int i = 0; i < n; ++i) out[i] = h->last_stats[i];
   return n;
 }
 
 int gcn_decomp_stage_times(gcn_decomp_t* h, float* ms, const char** names, int cap) {
   if (!h || cap < 0) return GCN_EINVAL;
+  std::lock_guard<std::mutex> g(h->smu);
   int n = std::min(cap, kStages);
   for (int i = 0; i < n; ++i) {
-    if (ms) ms[i] = h->stage_ms[i];
+    if (ms) ms[i] = h->last_ms[i];
     if (names) names[i] = kStageNames[i];
   }
   return n;

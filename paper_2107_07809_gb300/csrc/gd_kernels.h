@@ -7,9 +7,9 @@ namespace gd {
 // sets the text gcn_decomp_last_error returns on this thread
 void set_api_error(const char* msg);
 
-// kernels launched by this process (host-side count; one instance across units)
+// kernels launched by the calling host thread (one instance across units)
 inline uint64_t& launch_counter() {
-  static uint64_t c = 0;
+  thread_local uint64_t c = 0;
   return c;
 }
 
