@@ -6,7 +6,10 @@ method) through the C ABI.  Default workload: 10,000 seeded synthetic kernels
 with log-uniform lengths 50..2000 (the plain-method-at-scale configuration),
 one kernel per file, text resident in HBM when the timed region starts
 (`value`).  `e2e` measures the same through the host-buffer entry points
-(submit_batch + fetch_opencl), host<->device copies inside the timed region.
+(submit_batch + fetch_batch), host<->device copies inside the timed region.
+`per_kernel` times the plain form (one pipeline run per kernel) on a sample of
+the same kernels; `serve` drives the job service with open-loop Poisson
+arrivals at 1k, 10k and 100k requests/s and reports p50/p99 latency.
 
 --impl reference times the CPU oracle (single-threaded) on bounded samples of
 the same workload, the comparison arm.  Multi-GPU (torchrun): every rank
@@ -160,6 +163,130 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def per_kernel_form(pkg, torch, batch, local, n_sample):
+    """The plain form: one pipeline run (one launch sequence) per kernel, its
+    text already in HBM; each kernel's text starts 256-byte aligned."""
+    n = min(n_sample, len(batch))
+    offs = batch.offsets.astype(np.int64)
+    sizes = offs[1:n + 1] - offs[:n]
+    starts = np.zeros(n + 1, np.int64)
+    starts[1:] = np.cumsum((sizes + 255) // 256 * 256)
+    host = np.zeros(int(starts[-1]) + 256, np.uint8)
+    for i in range(n):
+        host[starts[i]:starts[i] + sizes[i]] = batch.text[offs[i]:offs[i + 1]]
+    d_text = torch.from_numpy(host).to(f"cuda:{local}")
+    pairs = np.zeros((n, 2), np.int64)
+    pairs[:, 1] = sizes
+    d_pairs = torch.from_numpy(pairs).to(f"cuda:{local}")
+    dec = pkg.Decompiler(local)
+    stream = torch.cuda.current_stream()
+    base, pbase = d_text.data_ptr(), d_pairs.data_ptr()
+
+    def one(i):
+        dec.run_device(base + int(starts[i]), int(sizes[i]), pbase + 16 * i, 1, stream.cuda_stream)
+
+    for i in range(min(n, 8)):
+        one(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n):
+        one(i)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dec.close()
+    ni = int(batch.ninstr[:n].sum())
+    return {"value": ni / dt, "unit": "instr/s", "kernels": n, "instrs": ni, "ms_per_kernel": dt * 1e3 / n,
+            "form": "one pipeline run per kernel, text in HBM"}
+
+
+def serve(pkg, local, rates, n_pool=1000, max_requests=20000, max_seconds=5.0, budget=20 << 30):
+    """Open-loop Poisson arrivals of single-kernel requests (lengths 100..50,000,
+    the batch mix) through submit_batch / poll / fetch_batch; latency is from
+    the scheduled arrival to the job's finish time."""
+    import threading
+
+    params = gcngen.preset(4)
+    pool = gcngen.generate(params, n_pool, seed=gcngen.SEED_BASE + 4, threads=os.cpu_count() or 4)
+    texts = [pool.kernel(i) for i in range(n_pool)]
+    ninstr = pool.ninstr.astype(np.int64)
+    out = {"budget_bytes": budget, "pool": f"{n_pool} seeded requests (lengths 100..50000), cycled",
+           "latency": "scheduled arrival -> job finished (CLOCK_MONOTONIC)", "rates": []}
+    with pkg.Decompiler(local, mem_budget_bytes=budget) as dec:
+        ids = dec.submit_batch(texts)
+        raw, offs, _ = dec.fetch_batch_raw(ids)
+        ref = [raw[offs[i]:offs[i + 1]] for i in range(n_pool)]
+        for rate in rates:
+            rng = np.random.default_rng(2107078090 + rate)
+            n = int(min(max_requests, rate * max_seconds))
+            arr = np.cumsum(rng.exponential(1.0 / rate, n))
+            which = rng.integers(0, n_pool, n)
+            id_to_req = {}
+            lock = threading.Lock()
+            lat = np.zeros(n)
+            done_ns = np.zeros(n, np.int64)
+            mism = [0]
+            t0 = time.monotonic_ns() + 20_000_000
+            arr_ns = (t0 + arr * 1e9).astype(np.int64)
+
+            def submitter():
+                i = 0
+                while i < n:
+                    now = time.monotonic_ns()
+                    j = int(np.searchsorted(arr_ns, now, side="right"))
+                    if j <= i:
+                        time.sleep(max(0.0, min(0.001, (arr_ns[i] - now) / 1e9)))
+                        continue
+                    try:
+                        got = dec.submit_batch([texts[w] for w in which[i:j]])
+                    except pkg.GcnDecompError as e:
+                        if e.rc != pkg.GCN_EAGAIN:
+                            raise
+                        got = []
+                    with lock:
+                        for q, jid in enumerate(got):
+                            id_to_req[jid] = i + q
+                    i += len(got)
+                    if i < j:
+                        time.sleep(0.0005)  # slots or memory budget full: retry soon
+
+            def fetcher():
+                seen = 0
+                waiting = []
+                while seen < n:
+                    got = dec.poll(cap=8192, timeout_ms=20)
+                    waiting += got
+                    if not waiting:
+                        continue
+                    with lock:
+                        ready = [j for j in waiting if j in id_to_req]
+                    if not ready:
+                        continue
+                    rs = set(ready)
+                    waiting = [j for j in waiting if j not in rs]
+                    infos = [dec.job_info(j)["t_done"] for j in ready]
+                    raw, offs, _ = dec.fetch_batch_raw(ready)
+                    for q, j in enumerate(ready):
+                        r = id_to_req[j]
+                        done_ns[r] = infos[q]
+                        lat[r] = (infos[q] - arr_ns[r]) / 1e6
+                        if raw[offs[q]:offs[q + 1]] != ref[which[r]]:
+                            mism[0] += 1
+                    seen += len(ready)
+
+            th = [threading.Thread(target=submitter), threading.Thread(target=fetcher)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            served = int(ninstr[which].sum())
+            span = (done_ns.max() - arr_ns[0]) / 1e9
+            out["rates"].append({
+                "rate_rps": rate, "requests": n, "offered_instr_s": float(rate * ninstr[which].mean()),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "throughput_instr_s": served / span, "mismatches": mism[0]})
+    return out
+
+
 def algorithmic_bytes(st):
     """Contract bytes of one pass: text in + OpenCL out + the IR arrays the
     parity tests compare (instruction records, block ids, block tables, headers)."""
@@ -181,6 +308,8 @@ def main():
     ap.add_argument("--kernels", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-kernel", type=int, default=300, help="kernels timed in the one-run-per-kernel form")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -259,6 +388,11 @@ def main():
         d2h = len(raw) + 12 * n_files
     e2e_val = total_instr * world / (statistics.median(e2e_ms) / 1e3) if e2e_ms else None
 
+    plain = per_kernel_form(pkg, torch, batch, local, args.per_kernel) if args.per_kernel > 0 else None
+    served = None
+    if rank == 0 and not args.no_serve:
+        served = serve(pkg, local, [1000, 10000, 100000])
+
     peaks, src = measured_peaks()
     ab = algorithmic_bytes(stats)
     bytes_per_pass = ab["text_in"] + ab["text_out"] + ab["ir"]
@@ -289,6 +423,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "instr/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.median(e2e_ms) if e2e_ms else None},
+            "per_kernel": plain, "serve": served,
             "gpu_launches": launches * args.steps, "clocks": clk.summary(), "stage_ms": stage_ms,
             "parity": parity, "run_stats": stats,
         }

@@ -253,12 +253,14 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   ra.kcnt = W.get<uint32_t>("kcnt", L + 1);
   ra.instr_excl = W.get<uint32_t>("instr_excl", L + 1);
   ra.label_excl = W.get<uint32_t>("label_excl", L + 1);
+  ra.cfg_excl = W.get<uint32_t>("cfg_excl", L + 1);
   if (L) launch_rows(text, line_start, L, file_off, F, ra, sc, tot, err, s);
   CK(cudaGetLastError());
   sync_totals();
   b.K = h->h_tot[0];
   b.I = h->h_tot[1];
   b.NL = h->h_tot[2];
+  b.NC = h->h_tot[14];
   b.rowtype = ra.rowtype;
   b.file_start = ra.file_start;
   b.kind = ra.kind;
@@ -269,7 +271,8 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.label_line = W.get<uint32_t>("label_line", b.NL + 1);
   b.label_instr = W.get<uint32_t>("label_instr", b.NL + 1);
   b.label_hash = W.get<uint32_t>("label_hash", b.NL + 1);
-  if (L) launch_scatter_rows(L, ra, b.instr_line, b.label_line, b.label_instr, b.kh, s);
+  b.cfg_line = W.get<uint32_t>("cfg_line", b.NC + 1);
+  if (L) launch_scatter_rows(L, ra, b.instr_line, b.label_line, b.label_instr, b.cfg_line, b.kh, s);
   CK(cudaEventRecord(h->ev[2], s));
   // S3
   launch_config(b, s);
@@ -299,6 +302,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.sense = W.get<uint8_t>("sense", b.I + 1);
   b.ltarget = W.get<uint32_t>("ltarget", b.I + 1);
   b.lblock_of = W.get<uint32_t>("lblock_of", b.I + 1);
+  b.exec_list = W.get<uint32_t>("exec_list", b.I + 1);
   launch_logical(b, sc, tot, s);
   CK(cudaGetLastError());
   sync_totals();

@@ -106,7 +106,7 @@ struct KHdr {
   uint32_t line;                  // the .kernel line
   uint32_t file;
   uint32_t name_off, name_len;
-  uint32_t cfg_end;               // first line after the kernel's rows
+  uint32_t first_cfg, n_cfg;       // the kernel's configuration rows (into cfg_line)
   uint32_t first_instr, n_instr;
   uint32_t first_label, n_label;
   uint32_t first_pblock, n_pblock;

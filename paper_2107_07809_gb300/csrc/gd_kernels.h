@@ -27,7 +27,7 @@ struct RowArrays {    // per line
   uint8_t* kind;
   uint8_t* rowtype;
   uint32_t *t0, *t1, *t2;
-  uint32_t *mkmax, *fsmax, *kcnt, *instr_excl, *label_excl;
+  uint32_t *mkmax, *fsmax, *kcnt, *instr_excl, *label_excl, *cfg_excl;
 };
 
 // everything the per-kernel stages read and write (device pointers)
@@ -35,7 +35,7 @@ struct Batch {
   const uint8_t* text;
   uint64_t text_len;
   const uint64_t* file_off;
-  uint32_t F, L, K, I, NL;       // files, lines, kernels, instructions, labels
+  uint32_t F, L, K, I, NL, NC;   // files, lines, kernels, instructions, labels, configuration rows
   uint32_t NPB, NLB;             // physical / logical blocks
   uint64_t NS;                   // block x register state words
   const uint32_t* line_start;
@@ -48,6 +48,7 @@ struct Batch {
   uint32_t* ikern;               // I: kernel of each instruction
   uint32_t* blen;                // I: length of a branch's label operand
   const uint32_t* kcnt;          // L: running count of .kernel rows
+  uint32_t* cfg_line;            // NC: line of each configuration row
   uint32_t* label_line;          // NL
   uint32_t* label_instr;         // NL (global instruction index)
   uint32_t* label_hash;          // NL
@@ -63,6 +64,7 @@ struct Batch {
   uint8_t* sense;                // I
   uint32_t* ltarget;             // I (kernel-relative)
   uint32_t* lleader;             // I
+  uint32_t* exec_list;           // I: the exec-mask form instructions, in order (S6 scratch)
   uint32_t* lblock_of;           // I (kernel-relative, kNone = dropped)
   BlockRec* lblocks;             // NLB (kernel-relative indices)
   uint32_t* lterm;               // NLB (kernel-relative instruction)
@@ -119,7 +121,7 @@ void launch_scan(const uint32_t* in, uint32_t* out, uint32_t n, int op, bool inc
 void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, const uint64_t* file_off, uint32_t F,
                  RowArrays& ra, ScanScratch sc, uint32_t* totals, uint32_t* err, cudaStream_t s);
 void launch_scatter_rows(uint32_t L, RowArrays& ra, uint32_t* instr_line, uint32_t* label_line, uint32_t* label_instr,
-                         KHdr* kh, cudaStream_t s);
+                         uint32_t* cfg_line, KHdr* kh, cudaStream_t s);
 
 // k_decode.cu
 void init_decode_tables();

@@ -170,9 +170,10 @@ __global__ void k_config(const __grid_constant__ Batch b) {
   K.partial = 0;
   K.status = 0;
   ArgRec* A = b.args + (size_t)k * kMaxArgs;
-  uint32_t l = K.line + 1;
-  for (; l < b.L && b.kind[l] != LK_KERNEL && !b.file_start[l]; ++l) {
-    if (b.rowtype[l] != RT_CFG) continue;
+  K.n_cfg = (k + 1 < b.K ? b.kh[k + 1].first_cfg : b.NC) - K.first_cfg;
+  // the configuration rows of this kernel, in line order
+  for (uint32_t c = K.first_cfg; c < K.first_cfg + K.n_cfg; ++c) {
+    const uint32_t l = b.cfg_line[c];
     const uint8_t* p = T + b.line_start[l];
     const uint8_t* e = T + b.line_start[l + 1] - 1;
     trim(p, e);
@@ -260,7 +261,6 @@ __global__ void k_config(const __grid_constant__ Batch b) {
       A[K.nargs++] = a;
     }
   }
-  K.cfg_end = l;
 }
 
 void launch_config(Batch& b, cudaStream_t s) {
@@ -565,7 +565,49 @@ struct Form {
 
 __device__ __forceinline__ bool same_pair(uint32_t a, uint32_t bb) { return otag(a) == TG_SGPR && a == bb; }
 
-__global__ void k_exec_forms(const __grid_constant__ Batch b) {
+// every instruction: default control, branches and s_endpgm; flag the
+// instructions that take part in exec-mask forms
+__device__ __forceinline__ bool exec_form_op(uint16_t op) {
+  return op == O_S_AND_SAVEEXEC || op == O_S_XOR_B64 || op == O_S_CBRANCH_EXECZ || op == O_S_OR_SAVEEXEC ||
+         op == O_S_OR_B64;
+}
+
+__global__ void k_exec_init(const __grid_constant__ Batch b, uint32_t* __restrict__ flag) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi > b.I) return;
+  if (gi == b.I) {
+    flag[gi] = 0;
+    return;
+  }
+  const InstrRec& r = b.ins[gi];
+  uint8_t c = C_NORMAL, sn = 0;
+  uint32_t t = kNone;
+  if (r.op == O_S_BRANCH) {
+    c = C_JMP;
+    t = r.target;
+  } else if (r.op == O_S_CBRANCH_SCC0 || r.op == O_S_CBRANCH_SCC1) {
+    c = C_CBR;
+    t = r.target;
+    sn = r.op == O_S_CBRANCH_SCC1;
+  } else if (r.op == O_S_ENDPGM) {
+    c = C_END;
+  }
+  b.ctl[gi] = c;
+  b.ltarget[gi] = t;
+  b.sense[gi] = sn;
+  flag[gi] = exec_form_op(r.op);
+}
+
+__global__ void k_exec_list(uint32_t I, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                            uint32_t* __restrict__ list) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi < I && flag[gi]) list[pos[gi]] = gi;
+}
+
+// per kernel: the exec-mask forms, matched over the kernel's exec-form
+// instructions only (in program order) with a stack of open forms
+__global__ void k_exec_forms(const __grid_constant__ Batch b, const uint32_t* __restrict__ pos,
+                             const uint32_t* __restrict__ list) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
@@ -573,16 +615,12 @@ __global__ void k_exec_forms(const __grid_constant__ Batch b) {
   uint8_t* ctl = b.ctl + K.first_instr;
   uint32_t* lt = b.ltarget + K.first_instr;
   uint8_t* sense = b.sense + K.first_instr;
-  uint32_t n = K.n_instr;
-  for (uint32_t i = 0; i < n; ++i) {
-    ctl[i] = C_NORMAL;
-    lt[i] = kNone;
-    sense[i] = 0;
-  }
+  const uint32_t c0 = pos[K.first_instr], c1 = pos[K.first_instr + K.n_instr];
   Form st[kMaxExecDepth];
   int sp = 0;
   bool bad = false;
-  for (uint32_t i = 0; i < n && !bad; ++i) {
+  for (uint32_t c = c0; c < c1 && !bad; ++c) {
+    const uint32_t i = list[c] - K.first_instr;
     const InstrRec& r = R[i];
     switch (r.op) {
       case O_S_AND_SAVEEXEC:
@@ -654,20 +692,7 @@ __global__ void k_exec_forms(const __grid_constant__ Batch b) {
     }
   }
   if (sp) bad = true;
-  if (bad) {
-    K.bad |= 4u;
-    return;
-  }
-  for (uint32_t i = 0; i < n; ++i) {
-    uint16_t op = R[i].op;
-    if (op == O_S_BRANCH) { ctl[i] = C_JMP; lt[i] = R[i].target; }
-    if (op == O_S_CBRANCH_SCC0 || op == O_S_CBRANCH_SCC1) {
-      ctl[i] = C_CBR;
-      lt[i] = R[i].target;
-      sense[i] = op == O_S_CBRANCH_SCC1;
-    }
-    if (op == O_S_ENDPGM) ctl[i] = C_END;
-  }
+  if (bad) K.bad |= 4u;
 }
 
 __device__ __forceinline__ uint32_t resolve_t(const uint8_t* ctl, uint32_t t, uint32_t n) {
@@ -741,7 +766,14 @@ __global__ void k_lblock_edges(const __grid_constant__ Batch b, const uint32_t* 
 void launch_logical(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
   const int T = 256;
   if (!b.I) return;
-  k_exec_forms<<<(b.K + 127) / 128, 128, 0, s>>>(b);
+  // pleader / lleader serve as flag and position arrays of the exec-form
+  // instructions until the logical leaders are computed
+  k_exec_init<<<(b.I + 1 + T - 1) / T, T, 0, s>>>(b, b.pleader);
+  ++launch_counter();
+  launch_scan(b.pleader, b.lleader, b.I + 1, 0, false, sc, nullptr, b.err, s);
+  k_exec_list<<<(b.I + T - 1) / T, T, 0, s>>>(b.I, b.pleader, b.lleader, b.exec_list);
+  ++launch_counter();
+  k_exec_forms<<<(b.K + 127) / 128, 128, 0, s>>>(b, b.lleader, b.exec_list);
   ++launch_counter();
   cudaMemsetAsync(b.pleader, 0, sizeof(uint32_t) * b.I, s);
   k_lleaders<<<(b.I + T - 1) / T, T, 0, s>>>(b);

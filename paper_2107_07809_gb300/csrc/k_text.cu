@@ -20,7 +20,7 @@ constexpr int LS_THREADS = 256;
 constexpr int LS_PER_THREAD = 64;
 constexpr int LS_TILE = LS_THREADS * LS_PER_THREAD;
 
-__global__ void __launch_bounds__(LS_THREADS) k_line_scan(const uint8_t* __restrict__ text, uint64_t n,
+__global__ void __launch_bounds__(LS_THREADS) k_line_scan(const uint8_t* __restrict__ text, uint64_t n, int use_bulk,
                                                           uint32_t* __restrict__ line_start,
                                                           uint64_t* __restrict__ status, uint32_t* counters,
                                                           uint32_t* err) {
@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(LS_THREADS) k_line_scan(const uint8_t* __restr
   const uint64_t base = (uint64_t)tile * LS_TILE;
   const uint64_t rem = n > base ? n - base : 0;
   const uint32_t nbytes = rem < (uint64_t)LS_TILE ? (uint32_t)rem : (uint32_t)LS_TILE;
-  const uint32_t bulk = nbytes & ~15u;  // TMA part: 16-byte multiple, 16-byte aligned source
+  // bulk-copy part: a 16-byte multiple from a 16-byte aligned source (a text
+  // that does not start 16-byte aligned is read with plain loads)
+  const uint32_t bulk = use_bulk ? (nbytes & ~15u) : 0u;
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
   const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
   if (threadIdx.x == 0 && bulk) {
@@ -108,7 +110,8 @@ void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uin
   if (!tiles) tiles = 1;
   cudaMemsetAsync(tile_status, 0, sizeof(uint64_t) * tiles, s);
   cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), s);
-  k_line_scan<<<tiles, LS_THREADS, 0, s>>>(text, n, line_start, tile_status, counters, err);
+  const int use_bulk = (reinterpret_cast<uintptr_t>(text) & 15u) == 0;
+  k_line_scan<<<tiles, LS_THREADS, 0, s>>>(text, n, use_bulk, line_start, tile_status, counters, err);
   ++launch_counter();
 }
 uint32_t line_scan_tiles(uint64_t n) { return (uint32_t)((n + LS_TILE - 1) / LS_TILE) + 1; }
@@ -245,7 +248,8 @@ __global__ void k_classify(const uint8_t* __restrict__ text, const uint32_t* __r
 // row type of every line: state from the last marker, kernel from the .kernel count
 __global__ void k_assign(const uint8_t* __restrict__ kind, const uint32_t* __restrict__ mkmax,
                          const uint32_t* __restrict__ fsmax, const uint32_t* __restrict__ kcnt, uint32_t L,
-                         uint8_t* __restrict__ rowtype, uint32_t* __restrict__ is_instr, uint32_t* __restrict__ is_label) {
+                         uint8_t* __restrict__ rowtype, uint32_t* __restrict__ is_instr, uint32_t* __restrict__ is_label,
+                         uint32_t* __restrict__ is_cfg) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L) return;
   uint8_t rt = RT_NONE;
@@ -263,12 +267,14 @@ __global__ void k_assign(const uint8_t* __restrict__ kind, const uint32_t* __res
   rowtype[i] = rt;
   is_instr[i] = rt == RT_INSTR;
   is_label[i] = rt == RT_LABEL;
+  is_cfg[i] = rt == RT_CFG;
 }
 
 __global__ void k_scatter_rows(const uint8_t* __restrict__ rowtype, const uint32_t* __restrict__ instr_excl,
-                               const uint32_t* __restrict__ label_excl, const uint32_t* __restrict__ kcnt, uint32_t L,
-                               uint32_t* __restrict__ instr_line, uint32_t* __restrict__ label_line,
-                               uint32_t* __restrict__ label_instr, KHdr* __restrict__ kh) {
+                               const uint32_t* __restrict__ label_excl, const uint32_t* __restrict__ cfg_excl,
+                               const uint32_t* __restrict__ kcnt, uint32_t L, uint32_t* __restrict__ instr_line,
+                               uint32_t* __restrict__ label_line, uint32_t* __restrict__ label_instr,
+                               uint32_t* __restrict__ cfg_line, KHdr* __restrict__ kh) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L) return;
   uint8_t rt = rowtype[i];
@@ -276,11 +282,14 @@ __global__ void k_scatter_rows(const uint8_t* __restrict__ rowtype, const uint32
   else if (rt == RT_LABEL) {
     label_line[label_excl[i]] = i;
     label_instr[label_excl[i]] = instr_excl[i];
+  } else if (rt == RT_CFG) {
+    cfg_line[cfg_excl[i]] = i;
   } else if (rt == RT_KERNEL) {
     KHdr& k = kh[kcnt[i] - 1];
     k.line = i;
     k.first_instr = instr_excl[i];
     k.first_label = label_excl[i];
+    k.first_cfg = cfg_excl[i];
   }
 }
 
@@ -297,17 +306,19 @@ void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, co
   launch_scan(ra.t0, ra.mkmax, L, 1, true, sc, nullptr, err, s);
   launch_scan(ra.t1, ra.fsmax, L, 1, true, sc, nullptr, err, s);
   launch_scan(ra.t2, ra.kcnt, L, 0, true, sc, &totals[0], err, s);  // totals[0] = kernels
-  k_assign<<<(L + T - 1) / T, T, 0, s>>>(ra.kind, ra.mkmax, ra.fsmax, ra.kcnt, L, ra.rowtype, ra.t0, ra.t1);
+  k_assign<<<(L + T - 1) / T, T, 0, s>>>(ra.kind, ra.mkmax, ra.fsmax, ra.kcnt, L, ra.rowtype, ra.t0, ra.t1, ra.t2);
   ++launch_counter();
   launch_scan(ra.t0, ra.instr_excl, L, 0, false, sc, &totals[1], err, s);  // totals[1] = instructions
   launch_scan(ra.t1, ra.label_excl, L, 0, false, sc, &totals[2], err, s);  // totals[2] = labels
+  launch_scan(ra.t2, ra.cfg_excl, L, 0, false, sc, &totals[14], err, s);   // totals[14] = configuration rows
 }
 
 void launch_scatter_rows(uint32_t L, RowArrays& ra, uint32_t* instr_line, uint32_t* label_line, uint32_t* label_instr,
-                         KHdr* kh, cudaStream_t s) {
+                         uint32_t* cfg_line, KHdr* kh, cudaStream_t s) {
   const int T = 256;
-  k_scatter_rows<<<(L + T - 1) / T, T, 0, s>>>(ra.rowtype, ra.instr_excl, ra.label_excl, ra.kcnt, L, instr_line,
-                                               label_line, label_instr, kh);
+  k_scatter_rows<<<(L + T - 1) / T, T, 0, s>>>(ra.rowtype, ra.instr_excl, ra.label_excl, ra.cfg_excl, ra.kcnt, L,
+                                               instr_line, label_line, label_instr, cfg_line, kh);
+  ++launch_counter();
 }
 
 }  // namespace gd
