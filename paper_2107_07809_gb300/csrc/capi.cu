@@ -370,7 +370,13 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   uint32_t* wl = W.get<uint32_t>("wl", (size_t)h->h_tot[9] + 8);
   uint64_t nbw = 3 * ((4ull * b.I + 63) / 32) + (b.NS + 63) / 32 + 4;
   uint32_t* bits = W.get<uint32_t>("reach_bits", nbw);
-  launch_analysis(b, wl, bits, nbw, s);
+  const uint64_t nvc = (uint64_t)b.NS + 4ull * b.I + 1;  // variable candidates (+ end)
+  uint32_t* vflag = W.get<uint32_t>("var_flag", nvc);
+  uint32_t* vpos = W.get<uint32_t>("var_pos", nvc);
+  ScanScratch scv = sc;
+  if (scan_tiles((uint32_t)nvc) + 64 > std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)) + 64)
+    scv.status = W.get<uint64_t>("tile_status_var", scan_tiles((uint32_t)nvc) + 64);
+  launch_analysis(b, wl, bits, nbw, blk_kern, vflag, vpos, scv, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[8], s));
   // S12

@@ -7,7 +7,8 @@
 // arguments fix the types of loads and scalars, instruction suffixes fix the
 // rest, bitwise operations and join versions take the join of their inputs in
 // the lattice none < {int, uint, float} < top32 (64-bit likewise), iterated to
-// the least fixed point.  One thread per kernel walks its nodes.
+// the least fixed point.  A warp (short kernels) or a thread block (long
+// kernels) walks a kernel's nodes.
 #include "k_analysis.cuh"
 
 namespace gd {
@@ -19,8 +20,8 @@ __device__ __forceinline__ uint32_t out_val(const Batch& b, const KHdr& K, uint3
 __device__ __forceinline__ uint32_t phi_blk(uint32_t r) { return (rid(r) >> 10) & 0x3FFFF; }
 __device__ __forceinline__ uint32_t phi_reg(uint32_t r) { return rid(r) & 0x3FF; }
 
-// Reachability and use counts, one warp per kernel.  Lanes pop up to 32
-// entries of the kernel's stack at a time; the first visit of a node or join
+// Reachability and use counts, one team per kernel.  Its threads pop up to
+// one entry each of the kernel's stack at a time; the first visit of a node or join
 // version is claimed with an atomic bit, use counts are atomic adds, so the
 // result does not depend on the order the lanes happen to take.
 __device__ __forceinline__ bool claim(uint32_t* bits, uint64_t g) {
@@ -28,14 +29,42 @@ __device__ __forceinline__ bool claim(uint32_t* bits, uint64_t g) {
   return !(atomicOr(&bits[g >> 5], m) & m);
 }
 
-__global__ void k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
+// Size buckets: a kernel of fewer than kBigKernel instructions is handled by
+// one warp (Team<true>), a longer one by a whole thread block (Team<false>);
+// both launches cover every kernel and a team leaves the kernels of the other
+// bucket alone.
+constexpr uint32_t kBigKernel = 4096;
+constexpr int kBigTeam = 512;
+
+template <bool WARP>
+struct Team {
+  static __device__ __forceinline__ uint32_t kid() {
+    return WARP ? blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32 : blockIdx.x;
+  }
+  static __device__ __forceinline__ uint32_t tid() { return WARP ? (threadIdx.x & 31u) : threadIdx.x; }
+  static __device__ __forceinline__ uint32_t size() { return WARP ? 32u : blockDim.x; }
+  static __device__ __forceinline__ uint32_t slot() { return WARP ? threadIdx.x / 32 : 0u; }
+  static __device__ __forceinline__ void sync() {
+    if (WARP) __syncwarp();
+    else __syncthreads();
+  }
+  static __device__ __forceinline__ bool any(bool p) {
+    if (WARP) return __any_sync(0xFFFFFFFFu, p);
+    return __syncthreads_or(p) != 0;
+  }
+  static __device__ __forceinline__ bool mine(const KHdr& K) { return (K.n_instr >= kBigKernel) != WARP; }
+};
+
+template <bool WARP>
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
                         uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits) {
+  using T = Team<WARP>;
   __shared__ uint32_t s_top[4], s_npl[4];
-  const uint32_t wid = threadIdx.x / 32, lane = threadIdx.x & 31u;
-  uint32_t k = blockIdx.x * (blockDim.x / 32) + wid;
+  const uint32_t wid = T::slot(), lane = T::tid(), TS = T::size();
+  uint32_t k = T::kid();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
-  if (K.bad) return;
+  if (K.bad || !T::mine(K)) return;
   KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint32_t* uses = b.uses + nb;
@@ -45,13 +74,13 @@ __global__ void k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ 
   uint32_t* pl = b.plist + K.state_off;
   const uint32_t nn = 4 * K.n_instr;
   const uint32_t cap = nn + K.n_lblock * K.R + 8;
-  for (uint32_t q = lane; q < nn; q += 32) uses[q] = 0;
-  for (size_t q = lane; q < (size_t)K.n_lblock * K.R; q += 32) pu[q] = 0;
+  for (uint32_t q = lane; q < nn; q += TS) uses[q] = 0;
+  for (size_t q = lane; q < (size_t)K.n_lblock * K.R; q += TS) pu[q] = 0;
   if (lane == 0) {
     s_top[wid] = 0;
     s_npl[wid] = 0;
   }
-  __syncwarp();
+  T::sync();
   auto push = [&](uint32_t r) {
     uint32_t at = atomicAdd(&s_top[wid], 1u);
     if (at < cap) wl[at] = r;
@@ -75,7 +104,7 @@ __global__ void k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ 
     if (claim(rbits, nb + id)) push(r & ~3u);
   };
   // roots: stores, loads, unsupported instructions (expanded), branch conditions (used)
-  for (uint32_t i = lane; i < K.n_instr; i += 32) {
+  for (uint32_t i = lane; i < K.n_instr; i += TS) {
     uint32_t gi = K.first_instr + i;
     uint32_t bl = b.lblock_of[gi];
     if (bl == kNone) continue;
@@ -87,16 +116,16 @@ __global__ void k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ 
     }
     if ((op_store(n.op) || op_gload(n.op) || n.op == O_UNKNOWN) && claim(rbits, nb + 4 * i)) push(mkref(4 * i, 0));
   }
-  __syncwarp();
+  T::sync();
   for (;;) {
     uint32_t top = s_top[wid];
     if (top > cap) top = cap;
-    uint32_t take = top < 32 ? top : 32;
+    uint32_t take = top < TS ? top : TS;
     if (!take) break;
     uint32_t r = lane < take ? wl[top - 1 - lane] : kTop;
-    __syncwarp();
+    T::sync();
     if (lane == 0) s_top[wid] = top - take;
-    __syncwarp();
+    T::sync();
     if (r != kTop) {
       if (r_phi(r)) {
         uint32_t B = (rid(r) >> 10) & 0x3FFFF, reg = rid(r) & 0x3FF;
@@ -114,10 +143,10 @@ __global__ void k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ 
         for (int q = 0; q < c; ++q) use(ch[q], blk);
       }
     }
-    __syncwarp();
+    T::sync();
   }
-  __syncwarp();
-  for (uint32_t q = lane; q < nn; q += 32) {
+  T::sync();
+  for (uint32_t q = lane; q < nn; q += TS) {
     uint64_t g = nb + q;
     uint32_t f = ((rbits[g >> 5] >> (g & 31)) & 1u) | (((cbits[g >> 5] >> (g & 31)) & 1u) << 1) |
                  (((ibits[g >> 5] >> (g & 31)) & 1u) << 2);
@@ -181,15 +210,17 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
   return TY_NONE;
 }
 
-// least fixed point of the type equations: one warp per kernel, lanes update
-// nodes and used join versions concurrently until a vote finds no change (the
-// equations are monotone, so every such iteration reaches the same solution)
-__global__ void k_types(const __grid_constant__ Batch b) {
-  uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  uint32_t lane = threadIdx.x & 31u;
+// least fixed point of the type equations: one team per kernel, its threads
+// update nodes and used join versions concurrently until a vote finds no
+// change (the equations are monotone, so every such iteration reaches the same
+// solution)
+template <bool WARP>
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_constant__ Batch b) {
+  using T = Team<WARP>;
+  const uint32_t k = T::kid(), lane = T::tid(), TS = T::size();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
-  if (K.bad) return;
+  if (K.bad || !T::mine(K)) return;
   KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint8_t* nt = b.ntype + nb;
@@ -197,17 +228,17 @@ __global__ void k_types(const __grid_constant__ Batch b) {
   uint8_t* pt = b.phi_type + K.state_off;
   const uint32_t* pl = b.plist + K.state_off;
   uint32_t nn = 4 * K.n_instr;
-  for (uint32_t q = lane; q < nn; q += 32) nt[q] = TY_NONE;
-  for (uint32_t q = lane; q < K.n_phis; q += 32) {
+  for (uint32_t q = lane; q < nn; q += TS) nt[q] = TY_NONE;
+  for (uint32_t q = lane; q < K.n_phis; q += TS) {
     uint32_t e = pl[q];
     pt[(size_t)(e >> 10) * K.R + (e & 0x3FF)] = TY_NONE;
   }
-  __syncwarp();
+  T::sync();
   bool changed = true;
   int guard = 0;
   while (changed && guard++ < 100000) {
     bool ch = false;
-    for (uint32_t id = lane; id < nn; id += 32) {
+    for (uint32_t id = lane; id < nn; id += TS) {
       if (!(fl[id] & 1)) continue;
       uint8_t t = tjoin(nt[id], node_type(v, nt, pt, id));
       if (t != nt[id]) {
@@ -215,8 +246,8 @@ __global__ void k_types(const __grid_constant__ Batch b) {
         ch = true;
       }
     }
-    __syncwarp();
-    for (uint32_t q = lane; q < K.n_phis; q += 32) {
+    T::sync();
+    for (uint32_t q = lane; q < K.n_phis; q += TS) {
       uint32_t e = pl[q];
       uint32_t B = e >> 10, reg = e & 0x3FF;
       size_t slot = (size_t)B * K.R + reg;
@@ -228,8 +259,8 @@ __global__ void k_types(const __grid_constant__ Batch b) {
         ch = true;
       }
     }
-    __syncwarp();
-    changed = __any_sync(0xFFFFFFFFu, ch);
+    T::sync();
+    changed = T::any(ch);
   }
   if (changed && lane == 0) atomicOr(b.err, ERR_CAPACITY);
 }
@@ -243,69 +274,96 @@ __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses
   return uses[id] >= 2 || (fl[id] & 6);
 }
 
-// variable numbers: per block its join versions (by register), then its nodes
-// by (instruction, slot); this is the order of their program points.  One warp
-// per kernel: lanes test 32 candidates at a time, a ballot numbers them in order.
-__global__ void k_vars(const __grid_constant__ Batch b) {
-  uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  uint32_t lane = threadIdx.x & 31u;
-  if (k >= b.K) return;
-  KHdr& K = b.kh[k];
+// Variable numbers: per block its join versions (by register), then its
+// nodes by (instruction, slot); this is the order of their program points.
+// Every candidate gets a position in that order inside its kernel's range of
+// a batch-wide array (join version r of block bl at bl*R + 4*first(bl) + r,
+// node slot s of instruction i of block bl at (bl+1)*R + 4*i + s; the range of
+// kernel k starts at state_off + 4*first_instr), a flag is set for each
+// variable, and one exclusive scan numbers them all.
+__device__ __forceinline__ size_t vbase(const KHdr& K) { return (size_t)K.state_off + 4 * (size_t)K.first_instr; }
+
+__global__ void k_var_flag_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ vflag) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 4ull * b.I) return;
+  const uint32_t gi = (uint32_t)(g >> 2), s = (uint32_t)(g & 3);
+  const uint32_t k = b.ikern[gi];
+  const KHdr& K = b.kh[k];
   if (K.bad) return;
-  KView v = make_view(b, K, k);
+  const uint32_t bl = b.lblock_of[gi];
+  if (bl == kNone) return;
+  const KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
-  int32_t* vo = b.var_of + nb;
-  const uint32_t* uses = b.uses + nb;
-  const uint8_t* fl = b.nflag + nb;
-  const uint8_t* nt = b.ntype + nb;
-  int32_t* pv = b.phi_var + K.state_off;
-  const uint8_t* pu = b.phi_used + K.state_off;
-  const uint8_t* pt = b.phi_type + K.state_off;
-  uint8_t* vt = b.var_type + nb + K.state_off;
-  for (uint32_t q = lane; q < 4 * K.n_instr; q += 32) vo[q] = -1;
-  __syncwarp();
-  int32_t n = 0;
-  const unsigned below = (1u << lane) - 1u;
-  for (uint32_t bl = 0; bl < K.n_lblock; ++bl) {
-    for (uint32_t r0 = 0; r0 < K.R; r0 += 32) {
-      uint32_t r = r0 + lane;
-      size_t q = (size_t)bl * K.R + r;
-      bool used = r < K.R && pu[q];
-      unsigned m = __ballot_sync(0xFFFFFFFFu, used);
-      if (r < K.R) {
-        if (used) {
-          int32_t x = n + __popc(m & below);
-          pv[q] = x;
-          vt[x] = tresolve(pt[q], 32);
-        } else {
-          pv[q] = -1;
-        }
-      }
-      n += __popc(m);
-    }
-    const BlockRec& B = b.lblocks[K.first_lblock + bl];
-    for (uint32_t i0 = B.first; i0 < B.end; i0 += 8) {  // 8 instructions = 32 slots
-      uint32_t i = i0 + lane / 4, s = lane & 3u;
-      uint32_t id = 4 * i + s;
-      bool inb = i < B.end;
-      bool mine = inb && b.lblock_of[K.first_instr + i] == bl;
-      bool isv = mine && is_var_node(v, uses, fl, id);
-      unsigned m = __ballot_sync(0xFFFFFFFFu, isv);
-      if (mine) {
-        if (isv) {
-          int32_t x = n + __popc(m & below);
-          vo[id] = x;
-          vt[x] = tresolve(nt[id], node_width(v, id));
-        } else {
-          vo[id] = -1;
-        }
-      } else if (inb) {
-        vo[id] = -1;
-      }
-      n += __popc(m);
+  const uint32_t id = (uint32_t)(g - nb);
+  if (is_var_node(v, b.uses + nb, b.nflag + nb, id))
+    vflag[vbase(K) + (size_t)(bl + 1) * K.R + id] = 1;  // id = 4 * i + s
+}
+
+__global__ void k_var_flag_joins(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern,
+                                 uint32_t* __restrict__ vflag) {
+  const uint32_t gb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gb >= b.NLB) return;
+  const uint32_t k = blk_kern[gb];
+  const KHdr& K = b.kh[k];
+  if (K.bad) return;
+  const uint32_t bl = gb - K.first_lblock;
+  const uint8_t* pu = b.phi_used + K.state_off + (size_t)bl * K.R;
+  uint32_t* f = vflag + vbase(K) + (size_t)bl * K.R + 4 * (size_t)b.lblocks[gb].first;
+  for (uint32_t r = 0; r < K.R; ++r)
+    if (pu[r]) f[r] = 1;
+}
+
+__global__ void k_var_nodes(const __grid_constant__ Batch b, const uint32_t* __restrict__ vflag,
+                            const uint32_t* __restrict__ vpos) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 4ull * b.I) return;
+  const uint32_t gi = (uint32_t)(g >> 2);
+  const uint32_t k = b.ikern[gi];
+  const KHdr& K = b.kh[k];
+  if (K.bad) return;
+  const size_t nb = 4 * (size_t)K.first_instr;
+  const uint32_t id = (uint32_t)(g - nb);
+  const uint32_t bl = b.lblock_of[gi];
+  int32_t x = -1;
+  if (bl != kNone) {
+    const size_t at = vbase(K) + (size_t)(bl + 1) * K.R + id;
+    if (vflag[at]) {
+      x = (int32_t)(vpos[at] - vpos[vbase(K)]);
+      const KView v = make_view(b, K, k);
+      b.var_type[nb + K.state_off + x] = tresolve(b.ntype[nb + id], node_width(v, id));
     }
   }
-  if (lane == 0) K.n_vars = (uint32_t)n;
+  b.var_of[nb + id] = x;
+}
+
+__global__ void k_var_joins(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern,
+                            const uint32_t* __restrict__ vflag, const uint32_t* __restrict__ vpos) {
+  const uint32_t gb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gb >= b.NLB) return;
+  const uint32_t k = blk_kern[gb];
+  const KHdr& K = b.kh[k];
+  if (K.bad) return;
+  const uint32_t bl = gb - K.first_lblock;
+  const size_t q0 = (size_t)bl * K.R;
+  const size_t at0 = vbase(K) + q0 + 4 * (size_t)b.lblocks[gb].first;
+  const uint32_t p0 = vpos[vbase(K)];
+  const size_t nb = 4 * (size_t)K.first_instr;
+  for (uint32_t r = 0; r < K.R; ++r) {
+    int32_t x = -1;
+    if (vflag[at0 + r]) {
+      x = (int32_t)(vpos[at0 + r] - p0);
+      b.var_type[nb + K.state_off + x] = tresolve(b.phi_type[K.state_off + q0 + r], 32);
+    }
+    b.phi_var[K.state_off + q0 + r] = x;
+  }
+}
+
+__global__ void k_var_count(const __grid_constant__ Batch b, const uint32_t* __restrict__ vpos) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KHdr& K = b.kh[k];
+  const size_t end = k + 1 < b.K ? vbase(b.kh[k + 1]) : (size_t)b.NS + 4 * (size_t)b.I;
+  K.n_vars = K.bad ? 0u : vpos[end] - vpos[vbase(K)];
 }
 
 __global__ void k_wl_size(const __grid_constant__ Batch b, uint32_t* __restrict__ sz) {
@@ -370,17 +428,39 @@ void launch_node_cache(Batch& b, cudaStream_t s) {
   ++launch_counter();
 }
 
-void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, cudaStream_t s) {
+void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, const uint32_t* blk_kern,
+                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, cudaStream_t s) {
   if (!b.K) return;
   // four bitmaps: reached nodes, cross-block uses, join inputs (4I bits each), used joins (NS bits)
   uint64_t wn = (4ull * b.I + 63) / 32;
   uint32_t *rb = bits, *cb = bits + wn, *ib = bits + 2 * wn, *pb = bits + 3 * wn;
   cudaMemsetAsync(bits, 0, sizeof(uint32_t) * nbits_words, s);
-  k_reach<<<(b.K + 3) / 4, 128, 0, s>>>(b, wl, rb, cb, ib, pb);
-  ++launch_counter();
-  k_types<<<(b.K + 3) / 4, 128, 0, s>>>(b);
-  ++launch_counter();
-  k_vars<<<(b.K + 3) / 4, 128, 0, s>>>(b);
+  k_reach<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl, rb, cb, ib, pb);
+  k_reach<false><<<b.K, kBigTeam, 0, s>>>(b, wl, rb, cb, ib, pb);
+  k_types<true><<<(b.K + 3) / 4, 128, 0, s>>>(b);
+  k_types<false><<<b.K, kBigTeam, 0, s>>>(b);
+  launch_counter() += 4;
+  // variable numbers over the candidate array of NS + 4I positions
+  const uint64_t nc = (uint64_t)b.NS + 4ull * b.I;
+  cudaMemsetAsync(vflag, 0, sizeof(uint32_t) * (nc + 1), s);
+  if (b.I) {
+    k_var_flag_nodes<<<(uint32_t)((4ull * b.I + 255) / 256), 256, 0, s>>>(b, vflag);
+    ++launch_counter();
+  }
+  if (b.NLB) {
+    k_var_flag_joins<<<(b.NLB + 127) / 128, 128, 0, s>>>(b, blk_kern, vflag);
+    ++launch_counter();
+  }
+  launch_scan(vflag, vpos, (uint32_t)(nc + 1), 0, false, sc, nullptr, b.err, s);
+  if (b.I) {
+    k_var_nodes<<<(uint32_t)((4ull * b.I + 255) / 256), 256, 0, s>>>(b, vflag, vpos);
+    ++launch_counter();
+  }
+  if (b.NLB) {
+    k_var_joins<<<(b.NLB + 127) / 128, 128, 0, s>>>(b, blk_kern, vflag, vpos);
+    ++launch_counter();
+  }
+  k_var_count<<<(b.K + 127) / 128, 128, 0, s>>>(b, vpos);
   ++launch_counter();
 }
 
