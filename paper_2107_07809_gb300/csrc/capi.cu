@@ -381,11 +381,12 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   CK(cudaEventRecord(h->ev[8], s));
   // S12
   b.rg = W.get<uint32_t>("regions", 12ull * kRegionsPerBlock * b.NLB + 24);
-  uint32_t* seen = W.get<uint32_t>("rg_seen", (size_t)kRegionsPerBlock * b.NLB + 2);
+  // region reduction work: 64 words per block + 128 per kernel (red_work_words)
+  uint32_t* rwork = W.get<uint32_t>("rg_work", 64ull * b.NLB + 128ull * b.K + 64);
   uint32_t* rstk = W.get<uint32_t>("rg_stack", (size_t)kStackPerBlock * b.NLB + 4);
   uint8_t* alive = W.get<uint8_t>("rg_alive", (size_t)kRegionsPerBlock * b.NLB + 2);
   uint8_t* cond = W.get<uint8_t>("rg_cond", b.NLB + 1);
-  launch_regions(b, seen, rstk, alive, cond, s);
+  launch_regions(b, rwork, rstk, alive, cond, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[9], s));
   // S13: layout (count, scan, write), item sizes, scan, item text

@@ -151,7 +151,7 @@ void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_word
                      uint32_t* vflag, uint32_t* vpos, ScanScratch sc, cudaStream_t s);
 
 // k_region.cu
-void launch_regions(Batch& b, uint32_t* seen, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s);
+void launch_regions(Batch& b, uint32_t* work, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s);
 
 // k_emit.cu
 struct Item {

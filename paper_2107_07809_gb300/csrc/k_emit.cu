@@ -20,6 +20,7 @@
 // there made the emission kernel megabytes long (instruction-cache bound).
 #define GD_MATCH_INLINE __noinline__
 #include "k_analysis.cuh"
+#include "region_red.cuh"
 
 namespace gd {
 
@@ -663,9 +664,6 @@ struct Em {
   }
 };
 
-enum : uint32_t { R_BLOCK = 0, R_SEQ = 1, R_IF = 2, R_IFELSE = 3, R_LOOP = 4 };
-enum { RG_KIND = 0, RG_NCH = 1, RG_CH = 2, RG_BLOCK = 6, RG_S0 = 7, RG_S1 = 8, RG_NPRED = 9, RG_HEAD = 10, RG_TAIL = 11 };
-constexpr int RGW = 12;
 
 __device__ void print_args(Wr& w, const Batch& b, const KHdr& K, const ArgRec* A) {
   bool any = false;
