@@ -394,18 +394,36 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   uint32_t* icnt = W.get<uint32_t>("item_cnt", b.K + 1);
   uint32_t* ibase = W.get<uint32_t>("item_base", b.K + 1);
   const uint32_t* pbits = bits + 3 * ((4ull * b.I + 63) / 32);  // used join versions (reachability)
-  launch_layout(b, nullptr, nullptr, icnt, wl, rstk, pbits, 0, s);
+  // copies on every CFG edge into a join block
+  b.cs_off = W.get<uint32_t>("cs_off", 2ull * b.NLB + 1);
+  b.cs_cnt = W.get<uint32_t>("cs_cnt", 2ull * b.NLB + 1);
+  b.cs_cyc = W.get<uint8_t>("cs_cyc", 2ull * b.NLB + 1);
+  launch_copy_sets(b, blk_kern, pbits, b.cs_cnt, 0, s);  // bounds, then their scan
+  if (b.NLB) launch_scan(b.cs_cnt, b.cs_off, 2 * b.NLB + 1, 0, false, sc, &tot[10], b.err, s);
+  // layout slices: bounds and their scan (the total has a host-side bound)
+  uint32_t* loff = W.get<uint32_t>("layout_off", b.K + 1);
+  launch_layout(b, nullptr, loff, nullptr, nullptr, 0, s);
+  if (b.K) launch_scan(loff, loff, b.K, 0, false, sc, &tot[14], b.err, s);
+  CK(cudaGetLastError());
+  sync_totals();
+  const uint32_t NCS = b.NLB ? h->h_tot[10] : 0;
+  const uint32_t LUB = b.K ? h->h_tot[14] : 0;
+  b.cs_reg = W.get<uint32_t>("cs_reg", (size_t)NCS + 1);
+  uint32_t* cs_src = W.get<uint32_t>("cs_src", (size_t)NCS + 1);
+  launch_copy_sets(b, blk_kern, pbits, cs_src, 1, s);
+  Item* lstage = W.get<Item>("layout_stage", (size_t)LUB + 1);
+  launch_layout(b, lstage, loff, icnt, rstk, 1, s);
   if (b.K) launch_scan(icnt, ibase, b.K, 0, false, sc, &tot[10], b.err, s);
   CK(cudaGetLastError());
   sync_totals();
   uint32_t NI = b.K ? h->h_tot[10] : 0;
   Item* items = W.get<Item>("items", (size_t)NI + 1);
+  launch_items_place(lstage, loff, b.K, LUB, icnt, ibase, items, s);
   uint32_t* iw = W.get<uint32_t>("item_weight", (size_t)NI + 1);
   uint32_t* sub0 = W.get<uint32_t>("item_sub0", (size_t)NI + 1);
   uint32_t* pflag = W.get<uint32_t>("print_flag", (size_t)b.I + 1);
   uint32_t* prank = W.get<uint32_t>("print_rank", (size_t)b.I + 1);
   uint32_t* plist = W.get<uint32_t>("print_instr", (size_t)b.I + 1);
-  launch_layout(b, items, ibase, icnt, wl, rstk, pbits, 1, s);
   launch_print_list(b, pflag, nullptr, nullptr, 0, s);
   launch_scan(pflag, prank, b.I + 1, 0, false, sc, nullptr, b.err, s);
   launch_print_list(b, pflag, prank, plist, 1, s);

@@ -113,6 +113,7 @@ struct KHdr {
   uint32_t first_lblock, n_lblock;
   uint32_t dims, cws[3], sgprs, vgprs, useargs, nargs, nuser;
   uint32_t R, nspill;
+  uint32_t entry_target;          // some block branches to the entry block
   uint32_t state_off;             // into block x register arrays
   uint32_t region_off;            // into region arrays (2 per block)
   uint32_t wl_off;                // into the reachability worklist

@@ -105,6 +105,10 @@ struct Batch {
   // emission
   uint32_t* kout_len;            // K (text length of each kernel incl. separator)
   uint32_t* kout_off;            // K (exclusive scan)
+  uint32_t* cs_off;              // 2 NLB + 1: copies on each CFG edge (2 per logical block)
+  uint32_t* cs_cnt;              // 2 NLB
+  uint8_t* cs_cyc;               // 2 NLB: the copies form a cycle
+  uint32_t* cs_reg;              // registers of the copies, in printing order
   uint8_t* out;                  // output text
   uint64_t* file_out_off;        // F + 1
   int32_t* file_status;          // F
@@ -159,8 +163,12 @@ struct Item {
   uint32_t k;   // kernel
   uint32_t a, b;
 };
-void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* item_cnt, uint32_t* scratch,
-                   uint32_t* stk, const uint32_t* pbits, int write, cudaStream_t s);
+void launch_copy_sets(Batch& b, const uint32_t* blk_kern, const uint32_t* pbits, uint32_t* bound_or_tmp, int phase,
+                      cudaStream_t s);
+void launch_layout(Batch& b, Item* stage, uint32_t* stage_off, uint32_t* item_cnt, uint32_t* stk, int phase,
+                   cudaStream_t s);
+void launch_items_place(const Item* stage, const uint32_t* stage_off, uint32_t K, uint32_t total,
+                        const uint32_t* item_cnt, const uint32_t* item_base, Item* items, cudaStream_t s);
 constexpr uint32_t kEmitSlot = 256;  // staging bytes per emission sub-item
 void launch_print_list(Batch& b, uint32_t* flag, const uint32_t* rank, uint32_t* list, int phase, cudaStream_t s);
 void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* prank, uint32_t* weight,

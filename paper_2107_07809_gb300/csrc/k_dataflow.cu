@@ -113,25 +113,29 @@ __device__ __forceinline__ bool defines_vcc(const InstrRec& r) {
 // ---------------------------------------------------------------------------
 // sizes: spill slots, register count, limits
 // ---------------------------------------------------------------------------
+// spill slots: the largest scratch offset of a buffer load/store (thread per instruction)
+__global__ void k_df_spill(const __grid_constant__ Batch b) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const InstrRec& r = b.ins[gi];
+  if (r.op == O_BUFFER_LOAD_DWORD || r.op == O_BUFFER_STORE_DWORD) atomicMax(&b.kh[b.ikern[gi]].nspill, r.imm / 4 + 1);
+}
+
+// the entry block may not be the target of a branch (thread per logical block)
+__global__ void k_df_entry(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.NLB) return;
+  const BlockRec& B = b.lblocks[g];
+  if (B.succ0 == 0 || B.succ1 == 0) atomicOr(&b.kh[blk_kern[g]].entry_target, 1u);
+}
+
 __global__ void k_df_sizes(const __grid_constant__ Batch b, uint32_t* __restrict__ kstate) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
-  uint32_t ns = 0;
-  for (uint32_t i = 0; i < K.n_instr; ++i) {
-    const InstrRec& r = b.ins[K.first_instr + i];
-    if (r.op == O_BUFFER_LOAD_DWORD || r.op == O_BUFFER_STORE_DWORD) ns = max(ns, r.imm / 4 + 1);
-  }
-  K.nspill = ns;
-  K.R = K.vgprs + K.sgprs + 2 + ns;
+  K.R = K.vgprs + K.sgprs + 2 + K.nspill;
   if (!K.bad && (K.R > kMaxRegs || K.n_lblock >= kMaxBlocks || K.n_instr >= (1u << 26))) K.bad |= 16u;
-  if (!K.bad && K.n_lblock) {
-    // the entry block may not be the target of a branch
-    for (uint32_t q = 0; q < K.n_lblock; ++q) {
-      const BlockRec& B = b.lblocks[K.first_lblock + q];
-      if (B.succ0 == 0 || B.succ1 == 0) K.bad |= 32u;
-    }
-  }
+  if (!K.bad && K.n_lblock && K.entry_target) K.bad |= 32u;
   kstate[k] = K.bad ? 0u : K.n_lblock * K.R;
 }
 
@@ -593,6 +597,14 @@ __global__ void k_bits_size(const __grid_constant__ Batch b, uint32_t* __restric
 void launch_df_counts(Batch& b, DfScratch& d, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
   const int T = 256;
   if (!b.K) return;
+  if (b.I) {
+    k_df_spill<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+    ++launch_counter();
+  }
+  if (b.NLB) {
+    k_df_entry<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, d.blk_kern);
+    ++launch_counter();
+  }
   k_df_sizes<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kstate);
   ++launch_counter();
   k_bits_size<<<(b.K + 127) / 128, 128, 0, s>>>(b, d.kbits);

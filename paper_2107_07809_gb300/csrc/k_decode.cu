@@ -168,6 +168,8 @@ __global__ void k_config(const __grid_constant__ Batch b) {
   K.nuser = 0;
   K.bad = 0;
   K.partial = 0;
+  K.nspill = 0;
+  K.entry_target = 0;
   K.status = 0;
   ArgRec* A = b.args + (size_t)k * kMaxArgs;
   K.n_cfg = (k + 1 < b.K ? b.kh[k + 1].first_cfg : b.NC) - K.first_cfg;

@@ -203,8 +203,6 @@ struct Em {
   const int32_t* vo;
   const int32_t* pv;
   const uint8_t* vt;
-  uint32_t* scratch;  // per-kernel: copies list (3 words per pending copy)
-  uint32_t scap;      // its capacity in words
   Wr w;
   bool partial;
   bool deep;
@@ -581,54 +579,6 @@ struct Em {
     w.s(";\n");
   }
 
-  // assignments of the join versions of block s along the edge p -> s
-  __device__ void copies(uint32_t p, uint32_t s, int lvl) {
-    uint32_t R = K->R;
-    uint32_t m = 0;
-    const uint8_t* pu = b->phi_used + K->state_off;
-    for (uint32_t reg = 0; reg < R; ++reg) {
-      if (!pu[(size_t)s * R + reg]) continue;
-      uint32_t dst = phiref(s, reg);
-      uint32_t o = b->st_out[K->state_off + (size_t)p * R + reg];
-      uint32_t src = fwd(v, o == kTop ? kUndef : o);
-      if (src == dst || src == kUndef) continue;
-      if (3 * (m + 1) > scap) {
-        atomicOr(b->err, ERR_CAPACITY);
-        break;
-      }
-      scratch[3 * m] = reg;
-      scratch[3 * m + 1] = dst;
-      scratch[3 * m + 2] = src;
-      ++m;
-    }
-    while (m) {
-      uint32_t pick = m;
-      for (uint32_t k = 0; k < m && pick == m; ++k) {
-        bool read = false;
-        for (uint32_t q = 0; q < m; ++q)
-          if (q != k && scratch[3 * q + 2] == scratch[3 * k + 1]) read = true;
-        if (!read) pick = k;
-      }
-      if (pick == m) {
-        partial = true;
-        pick = 0;
-      }
-      uint32_t dst = scratch[3 * pick + 1], src = scratch[3 * pick + 2];
-      int32_t x = phivar(dst);
-      w.indent(lvl);
-      w.s("var");
-      w.u64((uint64_t)x);
-      w.s(" = ");
-      E(src, vt[x], 0);
-      w.s(";\n");
-      for (uint32_t q = pick; q + 1 < m; ++q) {
-        scratch[3 * q] = scratch[3 * q + 3];
-        scratch[3 * q + 1] = scratch[3 * q + 4];
-        scratch[3 * q + 2] = scratch[3 * q + 5];
-      }
-      --m;
-    }
-  }
 
   // condition under which block t's terminator goes to block dst
   __device__ __noinline__ void cond_to(uint32_t t, uint32_t dst) {
@@ -691,116 +641,160 @@ __device__ void print_args(Wr& w, const Batch& b, const KHdr& K, const ArgRec* A
 // write at scanned offsets); one thread per item sizes it and, after a scan,
 // writes it
 // ---------------------------------------------------------------------------
-enum : uint32_t { IT_NONE = 0, IT_HEAD, IT_DECLS, IT_BLOCK, IT_COPY, IT_IF, IT_ELSE, IT_CLOSE, IT_DO, IT_WHILE,
+enum : uint32_t { IT_NONE = 0, IT_HEAD, IT_DECLS, IT_BLOCK, IT_COPYSET, IT_IF, IT_ELSE, IT_CLOSE, IT_DO, IT_WHILE,
                   IT_TAIL, IT_FAIL };
 constexpr uint32_t kDeclChunk = 64;
+
+// ---------------------------------------------------------------------------
+// Copies on the edges into join blocks.  For CFG edge e = 2 * (global block p)
+// + q (q = 0: succ0, 1: succ1) into block s: the used join versions of s
+// whose incoming value along the edge differs from the version itself, in an
+// order where no copy overwrites a version that a later copy still reads (a
+// cycle marks the kernel partial when the edge is printed).  One thread per
+// edge; the layout refers to an edge's copies as one item.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t next_used_bit(const uint32_t* pbits, uint64_t base, uint32_t reg, uint32_t R) {
+  while (reg < R) {
+    uint64_t g = base + reg;
+    uint32_t w = pbits[g >> 5] >> (g & 31);
+    if (w) {
+      uint32_t r = reg + (uint32_t)(__ffs(w) - 1);
+      return r < R ? r : R;
+    }
+    reg += 32 - (uint32_t)(g & 31);
+  }
+  return R;
+}
+
+// upper bound of the copies of each edge: the used join versions of its target
+__global__ void k_copy_bound(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern,
+                             const uint32_t* __restrict__ pbits, uint32_t* __restrict__ bound) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e > 2 * b.NLB) return;
+  if (e == 2 * b.NLB) {  // the end of the scanned array
+    bound[e] = 0;
+    return;
+  }
+  const uint32_t g = e >> 1;
+  const KHdr& K = b.kh[blk_kern[g]];
+  const BlockRec& B = b.lblocks[g];
+  const uint32_t s = (e & 1) ? B.succ1 : B.succ0;
+  uint32_t c = 0;
+  if (!K.bad && s != kNone) {
+    const uint64_t base = (uint64_t)K.state_off + (uint64_t)s * K.R;
+    for (uint32_t r = next_used_bit(pbits, base, 0, K.R); r < K.R; r = next_used_bit(pbits, base, r + 1, K.R)) ++c;
+  }
+  bound[e] = c;
+}
+
+__global__ void k_copy_sets(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern,
+                            const uint32_t* __restrict__ pbits, uint32_t* __restrict__ src_tmp) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * b.NLB) return;
+  const uint32_t g = e >> 1;
+  const uint32_t k = blk_kern[g];
+  const KHdr& K = b.kh[k];
+  const BlockRec& B = b.lblocks[g];
+  const uint32_t s = (e & 1) ? B.succ1 : B.succ0;
+  uint32_t m = 0;
+  uint8_t cyc = 0;
+  if (!K.bad && s != kNone) {
+    const KView v = make_view(b, K, k);
+    const uint32_t p = g - K.first_lblock, R = K.R, off = b.cs_off[e];
+    uint32_t* reg_of = b.cs_reg + off;  // candidates, then the printing order
+    uint32_t* src_of = src_tmp + off;
+    const uint64_t base = (uint64_t)K.state_off + (uint64_t)s * R;
+    for (uint32_t r = next_used_bit(pbits, base, 0, R); r < R; r = next_used_bit(pbits, base, r + 1, R)) {
+      const uint32_t o = b.st_out[K.state_off + (size_t)p * R + r];
+      const uint32_t src = fwd(v, o == kTop ? kUndef : o);
+      if (src == phiref(s, r) || src == kUndef) continue;
+      reg_of[m] = r;
+      src_of[m] = src;
+      ++m;
+    }
+    // sequentialise: repeatedly take the first copy whose destination no
+    // other pending copy reads; the chosen order is written back in place
+    uint32_t done = 0;
+    while (done < m) {
+      uint32_t pick = m;
+      for (uint32_t q = done; q < m && pick == m; ++q) {
+        const uint32_t dq = phiref(s, reg_of[q]);
+        bool read = false;
+        for (uint32_t x = done; x < m && !read; ++x)
+          if (x != q && src_of[x] == dq) read = true;
+        if (!read) pick = q;
+      }
+      if (pick == m) {
+        cyc = 1;
+        pick = done;
+      }
+      const uint32_t rr = reg_of[pick], ss = src_of[pick];
+      for (uint32_t x = pick; x > done; --x) {  // keep the others in order
+        reg_of[x] = reg_of[x - 1];
+        src_of[x] = src_of[x - 1];
+      }
+      reg_of[done] = rr;
+      src_of[done] = ss;
+      ++done;
+    }
+  }
+  b.cs_cnt[e] = m;
+  b.cs_cyc[e] = cyc;
+}
+
+// ---------------------------------------------------------------------------
+// Layout: one thread per kernel walks the region tree once and writes the
+// kernel's items into its slice of a staging array (size bounded by
+// layout_bound), counting them; a scan places the kernels and a copy compacts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t layout_bound(const KHdr& K) {
+  return 4 + (K.n_vars + kDeclChunk - 1) / kDeclChunk + 4 * kRegionsPerBlock * K.n_lblock;
+}
+
+__global__ void k_layout_bound(const __grid_constant__ Batch b, uint32_t* __restrict__ bound) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < b.K) bound[k] = layout_bound(b.kh[k]);
+}
 
 struct LayoutCtx {
   const Batch* b;
   KHdr* K;
-  KView v;
+  const BlockRec* BL;
   Item* items;
-  uint32_t base, n;
-  bool write;
-  uint32_t* scratch;
-  uint32_t scap;
+  uint32_t n, cap, k;
+  bool over;
   __device__ void put(uint32_t kind, uint32_t lvl, uint32_t a, uint32_t bb) {
-    if (write) items[base + n] = Item{kind | (lvl << 8), v.k, a, bb};
+    if (n < cap) items[n] = Item{kind | (lvl << 8), k, a, bb};
+    else over = true;
     ++n;
   }
-  // the copies along p -> s, in an order where no copy overwrites a version
-  // that a later copy still reads (a cycle marks the kernel partial)
-  const uint32_t* pbits;  // used join versions, bit (state_off + block * R + reg)
-  // next used join version of block s at a register >= reg (or R)
-  __device__ uint32_t next_used(uint32_t s, uint32_t reg) const {
-    const KHdr& Kr = *K;
-    uint64_t base = (uint64_t)Kr.state_off + (uint64_t)s * Kr.R;
-    while (reg < Kr.R) {
-      uint64_t g = base + reg;
-      uint32_t w = pbits[g >> 5] >> (g & 31);
-      if (w) {
-        uint32_t r = reg + (uint32_t)(__ffs(w) - 1);
-        return r < Kr.R ? r : Kr.R;
-      }
-      reg += 32 - (uint32_t)(g & 31);
-    }
-    return Kr.R;
+  __device__ uint32_t edge(uint32_t p, uint32_t s) const {
+    return 2 * (K->first_lblock + p) + (BL[p].succ0 == s ? 0u : 1u);
   }
+  __device__ uint32_t ncopies(uint32_t p, uint32_t s) const { return b->cs_cnt[edge(p, s)]; }
   __device__ void copies(uint32_t p, uint32_t s, uint32_t lvl) {
-    const KHdr& Kr = *K;
-    uint32_t R = Kr.R, m = 0;
-    for (uint32_t reg = next_used(s, 0); reg < R; reg = next_used(s, reg + 1)) {
-      uint32_t dst = phiref(s, reg);
-      uint32_t o = b->st_out[Kr.state_off + (size_t)p * R + reg];
-      uint32_t src = fwd(v, o == kTop ? kUndef : o);
-      if (src == dst || src == kUndef) continue;
-      if (!write) {
-        ++m;
-        continue;
-      }
-      if (2 * (m + 1) > scap) {
-        atomicOr(b->err, ERR_CAPACITY);
-        break;
-      }
-      scratch[2 * m] = reg;
-      scratch[2 * m + 1] = src;
-      ++m;
-    }
-    if (!write) {
-      n += m;
-      return;
-    }
-    while (m) {
-      uint32_t pick = m;
-      for (uint32_t k = 0; k < m && pick == m; ++k) {
-        uint32_t dk = phiref(s, scratch[2 * k]);
-        bool read = false;
-        for (uint32_t q = 0; q < m && !read; ++q)
-          if (q != k && scratch[2 * q + 1] == dk) read = true;
-        if (!read) pick = k;
-      }
-      if (pick == m) {
-        atomicOr(&K->partial, 1u);
-        pick = 0;
-      }
-      put(IT_COPY, lvl, (s << 10) | scratch[2 * pick], p);
-      for (uint32_t q = pick; q + 1 < m; ++q) {
-        scratch[2 * q] = scratch[2 * q + 2];
-        scratch[2 * q + 1] = scratch[2 * q + 3];
-      }
-      --m;
-    }
-  }
-  __device__ uint32_t ncopies(uint32_t p, uint32_t s) {
-    const KHdr& Kr = *K;
-    uint32_t c = 0;
-    for (uint32_t reg = next_used(s, 0); reg < Kr.R; reg = next_used(s, reg + 1)) {
-      uint32_t o = b->st_out[Kr.state_off + (size_t)p * Kr.R + reg];
-      uint32_t src = fwd(v, o == kTop ? kUndef : o);
-      if (src != phiref(s, reg) && src != kUndef) ++c;
-    }
-    return c;
+    const uint32_t e = edge(p, s);
+    if (!b->cs_cnt[e]) return;
+    put(IT_COPYSET, lvl, e, 0);
+    if (b->cs_cyc[e]) atomicOr(&K->partial, 1u);
   }
 };
 
-__global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ items, const uint32_t* __restrict__ item_base,
-                         uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ scratch_all,
-                         uint32_t* __restrict__ stk_all, const uint32_t* __restrict__ pbits, int write) {
+__global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ stage, const uint32_t* __restrict__ stage_off,
+                         uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ stk_all) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   LayoutCtx L;
   L.b = &b;
   L.K = &K;
-  L.v = make_view(b, K, k);
-  L.items = items;
-  L.base = write ? item_base[k] : 0;
+  L.BL = b.lblocks + K.first_lblock;
+  L.items = stage + stage_off[k];
   L.n = 0;
-  L.write = write != 0;
-  L.scratch = scratch_all + K.wl_off;
-  L.scap = 4 * K.n_instr + K.n_lblock * K.R + 3 * K.R + 8;
-  L.pbits = pbits;
-  if (!write) K.partial = 0;
+  L.cap = layout_bound(K);
+  L.k = k;
+  L.over = false;
+  K.partial = 0;
   if (K.bad) {
     L.put(IT_FAIL, 0, 0, 0);
     L.put(IT_TAIL, 0, 1, 0);
@@ -812,7 +806,7 @@ __global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ ite
     for (uint32_t x = 0; x < K.n_vars; x += kDeclChunk) L.put(IT_DECLS, 1, x, min(kDeclChunk, K.n_vars - x));
     if (K.n_lblock) {
       const uint32_t* RG = b.rg + (size_t)kRegionsPerBlock * K.first_lblock * RGW;
-      const BlockRec* BL = b.lblocks + K.first_lblock;
+      const BlockRec* BL = L.BL;
       uint32_t* st = stk_all + kStackPerBlock * (size_t)K.first_lblock;
       uint32_t cap = kStackPerBlock * K.n_lblock, sp = 0;
       auto push = [&](uint32_t r, uint32_t lvl, uint32_t ph) {
@@ -909,7 +903,24 @@ __global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ ite
     }
     L.put(IT_TAIL, 0, 0, 0);
   }
-  if (!write) item_cnt[k] = L.n;
+  if (L.over) atomicOr(b.err, ERR_CAPACITY);
+  item_cnt[k] = min(L.n, L.cap);
+}
+
+// staged items -> their final places (thread per staging slot)
+__global__ void k_items_place(const Item* __restrict__ stage, const uint32_t* __restrict__ stage_off, uint32_t K,
+                              uint32_t total, const uint32_t* __restrict__ item_cnt,
+                              const uint32_t* __restrict__ item_base, Item* __restrict__ items) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  uint32_t lo = 0, hi = K;  // last kernel with stage_off <= t
+  while (lo + 1 < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (stage_off[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  const uint32_t i = t - stage_off[lo];
+  if (i < item_cnt[lo]) items[item_base[lo] + i] = stage[t];
 }
 
 // Sub-items.  Every instruction that may print a statement (a variable
@@ -947,6 +958,8 @@ __global__ void k_item_weight(const __grid_constant__ Batch b, const Item* __res
     const KHdr& K = b.kh[it.k];
     const BlockRec& B = b.lblocks[K.first_lblock + it.a];
     w = prank[K.first_instr + B.end] - prank[K.first_instr + B.first];
+  } else if ((it.kl & 0xFF) == IT_COPYSET) {
+    w = b.cs_cnt[it.a];
   }
   weight[i] = w;
 }
@@ -1005,8 +1018,6 @@ __global__ void __launch_bounds__(128)
   em.vo = b.var_of + nb;
   em.pv = b.phi_var + K.state_off;
   em.vt = b.var_type + nb + K.state_off;
-  em.scratch = nullptr;
-  em.scap = 0;
   if (stage) em.w = Wr{stage + (size_t)sidx * kEmitSlot, 0, kEmitSlot, false};
   else em.w = Wr{b.out + item_off[sidx], 0, item_len[sidx], false};
   em.partial = false;
@@ -1036,7 +1047,12 @@ __global__ void __launch_bounds__(128)
       }
       break;
     case IT_BLOCK: em.instr_stmts(q_stmt, (int)lvl); break;
-    case IT_COPY: em.one_copy(it.a >> 10, it.a & 0x3FF, it.b, (int)lvl); break;
+    case IT_COPYSET: {
+      const uint32_t p = (it.a >> 1) - K.first_lblock;
+      const BlockRec& B = b.lblocks[it.a >> 1];
+      em.one_copy((it.a & 1) ? B.succ1 : B.succ0, b.cs_reg[b.cs_off[it.a] + j], p, (int)lvl);
+      break;
+    }
     case IT_IF:
       w.indent((int)lvl);
       w.s("if (");
@@ -1095,10 +1111,27 @@ __global__ void k_file_out(const __grid_constant__ Batch b, uint32_t total) {
   b.file_status[f] = st;
 }
 
-void launch_layout(Batch& b, Item* items, const uint32_t* item_base, uint32_t* item_cnt, uint32_t* scratch,
-                   uint32_t* stk, const uint32_t* pbits, int write, cudaStream_t s) {
+void launch_copy_sets(Batch& b, const uint32_t* blk_kern, const uint32_t* pbits, uint32_t* bound_or_tmp, int phase,
+                      cudaStream_t s) {
+  if (!b.NLB) return;
+  const uint32_t ne = 2 * b.NLB;
+  if (phase == 0) k_copy_bound<<<(ne + 1 + 255) / 256, 256, 0, s>>>(b, blk_kern, pbits, bound_or_tmp);
+  else k_copy_sets<<<(ne + 127) / 128, 128, 0, s>>>(b, blk_kern, pbits, bound_or_tmp);
+  ++launch_counter();
+}
+
+void launch_layout(Batch& b, Item* stage, uint32_t* stage_off, uint32_t* item_cnt, uint32_t* stk, int phase,
+                   cudaStream_t s) {
   if (!b.K) return;
-  k_layout<<<(b.K + 63) / 64, 64, 0, s>>>(b, items, item_base, item_cnt, scratch, stk, pbits, write);
+  if (phase == 0) k_layout_bound<<<(b.K + 127) / 128, 128, 0, s>>>(b, stage_off);
+  else k_layout<<<(b.K + 63) / 64, 64, 0, s>>>(b, stage, stage_off, item_cnt, stk);
+  ++launch_counter();
+}
+
+void launch_items_place(const Item* stage, const uint32_t* stage_off, uint32_t K, uint32_t total,
+                        const uint32_t* item_cnt, const uint32_t* item_base, Item* items, cudaStream_t s) {
+  if (!total || !K) return;
+  k_items_place<<<(total + 255) / 256, 256, 0, s>>>(stage, stage_off, K, total, item_cnt, item_base, items);
   ++launch_counter();
 }
 
