@@ -287,6 +287,12 @@ def serve(pkg, local, rates, n_pool=1000, max_requests=20000, max_seconds=5.0, b
     return out
 
 
+# the library's event timing of the statement-printing kernel alone (not a stage)
+KERNEL_TIMING = "k_items (S13 print)"
+# ncu counters of one k_items launch (4,000 kernels of the batch distribution)
+K_ITEMS_TRAFFIC = {"instrs": 2201608, "bytes": 2.055555e9 + 0.980455168e9}
+
+
 def algorithmic_bytes(st):
     """Contract bytes of one pass: text in + OpenCL out + the IR arrays the
     parity tests compare (instruction records, block ids, block tables, headers)."""
@@ -396,13 +402,21 @@ def main():
     peaks, src = measured_peaks()
     ab = algorithmic_bytes(stats)
     bytes_per_pass = ab["text_in"] + ab["text_out"] + ab["ir"]
+    kern_ms = stage_ms.pop(KERNEL_TIMING, None)
     dom = max(stage_ms, key=stage_ms.get)
-    dom_ms = stage_ms[dom]
-    achieved = bytes_per_pass / (dom_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+    roofline = {"bound": "hbm", "kernel": "k_items (S13 statement printing, the longest kernel of a pass)",
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src,
                 "bytes_per_instr": bytes_per_pass / total_instr,
+                "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_items launch on "
+                                  f"{K_ITEMS_TRAFFIC['instrs']} instructions, scaled by instructions "
+                                  f"(profiles/k_items_config1_4000.md)",
+                "dominant_stage": {"name": dom, "ms": stage_ms[dom],
+                                   "achieved": bytes_per_pass / (stage_ms[dom] / 1e3) / 1e9},
                 "path_frac": bytes_per_pass / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    if kern_ms:
+        achieved = bytes_per_pass / (kern_ms / 1e3) / 1e9
+        roofline.update({"achieved": achieved, "frac": achieved / peaks["hbm_gbs"], "kernel_ms": kern_ms,
+                         "traffic": K_ITEMS_TRAFFIC["bytes"] / K_ITEMS_TRAFFIC["instrs"] * total_instr})
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -418,7 +432,9 @@ def main():
             "config": {"workload": f"{args.workload}: {n_files} seeded synthetic kernels (preset {cfg}), "
                                    f"{total_instr} instrs, {stats['text_bytes']} text bytes per GPU",
                        "kernels": n_files, "instrs": total_instr, "text_bytes": stats["text_bytes"],
-                       "l2": "inputs larger than L2 (text > 129 MB); no flush between steps",
+                       "l2": ("inputs larger than L2 (text > 129 MB); no flush between steps"
+                              if stats["text_bytes"] > 129e6 else
+                              "text smaller than L2 but the IR arrays of a pass exceed it; no flush"),
                        "form": "batched: one pipeline pass over all kernels per step"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "instr/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -161,7 +161,8 @@ int gcn_decomp_result_copy(gcn_decomp_t *h, uint64_t f0, uint64_t f1, void *buf,
                            int32_t *status_out);
 
 /* Per-stage device times of the last run of either form (milliseconds, CUDA
- * events on the run's stream), stage names in *names (static strings).  Returns the number
+ * events on the run's stream), stage names in *names (static strings): the
+ * ten stages S1..S13, then the statement-printing kernel of S13 alone.  Returns the number
  * of stages (<= cap) or a negative code. */
 int gcn_decomp_stage_times(gcn_decomp_t *h, float *ms, const char **names, int cap);
 

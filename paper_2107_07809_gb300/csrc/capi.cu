@@ -104,8 +104,10 @@ struct Workspace {
 };
 
 const char* kStageNames[] = {"S1 tokenise", "S2 segment", "S3 config", "S4 decode", "S5 cfg", "S6 logical cfg",
-                             "S7-S8 dataflow", "S9-S11 analysis", "S12 regions", "S13 emit"};
+                             "S7-S8 dataflow", "S9-S11 analysis", "S12 regions", "S13 emit",
+                             "k_items (S13 print)"};
 constexpr int kStages = 10;
+constexpr int kTimings = kStages + 1;  // the stages, then the emission kernel alone
 
 struct Run {
   bool valid = false;
@@ -119,8 +121,8 @@ struct Run {
 struct Engine {
   Workspace ws;
   Run run;
-  cudaEvent_t ev[kStages + 1] = {};
-  float stage_ms[kStages] = {0};
+  cudaEvent_t ev[kStages + 3] = {};  // stage boundaries, then around the k_items print launch
+  float stage_ms[kTimings] = {0};
   uint64_t launches = 0;
   uint32_t* h_tot = nullptr;  // pinned counters
   // job service: the batch whose IR the workspace holds and its unfetched jobs
@@ -196,7 +198,7 @@ struct gcn_decomp {
   std::atomic<uint64_t> pool{0};
   // most recent completed pipeline run (either form)
   std::mutex smu;
-  float last_ms[kStages] = {0};
+  float last_ms[kTimings] = {0};
   uint64_t last_stats[9] = {0};
   uint64_t last_launches = 0;
 };
@@ -446,7 +448,9 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   CK(cudaMemsetAsync(&tot[13], 0, 4, s));
   // one thread per statement while staging (measured faster than a warp per
   // statement); one warp per statement for the few long ones redone in place
+  CK(cudaEventRecord(h->ev[kStages + 1], s));
   launch_items(b, items, sitem, sub0, prank, plist, NS2, nullptr, ilen, ioff, stage, ovl, &tot[13], 0, s);
+  CK(cudaEventRecord(h->ev[kStages + 2], s));
   if (NS2) launch_scan(ilen, ioff, NS2, 0, false, sc2, &tot[11], b.err, s);
   CK(cudaGetLastError());
   sync_totals();
@@ -473,6 +477,7 @@ void finish_run(Engine* h, cudaStream_t s) {
   if (b.K) CK(cudaMemcpyAsync(R.kh.data(), b.kh, sizeof(KHdr) * b.K, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&h->stage_ms[i], h->ev[i], h->ev[i + 1]);
+  cudaEventElapsedTime(&h->stage_ms[kStages], h->ev[kStages + 1], h->ev[kStages + 2]);
   if (uint32_t e = h->h_tot[15]) {
     set_err("device error flags " + std::to_string(e));
     throw GCN_ECUDA;
@@ -506,7 +511,7 @@ void note_run(gcn_decomp* h, const Engine* E) {
   const Batch& b = E->run.b;
   const uint64_t v[9] = {b.L, b.K, b.I, b.NL, b.NPB, b.NLB, b.NS, E->run.out_bytes, E->ws.total};
   for (int i = 0; i < 9; ++i) h->last_stats[i] = v[i];
-  for (int i = 0; i < kStages; ++i) h->last_ms[i] = E->stage_ms[i];
+  for (int i = 0; i < kTimings; ++i) h->last_ms[i] = E->stage_ms[i];
   h->last_launches = E->launches;
 }
 
@@ -1080,7 +1085,7 @@ int gcn_decomp_run_stats(gcn_decomp_t* h, uint64_t* out, int cap) {
 int gcn_decomp_stage_times(gcn_decomp_t* h, float* ms, const char** names, int cap) {
   if (!h || cap < 0) return GCN_EINVAL;
   std::lock_guard<std::mutex> g(h->smu);
-  int n = std::min(cap, kStages);
+  int n = std::min(cap, kTimings);
   for (int i = 0; i < n; ++i) {
     if (ms) ms[i] = h->last_ms[i];
     if (names) names[i] = kStageNames[i];
