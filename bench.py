@@ -28,6 +28,8 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# runtime parameters picked by paper_2107_07809_gb300/autotune.py on a GB300 (if present)
+TUNING = os.path.join(ROOT, "paper_2107_07809_gb300", "tuning", "gb300.tune")
 
 import gcngen  # noqa: E402
 
@@ -211,10 +213,11 @@ def serve(pkg, local, rates, n_pool=1000, max_requests=20000, max_seconds=5.0, b
     ninstr = pool.ninstr.astype(np.int64)
     out = {"budget_bytes": budget, "pool": f"{n_pool} seeded requests (lengths 100..50000), cycled",
            "latency": "scheduled arrival -> job finished (CLOCK_MONOTONIC)", "rates": []}
-    with pkg.Decompiler(local, mem_budget_bytes=budget) as dec:
+    with pkg.Decompiler(local, mem_budget_bytes=budget,
+                        tuning_file=TUNING if os.path.exists(TUNING) else None) as dec:
         ids = dec.submit_batch(texts)
         raw, offs, _ = dec.fetch_batch_raw(ids)
-        ref = [raw[offs[i]:offs[i + 1]] for i in range(n_pool)]
+        ref = [raw[offs[i]:offs[i + 1]].tobytes() for i in range(n_pool)]
         for rate in rates:
             rng = np.random.default_rng(2107078090 + rate)
             n = int(min(max_requests, rate * max_seconds))
@@ -269,7 +272,7 @@ def serve(pkg, local, rates, n_pool=1000, max_requests=20000, max_seconds=5.0, b
                         r = id_to_req[j]
                         done_ns[r] = infos[q]
                         lat[r] = (infos[q] - arr_ns[r]) / 1e6
-                        if raw[offs[q]:offs[q + 1]] != ref[which[r]]:
+                        if raw[offs[q]:offs[q + 1]].tobytes() != ref[which[r]]:
                             mism[0] += 1
                     seen += len(ready)
 
@@ -307,7 +310,7 @@ def algorithmic_bytes(st):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config1", choices=sorted(WORKLOADS))
@@ -334,7 +337,7 @@ def main():
     total_instr = batch.total_instr
     d_text = torch.from_numpy(batch.text).to(f"cuda:{local}")
     d_off = torch.from_numpy(batch.offsets.view(np.int64)).to(f"cuda:{local}")
-    dec = pkg.Decompiler(local)
+    dec = pkg.Decompiler(local, tuning_file=TUNING if os.path.exists(TUNING) else None)
     stream = torch.cuda.current_stream()
 
     def step():

@@ -24,7 +24,7 @@
  * Jobs (submit_batch / fetch_*) are served by continuous batching: admitted
  * jobs queue on the host; each of the handle's worker lanes (a host thread
  * with its own CUDA stream) takes everything queued when it becomes free, up
- * to 64 MiB of text, and runs it as one batch, so jobs that arrive while
+ * to 64 MiB of text (tuning: batch_mib), and runs it as one batch, so jobs that arrive while
  * others are on the GPU start as soon as a lane frees up, and the batches of
  * different lanes overlap on the device.  A job's result does not depend on
  * which jobs share its batch.
@@ -62,7 +62,11 @@ typedef struct {
   int device;                 /* CUDA device ordinal */
   uint64_t mem_budget_bytes;  /* device memory the handle may hold (0 = no limit) */
   uint32_t max_slots;         /* jobs resident at once (0 = 65536) */
-  const char *tuning_file;    /* reserved (NULL) */
+  const char *tuning_file;    /* NULL, or a file of "key=value" lines written by the autotuner:
+                                 lanes (worker lanes, 1..8; default 2), batch_mib (text one lane
+                                 takes at once; default 64), big_kernel (instructions from which
+                                 a kernel is analysed by a thread block instead of a warp;
+                                 default 4096); a malformed file makes create fail (GCN_EINVAL) */
   uint32_t flags;             /* reserved (0) */
 } gcn_decomp_config;
 

@@ -129,9 +129,10 @@ def _ck(rc: int, what: str):
 class Decompiler:
     """One handle on ``device``: device memory, CUDA streams and the worker lanes of the job service."""
 
-    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_slots: int = 0):
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_slots: int = 0,
+                 tuning_file: str | None = None):
         self._h = ctypes.c_void_p()
-        cfg = Config(device, mem_budget_bytes, max_slots, None, 0)
+        cfg = Config(device, mem_budget_bytes, max_slots, tuning_file.encode() if tuning_file else None, 0)
         _ck(lib().gcn_decomp_create(ctypes.byref(cfg), ctypes.byref(self._h)), "gcn_decomp_create")
 
     def close(self):
@@ -191,16 +192,20 @@ class Decompiler:
         raw = buf.raw
         return [raw[offs[i]:offs[i + 1]].decode() for i in range(n)], [int(st[i]) for i in range(n)]
 
-    def fetch_batch_raw(self, ids: list[int]) -> tuple[bytes, list[int], list[int]]:
-        """Like fetch_batch, without splitting: (texts back to back, offsets, statuses)."""
+    def fetch_batch_raw(self, ids: list[int]):
+        """Like fetch_batch, without splitting or decoding: (texts back to back as a numpy uint8
+        array, offsets, statuses)."""
+        import numpy as np
+
         n = len(ids)
         arr = (ctypes.c_uint64 * max(n, 1))(*ids)
         offs = (ctypes.c_uint64 * (n + 1))()
         st = (ctypes.c_int32 * max(n, 1))()
         _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, None, 0, offs, st, 1), "gcn_decomp_fetch_batch")
-        buf = ctypes.create_string_buffer(max(int(offs[n]), 1))
-        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, buf, int(offs[n]), offs, st, 1), "gcn_decomp_fetch_batch")
-        return buf.raw[: int(offs[n])], list(offs), list(st)
+        buf = np.empty(max(int(offs[n]), 1), dtype=np.uint8)
+        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, buf.ctypes.data, int(offs[n]), offs, st, 1),
+            "gcn_decomp_fetch_batch")
+        return buf[: int(offs[n])], list(offs), list(st)
 
     def poll(self, cap: int = 4096, timeout_ms: int = 0) -> list[int]:
         """Finished jobs not reported before (waits up to timeout_ms for one)."""

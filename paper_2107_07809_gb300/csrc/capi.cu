@@ -125,6 +125,7 @@ struct Engine {
   float stage_ms[kTimings] = {0};
   uint64_t launches = 0;
   uint32_t* h_tot = nullptr;  // pinned counters
+  uint32_t big_kernel = 4096;  // size-bucket threshold
   // job service: the batch whose IR the workspace holds and its unfetched jobs
   uint64_t batch = 0;
   uint32_t live = 0;
@@ -134,7 +135,8 @@ struct Engine {
 enum JobState : int { JOB_PENDING = 0, JOB_RUNNING = 1, JOB_DONE = 2 };
 
 struct JobRec {
-  std::string in;    // input file text (ends with '\n'); dropped once run
+  std::unique_ptr<uint8_t[]> in;  // input file text (ends with '\n'); dropped once run
+  size_t in_len = 0;
   std::string text;  // OpenCL output
   int status = 0;
   int rc = GCN_OK;   // a batch failure reported at fetch
@@ -166,11 +168,45 @@ uint64_t now_ns() {
       .count();
 }
 
-constexpr int kLanes = 2;                      // worker lanes per handle
-constexpr int kPoolEngines = kLanes + 2;       // engines of the job service
-constexpr uint64_t kMaxBatchText = 64ull << 20;  // text bytes one lane takes at once
-constexpr uint64_t kEstPerTextByte = 48;       // device bytes per input byte (admission estimate)
+// Runtime parameters of a handle (defaults, or a tuning file written by the
+// project's autotuner: `lanes=`, `batch_mib=`, `big_kernel=` lines).
+struct Tuning {
+  int lanes = 2;                     // worker lanes of the job service
+  uint64_t batch_bytes = 64ull << 20;  // text bytes one lane takes at once
+  uint32_t big_kernel = 4096;        // kernels of this many instructions or more get a thread block
+};
+constexpr int kMaxLanes = 8;
+constexpr uint64_t kEstPerTextByte = 48;  // device bytes per input byte (admission estimate)
 constexpr uint64_t kEstPerJob = 1ull << 20;
+
+bool read_tuning(const char* path, Tuning* t) {
+  FILE* f = fopen(path, "r");
+  if (!f) {
+    set_err(std::string("cannot open tuning file ") + path);
+    return false;
+  }
+  char line[256];
+  bool ok = true;
+  while (ok && fgets(line, sizeof line, f)) {
+    char* p = line;
+    while (*p == ' ' || *p == '\t') ++p;
+    if (*p == '#' || *p == '\n' || *p == '\r' || !*p) continue;
+    char key[64];
+    unsigned long long v = 0;
+    if (sscanf(p, "%63[a-z_] = %llu", key, &v) != 2) {
+      ok = false;
+      break;
+    }
+    const std::string k = key;
+    if (k == "lanes" && v >= 1 && v <= (unsigned long long)kMaxLanes) t->lanes = (int)v;
+    else if (k == "batch_mib" && v >= 1 && v <= 4095) t->batch_bytes = v << 20;
+    else if (k == "big_kernel" && v >= 32 && v <= (1ull << 26)) t->big_kernel = (uint32_t)v;
+    else ok = false;
+  }
+  fclose(f);
+  if (!ok) set_err(std::string("malformed tuning file ") + path);
+  return ok;
+}
 
 }  // namespace
 
@@ -194,6 +230,7 @@ struct gcn_decomp {
   uint64_t next_job = 1, next_batch = 1;
   uint32_t max_slots = 65536;
   uint64_t budget = 0;
+  Tuning tune;
   uint64_t admitted = 0;  // estimated device bytes of admitted, unfetched jobs
   std::atomic<uint64_t> pool{0};
   // most recent completed pipeline run (either form)
@@ -218,6 +255,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.text_len = n;
   b.file_off = file_off;
   b.F = F;
+  b.big_kernel = h->big_kernel;
   uint32_t* tot = W.get<uint32_t>("totals", 16);
   uint32_t* err = W.get<uint32_t>("err", 4);
   b.err = err;
@@ -492,6 +530,7 @@ void finish_run(Engine* h, cudaStream_t s) {
 }
 
 void engine_init(gcn_decomp* h, Engine* E) {
+  E->big_kernel = h->tune.big_kernel;
   E->ws.budget = h->budget;
   E->ws.pool = &h->pool;
   for (auto& e : E->ev) CK(cudaEventCreate(&e));
@@ -539,7 +578,7 @@ Engine* acquire_engine(gcn_decomp* h) {
   Engine* pick = nullptr;
   for (auto& e : h->engines)
     if (!e->busy && !e->live && (!pick || e->ws.total > pick->ws.total)) pick = e.get();
-  if (!pick && (int)h->engines.size() < kPoolEngines) {
+  if (!pick && (int)h->engines.size() < h->tune.lanes + 2) {
     h->engines.emplace_back(new Engine);
     pick = h->engines.back().get();
     engine_init(h, pick);
@@ -571,7 +610,7 @@ void run_jobs(gcn_decomp* h, Lane* L, Engine* E, const std::vector<JobRec*>& js)
   uint64_t N = 0;
   for (size_t i = 0; i < n; ++i) {
     L->h_off[i] = N;
-    N += js[i]->in.size();
+    N += js[i]->in_len;
   }
   L->h_off[n] = N;
   if (N >= (1ull << 32)) {
@@ -579,7 +618,7 @@ void run_jobs(gcn_decomp* h, Lane* L, Engine* E, const std::vector<JobRec*>& js)
     throw GCN_ENOMEM;
   }
   grow_pinned(L->h_in, L->h_in_cap, N + 1);
-  for (size_t i = 0; i < n; ++i) memcpy(L->h_in + L->h_off[i], js[i]->in.data(), js[i]->in.size());
+  for (size_t i = 0; i < n; ++i) memcpy(L->h_in + L->h_off[i], js[i]->in.get(), js[i]->in_len);
   uint8_t* d_text = E->ws.get<uint8_t>("in_text", N + 16);
   uint64_t* d_off = E->ws.get<uint64_t>("in_off", n + 1);
   CK(cudaMemcpyAsync(d_text, L->h_in, N, cudaMemcpyHostToDevice, s));
@@ -609,7 +648,8 @@ void finish_jobs(gcn_decomp* h, const std::vector<uint64_t>& ids, Engine* E, uin
     j.state = JOB_DONE;
     j.rc = rc;
     j.t_done = t;
-    std::string().swap(j.in);
+    j.in.reset();
+    j.in_len = 0;
     j.eng = rc == GCN_OK ? E : nullptr;
     j.batch = batch;
     h->done_q.push_back(id);
@@ -635,11 +675,11 @@ void lane_main(gcn_decomp* h, Lane* L) {
     const uint64_t t = now_ns();
     while (!h->pending.empty()) {
       JobRec& j = h->jobs[h->pending.front()];
-      if (!ids.empty() && bytes + j.in.size() > kMaxBatchText) break;
+      if (!ids.empty() && bytes + j.in_len > h->tune.batch_bytes) break;
       ids.push_back(h->pending.front());
       js.push_back(&j);
       h->pending.pop_front();
-      bytes += j.in.size();
+      bytes += j.in_len;
       j.state = JOB_RUNNING;
       j.t_start = t;
     }
@@ -684,7 +724,7 @@ void lane_main(gcn_decomp* h, Lane* L) {
 }
 
 void start_lanes(gcn_decomp* h) {
-  for (int i = 0; i < kLanes; ++i) {
+  for (int i = 0; i < h->tune.lanes; ++i) {
     h->lanes.emplace_back(new Lane);
     Lane* L = h->lanes.back().get();
     CK(cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking));
@@ -773,6 +813,7 @@ int gcn_decomp_create(const gcn_decomp_config* cfg, gcn_decomp_t** out) {
     h->device = cfg->device;
     h->budget = cfg->mem_budget_bytes;
     if (cfg->max_slots) h->max_slots = cfg->max_slots;
+    if (cfg->tuning_file && !read_tuning(cfg->tuning_file, &h->tune)) throw GCN_EINVAL;
     CK(cudaSetDevice(h->device));
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaDeviceSetLimit(cudaLimitStackSize, 16384));
@@ -884,7 +925,9 @@ int gcn_decomp_submit_batch(gcn_decomp_t* h, const char* const* text, const size
   if (n_admitted) *n_admitted = 0;
   std::unique_lock<std::mutex> lk(h->mu);
   size_t take = 0;
+  uint64_t total = 0;
   const uint64_t t = now_ns();
+  std::vector<JobRec*> recs;
   for (; take < n; ++take) {
     if (h->jobs.size() >= h->max_slots) break;
     const size_t l = len[take];
@@ -894,15 +937,34 @@ int gcn_decomp_submit_batch(gcn_decomp_t* h, const char* const* text, const size
     const uint64_t id = h->next_job++;
     JobRec& j = h->jobs[id];
     const bool nl = l && text[take][l - 1] == '\n';
-    j.in.reserve(l + 1);
-    j.in.assign(text[take], l);
-    if (l && !nl) j.in.push_back('\n');
+    j.in_len = l + ((l && !nl) ? 1 : 0);
+    j.in.reset(new uint8_t[j.in_len ? j.in_len : 1]);
+    if (j.in_len > l) j.in[l] = '\n';
     j.est = est;
     j.t_submit = t;
     h->admitted += est;
-    h->pending.push_back(id);
+    recs.push_back(&j);
     job_ids[take] = id;
+    total += l;
   }
+  lk.unlock();
+  // copy the texts (outside the lock; the jobs are not queued yet)
+  auto copy_range = [&](size_t a, size_t z) {
+    for (size_t i = a; i < z; ++i)
+      if (len[i]) memcpy(recs[i]->in.get(), text[i], len[i]);
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nth = total >= (16ull << 20) ? std::min<size_t>({(size_t)8, (size_t)hw, take}) : 1;
+  if (nth > 1) {
+    std::vector<std::thread> th;
+    for (size_t q = 1; q < nth; ++q) th.emplace_back(copy_range, take * q / nth, take * (q + 1) / nth);
+    copy_range(0, take / nth);
+    for (auto& x : th) x.join();
+  } else {
+    copy_range(0, take);
+  }
+  lk.lock();
+  for (size_t i = 0; i < take; ++i) h->pending.push_back(job_ids[i]);
   if (n_admitted) *n_admitted = take;
   lk.unlock();
   if (take) h->cv_work.notify_all();

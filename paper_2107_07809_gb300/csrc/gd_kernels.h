@@ -36,6 +36,7 @@ struct Batch {
   uint64_t text_len;
   const uint64_t* file_off;
   uint32_t F, L, K, I, NL, NC;   // files, lines, kernels, instructions, labels, configuration rows
+  uint32_t big_kernel;           // size buckets: kernels this long or longer get a thread block
   uint32_t NPB, NLB;             // physical / logical blocks
   uint64_t NS;                   // block x register state words
   const uint32_t* line_start;

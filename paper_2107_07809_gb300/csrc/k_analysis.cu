@@ -29,11 +29,10 @@ __device__ __forceinline__ bool claim(uint32_t* bits, uint64_t g) {
   return !(atomicOr(&bits[g >> 5], m) & m);
 }
 
-// Size buckets: a kernel of fewer than kBigKernel instructions is handled by
-// one warp (Team<true>), a longer one by a whole thread block (Team<false>);
-// both launches cover every kernel and a team leaves the kernels of the other
-// bucket alone.
-constexpr uint32_t kBigKernel = 4096;
+// Size buckets: a kernel of fewer than b.big_kernel instructions (a tuning
+// parameter) is handled by one warp (Team<true>), a longer one by a whole
+// thread block (Team<false>); both launches cover every kernel and a team
+// leaves the kernels of the other bucket alone.
 constexpr int kBigTeam = 512;
 
 template <bool WARP>
@@ -52,7 +51,7 @@ struct Team {
     if (WARP) return __any_sync(0xFFFFFFFFu, p);
     return __syncthreads_or(p) != 0;
   }
-  static __device__ __forceinline__ bool mine(const KHdr& K) { return (K.n_instr >= kBigKernel) != WARP; }
+  static __device__ __forceinline__ bool mine(const KHdr& K, uint32_t big) { return (K.n_instr >= big) != WARP; }
 };
 
 template <bool WARP>
@@ -64,7 +63,7 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_co
   uint32_t k = T::kid();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
-  if (K.bad || !T::mine(K)) return;
+  if (K.bad || !T::mine(K, b.big_kernel)) return;
   KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint32_t* uses = b.uses + nb;
@@ -220,7 +219,7 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_co
   const uint32_t k = T::kid(), lane = T::tid(), TS = T::size();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
-  if (K.bad || !T::mine(K)) return;
+  if (K.bad || !T::mine(K, b.big_kernel)) return;
   KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint8_t* nt = b.ntype + nb;

@@ -105,3 +105,20 @@ def test_admission_under_memory_budget(reqs):
         out2 = dec.fetch_batch(rest)
     got = list(zip(out[0], out[1])) + list(zip(out2[0], out2[1]))
     assert got == ref[: len(got)]
+
+
+def test_tuning_file(reqs, tmp_path):
+    """Runtime parameters from a tuning file: one lane taking 1 MiB batches splits the
+    requests into many batches; the results do not change.  A malformed file is refused."""
+    pkg.build()
+    good = tmp_path / "t.tune"
+    good.write_text("# test\nlanes=1\nbatch_mib=1\nbig_kernel=1024\n")
+    bad = tmp_path / "bad.tune"
+    bad.write_text("lanes=99\n")
+    with pkg.Decompiler(0) as dec:
+        ref = dec.decompile(reqs)
+    with pkg.Decompiler(0, tuning_file=str(good)) as dec:
+        assert dec.decompile(reqs) == ref
+    with pytest.raises(pkg.GcnDecompError) as e:
+        pkg.Decompiler(0, tuning_file=str(bad))
+    assert e.value.rc == pkg.GCN_EINVAL
