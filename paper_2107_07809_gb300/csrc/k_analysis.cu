@@ -213,10 +213,24 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
 // update nodes and used join versions concurrently until a vote finds no
 // change (the equations are monotone, so every such iteration reaches the same
 // solution)
+// nodes whose type comes from the types of their operands (the others' types
+// follow from their operation, class or argument alone)
+__device__ __forceinline__ bool type_from_operands(const Node& n) {
+  if (n.kind != N_OP) return false;
+  switch (n.op) {
+    case O_S_LSHL_B32: case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_LSHLREV_B32:
+    case O_V_LSHLREV_B64: return true;
+    case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused != 0;
+  }
+  return false;
+}
+
 template <bool WARP>
-__global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_constant__ Batch b) {
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_constant__ Batch b,
+                                                                 uint32_t* __restrict__ wl_all) {
   using T = Team<WARP>;
-  const uint32_t k = T::kid(), lane = T::tid(), TS = T::size();
+  __shared__ uint32_t s_nd[4];
+  const uint32_t k = T::kid(), lane = T::tid(), TS = T::size(), wid = T::slot();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad || !T::mine(K, b.big_kernel)) return;
@@ -226,19 +240,32 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_co
   const uint8_t* fl = b.nflag + nb;
   uint8_t* pt = b.phi_type + K.state_off;
   const uint32_t* pl = b.plist + K.state_off;
+  uint32_t* dyn = wl_all + K.wl_off;  // the reachability work list is free again
   uint32_t nn = 4 * K.n_instr;
-  for (uint32_t q = lane; q < nn; q += TS) nt[q] = TY_NONE;
+  if (lane == 0) s_nd[wid] = 0;
   for (uint32_t q = lane; q < K.n_phis; q += TS) {
     uint32_t e = pl[q];
     pt[(size_t)(e >> 10) * K.R + (e & 0x3FF)] = TY_NONE;
   }
   T::sync();
+  // a node typed by its operation alone is final after one evaluation (its
+  // equation has no unknowns); the others are listed for the iteration
+  for (uint32_t id = lane; id < nn; id += TS) {
+    uint8_t t = TY_NONE;
+    if (fl[id] & 1) {
+      if (type_from_operands(v.node(id))) dyn[atomicAdd(&s_nd[wid], 1u)] = id;
+      else t = node_type(v, nt, pt, id);
+    }
+    nt[id] = t;
+  }
+  T::sync();
+  const uint32_t nd = s_nd[wid];
   bool changed = true;
   int guard = 0;
   while (changed && guard++ < 100000) {
     bool ch = false;
-    for (uint32_t id = lane; id < nn; id += TS) {
-      if (!(fl[id] & 1)) continue;
+    for (uint32_t q = lane; q < nd; q += TS) {
+      const uint32_t id = dyn[q];
       uint8_t t = tjoin(nt[id], node_type(v, nt, pt, id));
       if (t != nt[id]) {
         nt[id] = t;
@@ -436,8 +463,8 @@ void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_word
   cudaMemsetAsync(bits, 0, sizeof(uint32_t) * nbits_words, s);
   k_reach<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl, rb, cb, ib, pb);
   k_reach<false><<<b.K, kBigTeam, 0, s>>>(b, wl, rb, cb, ib, pb);
-  k_types<true><<<(b.K + 3) / 4, 128, 0, s>>>(b);
-  k_types<false><<<b.K, kBigTeam, 0, s>>>(b);
+  k_types<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl);
+  k_types<false><<<b.K, kBigTeam, 0, s>>>(b, wl);
   launch_counter() += 4;
   // variable numbers over the candidate array of NS + 4I positions
   const uint64_t nc = (uint64_t)b.NS + 4ull * b.I;
