@@ -90,11 +90,18 @@ __device__ __forceinline__ int ilog2_exact(uint32_t x) {
   return (x && !(x & (x - 1)) && x < (1u << 31)) ? (31 - __clz(x)) : -1;
 }
 
-static __device__ Cls classify(const KView& v, uint32_t r);
+// A class other than none is derived from operands at most three levels down
+// (get_global_id <- group id * size + local id <- group id * size <- group id;
+// a settings load <- the settings pointer), and an operand without a class
+// can only keep a pattern from matching.  So the recursion stops below
+// kClassDepth levels without changing any class, which bounds the work on
+// long chains of additions.
+constexpr int kClassDepth = 4;
+static __device__ Cls classify_d(const KView& v, uint32_t r, int d);
 
-static __device__ GD_MATCH_INLINE Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide) {
+static __device__ GD_MATCH_INLINE Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide, int d) {
   Cls none{K_NONE, 0};
-  Cls base = classify(v, nsrc(v, n, 0));
+  Cls base = classify_d(v, nsrc(v, n, 0), d + 1);
   if (base.c != K_KARG || (n.cval & 7u)) return none;
   uint32_t slot = n.cval / 8;
   if (slot >= v.K->nargs) return none;
@@ -124,10 +131,11 @@ __device__ __forceinline__ int64_t const_src(const KView& v, const Node& n, int 
   return const_of_f(v, nsrc(v, n, q));
 }
 
-static __device__ GD_MATCH_INLINE Cls classify(const KView& v, uint32_t r) {
+static __device__ GD_MATCH_INLINE Cls classify_d(const KView& v, uint32_t r, int d) {
   Cls none{K_NONE, 0};
   if (r == kUndef || r == kTop) return Cls{K_UNDEF, 0};
   if (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) return Cls{v.cc[rid(r)], v.ck[rid(r)]};
+  if (d > kClassDepth && r_node(r)) return none;
   if (r_leaf(r)) {
     uint32_t id = rid(r) & 0x0FFFFFFFu;
     uint32_t kind = id >> 8, k = id & 0xFF;
@@ -142,25 +150,25 @@ static __device__ GD_MATCH_INLINE Cls classify(const KView& v, uint32_t r) {
   uint32_t part = rpart(r);
   if (n.kind == N_CONST) return Cls{K_CONST32, 0};
   if (n.kind == N_PAIR && part == PART_ENTIRE) {
-    Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1));
+    Cls a = classify_d(v, nsrc(v, n, 0), d + 1), b = classify_d(v, nsrc(v, n, 1), d + 1);
     return (a.c == K_CONST32 && b.c == K_CONST32) ? Cls{K_CONST64, 0} : none;
   }
-  if (n.kind == N_SLOAD64B) return settings_load(v, n, part, true);
+  if (n.kind == N_SLOAD64B) return settings_load(v, n, part, true, d);
   if (n.kind != N_OP) return none;
-  if (n.op == O_S_LOAD_DWORDX2 || n.op == O_S_LOAD_DWORDX4) return settings_load(v, n, part, true);
-  if (n.op == O_S_LOAD_DWORD) return settings_load(v, n, part, false);
+  if (n.op == O_S_LOAD_DWORDX2 || n.op == O_S_LOAD_DWORDX4) return settings_load(v, n, part, true, d);
+  if (n.op == O_S_LOAD_DWORD) return settings_load(v, n, part, false, d);
   if (part != PART_ENTIRE) return none;
   const uint32_t* cws = v.K->cws;
   auto cw = [&](int d) -> int64_t { return d < 3 ? (int64_t)cws[d] : -1; };
   switch (n.op) {
     case O_S_MUL_I32: {
-      Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1));
+      Cls a = classify_d(v, nsrc(v, n, 0), d + 1), b = classify_d(v, nsrc(v, n, 1), d + 1);
       if (a.c == K_GRP && const_src(v, n, 1) == cw(a.k)) return Cls{K_MULGRP, a.k};
       if (b.c == K_GRP && const_src(v, n, 0) == cw(b.k)) return Cls{K_MULGRP, b.k};
       return none;
     }
     case O_S_LSHL_B32: {
-      Cls a = classify(v, nsrc(v, n, 0));
+      Cls a = classify_d(v, nsrc(v, n, 0), d + 1);
       if (a.c == K_GRP) {
         int l = ilog2_exact((uint32_t)cw(a.k));
         if (l >= 0 && const_src(v, n, 1) == l) return Cls{K_MULGRP, a.k};
@@ -168,7 +176,7 @@ static __device__ GD_MATCH_INLINE Cls classify(const KView& v, uint32_t r) {
       return none;
     }
     case O_V_ADD_U32: {
-      Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1));
+      Cls a = classify_d(v, nsrc(v, n, 0), d + 1), b = classify_d(v, nsrc(v, n, 1), d + 1);
       if (a.c == K_MULGRP && b.c == K_LID && a.k == b.k) return Cls{K_GIDNO, a.k};
       if (b.c == K_MULGRP && a.c == K_LID && a.k == b.k) return Cls{K_GIDNO, a.k};
       if (a.c == K_GIDNO && b.c == K_GOFSLO && a.k == b.k) return Cls{K_GID, a.k};
@@ -176,7 +184,7 @@ static __device__ GD_MATCH_INLINE Cls classify(const KView& v, uint32_t r) {
       return none;
     }
     case O_V_MAD_U32_U24: {
-      Cls a = classify(v, nsrc(v, n, 0)), b = classify(v, nsrc(v, n, 1)), c = classify(v, nsrc(v, n, 2));
+      Cls a = classify_d(v, nsrc(v, n, 0), d + 1), b = classify_d(v, nsrc(v, n, 1), d + 1), c = classify_d(v, nsrc(v, n, 2), d + 1);
       if (c.c != K_LID) return none;
       if (a.c == K_GRP && a.k == c.k && const_src(v, n, 1) == cw(a.k)) return Cls{K_GIDNO, a.k};
       if (b.c == K_GRP && b.k == c.k && const_src(v, n, 0) == cw(b.k)) return Cls{K_GIDNO, b.k};
@@ -185,6 +193,9 @@ static __device__ GD_MATCH_INLINE Cls classify(const KView& v, uint32_t r) {
   }
   return none;
 }
+
+// the class of value r
+__device__ __forceinline__ Cls classify(const KView& v, uint32_t r) { return classify_d(v, r, 0); }
 
 // memory access: argument pointer + (32-bit index, extended) << log2(element size)
 struct Mem {
