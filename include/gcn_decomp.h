@@ -130,8 +130,9 @@ int gcn_decomp_job_info(gcn_decomp_t *h, uint64_t job_id, uint64_t *info, int ca
  *     dims, cws x/y/z, sgprs, vgprs, useargs, user args)
  * concatenated over the job's kernels in file order.  Sizes as for fetch.
  * Waits for the job; does not release it.  The IR stays on the device until
- * the job is fetched, unless the engine holding it is needed for a newer
- * batch (then GCN_ENOJOB).  Errors: GCN_ENOJOB, GCN_EINVAL. */
+ * the job is fetched, unless the memory budget runs out or more than 32
+ * batches are finished and unfetched (then the oldest batches' IR is dropped
+ * and this returns GCN_ENOJOB).  Errors: GCN_ENOJOB, GCN_EINVAL. */
 int gcn_decomp_fetch_ir(gcn_decomp_t *h, uint64_t job_id, int which, void *buf, size_t cap, size_t *len_out);
 
 /* Stop the worker lanes (a batch already on the GPU finishes; queued jobs are

@@ -16,12 +16,12 @@
 //    admitted under the slot limit and the device-memory budget and queued;
 //    each worker lane (a host thread with its own CUDA stream and pinned
 //    staging buffers) takes everything queued when it becomes free (up to a
-//    batch limit), stages it, runs the pipeline on an engine of a small pool
-//    and publishes the results, so batches of different lanes overlap on the
+//    batch limit), stages it, runs the pipeline on an engine of a pool and
+//    publishes the results, so batches of different lanes overlap on the
 //    device.  A finished batch keeps its engine (and so its IR) until all its
-//    jobs are fetched, unless the pool needs the engine back, in which case
-//    the IR of the oldest finished batch is dropped (its texts stay
-//    fetchable).
+//    jobs are fetched; only when the pool is at its limit or the memory
+//    budget runs out is the IR of the oldest finished batches dropped (their
+//    texts stay fetchable).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -176,6 +176,10 @@ struct Tuning {
   uint32_t big_kernel = 4096;        // kernels of this many instructions or more get a thread block
 };
 constexpr int kMaxLanes = 8;
+// engines of the job service: a finished batch keeps its engine (its IR) until
+// its jobs are fetched; the pool grows up to this many, and beyond it (or when
+// the memory budget runs out) the IR of the oldest finished batches is dropped
+constexpr int kMaxEngines = 32;
 constexpr uint64_t kEstPerTextByte = 48;  // device bytes per input byte (admission estimate)
 constexpr uint64_t kEstPerJob = 1ull << 20;
 
@@ -578,7 +582,7 @@ Engine* acquire_engine(gcn_decomp* h) {
   Engine* pick = nullptr;
   for (auto& e : h->engines)
     if (!e->busy && !e->live && (!pick || e->ws.total > pick->ws.total)) pick = e.get();
-  if (!pick && (int)h->engines.size() < h->tune.lanes + 2) {
+  if (!pick && (int)h->engines.size() < kMaxEngines) {
     h->engines.emplace_back(new Engine);
     pick = h->engines.back().get();
     engine_init(h, pick);
