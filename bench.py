@@ -38,6 +38,7 @@ WORKLOADS = {
     "config1": (1, 10_000),
     "config2": (2, 1_000_000),  # streamed in chunks (large_batch)
     "config3": (3, 64),
+    "select": (5, 10_000),  # the batch mix with ternaries (v_cndmask_b32)
 }
 
 

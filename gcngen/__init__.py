@@ -13,6 +13,7 @@ Workload presets (``preset(i)``) follow the five synthetic workloads:
   2  same distribution as 1 (used for large batches)
   3  200,000-instr kernels, int32/int64, loops nested to depth 6, spills
   4  100..50,000-instr kernels with the mix of 1 (serving requests)
+  5  the mix of 1 with selects (v_cndmask_b32, the ternary) in 15% of 32-bit operations
 Seeds: ``SEED_BASE + workload index``; kernel k of a stream uses mix(seed, k).
 """
 from __future__ import annotations
@@ -38,7 +39,7 @@ class Params(ctypes.Structure):
         for n in (
             "w_if", "w_ifelse", "w_loop", "w_uif", "p_ctrl", "max_depth", "min_bufs", "max_bufs",
             "vgpr_budget", "sgpr_budget", "spills", "max_locals", "expr_depth", "trip_max", "dims",
-            "cws0", "cws1", "fixed_args", "one_ifelse", "form_mask",
+            "cws0", "cws1", "fixed_args", "one_ifelse", "form_mask", "p_select",
         )
     ]
 

@@ -76,6 +76,7 @@ struct gcngen_params {
   int32_t fixed_args;          // 1 = (__global int *a, __global float *b, uint n)
   int32_t one_ifelse;          // 1 = exactly one divergent if/else of the first form
   int32_t form_mask;           // bit f set = if-else form f+1 allowed
+  int32_t p_select;            // percent chance that a 32-bit operation is a select (ternary); 0 = never
 };
 }
 
@@ -408,7 +409,21 @@ struct Gen {
     return r;
   }
 
+  // ternary ("Search for control structures": one instruction, no template):
+  //   v_cmp_<cc>_<ty> vcc, a, b;  v_cndmask_b32 vD, f, t, vcc   (vD = vcc ? t : f)
+  // the values first: their code may itself write vcc
+  Opd gen_select(int t, int d) {
+    int mark = vtop;
+    Opd fv = vgpr(gen32(t, d - 1));
+    Opd tv = vgpr(gen32(t, d - 1));
+    divergent_cond_depth(d - 1);
+    int r = res32(mark);
+    ins(f("v_cndmask_b32 v%d, %s, %s, vcc", r, fv.s().c_str(), tv.s().c_str()));
+    return V(r);
+  }
+
   Opd gen32op(int t, int d) {
+    if (P.p_select > 0 && rng.chance(P.p_select)) return gen_select(t, d);
     int mark = vtop;
     int r;
     if (t == TF) {
@@ -596,13 +611,16 @@ struct Gen {
     }
   }
 
-  void divergent_cond() {
+  void divergent_cond() { divergent_cond_depth(-1); }
+
+  // a comparison into vcc (operand depth d, or a random shallow depth when d < 0)
+  void divergent_cond_depth(int d) {
     int cands[3], n = 0;
     if (allowed(TI)) cands[n++] = TI;
     if (allowed(TU)) cands[n++] = TU;
     if (allowed(TF)) cands[n++] = TF;
     int t = n ? cands[rng.below(n)] : TU;
-    int d = rng.range(0, P.expr_depth > 2 ? 2 : P.expr_depth);
+    if (d < 0) d = rng.range(0, P.expr_depth > 2 ? 2 : P.expr_depth);
     Opd a = gen32(t, d);
     Opd b = vgpr(gen32(t, d));
     static const char* cc[6] = {"lt", "gt", "le", "ge", "eq", "ne"};
@@ -897,6 +915,11 @@ gcngen_params preset(int cfg) {
       p.max_locals = 300;
       p.expr_depth = 2;
       break;
+    case 5:  // the batch mix with selects (v_cndmask_b32) in 15% of 32-bit operations
+      p.min_len = 50;
+      p.max_len = 2000;
+      p.p_select = 15;
+      break;
     case 4:  // serving requests: 100..50000 instrs, config-1 mix
       p.min_len = 100;
       p.max_len = 50000;
@@ -917,7 +940,7 @@ extern "C" {
 
 // Default knobs of workload `cfg` (0..4).  Returns 0, or -1 for an unknown index.
 int gcngen_preset(int cfg, gcngen_params* out) {
-  if (cfg < 0 || cfg > 4 || !out) return -1;
+  if (cfg < 0 || cfg > 5 || !out) return -1;
   *out = preset(cfg);
   return 0;
 }

@@ -256,7 +256,8 @@ enum Op : uint16_t {
   V_LSHLREV_B64 = 73, V_ADD_F64 = 74, V_MUL_F64 = 75, V_FMA_F64 = 76,
   GLOBAL_LOAD_DWORD = 77, GLOBAL_LOAD_DWORDX2 = 78, GLOBAL_STORE_DWORD = 79, GLOBAL_STORE_DWORDX2 = 80,
   BUFFER_LOAD_DWORD = 81, BUFFER_STORE_DWORD = 82,
-  OP_COUNT = 83
+  V_CNDMASK_B32 = 83,  // the ternary: vD = vcc ? src1 : src0
+  OP_COUNT = 84
 };
 
 // comparison codes shared by s_cmp and v_cmp: eq, ne(lg/neq), gt, lt, ge, le
@@ -337,6 +338,7 @@ std::vector<OpInfo> build_table() {
   set(V_ADD_F64, "v_add_f64", "W,W,W");
   set(V_MUL_F64, "v_mul_f64", "W,W,W");
   set(V_FMA_F64, "v_fma_f64", "W,W,W,W");
+  set(V_CNDMASK_B32, "v_cndmask_b32", "V,S,S,c");
   set(GLOBAL_LOAD_DWORD, "global_load_dword", "V,W,o");
   set(GLOBAL_LOAD_DWORDX2, "global_load_dwordx2", "W,W,o");
   set(GLOBAL_STORE_DWORD, "global_store_dword", "W,V,o");
@@ -1656,7 +1658,7 @@ struct Emitter {
       case S_ADD_U32: return T_UINT;
       case S_LSHL_B32: return st(0);
       case V_ADD_U32: case V_SUB_U32: case V_MUL_LO_U32: case V_MAD_U32_U24: case V_MUL_U32_U24: return T_UINT;
-      case V_AND_B32: case V_OR_B32: case V_XOR_B32: return tjoin(st(0), st(1));
+      case V_AND_B32: case V_OR_B32: case V_XOR_B32: case V_CNDMASK_B32: return tjoin(st(0), st(1));
       case V_LSHLREV_B32: return st(1);
       case V_LSHRREV_B32: return T_UINT;
       case V_ASHRREV_I32: return T_INT;
@@ -1881,6 +1883,8 @@ struct Emitter {
       case V_ADD_F64: return binop(n, "+", T_DOUBLE);
       case V_MUL_F64: return binop(n, "*", T_DOUBLE);
       case V_FMA_F64: return Ex{"fma(" + S(0, T_DOUBLE) + ", " + S(1, T_DOUBLE) + ", " + S(2, T_DOUBLE) + ")", T_DOUBLE};
+      case V_CNDMASK_B32:  // "Search for control structures": the ternary operator, one instruction
+        return Ex{"(" + S(2, T_NONE) + " ? " + S(1, NT) + " : " + S(0, NT) + ")", NT};
       case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: {
         int elem;
         std::string m = memref(n, op == GLOBAL_LOAD_DWORDX2 ? 8 : 4, &elem);

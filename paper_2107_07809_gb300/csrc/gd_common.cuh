@@ -47,7 +47,9 @@ enum : uint16_t {
   O_V_CVT_F32_F64 = 50, O_V_CMP0 = 51, O_V_ADD_CO_U32 = 69, O_V_ADDC_CO_U32 = 70, O_V_SUB_CO_U32 = 71,
   O_V_SUBB_CO_U32 = 72, O_V_LSHLREV_B64 = 73, O_V_ADD_F64 = 74, O_V_MUL_F64 = 75, O_V_FMA_F64 = 76,
   O_GLOBAL_LOAD_DWORD = 77, O_GLOBAL_LOAD_DWORDX2 = 78, O_GLOBAL_STORE_DWORD = 79, O_GLOBAL_STORE_DWORDX2 = 80,
-  O_BUFFER_LOAD_DWORD = 81, O_BUFFER_STORE_DWORD = 82, O_COUNT = 83
+  O_BUFFER_LOAD_DWORD = 81, O_BUFFER_STORE_DWORD = 82,
+  O_V_CNDMASK_B32 = 83,  // the ternary ("Search for control structures"): vD = vcc ? src1 : src0
+  O_COUNT = 84
 };
 
 // ---- operand word: tag<<28 | count<<24 | payload -----------------------------------
@@ -73,7 +75,7 @@ static __constant__ char c_sig[O_COUNT][12] = {
     "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S",
     "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S",
     "V,c,S,S", "V,c,S,S,c", "V,c,S,S", "V,c,S,S,c", "W,S,W", "W,W,W", "W,W,W", "W,W,W,W",
-    "V,W,o", "W,W,o", "W,V,o", "W,W,o", "V,o,q,s", "V,o,q,s"};
+    "V,W,o", "W,W,o", "W,V,o", "W,W,o", "V,o,q,s", "V,o,q,s", "V,S,S,c"};
 __device__ __forceinline__ int sig_count(uint16_t op) {
   const char* s = c_sig[op];
   int n = 0;

@@ -186,7 +186,7 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
     case O_S_ADD_U32: return TY_UINT;
     case O_S_LSHL_B32: return st(0);
     case O_V_ADD_U32: case O_V_SUB_U32: case O_V_MUL_LO_U32: case O_V_MAD_U32_U24: case O_V_MUL_U32_U24: return TY_UINT;
-    case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: return tjoin(st(0), st(1));
+    case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_CNDMASK_B32: return tjoin(st(0), st(1));
     case O_V_LSHLREV_B32: return st(1);
     case O_V_LSHRREV_B32: return TY_UINT;
     case O_V_ASHRREV_I32: return TY_INT;
@@ -219,7 +219,7 @@ __device__ __forceinline__ bool type_from_operands(const Node& n) {
   if (n.kind != N_OP) return false;
   switch (n.op) {
     case O_S_LSHL_B32: case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_LSHLREV_B32:
-    case O_V_LSHLREV_B64: return true;
+    case O_V_LSHLREV_B64: case O_V_CNDMASK_B32: return true;
     case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused != 0;
   }
   return false;

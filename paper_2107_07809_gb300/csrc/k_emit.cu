@@ -253,7 +253,7 @@ struct Em {
       case O_V_MUL_U32_U24: case O_V_LSHRREV_B32: case O_V_ADD_CO_U32: case O_V_SUB_CO_U32: return TY_UINT;
       case O_S_MUL_I32: case O_V_ASHRREV_I32: return TY_INT;
       case O_S_LSHL_B32: case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_LSHLREV_B32:
-      case O_V_LSHLREV_B64: return T;
+      case O_V_LSHLREV_B64: case O_V_CNDMASK_B32: return T;
       case O_V_ADD_F32: case O_V_SUB_F32: case O_V_MUL_F32: case O_V_FMA_F32: case O_V_CVT_F32_I32:
       case O_V_CVT_F32_U32: case O_V_CVT_F32_F64: return TY_FLOAT;
       case O_V_CVT_F64_F32: case O_V_CVT_F64_I32: case O_V_ADD_F64: case O_V_MUL_F64: case O_V_FMA_F64: return TY_DOUBLE;
@@ -511,6 +511,15 @@ struct Em {
       case O_V_FMA_F64: return call3("fma", n, 3, TY_DOUBLE, d);
       case O_GLOBAL_LOAD_DWORD: return memref(n, 4, d);
       case O_GLOBAL_LOAD_DWORDX2: return memref(n, 8, d);
+      case O_V_CNDMASK_B32:  // the ternary operator: one instruction, printed in place
+        w.c('(');
+        S(n, 2, TY_NONE, d);
+        w.s(" ? ");
+        S(n, 1, T, d);
+        w.s(" : ");
+        S(n, 0, T, d);
+        w.c(')');
+        return;
     }
     partial = true;
     w.s(T == TY_ULONG ? "0UL" : "0u");

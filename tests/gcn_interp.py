@@ -316,6 +316,11 @@ class Wave:
             with np.errstate(all="ignore"):
                 self.vcc = _cmpv(cc, a, b) & ex
             return None
+        if m == "v_cndmask_b32":  # vD = vcc ? src1 : src0
+            if o[3] != "vcc":
+                raise ValueError("v_cndmask_b32 selects on vcc only")
+            self.wr32(o[0], np.where(self.vcc, self.rd32(o[2]), self.rd32(o[1])))
+            return None
         if m in ("v_add_co_u32", "v_sub_co_u32"):
             a, b = self.rd32(o[2]).astype(np.int64), self.rd32(o[3]).astype(np.int64)
             r = a + b if m == "v_add_co_u32" else a - b

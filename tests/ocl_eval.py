@@ -28,7 +28,7 @@ _tok = re.compile(r"""
     (?P<num>(?:0x[0-9a-fA-F]+|\d+\.\d+(?:[eE][-+]?\d+)?f?|\d+)(?:UL|L|u)?)|
     (?P<id>[A-Za-z_][A-Za-z_0-9]*)|
     (?P<str>"(?:[^"\\]|\\.)*")|
-    (?P<op><<|>>|<=|>=|==|!=|&&|\|\||[-+*/%&|^!<>=(){}\[\];,])
+    (?P<op><<|>>|<=|>=|==|!=|&&|\|\||[-+*/%&|^!<>=(){}\[\];,?:])
 """, re.X)
 
 
@@ -168,12 +168,23 @@ class Parser:
     PREC = [("|",), ("^",), ("&",), ("==", "!="), ("<", ">", "<=", ">="), ("<<", ">>"), ("+", "-"), ("*",)]
 
     def expr(self, level=0):
+        if level == 0:  # conditional: c ? a : b (right associative, lowest precedence)
+            c = self.binary(0)
+            if self.peek() != "?":
+                return c
+            self.eat("?")
+            a = self.expr()
+            self.eat(":")
+            return ("cond", c, a, self.expr())
+        return self.binary(level)
+
+    def binary(self, level):
         if level == len(self.PREC):
             return self.unary()
-        left = self.expr(level + 1)
+        left = self.binary(level + 1)
         while self.peek() in self.PREC[level]:
             op = self.eat()
-            right = self.expr(level + 1)
+            right = self.binary(level + 1)
             left = ("bin", op, left, right)
         return left
 
@@ -350,6 +361,15 @@ def ev(e, env: Env):
                 raise EvalError("bitwise op on float")
             r = {"+": lv + rv, "-": lv - rv, "*": lv * rv}[op]
             return lt, T[lt](r)
+    if k == "cond":  # both arms are evaluated (they have no side effects) and must agree in type
+        ct, cv = ev(e[1], env)
+        if ct not in INTS:
+            raise EvalError("non-integer condition")
+        at, av = ev(e[2], env)
+        bt, bv = ev(e[3], env)
+        if at != bt:
+            raise EvalError(f"arms of ?: differ: {at} {bt}")
+        return at, av if int(cv) != 0 else bv
     if k == "deref":
         raise EvalError("raw pointer dereference")
     raise EvalError(f"cannot evaluate {k}")

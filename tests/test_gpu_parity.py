@@ -46,6 +46,10 @@ def test_ir_parity_config1_sample(dec):
     _check_ir(dec, _files(1, 300))
 
 
+def test_ir_parity_ternary_mix(dec):
+    _check_ir(dec, _files(5, 150))
+
+
 def test_ir_parity_multi_kernel_files(dec):
     ks = _files(1, 12, max_len=400)
     files = [b"".join(ks[0:4]), b"leading junk\n" + b"".join(ks[4:9]), ks[9], b"", b"".join(ks[10:12])]
@@ -72,6 +76,11 @@ def _check_text(dec, files):
 
 def test_text_parity_config0(dec):
     _check_text(dec, _files(0, 1))
+
+
+def test_text_parity_ternary_mix(dec):
+    """the batch mix with selects (v_cndmask_b32) in 15% of 32-bit operations"""
+    _check_text(dec, _files(5, 600))
 
 
 def test_text_parity_golden(dec):

@@ -46,6 +46,15 @@ def test_system_values(name):
     assert r.text == gold(name + ".cl")
 
 
+# ---- "Search for control structures": the ternary operator is one instruction ------
+def test_ternary_is_one_instruction():
+    """v_cndmask_b32 (vcc ? src1 : src0) becomes the conditional operator in place, with no
+    control-flow template: ReLU written by hand, its expected text derived by hand."""
+    r = oracle.decompile(gold("ternary_relu.s"))
+    assert r.status == [0]
+    assert r.text == gold("ternary_relu.cl")
+
+
 # ---- "Data type recovery": suffix typing -----------------------------------
 def test_suffix_u32_is_unsigned_addition():
     r = oracle.decompile(gold("suffix_uint_add.s"))
@@ -127,8 +136,9 @@ def test_join_versions_are_minimal():
     assert used > 0
 
 
-def test_output_is_wellformed_opencl():
-    b = _batch(1, 60, max_len=900)
+@pytest.mark.parametrize("cfg", [1, 5])
+def test_output_is_wellformed_opencl(cfg):
+    b = _batch(cfg, 60, max_len=900)
     out, oo, st = oracle.decompile_batch(b.text, b.offsets)
     assert (st == 0).all()
     for i in range(len(b)):
@@ -139,7 +149,7 @@ def test_output_is_wellformed_opencl():
 
 
 # ---- brute force: assembly vs decompiled OpenCL on random buffers -----------
-@pytest.mark.parametrize("cfg,n,maxlen", [(0, 4, 0), (1, 40, 400), (4, 6, 1500)])
+@pytest.mark.parametrize("cfg,n,maxlen", [(0, 4, 0), (1, 40, 400), (4, 6, 1500), (5, 40, 400)])
 def test_brute_force_semantics(cfg, n, maxlen):
     over = dict(cws0=8, cws1=4)
     if maxlen:
