@@ -135,8 +135,9 @@ struct Engine {
 enum JobState : int { JOB_PENDING = 0, JOB_RUNNING = 1, JOB_DONE = 2 };
 
 struct JobRec {
-  std::unique_ptr<uint8_t[]> in;  // input file text (ends with '\n'); dropped once run
+  const uint8_t* in = nullptr;  // input file text in a pinned slab (ends with '\n'); until run
   size_t in_len = 0;
+  int slab = -1;                // the slab holding it
   std::string text;  // OpenCL output
   int status = 0;
   int rc = GCN_OK;   // a batch failure reported at fetch
@@ -176,6 +177,15 @@ struct Tuning {
   uint32_t big_kernel = 4096;        // kernels of this many instructions or more get a thread block
 };
 constexpr int kMaxLanes = 8;
+// Job texts are copied once, at submit, into pinned host slabs; a batch whose
+// texts are contiguous in one slab goes to the device with one copy.  A slab is
+// reused when none of its jobs is left to run.
+struct Slab {
+  uint8_t* p = nullptr;
+  size_t cap = 0, used = 0;
+  uint32_t refs = 0;  // jobs whose text is in the slab and not yet run
+};
+constexpr size_t kSlabBytes = 256ull << 20;
 // engines of the job service: a finished batch keeps its engine (its IR) until
 // its jobs are fetched; the pool grows up to this many, and beyond it (or when
 // the memory budget runs out) the IR of the oldest finished batches is dropped
@@ -236,6 +246,7 @@ struct gcn_decomp {
   uint64_t budget = 0;
   Tuning tune;
   uint64_t admitted = 0;  // estimated device bytes of admitted, unfetched jobs
+  std::vector<Slab> slabs;
   std::atomic<uint64_t> pool{0};
   // most recent completed pipeline run (either form)
   std::mutex smu;
@@ -621,11 +632,19 @@ void run_jobs(gcn_decomp* h, Lane* L, Engine* E, const std::vector<JobRec*>& js)
     set_err("batch text exceeds 4 GiB");
     throw GCN_ENOMEM;
   }
-  grow_pinned(L->h_in, L->h_in_cap, N + 1);
-  for (size_t i = 0; i < n; ++i) memcpy(L->h_in + L->h_off[i], js[i]->in.get(), js[i]->in_len);
+  // the texts of consecutively submitted jobs lie back to back in their slab
+  bool contiguous = true;
+  for (size_t i = 1; i < n && contiguous; ++i)
+    contiguous = js[i]->slab == js[0]->slab && js[i]->in == js[i - 1]->in + js[i - 1]->in_len;
+  const uint8_t* src = n ? js[0]->in : nullptr;
+  if (!contiguous) {
+    grow_pinned(L->h_in, L->h_in_cap, N + 1);
+    for (size_t i = 0; i < n; ++i) memcpy(L->h_in + L->h_off[i], js[i]->in, js[i]->in_len);
+    src = L->h_in;
+  }
   uint8_t* d_text = E->ws.get<uint8_t>("in_text", N + 16);
   uint64_t* d_off = E->ws.get<uint64_t>("in_off", n + 1);
-  CK(cudaMemcpyAsync(d_text, L->h_in, N, cudaMemcpyHostToDevice, s));
+  if (N) CK(cudaMemcpyAsync(d_text, src, N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_off, L->h_off, sizeof(uint64_t) * (n + 1), cudaMemcpyHostToDevice, s));
   run_pipeline(E, d_text, N, d_off, (uint32_t)n, s);
   const Batch& b = E->run.b;
@@ -652,7 +671,12 @@ void finish_jobs(gcn_decomp* h, const std::vector<uint64_t>& ids, Engine* E, uin
     j.state = JOB_DONE;
     j.rc = rc;
     j.t_done = t;
-    j.in.reset();
+    if (j.slab >= 0) {
+      Slab& sl = h->slabs[j.slab];
+      if (--sl.refs == 0) sl.used = 0;
+    }
+    j.slab = -1;
+    j.in = nullptr;
     j.in_len = 0;
     j.eng = rc == GCN_OK ? E : nullptr;
     j.batch = batch;
@@ -841,6 +865,8 @@ void gcn_decomp_destroy(gcn_decomp_t* h) {
   for (auto& e : h->engines) engine_free(e.get());
   h->engines.clear();
   engine_free(&h->direct);
+  for (auto& sl : h->slabs)
+    if (sl.p) cudaFreeHost(sl.p);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -928,34 +954,67 @@ int gcn_decomp_submit_batch(gcn_decomp_t* h, const char* const* text, const size
   }
   if (n_admitted) *n_admitted = 0;
   std::unique_lock<std::mutex> lk(h->mu);
+  // admission: slots and the memory budget
   size_t take = 0;
-  uint64_t total = 0;
-  const uint64_t t = now_ns();
-  std::vector<JobRec*> recs;
+  uint64_t total = 0, est_sum = 0, pinned = 0;
   for (; take < n; ++take) {
-    if (h->jobs.size() >= h->max_slots) break;
+    if (h->jobs.size() + take >= h->max_slots) break;
     const size_t l = len[take];
     if (l && !text[take]) break;
     const uint64_t est = kEstPerTextByte * (uint64_t)l + kEstPerJob;
-    if (h->budget && h->admitted && h->admitted + est > h->budget) break;
+    if (h->budget && (h->admitted + est_sum) && h->admitted + est_sum + est > h->budget) break;
+    est_sum += est;
+    total += l;
+    pinned += l + ((l && text[take][l - 1] != '\n') ? 1 : 0);
+  }
+  // one contiguous region of a pinned slab for all of their texts
+  int si = -1;
+  for (size_t q = 0; q < h->slabs.size() && si < 0; ++q) {
+    Slab& sl = h->slabs[q];
+    if (!sl.refs) sl.used = 0;
+    if (sl.cap - sl.used >= pinned) si = (int)q;
+  }
+  if (si < 0 && take) {
+    Slab sl;
+    sl.cap = std::max<size_t>(kSlabBytes, pinned);
+    if (cudaMallocHost(&sl.p, sl.cap) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("cannot allocate pinned host memory for the job texts");
+      return GCN_ENOMEM;
+    }
+    h->slabs.push_back(sl);
+    si = (int)h->slabs.size() - 1;
+  }
+  uint8_t* region = take ? h->slabs[si].p + h->slabs[si].used : nullptr;
+  if (take) {
+    h->slabs[si].used += pinned;
+    h->slabs[si].refs += (uint32_t)take;
+  }
+  const uint64_t t = now_ns();
+  std::vector<JobRec*> recs;
+  recs.reserve(take);
+  size_t off = 0;
+  for (size_t i = 0; i < take; ++i) {
+    const size_t l = len[i];
     const uint64_t id = h->next_job++;
     JobRec& j = h->jobs[id];
-    const bool nl = l && text[take][l - 1] == '\n';
+    const bool nl = l && text[i][l - 1] == '\n';
+    j.in = region + off;
     j.in_len = l + ((l && !nl) ? 1 : 0);
-    j.in.reset(new uint8_t[j.in_len ? j.in_len : 1]);
-    if (j.in_len > l) j.in[l] = '\n';
-    j.est = est;
+    j.slab = si;
+    if (j.in_len > l) region[off + l] = '\n';
+    off += j.in_len;
+    j.est = kEstPerTextByte * (uint64_t)l + kEstPerJob;
     j.t_submit = t;
-    h->admitted += est;
+    h->admitted += j.est;
     recs.push_back(&j);
-    job_ids[take] = id;
-    total += l;
+    job_ids[i] = id;
   }
   lk.unlock();
   // copy the texts (outside the lock; the jobs are not queued yet)
   auto copy_range = [&](size_t a, size_t z) {
     for (size_t i = a; i < z; ++i)
-      if (len[i]) memcpy(recs[i]->in.get(), text[i], len[i]);
+      if (len[i]) memcpy((uint8_t*)recs[i]->in, text[i], len[i]);
   };
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
   const size_t nth = total >= (16ull << 20) ? std::min<size_t>({(size_t)8, (size_t)hw, take}) : 1;
