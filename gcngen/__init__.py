@@ -14,6 +14,8 @@ Workload presets (``preset(i)``) follow the five synthetic workloads:
   3  200,000-instr kernels, int32/int64, loops nested to depth 6, spills
   4  100..50,000-instr kernels with the mix of 1 (serving requests)
   5  the mix of 1 with selects (v_cndmask_b32, the ternary) in 15% of 32-bit operations
+  6  the mix of 1 with system values read through the dispatch packet (get_global_size,
+     get_num_groups, get_work_dim) and scalar bit fields / shifts in 10% of integer leaves
 Seeds: ``SEED_BASE + workload index``; kernel k of a stream uses mix(seed, k).
 """
 from __future__ import annotations
@@ -39,7 +41,7 @@ class Params(ctypes.Structure):
         for n in (
             "w_if", "w_ifelse", "w_loop", "w_uif", "p_ctrl", "max_depth", "min_bufs", "max_bufs",
             "vgpr_budget", "sgpr_budget", "spills", "max_locals", "expr_depth", "trip_max", "dims",
-            "cws0", "cws1", "fixed_args", "one_ifelse", "form_mask", "p_select",
+            "cws0", "cws1", "fixed_args", "one_ifelse", "form_mask", "p_select", "p_sysval",
         )
     ]
 

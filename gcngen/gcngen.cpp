@@ -77,6 +77,8 @@ struct gcngen_params {
   int32_t one_ifelse;          // 1 = exactly one divergent if/else of the first form
   int32_t form_mask;           // bit f set = if-else form f+1 allowed
   int32_t p_select;            // percent chance that a 32-bit operation is a select (ternary); 0 = never
+  int32_t p_sysval;            // percent chance that an integer leaf is a system value or a scalar
+                               // bit field (s_load from the dispatch packet, s_lshr_b32, s_bfe_u32); 0 = never
 };
 }
 
@@ -350,7 +352,49 @@ struct Gen {
   }
 
   // ---- expressions -----------------------------------------------------------
+  // a system value read through the dispatch packet pointer s[0:1] ("Search for memory
+  // accesses": the global size at 0xc/0x10/0x14, the number of groups as global size /
+  // work-group size, the dimension count as the field at bit 16, width 2, of the dword at
+  // 0x0), or a bit field / logical shift of the scalar argument.  s15 is the scalar
+  // temporary; the value moves to a VGPR at once, so s15 is free again for the next one.
+  Opd sysval() {
+    touchs(15);
+    int d = (int)rng.below((uint32_t)dims);
+    int k = (int)rng.below(5);
+    int lg = 0;
+    while ((1 << lg) < cws[d]) ++lg;
+    if (k == 1 && (1 << lg) != cws[d]) k = 0;  // the shift form needs a power-of-two size
+    switch (k) {
+      case 0:  // get_global_size(d)
+        ins(f("s_load_dword s15, s[0:1], 0x%x", 0xc + 4 * d));
+        ins("s_waitcnt lgkmcnt(0)");
+        break;
+      case 1:  // get_num_groups(d)
+        ins(f("s_load_dword s15, s[0:1], 0x%x", 0xc + 4 * d));
+        ins("s_waitcnt lgkmcnt(0)");
+        ins(f("s_lshr_b32 s15, s15, %d", lg));
+        break;
+      case 2:  // get_work_dim()
+        ins("s_load_dword s15, s[0:1], 0x0");
+        ins("s_waitcnt lgkmcnt(0)");
+        ins("s_bfe_u32 s15, s15, 0x20010");
+        break;
+      case 3: {  // a bit field of the scalar argument
+        int off = rng.range(0, 20), w = rng.range(1, 8);
+        ins(f("s_bfe_u32 s15, s%d, 0x%x", s_n, (w << 16) | off));
+        break;
+      }
+      default:  // a logical right shift of the scalar argument
+        ins(f("s_lshr_b32 s15, s%d, %d", s_n, rng.range(1, 12)));
+        break;
+    }
+    int r = tmp32();
+    ins(f("v_mov_b32 v%d, s15", r));
+    return V(r);
+  }
+
   Opd leaf32(int t, int d) {
+    if (t != TF && P.p_sysval > 0 && rng.chance(P.p_sysval)) return sysval();
     for (int attempt = 0; attempt < 6; ++attempt) {
       int c = rng.below(t == TF ? 6 : 7);
       if (t == TF) {
@@ -924,6 +968,11 @@ gcngen_params preset(int cfg) {
       p.min_len = 100;
       p.max_len = 50000;
       break;
+    case 6:  // the batch mix with system values and scalar bit fields in 10% of integer leaves
+      p.min_len = 50;
+      p.max_len = 2000;
+      p.p_sysval = 10;
+      break;
   }
   return p;
 }
@@ -938,9 +987,9 @@ struct Result {
 
 extern "C" {
 
-// Default knobs of workload `cfg` (0..4).  Returns 0, or -1 for an unknown index.
+// Default knobs of workload `cfg` (0..6).  Returns 0, or -1 for an unknown index.
 int gcngen_preset(int cfg, gcngen_params* out) {
-  if (cfg < 0 || cfg > 5 || !out) return -1;
+  if (cfg < 0 || cfg > 6 || !out) return -1;
   *out = preset(cfg);
   return 0;
 }

@@ -257,7 +257,8 @@ enum Op : uint16_t {
   GLOBAL_LOAD_DWORD = 77, GLOBAL_LOAD_DWORDX2 = 78, GLOBAL_STORE_DWORD = 79, GLOBAL_STORE_DWORDX2 = 80,
   BUFFER_LOAD_DWORD = 81, BUFFER_STORE_DWORD = 82,
   V_CNDMASK_B32 = 83,  // the ternary: vD = vcc ? src1 : src0
-  OP_COUNT = 84
+  S_LSHR_B32 = 84, S_BFE_U32 = 85,  // scalar shift right and bit-field extract (get_num_groups, get_work_dim)
+  OP_COUNT = 86
 };
 
 // comparison codes shared by s_cmp and v_cmp: eq, ne(lg/neq), gt, lt, ge, le
@@ -282,6 +283,8 @@ std::vector<OpInfo> build_table() {
   set(S_MUL_I32, "s_mul_i32", "s,S,S");
   set(S_LSHL_B32, "s_lshl_b32", "s,S,S");
   set(S_ADD_U32, "s_add_u32", "s,S,S");
+  set(S_LSHR_B32, "s_lshr_b32", "s,S,S");
+  set(S_BFE_U32, "s_bfe_u32", "s,S,S");
   static const char* scc[6] = {"eq", "lg", "gt", "lt", "ge", "le"};
   static const char* sty[2] = {"u32", "i32"};
   static std::vector<std::string> names;
@@ -795,13 +798,14 @@ LogicalCfg logical_cfg(const Decoded& d) {
 // reference: which definition (a node id, or a join version) the register holds
 // and which part of it (entire / low_part / high_part of a 64-bit value).
 // Registers are initialised from the ABI: v0..v2 = get_local_id(0..2),
-// s6..s8 = get_group_id(0..2) with .useargs, s[4:5] = settings pointer.
+// s6..s8 = get_group_id(0..2) with .useargs, s[4:5] = settings pointer,
+// s[0:1] = dispatch packet pointer.
 // At a block with several predecessors a register whose definitions differ
 // receives a new version (a join); versions that are used become variables.
 // ============================================================================
 enum Part : uint32_t { P_ENTIRE = 0, P_LO = 1, P_HI = 2 };
 const uint32_t ID_PHI = 1u << 28, ID_LEAF = 2u << 28;
-const uint32_t LEAF_UNDEF = 0, LEAF_LID = 1, LEAF_GRP = 2, LEAF_KARG = 3;
+const uint32_t LEAF_UNDEF = 0, LEAF_LID = 1, LEAF_GRP = 2, LEAF_KARG = 3, LEAF_DISP = 4;
 const uint32_t TOP = 0xFFFFFFFFu;  // unvisited
 
 uint32_t ref(uint32_t id, uint32_t part) { return (id << 2) | part; }
@@ -865,7 +869,7 @@ std::vector<Def> defs_of(const Decoded& d, const LogicalCfg& L, const Regs& R, u
       out.push_back({g[3], node_ref(i, 1, P_HI)});
       break;
     }
-    case S_ADD_U32: case S_MUL_I32: case S_LSHL_B32:
+    case S_ADD_U32: case S_MUL_I32: case S_LSHL_B32: case S_LSHR_B32: case S_BFE_U32:
       out.push_back({dst(0)[0], node_ref(i, 0, P_ENTIRE)});
       out.push_back({R.scc(), UNDEF});
       break;
@@ -1003,6 +1007,10 @@ std::vector<uint32_t> entry_state(const Kernel& K) {
   if (K.R.sgprs > 5) {
     s[K.R.s(4)] = leaf_ref(LEAF_KARG, 0, P_LO);
     s[K.R.s(5)] = leaf_ref(LEAF_KARG, 0, P_HI);
+  }
+  if (K.R.sgprs > 1) {  // the dispatch packet pointer (global size, dimension count)
+    s[K.R.s(0)] = leaf_ref(LEAF_DISP, 0, P_LO);
+    s[K.R.s(1)] = leaf_ref(LEAF_DISP, 0, P_HI);
   }
   return s;
 }
@@ -1288,9 +1296,22 @@ uint32_t fwd(const Kernel& K, uint32_t r, int depth = 0) {
 //   (that) + low part of get_global_offset(d)     -> get_global_id(d)
 // are recognised with the multiplication as s_mul_i32, s_lshl_b32 by log2(cws)
 // or folded into v_mad_u32_u24, in either operand order.
+// The global size, the number of groups and the dimension count come from a
+// second pointer, s[0:1], to the dispatch packet (the settings block cannot hold
+// both the offsets and the sizes at 0x10):
+//   s_load_dword from s[0:1] + 0xc/0x10/0x14     -> get_global_size(0/1/2)
+//   (that) >> log2(cws(d)), cws(d) a power of two  -> get_num_groups(d)
+//     (global size / work-group size; the paper gives no instruction for the division)
+//   s_bfe_u32 of the dword at s[0:1] + 0x0 with field 0x20010 (offset 16, width 2)
+//                                                  -> get_work_dim()
 // ============================================================================
 enum Cls { K_NONE, K_LID, K_GRP, K_KARG, K_UNDEF, K_GOFS64, K_GOFSLO, K_MULGRP, K_GIDNO, K_GID, K_ARGPTR,
-           K_ARG32, K_ARG64, K_CONST32, K_CONST64 };
+           K_ARG32, K_ARG64, K_CONST32, K_CONST64,
+           K_DISP,    // the dispatch packet pointer s[0:1]
+           K_DISP0,   // its first dword (header and setup; an intermediate, like K_MULGRP)
+           K_GSIZE,   // get_global_size(d)
+           K_NGRP,    // get_num_groups(d)
+           K_WDIM };  // get_work_dim()
 struct ClsV {
   int c = K_NONE;
   int k = 0;
@@ -1309,6 +1330,14 @@ ClsV classify(const Kernel& K, uint32_t r);
 ClsV settings_load(const Kernel& K, const Node& n, uint32_t part, bool wide) {
   ClsV v;
   ClsV base = classify(K, fwd(K, n.src[0]));
+  if (base.c == K_DISP) {
+    // the dispatch packet: the dword at 0x0 holds the dimension count in its setup
+    // field, the dwords at 0xc/0x10/0x14 the global size of dimension 0/1/2
+    if (wide || part != P_ENTIRE) return v;
+    if (n.cval == 0) return ClsV{K_DISP0, 0};
+    if (n.cval == 0xc || n.cval == 0x10 || n.cval == 0x14) return ClsV{K_GSIZE, (int)(n.cval - 0xc) / 4};
+    return v;
+  }
   if (base.c != K_KARG || (n.cval & 7u)) return v;
   uint32_t slot = n.cval / 8;
   if (slot >= K.cfg.args.size()) return v;
@@ -1339,6 +1368,7 @@ ClsV classify(const Kernel& K, uint32_t r) {
     if (kind == LEAF_LID && rpart(r) == P_ENTIRE) return ClsV{K_LID, (int)k};
     if (kind == LEAF_GRP && rpart(r) == P_ENTIRE) return ClsV{K_GRP, (int)k};
     if (kind == LEAF_KARG && rpart(r) == P_ENTIRE) return ClsV{K_KARG, 0};
+    if (kind == LEAF_DISP && rpart(r) == P_ENTIRE) return ClsV{K_DISP, 0};
     return v;
   }
   if (!is_node(r)) return v;
@@ -1377,6 +1407,15 @@ ClsV classify(const Kernel& K, uint32_t r) {
       if (a.c == K_GRP && log2_exact(cws(a.k)) >= 0 && cval(1) == log2_exact(cws(a.k))) return ClsV{K_MULGRP, a.k};
       return v;
     }
+    case S_LSHR_B32: {  // global size / work-group size, the size a power of two
+      ClsV a = cl(0);
+      if (a.c == K_GSIZE && log2_exact(cws(a.k)) >= 0 && cval(1) == log2_exact(cws(a.k))) return ClsV{K_NGRP, a.k};
+      return v;
+    }
+    case S_BFE_U32: {  // 0x20010: offset 16, width 2 = the dimension count
+      if (cl(0).c == K_DISP0 && cval(1) == 0x20010) return ClsV{K_WDIM, 0};
+      return v;
+    }
     case V_ADD_U32: {
       ClsV a = cl(0), b = cl(1);
       if (a.c == K_MULGRP && b.c == K_LID && a.k == b.k) return ClsV{K_GIDNO, a.k};
@@ -1396,7 +1435,7 @@ ClsV classify(const Kernel& K, uint32_t r) {
   return v;
 }
 
-bool leaf_like(int c) { return c != K_NONE && c != K_MULGRP; }
+bool leaf_like(int c) { return c != K_NONE && c != K_MULGRP && c != K_DISP0; }
 
 // ============================================================================
 // Memory accesses: base pointer (an argument's 8-byte slot, as a lo/hi pair)
@@ -1643,7 +1682,8 @@ struct Emitter {
     uint32_t r = ref(id, P_ENTIRE);
     ClsV c = cls(r);
     switch (c.c) {
-      case K_GID: case K_GIDNO: case K_LID: case K_GRP: case K_GOFSLO: return T_UINT;
+      case K_GID: case K_GIDNO: case K_LID: case K_GRP: case K_GOFSLO: case K_GSIZE: case K_NGRP: case K_WDIM:
+        return T_UINT;
       case K_GOFS64: case K_ARGPTR: case K_KARG: return T_ULONG;
       case K_ARG32: case K_ARG64: return K.cfg.args[c.k].elem;
       case K_CONST32: case K_CONST64: case K_UNDEF: return T_NONE;
@@ -1657,6 +1697,7 @@ struct Emitter {
       case S_MUL_I32: return T_INT;
       case S_ADD_U32: return T_UINT;
       case S_LSHL_B32: return st(0);
+      case S_LSHR_B32: case S_BFE_U32: return T_UINT;
       case V_ADD_U32: case V_SUB_U32: case V_MUL_LO_U32: case V_MAD_U32_U24: case V_MUL_U32_U24: return T_UINT;
       case V_AND_B32: case V_OR_B32: case V_XOR_B32: case V_CNDMASK_B32: return tjoin(st(0), st(1));
       case V_LSHLREV_B32: return st(1);
@@ -1849,6 +1890,18 @@ struct Emitter {
       case S_ADD_U32: return binop(n, "+", T_UINT);
       case S_MUL_I32: return binop(n, "*", T_INT);
       case S_LSHL_B32: return Ex{"(" + S(0, NT) + " << " + shamt(n.src[1], 31) + ")", NT};
+      case S_LSHR_B32: return Ex{"(" + S(0, T_UINT) + " >> " + shamt(n.src[1], 31) + ")", T_UINT};
+      case S_BFE_U32: {
+        // field operand: offset in bits [4:0], width in bits [22:16]; the result is
+        // (src >> offset) masked to width bits.  A field that is not a constant, or a
+        // width of 32 or more, is not written out.
+        uint32_t f = fwd(K, n.src[1]);
+        if (!is_node(f) || K.nodes[rid(f)].kind != N_CONST || rpart(f) != P_ENTIRE) { partial = true; return Ex{"0u", T_UINT}; }
+        uint32_t c = (uint32_t)K.nodes[rid(f)].cval, off = c & 31u, w = (c >> 16) & 0x7Fu;
+        if (w == 0) return Ex{"0u", T_UINT};
+        if (w >= 32) { partial = true; return Ex{"0u", T_UINT}; }
+        return Ex{"((" + S(0, T_UINT) + " >> " + std::to_string(off) + ") & " + lit32((1u << w) - 1u, T_UINT) + ")", T_UINT};
+      }
       case V_ADD_U32: return binop(n, "+", T_UINT);
       case V_SUB_U32: return binop(n, "-", T_UINT);
       case V_MUL_LO_U32: return binop(n, "*", T_UINT);
@@ -1914,7 +1967,10 @@ struct Emitter {
       case K_GOFS64: return Ex{"get_global_offset(" + std::to_string(c.k) + ")", T_ULONG};
       case K_ARG32: case K_ARG64: return Ex{K.cfg.args[c.k].name, K.cfg.args[c.k].elem};
       case K_ARGPTR: return Ex{"(ulong)" + K.cfg.args[c.k].name, T_ULONG};
-      case K_KARG: partial = true; return Ex{"0UL", T_ULONG};
+      case K_KARG: case K_DISP: partial = true; return Ex{"0UL", T_ULONG};
+      case K_GSIZE: return Ex{"get_global_size(" + std::to_string(c.k) + ")", T_UINT};
+      case K_NGRP: return Ex{"get_num_groups(" + std::to_string(c.k) + ")", T_UINT};
+      case K_WDIM: return Ex{"get_work_dim()", T_UINT};
       case K_CONST32: {
         int w = want == T_NONE ? T_UINT : want;
         if (width_of_type(w) == 64) w = T_UINT;

@@ -7,8 +7,11 @@ CUDA path.  Semantics follow the GCN machine model the paper describes
 ("The AMD GCN architecture"): 64 work-items per wavefront execute each
 instruction together, vector writes are masked by the 64-bit exec mask, scalar
 registers are shared by the wavefront, v0..v2 hold the local id, s6..s8 the
-group id (with .useargs) and s[4:5] points at the kernel settings (global
-offsets at 0x0/0x8/0x10, arguments from 0x30 in 8-byte slots).
+group id (with .useargs), s[4:5] points at the kernel settings (global
+offsets at 0x0/0x8/0x10, arguments from 0x30 in 8-byte slots) and s[0:1] at the
+dispatch packet (header and setup in the dword at 0x0, the dimension count in
+setup bits 0..1; work-group size as 16-bit fields at 0x4/0x6/0x8; global size
+as dwords at 0xc/0x10/0x14).
 """
 from __future__ import annotations
 
@@ -21,6 +24,11 @@ from fp_exact import fma32, fma64
 
 W = 64
 KARG_BASE = 0x1_0000_0000
+DISP_BASE = 0x2_0000_0000
+# packet header: kernel dispatch type with fences; the reserved setup bits above the
+# dimension count are not zero here, so that a wrong field width shows
+DISP_HEADER = 0x1402
+DISP_SETUP_RESERVED = 0x0054
 SCRATCH = object()
 INLINE_F = {"0.5": 0x3F000000, "-0.5": 0xBF000000, "1.0": 0x3F800000, "-1.0": 0xBF800000,
             "2.0": 0x40000000, "-2.0": 0xC0000000, "4.0": 0x40800000, "-4.0": 0xC0800000}
@@ -87,10 +95,11 @@ _one = re.compile(r"^([vs])(\d+)$")
 
 
 class Wave:
-    def __init__(self, prog: KernelText, mem, kargs: bytes, lid, grp, active):
+    def __init__(self, prog: KernelText, mem, kargs: bytes, lid, grp, active, disp: bytes = b""):
         self.p = prog
         self.mem = mem                    # dict base -> numpy array (buffers)
         self.karg = kargs
+        self.disp = disp
         self.v = np.zeros((256, W), dtype=np.uint32)
         self.s = np.zeros(112, dtype=np.uint32)
         self.vcc = np.zeros(W, dtype=bool)
@@ -103,6 +112,8 @@ class Wave:
                 self.s[6 + d] = grp[d]
         self.s[4] = KARG_BASE & 0xFFFFFFFF
         self.s[5] = KARG_BASE >> 32
+        self.s[0] = DISP_BASE & 0xFFFFFFFF
+        self.s[1] = DISP_BASE >> 32
 
     # ---- operand access ------------------------------------------------------
     def regs(self, t):
@@ -182,7 +193,11 @@ class Wave:
         raise IndexError(f"address {addr:#x} outside every buffer")
 
     def karg_load(self, addr, nd):
+        if DISP_BASE <= addr < DISP_BASE + len(self.disp):
+            return struct.unpack_from(f"<{nd}I", self.disp, addr - DISP_BASE)
         off = addr - KARG_BASE
+        if not 0 <= off <= len(self.karg) - 4 * nd:
+            raise IndexError(f"scalar load at {addr:#x} outside the settings and the dispatch packet")
         return struct.unpack_from(f"<{nd}I", self.karg, off)
 
     # ---- execution --------------------------------------------------------------
@@ -228,6 +243,18 @@ class Wave:
             else:
                 r = (a + b) & 0xFFFFFFFF
                 self.scc = a + b > 0xFFFFFFFF
+            self.wr32(o[0], np.uint32(r))
+            return None
+        if m in ("s_lshr_b32", "s_bfe_u32"):
+            a, b = int(self.rd32(o[1])[0]), int(self.rd32(o[2])[0])
+            if m == "s_lshr_b32":
+                r = a >> (b & 31)
+            else:  # field: offset bits [4:0], width bits [22:16]
+                w = (b >> 16) & 0x7F
+                if w >= 32:
+                    raise ValueError("s_bfe_u32 width >= 32")
+                r = (a >> (b & 31)) & ((1 << w) - 1)
+            self.scc = r != 0
             self.wr32(o[0], np.uint32(r))
             return None
         if m.startswith("s_cmp_"):
@@ -440,6 +467,15 @@ def make_kargs(prog: KernelText, buf_base: dict, scalars: dict, gofs) -> bytes:
     return bytes(b)
 
 
+def make_dispatch(dims: int, wg, grid) -> bytes:
+    """The 64-byte dispatch packet s[0:1] points at."""
+    b = bytearray(64)
+    struct.pack_into("<HH", b, 0, DISP_HEADER, dims | DISP_SETUP_RESERVED)
+    struct.pack_into("<HHH", b, 4, *wg)
+    struct.pack_into("<III", b, 0xc, *grid)
+    return bytes(b)
+
+
 def run_ndrange(text: str, buffers: dict, scalars: dict, groups=(2, 1), gofs=(0, 0, 0)):
     """Run every work-group of an NDRange of ``groups`` work-groups (per dim).
 
@@ -456,6 +492,7 @@ def run_ndrange(text: str, buffers: dict, scalars: dict, groups=(2, 1), gofs=(0,
     kargs = make_kargs(prog, base, scalars, gofs)
     c0, c1 = prog.cws[0], prog.cws[1] if prog.dims > 1 else 1
     g1n = groups[1] if prog.dims > 1 else 1
+    disp = make_dispatch(prog.dims, (c0, c1, 1), (groups[0] * c0, g1n * c1, 1))
     for g1 in range(g1n):
         for g0 in range(groups[0]):
             n = c0 * c1
@@ -464,6 +501,6 @@ def run_ndrange(text: str, buffers: dict, scalars: dict, groups=(2, 1), gofs=(0,
                 active = lanes < n
                 lid0 = np.where(active, lanes % c0, 0).astype(np.uint32)
                 lid1 = np.where(active, lanes // c0, 0).astype(np.uint32)
-                wave = Wave(prog, mem, kargs, (lid0, lid1, np.zeros(W, np.uint32)), (g0, g1, 0), active)
+                wave = Wave(prog, mem, kargs, (lid0, lid1, np.zeros(W, np.uint32)), (g0, g1, 0), active, disp)
                 wave.run()
     return prog

@@ -398,6 +398,13 @@ def call(nm, args, env: Env):
         d = int(args[0][1])
         key = {"get_global_id": "gid", "get_local_id": "lid", "get_group_id": "grp", "get_global_offset": "gofs"}[nm]
         return "uint", np.uint32(env.ids[key][d])
+    if nm in ("get_global_size", "get_num_groups"):
+        want(1)
+        d = int(args[0][1])
+        return "uint", np.uint32(env.ids["gsize" if nm == "get_global_size" else "ngrp"][d])
+    if nm == "get_work_dim":
+        want(0)
+        return "uint", np.uint32(env.ids["wdim"])
     if nm == "fma":
         want(3)
         tys = {a[0] for a in args}
@@ -473,7 +480,8 @@ def run_ndrange(k: Kernel, buffers, scalars, cws, dims, groups=(2, 1), gofs=(0, 
             for l1 in range(c1):
                 for l0 in range(c0):
                     ids = {"lid": (l0, l1, 0), "grp": (g0, g1, 0), "gofs": gofs,
-                           "gid": ((g0 * c0 + l0 + gofs[0]) & 0xFFFFFFFF, (g1 * c1 + l1 + gofs[1]) & 0xFFFFFFFF, 0)}
+                           "gid": ((g0 * c0 + l0 + gofs[0]) & 0xFFFFFFFF, (g1 * c1 + l1 + gofs[1]) & 0xFFFFFFFF, 0),
+                           "gsize": (groups[0] * c0, g1n * c1, 1), "ngrp": (groups[0], g1n, 1), "wdim": dims}
                     env = Env(k, buffers, scalars, ids)
                     with np.errstate(all="ignore"):
                         run_block(k.body, env)

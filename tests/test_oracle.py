@@ -6,6 +6,7 @@ Fig. 3, lattice laws, invariants of the dataflow, and brute force (a GCN
 interpreter running the assembly against an evaluator running the decompiled
 OpenCL on random buffers)."""
 import os
+import re
 
 import numpy as np
 import pytest
@@ -53,6 +54,41 @@ def test_ternary_is_one_instruction():
     r = oracle.decompile(gold("ternary_relu.s"))
     assert r.status == [0]
     assert r.text == gold("ternary_relu.cl")
+
+
+# ---- "Search for memory accesses": global size, number of groups, dimension count ------
+def test_dispatch_packet_system_values():
+    """s_load_dword from the dispatch packet pointer s[0:1] at 0xc/0x10 is get_global_size(0/1),
+    that shifted right by log2 of the work-group size of its dimension is get_num_groups (global
+    size / work-group size), s_bfe_u32 with field 0x20010 of the dword at 0x0 is get_work_dim();
+    other shifts and fields stay operators.  Written by hand, expected text derived by hand, and
+    run: the interpreter reads a real packet for a 3x2-group range of 16x8 work-groups."""
+    src = gold("sysvals_dispatch.s")
+    r = oracle.decompile(src)
+    assert r.status == [0]
+    assert r.text == gold("sysvals_dispatch.cl")
+    assert brute.check(src, r.text, groups=(3, 2)) is None
+    # each value is told apart by the run: the other dimension's count, a constant 1
+    # for the dimension count, the work-group size for the number of groups
+    for a, b in (("get_num_groups(1)", "get_num_groups(0)"), ("get_work_dim()", "1u"),
+                 ("get_global_size(0)", "get_global_size(1)")):
+        assert brute.check(src, r.text.replace(a, b, 1), groups=(3, 2)) is not None, (a, b)
+
+
+def test_brute_force_system_values():
+    """The mix of workload 1 with system values read through the dispatch packet and scalar
+    bit fields / shifts in 10% of integer leaves, on a 3x2-group range."""
+    b = _batch(6, 30, cws0=8, cws1=4, max_len=400)
+    seen = set()
+    for i in range(len(b)):
+        txt = b.kernel(i).decode()
+        r = oracle.decompile(txt)
+        assert r.status == [0]
+        seen |= {f for f in ("get_global_size(", "get_num_groups(", "get_work_dim()") if f in r.text}
+        seen |= {k for k, pat in (("field", r"s_bfe_u32 s15, s(?!15,)\d+,"), ("shift", r"s_lshr_b32 s15, s(?!15,)\d+,"))
+                 if re.search(pat, txt)}
+        assert brute.check(txt, r.text, seed=i, groups=(3, 2)) is None, f"kernel {i}"
+    assert len(seen) == 5, seen
 
 
 # ---- "Data type recovery": suffix typing -----------------------------------
@@ -136,7 +172,7 @@ def test_join_versions_are_minimal():
     assert used > 0
 
 
-@pytest.mark.parametrize("cfg", [1, 5])
+@pytest.mark.parametrize("cfg", [1, 5, 6])
 def test_output_is_wellformed_opencl(cfg):
     b = _batch(cfg, 60, max_len=900)
     out, oo, st = oracle.decompile_batch(b.text, b.offsets)
