@@ -39,6 +39,7 @@ WORKLOADS = {
     "config2": (2, 1_000_000),  # streamed in chunks (large_batch)
     "config3": (3, 64),
     "select": (5, 10_000),  # the batch mix with ternaries (v_cndmask_b32)
+    "sysval": (6, 10_000),  # the batch mix with dispatch-packet system values and scalar bit fields
 }
 
 

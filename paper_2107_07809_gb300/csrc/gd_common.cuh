@@ -49,7 +49,8 @@ enum : uint16_t {
   O_GLOBAL_LOAD_DWORD = 77, O_GLOBAL_LOAD_DWORDX2 = 78, O_GLOBAL_STORE_DWORD = 79, O_GLOBAL_STORE_DWORDX2 = 80,
   O_BUFFER_LOAD_DWORD = 81, O_BUFFER_STORE_DWORD = 82,
   O_V_CNDMASK_B32 = 83,  // the ternary ("Search for control structures"): vD = vcc ? src1 : src0
-  O_COUNT = 84
+  O_S_LSHR_B32 = 84, O_S_BFE_U32 = 85,  // scalar shift right, bit-field extract (get_num_groups, get_work_dim)
+  O_COUNT = 86
 };
 
 // ---- operand word: tag<<28 | count<<24 | payload -----------------------------------
@@ -75,7 +76,7 @@ static __constant__ char c_sig[O_COUNT][12] = {
     "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S",
     "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S",
     "V,c,S,S", "V,c,S,S,c", "V,c,S,S", "V,c,S,S,c", "W,S,W", "W,W,W", "W,W,W", "W,W,W,W",
-    "V,W,o", "W,W,o", "W,V,o", "W,W,o", "V,o,q,s", "V,o,q,s", "V,S,S,c"};
+    "V,W,o", "W,W,o", "W,V,o", "W,W,o", "V,o,q,s", "V,o,q,s", "V,S,S,c", "s,S,S", "s,S,S"};
 __device__ __forceinline__ int sig_count(uint16_t op) {
   const char* s = c_sig[op];
   int n = 0;
@@ -149,7 +150,7 @@ struct Node {
 enum : uint32_t { PART_ENTIRE = 0, PART_LO = 1, PART_HI = 2 };
 constexpr uint32_t kTop = 0xFFFFFFFFu;
 constexpr uint32_t kIdPhi = 1u << 28, kIdLeaf = 2u << 28;
-constexpr uint32_t LEAF_UNDEF = 0, LEAF_LID = 1, LEAF_GRP = 2, LEAF_KARG = 3;
+constexpr uint32_t LEAF_UNDEF = 0, LEAF_LID = 1, LEAF_GRP = 2, LEAF_KARG = 3, LEAF_DISP = 4;
 constexpr uint32_t kUndef = kIdLeaf << 2;
 __host__ __device__ __forceinline__ uint32_t mkref(uint32_t id, uint32_t part) { return (id << 2) | part; }
 __host__ __device__ __forceinline__ uint32_t rid(uint32_t r) { return r >> 2; }

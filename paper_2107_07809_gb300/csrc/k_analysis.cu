@@ -172,7 +172,8 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
   const Node& n = v.node(id);
   Cls c = classify(v, mkref(id, PART_ENTIRE));
   switch (c.c) {
-    case K_GID: case K_GIDNO: case K_LID: case K_GRP: case K_GOFSLO: return TY_UINT;
+    case K_GID: case K_GIDNO: case K_LID: case K_GRP: case K_GOFSLO: case K_GSIZE: case K_NGRP: case K_WDIM:
+      return TY_UINT;
     case K_GOFS64: case K_ARGPTR: case K_KARG: return TY_ULONG;
     case K_ARG32: case K_ARG64: return v.A[c.k].elem;
     case K_CONST32: case K_CONST64: case K_UNDEF: return TY_NONE;
@@ -185,6 +186,7 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
     case O_S_MUL_I32: return TY_INT;
     case O_S_ADD_U32: return TY_UINT;
     case O_S_LSHL_B32: return st(0);
+    case O_S_LSHR_B32: case O_S_BFE_U32: return TY_UINT;
     case O_V_ADD_U32: case O_V_SUB_U32: case O_V_MUL_LO_U32: case O_V_MAD_U32_U24: case O_V_MUL_U32_U24: return TY_UINT;
     case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_CNDMASK_B32: return tjoin(st(0), st(1));
     case O_V_LSHLREV_B32: return st(1);

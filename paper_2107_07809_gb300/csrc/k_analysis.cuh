@@ -80,11 +80,16 @@ __device__ __forceinline__ uint32_t nsrc(const KView& v, const Node& n, int q) {
 
 // classes of values
 enum : uint8_t { K_NONE = 0, K_LID, K_GRP, K_KARG, K_UNDEF, K_GOFS64, K_GOFSLO, K_MULGRP, K_GIDNO, K_GID, K_ARGPTR,
-                 K_ARG32, K_ARG64, K_CONST32, K_CONST64 };
+                 K_ARG32, K_ARG64, K_CONST32, K_CONST64,
+                 K_DISP,    // the dispatch packet pointer s[0:1]
+                 K_DISP0,   // the packet's first dword (header, setup): an intermediate like K_MULGRP
+                 K_GSIZE,   // get_global_size(d): the dword at 0xc + 4d
+                 K_NGRP,    // get_num_groups(d): global size >> log2(work-group size)
+                 K_WDIM };  // get_work_dim(): field 0x20010 (offset 16, width 2) of the first dword
 struct Cls {
   uint8_t c, k;
 };
-__device__ __forceinline__ bool leaf_like(uint8_t c) { return c != K_NONE && c != K_MULGRP; }
+__device__ __forceinline__ bool leaf_like(uint8_t c) { return c != K_NONE && c != K_MULGRP && c != K_DISP0; }
 __device__ __forceinline__ bool ty64(uint8_t t) { return t == TY_LONG || t == TY_ULONG || t == TY_DOUBLE || t == TY_TOP64; }
 __device__ __forceinline__ int ilog2_exact(uint32_t x) {
   return (x && !(x & (x - 1)) && x < (1u << 31)) ? (31 - __clz(x)) : -1;
@@ -92,7 +97,8 @@ __device__ __forceinline__ int ilog2_exact(uint32_t x) {
 
 // A class other than none is derived from operands at most three levels down
 // (get_global_id <- group id * size + local id <- group id * size <- group id;
-// a settings load <- the settings pointer), and an operand without a class
+// a settings load <- the settings pointer; get_num_groups / get_work_dim <- a
+// dispatch packet load <- the packet pointer), and an operand without a class
 // can only keep a pattern from matching.  So the recursion stops below
 // kClassDepth levels without changing any class, which bounds the work on
 // long chains of additions.
@@ -102,6 +108,12 @@ static __device__ Cls classify_d(const KView& v, uint32_t r, int d);
 static __device__ GD_MATCH_INLINE Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide, int d) {
   Cls none{K_NONE, 0};
   Cls base = classify_d(v, nsrc(v, n, 0), d + 1);
+  if (base.c == K_DISP) {  // dispatch packet: header/setup dword at 0x0, global sizes at 0xc/0x10/0x14
+    if (wide || part != PART_ENTIRE) return none;
+    if (n.cval == 0) return Cls{K_DISP0, 0};
+    if (n.cval == 0xc || n.cval == 0x10 || n.cval == 0x14) return Cls{K_GSIZE, (uint8_t)((n.cval - 0xc) / 4)};
+    return none;
+  }
   if (base.c != K_KARG || (n.cval & 7u)) return none;
   uint32_t slot = n.cval / 8;
   if (slot >= v.K->nargs) return none;
@@ -143,6 +155,7 @@ static __device__ GD_MATCH_INLINE Cls classify_d(const KView& v, uint32_t r, int
     if (kind == LEAF_LID) return Cls{K_LID, (uint8_t)k};
     if (kind == LEAF_GRP) return Cls{K_GRP, (uint8_t)k};
     if (kind == LEAF_KARG) return Cls{K_KARG, 0};
+    if (kind == LEAF_DISP) return Cls{K_DISP, 0};
     return none;
   }
   if (!r_node(r)) return none;
@@ -174,6 +187,18 @@ static __device__ GD_MATCH_INLINE Cls classify_d(const KView& v, uint32_t r, int
         if (l >= 0 && const_src(v, n, 1) == l) return Cls{K_MULGRP, a.k};
       }
       return none;
+    }
+    case O_S_LSHR_B32: {  // global size / work-group size, the size a power of two
+      Cls a = classify_d(v, nsrc(v, n, 0), d + 1);
+      if (a.c == K_GSIZE) {
+        int l = ilog2_exact((uint32_t)cw(a.k));
+        if (l >= 0 && const_src(v, n, 1) == l) return Cls{K_NGRP, a.k};
+      }
+      return none;
+    }
+    case O_S_BFE_U32: {
+      Cls a = classify_d(v, nsrc(v, n, 0), d + 1);
+      return (a.c == K_DISP0 && const_src(v, n, 1) == 0x20010) ? Cls{K_WDIM, 0} : none;
     }
     case O_V_ADD_U32: {
       Cls a = classify_d(v, nsrc(v, n, 0), d + 1), b = classify_d(v, nsrc(v, n, 1), d + 1);

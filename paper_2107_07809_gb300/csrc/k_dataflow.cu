@@ -60,7 +60,7 @@ __device__ int idefs(const Batch& b, const KHdr& K, const RegMap& M, uint32_t i,
       d[n++] = {reg_of(M, r.opnd[0], 2), mkref(base + 1, PART_LO)};
       d[n++] = {reg_of(M, r.opnd[0], 3), mkref(base + 1, PART_HI)};
       return n;
-    case O_S_ADD_U32: case O_S_MUL_I32: case O_S_LSHL_B32:
+    case O_S_ADD_U32: case O_S_MUL_I32: case O_S_LSHL_B32: case O_S_LSHR_B32: case O_S_BFE_U32:
       d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)};
       d[n++] = {M.scc(), kUndef};
       return n;
@@ -341,6 +341,8 @@ __device__ __forceinline__ uint32_t entry_value(const KHdr& K, uint32_t r) {
     if (K.useargs && s >= 6 && s < 6 + K.dims && s < 9) return leafref(LEAF_GRP, s - 6, PART_ENTIRE);
     if (K.sgprs > 5 && s == 4) return leafref(LEAF_KARG, 0, PART_LO);
     if (K.sgprs > 5 && s == 5) return leafref(LEAF_KARG, 0, PART_HI);
+    if (K.sgprs > 1 && s == 0) return leafref(LEAF_DISP, 0, PART_LO);  // the dispatch packet pointer
+    if (K.sgprs > 1 && s == 1) return leafref(LEAF_DISP, 0, PART_HI);
   }
   return kUndef;
 }

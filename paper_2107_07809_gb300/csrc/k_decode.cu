@@ -50,7 +50,8 @@ static const OpName kOps[O_COUNT] = {
     {"v_subb_co_u32", "V,c,S,S,c"}, {"v_lshlrev_b64", "W,S,W"}, {"v_add_f64", "W,W,W"}, {"v_mul_f64", "W,W,W"},
     {"v_fma_f64", "W,W,W,W"}, {"global_load_dword", "V,W,o"}, {"global_load_dwordx2", "W,W,o"},
     {"global_store_dword", "W,V,o"}, {"global_store_dwordx2", "W,W,o"}, {"buffer_load_dword", "V,o,q,s"},
-    {"buffer_store_dword", "V,o,q,s"}, {"v_cndmask_b32", "V,S,S,c"},
+    {"buffer_store_dword", "V,o,q,s"}, {"v_cndmask_b32", "V,S,S,c"}, {"s_lshr_b32", "s,S,S"},
+    {"s_bfe_u32", "s,S,S"},
 };
 
 constexpr int kHash = 512;

@@ -250,7 +250,8 @@ struct Em {
     if (op_scmp(op) || op_vcmp(op)) return TY_INT;
     switch (op) {
       case O_S_ADD_U32: case O_V_ADD_U32: case O_V_SUB_U32: case O_V_MUL_LO_U32: case O_V_MAD_U32_U24:
-      case O_V_MUL_U32_U24: case O_V_LSHRREV_B32: case O_V_ADD_CO_U32: case O_V_SUB_CO_U32: return TY_UINT;
+      case O_V_MUL_U32_U24: case O_V_LSHRREV_B32: case O_V_ADD_CO_U32: case O_V_SUB_CO_U32: case O_S_LSHR_B32:
+      case O_S_BFE_U32: return TY_UINT;
       case O_S_MUL_I32: case O_V_ASHRREV_I32: return TY_INT;
       case O_S_LSHL_B32: case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_LSHLREV_B32:
       case O_V_LSHLREV_B64: case O_V_CNDMASK_B32: return T;
@@ -272,8 +273,9 @@ struct Em {
     }
     Cls c = classify(v, r);
     switch (c.c) {
-      case K_UNDEF: case K_LID: case K_GRP: case K_GID: case K_GIDNO: case K_GOFSLO: return TY_UINT;
-      case K_GOFS64: case K_ARGPTR: case K_KARG: return TY_ULONG;
+      case K_UNDEF: case K_LID: case K_GRP: case K_GID: case K_GIDNO: case K_GOFSLO: case K_GSIZE: case K_NGRP:
+      case K_WDIM: return TY_UINT;
+      case K_GOFS64: case K_ARGPTR: case K_KARG: case K_DISP: return TY_ULONG;
       case K_ARG32: case K_ARG64: return v.A[c.k].elem;
       case K_CONST32: {
         uint8_t t = want == TY_NONE ? TY_UINT : want;
@@ -335,7 +337,10 @@ struct Em {
       case K_GOFSLO: case K_GOFS64: w.s("get_global_offset("); w.u64(c.k); w.c(')'); return;
       case K_ARG32: case K_ARG64: name(c.k); return;
       case K_ARGPTR: w.s("(ulong)"); name(c.k); return;
-      case K_KARG: partial = true; w.s("0UL"); return;
+      case K_KARG: case K_DISP: partial = true; w.s("0UL"); return;
+      case K_GSIZE: w.s("get_global_size("); w.u64(c.k); w.c(')'); return;
+      case K_NGRP: w.s("get_num_groups("); w.u64(c.k); w.c(')'); return;
+      case K_WDIM: w.s("get_work_dim()"); return;
       case K_CONST32: {
         uint8_t t = want == TY_NONE ? TY_UINT : want;
         if (twidth(t) == 64) t = TY_UINT;
@@ -477,6 +482,24 @@ struct Em {
       case O_S_ADD_U32: return binop(n, "+", TY_UINT, d);
       case O_S_MUL_I32: return binop(n, "*", TY_INT, d);
       case O_S_LSHL_B32: return shift(n, 0, 1, T, "<<", 31, d);
+      case O_S_LSHR_B32: return shift(n, 0, 1, TY_UINT, ">>", 31, d);
+      case O_S_BFE_U32: {
+        // field operand: offset bits [4:0], width bits [22:16]; (src >> offset) masked to
+        // width bits.  A field that is not a constant, or 32 bits wide or more, is not written.
+        uint32_t f = nsrc(v, n, 1);
+        if (!(r_node(f) && rpart(f) == PART_ENTIRE && v.node(rid(f)).kind == N_CONST)) break;
+        uint32_t c = v.node(rid(f)).cval, off = c & 31u, wd = (c >> 16) & 0x7Fu;
+        if (wd >= 32) break;
+        if (wd == 0) { w.s("0u"); return; }
+        w.s("((");
+        S(n, 0, TY_UINT, d);
+        w.s(" >> ");
+        w.u64(off);
+        w.s(") & ");
+        lit32(w, (1u << wd) - 1u, TY_UINT);
+        w.c(')');
+        return;
+      }
       case O_V_ADD_U32: return binop(n, "+", TY_UINT, d);
       case O_V_SUB_U32: return binop(n, "-", TY_UINT, d);
       case O_V_MUL_LO_U32: return binop(n, "*", TY_UINT, d);

@@ -50,6 +50,10 @@ def test_ir_parity_ternary_mix(dec):
     _check_ir(dec, _files(5, 150))
 
 
+def test_ir_parity_sysval_mix(dec):
+    _check_ir(dec, _files(6, 150))
+
+
 def test_ir_parity_multi_kernel_files(dec):
     ks = _files(1, 12, max_len=400)
     files = [b"".join(ks[0:4]), b"leading junk\n" + b"".join(ks[4:9]), ks[9], b"", b"".join(ks[10:12])]
@@ -81,6 +85,36 @@ def test_text_parity_config0(dec):
 def test_text_parity_ternary_mix(dec):
     """the batch mix with selects (v_cndmask_b32) in 15% of 32-bit operations"""
     _check_text(dec, _files(5, 600))
+
+
+def test_text_parity_sysval_mix(dec):
+    """the batch mix with dispatch-packet system values and scalar bit fields in 10% of integer leaves"""
+    _check_text(dec, _files(6, 600))
+
+
+def test_text_parity_sysval_edge_cases(dec):
+    """dispatch packet loads and fields that are not system values: other offsets, a wide load,
+    shifts by the other dimension's size, fields of width 0 and 32, a field and a shift amount
+    held in registers"""
+    import os
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    base = open(os.path.join(g, "sysvals_dispatch.s"), "rb").read()
+    files = [
+        base.replace(b"s_load_dword s10, s[0:1], 0xc", b"s_load_dword s10, s[0:1], 0x4"),
+        base.replace(b"s_load_dword s10, s[0:1], 0xc", b"s_load_dword s10, s[0:1], 0x18"),
+        base.replace(b"s_load_dword s12, s[0:1], 0x0", b"s_load_dword s12, s[0:1], 0x8"),
+        base.replace(b"s_load_dword s11, s[0:1], 0x10", b"s_load_dwordx2 s[14:15], s[0:1], 0x10\n        s_mov_b32 s11, s14"),
+        base.replace(b"s_lshr_b32 s11, s11, 3", b"s_lshr_b32 s11, s11, 4"),
+        base.replace(b"s_lshr_b32 s11, s11, 3", b"s_lshr_b32 s11, s11, s13"),
+        base.replace(b"s_bfe_u32 s12, s12, 0x20010", b"s_bfe_u32 s12, s12, 0x30010"),
+        base.replace(b"s_bfe_u32 s13, s10, 0x40004", b"s_bfe_u32 s13, s10, 0x4"),
+        base.replace(b"s_bfe_u32 s13, s10, 0x40004", b"s_bfe_u32 s13, s10, 0x200004"),
+        base.replace(b"s_bfe_u32 s13, s10, 0x40004", b"s_bfe_u32 s13, s10, s11"),
+        base.replace(b"s_load_dword s10, s[0:1], 0xc", b"s_load_dword s10, s[2:3], 0xc"),
+        base.replace(b".dims xy", b".dims x").replace(b".cws 16, 8, 1", b".cws 16, 1, 1"),
+    ]
+    assert len(set(files)) == len(files)
+    _check_text(dec, files)
 
 
 def test_text_parity_golden(dec):
