@@ -501,8 +501,12 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   CK(cudaMemsetAsync(&tot[13], 0, 4, s));
   // one thread per statement while staging (measured faster than a warp per
   // statement); one warp per statement for the few long ones redone in place
+  uint32_t* skey = W.get<uint32_t>("sub_key", (size_t)NS2 + 1);
+  uint32_t* sorder = W.get<uint32_t>("sub_order", (size_t)NS2 + 1);
+  uint32_t* shist = W.get<uint32_t>("sub_hist", shape_buckets() + 1);
+  launch_sub_order(b, items, sitem, sub0, prank, plist, NS2, skey, shist, sorder, sc2, s);
   CK(cudaEventRecord(h->ev[kStages + 1], s));
-  launch_items(b, items, sitem, sub0, prank, plist, NS2, nullptr, ilen, ioff, stage, ovl, &tot[13], 0, s);
+  launch_items(b, items, sitem, sub0, prank, plist, NS2, sorder, ilen, ioff, stage, ovl, &tot[13], 0, s);
   CK(cudaEventRecord(h->ev[kStages + 2], s));
   if (NS2) launch_scan(ilen, ioff, NS2, 0, false, sc2, &tot[11], b.err, s);
   CK(cudaGetLastError());

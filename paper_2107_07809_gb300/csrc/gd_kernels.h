@@ -174,6 +174,10 @@ constexpr uint32_t kEmitSlot = 256;  // staging bytes per emission sub-item
 void launch_print_list(Batch& b, uint32_t* flag, const uint32_t* rank, uint32_t* list, int phase, cudaStream_t s);
 void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* prank, uint32_t* weight,
                      const uint32_t* sub0, uint32_t* sub_item, uint32_t NS2, int phase, cudaStream_t s);
+void launch_sub_order(Batch& b, const Item* items, const uint32_t* sub_item, const uint32_t* sub0,
+                      const uint32_t* prank, const uint32_t* pinstr, uint32_t N, uint32_t* key, uint32_t* hist,
+                      uint32_t* order, ScanScratch sc, cudaStream_t s);
+uint32_t shape_buckets();
 void launch_items(Batch& b, const Item* items, const uint32_t* sub_item, const uint32_t* sub0, const uint32_t* prank,
                   const uint32_t* pinstr, uint32_t N, const uint32_t* list, uint32_t* item_len,
                   const uint32_t* item_off, uint8_t* stage, uint32_t* ovf_list, uint32_t* ovf_count,

@@ -294,34 +294,133 @@ struct Em {
   }
 
   // ---- printing -------------------------------------------------------------
-  __device__ __noinline__ void E(uint32_t r, uint8_t want, int d) {
-    uint8_t t = expr_type(r, want);
-    conv_open(t, want);
-    ex(r, want, d);
-    conv_close(t, want);
+  // P(r, want, d) prints value r for a use of type `want`: a conversion when the value's own type
+  // differs, then the value (a join variable, a recovered system value or argument, a literal, a
+  // variable, or the node's expression with its operands printed by P again).  With `top` set it
+  // prints node rid(r)'s own expression, ignoring its variable, with no conversion (the right-hand
+  // side of a statement, a branch condition).  The operand helpers below are inlined into P, so
+  // an expression level costs one call frame.
+  __device__ __forceinline__ void cv_open(uint8_t t, uint8_t want) {
+    if (want != TY_NONE && t != want) conv_open(t, want);
+  }
+  __device__ __forceinline__ void cv_close(uint8_t t, uint8_t want) {
+    if (want != TY_NONE && t != want) conv_close(t, want);
   }
 
-  __device__ void name(uint32_t slot) { w.mem(b->text + v.A[slot].name_off, v.A[slot].name_len); }
-
-  __device__ __noinline__ void ex(uint32_t r, uint8_t want, int d) {
-    if (d > 200) {
-      deep = true;
-      w.s("0u");
-      return;
-    }
-    r = fwd(v, r);
-    if (r_phi(r)) {
-      int32_t x = phivar(r);
-      if (x < 0) {
-        partial = true;
-        w.s("0u");
-      } else {
-        w.s("var");
-        w.u64((uint64_t)x);
+  __device__ __noinline__ void P(uint32_t r, uint8_t want, int d, bool top) {
+    uint32_t id;
+    uint8_t t = TY_NONE;
+    if (top) {
+      id = rid(r);
+    } else {
+      r = fwd(v, r);
+      if (r_phi(r)) {
+        const int32_t x = phivar(r);
+        t = x < 0 ? TY_UINT : vt[x];
+        cv_open(t, want);
+        if (d > 200) {
+          deep = true;
+          w.s("0u");
+        } else if (x < 0) {
+          partial = true;
+          w.s("0u");
+        } else {
+          w.s("var");
+          w.u64((uint64_t)x);
+        }
+        cv_close(t, want);
+        return;
       }
-      return;
+      const Cls c = (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) ? Cls{v.cc[rid(r)], v.ck[rid(r)]} : classify(v, r);
+      bool cls = true;
+      switch (c.c) {
+        case K_UNDEF: case K_LID: case K_GRP: case K_GID: case K_GIDNO: case K_GOFSLO: case K_GSIZE: case K_NGRP:
+        case K_WDIM: t = TY_UINT; break;
+        case K_GOFS64: case K_ARGPTR: case K_KARG: case K_DISP: t = TY_ULONG; break;
+        case K_ARG32: case K_ARG64: t = v.A[c.k].elem; break;
+        case K_CONST32: {
+          const uint8_t u = want == TY_NONE ? TY_UINT : want;
+          t = twidth(u) == 64 ? TY_UINT : u;
+          break;
+        }
+        case K_CONST64: {
+          const uint8_t u = want == TY_NONE ? TY_ULONG : want;
+          t = twidth(u) == 32 ? TY_ULONG : u;
+          break;
+        }
+        default: cls = false;
+      }
+      if (cls) {
+        cv_open(t, want);
+        if (d > 200) {
+          deep = true;
+          w.s("0u");
+        } else {
+          leaf(c, r, want);
+        }
+        cv_close(t, want);
+        return;
+      }
+      if (!r_node(r)) {
+        cv_open(TY_UINT, want);
+        if (d > 200) deep = true;
+        else partial = true;
+        w.s("0u");
+        cv_close(TY_UINT, want);
+        return;
+      }
+      id = rid(r);
+      if (rpart(r) != PART_ENTIRE) {
+        cv_open(TY_UINT, want);
+        if (d > 200) {
+          deep = true;
+          w.s("0u");
+        } else {
+          const uint32_t whole = mkref(id, PART_ENTIRE);
+          const bool dbl = expr_type(whole, TY_NONE) == TY_DOUBLE;
+          if (rpart(r) == PART_LO) {
+            w.s(dbl ? "(uint)as_ulong(" : "(uint)");
+            P(whole, TY_NONE, d + 1, false);
+            if (dbl) w.c(')');
+          } else {
+            w.s(dbl ? "(uint)(as_ulong(" : "(uint)(");
+            P(whole, TY_NONE, d + 1, false);
+            w.s(dbl ? ") >> 32)" : " >> 32)");
+          }
+        }
+        cv_close(TY_UINT, want);
+        return;
+      }
+      if (vo[id] >= 0) {
+        const int32_t x = vo[id];
+        t = vt[x];
+        cv_open(t, want);
+        if (d > 200) {
+          deep = true;
+          w.s("0u");
+        } else {
+          w.s("var");
+          w.u64((uint64_t)x);
+        }
+        cv_close(t, want);
+        return;
+      }
+      t = node_expr_type(id);
+      cv_open(t, want);
+      if (d > 200) {
+        deep = true;
+        w.s("0u");
+        cv_close(t, want);
+        return;
+      }
+      ++d;
     }
-    Cls c = classify(v, r);
+    body(id, d);
+    if (!top) cv_close(t, want);
+  }
+
+  // a recovered system value, argument or literal
+  __device__ __forceinline__ void leaf(Cls c, uint32_t r, uint8_t want) {
     switch (c.c) {
       case K_UNDEF: partial = true; w.s("0u"); return;
       case K_LID: w.s("get_local_id("); w.u64(c.k); w.c(')'); return;
@@ -356,36 +455,12 @@ struct Em {
         return;
       }
     }
-    if (!r_node(r)) {
-      partial = true;
-      w.s("0u");
-      return;
-    }
-    uint32_t id = rid(r);
-    if (rpart(r) != PART_ENTIRE) {
-      uint32_t whole = mkref(id, PART_ENTIRE);
-      bool dbl = expr_type(whole, TY_NONE) == TY_DOUBLE;
-      if (rpart(r) == PART_LO) {
-        w.s(dbl ? "(uint)as_ulong(" : "(uint)");
-        ex(whole, TY_NONE, d + 1);
-        if (dbl) w.c(')');
-      } else {
-        w.s(dbl ? "(uint)(as_ulong(" : "(uint)(");
-        ex(whole, TY_NONE, d + 1);
-        w.s(dbl ? ") >> 32)" : " >> 32)");
-      }
-      return;
-    }
-    if (vo[id] >= 0) {
-      w.s("var");
-      w.u64((uint64_t)vo[id]);
-      return;
-    }
-    node_expr(id, d + 1);
   }
 
-  __device__ void S(const Node& n, int q, uint8_t t, int d) { E(nsrc(v, n, q), t, d); }
-  __device__ __noinline__ void binop(const Node& n, const char* sym, uint8_t ot, int d) {
+  __device__ void name(uint32_t slot) { w.mem(b->text + v.A[slot].name_off, v.A[slot].name_len); }
+
+  __device__ __forceinline__ void S(const Node& n, int q, uint8_t t, int d) { P(nsrc(v, n, q), t, d, false); }
+  __device__ __forceinline__ void binop(const Node& n, const char* sym, uint8_t ot, int d) {
     w.c('(');
     S(n, 0, ot, d);
     w.c(' ');
@@ -394,18 +469,18 @@ struct Em {
     S(n, 1, ot, d);
     w.c(')');
   }
-  __device__ __noinline__ void shamt(uint32_t f, uint32_t mask, int d) {
+  __device__ __forceinline__ void shamt(uint32_t f, uint32_t mask, int d) {
     if (r_node(f) && rpart(f) == PART_ENTIRE && v.node(rid(f)).kind == N_CONST) {
       w.u64(v.node(rid(f)).cval & mask);
       return;
     }
     w.c('(');
-    E(f, TY_UINT, d);
+    P(f, TY_UINT, d, false);
     w.s(" & ");
     w.u64(mask);
     w.s("u)");
   }
-  __device__ __noinline__ void call3(const char* fn, const Node& n, int k, uint8_t t, int d) {
+  __device__ __forceinline__ void call3(const char* fn, const Node& n, int k, uint8_t t, int d) {
     w.s(fn);
     w.c('(');
     for (int q = 0; q < k; ++q) {
@@ -414,11 +489,11 @@ struct Em {
     }
     w.c(')');
   }
-  __device__ __noinline__ void cast1(const char* pre, const Node& n, uint8_t t, int d) {
+  __device__ __forceinline__ void cast1(const char* pre, const Node& n, uint8_t t, int d) {
     w.s(pre);
     S(n, 0, t, d);
   }
-  __device__ __noinline__ void shift(const Node& n, int vq, int sq, uint8_t t, const char* sym, uint32_t mask, int d) {
+  __device__ __forceinline__ void shift(const Node& n, int vq, int sq, uint8_t t, const char* sym, uint32_t mask, int d) {
     w.c('(');
     S(n, vq, t, d);
     w.c(' ');
@@ -434,19 +509,20 @@ struct Em {
       name(m.arg);
       w.c('[');
       if (m.idx == kTop) w.c('0');
-      else E(m.idx, TY_NONE, d);
+      else P(m.idx, TY_NONE, d, false);
       w.c(']');
       return;
     }
     w.s("*((__global ");
     w.s(width == 8 ? "ulong" : "uint");
     w.s(" *)(");
-    E(nsrc(v, n, 0), TY_ULONG, d);
+    P(nsrc(v, n, 0), TY_ULONG, d, false);
     w.s("))");
   }
 
-  // a node's own expression (ignoring its variable)
-  __device__ __noinline__ void node_expr(uint32_t id, int d) {
+  // a node's own expression (ignoring its variable), operands at depth d
+  __device__ __noinline__ void node_expr(uint32_t id, int d) { P(mkref(id, PART_ENTIRE), TY_NONE, d, true); }
+  __device__ __forceinline__ void body(uint32_t id, int d) {
     const Node& n = v.node(id);
     uint8_t T = NT(id);
     if (n.kind == N_PAIR) {
@@ -578,7 +654,7 @@ struct Em {
           w.indent(lvl);
           memref(n, width, 0);
           w.s(" = ");
-          E(nsrc(v, n, 1), elem, 0);
+          P(nsrc(v, n, 1), elem, 0, false);
           w.s(";\n");
           continue;
         }
@@ -607,7 +683,7 @@ struct Em {
     w.s("var");
     w.u64((uint64_t)x);
     w.s(" = ");
-    E(src, vt[x], 0);
+    P(src, vt[x], 0, false);
     w.s(";\n");
   }
 
@@ -641,7 +717,7 @@ struct Em {
       }
     }
     if (!positive) w.s("!(");
-    E(c, TY_NONE, 0);
+    P(c, TY_NONE, 0, false);
     if (!positive) w.c(')');
   }
 };
@@ -1039,7 +1115,10 @@ __global__ void __launch_bounds__(128)
     }
   }
   const ArgRec* A = b.args + (size_t)k * kMaxArgs;
-  Em em;
+  // the printer's state lives in shared memory: its fields (the writer's cursor above all) are
+  // read and written through `this` on every call, and local memory would send them through L1/L2
+  __shared__ Em s_em[128];
+  Em& em = s_em[threadIdx.x];
   em.v = make_view(b, K, k);
   em.b = &b;
   em.K = &K;
@@ -1211,6 +1290,95 @@ __global__ void __launch_bounds__(256)
     for (uint32_t q = lane; q < l; q += 32) out[o + q] = from[q];
   }
 }
+
+// Printing order.  Lanes of a warp that print statements of different shapes
+// walk different parts of the printer one after another (divergence, and an
+// instruction working set larger than the instruction cache).  Sub-items are
+// therefore printed in an order grouped by a shape key: the item kind, and for
+// a block statement the printing node's operation and the shape of its first
+// two operands (a variable, a recovered value, or the operation of an inlined
+// expression).  The order only decides which thread prints which sub-item;
+// every sub-item still prints into its own slot, so the output is unchanged.
+constexpr uint32_t kShapeBuckets = 16384;
+
+__device__ __forceinline__ uint32_t ref_shape(const KView& v, const int32_t* vo, uint32_t r) {
+  if (r == kTop) return 1;
+  if (r_phi(r)) return 2;
+  if (!r_node(r)) return 3;
+  const uint32_t id = rid(r);
+  if (rpart(r) != PART_ENTIRE) return 4;
+  if (vo[id] >= 0) return 5;
+  const uint8_t c = v.cc[id];
+  if (leaf_like(c)) return 8 + c;
+  const Node& n = v.node(id);
+  return n.kind == N_OP ? 32 + n.op : 28 + n.kind;
+}
+
+__global__ void __launch_bounds__(256)
+    k_sub_key(const __grid_constant__ Batch b, const Item* __restrict__ items, const uint32_t* __restrict__ sub_item,
+              const uint32_t* __restrict__ sub0, const uint32_t* __restrict__ prank, const uint32_t* __restrict__ pinstr,
+              uint32_t N, uint32_t* __restrict__ key, uint32_t* __restrict__ hist) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t kk = kShapeBuckets;  // lanes past the end take no part
+  if (t < N) {
+    const uint32_t i = sub_item[t];
+    const Item it = items[i];
+    const uint32_t kind = it.kl & 0xFF;
+    kk = kind;
+    if (kind == IT_BLOCK) {
+      const KHdr& K = b.kh[it.k];
+      const BlockRec& B = b.lblocks[K.first_lblock + it.a];
+      const uint32_t gi = pinstr[prank[K.first_instr + B.first] + (t - sub0[i])];
+      if (b.lblock_of[gi] == it.a) {
+        const KView v = make_view(b, K, it.k);
+        const int32_t* vo = b.var_of + 4 * (size_t)K.first_instr;
+        const uint32_t id = 4 * (gi - K.first_instr);
+        const Node& n = v.node(id);
+        uint32_t h = n.kind == N_OP ? n.op : 200u + n.kind, s0 = 0, s1 = 0;
+        if (n.kind == N_OP && op_store(n.op)) {
+          s0 = ref_shape(v, vo, nsrc(v, n, 1));
+          const uint32_t x = v.midx[id / 4];
+          s1 = v.marg[id / 4] == kNone ? 1 : (x == kTop ? 0 : ref_shape(v, vo, x));
+        } else if (n.kind == N_OP && !op_gload(n.op)) {
+          if (n.nsrc > 0) s0 = ref_shape(v, vo, nsrc(v, n, 0));
+          if (n.nsrc > 1) s1 = ref_shape(v, vo, nsrc(v, n, 1));
+        }
+        h = h * 0x9E3779B1u ^ (s0 * 0x85EBCA77u) ^ (s1 * 0xC2B2AE3Du);
+        h ^= h >> 15;
+        kk = 16 + h % (kShapeBuckets - 16);
+      }
+    }
+    key[t] = kk;
+  }
+  // one atomic per distinct key of the warp
+  const unsigned grp = __match_any_sync(0xFFFFFFFFu, kk);
+  if (kk < kShapeBuckets && (threadIdx.x & 31u) == (uint32_t)(__ffs(grp) - 1)) atomicAdd(&hist[kk], (uint32_t)__popc(grp));
+}
+
+__global__ void __launch_bounds__(256)
+    k_sub_scatter(const uint32_t* __restrict__ key, uint32_t N, uint32_t* __restrict__ cursor,
+                  uint32_t* __restrict__ order) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t kk = t < N ? key[t] : kShapeBuckets;
+  const unsigned grp = __match_any_sync(0xFFFFFFFFu, kk);
+  const uint32_t lane = threadIdx.x & 31u, leader = (uint32_t)(__ffs(grp) - 1);
+  uint32_t base = 0;
+  if (kk < kShapeBuckets && lane == leader) base = atomicAdd(&cursor[kk], (uint32_t)__popc(grp));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (kk < kShapeBuckets) order[base + __popc(grp & ((1u << lane) - 1u))] = t;
+}
+
+void launch_sub_order(Batch& b, const Item* items, const uint32_t* sub_item, const uint32_t* sub0,
+                      const uint32_t* prank, const uint32_t* pinstr, uint32_t N, uint32_t* key, uint32_t* hist,
+                      uint32_t* order, ScanScratch sc, cudaStream_t s) {
+  if (!N) return;
+  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kShapeBuckets, s);
+  k_sub_key<<<(N + 255) / 256, 256, 0, s>>>(b, items, sub_item, sub0, prank, pinstr, N, key, hist);
+  launch_scan(hist, hist, kShapeBuckets, 0, false, sc, nullptr, b.err, s);
+  k_sub_scatter<<<(N + 255) / 256, 256, 0, s>>>(key, N, hist, order);
+  launch_counter() += 2;
+}
+uint32_t shape_buckets() { return kShapeBuckets; }
 
 void launch_items(Batch& b, const Item* items, const uint32_t* sub_item, const uint32_t* sub0, const uint32_t* prank,
                   const uint32_t* pinstr, uint32_t N, const uint32_t* list, uint32_t* item_len,
