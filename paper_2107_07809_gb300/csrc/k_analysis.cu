@@ -417,42 +417,49 @@ void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint3
 
 // one thread per node: its class, its forwarded sources and, for a load or
 // store, its memory match; later stages read these instead of recomputing
-__global__ void k_node_cache(const __grid_constant__ Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck, uint32_t* __restrict__ sf,
-                             uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
-  uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= 4ull * b.I) return;
-  uint32_t gi = (uint32_t)(g / 4);
-  uint32_t k = b.ikern[gi];
+__global__ void __launch_bounds__(128)
+    k_node_cache(const __grid_constant__ Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck,
+                 uint32_t* __restrict__ sf, uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
+  // one thread per instruction, over its four node slots (most instructions
+  // define one value, so a thread per slot left three lanes in four idle)
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const uint32_t k = b.ikern[gi];
   const KHdr& K = b.kh[k];
   KView v = make_view(b, K, k);  // b carries no caches here
-  uint32_t id = (uint32_t)(g - 4ull * K.first_instr);
-  const Node& n = v.node(id);
-  Cls c{K_NONE, 0};
-  if (!K.bad && n.kind != N_NONE) c = classify(v, mkref(id, PART_ENTIRE));
-  cc[g] = c.c;
-  ck[g] = c.k;
-  for (int q = 0; q < 3; ++q) sf[3 * g + q] = (!K.bad && q < n.nsrc) ? fwd(v, n.src[q]) : kTop;
-  if ((g & 3) == 0) {
-    uint32_t a = kNone, x = kTop;
-    if (!K.bad && n.kind == N_OP && (op_gload(n.op) || op_store(n.op))) {
-      uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
-      Mem m = match_addr(v, fwd(v, n.src[0]), w);
-      if (m.ok) {
-        a = m.arg;
-        x = m.idx;
-      }
-    }
-    marg[gi] = a;
-    midx[gi] = x;
+  const bool bad = K.bad;
+  const uint32_t id0 = 4 * (gi - K.first_instr);
+  uint32_t cls = 0, clk = 0;
+  for (int s = 0; s < 4; ++s) {
+    const uint64_t g = 4ull * gi + s;
+    const Node& n = v.node(id0 + s);
+    Cls c{K_NONE, 0};
+    if (!bad && n.kind != N_NONE) c = classify(v, mkref(id0 + s, PART_ENTIRE));
+    cls |= (uint32_t)c.c << (8 * s);
+    clk |= (uint32_t)c.k << (8 * s);
+    for (int q = 0; q < 3; ++q) sf[3 * g + q] = (!bad && q < n.nsrc) ? fwd(v, n.src[q]) : kTop;
   }
+  reinterpret_cast<uint32_t*>(cc)[gi] = cls;
+  reinterpret_cast<uint32_t*>(ck)[gi] = clk;
+  uint32_t a = kNone, x = kTop;
+  const Node& n = v.node(id0);
+  if (!bad && n.kind == N_OP && (op_gload(n.op) || op_store(n.op))) {
+    uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
+    Mem m = match_addr(v, fwd(v, n.src[0]), w);
+    if (m.ok) {
+      a = m.arg;
+      x = m.idx;
+    }
+  }
+  marg[gi] = a;
+  midx[gi] = x;
 }
 
 void launch_node_cache(Batch& b, cudaStream_t s) {
   if (!b.I) return;
   Batch raw = b;
   raw.ncls = nullptr;
-  uint64_t n = 4ull * b.I;
-  k_node_cache<<<(uint32_t)((n + 255) / 256), 256, 0, s>>>(raw, b.ncls, b.nclsk, b.nsrcf, b.mem_arg, b.mem_idx);
+  k_node_cache<<<(b.I + 127) / 128, 128, 0, s>>>(raw, b.ncls, b.nclsk, b.nsrcf, b.mem_arg, b.mem_idx);
   ++launch_counter();
 }
 

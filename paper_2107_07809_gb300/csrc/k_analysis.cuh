@@ -143,6 +143,28 @@ __device__ __forceinline__ int64_t const_src(const KView& v, const Node& n, int 
   return const_of_f(v, nsrc(v, n, q));
 }
 
+// a scalar load (the only source of settings and dispatch packet values)
+__device__ __forceinline__ bool may_sload(const KView& v, uint32_t r) {
+  if (!r_node(r)) return false;
+  const Node& n = v.node(rid(r));
+  return n.kind == N_SLOAD64B ||
+         (n.kind == N_OP && (n.op == O_S_LOAD_DWORD || n.op == O_S_LOAD_DWORDX2 || n.op == O_S_LOAD_DWORDX4));
+}
+// a value that may be a part of the global id chain: the local id (a leaf),
+// group id * size, the offset-free id, or the low half of a global offset
+__device__ __forceinline__ bool may_gid_part(const KView& v, uint32_t r) {
+  if (r_leaf(r)) return true;
+  if (!r_node(r)) return false;
+  const Node& n = v.node(rid(r));
+  if (n.kind == N_SLOAD64B) return true;
+  if (n.kind != N_OP) return false;
+  switch (n.op) {
+    case O_S_LOAD_DWORD: case O_S_LOAD_DWORDX2: case O_S_LOAD_DWORDX4: case O_S_MUL_I32: case O_S_LSHL_B32:
+    case O_V_ADD_U32: case O_V_MAD_U32_U24: return true;
+  }
+  return false;
+}
+
 static __device__ GD_MATCH_INLINE Cls classify_d(const KView& v, uint32_t r, int d) {
   Cls none{K_NONE, 0};
   if (r == kUndef || r == kTop) return Cls{K_UNDEF, 0};
@@ -171,6 +193,28 @@ static __device__ GD_MATCH_INLINE Cls classify_d(const KView& v, uint32_t r, int
   if (n.op == O_S_LOAD_DWORDX2 || n.op == O_S_LOAD_DWORDX4) return settings_load(v, n, part, true, d);
   if (n.op == O_S_LOAD_DWORD) return settings_load(v, n, part, false, d);
   if (part != PART_ENTIRE) return none;
+  // Operand screens: each pattern below needs its operands to be of particular
+  // kinds (a leaf for the group or local id, a scalar load for a settings or
+  // packet value, one of the chain's operations), so an operand of any other
+  // kind gives no class and the recursion into it is skipped.  This only
+  // avoids work: the class returned is the same.
+  switch (n.op) {
+    case O_S_MUL_I32:
+      if (!r_leaf(nsrc(v, n, 0)) && !r_leaf(nsrc(v, n, 1))) return none;
+      break;
+    case O_S_LSHL_B32:
+      if (!r_leaf(nsrc(v, n, 0))) return none;
+      break;
+    case O_S_LSHR_B32: case O_S_BFE_U32:
+      if (!may_sload(v, nsrc(v, n, 0))) return none;
+      break;
+    case O_V_ADD_U32:
+      if (!may_gid_part(v, nsrc(v, n, 0)) || !may_gid_part(v, nsrc(v, n, 1))) return none;
+      break;
+    case O_V_MAD_U32_U24:
+      if (!r_leaf(nsrc(v, n, 2)) || (!r_leaf(nsrc(v, n, 0)) && !r_leaf(nsrc(v, n, 1)))) return none;
+      break;
+  }
   const uint32_t* cws = v.K->cws;
   auto cw = [&](int d) -> int64_t { return d < 3 ? (int64_t)cws[d] : -1; };
   switch (n.op) {
