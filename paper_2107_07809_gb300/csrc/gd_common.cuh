@@ -144,6 +144,7 @@ struct Node {
   uint32_t src[3];
   uint32_t cval;
 };
+static_assert(sizeof(Node) == 24, "Node is 24 bytes");
 
 // value references: id << 2 | part; ids: node = 4*instr+slot, join = 1<<28 | block<<10 | reg,
 // ABI leaf = 2<<28 | kind<<8 | k

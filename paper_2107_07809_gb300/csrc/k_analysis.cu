@@ -311,20 +311,23 @@ __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses
 // variable, and one exclusive scan numbers them all.
 __device__ __forceinline__ size_t vbase(const KHdr& K) { return (size_t)K.state_off + 4 * (size_t)K.first_instr; }
 
+// one thread per instruction over its four node slots
 __global__ void k_var_flag_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ vflag) {
-  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= 4ull * b.I) return;
-  const uint32_t gi = (uint32_t)(g >> 2), s = (uint32_t)(g & 3);
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const uint32_t bl = b.lblock_of[gi];
+  if (bl == kNone) return;
+  const uint32_t f4 = reinterpret_cast<const uint32_t*>(b.nflag)[gi];
+  if (!(f4 & 0x01010101u)) return;  // no slot is reached
   const uint32_t k = b.ikern[gi];
   const KHdr& K = b.kh[k];
   if (K.bad) return;
-  const uint32_t bl = b.lblock_of[gi];
-  if (bl == kNone) return;
   const KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
-  const uint32_t id = (uint32_t)(g - nb);
-  if (is_var_node(v, b.uses + nb, b.nflag + nb, id))
-    vflag[vbase(K) + (size_t)(bl + 1) * K.R + id] = 1;  // id = 4 * i + s
+  const uint32_t id0 = 4 * (gi - K.first_instr);
+  uint32_t* f = vflag + vbase(K) + (size_t)(bl + 1) * K.R;
+  for (uint32_t s = 0; s < 4; ++s)
+    if (((f4 >> (8 * s)) & 1) && is_var_node(v, b.uses + nb, b.nflag + nb, id0 + s)) f[id0 + s] = 1;
 }
 
 __global__ void k_var_flag_joins(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern,
@@ -343,25 +346,28 @@ __global__ void k_var_flag_joins(const __grid_constant__ Batch b, const uint32_t
 
 __global__ void k_var_nodes(const __grid_constant__ Batch b, const uint32_t* __restrict__ vflag,
                             const uint32_t* __restrict__ vpos) {
-  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= 4ull * b.I) return;
-  const uint32_t gi = (uint32_t)(g >> 2);
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
   const uint32_t k = b.ikern[gi];
   const KHdr& K = b.kh[k];
   if (K.bad) return;
   const size_t nb = 4 * (size_t)K.first_instr;
-  const uint32_t id = (uint32_t)(g - nb);
+  const uint32_t id0 = 4 * (gi - K.first_instr);
   const uint32_t bl = b.lblock_of[gi];
-  int32_t x = -1;
+  int4 x4 = make_int4(-1, -1, -1, -1);
   if (bl != kNone) {
-    const size_t at = vbase(K) + (size_t)(bl + 1) * K.R + id;
-    if (vflag[at]) {
-      x = (int32_t)(vpos[at] - vpos[vbase(K)]);
-      const KView v = make_view(b, K, k);
-      b.var_type[nb + K.state_off + x] = tresolve(b.ntype[nb + id], node_width(v, id));
+    const size_t at = vbase(K) + (size_t)(bl + 1) * K.R + id0;
+    const uint32_t base = vpos[vbase(K)];
+    int* x = &x4.x;
+    for (uint32_t s = 0; s < 4; ++s) {
+      if (vflag[at + s]) {
+        x[s] = (int32_t)(vpos[at + s] - base);
+        const KView v = make_view(b, K, k);
+        b.var_type[nb + K.state_off + x[s]] = tresolve(b.ntype[nb + id0 + s], node_width(v, id0 + s));
+      }
     }
   }
-  b.var_of[nb + id] = x;
+  reinterpret_cast<int4*>(b.var_of)[gi] = x4;
 }
 
 __global__ void k_var_joins(const __grid_constant__ Batch b, const uint32_t* __restrict__ blk_kern,
@@ -479,7 +485,7 @@ void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_word
   const uint64_t nc = (uint64_t)b.NS + 4ull * b.I;
   cudaMemsetAsync(vflag, 0, sizeof(uint32_t) * (nc + 1), s);
   if (b.I) {
-    k_var_flag_nodes<<<(uint32_t)((4ull * b.I + 255) / 256), 256, 0, s>>>(b, vflag);
+    k_var_flag_nodes<<<(b.I + 127) / 128, 128, 0, s>>>(b, vflag);
     ++launch_counter();
   }
   if (b.NLB) {
@@ -488,7 +494,7 @@ void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_word
   }
   launch_scan(vflag, vpos, (uint32_t)(nc + 1), 0, false, sc, nullptr, b.err, s);
   if (b.I) {
-    k_var_nodes<<<(uint32_t)((4ull * b.I + 255) / 256), 256, 0, s>>>(b, vflag, vpos);
+    k_var_nodes<<<(b.I + 127) / 128, 128, 0, s>>>(b, vflag, vpos);
     ++launch_counter();
   }
   if (b.NLB) {

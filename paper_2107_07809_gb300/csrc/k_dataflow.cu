@@ -11,7 +11,7 @@
 //   - the frontier closure for all registers at once: one warp per kernel, each
 //     lane owns 32 registers of a bitset, walking the frontier paths together;
 //   - values: the same warp walks blocks in reverse postorder, lanes over registers;
-//   - nodes: one thread per instruction, scanning back inside its block.
+//   - nodes: one warp per block, 32 instructions at a time (k_nodes).
 #include "gd_kernels.h"
 
 namespace gd {
@@ -421,10 +421,19 @@ struct NodeCtx {
   const KHdr* K;
   RegMap M;
   uint32_t i;
-  uint32_t* row;  // current register values of the block (its in-state, then updated)
+  const uint32_t* row;  // register values at the start of the current chunk of the block
+  // definitions of the chunk's instructions (lane m: instruction first + m), kNone when absent
+  const uint32_t (*dreg)[4];
+  const uint32_t (*dval)[4];
+  uint32_t lane;  // this instruction's place in the chunk
 };
 
+// value of register reg just before instruction c.i: the last definition of
+// an earlier instruction of the chunk, else the value at the chunk's start
 __device__ __forceinline__ uint32_t reg_now(const NodeCtx& c, uint32_t reg) {
+  for (int m = (int)c.lane - 1; m >= 0; --m)
+    for (int t = 3; t >= 0; --t)
+      if (c.dreg[m][t] == reg) return c.dval[m][t] == kTop ? kUndef : c.dval[m][t];
   uint32_t v = c.row[reg];
   return v == kTop ? kUndef : v;
 }
@@ -545,44 +554,78 @@ __device__ void build_instr_nodes(const Batch& b, const KHdr& K, NodeCtx& c, Nod
   if (r.op == O_V_ADD_CO_U32 || r.op == O_V_SUB_CO_U32) nodes[3].kind = N_CARRY;
 }
 
+// every node slot to "no node" (instruction i's four 24-byte slots as six 16-byte stores)
 __global__ void k_clear_nodes(const __grid_constant__ Batch b) {
-  uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= 4ull * b.I) return;
-  Node& n = b.nodes[g];
-  n.kind = N_NONE;
-  n.nsrc = 0;
-  n.fused = 0;
-  n.op = 0;
-  n.src[0] = n.src[1] = n.src[2] = kTop;
-  n.cval = 0;
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;  // 16-byte word
+  if (g >= 6ull * b.I) return;
+  // a cleared Node: kind, nsrc, fused, pad, op, pad2 = 0; src[3] = kTop; cval = 0
+  const uint32_t w = (uint32_t)(g % 6);  // word w of an instruction's 96 bytes: bytes 16w..16w+15
+  uint32_t q[4];
+  for (int e = 0; e < 4; ++e) {
+    const uint32_t byte = 16 * w + 4 * e, off = byte % 24;  // offset inside its Node
+    q[e] = (off >= 8 && off < 20) ? kTop : 0u;
+  }
+  reinterpret_cast<uint4*>(b.nodes)[g] = make_uint4(q[0], q[1], q[2], q[3]);
 }
 
-// one thread per logical block: copy the block's in-state into a working row,
-// then build each instruction's nodes and apply its definitions in order
-__global__ void k_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ rows, const uint32_t* __restrict__ blk_kern) {
-  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per logical block.  The warp copies the block's in-state into a
+// working row, then takes the block's instructions 32 at a time: every lane
+// lists its instruction's definitions in shared memory, builds its nodes
+// (a source register takes the last definition of an earlier lane, else the
+// row), and the chunk's last definition of each register goes into the row.
+// Carry halves fused with a low half of the same chunk are built after the
+// other nodes, as they read the low half's node.
+constexpr int kNodeWarps = 4;
+__global__ void __launch_bounds__(32 * kNodeWarps)
+    k_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ rows, const uint32_t* __restrict__ blk_kern) {
+  __shared__ uint32_t s_reg[kNodeWarps][32][4], s_val[kNodeWarps][32][4];
+  const uint32_t wp = threadIdx.x / 32, lane = threadIdx.x & 31u;
+  const uint32_t g = blockIdx.x * kNodeWarps + wp;
   if (g >= b.NLB) return;
-  uint32_t k = blk_kern[g];
+  const uint32_t k = blk_kern[g];
   const KHdr& K = b.kh[k];
   if (K.bad) return;
-  uint32_t bl = g - K.first_lblock;
+  const uint32_t bl = g - K.first_lblock;
   const BlockRec& B = b.lblocks[g];
   uint32_t* row = rows + K.state_off + (size_t)bl * K.R;
   const uint32_t* in = b.st_in + K.state_off + (size_t)bl * K.R;
-  for (uint32_t r = 0; r < K.R; ++r) row[r] = in[r];
+  for (uint32_t r = lane; r < K.R; r += 32) row[r] = in[r];
+  __syncwarp();
   NodeCtx c;
   c.b = &b;
   c.K = &K;
   c.M = RegMap{K.vgprs, K.sgprs};
   c.row = row;
+  c.dreg = s_reg[wp];
+  c.dval = s_val[wp];
+  c.lane = lane;
   Node* knodes = b.nodes + 4 * (size_t)K.first_instr;
-  for (uint32_t i = B.first; i < B.end; ++i) {
-    if (b.lblock_of[K.first_instr + i] != bl) continue;
-    c.i = i;
-    build_instr_nodes(b, K, c, knodes);
+  for (uint32_t first = B.first; first < B.end; first += 32) {
+    const uint32_t i = first + lane;
+    const bool mine = i < B.end && b.lblock_of[K.first_instr + i] == bl;
     Def d[4];
-    int n = idefs(b, K, c.M, i, d);
-    for (int t = 0; t < n; ++t) row[d[t].reg] = d[t].val;
+    const int n = mine ? idefs(b, K, c.M, i, d) : 0;
+    for (int t = 0; t < 4; ++t) {
+      s_reg[wp][lane][t] = t < n ? d[t].reg : kNone;
+      s_val[wp][lane][t] = t < n ? d[t].val : kNone;
+    }
+    __syncwarp();
+    c.i = i;
+    const uint32_t gi = K.first_instr + i;
+    const bool late = mine && b.fused[gi];  // fused carry half
+    if (mine && !late) build_instr_nodes(b, K, c, knodes);
+    __syncwarp();
+    if (late) build_instr_nodes(b, K, c, knodes);
+    // the row after the chunk: a register takes the chunk's last definition of it
+    for (int t = 0; t < n; ++t) {
+      const uint32_t reg = d[t].reg;
+      bool last = true;
+      for (int u = t + 1; u < n; ++u) last = last && d[u].reg != reg;
+      for (uint32_t m = lane + 1; m < 32 && last; ++m)
+        for (int u = 0; u < 4; ++u) last = last && s_reg[wp][m][u] != reg;
+      if (last) row[reg] = d[t].val;
+    }
+    __syncwarp();
   }
 }
 
@@ -651,12 +694,12 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
   k_versions<<<(b.K + 3) / 4, 128, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
   ++launch_counter();
   if (b.I) {
-    uint64_t nn = 4ull * b.I;
-    k_clear_nodes<<<(uint32_t)((nn + T - 1) / T), T, 0, s>>>(b);
+    const uint64_t nw = 6ull * b.I;
+    k_clear_nodes<<<(uint32_t)((nw + T - 1) / T), T, 0, s>>>(b);
     ++launch_counter();
   }
   if (b.NLB) {
-    k_nodes<<<(b.NLB + 63) / 64, 64, 0, s>>>(b, d.rows, d.blk_kern);
+    k_nodes<<<(b.NLB + kNodeWarps - 1) / kNodeWarps, 32 * kNodeWarps, 0, s>>>(b, d.rows, d.blk_kern);
     ++launch_counter();
   }
 }
