@@ -423,27 +423,44 @@ void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint3
 
 // one thread per node: its class, its forwarded sources and, for a load or
 // store, its memory match; later stages read these instead of recomputing
+// Node caches, in two passes of one thread per instruction over its four node
+// slots (most instructions define one value, so a thread per slot left three
+// lanes in four idle).  First the forwarded sources of every node, then the
+// classes and memory matches, whose pattern walks read those sources.
 __global__ void __launch_bounds__(128)
-    k_node_cache(const __grid_constant__ Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck,
-                 uint32_t* __restrict__ sf, uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
-  // one thread per instruction, over its four node slots (most instructions
-  // define one value, so a thread per slot left three lanes in four idle)
+    k_node_fwd(const __grid_constant__ Batch b, uint32_t* __restrict__ sf) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= b.I) return;
   const uint32_t k = b.ikern[gi];
   const KHdr& K = b.kh[k];
-  KView v = make_view(b, K, k);  // b carries no caches here
+  const KView v = make_view(b, K, k);  // b carries no caches here
+  const bool bad = K.bad;
+  const uint32_t id0 = 4 * (gi - K.first_instr);
+  for (int s = 0; s < 4; ++s) {
+    const Node& n = v.node(id0 + s);
+    uint32_t* o = sf + 3 * (4ull * gi + s);
+    for (int q = 0; q < 3; ++q) o[q] = (!bad && q < n.nsrc) ? fwd(v, n.src[q]) : kTop;
+  }
+}
+
+__global__ void __launch_bounds__(128)
+    k_node_cache(const __grid_constant__ Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck,
+                 const uint32_t* __restrict__ sf, uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const uint32_t k = b.ikern[gi];
+  const KHdr& K = b.kh[k];
+  KView v = make_view(b, K, k);  // b carries no caches here: only the forwarded sources
+  v.sf = sf + 12 * (size_t)K.first_instr;
   const bool bad = K.bad;
   const uint32_t id0 = 4 * (gi - K.first_instr);
   uint32_t cls = 0, clk = 0;
   for (int s = 0; s < 4; ++s) {
-    const uint64_t g = 4ull * gi + s;
     const Node& n = v.node(id0 + s);
     Cls c{K_NONE, 0};
     if (!bad && n.kind != N_NONE) c = classify(v, mkref(id0 + s, PART_ENTIRE));
     cls |= (uint32_t)c.c << (8 * s);
     clk |= (uint32_t)c.k << (8 * s);
-    for (int q = 0; q < 3; ++q) sf[3 * g + q] = (!bad && q < n.nsrc) ? fwd(v, n.src[q]) : kTop;
   }
   reinterpret_cast<uint32_t*>(cc)[gi] = cls;
   reinterpret_cast<uint32_t*>(ck)[gi] = clk;
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(128)
   const Node& n = v.node(id0);
   if (!bad && n.kind == N_OP && (op_gload(n.op) || op_store(n.op))) {
     uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
-    Mem m = match_addr(v, fwd(v, n.src[0]), w);
+    Mem m = match_addr(v, nsrc(v, n, 0), w);
     if (m.ok) {
       a = m.arg;
       x = m.idx;
@@ -465,7 +482,9 @@ void launch_node_cache(Batch& b, cudaStream_t s) {
   if (!b.I) return;
   Batch raw = b;
   raw.ncls = nullptr;
+  k_node_fwd<<<(b.I + 127) / 128, 128, 0, s>>>(raw, b.nsrcf);
   k_node_cache<<<(b.I + 127) / 128, 128, 0, s>>>(raw, b.ncls, b.nclsk, b.nsrcf, b.mem_arg, b.mem_idx);
+  ++launch_counter();
   ++launch_counter();
 }
 

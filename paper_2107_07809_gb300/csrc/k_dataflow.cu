@@ -307,27 +307,43 @@ __global__ void k_dominators(const __grid_constant__ Batch b, uint32_t* __restri
 // per-block definitions: last definition of every register (into st_out) and
 // the block's definition bitset
 // ---------------------------------------------------------------------------
-__global__ void k_local_defs(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off,
-                             const uint32_t* __restrict__ blk_kern) {
-  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per block, 32 instructions at a time: the lanes list their
+// instructions' definitions in shared memory, set the definition bits, and the
+// chunk's last definition of each register is written (later chunks overwrite
+// earlier ones, so the row ends as the block's last definitions).
+constexpr int kDefWarps = 4;
+__global__ void __launch_bounds__(32 * kDefWarps)
+    k_local_defs(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off,
+                 const uint32_t* __restrict__ blk_kern) {
+  __shared__ uint32_t s_reg[kDefWarps][32][4];
+  const uint32_t wp = threadIdx.x / 32, lane = threadIdx.x & 31u;
+  const uint32_t g = blockIdx.x * kDefWarps + wp;
   if (g >= b.NLB) return;
-  uint32_t k = blk_kern[g];
+  const uint32_t k = blk_kern[g];
   const KHdr& K = b.kh[k];
   if (K.bad) return;
-  uint32_t bl = g - K.first_lblock;
+  const uint32_t bl = g - K.first_lblock;
   const BlockRec& B = b.lblocks[g];
-  RegMap M{K.vgprs, K.sgprs};
-  uint32_t words = (K.R + 31) / 32;
+  const RegMap M{K.vgprs, K.sgprs};
+  const uint32_t words = (K.R + 31) / 32;
   uint32_t* db = defbits + bits_off[k] + (size_t)bl * words;
   uint32_t* out = b.st_out + K.state_off + (size_t)bl * K.R;
-  for (uint32_t i = B.first; i < B.end; ++i) {
-    if (b.lblock_of[K.first_instr + i] != bl) continue;
+  for (uint32_t first = B.first; first < B.end; first += 32) {
+    const uint32_t i = first + lane;
     Def d[4];
-    int n = idefs(b, K, M, i, d);
-    for (int t = 0; t < n; ++t) {  // later definitions overwrite: the row ends as the last ones
-      db[d[t].reg >> 5] |= 1u << (d[t].reg & 31);
-      out[d[t].reg] = d[t].val;
+    const int n = (i < B.end && b.lblock_of[K.first_instr + i] == bl) ? idefs(b, K, M, i, d) : 0;
+    for (int t = 0; t < 4; ++t) s_reg[wp][lane][t] = t < n ? d[t].reg : kNone;
+    __syncwarp();
+    for (int t = 0; t < n; ++t) {
+      const uint32_t reg = d[t].reg;
+      atomicOr(&db[reg >> 5], 1u << (reg & 31));
+      bool last = true;
+      for (int u = t + 1; u < n; ++u) last = last && d[u].reg != reg;
+      for (uint32_t m = lane + 1; m < 32 && last; ++m)
+        for (int u = 0; u < 4; ++u) last = last && s_reg[wp][m][u] != reg;
+      if (last) out[reg] = d[t].val;
     }
+    __syncwarp();
   }
 }
 
@@ -688,7 +704,7 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
     cudaMemsetAsync(d.phibits, 0, sizeof(uint32_t) * d.NW, s);
   }
   if (b.NLB) {
-    k_local_defs<<<(b.NLB + T - 1) / T, T, 0, s>>>(b, d.defbits, d.bits_off, d.blk_kern);
+    k_local_defs<<<(b.NLB + kDefWarps - 1) / kDefWarps, 32 * kDefWarps, 0, s>>>(b, d.defbits, d.bits_off, d.blk_kern);
     ++launch_counter();
   }
   k_versions<<<(b.K + 3) / 4, 128, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
