@@ -193,6 +193,110 @@ __device__ __noinline__ void lit64(Wr& w, uint64_t bits, uint8_t want) {
   }
 }
 
+// How each operation is printed.  A template's characters are copied, except
+// 1..3 (operand 0..2, converted to the type in ty: a TY_ value or kSelf, the
+// node's own type) and 4..6 (the shift amount held by operand 0..2, masked
+// with `mask`).  One template loop serves every operation, so lanes of a warp
+// printing different operations run the same code.  Entry O_COUNT is a pair of
+// 32-bit halves.
+enum : uint8_t { F_NONE = 0, F_TPL, F_CARRY, F_LOAD4, F_LOAD8, F_BFE };
+constexpr uint8_t kSelf = 0xFE;
+struct Fmt {
+  char tpl[24];
+  uint8_t ty[3];
+  uint8_t mask;
+  uint8_t kind;
+};
+__device__ const Fmt g_fmt[O_COUNT + 1] = {
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"(\1 * \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 << \5)", {kSelf, TY_NONE, TY_NONE}, 31, F_TPL},
+    {"(\1 + \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 == \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 != \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 > \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 < \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 >= \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 <= \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 == \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 != \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 > \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 < \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 >= \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 <= \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"(\1 + \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 - \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 * \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"mad24(\1, \2, \3)", {TY_UINT, TY_UINT, TY_UINT}, 0, F_TPL},
+    {"mul24(\1, \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 & \2)", {kSelf, kSelf, TY_NONE}, 0, F_TPL},
+    {"(\1 | \2)", {kSelf, kSelf, TY_NONE}, 0, F_TPL},
+    {"(\1 ^ \2)", {kSelf, kSelf, TY_NONE}, 0, F_TPL},
+    {"(\2 << \4)", {TY_NONE, kSelf, TY_NONE}, 31, F_TPL},
+    {"(\2 >> \4)", {TY_NONE, TY_UINT, TY_NONE}, 31, F_TPL},
+    {"(\2 >> \4)", {TY_NONE, TY_INT, TY_NONE}, 31, F_TPL},
+    {"(\1 + \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 - \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 * \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"fma(\1, \2, \3)", {TY_FLOAT, TY_FLOAT, TY_FLOAT}, 0, F_TPL},
+    {"(float)\1", {TY_INT, TY_NONE, TY_NONE}, 0, F_TPL},
+    {"(float)\1", {TY_UINT, TY_NONE, TY_NONE}, 0, F_TPL},
+    {"(double)\1", {TY_FLOAT, TY_NONE, TY_NONE}, 0, F_TPL},
+    {"(double)\1", {TY_INT, TY_NONE, TY_NONE}, 0, F_TPL},
+    {"(float)\1", {TY_DOUBLE, TY_NONE, TY_NONE}, 0, F_TPL},
+    {"(\1 == \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 != \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 > \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 < \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 >= \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 <= \2)", {TY_INT, TY_INT, TY_NONE}, 0, F_TPL},
+    {"(\1 == \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 != \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 > \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 < \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 >= \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 <= \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 == \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 != \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 > \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 < \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 >= \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 <= \2)", {TY_FLOAT, TY_FLOAT, TY_NONE}, 0, F_TPL},
+    {"(\1 + \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 + \2)", {kSelf, kSelf, TY_NONE}, 0, F_CARRY},
+    {"(\1 - \2)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"(\1 - \2)", {kSelf, kSelf, TY_NONE}, 0, F_CARRY},
+    {"(\2 << \4)", {TY_NONE, kSelf, TY_NONE}, 63, F_TPL},
+    {"(\1 + \2)", {TY_DOUBLE, TY_DOUBLE, TY_NONE}, 0, F_TPL},
+    {"(\1 * \2)", {TY_DOUBLE, TY_DOUBLE, TY_NONE}, 0, F_TPL},
+    {"fma(\1, \2, \3)", {TY_DOUBLE, TY_DOUBLE, TY_DOUBLE}, 0, F_TPL},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_LOAD4},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_LOAD8},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},
+    {"(\3 ? \2 : \1)", {kSelf, kSelf, TY_NONE}, 0, F_TPL},
+    {"(\1 >> \5)", {TY_UINT, TY_NONE, TY_NONE}, 31, F_TPL},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_BFE},
+    {"upsample(\2, \1)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+};
+
 struct Em {
   KView v;
   const Batch* b;
@@ -524,104 +628,57 @@ struct Em {
   __device__ __noinline__ void node_expr(uint32_t id, int d) { P(mkref(id, PART_ENTIRE), TY_NONE, d, true); }
   __device__ __forceinline__ void body(uint32_t id, int d) {
     const Node& n = v.node(id);
-    uint8_t T = NT(id);
-    if (n.kind == N_PAIR) {
-      w.s("upsample(");
-      S(n, 1, TY_UINT, d);
-      w.s(", ");
-      S(n, 0, TY_UINT, d);
-      w.c(')');
-      return;
-    }
-    if (n.kind != N_OP) {
+    const uint8_t T = NT(id);
+    if (n.kind != N_OP && n.kind != N_PAIR) {
       partial = true;
       w.s("0u");
       return;
     }
-    uint16_t op = n.op;
-    if (op_scmp(op) || op_vcmp(op)) {
-      uint32_t cc;
-      uint8_t ot;
-      if (op_scmp(op)) {
-        cc = (op - O_S_CMP0) % 6;
-        ot = (op - O_S_CMP0) / 6 == 0 ? TY_UINT : TY_INT;
-      } else {
-        cc = (op - O_V_CMP0) % 6;
-        uint32_t ty = (op - O_V_CMP0) / 6;
-        ot = ty == 0 ? TY_INT : (ty == 1 ? TY_UINT : TY_FLOAT);
+    const Fmt& f = g_fmt[n.kind == N_PAIR ? O_COUNT : n.op];
+    const uint8_t fk = f.kind;
+    if (fk == F_LOAD4 || fk == F_LOAD8) return memref(n, fk == F_LOAD8 ? 8 : 4, d);
+    if (fk == F_BFE) {
+      // field operand: offset bits [4:0], width bits [22:16]; (src >> offset) masked to
+      // width bits.  A field that is not a constant, or 32 bits wide or more, is not written.
+      const uint32_t fo = nsrc(v, n, 1);
+      if (r_node(fo) && rpart(fo) == PART_ENTIRE && v.node(rid(fo)).kind == N_CONST) {
+        const uint32_t c = v.node(rid(fo)).cval, off = c & 31u, wd = (c >> 16) & 0x7Fu;
+        if (wd < 32) {
+          if (wd == 0) {
+            w.s("0u");
+            return;
+          }
+          w.s("((");
+          S(n, 0, TY_UINT, d);
+          w.s(" >> ");
+          w.u64(off);
+          w.s(") & ");
+          lit32(w, (1u << wd) - 1u, TY_UINT);
+          w.c(')');
+          return;
+        }
       }
-      const char* sym[6] = {"==", "!=", ">", "<", ">=", "<="};
-      binop(n, sym[cc], ot, d);
+    }
+    if (fk == F_NONE || fk == F_BFE) {
+      partial = true;
+      w.s(T == TY_ULONG ? "0UL" : "0u");
       return;
     }
-    switch (op) {
-      case O_S_ADD_U32: return binop(n, "+", TY_UINT, d);
-      case O_S_MUL_I32: return binop(n, "*", TY_INT, d);
-      case O_S_LSHL_B32: return shift(n, 0, 1, T, "<<", 31, d);
-      case O_S_LSHR_B32: return shift(n, 0, 1, TY_UINT, ">>", 31, d);
-      case O_S_BFE_U32: {
-        // field operand: offset bits [4:0], width bits [22:16]; (src >> offset) masked to
-        // width bits.  A field that is not a constant, or 32 bits wide or more, is not written.
-        uint32_t f = nsrc(v, n, 1);
-        if (!(r_node(f) && rpart(f) == PART_ENTIRE && v.node(rid(f)).kind == N_CONST)) break;
-        uint32_t c = v.node(rid(f)).cval, off = c & 31u, wd = (c >> 16) & 0x7Fu;
-        if (wd >= 32) break;
-        if (wd == 0) { w.s("0u"); return; }
-        w.s("((");
-        S(n, 0, TY_UINT, d);
-        w.s(" >> ");
-        w.u64(off);
-        w.s(") & ");
-        lit32(w, (1u << wd) - 1u, TY_UINT);
-        w.c(')');
-        return;
+    // a carry half not fused into a 64-bit operation keeps 32-bit operands and is not exact
+    const bool lone = fk == F_CARRY && !n.fused;
+    if (lone) partial = true;
+    for (int i = 0; i < (int)sizeof(f.tpl); ++i) {
+      const char c = f.tpl[i];
+      if (!c) break;
+      if (c <= 3) {
+        const uint8_t t = f.ty[c - 1];
+        S(n, c - 1, t != kSelf ? t : (lone ? TY_UINT : T), d);
+      } else if (c <= 6) {
+        shamt(nsrc(v, n, c - 4), f.mask, d);
+      } else {
+        w.c(c);
       }
-      case O_V_ADD_U32: return binop(n, "+", TY_UINT, d);
-      case O_V_SUB_U32: return binop(n, "-", TY_UINT, d);
-      case O_V_MUL_LO_U32: return binop(n, "*", TY_UINT, d);
-      case O_V_MAD_U32_U24: return call3("mad24", n, 3, TY_UINT, d);
-      case O_V_MUL_U32_U24: return call3("mul24", n, 2, TY_UINT, d);
-      case O_V_AND_B32: return binop(n, "&", T, d);
-      case O_V_OR_B32: return binop(n, "|", T, d);
-      case O_V_XOR_B32: return binop(n, "^", T, d);
-      case O_V_LSHLREV_B32: return shift(n, 1, 0, T, "<<", 31, d);
-      case O_V_LSHRREV_B32: return shift(n, 1, 0, TY_UINT, ">>", 31, d);
-      case O_V_ASHRREV_I32: return shift(n, 1, 0, TY_INT, ">>", 31, d);
-      case O_V_ADD_F32: return binop(n, "+", TY_FLOAT, d);
-      case O_V_SUB_F32: return binop(n, "-", TY_FLOAT, d);
-      case O_V_MUL_F32: return binop(n, "*", TY_FLOAT, d);
-      case O_V_FMA_F32: return call3("fma", n, 3, TY_FLOAT, d);
-      case O_V_CVT_F32_I32: return cast1("(float)", n, TY_INT, d);
-      case O_V_CVT_F32_U32: return cast1("(float)", n, TY_UINT, d);
-      case O_V_CVT_F64_F32: return cast1("(double)", n, TY_FLOAT, d);
-      case O_V_CVT_F64_I32: return cast1("(double)", n, TY_INT, d);
-      case O_V_CVT_F32_F64: return cast1("(float)", n, TY_DOUBLE, d);
-      case O_V_ADD_CO_U32: return binop(n, "+", TY_UINT, d);
-      case O_V_SUB_CO_U32: return binop(n, "-", TY_UINT, d);
-      case O_V_ADDC_CO_U32:
-        if (!n.fused) partial = true;
-        return binop(n, "+", n.fused ? T : TY_UINT, d);
-      case O_V_SUBB_CO_U32:
-        if (!n.fused) partial = true;
-        return binop(n, "-", n.fused ? T : TY_UINT, d);
-      case O_V_LSHLREV_B64: return shift(n, 1, 0, T, "<<", 63, d);
-      case O_V_ADD_F64: return binop(n, "+", TY_DOUBLE, d);
-      case O_V_MUL_F64: return binop(n, "*", TY_DOUBLE, d);
-      case O_V_FMA_F64: return call3("fma", n, 3, TY_DOUBLE, d);
-      case O_GLOBAL_LOAD_DWORD: return memref(n, 4, d);
-      case O_GLOBAL_LOAD_DWORDX2: return memref(n, 8, d);
-      case O_V_CNDMASK_B32:  // the ternary operator: one instruction, printed in place
-        w.c('(');
-        S(n, 2, TY_NONE, d);
-        w.s(" ? ");
-        S(n, 1, T, d);
-        w.s(" : ");
-        S(n, 0, T, d);
-        w.c(')');
-        return;
     }
-    partial = true;
-    w.s(T == TY_ULONG ? "0UL" : "0u");
   }
 
   // ---- statements ---------------------------------------------------------------
