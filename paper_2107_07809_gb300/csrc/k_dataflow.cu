@@ -307,6 +307,26 @@ __global__ void k_dominators(const __grid_constant__ Batch b, uint32_t* __restri
 // per-block definitions: last definition of every register (into st_out) and
 // the block's definition bitset
 // ---------------------------------------------------------------------------
+// Registers are hashed into buckets; a bucket's mask holds the lanes of the
+// chunk that define a register of that bucket, so a lookup checks only those.
+constexpr uint32_t kDefBuckets = 64;
+
+// the latest lane below `below` (a lane mask) that defines reg, or -1; its definition slot in *slot
+__device__ __forceinline__ int last_def(const uint32_t (*dreg)[4], const uint32_t* dmask, uint32_t reg,
+                                        uint32_t below, int* slot) {
+  uint32_t cand = dmask[reg % kDefBuckets] & below;
+  while (cand) {
+    const int m = 31 - __clz(cand);
+    for (int t = 3; t >= 0; --t)
+      if (dreg[m][t] == reg) {
+        *slot = t;
+        return m;
+      }
+    cand &= ~(1u << m);
+  }
+  return -1;
+}
+
 // One warp per block, 32 instructions at a time: the lanes list their
 // instructions' definitions in shared memory, set the definition bits, and the
 // chunk's last definition of each register is written (later chunks overwrite
@@ -315,7 +335,7 @@ constexpr int kDefWarps = 4;
 __global__ void __launch_bounds__(32 * kDefWarps)
     k_local_defs(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off,
                  const uint32_t* __restrict__ blk_kern) {
-  __shared__ uint32_t s_reg[kDefWarps][32][4];
+  __shared__ uint32_t s_reg[kDefWarps][32][4], s_mask[kDefWarps][kDefBuckets];
   const uint32_t wp = threadIdx.x / 32, lane = threadIdx.x & 31u;
   const uint32_t g = blockIdx.x * kDefWarps + wp;
   if (g >= b.NLB) return;
@@ -333,15 +353,18 @@ __global__ void __launch_bounds__(32 * kDefWarps)
     Def d[4];
     const int n = (i < B.end && b.lblock_of[K.first_instr + i] == bl) ? idefs(b, K, M, i, d) : 0;
     for (int t = 0; t < 4; ++t) s_reg[wp][lane][t] = t < n ? d[t].reg : kNone;
+    for (uint32_t q = lane; q < kDefBuckets; q += 32) s_mask[wp][q] = 0;
     __syncwarp();
+    for (int t = 0; t < n; ++t) atomicOr(&s_mask[wp][d[t].reg % kDefBuckets], 1u << lane);
+    __syncwarp();
+    const uint32_t above = ~((2u << lane) - 1u);  // lanes after this one
     for (int t = 0; t < n; ++t) {
       const uint32_t reg = d[t].reg;
       atomicOr(&db[reg >> 5], 1u << (reg & 31));
       bool last = true;
       for (int u = t + 1; u < n; ++u) last = last && d[u].reg != reg;
-      for (uint32_t m = lane + 1; m < 32 && last; ++m)
-        for (int u = 0; u < 4; ++u) last = last && s_reg[wp][m][u] != reg;
-      if (last) out[reg] = d[t].val;
+      int u;
+      if (last && last_def(s_reg[wp], s_mask[wp], reg, above, &u) < 0) out[reg] = d[t].val;
     }
     __syncwarp();
   }
@@ -441,16 +464,16 @@ struct NodeCtx {
   // definitions of the chunk's instructions (lane m: instruction first + m), kNone when absent
   const uint32_t (*dreg)[4];
   const uint32_t (*dval)[4];
+  const uint32_t* dmask;  // per register bucket (reg % kDefBuckets): the lanes defining such a register
   uint32_t lane;  // this instruction's place in the chunk
 };
 
 // value of register reg just before instruction c.i: the last definition of
 // an earlier instruction of the chunk, else the value at the chunk's start
 __device__ __forceinline__ uint32_t reg_now(const NodeCtx& c, uint32_t reg) {
-  for (int m = (int)c.lane - 1; m >= 0; --m)
-    for (int t = 3; t >= 0; --t)
-      if (c.dreg[m][t] == reg) return c.dval[m][t] == kTop ? kUndef : c.dval[m][t];
-  uint32_t v = c.row[reg];
+  int t;
+  const int m = last_def(c.dreg, c.dmask, reg, (1u << c.lane) - 1u, &t);
+  const uint32_t v = m >= 0 ? c.dval[m][t] : c.row[reg];
   return v == kTop ? kUndef : v;
 }
 
@@ -594,7 +617,7 @@ __global__ void k_clear_nodes(const __grid_constant__ Batch b) {
 constexpr int kNodeWarps = 4;
 __global__ void __launch_bounds__(32 * kNodeWarps)
     k_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ rows, const uint32_t* __restrict__ blk_kern) {
-  __shared__ uint32_t s_reg[kNodeWarps][32][4], s_val[kNodeWarps][32][4];
+  __shared__ uint32_t s_reg[kNodeWarps][32][4], s_val[kNodeWarps][32][4], s_mask[kNodeWarps][kDefBuckets];
   const uint32_t wp = threadIdx.x / 32, lane = threadIdx.x & 31u;
   const uint32_t g = blockIdx.x * kNodeWarps + wp;
   if (g >= b.NLB) return;
@@ -614,6 +637,7 @@ __global__ void __launch_bounds__(32 * kNodeWarps)
   c.row = row;
   c.dreg = s_reg[wp];
   c.dval = s_val[wp];
+  c.dmask = s_mask[wp];
   c.lane = lane;
   Node* knodes = b.nodes + 4 * (size_t)K.first_instr;
   for (uint32_t first = B.first; first < B.end; first += 32) {
@@ -625,6 +649,9 @@ __global__ void __launch_bounds__(32 * kNodeWarps)
       s_reg[wp][lane][t] = t < n ? d[t].reg : kNone;
       s_val[wp][lane][t] = t < n ? d[t].val : kNone;
     }
+    for (uint32_t q = lane; q < kDefBuckets; q += 32) s_mask[wp][q] = 0;
+    __syncwarp();
+    for (int t = 0; t < n; ++t) atomicOr(&s_mask[wp][d[t].reg % kDefBuckets], 1u << lane);
     __syncwarp();
     c.i = i;
     const uint32_t gi = K.first_instr + i;
@@ -633,13 +660,13 @@ __global__ void __launch_bounds__(32 * kNodeWarps)
     __syncwarp();
     if (late) build_instr_nodes(b, K, c, knodes);
     // the row after the chunk: a register takes the chunk's last definition of it
+    const uint32_t above = ~((2u << lane) - 1u);  // lanes after this one
     for (int t = 0; t < n; ++t) {
       const uint32_t reg = d[t].reg;
       bool last = true;
       for (int u = t + 1; u < n; ++u) last = last && d[u].reg != reg;
-      for (uint32_t m = lane + 1; m < 32 && last; ++m)
-        for (int u = 0; u < 4; ++u) last = last && s_reg[wp][m][u] != reg;
-      if (last) row[reg] = d[t].val;
+      int u;
+      if (last && last_def(s_reg[wp], s_mask[wp], reg, above, &u) < 0) row[reg] = d[t].val;
     }
     __syncwarp();
   }

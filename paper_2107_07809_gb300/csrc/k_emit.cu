@@ -808,7 +808,9 @@ __device__ void print_args(Wr& w, const Batch& b, const KHdr& K, const ArgRec* A
 // ---------------------------------------------------------------------------
 enum : uint32_t { IT_NONE = 0, IT_HEAD, IT_DECLS, IT_BLOCK, IT_COPYSET, IT_IF, IT_ELSE, IT_CLOSE, IT_DO, IT_WHILE,
                   IT_TAIL, IT_FAIL };
-constexpr uint32_t kDeclChunk = 64;
+// declarations per item: ten lines of at most 22 bytes ("    double var800000;") fit a
+// staging slot, so declaration items are never printed twice
+constexpr uint32_t kDeclChunk = 10;
 
 // ---------------------------------------------------------------------------
 // Copies on the edges into join blocks.  For CFG edge e = 2 * (global block p)
