@@ -427,6 +427,45 @@ void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint3
 // slots (most instructions define one value, so a thread per slot left three
 // lanes in four idle).  First the forwarded sources of every node, then the
 // classes and memory matches, whose pattern walks read those sources.
+// fwd_d(v, r, 0) with its loop in line: only a whole pair (its two halves
+// forwarded separately) makes a recursive call
+__device__ __forceinline__ uint32_t fwd_inline(const KView& v, uint32_t r) {
+  for (int step = 0; step < 512; ++step) {
+    if (r == kTop) return kUndef;
+    if (!r_node(r)) return r;
+    const Node& n = v.node(rid(r));
+    const uint32_t part = rpart(r);
+    if (is_copy_node(n) && part == PART_ENTIRE) {
+      r = n.src[0];
+      continue;
+    }
+    if (n.kind == N_PAIR) {
+      if (part == PART_LO) { r = n.src[0]; continue; }
+      if (part == PART_HI) { r = n.src[1]; continue; }
+      return fwd_d(v, r, 0);
+    }
+    return r;
+  }
+  return r;
+}
+
+// classify(v, r) for a node without a class cache, with the nodes that
+// classify_d turns down before looking at any operand answered in line
+__device__ __forceinline__ Cls classify_node(const KView& v, uint32_t id) {
+  const Node& n = v.node(id);
+  if (n.kind == N_CONST) return Cls{K_CONST32, 0};
+  if (n.kind == N_OP) {
+    switch (n.op) {
+      case O_S_LOAD_DWORD: case O_S_LOAD_DWORDX2: case O_S_LOAD_DWORDX4: case O_S_MUL_I32: case O_S_LSHL_B32:
+      case O_S_LSHR_B32: case O_S_BFE_U32: case O_V_ADD_U32: case O_V_MAD_U32_U24: break;
+      default: return Cls{K_NONE, 0};
+    }
+  } else if (n.kind != N_PAIR && n.kind != N_SLOAD64B) {
+    return Cls{K_NONE, 0};
+  }
+  return classify(v, mkref(id, PART_ENTIRE));
+}
+
 __global__ void __launch_bounds__(128)
     k_node_fwd(const __grid_constant__ Batch b, uint32_t* __restrict__ sf) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
@@ -439,7 +478,7 @@ __global__ void __launch_bounds__(128)
   for (int s = 0; s < 4; ++s) {
     const Node& n = v.node(id0 + s);
     uint32_t* o = sf + 3 * (4ull * gi + s);
-    for (int q = 0; q < 3; ++q) o[q] = (!bad && q < n.nsrc) ? fwd(v, n.src[q]) : kTop;
+    for (int q = 0; q < 3; ++q) o[q] = (!bad && q < n.nsrc) ? fwd_inline(v, n.src[q]) : kTop;
   }
 }
 
@@ -458,7 +497,7 @@ __global__ void __launch_bounds__(128)
   for (int s = 0; s < 4; ++s) {
     const Node& n = v.node(id0 + s);
     Cls c{K_NONE, 0};
-    if (!bad && n.kind != N_NONE) c = classify(v, mkref(id0 + s, PART_ENTIRE));
+    if (!bad && n.kind != N_NONE) c = classify_node(v, id0 + s);
     cls |= (uint32_t)c.c << (8 * s);
     clk |= (uint32_t)c.k << (8 * s);
   }
