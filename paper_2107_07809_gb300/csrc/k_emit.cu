@@ -297,6 +297,61 @@ __device__ const Fmt g_fmt[O_COUNT + 1] = {
     {"upsample(\2, \1)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
 };
 
+// Leaves: how a value reduced to a leaf kind (its class, or a variable) and a
+// number is printed: pre, the number (or argument name, or literal), mid, the
+// number again (NUM2), suf.  Every leaf goes through the same code.
+enum : uint8_t { LF_F_NUM = 1, LF_F_NUM2 = 2, LF_F_NAME = 4, LF_F_LIT32 = 8, LF_F_LIT64 = 16, LF_F_PARTIAL = 32 };
+constexpr uint8_t LF_VAR = 20, LF_EXPR = 21, LF_PART = 22;
+struct LeafFmt {
+  char pre[20];
+  char mid[24];
+  char suf[4];
+  uint8_t flags;
+};
+static_assert(K_LID == 1 && K_UNDEF == 4 && K_GIDNO == 8 && K_ARGPTR == 10 && K_CONST64 == 14 && K_DISP == 15 &&
+                  K_WDIM == 19, "leaf table order");
+__device__ const LeafFmt g_leaf[LF_VAR + 1] = {
+    {"", "", "", 0},                                                   // K_NONE
+    {"get_local_id(", "", ")", LF_F_NUM},                              // K_LID
+    {"get_group_id(", "", ")", LF_F_NUM},                              // K_GRP
+    {"0UL", "", "", LF_F_PARTIAL},                                     // K_KARG
+    {"0u", "", "", LF_F_PARTIAL},                                      // K_UNDEF
+    {"get_global_offset(", "", ")", LF_F_NUM},                         // K_GOFS64
+    {"get_global_offset(", "", ")", LF_F_NUM},                         // K_GOFSLO
+    {"", "", "", 0},                                                   // K_MULGRP (never a leaf)
+    {"(get_global_id(", ") - get_global_offset(", "))", LF_F_NUM | LF_F_NUM2},  // K_GIDNO
+    {"get_global_id(", "", ")", LF_F_NUM},                             // K_GID
+    {"(ulong)", "", "", LF_F_NAME},                                    // K_ARGPTR
+    {"", "", "", LF_F_NAME},                                           // K_ARG32
+    {"", "", "", LF_F_NAME},                                           // K_ARG64
+    {"", "", "", LF_F_LIT32},                                          // K_CONST32
+    {"", "", "", LF_F_LIT64},                                          // K_CONST64
+    {"0UL", "", "", LF_F_PARTIAL},                                     // K_DISP
+    {"", "", "", 0},                                                   // K_DISP0 (never a leaf)
+    {"get_global_size(", "", ")", LF_F_NUM},                           // K_GSIZE
+    {"get_num_groups(", "", ")", LF_F_NUM},                            // K_NGRP
+    {"get_work_dim()", "", "", 0},                                     // K_WDIM
+    {"var", "", "", LF_F_NUM},                                         // LF_VAR
+};
+
+// conversions: g_conv[want][from] is printed around a value of type `from` used as `want`
+// (integer to integer and across widths a cast, same width otherwise as_T)
+struct ConvFmt {
+  char pre[12];
+  char suf[2];
+};
+__device__ const ConvFmt g_conv[9][9] = {
+    {{"", ""}, {"", ""}, {"", ""}, {"", ""}, {"", ""}, {"", ""}, {"", ""}, {"", ""}, {"", ""}},
+    {{"as_int(", ")"}, {"", ""}, {"(int)", ""}, {"as_int(", ")"}, {"(int)", ""}, {"(int)", ""}, {"(int)", ""}, {"as_int(", ")"}, {"(int)", ""}},
+    {{"as_uint(", ")"}, {"(uint)", ""}, {"", ""}, {"as_uint(", ")"}, {"(uint)", ""}, {"(uint)", ""}, {"(uint)", ""}, {"as_uint(", ")"}, {"(uint)", ""}},
+    {{"as_float(", ")"}, {"as_float(", ")"}, {"as_float(", ")"}, {"", ""}, {"(float)", ""}, {"(float)", ""}, {"(float)", ""}, {"as_float(", ")"}, {"(float)", ""}},
+    {{"(long)", ""}, {"(long)", ""}, {"(long)", ""}, {"(long)", ""}, {"", ""}, {"(long)", ""}, {"as_long(", ")"}, {"(long)", ""}, {"as_long(", ")"}},
+    {{"(ulong)", ""}, {"(ulong)", ""}, {"(ulong)", ""}, {"(ulong)", ""}, {"(ulong)", ""}, {"", ""}, {"as_ulong(", ")"}, {"(ulong)", ""}, {"as_ulong(", ")"}},
+    {{"(double)", ""}, {"(double)", ""}, {"(double)", ""}, {"(double)", ""}, {"as_double(", ")"}, {"as_double(", ")"}, {"", ""}, {"(double)", ""}, {"as_double(", ")"}},
+    {{"as_uint(", ")"}, {"as_uint(", ")"}, {"as_uint(", ")"}, {"as_uint(", ")"}, {"(uint)", ""}, {"(uint)", ""}, {"(uint)", ""}, {"", ""}, {"(uint)", ""}},
+    {{"(uint)", ""}, {"(uint)", ""}, {"(uint)", ""}, {"(uint)", ""}, {"as_uint(", ")"}, {"as_uint(", ")"}, {"as_uint(", ")"}, {"(uint)", ""}, {"", ""}},
+};
+
 struct Em {
   KView v;
   const Batch* b;
@@ -402,41 +457,23 @@ struct Em {
   // differs, then the value (a join variable, a recovered system value or argument, a literal, a
   // variable, or the node's expression with its operands printed by P again).  With `top` set it
   // prints node rid(r)'s own expression, ignoring its variable, with no conversion (the right-hand
-  // side of a statement, a branch condition).  The operand helpers below are inlined into P, so
-  // an expression level costs one call frame.
-  __device__ __forceinline__ void cv_open(uint8_t t, uint8_t want) {
-    if (want != TY_NONE && t != want) conv_open(t, want);
-  }
-  __device__ __forceinline__ void cv_close(uint8_t t, uint8_t want) {
-    if (want != TY_NONE && t != want) conv_close(t, want);
-  }
-
+  // side of a statement, a branch condition).  The value is first reduced to a leaf kind and a
+  // number, printed through the leaf table by one code path, or to an expression; the operand
+  // helpers are inlined into P, so an expression level costs one call frame.
   __device__ __noinline__ void P(uint32_t r, uint8_t want, int d, bool top) {
-    uint32_t id;
-    uint8_t t = TY_NONE;
-    if (top) {
-      id = rid(r);
+    if (top) return body(rid(r), d);
+    r = fwd(v, r);
+    uint8_t t, lk;  // the value's type; its leaf kind (a class, LF_VAR, or LF_EXPR / LF_PART)
+    uint32_t num = 0, id = 0;
+    if (r_phi(r)) {
+      const int32_t x = phivar(r);
+      t = x < 0 ? TY_UINT : vt[x];
+      lk = x < 0 ? (uint8_t)K_UNDEF : LF_VAR;
+      num = (uint32_t)x;
     } else {
-      r = fwd(v, r);
-      if (r_phi(r)) {
-        const int32_t x = phivar(r);
-        t = x < 0 ? TY_UINT : vt[x];
-        cv_open(t, want);
-        if (d > 200) {
-          deep = true;
-          w.s("0u");
-        } else if (x < 0) {
-          partial = true;
-          w.s("0u");
-        } else {
-          w.s("var");
-          w.u64((uint64_t)x);
-        }
-        cv_close(t, want);
-        return;
-      }
       const Cls c = (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) ? Cls{v.cc[rid(r)], v.ck[rid(r)]} : classify(v, r);
-      bool cls = true;
+      lk = c.c;
+      num = c.k;
       switch (c.c) {
         case K_UNDEF: case K_LID: case K_GRP: case K_GID: case K_GIDNO: case K_GOFSLO: case K_GSIZE: case K_NGRP:
         case K_WDIM: t = TY_UINT; break;
@@ -452,113 +489,69 @@ struct Em {
           t = twidth(u) == 32 ? TY_ULONG : u;
           break;
         }
-        default: cls = false;
-      }
-      if (cls) {
-        cv_open(t, want);
-        if (d > 200) {
-          deep = true;
-          w.s("0u");
-        } else {
-          leaf(c, r, want);
-        }
-        cv_close(t, want);
-        return;
-      }
-      if (!r_node(r)) {
-        cv_open(TY_UINT, want);
-        if (d > 200) deep = true;
-        else partial = true;
-        w.s("0u");
-        cv_close(TY_UINT, want);
-        return;
-      }
-      id = rid(r);
-      if (rpart(r) != PART_ENTIRE) {
-        cv_open(TY_UINT, want);
-        if (d > 200) {
-          deep = true;
-          w.s("0u");
-        } else {
-          const uint32_t whole = mkref(id, PART_ENTIRE);
-          const bool dbl = expr_type(whole, TY_NONE) == TY_DOUBLE;
-          if (rpart(r) == PART_LO) {
-            w.s(dbl ? "(uint)as_ulong(" : "(uint)");
-            P(whole, TY_NONE, d + 1, false);
-            if (dbl) w.c(')');
+        default:
+          if (!r_node(r)) {
+            t = TY_UINT;
+            lk = K_UNDEF;
+          } else if (rpart(r) != PART_ENTIRE) {
+            t = TY_UINT;
+            lk = LF_PART;
+            id = rid(r);
+          } else if (vo[rid(r)] >= 0) {
+            num = (uint32_t)vo[rid(r)];
+            t = vt[num];
+            lk = LF_VAR;
           } else {
-            w.s(dbl ? "(uint)(as_ulong(" : "(uint)(");
-            P(whole, TY_NONE, d + 1, false);
-            w.s(dbl ? ") >> 32)" : " >> 32)");
+            id = rid(r);
+            t = node_expr_type(id);
+            lk = LF_EXPR;
           }
-        }
-        cv_close(TY_UINT, want);
-        return;
       }
-      if (vo[id] >= 0) {
-        const int32_t x = vo[id];
-        t = vt[x];
-        cv_open(t, want);
-        if (d > 200) {
-          deep = true;
-          w.s("0u");
-        } else {
-          w.s("var");
-          w.u64((uint64_t)x);
-        }
-        cv_close(t, want);
-        return;
-      }
-      t = node_expr_type(id);
-      cv_open(t, want);
-      if (d > 200) {
-        deep = true;
-        w.s("0u");
-        cv_close(t, want);
-        return;
-      }
-      ++d;
     }
-    body(id, d);
-    if (!top) cv_close(t, want);
-  }
-
-  // a recovered system value, argument or literal
-  __device__ __forceinline__ void leaf(Cls c, uint32_t r, uint8_t want) {
-    switch (c.c) {
-      case K_UNDEF: partial = true; w.s("0u"); return;
-      case K_LID: w.s("get_local_id("); w.u64(c.k); w.c(')'); return;
-      case K_GRP: w.s("get_group_id("); w.u64(c.k); w.c(')'); return;
-      case K_GID: w.s("get_global_id("); w.u64(c.k); w.c(')'); return;
-      case K_GIDNO:
-        w.s("(get_global_id(");
-        w.u64(c.k);
-        w.s(") - get_global_offset(");
-        w.u64(c.k);
-        w.s("))");
-        return;
-      case K_GOFSLO: case K_GOFS64: w.s("get_global_offset("); w.u64(c.k); w.c(')'); return;
-      case K_ARG32: case K_ARG64: name(c.k); return;
-      case K_ARGPTR: w.s("(ulong)"); name(c.k); return;
-      case K_KARG: case K_DISP: partial = true; w.s("0UL"); return;
-      case K_GSIZE: w.s("get_global_size("); w.u64(c.k); w.c(')'); return;
-      case K_NGRP: w.s("get_num_groups("); w.u64(c.k); w.c(')'); return;
-      case K_WDIM: w.s("get_work_dim()"); return;
-      case K_CONST32: {
-        uint8_t t = want == TY_NONE ? TY_UINT : want;
-        if (twidth(t) == 64) t = TY_UINT;
-        lit32(w, v.node(rid(r)).cval, t);
-        return;
+    const bool conv = want != TY_NONE && t != want;
+    // (a code beyond the lattice prints like top32: "uint", 32 bits wide, not an integer type)
+    const ConvFmt& cf = g_conv[want > TY_TOP64 ? TY_TOP32 : want][t > TY_TOP64 ? TY_TOP32 : t];
+    if (conv) w.s(cf.pre);
+    if (d > 200) {
+      deep = true;
+      w.s("0u");
+    } else if (lk == LF_EXPR) {
+      body(id, d + 1);
+    } else if (lk == LF_PART) {
+      const uint32_t whole = mkref(id, PART_ENTIRE);
+      const bool dbl = expr_type(whole, TY_NONE) == TY_DOUBLE;
+      if (rpart(r) == PART_LO) {
+        w.s(dbl ? "(uint)as_ulong(" : "(uint)");
+        P(whole, TY_NONE, d + 1, false);
+        if (dbl) w.c(')');
+      } else {
+        w.s(dbl ? "(uint)(as_ulong(" : "(uint)(");
+        P(whole, TY_NONE, d + 1, false);
+        w.s(dbl ? ") >> 32)" : " >> 32)");
       }
-      case K_CONST64: {
+    } else {
+      const LeafFmt& L = g_leaf[lk];
+      const uint8_t f = L.flags;
+      if (f & LF_F_PARTIAL) partial = true;
+      w.s(L.pre);
+      if (f & LF_F_NAME) name(num);
+      else if (f & LF_F_NUM) w.u64(num);
+      else if (f & LF_F_LIT32) {
+        uint8_t u = want == TY_NONE ? TY_UINT : want;
+        if (twidth(u) == 64) u = TY_UINT;
+        lit32(w, v.node(rid(r)).cval, u);
+      } else if (f & LF_F_LIT64) {
         const Node& p = v.node(rid(r));
-        uint64_t lo = v.node(rid(nsrc(v, p, 0))).cval, hi = v.node(rid(nsrc(v, p, 1))).cval;
-        uint8_t t = want == TY_NONE ? TY_ULONG : want;
-        if (twidth(t) == 32) t = TY_ULONG;
-        lit64(w, lo | (hi << 32), t);
-        return;
+        const uint64_t lo = v.node(rid(nsrc(v, p, 0))).cval, hi = v.node(rid(nsrc(v, p, 1))).cval;
+        uint8_t u = want == TY_NONE ? TY_ULONG : want;
+        if (twidth(u) == 32) u = TY_ULONG;
+        lit64(w, lo | (hi << 32), u);
       }
+      w.s(L.mid);
+      if (f & LF_F_NUM2) w.u64(num);
+      w.s(L.suf);
     }
+    if (conv) w.s(cf.suf);
   }
 
   __device__ void name(uint32_t slot) { w.mem(b->text + v.A[slot].name_off, v.A[slot].name_len); }
