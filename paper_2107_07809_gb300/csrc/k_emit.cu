@@ -1137,7 +1137,7 @@ __global__ void k_sub_heads(const uint32_t* __restrict__ sub0, uint32_t NI, uint
 // appends itself to ovf_list when the text did not fit.  Direct mode
 // (stage == null): sub-item list[t] prints straight into its final place in
 // the output (used for the sub-items that overflowed their slot).
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 12)
     k_items(const __grid_constant__ Batch b, const Item* __restrict__ items, const uint32_t* __restrict__ sub_item,
             const uint32_t* __restrict__ sub0, const uint32_t* __restrict__ prank, const uint32_t* __restrict__ pinstr,
             uint32_t N, const uint32_t* __restrict__ list, uint32_t* __restrict__ item_len,
@@ -1167,10 +1167,7 @@ __global__ void __launch_bounds__(128)
     }
   }
   const ArgRec* A = b.args + (size_t)k * kMaxArgs;
-  // the printer's state lives in shared memory: its fields (the writer's cursor above all) are
-  // read and written through `this` on every call, and local memory would send them through L1/L2
-  __shared__ Em s_em[128];
-  Em& em = s_em[threadIdx.x];
+  Em em;
   em.v = make_view(b, K, k);
   em.b = &b;
   em.K = &K;
