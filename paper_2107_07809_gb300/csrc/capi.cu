@@ -126,6 +126,7 @@ struct Engine {
   uint64_t launches = 0;
   uint32_t* h_tot = nullptr;  // pinned counters
   uint32_t big_kernel = 4096;  // size-bucket threshold
+  SideStream fk{};             // second stream for launches that overlap the main one
   // job service: the batch whose IR the workspace holds and its unfetched jobs
   uint64_t batch = 0;
   uint32_t live = 0;
@@ -431,7 +432,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   ScanScratch scv = sc;
   if (scan_tiles((uint32_t)nvc) + 64 > std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)) + 64)
     scv.status = W.get<uint64_t>("tile_status_var", scan_tiles((uint32_t)nvc) + 64);
-  launch_analysis(b, wl, bits, nbw, blk_kern, vflag, vpos, scv, s);
+  launch_analysis(b, wl, bits, nbw, blk_kern, vflag, vpos, scv, h->fk, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[8], s));
   // S12
@@ -553,6 +554,9 @@ void engine_init(gcn_decomp* h, Engine* E) {
   E->ws.budget = h->budget;
   E->ws.pool = &h->pool;
   for (auto& e : E->ev) CK(cudaEventCreate(&e));
+  CK(cudaStreamCreateWithFlags(&E->fk.side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&E->fk.fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&E->fk.join, cudaEventDisableTiming));
   CK(cudaMallocHost(&E->h_tot, 64));
 }
 
@@ -560,6 +564,10 @@ void engine_free(Engine* E) {
   E->ws.release();
   for (auto& e : E->ev)
     if (e) cudaEventDestroy(e);
+  if (E->fk.side) cudaStreamDestroy(E->fk.side);
+  if (E->fk.fork) cudaEventDestroy(E->fk.fork);
+  if (E->fk.join) cudaEventDestroy(E->fk.join);
+  E->fk = SideStream{};
   if (E->h_tot) cudaFreeHost(E->h_tot);
   E->h_tot = nullptr;
 }

@@ -152,8 +152,14 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s);
 // k_analysis.cu
 void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint32_t* total, cudaStream_t s);
 void launch_node_cache(Batch& b, cudaStream_t s);
+// a second stream for launches that may overlap those of the main stream, with
+// the events that fork work onto it and join it back
+struct SideStream {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
 void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, const uint32_t* blk_kern,
-                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, cudaStream_t s);
+                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, SideStream fk, cudaStream_t s);
 
 // k_region.cu
 void launch_regions(Batch& b, uint32_t* work, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s);

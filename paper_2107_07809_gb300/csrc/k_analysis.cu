@@ -528,16 +528,22 @@ void launch_node_cache(Batch& b, cudaStream_t s) {
 }
 
 void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, const uint32_t* blk_kern,
-                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, cudaStream_t s) {
+                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, SideStream fk, cudaStream_t s) {
   if (!b.K) return;
   // four bitmaps: reached nodes, cross-block uses, join inputs (4I bits each), used joins (NS bits)
   uint64_t wn = (4ull * b.I + 63) / 32;
   uint32_t *rb = bits, *cb = bits + wn, *ib = bits + 2 * wn, *pb = bits + 3 * wn;
   cudaMemsetAsync(bits, 0, sizeof(uint32_t) * nbits_words, s);
+  // the two size buckets touch disjoint kernels (shared bitmap words only through atomics):
+  // the block-per-kernel bucket runs on the side stream, beside the warp-per-kernel one
+  cudaEventRecord(fk.fork, s);
+  cudaStreamWaitEvent(fk.side, fk.fork, 0);
+  k_reach<false><<<b.K, kBigTeam, 0, fk.side>>>(b, wl, rb, cb, ib, pb);
+  k_types<false><<<b.K, kBigTeam, 0, fk.side>>>(b, wl);
   k_reach<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl, rb, cb, ib, pb);
-  k_reach<false><<<b.K, kBigTeam, 0, s>>>(b, wl, rb, cb, ib, pb);
   k_types<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl);
-  k_types<false><<<b.K, kBigTeam, 0, s>>>(b, wl);
+  cudaEventRecord(fk.join, fk.side);
+  cudaStreamWaitEvent(s, fk.join, 0);
   launch_counter() += 4;
   // variable numbers over the candidate array of NS + 4I positions
   const uint64_t nc = (uint64_t)b.NS + 4ull * b.I;
