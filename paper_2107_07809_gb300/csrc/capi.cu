@@ -127,6 +127,8 @@ struct Engine {
   uint32_t* h_tot = nullptr;  // pinned counters
   uint32_t big_kernel = 4096;  // size-bucket threshold
   SideStream fk{};             // second stream for launches that overlap the main one
+  SideStream rs{};             // stream of the region reduction (S12), beside S7-S11
+  cudaEvent_t rs_ev[2] = {};   // around the region reduction
   // job service: the batch whose IR the workspace holds and its unfetched jobs
   uint64_t batch = 0;
   uint32_t live = 0;
@@ -383,6 +385,21 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   launch_df_counts(b, d, sc, tot, s);
   CK(cudaGetLastError());
   sync_totals();
+  // S12 needs the logical CFG and the parse flags only, final once the sizes above are taken:
+  // it runs on its own stream beside S7-S11
+  b.rg = W.get<uint32_t>("regions", 12ull * kRegionsPerBlock * b.NLB + 24);
+  // region reduction work: 64 words per block + 128 per kernel (red_work_words)
+  uint32_t* rwork = W.get<uint32_t>("rg_work", 64ull * b.NLB + 128ull * b.K + 64);
+  uint32_t* rstk = W.get<uint32_t>("rg_stack", (size_t)kStackPerBlock * b.NLB + 4);
+  uint8_t* alive = W.get<uint8_t>("rg_alive", (size_t)kRegionsPerBlock * b.NLB + 2);
+  uint8_t* cond = W.get<uint8_t>("rg_cond", b.NLB + 1);
+  CK(cudaEventRecord(h->rs.fork, s));
+  CK(cudaStreamWaitEvent(h->rs.side, h->rs.fork, 0));
+  CK(cudaEventRecord(h->rs_ev[0], h->rs.side));
+  launch_regions(b, rwork, rstk, alive, cond, h->rs.side);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->rs_ev[1], h->rs.side));
+  CK(cudaEventRecord(h->rs.join, h->rs.side));
   b.NS = h->h_tot[5];
   d.NW = h->h_tot[6];
   uint32_t NE = h->h_tot[7];
@@ -435,15 +452,8 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   launch_analysis(b, wl, bits, nbw, blk_kern, vflag, vpos, scv, h->fk, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[8], s));
-  // S12
-  b.rg = W.get<uint32_t>("regions", 12ull * kRegionsPerBlock * b.NLB + 24);
-  // region reduction work: 64 words per block + 128 per kernel (red_work_words)
-  uint32_t* rwork = W.get<uint32_t>("rg_work", 64ull * b.NLB + 128ull * b.K + 64);
-  uint32_t* rstk = W.get<uint32_t>("rg_stack", (size_t)kStackPerBlock * b.NLB + 4);
-  uint8_t* alive = W.get<uint8_t>("rg_alive", (size_t)kRegionsPerBlock * b.NLB + 2);
-  uint8_t* cond = W.get<uint8_t>("rg_cond", b.NLB + 1);
-  launch_regions(b, rwork, rstk, alive, cond, s);
-  CK(cudaGetLastError());
+  // S12, launched beside S7-S11, joined here
+  CK(cudaStreamWaitEvent(s, h->rs.join, 0));
   CK(cudaEventRecord(h->ev[9], s));
   // S13: layout (count, scan, write), item sizes, scan, item text
   b.kout_off = W.get<uint32_t>("kout_off", b.K + 1);
@@ -535,6 +545,7 @@ void finish_run(Engine* h, cudaStream_t s) {
   if (b.K) CK(cudaMemcpyAsync(R.kh.data(), b.kh, sizeof(KHdr) * b.K, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&h->stage_ms[i], h->ev[i], h->ev[i + 1]);
+  cudaEventElapsedTime(&h->stage_ms[8], h->rs_ev[0], h->rs_ev[1]);  // S12 ran on its own stream
   cudaEventElapsedTime(&h->stage_ms[kStages], h->ev[kStages + 1], h->ev[kStages + 2]);
   if (uint32_t e = h->h_tot[15]) {
     set_err("device error flags " + std::to_string(e));
@@ -554,9 +565,12 @@ void engine_init(gcn_decomp* h, Engine* E) {
   E->ws.budget = h->budget;
   E->ws.pool = &h->pool;
   for (auto& e : E->ev) CK(cudaEventCreate(&e));
-  CK(cudaStreamCreateWithFlags(&E->fk.side, cudaStreamNonBlocking));
-  CK(cudaEventCreateWithFlags(&E->fk.fork, cudaEventDisableTiming));
-  CK(cudaEventCreateWithFlags(&E->fk.join, cudaEventDisableTiming));
+  for (SideStream* q : {&E->fk, &E->rs}) {
+    CK(cudaStreamCreateWithFlags(&q->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&q->fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&q->join, cudaEventDisableTiming));
+  }
+  for (auto& e : E->rs_ev) CK(cudaEventCreate(&e));
   CK(cudaMallocHost(&E->h_tot, 64));
 }
 
@@ -564,10 +578,16 @@ void engine_free(Engine* E) {
   E->ws.release();
   for (auto& e : E->ev)
     if (e) cudaEventDestroy(e);
-  if (E->fk.side) cudaStreamDestroy(E->fk.side);
-  if (E->fk.fork) cudaEventDestroy(E->fk.fork);
-  if (E->fk.join) cudaEventDestroy(E->fk.join);
-  E->fk = SideStream{};
+  for (SideStream* q : {&E->fk, &E->rs}) {
+    if (q->side) cudaStreamDestroy(q->side);
+    if (q->fork) cudaEventDestroy(q->fork);
+    if (q->join) cudaEventDestroy(q->join);
+    *q = SideStream{};
+  }
+  for (auto& e : E->rs_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   if (E->h_tot) cudaFreeHost(E->h_tot);
   E->h_tot = nullptr;
 }
