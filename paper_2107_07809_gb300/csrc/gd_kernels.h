@@ -116,6 +116,16 @@ struct Batch {
   uint32_t* err;
 };
 
+// Per-kernel serial walks run one warp per kernel, its lane 0 working: 32
+// kernels packed into one warp would run their diverging walks one after the
+// other, while a warp each lets the SMs interleave them (and a batch of a few
+// large kernels spreads over several SMs instead of sharing one).
+constexpr uint32_t kWalkWarps = 4;  // kernels (warps) per thread block
+__device__ __forceinline__ uint32_t walk_kernel() {
+  return (threadIdx.x & 31u) ? 0xFFFFFFFFu : blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+}
+inline uint32_t walk_blocks(uint32_t K) { return (K + kWalkWarps - 1) / kWalkWarps; }
+
 // k_text.cu
 uint32_t line_scan_tiles(uint64_t n);
 uint32_t scan_tiles(uint32_t n);

@@ -233,7 +233,7 @@ __global__ void k_pred_sort(const __grid_constant__ Batch b) {
 // ---------------------------------------------------------------------------
 __global__ void k_dominators(const __grid_constant__ Batch b, uint32_t* __restrict__ rpo_index, uint32_t* __restrict__ stk,
                              uint8_t* __restrict__ child) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t k = walk_kernel();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   uint32_t nb = K.n_lblock, base = K.first_lblock;
@@ -722,7 +722,7 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
     ++launch_counter();
     k_pred_sort<<<(b.NLB + T - 1) / T, T, 0, s>>>(b);
     ++launch_counter();
-    k_dominators<<<(b.K + 63) / 64, 64, 0, s>>>(b, d.rpo_index, d.stack, d.child);
+    k_dominators<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, d.rpo_index, d.stack, d.child);
     ++launch_counter();
   }
   if (b.NS) cudaMemsetAsync(b.st_out, 0xFF, sizeof(uint32_t) * b.NS, s);

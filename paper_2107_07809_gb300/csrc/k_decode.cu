@@ -611,7 +611,7 @@ __global__ void k_exec_list(uint32_t I, const uint32_t* __restrict__ flag, const
 // instructions only (in program order) with a stack of open forms
 __global__ void k_exec_forms(const __grid_constant__ Batch b, const uint32_t* __restrict__ pos,
                              const uint32_t* __restrict__ list) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t k = walk_kernel();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   const InstrRec* R = b.ins + K.first_instr;
@@ -776,7 +776,7 @@ void launch_logical(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) 
   launch_scan(b.pleader, b.lleader, b.I + 1, 0, false, sc, nullptr, b.err, s);
   k_exec_list<<<(b.I + T - 1) / T, T, 0, s>>>(b.I, b.pleader, b.lleader, b.exec_list);
   ++launch_counter();
-  k_exec_forms<<<(b.K + 127) / 128, 128, 0, s>>>(b, b.lleader, b.exec_list);
+  k_exec_forms<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, b.lleader, b.exec_list);
   ++launch_counter();
   cudaMemsetAsync(b.pleader, 0, sizeof(uint32_t) * b.I, s);
   k_lleaders<<<(b.I + T - 1) / T, T, 0, s>>>(b);

@@ -942,7 +942,7 @@ struct LayoutCtx {
 
 __global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ stage, const uint32_t* __restrict__ stage_off,
                          uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ stk_all) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t k = walk_kernel();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   LayoutCtx L;
@@ -1284,7 +1284,7 @@ void launch_layout(Batch& b, Item* stage, uint32_t* stage_off, uint32_t* item_cn
                    cudaStream_t s) {
   if (!b.K) return;
   if (phase == 0) k_layout_bound<<<(b.K + 127) / 128, 128, 0, s>>>(b, stage_off);
-  else k_layout<<<(b.K + 63) / 64, 64, 0, s>>>(b, stage, stage_off, item_cnt, stk);
+  else k_layout<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, stage, stage_off, item_cnt, stk);
   ++launch_counter();
 }
 

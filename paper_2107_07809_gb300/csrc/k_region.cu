@@ -10,7 +10,7 @@ namespace gd {
 __global__ void k_regions(const __grid_constant__ Batch b, uint32_t* __restrict__ work_all,
                           uint32_t* __restrict__ stk_all, uint8_t* __restrict__ alive_all,
                           uint8_t* __restrict__ cond_all) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t k = walk_kernel();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   K.root = kNone;
@@ -50,7 +50,7 @@ __global__ void k_regions(const __grid_constant__ Batch b, uint32_t* __restrict_
 
 void launch_regions(Batch& b, uint32_t* work, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s) {
   if (!b.K) return;
-  k_regions<<<(b.K + 63) / 64, 64, 0, s>>>(b, work, stk, alive, cond);
+  k_regions<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, work, stk, alive, cond);
   ++launch_counter();
 }
 
