@@ -126,6 +126,31 @@ __device__ __forceinline__ uint32_t walk_kernel() {
 }
 inline uint32_t walk_blocks(uint32_t K) { return (K + kWalkWarps - 1) / kWalkWarps; }
 
+// Size buckets: a kernel of fewer than b.big_kernel instructions (a tuning
+// parameter) is handled by one warp (Team<true>), a longer one by a whole
+// thread block (Team<false>); both launches cover every kernel and a team
+// leaves the kernels of the other bucket alone.
+constexpr int kBigTeam = 512;
+
+template <bool WARP>
+struct Team {
+  static __device__ __forceinline__ uint32_t kid() {
+    return WARP ? blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32 : blockIdx.x;
+  }
+  static __device__ __forceinline__ uint32_t tid() { return WARP ? (threadIdx.x & 31u) : threadIdx.x; }
+  static __device__ __forceinline__ uint32_t size() { return WARP ? 32u : blockDim.x; }
+  static __device__ __forceinline__ uint32_t slot() { return WARP ? threadIdx.x / 32 : 0u; }
+  static __device__ __forceinline__ void sync() {
+    if (WARP) __syncwarp();
+    else __syncthreads();
+  }
+  static __device__ __forceinline__ bool any(bool p) {
+    if (WARP) return __any_sync(0xFFFFFFFFu, p);
+    return __syncthreads_or(p) != 0;
+  }
+  static __device__ __forceinline__ bool mine(const KHdr& K, uint32_t big) { return (K.n_instr >= big) != WARP; }
+};
+
 // k_text.cu
 uint32_t line_scan_tiles(uint64_t n);
 uint32_t scan_tiles(uint32_t n);

@@ -29,31 +29,6 @@ __device__ __forceinline__ bool claim(uint32_t* bits, uint64_t g) {
   return !(atomicOr(&bits[g >> 5], m) & m);
 }
 
-// Size buckets: a kernel of fewer than b.big_kernel instructions (a tuning
-// parameter) is handled by one warp (Team<true>), a longer one by a whole
-// thread block (Team<false>); both launches cover every kernel and a team
-// leaves the kernels of the other bucket alone.
-constexpr int kBigTeam = 512;
-
-template <bool WARP>
-struct Team {
-  static __device__ __forceinline__ uint32_t kid() {
-    return WARP ? blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32 : blockIdx.x;
-  }
-  static __device__ __forceinline__ uint32_t tid() { return WARP ? (threadIdx.x & 31u) : threadIdx.x; }
-  static __device__ __forceinline__ uint32_t size() { return WARP ? 32u : blockDim.x; }
-  static __device__ __forceinline__ uint32_t slot() { return WARP ? threadIdx.x / 32 : 0u; }
-  static __device__ __forceinline__ void sync() {
-    if (WARP) __syncwarp();
-    else __syncthreads();
-  }
-  static __device__ __forceinline__ bool any(bool p) {
-    if (WARP) return __any_sync(0xFFFFFFFFu, p);
-    return __syncthreads_or(p) != 0;
-  }
-  static __device__ __forceinline__ bool mine(const KHdr& K, uint32_t big) { return (K.n_instr >= big) != WARP; }
-};
-
 template <bool WARP>
 __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
                         uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits) {

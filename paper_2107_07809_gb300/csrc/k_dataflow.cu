@@ -390,37 +390,47 @@ __device__ __forceinline__ uint32_t entry_value(const KHdr& K, uint32_t r) {
 // versions: frontier closure (warp per kernel, lane = 32 registers), then
 // values in reverse postorder (lanes over registers)
 // ---------------------------------------------------------------------------
-__global__ void k_versions(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, uint32_t* __restrict__ phibits,
-                           const uint32_t* __restrict__ bits_off, uint32_t* __restrict__ err) {
-  uint32_t k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  uint32_t lane = threadIdx.x & 31u;
+// a word another thread of the team may be writing (read afresh every time)
+__device__ __forceinline__ uint32_t volatile_ld(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+template <bool WARP>
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam)
+    k_versions(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, uint32_t* __restrict__ phibits,
+               const uint32_t* __restrict__ bits_off, uint32_t* __restrict__ err) {
+  using T = Team<WARP>;
+  const uint32_t k = T::kid(), tid = T::tid(), TS = T::size();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
-  if (K.bad || !K.n_lblock) return;
+  if (K.bad || !K.n_lblock || !T::mine(K, b.big_kernel)) return;
   uint32_t nb = K.n_lblock, base = K.first_lblock, R = K.R, words = (R + 31) / 32;
   uint32_t* db = defbits + bits_off[k];
   uint32_t* pb = phibits + bits_off[k];
   const uint32_t* idom = b.idom + base;
   // the entry defines every register
-  for (uint32_t w = lane; w < words; w += 32) db[w] = 0xFFFFFFFFu;
-  __syncwarp();
+  for (uint32_t w = tid; w < words; w += TS) db[w] = 0xFFFFFFFFu;
+  T::sync();
+  // Join versions: the iterated dominance frontier of the defining blocks.  Each
+  // thread takes join blocks x and adds, along the dominator-tree path from each
+  // predecessor up to idom(x), the definitions and versions found there; sweeps
+  // repeat until nothing changes (a monotone closure: the order does not matter).
   bool changed = true;
   uint32_t sweeps = 0;
   while (changed) {
     changed = false;
     if (++sweeps > 4 * nb + 8) {  // cannot happen for a closure; bounded all the same
-      if (lane == 0) atomicOr(err, ERR_CAPACITY);
+      if (tid == 0) atomicOr(err, ERR_CAPACITY);
       break;
     }
-    for (uint32_t x = 0; x < nb; ++x) {
+    for (uint32_t x = tid; x < nb; x += TS) {
       uint32_t np = b.pred_off[base + x + 1] - b.pred_off[base + x];
       if (np < 2 || idom[x] == kNone) continue;
       for (uint32_t pi = b.pred_off[base + x]; pi < b.pred_off[base + x + 1]; ++pi) {
         uint32_t r = b.preds[pi];
         if (idom[r] == kNone) continue;  // unreachable predecessor
         while (r != idom[x]) {
-          for (uint32_t w = lane; w < words; w += 32) {
-            uint32_t add = (db[(size_t)r * words + w] | pb[(size_t)r * words + w]) & ~pb[(size_t)x * words + w];
+          for (uint32_t w = 0; w < words; ++w) {
+            const uint32_t add =
+                (db[(size_t)r * words + w] | volatile_ld(&pb[(size_t)r * words + w])) & ~pb[(size_t)x * words + w];
             if (add) {
               pb[(size_t)x * words + w] |= add;
               changed = true;
@@ -430,17 +440,18 @@ __global__ void k_versions(const __grid_constant__ Batch b, uint32_t* __restrict
         }
       }
     }
-    changed = __any_sync(0xFFFFFFFFu, changed);
+    T::sync();
+    changed = T::any(changed);
   }
-  __syncwarp();
-  // values
+  T::sync();
+  // values, block by block in reverse postorder, threads over registers
   uint32_t* in = b.st_in + K.state_off;
   uint32_t* out = b.st_out + K.state_off;
   uint8_t* hp = b.has_phi + K.state_off;
   for (uint32_t q = 0; q < nb; ++q) {
     uint32_t x = b.rpo[base + q];
     if (x == kNone) break;
-    for (uint32_t r = lane; r < R; r += 32) {
+    for (uint32_t r = tid; r < R; r += TS) {
       bool phi = (pb[(size_t)x * words + (r >> 5)] >> (r & 31)) & 1u;
       hp[(size_t)x * R + r] = phi;
       uint32_t v = phi ? phiref(x, r) : (x == 0 ? entry_value(K, r) : out[(size_t)idom[x] * R + r]);
@@ -448,7 +459,7 @@ __global__ void k_versions(const __grid_constant__ Batch b, uint32_t* __restrict
       uint32_t o = out[(size_t)x * R + r];
       if (o == kTop) out[(size_t)x * R + r] = v;
     }
-    __syncwarp();
+    T::sync();
   }
 }
 
@@ -734,8 +745,9 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
     k_local_defs<<<(b.NLB + kDefWarps - 1) / kDefWarps, 32 * kDefWarps, 0, s>>>(b, d.defbits, d.bits_off, d.blk_kern);
     ++launch_counter();
   }
-  k_versions<<<(b.K + 3) / 4, 128, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
-  ++launch_counter();
+  k_versions<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
+  k_versions<false><<<b.K, kBigTeam, 0, s>>>(b, d.defbits, d.phibits, d.bits_off, b.err);
+  launch_counter() += 2;
   if (b.I) {
     const uint64_t nw = 6ull * b.I;
     k_clear_nodes<<<(uint32_t)((nw + T - 1) / T), T, 0, s>>>(b);
