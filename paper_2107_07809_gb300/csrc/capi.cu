@@ -329,6 +329,9 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.label_line = W.get<uint32_t>("label_line", b.NL + 1);
   b.label_instr = W.get<uint32_t>("label_instr", b.NL + 1);
   b.label_hash = W.get<uint32_t>("label_hash", b.NL + 1);
+  b.label_tab_mask = 1;
+  while (b.label_tab_mask + 1 < 2ull * b.NL) b.label_tab_mask = 2 * b.label_tab_mask + 1;
+  b.label_tab = W.get<uint32_t>("label_tab", (size_t)b.label_tab_mask + 1);
   b.cfg_line = W.get<uint32_t>("cfg_line", b.NC + 1);
   if (L) launch_scatter_rows(L, ra, b.instr_line, b.label_line, b.label_instr, b.cfg_line, b.kh, s);
   CK(cudaEventRecord(h->ev[2], s));

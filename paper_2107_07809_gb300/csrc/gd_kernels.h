@@ -53,6 +53,8 @@ struct Batch {
   uint32_t* label_line;          // NL
   uint32_t* label_instr;         // NL (global instruction index)
   uint32_t* label_hash;          // NL
+  uint32_t* label_tab;           // open-addressing table of label indices (kNone = empty), label_tab_mask + 1 slots
+  uint32_t label_tab_mask;
   InstrRec* ins;                 // I
   uint32_t* branch_hash;         // I (label name hash of a branch)
   uint32_t* branch_pos;          // I (byte offset | len<<24 of the label operand)

@@ -443,6 +443,18 @@ __global__ void k_decode(const __grid_constant__ Batch b) {
   b.ikern[i] = k;
 }
 
+// Labels are found through a batch-wide open-addressing table keyed by
+// (kernel, FNV-1a of the name): a branch probes from its key's slot to the
+// first empty one and takes the lowest label index whose name matches exactly
+// (the first definition of a label wins).
+__device__ __forceinline__ uint32_t label_slot(uint32_t k, uint32_t h, uint32_t mask) {
+  uint32_t x = h ^ (k * 0x9E3779B1u);
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  return x & mask;
+}
+
 __global__ void k_label_hash(const __grid_constant__ Batch b) {
   uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= b.NL) return;
@@ -450,7 +462,14 @@ __global__ void k_label_hash(const __grid_constant__ Batch b) {
   const uint8_t* p = b.text + b.line_start[line];
   const uint8_t* e = b.text + b.line_start[line + 1] - 1;
   trim(p, e);
-  b.label_hash[j] = fnv1a(p, (uint32_t)(e - p - 1));
+  const uint32_t h = fnv1a(p, (uint32_t)(e - p - 1));
+  b.label_hash[j] = h;
+  uint32_t slot = label_slot(b.kcnt[line] - 1, h, b.label_tab_mask);
+  for (uint32_t probe = 0; probe <= b.label_tab_mask; ++probe) {
+    if (atomicCAS(&b.label_tab[slot], kNone, j) == kNone) return;
+    slot = (slot + 1) & b.label_tab_mask;
+  }
+  atomicOr(b.err, ERR_CAPACITY);  // more labels than slots: cannot happen (twice as many slots)
 }
 
 // branch targets (first definition of the label wins), per-kernel parse flags, leaders
@@ -464,17 +483,21 @@ __global__ void k_resolve(const __grid_constant__ Batch b) {
     uint32_t len = b.blen[i];
     const uint8_t* s = b.text + b.branch_pos[i];
     uint32_t h = b.branch_hash[i];
-    uint32_t found = kNone;
-    for (uint32_t j = K.first_label; j < K.first_label + K.n_label && found == kNone; ++j) {
-      if (b.label_hash[j] != h) continue;
+    uint32_t best = kNone;  // lowest matching label index
+    uint32_t slot = label_slot(k, h, b.label_tab_mask);
+    for (uint32_t probe = 0; probe <= b.label_tab_mask; ++probe) {
+      const uint32_t j = b.label_tab[slot];
+      if (j == kNone) break;
+      slot = (slot + 1) & b.label_tab_mask;
+      if (j >= best || b.label_hash[j] != h || j < K.first_label || j >= K.first_label + K.n_label) continue;
       const uint8_t* p = b.text + b.line_start[b.label_line[j]];
       while (is_space(*p)) ++p;
       bool eq = true;
       for (uint32_t q = 0; q < len && eq; ++q) eq = p[q] == s[q];
-      if (eq && p[len] == ':') found = b.label_instr[j] - K.first_instr;
+      if (eq && p[len] == ':') best = j;
     }
-    if (found == kNone) r.flags |= FL_NOLABEL;
-    else r.target = found;
+    if (best == kNone) r.flags |= FL_NOLABEL;
+    else r.target = b.label_instr[best] - K.first_instr;
   }
   if (r.flags & (FL_BAD | FL_REGRANGE | FL_NOLABEL)) atomicOr(&K.bad, 2u);
 }
@@ -537,6 +560,7 @@ void launch_decode(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
   k_decode<<<(b.I + T - 1) / T, T, 0, s>>>(b);
   ++launch_counter();
   if (b.NL) {
+    cudaMemsetAsync(b.label_tab, 0xFF, sizeof(uint32_t) * ((size_t)b.label_tab_mask + 1), s);
     k_label_hash<<<(b.NL + T - 1) / T, T, 0, s>>>(b);
     ++launch_counter();
   }
