@@ -122,11 +122,14 @@ struct Batch {
 // kernels packed into one warp would run their diverging walks one after the
 // other, while a warp each lets the SMs interleave them (and a batch of a few
 // large kernels spreads over several SMs instead of sharing one).
-constexpr uint32_t kWalkWarps = 4;  // kernels (warps) per thread block
+// A batch of few kernels (at most a few per SM) gives each its own thread block, so that each
+// walk has an SM's L1 cache to itself; larger batches pack four kernels per block.
 __device__ __forceinline__ uint32_t walk_kernel() {
   return (threadIdx.x & 31u) ? 0xFFFFFFFFu : blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
 }
-inline uint32_t walk_blocks(uint32_t K) { return (K + kWalkWarps - 1) / kWalkWarps; }
+inline uint32_t walk_warps(uint32_t K) { return K <= 1024 ? 1u : 4u; }
+inline uint32_t walk_blocks(uint32_t K) { return (K + walk_warps(K) - 1) / walk_warps(K); }
+inline uint32_t walk_threads(uint32_t K) { return 32 * walk_warps(K); }
 
 // Size buckets: a kernel of fewer than b.big_kernel instructions (a tuning
 // parameter) is handled by one warp (Team<true>), a longer one by a whole

@@ -733,7 +733,7 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
     ++launch_counter();
     k_pred_sort<<<(b.NLB + T - 1) / T, T, 0, s>>>(b);
     ++launch_counter();
-    k_dominators<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, d.rpo_index, d.stack, d.child);
+    k_dominators<<<walk_blocks(b.K), walk_threads(b.K), 0, s>>>(b, d.rpo_index, d.stack, d.child);
     ++launch_counter();
   }
   if (b.NS) cudaMemsetAsync(b.st_out, 0xFF, sizeof(uint32_t) * b.NS, s);

@@ -800,7 +800,7 @@ void launch_logical(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) 
   launch_scan(b.pleader, b.lleader, b.I + 1, 0, false, sc, nullptr, b.err, s);
   k_exec_list<<<(b.I + T - 1) / T, T, 0, s>>>(b.I, b.pleader, b.lleader, b.exec_list);
   ++launch_counter();
-  k_exec_forms<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, b.lleader, b.exec_list);
+  k_exec_forms<<<walk_blocks(b.K), walk_threads(b.K), 0, s>>>(b, b.lleader, b.exec_list);
   ++launch_counter();
   cudaMemsetAsync(b.pleader, 0, sizeof(uint32_t) * b.I, s);
   k_lleaders<<<(b.I + T - 1) / T, T, 0, s>>>(b);

@@ -1284,7 +1284,7 @@ void launch_layout(Batch& b, Item* stage, uint32_t* stage_off, uint32_t* item_cn
                    cudaStream_t s) {
   if (!b.K) return;
   if (phase == 0) k_layout_bound<<<(b.K + 127) / 128, 128, 0, s>>>(b, stage_off);
-  else k_layout<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, stage, stage_off, item_cnt, stk);
+  else k_layout<<<walk_blocks(b.K), walk_threads(b.K), 0, s>>>(b, stage, stage_off, item_cnt, stk);
   ++launch_counter();
 }
 

@@ -50,7 +50,7 @@ __global__ void k_regions(const __grid_constant__ Batch b, uint32_t* __restrict_
 
 void launch_regions(Batch& b, uint32_t* work, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s) {
   if (!b.K) return;
-  k_regions<<<walk_blocks(b.K), 32 * kWalkWarps, 0, s>>>(b, work, stk, alive, cond);
+  k_regions<<<walk_blocks(b.K), walk_threads(b.K), 0, s>>>(b, work, stk, alive, cond);
   ++launch_counter();
 }
 
