@@ -8,16 +8,20 @@
 // a value at a join is assigned on the edges into the join; 4-space indent.
 // Unsupported instructions stay as inline asm ("Practical implementation").
 //
-// Layout: one thread per kernel walks the region tree (explicit stack) and
-// lays out items: the head, declaration chunks, the statements of a block,
+// Layout: a warp per kernel (lane 0) walks the region tree (explicit stack)
+// and lays out items: the head, declaration chunks, the statements of a block,
 // join copies and control lines.  Printing: the statements of blocks become
-// one sub-item per printing instruction, every other item one sub-item; one
-// thread per sub-item prints into a fixed staging slot (expressions
-// recursively, with a depth guard) and records the exact length, a scan
-// places every sub-item, a warp-per-32 copy moves the staged bytes, and the
-// few sub-items longer than a slot are printed again straight into place.
-// The printer calls the pattern matchers from many places; inlining them
-// there made the emission kernel megabytes long (instruction-cache bound).
+// one sub-item per printing instruction, every other item one sub-item.  The
+// sub-items are ordered by shape (a counting sort on the item kind, the
+// printing node's operation and the shapes of its first two operands), so
+// that the lanes of a warp print alike statements; one thread per sub-item
+// prints into a fixed staging slot (expressions recursively, one call frame
+// per level, with a depth guard; operations, leaves and conversions through
+// tables) and records the exact length, a scan places every sub-item, a
+// warp-per-32 copy moves the staged bytes, and the few sub-items longer than
+// a slot are printed again straight into place.  The printer calls the
+// pattern matchers from many places; inlining them there made the emission
+// kernel megabytes long (instruction-cache bound).
 #define GD_MATCH_INLINE __noinline__
 #include "k_analysis.cuh"
 #include "region_red.cuh"
@@ -557,15 +561,6 @@ struct Em {
   __device__ void name(uint32_t slot) { w.mem(b->text + v.A[slot].name_off, v.A[slot].name_len); }
 
   __device__ __forceinline__ void S(const Node& n, int q, uint8_t t, int d) { P(nsrc(v, n, q), t, d, false); }
-  __device__ __forceinline__ void binop(const Node& n, const char* sym, uint8_t ot, int d) {
-    w.c('(');
-    S(n, 0, ot, d);
-    w.c(' ');
-    w.s(sym);
-    w.c(' ');
-    S(n, 1, ot, d);
-    w.c(')');
-  }
   __device__ __forceinline__ void shamt(uint32_t f, uint32_t mask, int d) {
     if (r_node(f) && rpart(f) == PART_ENTIRE && v.node(rid(f)).kind == N_CONST) {
       w.u64(v.node(rid(f)).cval & mask);
@@ -577,29 +572,6 @@ struct Em {
     w.u64(mask);
     w.s("u)");
   }
-  __device__ __forceinline__ void call3(const char* fn, const Node& n, int k, uint8_t t, int d) {
-    w.s(fn);
-    w.c('(');
-    for (int q = 0; q < k; ++q) {
-      if (q) w.s(", ");
-      S(n, q, t, d);
-    }
-    w.c(')');
-  }
-  __device__ __forceinline__ void cast1(const char* pre, const Node& n, uint8_t t, int d) {
-    w.s(pre);
-    S(n, 0, t, d);
-  }
-  __device__ __forceinline__ void shift(const Node& n, int vq, int sq, uint8_t t, const char* sym, uint32_t mask, int d) {
-    w.c('(');
-    S(n, vq, t, d);
-    w.c(' ');
-    w.s(sym);
-    w.c(' ');
-    shamt(nsrc(v, n, sq), mask, d);
-    w.c(')');
-  }
-
   __device__ __noinline__ void memref(const Node& n, uint32_t width, int d) {
     Mem m = mem_of(v, (uint32_t)(&n - v.N));
     if (m.ok) {
