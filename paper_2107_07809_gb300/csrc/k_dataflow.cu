@@ -6,11 +6,15 @@
 // minimal one: register r gets a new version at block B exactly when B is in
 // the iterated dominance frontier of r's defining blocks (the entry defines
 // every register with its ABI value).  GPU mapping:
-//   - definitions and 64-bit carry pairs: one thread per instruction;
-//   - dominators (reverse postorder + iterative intersection): one thread per kernel;
-//   - the frontier closure for all registers at once: one warp per kernel, each
-//     lane owns 32 registers of a bitset, walking the frontier paths together;
-//   - values: the same warp walks blocks in reverse postorder, lanes over registers;
+//   - 64-bit carry pairs: one thread per instruction; a block's definitions:
+//     one warp per block, 32 instructions at a time (k_local_defs);
+//   - dominators (reverse postorder + iterative intersection): one warp per
+//     kernel, lane 0 walking;
+//   - the frontier closure for all registers at once: a warp per kernel, or a
+//     thread block for a long kernel; its threads take join blocks and walk the
+//     dominator-tree paths from their predecessors, the bitsets of all
+//     registers at once, in sweeps until nothing changes;
+//   - values: the same team walks blocks in reverse postorder, threads over registers;
 //   - nodes: one warp per block, 32 instructions at a time (k_nodes).
 #include "gd_kernels.h"
 
@@ -387,8 +391,8 @@ __device__ __forceinline__ uint32_t entry_value(const KHdr& K, uint32_t r) {
 }
 
 // ---------------------------------------------------------------------------
-// versions: frontier closure (warp per kernel, lane = 32 registers), then
-// values in reverse postorder (lanes over registers)
+// versions: frontier closure (a team per kernel, threads over join blocks),
+// then values in reverse postorder (threads over registers)
 // ---------------------------------------------------------------------------
 // a word another thread of the team may be writing (read afresh every time)
 __device__ __forceinline__ uint32_t volatile_ld(const uint32_t* p) { return *(const volatile uint32_t*)p; }
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam)
 }
 
 // ---------------------------------------------------------------------------
-// nodes: one thread per instruction
+// nodes: one warp per block
 // ---------------------------------------------------------------------------
 struct NodeCtx {
   const Batch* b;
