@@ -216,7 +216,7 @@ void launch_layout(Batch& b, Item* stage, uint32_t* stage_off, uint32_t* item_cn
                    cudaStream_t s);
 void launch_items_place(const Item* stage, const uint32_t* stage_off, uint32_t K, uint32_t total,
                         const uint32_t* item_cnt, const uint32_t* item_base, Item* items, cudaStream_t s);
-constexpr uint32_t kEmitSlot = 512;  // staging bytes per emission sub-item
+constexpr uint32_t kEmitSlot = 1024;  // staging bytes per emission sub-item
 void launch_print_list(Batch& b, uint32_t* flag, const uint32_t* rank, uint32_t* list, int phase, cudaStream_t s);
 void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* prank, uint32_t* weight,
                      const uint32_t* sub0, uint32_t* sub_item, uint32_t NS2, int phase, cudaStream_t s);
