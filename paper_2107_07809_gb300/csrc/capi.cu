@@ -439,6 +439,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.phi_type = W.get<uint8_t>("phi_type", b.NS + 1);
   b.phi_var = W.get<int32_t>("phi_var", b.NS + 1);
   b.var_type = W.get<uint8_t>("var_type", 4ull * b.I + b.NS + 4);
+  b.dyn_count = W.get<uint32_t>("dyn_count", b.K + 1);
   uint32_t* wlsz = W.get<uint32_t>("wl_size", b.K + 1);
   uint32_t* wloff = W.get<uint32_t>("wl_off", b.K + 1);
   launch_wl_size(b, wlsz, wloff, sc, &tot[9], s);

@@ -53,6 +53,7 @@ struct Batch {
   uint32_t* label_line;          // NL
   uint32_t* label_instr;         // NL (global instruction index)
   uint32_t* label_hash;          // NL
+  uint32_t* dyn_count;           // K: nodes of each kernel whose type comes from their operands
   uint32_t* label_tab;           // open-addressing table of label indices (kNone = empty), label_tab_mask + 1 slots
   uint32_t label_tab_mask;
   InstrRec* ins;                 // I

@@ -42,14 +42,12 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_co
   KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint32_t* uses = b.uses + nb;
-  uint8_t* fl = b.nflag + nb;
   uint8_t* pu = b.phi_used + K.state_off;
   uint32_t* wl = wl_all + K.wl_off;
   uint32_t* pl = b.plist + K.state_off;
   const uint32_t nn = 4 * K.n_instr;
   const uint32_t cap = nn + K.n_lblock * K.R + 8;
-  for (uint32_t q = lane; q < nn; q += TS) uses[q] = 0;
-  for (size_t q = lane; q < (size_t)K.n_lblock * K.R; q += TS) pu[q] = 0;
+  // uses and phi_used start zeroed for the whole batch (a memset before the launch)
   if (lane == 0) {
     s_top[wid] = 0;
     s_npl[wid] = 0;
@@ -120,13 +118,21 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_co
     T::sync();
   }
   T::sync();
-  for (uint32_t q = lane; q < nn; q += TS) {
-    uint64_t g = nb + q;
-    uint32_t f = ((rbits[g >> 5] >> (g & 31)) & 1u) | (((cbits[g >> 5] >> (g & 31)) & 1u) << 1) |
-                 (((ibits[g >> 5] >> (g & 31)) & 1u) << 2);
-    fl[q] = (uint8_t)f;
-  }
   if (lane == 0) K.n_phis = s_npl[wid];
+}
+
+// node flags from the reachability bitmaps (reached, used in another block,
+// feeds a join version): one thread per instruction, its four slots' bytes at once
+__global__ void k_reach_flags(const __grid_constant__ Batch b, const uint32_t* __restrict__ rbits,
+                              const uint32_t* __restrict__ cbits, const uint32_t* __restrict__ ibits) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const uint64_t g = 4ull * gi;  // four bits of one word
+  const uint32_t sh = (uint32_t)(g & 31), w = (uint32_t)(g >> 5);
+  const uint32_t r = (rbits[w] >> sh) & 0xFu, c = (cbits[w] >> sh) & 0xFu, x = (ibits[w] >> sh) & 0xFu;
+  uint32_t f = 0;
+  for (int q = 0; q < 4; ++q) f |= (((r >> q) & 1u) | (((c >> q) & 1u) << 1) | (((x >> q) & 1u) << 2)) << (8 * q);
+  reinterpret_cast<uint32_t*>(b.nflag)[gi] = f;
 }
 
 // ---------------------------------------------------------------------------
@@ -202,41 +208,54 @@ __device__ __forceinline__ bool type_from_operands(const Node& n) {
   return false;
 }
 
+// A node typed by its operation alone is final after one evaluation (its
+// equation has no unknowns): one thread per instruction types those of its four
+// slots and lists the others, whose type comes from their operands, in its
+// kernel's list for the iteration (the reachability work list, free again).
+__global__ void k_types_static(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  const uint32_t k = b.ikern[gi];
+  const KHdr& K = b.kh[k];
+  if (K.bad) return;
+  const KView v = make_view(b, K, k);
+  const size_t nb = 4 * (size_t)K.first_instr;
+  uint8_t* nt = b.ntype + nb;
+  const uint8_t* pt = b.phi_type + K.state_off;
+  const uint32_t id0 = 4 * (gi - K.first_instr);
+  const uint32_t f4 = reinterpret_cast<const uint32_t*>(b.nflag)[gi];
+  uint32_t t4 = 0;
+  for (uint32_t s = 0; s < 4; ++s) {
+    uint8_t t = TY_NONE;
+    if ((f4 >> (8 * s)) & 1u) {
+      if (type_from_operands(v.node(id0 + s))) wl_all[K.wl_off + atomicAdd(&b.dyn_count[k], 1u)] = id0 + s;
+      else t = node_type(v, nt, pt, id0 + s);
+    }
+    t4 |= (uint32_t)t << (8 * s);
+  }
+  reinterpret_cast<uint32_t*>(b.ntype)[gi] = t4;
+}
+
 template <bool WARP>
 __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_constant__ Batch b,
                                                                  uint32_t* __restrict__ wl_all) {
   using T = Team<WARP>;
-  __shared__ uint32_t s_nd[4];
-  const uint32_t k = T::kid(), lane = T::tid(), TS = T::size(), wid = T::slot();
+  const uint32_t k = T::kid(), lane = T::tid(), TS = T::size();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad || !T::mine(K, b.big_kernel)) return;
   KView v = make_view(b, K, k);
   const size_t nb = 4 * (size_t)K.first_instr;
   uint8_t* nt = b.ntype + nb;
-  const uint8_t* fl = b.nflag + nb;
   uint8_t* pt = b.phi_type + K.state_off;
   const uint32_t* pl = b.plist + K.state_off;
   uint32_t* dyn = wl_all + K.wl_off;  // the reachability work list is free again
-  uint32_t nn = 4 * K.n_instr;
-  if (lane == 0) s_nd[wid] = 0;
   for (uint32_t q = lane; q < K.n_phis; q += TS) {
     uint32_t e = pl[q];
     pt[(size_t)(e >> 10) * K.R + (e & 0x3FF)] = TY_NONE;
   }
   T::sync();
-  // a node typed by its operation alone is final after one evaluation (its
-  // equation has no unknowns); the others are listed for the iteration
-  for (uint32_t id = lane; id < nn; id += TS) {
-    uint8_t t = TY_NONE;
-    if (fl[id] & 1) {
-      if (type_from_operands(v.node(id))) dyn[atomicAdd(&s_nd[wid], 1u)] = id;
-      else t = node_type(v, nt, pt, id);
-    }
-    nt[id] = t;
-  }
-  T::sync();
-  const uint32_t nd = s_nd[wid];
+  const uint32_t nd = b.dyn_count[k];  // listed by k_types_static
   bool changed = true;
   int guard = 0;
   while (changed && guard++ < 100000) {
@@ -511,11 +530,23 @@ void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_word
   cudaMemsetAsync(bits, 0, sizeof(uint32_t) * nbits_words, s);
   // the two size buckets touch disjoint kernels (shared bitmap words only through atomics):
   // the block-per-kernel bucket runs on the side stream, beside the warp-per-kernel one
+  cudaMemsetAsync(b.uses, 0, sizeof(uint32_t) * 4ull * b.I, s);
+  if (b.NS) cudaMemsetAsync(b.phi_used, 0, b.NS, s);
+  cudaMemsetAsync(b.dyn_count, 0, sizeof(uint32_t) * b.K, s);
   cudaEventRecord(fk.fork, s);
   cudaStreamWaitEvent(fk.side, fk.fork, 0);
   k_reach<false><<<b.K, kBigTeam, 0, fk.side>>>(b, wl, rb, cb, ib, pb);
-  k_types<false><<<b.K, kBigTeam, 0, fk.side>>>(b, wl);
   k_reach<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl, rb, cb, ib, pb);
+  cudaEventRecord(fk.join, fk.side);
+  cudaStreamWaitEvent(s, fk.join, 0);
+  if (b.I) {
+    k_reach_flags<<<(b.I + 255) / 256, 256, 0, s>>>(b, rb, cb, ib);
+    k_types_static<<<(b.I + 127) / 128, 128, 0, s>>>(b, wl);
+    launch_counter() += 2;
+  }
+  cudaEventRecord(fk.fork, s);
+  cudaStreamWaitEvent(fk.side, fk.fork, 0);
+  k_types<false><<<b.K, kBigTeam, 0, fk.side>>>(b, wl);
   k_types<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl);
   cudaEventRecord(fk.join, fk.side);
   cudaStreamWaitEvent(s, fk.join, 0);
