@@ -458,14 +458,13 @@ def main():
     value = total_instr * world / (ms / 1e3)
 
     # end to end through the host-buffer API
-    files = [batch.kernel(i) for i in range(n_files)]
     h2d = int(batch.text.nbytes) + 8 * (n_files + 1)
     e2e_ms = []
     d2h = 0
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ids = dec.submit_batch(files)
+        ids = dec.submit_packed(batch.text, batch.offsets)
         raw, offs, sts = dec.fetch_batch_raw(ids)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)

@@ -162,6 +162,28 @@ class Decompiler:
         _ck(lib().gcn_decomp_submit_batch(self._h, arr, lens, n, ids, ctypes.byref(got)), "gcn_decomp_submit_batch")
         return list(ids[: got.value])
 
+    def submit_packed(self, text, offsets) -> list[int]:
+        """submit_batch for files held back to back in one buffer: file i is
+        text[offsets[i]:offsets[i+1]] (``text`` a contiguous uint8 numpy array,
+        ``offsets`` n+1 integers).  The pointer and length arrays are built with
+        numpy instead of one Python object per file."""
+        import numpy as np
+
+        text = np.ascontiguousarray(text, dtype=np.uint8)
+        offs = np.asarray(offsets, dtype=np.uint64)
+        n = len(offs) - 1
+        if n <= 0:
+            return []
+        ptrs = (np.uint64(text.ctypes.data) + offs[:-1]).astype(np.uint64)
+        lens = (offs[1:] - offs[:-1]).astype(np.uint64)
+        ids = np.zeros(n, dtype=np.uint64)
+        got = ctypes.c_size_t()
+        _ck(lib().gcn_decomp_submit_batch(self._h, ptrs.ctypes.data_as(ctypes.POINTER(ctypes.c_char_p)),
+                                          lens.ctypes.data_as(ctypes.POINTER(ctypes.c_size_t)), n,
+                                          ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(got)),
+            "gcn_decomp_submit_batch")
+        return ids[: got.value].tolist()
+
     def fetch_opencl(self, job: int, wait: bool = True) -> tuple[str, int]:
         n = ctypes.c_size_t()
         st = ctypes.c_int()
@@ -194,18 +216,21 @@ class Decompiler:
 
     def fetch_batch_raw(self, ids: list[int]):
         """Like fetch_batch, without splitting or decoding: (texts back to back as a numpy uint8
-        array, offsets, statuses)."""
+        array, offsets and statuses as numpy arrays)."""
         import numpy as np
 
         n = len(ids)
-        arr = (ctypes.c_uint64 * max(n, 1))(*ids)
-        offs = (ctypes.c_uint64 * (n + 1))()
-        st = (ctypes.c_int32 * max(n, 1))()
-        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, None, 0, offs, st, 1), "gcn_decomp_fetch_batch")
+        arr = np.asarray(ids if n else [0], dtype=np.uint64)
+        offs = np.zeros(n + 1, dtype=np.uint64)
+        st = np.zeros(max(n, 1), dtype=np.int32)
+        pa = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        po = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        ps = st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        _ck(lib().gcn_decomp_fetch_batch(self._h, pa, n, None, 0, po, ps, 1), "gcn_decomp_fetch_batch")
         buf = np.empty(max(int(offs[n]), 1), dtype=np.uint8)
-        _ck(lib().gcn_decomp_fetch_batch(self._h, arr, n, buf.ctypes.data, int(offs[n]), offs, st, 1),
+        _ck(lib().gcn_decomp_fetch_batch(self._h, pa, n, buf.ctypes.data, int(offs[n]), po, ps, 1),
             "gcn_decomp_fetch_batch")
-        return buf[: int(offs[n])], list(offs), list(st)
+        return buf[: int(offs[n])], offs.astype(np.int64), st[:n]
 
     def poll(self, cap: int = 4096, timeout_ms: int = 0) -> list[int]:
         """Finished jobs not reported before (waits up to timeout_ms for one)."""

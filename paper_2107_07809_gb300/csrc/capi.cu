@@ -1135,9 +1135,22 @@ int gcn_decomp_fetch_batch(gcn_decomp_t* h, const uint64_t* job_ids, size_t n, c
     set_err("buffer too small");
     return GCN_EINVAL;
   }
-  for (size_t i = 0; i < n; ++i) {
-    const std::string& t = its[i]->second.text;
-    if (!t.empty()) memcpy(buf + off_out[i], t.data(), t.size());
+  auto copy_range = [&](size_t a, size_t z) {
+    for (size_t i = a; i < z; ++i) {
+      const std::string& t = its[i]->second.text;
+      if (!t.empty()) memcpy(buf + off_out[i], t.data(), t.size());
+    }
+  };
+  // large fetches are copied by several threads (the jobs are done: nothing else writes them)
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nth = o >= (16ull << 20) ? std::min<size_t>({(size_t)8, (size_t)hw, n}) : 1;
+  if (nth > 1) {
+    std::vector<std::thread> th;
+    for (size_t q = 1; q < nth; ++q) th.emplace_back(copy_range, n * q / nth, n * (q + 1) / nth);
+    copy_range(0, n / nth);
+    for (auto& x : th) x.join();
+  } else {
+    copy_range(0, n);
   }
   for (size_t i = 0; i < n; ++i) release_job(h, its[i]);
   return GCN_OK;

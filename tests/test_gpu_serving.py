@@ -122,3 +122,20 @@ def test_tuning_file(reqs, tmp_path):
     with pytest.raises(pkg.GcnDecompError) as e:
         pkg.Decompiler(0, tuning_file=str(bad))
     assert e.value.rc == pkg.GCN_EINVAL
+
+
+def test_packed_submit_and_raw_fetch(reqs):
+    """Files submitted back to back from one buffer, and fetched as one buffer with numpy
+    offsets, give the same texts and statuses as the per-file calls."""
+    import numpy as np
+
+    pkg.build()
+    offs = np.zeros(len(reqs) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(r) for r in reqs])
+    packed = np.frombuffer(b"".join(reqs), dtype=np.uint8)
+    with pkg.Decompiler(0) as dec:
+        want = dec.decompile(reqs)
+        ids = dec.submit_packed(packed, offs)
+        raw, o, st = dec.fetch_batch_raw(ids)
+    got = [(raw[o[i]:o[i + 1]].tobytes().decode(), int(st[i])) for i in range(len(reqs))]
+    assert got == want
