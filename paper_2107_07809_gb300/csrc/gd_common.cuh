@@ -67,7 +67,8 @@ enum : uint8_t { FL_UNSUPPORTED = 1, FL_BAD = 2, FL_REGRANGE = 4, FL_NOLABEL = 8
 
 // operand signature of every opcode: V vgpr, W vgpr pair, s sgpr, p sgpr pair,
 // q sgpr quad, S 32-bit source, M 64-bit mask, c vcc, o off, K constant, L label, * free
-static __constant__ char c_sig[O_COUNT][12] = {
+// (global memory, not the constant bank: lanes read the signatures of different opcodes)
+static __device__ char c_sig[O_COUNT][12] = {
     "?", "s,p,K", "p,p,K", "q,p,K", "*", "s,S", "s,S,S", "s,S,S", "s,S,S",
     "S,S", "S,S", "S,S", "S,S", "S,S", "S,S", "S,S", "S,S", "S,S", "S,S", "S,S", "S,S",
     "M,M", "M,M,M", "M,M,M", "M,M", "L", "L", "L", "L", "",

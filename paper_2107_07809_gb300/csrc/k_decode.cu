@@ -62,7 +62,9 @@ struct DecodeTables {
   uint8_t nsig[O_COUNT];   // operand count of the signature
   uint16_t ht[kHash];      // hash slot -> op + 1 (0 = empty)
 };
-__constant__ DecodeTables c_tab;
+// in global memory, not the constant bank: lanes look up different mnemonics,
+// and the constant cache serves one address per access
+__device__ DecodeTables c_tab;
 
 static const uint32_t kInlineFloatBits[8] = {0x3f000000u, 0xbf000000u, 0x3f800000u, 0xbf800000u,
                                              0x40000000u, 0xc0000000u, 0x40800000u, 0xc0800000u};

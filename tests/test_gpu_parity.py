@@ -155,3 +155,18 @@ def test_text_parity_edge_cases(dec):
         b"no kernel here\n",
     ]
     _check_text(dec, files)
+
+
+def test_text_parity_label_cases(dec):
+    """Label lookup through the batch-wide table: a label defined twice (the first definition
+    wins), a longer label sharing the branch's name as a prefix, a branch to a name only the
+    longer label has (parse error), and a branch to a label only another kernel of the file
+    defines (parse error in that kernel only)."""
+    t = gcngen.generate(0, 1).kernel(0)
+    lines = t.split(b"\n")
+    i0 = lines.index(b".L0:")
+    dup = b"\n".join(lines[: i0 + 1] + [b".L1:"] + lines[i0 + 1:])
+    pre = t.replace(b".L1:", b".L10:\n.L1:")
+    only_long = t.replace(b".L1:", b".L10:")
+    cross = t + t.replace(b".kernel k0", b".kernel k1").replace(b".L0:", b".M0:")
+    _check_text(dec, [dup, pre, only_long, cross])
