@@ -520,6 +520,9 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   uint32_t* sorder = W.get<uint32_t>("sub_order", (size_t)NS2 + 1);
   uint32_t* shist = W.get<uint32_t>("sub_hist", shape_buckets() + 1);
   launch_sub_order(b, items, sitem, sub0, prank, plist, NS2, skey, shist, sorder, sc2, s);
+  b.prec = reinterpret_cast<PRec*>(W.get<uint4>("print_rec", 4ull * b.I + 4));
+  static_assert(sizeof(uint4) == kPRecBytes, "one uint4 per print record");
+  launch_print_records(b, s);
   CK(cudaEventRecord(h->ev[kStages + 1], s));
   launch_items(b, items, sitem, sub0, prank, plist, NS2, sorder, ilen, ioff, stage, ovl, &tot[13], 0, s);
   CK(cudaEventRecord(h->ev[kStages + 2], s));

@@ -54,6 +54,7 @@ struct Batch {
   uint32_t* label_instr;         // NL (global instruction index)
   uint32_t* label_hash;          // NL
   uint32_t* dyn_count;           // K: nodes of each kernel whose type comes from their operands
+  struct PRec* prec;             // 4I: the printer's record of every node slot (S13)
   uint32_t* label_tab;           // open-addressing table of label indices (kNone = empty), label_tab_mask + 1 slots
   uint32_t label_tab_mask;
   InstrRec* ins;                 // I
@@ -217,6 +218,7 @@ void launch_layout(Batch& b, Item* stage, uint32_t* stage_off, uint32_t* item_cn
                    cudaStream_t s);
 void launch_items_place(const Item* stage, const uint32_t* stage_off, uint32_t K, uint32_t total,
                         const uint32_t* item_cnt, const uint32_t* item_base, Item* items, cudaStream_t s);
+constexpr uint32_t kPRecBytes = 16;  // size of a print record (k_emit.cu)
 constexpr uint32_t kEmitSlot = 1024;  // staging bytes per emission sub-item
 void launch_print_list(Batch& b, uint32_t* flag, const uint32_t* rank, uint32_t* list, int phase, cudaStream_t s);
 void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* prank, uint32_t* weight,
@@ -225,6 +227,7 @@ void launch_sub_order(Batch& b, const Item* items, const uint32_t* sub_item, con
                       const uint32_t* prank, const uint32_t* pinstr, uint32_t N, uint32_t* key, uint32_t* hist,
                       uint32_t* order, ScanScratch sc, cudaStream_t s);
 uint32_t shape_buckets();
+void launch_print_records(Batch& b, cudaStream_t s);
 void launch_items(Batch& b, const Item* items, const uint32_t* sub_item, const uint32_t* sub0, const uint32_t* prank,
                   const uint32_t* pinstr, uint32_t N, const uint32_t* list, uint32_t* item_len,
                   const uint32_t* item_off, uint8_t* stage, uint32_t* ovf_list, uint32_t* ovf_count,

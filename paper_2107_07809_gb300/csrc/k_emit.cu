@@ -356,8 +356,58 @@ __device__ const ConvFmt g_conv[9][9] = {
     {{"(uint)", ""}, {"(uint)", ""}, {"(uint)", ""}, {"(uint)", ""}, {"as_uint(", ")"}, {"as_uint(", ")"}, {"as_uint(", ")"}, {"(uint)", ""}, {"", ""}},
 };
 
+// element type of load/store node id (slot 0 of its instruction): the argument's, else by width
+__device__ __noinline__ uint8_t mem_elem_of(const KView& v, uint32_t id, uint32_t width) {
+  Mem m = mem_of(v, id);
+  if (m.ok) return v.A[m.arg].elem;
+  return width == 8 ? TY_ULONG : TY_UINT;
+}
+
+// type of node id's own expression (nt: the kernel's node types)
+__device__ __noinline__ uint8_t node_expr_type_of(const KView& v, const uint8_t* nt, uint32_t id) {
+  const Node& n = v.node(id);
+  uint8_t T = tresolve(nt[id], node_width(v, id));
+  if (n.kind == N_PAIR) return TY_ULONG;
+  if (n.kind != N_OP) return TY_UINT;
+  uint16_t op = n.op;
+  if (op_scmp(op) || op_vcmp(op)) return TY_INT;
+  switch (op) {
+    case O_S_ADD_U32: case O_V_ADD_U32: case O_V_SUB_U32: case O_V_MUL_LO_U32: case O_V_MAD_U32_U24:
+    case O_V_MUL_U32_U24: case O_V_LSHRREV_B32: case O_V_ADD_CO_U32: case O_V_SUB_CO_U32: case O_S_LSHR_B32:
+    case O_S_BFE_U32: return TY_UINT;
+    case O_S_MUL_I32: case O_V_ASHRREV_I32: return TY_INT;
+    case O_S_LSHL_B32: case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_LSHLREV_B32:
+    case O_V_LSHLREV_B64: case O_V_CNDMASK_B32: return T;
+    case O_V_ADD_F32: case O_V_SUB_F32: case O_V_MUL_F32: case O_V_FMA_F32: case O_V_CVT_F32_I32:
+    case O_V_CVT_F32_U32: case O_V_CVT_F32_F64: return TY_FLOAT;
+    case O_V_CVT_F64_F32: case O_V_CVT_F64_I32: case O_V_ADD_F64: case O_V_MUL_F64: case O_V_FMA_F64: return TY_DOUBLE;
+    case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused ? T : TY_UINT;
+    case O_GLOBAL_LOAD_DWORD: return mem_elem_of(v, id, 4);
+    case O_GLOBAL_LOAD_DWORDX2: return mem_elem_of(v, id, 8);
+  }
+  return T == TY_ULONG ? TY_ULONG : TY_UINT;
+}
+
+// What the printer reads of a node, in one 16-byte record per node slot,
+// written after the analysis (k_print_records): one load per expression level
+// instead of the node, its class, its variable and its types from six arrays.
+struct PRec {
+  uint16_t op;    // the node's operation
+  uint8_t kind;   // N_*
+  uint8_t fused;  // a fused 64-bit carry half
+  uint8_t cls;    // class (K_*) and its number
+  uint8_t clk;
+  uint8_t nt;     // resolved node type
+  uint8_t etype;  // type of the node's own expression
+  int32_t var;    // its variable, or -1
+  uint8_t vtype;  // the variable's type
+  uint8_t pad[3];
+};
+static_assert(sizeof(PRec) == kPRecBytes, "PRec is 16 bytes");
+
 struct Em {
   KView v;
+  const PRec* pr;  // the kernel's print records (null: not built yet)
   const Batch* b;
   const KHdr* K;
   const uint32_t* uses;
@@ -398,35 +448,10 @@ struct Em {
   }
 
   // ---- types of expressions (computed before printing) ------------------------
-  __device__ __noinline__ uint8_t mem_elem(const Node& n, uint32_t width) {
-    Mem m = mem_of(v, (uint32_t)(&n - v.N));
-    if (m.ok) return v.A[m.arg].elem;
-    return width == 8 ? TY_ULONG : TY_UINT;
+  __device__ __forceinline__ uint8_t mem_elem(const Node& n, uint32_t width) {
+    return mem_elem_of(v, (uint32_t)(&n - v.N), width);
   }
-
-  __device__ __noinline__ uint8_t node_expr_type(uint32_t id) {
-    const Node& n = v.node(id);
-    uint8_t T = NT(id);
-    if (n.kind == N_PAIR) return TY_ULONG;
-    if (n.kind != N_OP) return TY_UINT;
-    uint16_t op = n.op;
-    if (op_scmp(op) || op_vcmp(op)) return TY_INT;
-    switch (op) {
-      case O_S_ADD_U32: case O_V_ADD_U32: case O_V_SUB_U32: case O_V_MUL_LO_U32: case O_V_MAD_U32_U24:
-      case O_V_MUL_U32_U24: case O_V_LSHRREV_B32: case O_V_ADD_CO_U32: case O_V_SUB_CO_U32: case O_S_LSHR_B32:
-      case O_S_BFE_U32: return TY_UINT;
-      case O_S_MUL_I32: case O_V_ASHRREV_I32: return TY_INT;
-      case O_S_LSHL_B32: case O_V_AND_B32: case O_V_OR_B32: case O_V_XOR_B32: case O_V_LSHLREV_B32:
-      case O_V_LSHLREV_B64: case O_V_CNDMASK_B32: return T;
-      case O_V_ADD_F32: case O_V_SUB_F32: case O_V_MUL_F32: case O_V_FMA_F32: case O_V_CVT_F32_I32:
-      case O_V_CVT_F32_U32: case O_V_CVT_F32_F64: return TY_FLOAT;
-      case O_V_CVT_F64_F32: case O_V_CVT_F64_I32: case O_V_ADD_F64: case O_V_MUL_F64: case O_V_FMA_F64: return TY_DOUBLE;
-      case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused ? T : TY_UINT;
-      case O_GLOBAL_LOAD_DWORD: return mem_elem(n, 4);
-      case O_GLOBAL_LOAD_DWORDX2: return mem_elem(n, 8);
-    }
-    return T == TY_ULONG ? TY_ULONG : TY_UINT;
-  }
+  __device__ __forceinline__ uint8_t node_expr_type(uint32_t id) { return node_expr_type_of(v, nt, id); }
 
   __device__ __noinline__ uint8_t expr_type(uint32_t r, uint8_t want) {
     r = fwd(v, r);
@@ -466,7 +491,19 @@ struct Em {
   // helpers are inlined into P, so an expression level costs one call frame.
   __device__ __noinline__ void P(uint32_t r, uint8_t want, int d, bool top) {
     if (top) return body(rid(r), d);
-    r = fwd(v, r);
+    // the node's record answers forwarding, class, variable and types at once; a copy or a pair
+    // goes the long way
+    PRec rec;
+    bool pre = false;  // rec belongs to node rid(r), and r needs no forwarding
+    if (r_node(r)) {
+      rec = pr[rid(r)];
+      const bool copy = rec.kind == N_OP && (rec.op == O_V_MOV_B32 || rec.op == O_S_MOV_B32 ||
+                                             rec.op == O_BUFFER_STORE_DWORD || rec.op == O_BUFFER_LOAD_DWORD);
+      if ((copy && rpart(r) == PART_ENTIRE) || rec.kind == N_PAIR) r = fwd(v, r);
+      else pre = true;
+    } else if (r == kTop) {
+      r = kUndef;  // what forwarding makes of it
+    }
     uint8_t t, lk;  // the value's type; its leaf kind (a class, LF_VAR, or LF_EXPR / LF_PART)
     uint32_t num = 0, id = 0;
     if (r_phi(r)) {
@@ -475,7 +512,9 @@ struct Em {
       lk = x < 0 ? (uint8_t)K_UNDEF : LF_VAR;
       num = (uint32_t)x;
     } else {
-      const Cls c = (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) ? Cls{v.cc[rid(r)], v.ck[rid(r)]} : classify(v, r);
+      const Cls c = (pre && rpart(r) == PART_ENTIRE)                  ? Cls{rec.cls, rec.clk}
+                    : (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) ? Cls{v.cc[rid(r)], v.ck[rid(r)]}
+                                                                     : classify(v, r);
       lk = c.c;
       num = c.k;
       switch (c.c) {
@@ -501,13 +540,13 @@ struct Em {
             t = TY_UINT;
             lk = LF_PART;
             id = rid(r);
-          } else if (vo[rid(r)] >= 0) {
-            num = (uint32_t)vo[rid(r)];
-            t = vt[num];
+          } else if ((pre ? rec.var : vo[rid(r)]) >= 0) {
+            num = (uint32_t)(pre ? rec.var : vo[rid(r)]);
+            t = pre ? rec.vtype : vt[num];
             lk = LF_VAR;
           } else {
             id = rid(r);
-            t = node_expr_type(id);
+            t = pre ? rec.etype : node_expr_type(id);
             lk = LF_EXPR;
           }
       }
@@ -592,14 +631,15 @@ struct Em {
   // a node's own expression (ignoring its variable), operands at depth d
   __device__ __noinline__ void node_expr(uint32_t id, int d) { P(mkref(id, PART_ENTIRE), TY_NONE, d, true); }
   __device__ __forceinline__ void body(uint32_t id, int d) {
-    const Node& n = v.node(id);
-    const uint8_t T = NT(id);
-    if (n.kind != N_OP && n.kind != N_PAIR) {
+    const Node& n = v.node(id);  // its sources and constants, where a template needs them
+    const PRec rec = pr[id];
+    const uint8_t T = rec.nt;
+    if (rec.kind != N_OP && rec.kind != N_PAIR) {
       partial = true;
       w.s("0u");
       return;
     }
-    const Fmt& f = g_fmt[n.kind == N_PAIR ? O_COUNT : n.op];
+    const Fmt& f = g_fmt[rec.kind == N_PAIR ? O_COUNT : rec.op];
     const uint8_t fk = f.kind;
     if (fk == F_LOAD4 || fk == F_LOAD8) return memref(n, fk == F_LOAD8 ? 8 : 4, d);
     if (fk == F_BFE) {
@@ -630,7 +670,7 @@ struct Em {
       return;
     }
     // a carry half not fused into a 64-bit operation keeps 32-bit operands and is not exact
-    const bool lone = fk == F_CARRY && !n.fused;
+    const bool lone = fk == F_CARRY && !rec.fused;
     if (lone) partial = true;
     for (int i = 0; i < (int)sizeof(f.tpl); ++i) {
       const char c = f.tpl[i];
@@ -1150,6 +1190,7 @@ __global__ void __launch_bounds__(128, 12)
   em.vo = b.var_of + nb;
   em.pv = b.phi_var + K.state_off;
   em.vt = b.var_type + nb + K.state_off;
+  em.pr = b.prec + nb;
   if (stage) em.w = Wr{stage + (size_t)sidx * kEmitSlot, 0, kEmitSlot, false};
   else em.w = Wr{b.out + item_off[sidx], 0, item_len[sidx], false};
   em.partial = false;
@@ -1310,6 +1351,49 @@ __global__ void __launch_bounds__(256)
     const uint8_t* from = stage + (size_t)(s0 + src) * kEmitSlot;
     for (uint32_t q = lane; q < l; q += 32) out[o + q] = from[q];
   }
+}
+
+// Print records: one thread per instruction, its four node slots.
+__global__ void __launch_bounds__(128, 8) k_print_records(const __grid_constant__ Batch b) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= b.I) return;
+  // only reached nodes are ever printed (the reachability walk follows the printed operands)
+  const uint32_t f4 = reinterpret_cast<const uint32_t*>(b.nflag)[gi];
+  if (!(f4 & 0x01010101u)) return;
+  const uint32_t k = b.ikern[gi];
+  const KHdr& K = b.kh[k];
+  if (K.bad) return;
+  const size_t nb = 4 * (size_t)K.first_instr;
+  const KView v = make_view(b, K, k);
+  const uint8_t* nt = b.ntype + nb;
+  const int32_t* vo = b.var_of + nb;
+  const uint8_t* vt = b.var_type + nb + K.state_off;
+  const uint32_t id0 = 4 * (gi - K.first_instr);
+  for (uint32_t s = 0; s < 4; ++s) {
+    if (!((f4 >> (8 * s)) & 1u)) continue;
+    const uint32_t id = id0 + s;
+    const Node& n = v.node(id);
+    PRec r;
+    r.op = n.op;
+    r.kind = n.kind;
+    r.fused = n.fused;
+    r.cls = v.cc[id];
+    r.clk = v.ck[id];
+    r.nt = tresolve(nt[id], node_width(v, id));
+    r.var = vo[id];
+    // the expression's type is read for a node printed in place (no variable, no leaf class)
+    r.etype = (r.var < 0 && !leaf_like(r.cls) && (n.kind == N_OP || n.kind == N_PAIR)) ? node_expr_type_of(v, nt, id)
+                                                                                        : TY_UINT;
+    r.vtype = r.var >= 0 ? vt[r.var] : 0;
+    r.pad[0] = r.pad[1] = r.pad[2] = 0;
+    b.prec[nb + id] = r;
+  }
+}
+
+void launch_print_records(Batch& b, cudaStream_t s) {
+  if (!b.I) return;
+  k_print_records<<<(b.I + 127) / 128, 128, 0, s>>>(b);
+  ++launch_counter();
 }
 
 // Printing order.  Lanes of a warp that print statements of different shapes
