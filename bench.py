@@ -296,7 +296,7 @@ def serve(pkg, local, rates, n_pool=1000, max_requests=20000, max_seconds=5.0, b
 # the library's event timing of the statement-printing kernel alone (not a stage)
 KERNEL_TIMING = "k_items (S13 print)"
 # ncu counters of one k_items launch (4,000 kernels of the batch distribution)
-K_ITEMS_TRAFFIC = {"instrs": 2201608, "bytes": 0.727066880e9 + 0.286976768e9}
+K_ITEMS_TRAFFIC = {"instrs": 2201608, "bytes": 0.579754240e9 + 0.252110336e9}
 
 
 def large_batch(args, pkg, torch, rank, world, local):
