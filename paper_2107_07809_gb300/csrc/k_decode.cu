@@ -635,9 +635,14 @@ __global__ void k_exec_list(uint32_t I, const uint32_t* __restrict__ flag, const
 
 // per kernel: the exec-mask forms, matched over the kernel's exec-form
 // instructions only (in program order) with a stack of open forms
+// A warp per kernel: the lanes load the kernel's next 32 exec-mask instructions
+// into shared memory together, then lane 0 runs the form matcher over them.
 __global__ void k_exec_forms(const __grid_constant__ Batch b, const uint32_t* __restrict__ pos,
                              const uint32_t* __restrict__ list) {
-  uint32_t k = walk_kernel();
+  __shared__ InstrRec s_rec[4][32];
+  __shared__ uint32_t s_idx[4][32];
+  const uint32_t wp = threadIdx.x / 32, lane = threadIdx.x & 31u;
+  const uint32_t k = blockIdx.x * (blockDim.x / 32) + wp;  // at most four warps per block (walk_threads)
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   const InstrRec* R = b.ins + K.first_instr;
@@ -648,9 +653,17 @@ __global__ void k_exec_forms(const __grid_constant__ Batch b, const uint32_t* __
   Form st[kMaxExecDepth];
   int sp = 0;
   bool bad = false;
-  for (uint32_t c = c0; c < c1 && !bad; ++c) {
-    const uint32_t i = list[c] - K.first_instr;
-    const InstrRec& r = R[i];
+  for (uint32_t base = c0; base < c1; base += 32) {
+    if (base + lane < c1) {
+      const uint32_t i = list[base + lane] - K.first_instr;
+      s_idx[wp][lane] = i;
+      s_rec[wp][lane] = R[i];
+    }
+    __syncwarp();
+    const uint32_t m = min(32u, c1 - base);
+    for (uint32_t q = 0; lane == 0 && q < m && !bad; ++q) {
+    const uint32_t i = s_idx[wp][q];
+    const InstrRec& r = s_rec[wp][q];
     switch (r.op) {
       case O_S_AND_SAVEEXEC:
         if (otag(r.opnd[0]) != TG_SGPR || otag(r.opnd[1]) != TG_VCC || sp == kMaxExecDepth) { bad = true; break; }
@@ -719,9 +732,14 @@ __global__ void k_exec_forms(const __grid_constant__ Batch b, const uint32_t* __
       default:
         break;
     }
+    }
+    if (__shfl_sync(0xFFFFFFFFu, (int)bad, 0)) break;
+    __syncwarp();
   }
-  if (sp) bad = true;
-  if (bad) K.bad |= 4u;
+  if (lane == 0) {
+    if (sp) bad = true;
+    if (bad) K.bad |= 4u;
+  }
 }
 
 __device__ __forceinline__ uint32_t resolve_t(const uint8_t* ctl, uint32_t t, uint32_t n) {
