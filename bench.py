@@ -5,8 +5,9 @@ One step decompiles the whole workload batch (every stage S1..S13 of the
 method) through the C ABI.  Default workload: 10,000 seeded synthetic kernels
 with log-uniform lengths 50..2000 (the plain-method-at-scale configuration),
 one kernel per file, text resident in HBM when the timed region starts
-(`value`).  `e2e` measures the same through the host-buffer entry points
-(submit_batch + fetch_batch), host<->device copies inside the timed region.
+(`value`).  `e2e` measures the same through the job service's host-buffer
+entry points (submit_batch, given the whole batch as one buffer and its
+offsets, and fetch_batch), host<->device copies inside the timed region.
 `per_kernel` times the plain form (one pipeline run per kernel) on a sample of
 the same kernels; `serve` drives the job service with open-loop Poisson
 arrivals at 1k, 10k and 100k requests/s and reports p50/p99 latency.
