@@ -79,6 +79,10 @@ struct gcngen_params {
   int32_t p_select;            // percent chance that a 32-bit operation is a select (ternary); 0 = never
   int32_t p_sysval;            // percent chance that an integer leaf is a system value or a scalar
                                // bit field (s_load from the dispatch packet, s_lshr_b32, s_bfe_u32); 0 = never
+  int32_t p_flat;              // percent chance that a buffer load or store is a FLAT instruction
+                               // (flat_load_dword[x2] / flat_store_dword[x2]); 0 = never
+  int32_t p_mulhi;             // percent chance that a 32-bit integer operation is a double-suffix
+                               // high multiply (v_mul_hi_u32_u24 / v_mul_hi_i32_i24); 0 = never
 };
 }
 
@@ -306,13 +310,16 @@ struct Gen {
     Opd idx = index_for(b, d);
     int a = address(b, idx);
     int r;
+    const bool flat = P.p_flat > 0 && rng.chance(P.p_flat);
     if (is64(buf_ty[b])) {
       r = mark + (mark & 1);
-      ins(f("global_load_dwordx2 v[%d:%d], v[%d:%d], off", r, r + 1, a, a + 1));
+      if (flat) ins(f("flat_load_dwordx2 v[%d:%d], v[%d:%d]", r, r + 1, a, a + 1));
+      else ins(f("global_load_dwordx2 v[%d:%d], v[%d:%d], off", r, r + 1, a, a + 1));
       vtop = r + 2;
     } else {
       r = mark;
-      ins(f("global_load_dword v%d, v[%d:%d], off", r, a, a + 1));
+      if (flat) ins(f("flat_load_dword v%d, v[%d:%d]", r, a, a + 1));
+      else ins(f("global_load_dword v%d, v[%d:%d], off", r, a, a + 1));
       vtop = r + 1;
     }
     touchv(r, is64(buf_ty[b]) ? 2 : 1);
@@ -485,6 +492,13 @@ struct Gen {
       ins(f("%s v%d, %s, %s", nm[op], r, a.s().c_str(), b.s().c_str()));
       return V(r);
     }
+    if (P.p_mulhi > 0 && rng.chance(P.p_mulhi)) {  // high half of a 24-bit multiply (double suffix)
+      Opd a = gen32(t, d - 1);
+      Opd b = vgpr(gen32(t, d - 1));
+      r = res32(mark);
+      ins(f("%s v%d, %s, %s", t == TI ? "v_mul_hi_i32_i24" : "v_mul_hi_u32_u24", r, a.s().c_str(), b.s().c_str()));
+      return V(r);
+    }
     int op = rng.below(t == TU ? 9 : 8);
     Opd a = gen32(t, d - 1);
     if (op == 6 || op == 7) {  // shifts by a constant
@@ -590,11 +604,13 @@ struct Gen {
     if (is64(t)) {
       int v = gen64(t, d);
       int a = address(b, lin());
-      ins(f("global_store_dwordx2 v[%d:%d], v[%d:%d], off", a, a + 1, v, v + 1));
+      if (P.p_flat > 0 && rng.chance(P.p_flat)) ins(f("flat_store_dwordx2 v[%d:%d], v[%d:%d]", a, a + 1, v, v + 1));
+      else ins(f("global_store_dwordx2 v[%d:%d], v[%d:%d], off", a, a + 1, v, v + 1));
     } else {
       Opd v = vgpr(gen32(t, d));
       int a = address(b, lin());
-      ins(f("global_store_dword v[%d:%d], %s, off", a, a + 1, v.s().c_str()));
+      if (P.p_flat > 0 && rng.chance(P.p_flat)) ins(f("flat_store_dword v[%d:%d], %s", a, a + 1, v.s().c_str()));
+      else ins(f("global_store_dword v[%d:%d], %s, off", a, a + 1, v.s().c_str()));
     }
   }
 
@@ -973,6 +989,23 @@ gcngen_params preset(int cfg) {
       p.max_len = 2000;
       p.p_sysval = 10;
       break;
+    case 7:  // the batch mix with FLAT loads/stores (30%) and double-suffix high multiplies (10%)
+      p.min_len = 50;
+      p.max_len = 2000;
+      p.p_flat = 30;
+      p.p_mulhi = 10;
+      break;
+    case 8:  // mixed uniform and divergent nesting: divergent if / if-else (forms 1-3), uniform
+             // if / if-else and loops interleaved, nesting <= 4
+      p.min_len = 50;
+      p.max_len = 2000;
+      p.w_if = 30;
+      p.w_ifelse = 30;
+      p.w_loop = 15;
+      p.w_uif = 25;
+      p.max_depth = 4;
+      p.p_ctrl = 18;
+      break;
   }
   return p;
 }
@@ -987,9 +1020,9 @@ struct Result {
 
 extern "C" {
 
-// Default knobs of workload `cfg` (0..6).  Returns 0, or -1 for an unknown index.
+// Default knobs of workload `cfg` (0..8).  Returns 0, or -1 for an unknown index.
 int gcngen_preset(int cfg, gcngen_params* out) {
-  if (cfg < 0 || cfg > 6 || !out) return -1;
+  if (cfg < 0 || cfg > 8 || !out) return -1;
   *out = preset(cfg);
   return 0;
 }

@@ -65,6 +65,7 @@ def lib():
             L.oracle_batch_free.argtypes = [vp]
             L.oracle_reduce_graph.argtypes = [i32, vp, vp, vp, i32]
             L.oracle_type_join.argtypes = [i32, i32]
+            L.oracle_set_type_sweep_limit.argtypes = [ctypes.c_uint32]
             _lib = L
     return _lib
 
@@ -105,6 +106,13 @@ def decompile(text: bytes | str, with_ir: bool = False) -> Result:
         return Result(buf.raw[:n].decode(), st, ir)
     finally:
         L.oracle_free(h)
+
+
+def set_type_sweep_limit(n: int = 0) -> None:
+    """Sweep limit of the type fixed point for later calls (0 = the default, never reached).  A
+    kernel whose types still change in the last allowed sweep is not decompiled: status 3 and the
+    text `/* not decompiled: fixed-point limit */` (a test hook for the capped path)."""
+    lib().oracle_set_type_sweep_limit(n)
 
 
 def decompile_batch(text: np.ndarray, offsets: np.ndarray, threads: int = 1):

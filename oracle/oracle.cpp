@@ -258,7 +258,11 @@ enum Op : uint16_t {
   BUFFER_LOAD_DWORD = 81, BUFFER_STORE_DWORD = 82,
   V_CNDMASK_B32 = 83,  // the ternary: vD = vcc ? src1 : src0
   S_LSHR_B32 = 84, S_BFE_U32 = 85,  // scalar shift right and bit-field extract (get_num_groups, get_work_dim)
-  OP_COUNT = 86
+  // "The body extraction": FLAT instructions (prefix "flat", a VGPR pair holds the 64-bit
+  // address) and the double-suffix V_MUL_HI family (result type, then operand type)
+  FLAT_LOAD_DWORD = 86, FLAT_LOAD_DWORDX2 = 87, FLAT_STORE_DWORD = 88, FLAT_STORE_DWORDX2 = 89,
+  V_MUL_HI_U32_U24 = 90, V_MUL_HI_I32_I24 = 91,
+  OP_COUNT = 92
 };
 
 // comparison codes shared by s_cmp and v_cmp: eq, ne(lg/neq), gt, lt, ge, le
@@ -348,6 +352,12 @@ std::vector<OpInfo> build_table() {
   set(GLOBAL_STORE_DWORDX2, "global_store_dwordx2", "W,W,o");
   set(BUFFER_LOAD_DWORD, "buffer_load_dword", "V,o,q,s");
   set(BUFFER_STORE_DWORD, "buffer_store_dword", "V,o,q,s");
+  set(FLAT_LOAD_DWORD, "flat_load_dword", "V,W");
+  set(FLAT_LOAD_DWORDX2, "flat_load_dwordx2", "W,W");
+  set(FLAT_STORE_DWORD, "flat_store_dword", "W,V");
+  set(FLAT_STORE_DWORDX2, "flat_store_dwordx2", "W,W");
+  set(V_MUL_HI_U32_U24, "v_mul_hi_u32_u24", "V,S,S");
+  set(V_MUL_HI_I32_I24, "v_mul_hi_i32_i24", "V,S,S");
   return t;
 }
 
@@ -528,6 +538,12 @@ Decoded decode(const std::vector<std::string>& rows, const Config& cfg) {
           tag_of(rec.opnd[2]) == TG_ICONST)
         rec.imm = (uint32_t)iconst_value(rec.opnd[2]);
       if ((rec.op == BUFFER_LOAD_DWORD || rec.op == BUFFER_STORE_DWORD) && (rec.imm & 3u)) rec.flags |= F_BAD;
+      // a global or FLAT access with a constant byte offset reaches another element than its
+      // address operand names; offsets are not folded into the address, so the instruction
+      // stays inline assembly
+      if (rec.op >= GLOBAL_LOAD_DWORD && rec.op <= GLOBAL_STORE_DWORDX2 && rec.imm) rec.op = OP_UNKNOWN;
+      if (rec.op >= FLAT_LOAD_DWORD && rec.op <= FLAT_STORE_DWORDX2 && rec.imm) rec.op = OP_UNKNOWN;
+      if (rec.op == OP_UNKNOWN) rec.flags |= F_UNSUPPORTED;
     }
     if (rec.op == S_WAITCNT) rec.nops = 0;
     // register ranges against the configuration
@@ -840,7 +856,8 @@ std::vector<uint32_t> regs_of(const Regs& R, uint32_t o) {
 
 bool is64_result(int op) {
   return op == S_LOAD_DWORDX2 || op == V_CVT_F64_F32 || op == V_CVT_F64_I32 || op == V_LSHLREV_B64 ||
-         op == V_ADD_F64 || op == V_MUL_F64 || op == V_FMA_F64 || op == GLOBAL_LOAD_DWORDX2;
+         op == V_ADD_F64 || op == V_MUL_F64 || op == V_FMA_F64 || op == GLOBAL_LOAD_DWORDX2 ||
+         op == FLAT_LOAD_DWORDX2;
 }
 bool is_scmp(int op) { return op >= S_CMP_FIRST && op < S_CMP_FIRST + 12; }
 bool is_vcmp(int op) { return op >= V_CMP_FIRST && op < V_CMP_FIRST + 18; }
@@ -886,7 +903,7 @@ std::vector<Def> defs_of(const Decoded& d, const LogicalCfg& L, const Regs& R, u
       }
       out.push_back({R.vcc(), UNDEF});
       break;
-    case GLOBAL_STORE_DWORD: case GLOBAL_STORE_DWORDX2: break;
+    case GLOBAL_STORE_DWORD: case GLOBAL_STORE_DWORDX2: case FLAT_STORE_DWORD: case FLAT_STORE_DWORDX2: break;
     case BUFFER_STORE_DWORD: out.push_back({R.spill(r.imm / 4), node_ref(i, 0, P_ENTIRE)}); break;
     case OP_UNKNOWN: {
       if (r.nops == 0) break;
@@ -1225,7 +1242,9 @@ void build_nodes(Kernel& K) {
               char s = sig[2 * k];
               bool is_dst = (k == 0 && (s == 'V' || s == 'W' || s == 's' || s == 'p' || s == 'q' || s == 'c')) ||
                             (k == 1 && s == 'c' && (op == V_ADD_CO_U32 || op == V_SUB_CO_U32));
-              if (op == GLOBAL_STORE_DWORD || op == GLOBAL_STORE_DWORDX2) is_dst = false;
+              if (op == GLOBAL_STORE_DWORD || op == GLOBAL_STORE_DWORDX2 || op == FLAT_STORE_DWORD ||
+                  op == FLAT_STORE_DWORDX2)
+                is_dst = false;
               if (is_scmp(op)) is_dst = false;
               if (is_dst || s == 'o') continue;
               uint32_t slot = 1 + (uint32_t)srcs.size();
@@ -1527,8 +1546,29 @@ int resolve_type(int t, int width) {
   return t;
 }
 
-bool is_store(int op) { return op == GLOBAL_STORE_DWORD || op == GLOBAL_STORE_DWORDX2; }
-bool is_gload(int op) { return op == GLOBAL_LOAD_DWORD || op == GLOBAL_LOAD_DWORDX2; }
+// Memory accesses.  FLAT instructions may address global memory, LDS or scratch
+// ("The body extraction"); in this dialect their address is always formed from
+// a __global buffer argument, exactly as for the GLOBAL instructions, so both
+// are the same access: the same dataflow, address match and output.
+bool is_store(int op) {
+  return op == GLOBAL_STORE_DWORD || op == GLOBAL_STORE_DWORDX2 || op == FLAT_STORE_DWORD || op == FLAT_STORE_DWORDX2;
+}
+bool is_gload(int op) {
+  return op == GLOBAL_LOAD_DWORD || op == GLOBAL_LOAD_DWORDX2 || op == FLAT_LOAD_DWORD || op == FLAT_LOAD_DWORDX2;
+}
+// bytes one access moves
+int mem_width(int op) {
+  return op == GLOBAL_LOAD_DWORDX2 || op == GLOBAL_STORE_DWORDX2 || op == FLAT_LOAD_DWORDX2 || op == FLAT_STORE_DWORDX2
+             ? 8
+             : 4;
+}
+
+// Sweep limit of the type fixed point.  The lattice is finite and a sweep that
+// changes something raises at least one type, so the default is never reached;
+// a smaller limit (oracle_set_type_sweep_limit, a test hook) caps kernels, which
+// are then not decompiled (FIXPOINT_CAP).
+constexpr uint32_t kTypeSweepDefault = 100000;
+static uint32_t g_type_sweep_limit = kTypeSweepDefault;
 
 struct Emitter {
   Kernel& K;
@@ -1575,7 +1615,7 @@ struct Emitter {
     }
     if (n.kind != N_OP) return ch;
     if (is_gload(n.op) || is_store(n.op)) {
-      MemRef m = match_addr(K, fwd(K, n.src[0]), n.op == GLOBAL_LOAD_DWORDX2 || n.op == GLOBAL_STORE_DWORDX2 ? 8 : 4);
+      MemRef m = match_addr(K, fwd(K, n.src[0]), mem_width(n.op));
       if (m.ok) {
         if (m.idx != TOP) ch.push_back(m.idx);
       } else {
@@ -1709,8 +1749,10 @@ struct Emitter {
       case V_ADD_CO_U32: case V_SUB_CO_U32: return T_UINT;
       case V_ADDC_CO_U32: case V_SUBB_CO_U32: return n.fused ? tjoin(st(0), st(1)) : T_UINT;
       case V_LSHLREV_B64: return st(1);
-      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: {
-        int w = n.op == GLOBAL_LOAD_DWORDX2 ? 8 : 4;
+      case V_MUL_HI_U32_U24: return T_UINT;
+      case V_MUL_HI_I32_I24: return T_INT;
+      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: case FLAT_LOAD_DWORD: case FLAT_LOAD_DWORDX2: {
+        int w = mem_width(n.op);
         MemRef m = match_addr(K, fwd(K, n.src[0]), w);
         if (m.ok) return K.cfg.args[m.arg].elem;
         return w == 8 ? T_ULONG : T_UINT;
@@ -1723,24 +1765,53 @@ struct Emitter {
     return T_NONE;
   }
 
+  // A node whose type is its operands' type ("Data type recovery": the b32/b64
+  // suffixes carry no type, so bitwise operations, shifts that keep their
+  // operand's type, selects and the high half of a fused 64-bit add take the
+  // type of what flows into them).  Every other node has its type from its
+  // operation, its suffix or the argument it reads, whatever its operands are.
+  static bool typed_by_operands(const Node& n) {
+    if (n.kind != N_OP) return false;
+    switch (n.op) {
+      case S_LSHL_B32: case V_AND_B32: case V_OR_B32: case V_XOR_B32: case V_LSHLREV_B32: case V_LSHLREV_B64:
+      case V_CNDMASK_B32: return true;
+      case V_ADDC_CO_U32: case V_SUBB_CO_U32: return n.fused != 0;
+    }
+    return false;
+  }
+
+  // The least fixed point of the type equations: nodes typed by their
+  // operation are set once; the nodes typed by their operands and the used join
+  // versions start at the bottom and are swept (in node order, then the joins)
+  // until a sweep changes nothing.  A kernel still changing in sweep number
+  // g_type_sweep_limit is capped (types_capped).
+  bool types_capped = false;
   void infer_types() {
     ntype.assign(K.nodes.size(), T_NONE);
+    std::vector<uint32_t> dyn;
+    for (uint32_t id = 0; id < K.nodes.size(); ++id) {
+      if (!reach[id]) continue;
+      if (typed_by_operands(K.nodes[id])) dyn.push_back(id);
+      else ntype[id] = node_type(id);
+    }
+    for (uint32_t r : used_phis) ptype[r] = T_NONE;
     bool changed = true;
-    int guard = 0;
-    while (changed && guard++ < 100000) {
+    uint32_t sweeps = 0;
+    while (changed && sweeps < g_type_sweep_limit) {
+      ++sweeps;
       changed = false;
-      for (uint32_t id = 0; id < K.nodes.size(); ++id) {
-        if (!reach[id]) continue;
+      for (uint32_t id : dyn) {
         int t = tjoin(ntype[id], node_type(id));
         if (t != ntype[id]) { ntype[id] = t; changed = true; }
       }
       for (uint32_t r : used_phis) {
-        int t = ptype.count(r) ? ptype[r] : T_NONE;
+        int t = ptype[r];
         uint32_t B = phi_block(r), reg = phi_reg(r);
         for (uint32_t p : K.preds[B]) t = tjoin(t, ref_type(fwd(K, out_val(p, reg))));
-        if (!ptype.count(r) || ptype[r] != t) { ptype[r] = t; changed = true; }
+        if (ptype[r] != t) { ptype[r] = t; changed = true; }
       }
     }
+    types_capped = changed;
   }
 
   void number_vars() {
@@ -1907,6 +1978,13 @@ struct Emitter {
       case V_MUL_LO_U32: return binop(n, "*", T_UINT);
       case V_MAD_U32_U24: return Ex{"mad24(" + S(0, T_UINT) + ", " + S(1, T_UINT) + ", " + S(2, T_UINT) + ")", T_UINT};
       case V_MUL_U32_U24: return Ex{"mul24(" + S(0, T_UINT) + ", " + S(1, T_UINT) + ")", T_UINT};
+      // the double-suffix high multiplies: the high 32 bits of the 48-bit product of the low 24
+      // bits of the operands, zero-extended (u24) or sign-extended (i24); OpenCL's mul_hi of the
+      // operands reduced to 24 bits is exactly that
+      case V_MUL_HI_U32_U24:
+        return Ex{"mul_hi((" + S(0, T_UINT) + " & 16777215u), (" + S(1, T_UINT) + " & 16777215u))", T_UINT};
+      case V_MUL_HI_I32_I24:
+        return Ex{"mul_hi(((int)(" + S(0, T_UINT) + " << 8) >> 8), ((int)(" + S(1, T_UINT) + " << 8) >> 8))", T_INT};
       case V_AND_B32: return binop(n, "&", NT);
       case V_OR_B32: return binop(n, "|", NT);
       case V_XOR_B32: return binop(n, "^", NT);
@@ -1938,9 +2016,9 @@ struct Emitter {
       case V_FMA_F64: return Ex{"fma(" + S(0, T_DOUBLE) + ", " + S(1, T_DOUBLE) + ", " + S(2, T_DOUBLE) + ")", T_DOUBLE};
       case V_CNDMASK_B32:  // "Search for control structures": the ternary operator, one instruction
         return Ex{"(" + S(2, T_NONE) + " ? " + S(1, NT) + " : " + S(0, NT) + ")", NT};
-      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: {
+      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: case FLAT_LOAD_DWORD: case FLAT_LOAD_DWORDX2: {
         int elem;
-        std::string m = memref(n, op == GLOBAL_LOAD_DWORDX2 ? 8 : 4, &elem);
+        std::string m = memref(n, mem_width(op), &elem);
         return Ex{m, elem};
       }
     }
@@ -2029,7 +2107,7 @@ struct Emitter {
         }
         if (n.kind == N_OP && order[q] == 0 && is_store(n.op) && reach[id]) {
           int elem;
-          std::string m = memref(n, n.op == GLOBAL_STORE_DWORDX2 ? 8 : 4, &elem);
+          std::string m = memref(n, mem_width(n.op), &elem);
           line(lvl, m + " = " + E(fwd(K, n.src[1]), elem) + ";");
           continue;
         }
@@ -2417,6 +2495,7 @@ void decompile_kernel(Kernel& K, const RawKernel& raw) {
   Emitter em(K);
   em.mark_reach();
   em.infer_types();
+  if (em.types_capped) return fail(ST_FIXPOINT_CAP, "fixed-point limit", true);
   em.number_vars();
   for (uint32_t id = 0; id < K.nodes.size(); ++id) {
     if (!em.reach[id]) continue;
@@ -2484,6 +2563,8 @@ void oracle_text(void* h, char* dst) {
   memcpy(dst, s.data(), s.size());
 }
 int oracle_nkernels(void* h) { return (int)((FileResult*)h)->kernels.size(); }
+// sweep limit of the type fixed point for later calls (0 = the default); a test hook
+void oracle_set_type_sweep_limit(uint32_t n) { g_type_sweep_limit = n ? n : kTypeSweepDefault; }
 int oracle_kernel_status(void* h, int k) { return ((FileResult*)h)->kernels[k].status; }
 
 // IR arrays: 0 InstrRec[n]; 1 physical block_of[n]; 2 physical blocks;

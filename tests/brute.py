@@ -17,7 +17,10 @@ BUF_LEN = 4096
 GOFS = (3, 5, 0)
 
 
-def random_buffers(prog: gcn_interp.KernelText, seed: int):
+def random_buffers(prog: gcn_interp.KernelText, seed: int, wide: bool = False):
+    """Seeded buffers for the kernel's pointer arguments and values for its scalars.  With
+    `wide`, 32-bit integer buffers take values over their whole range (so that the high half of
+    a 24-bit product is not always zero); floats stay small and exact."""
     rng = np.random.default_rng(seed)
     bufs, scal = {}, {}
     for name, hidden, ptr, elem in prog.args:
@@ -27,9 +30,9 @@ def random_buffers(prog: gcn_interp.KernelText, seed: int):
             scal[name] = int(rng.integers(0, 40))
             continue
         if elem == "int":
-            a = rng.integers(-1000, 1000, BUF_LEN).astype(np.int32)
+            a = (rng.integers(-2**31, 2**31, BUF_LEN) if wide else rng.integers(-1000, 1000, BUF_LEN)).astype(np.int32)
         elif elem == "uint":
-            a = rng.integers(0, 2000, BUF_LEN).astype(np.uint32)
+            a = (rng.integers(0, 2**32, BUF_LEN) if wide else rng.integers(0, 2000, BUF_LEN)).astype(np.uint32)
         elif elem == "long":
             a = rng.integers(-10**6, 10**6, BUF_LEN).astype(np.int64)
         elif elem == "float":
@@ -42,10 +45,10 @@ def random_buffers(prog: gcn_interp.KernelText, seed: int):
     return bufs, scal
 
 
-def check(asm_text: str, ocl_text: str, seed: int = 0, groups=(2, 1)):
+def check(asm_text: str, ocl_text: str, seed: int = 0, groups=(2, 1), wide: bool = False):
     """Returns None when both executions agree, else a description."""
     prog = gcn_interp.KernelText(asm_text)
-    bufs, scal = random_buffers(prog, seed)
+    bufs, scal = random_buffers(prog, seed, wide)
     b_asm = {k: v.copy() for k, v in bufs.items()}
     b_ocl = {k: v.copy() for k, v in bufs.items()}
     gcn_interp.run_ndrange(asm_text, b_asm, scal, groups=groups, gofs=GOFS)

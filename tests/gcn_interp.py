@@ -378,9 +378,11 @@ class Wave:
             r = np.array([fma64(a[i], b[i], c[i]) if ex[i] else 0.0 for i in range(W)], dtype=np.float64)
             self.wr64(o[0], r.view(np.uint64))
             return None
-        if m in ("global_load_dword", "global_load_dwordx2"):
+        if m in ("global_load_dword", "global_load_dwordx2", "flat_load_dword", "flat_load_dwordx2"):
+            # a FLAT access here always reaches global memory (the generator forms its address
+            # from a buffer argument), so it behaves as the GLOBAL one
             addr = self.rd64(o[1])
-            nb = 4 if m == "global_load_dword" else 8
+            nb = 4 if m in ("global_load_dword", "flat_load_dword") else 8
             val = np.zeros(W, dtype=np.uint64)
             for i in range(W):
                 if ex[i]:
@@ -391,9 +393,9 @@ class Wave:
             else:
                 self.wr64(o[0], val)
             return None
-        if m in ("global_store_dword", "global_store_dwordx2"):
+        if m in ("global_store_dword", "global_store_dwordx2", "flat_store_dword", "flat_store_dwordx2"):
             addr = self.rd64(o[0])
-            nb = 4 if m == "global_store_dword" else 8
+            nb = 4 if m in ("global_store_dword", "flat_store_dword") else 8
             val = self.rd32(o[1]).astype(np.uint64) if nb == 4 else self.rd64(o[1])
             for i in range(W):
                 if ex[i]:
@@ -420,6 +422,11 @@ def _unbits(m: int):
     return np.array([(m >> i) & 1 == 1 for i in range(W)], dtype=bool)
 
 
+def _sext24(x):
+    x &= 0xFFFFFF
+    return x - (1 << 24) if x & 0x800000 else x
+
+
 def _s32(x):
     return x - (1 << 32) if x & 0x80000000 else x
 
@@ -441,6 +448,10 @@ _VOP2_INT = {
     "v_sub_u32": lambda a, b: (a - b) & _M32,
     "v_mul_lo_u32": lambda a, b: (a * b) & _M32,
     "v_mul_u32_u24": lambda a, b: (a & np.uint64(0xFFFFFF)) * (b & np.uint64(0xFFFFFF)),
+    # high 32 bits of the 48-bit product of the low 24 bits (zero- / sign-extended)
+    "v_mul_hi_u32_u24": lambda a, b: ((a & np.uint64(0xFFFFFF)) * (b & np.uint64(0xFFFFFF))) >> np.uint64(32),
+    "v_mul_hi_i32_i24": lambda a, b: np.array(
+        [((_sext24(int(x)) * _sext24(int(y))) >> 32) & 0xFFFFFFFF for x, y in zip(a, b)], dtype=np.uint64),
     "v_and_b32": lambda a, b: a & b,
     "v_or_b32": lambda a, b: a | b,
     "v_xor_b32": lambda a, b: a ^ b,

@@ -7,7 +7,8 @@ uses an undeclared variable, or mixes operand types without an explicit cast
 is rejected.  Semantics are C's with the following readings: integers wrap
 (two's complement), >> of a signed value is arithmetic, the work-item
 functions return uint (the decompiler treats them as 32-bit values), mad24 and
-mul24 use the low 24 bits of their operands, fma rounds once.
+mul24 use the low 24 bits of their operands, mul_hi is the high half of the
+full product, fma rounds once.
 """
 from __future__ import annotations
 
@@ -422,6 +423,13 @@ def call(nm, args, env: Env):
         if nm == "mad24":
             r += int(args[2][1])
         return "uint", _wrap(r, "uint")
+    if nm == "mul_hi":  # high half of the full product of two 32-bit integers of one type
+        want(2)
+        if args[0][0] != args[1][0] or args[0][0] not in ("int", "uint"):
+            raise EvalError("mul_hi operand types")
+        ty = args[0][0]
+        x, y = int(args[0][1]), int(args[1][1])
+        return ty, _wrap((x * y) >> 32, ty)
     if nm == "upsample":
         want(2)
         if args[0][0] != "uint" or args[1][0] != "uint":

@@ -172,7 +172,7 @@ def test_join_versions_are_minimal():
     assert used > 0
 
 
-@pytest.mark.parametrize("cfg", [1, 5, 6])
+@pytest.mark.parametrize("cfg", [1, 5, 6, 7])
 def test_output_is_wellformed_opencl(cfg):
     b = _batch(cfg, 60, max_len=900)
     out, oo, st = oracle.decompile_batch(b.text, b.offsets)
@@ -249,3 +249,118 @@ def test_parse_errors(mut):
     r = oracle.decompile(txt)
     assert r.status == [2]
     assert "not decompiled" in r.text
+
+
+# ---- the type fixed point's sweep limit ("Data type recovery"; the paper gives no limit) ----
+# A kernel whose every node is typed by its operation (no bitwise operation, select or
+# type-keeping shift whose type comes from its operands, no join) has nothing to solve:
+# the first sweep changes nothing, so even a limit of one sweep leaves it decompiled.
+NO_OPERAND_TYPED = """.kernel plain_store
+  .config
+    .dims x
+    .cws 64, 1, 1
+    .sgprsnum 16
+    .vgprsnum 8
+    .floatmode 0xc0
+    .useargs
+    .priority 0
+    .arg _.global_offset_0, "size_t", long
+    .arg _.global_offset_1, "size_t", long
+    .arg _.global_offset_2, "size_t", long
+    .arg _.printf_buffer, "size_t", void*, global, , rdonly
+    .arg _.vqueue_pointer, "size_t", long
+    .arg _.aqlwrap_pointer, "size_t", long
+    .arg out, "uint*", uint*, global,
+    .arg n, "uint", uint
+  .text
+    s_load_dwordx2 s[8:9], s[4:5], 0x30
+    s_load_dword s10, s[4:5], 0x38
+    s_waitcnt lgkmcnt(0)
+    v_mov_b32 v2, s8
+    v_mov_b32 v3, s9
+    v_add_u32 v1, s10, v0
+    global_store_dword v[2:3], v1, off
+    s_endpgm
+"""
+
+
+def _with_sweep_limit(n, texts):
+    oracle.set_type_sweep_limit(n)
+    try:
+        return [oracle.decompile(t) for t in texts]
+    finally:
+        oracle.set_type_sweep_limit(0)
+
+
+def test_sweep_limit_caps_kernels_that_still_change():
+    """At a limit of one sweep, a kernel whose first sweep still raises a type (most generated
+    kernels: their reached bitwise operations take the type of their operands) is capped: status
+    3 and the not-decompiled text under the kernel's signature; a kernel whose first sweep
+    changes nothing is printed as without a limit; the default limit caps nothing."""
+    b = gcngen.generate(1, 6)
+    texts = [b.kernel(i) for i in range(6)] + [NO_OPERAND_TYPED, gold("listing3_copy.s")]
+    base = [oracle.decompile(t) for t in texts]
+    assert all(r.worst != 3 for r in base)
+    capped = _with_sweep_limit(1, texts)
+    assert sum(r.status == [3] for r in capped[:6]) >= 3
+    for r, full in zip(capped, base):
+        if r.status == [3]:
+            head = full.text.split("\n")[0]
+            assert r.text == head + "\n{\n    /* not decompiled: fixed-point limit */\n}\n"
+        else:
+            assert r.text == full.text and r.status == full.status
+    assert [r.status for r in capped[6:]] == [[0], [0]]
+
+
+def test_sweep_limit_is_monotone_and_bounded_by_the_lattice_height():
+    """A kernel capped at limit L is capped at every smaller limit; it is never capped at
+    2 * (nodes + joins) + 1 sweeps, since every sweep that changes something raises one of
+    them and each can rise at most twice (bottom, a type, top)."""
+    b = gcngen.generate(gcngen.preset(1, w_if=0, w_ifelse=0, w_loop=1), 4, seed=gcngen.SEED_BASE + 41)
+    for i in range(4):
+        t = b.kernel(i)
+        capped = [r.worst == 3 for r in (_with_sweep_limit(L, [t])[0] for L in range(1, 9))]
+        first_ok = capped.index(False) if False in capped else None
+        assert first_ok is not None and all(capped[:first_ok]) and not any(capped[first_ok:])
+        n_nodes = 4 * len(t.split(b"\n"))
+        assert _with_sweep_limit(2 * n_nodes + 1, [t])[0].worst != 3
+
+
+# ---- "The body extraction": FLAT instructions and the double-suffix V_MUL_HI family ----------
+def test_flat_and_mul_hi_golden():
+    """flat_load/flat_store through a buffer address are that buffer's elements, like the GLOBAL
+    instructions; v_mul_hi_u32_u24 / v_mul_hi_i32_i24 are the high half of the 24-bit products,
+    typed by their first suffix (uint / int).  The expected text is derived by hand."""
+    r = oracle.decompile(gold("flat_mulhi.s"))
+    assert r.status == [0]
+    assert r.text == gold("flat_mulhi.cl")
+
+
+def test_brute_force_flat_and_mul_hi_golden():
+    """The golden kernel and its text compute the same buffers on full-range operands, and three
+    planted mistakes fail: no 24-bit mask, no sign extension, and the low half instead."""
+    asm, good = gold("flat_mulhi.s"), gold("flat_mulhi.cl")
+    for seed in range(3):
+        assert brute.check(asm, good, seed=seed, wide=True) is None
+    planted = [good.replace("(var0 & 16777215u)", "var0", 1),
+               good.replace("((int)(var0 << 8) >> 8)", "(int)var0", 1),
+               good.replace("(uint)mul_hi(", "(uint)mul24(", 1).replace(
+                   "mul24(((int)(8388609u << 8) >> 8), ((int)(var0 << 8) >> 8))", "mul24(8388609u, var0)", 1)]
+    for bad in planted:
+        assert bad != good
+        assert brute.check(asm, bad, seed=0, wide=True) is not None
+
+
+def test_brute_force_flat_and_mul_hi_preset():
+    """Generated kernels with FLAT accesses and high multiplies (preset 7): the decompiled text
+    computes the assembly's buffers on full-range operands."""
+    b = _batch(7, 30, max_len=400, cws0=8, cws1=4)
+    seen = {"flat_load": 0, "flat_store": 0, "v_mul_hi_u32_u24": 0, "v_mul_hi_i32_i24": 0}
+    for i in range(len(b)):
+        txt = b.kernel(i).decode()
+        for k in seen:
+            seen[k] += txt.count(k)
+        r = oracle.decompile(txt)
+        assert r.status == [0]
+        assert brute.check(txt, r.text, seed=i, wide=True) is None, f"kernel {i}"
+    assert all(seen.values()), seen
