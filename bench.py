@@ -1,20 +1,30 @@
 #!/usr/bin/env python3
 """Throughput benchmark: GCN instructions decompiled per second on GB300.
 
-One step decompiles the whole workload batch (every stage S1..S13 of the
-method) through the C ABI.  Default workload: 10,000 seeded synthetic kernels
-with log-uniform lengths 50..2000 (the plain-method-at-scale configuration),
-one kernel per file, text resident in HBM when the timed region starts
-(`value`).  `e2e` measures the same through the job service's host-buffer
-entry points (submit_batch, given the whole batch as one buffer and its
-offsets, and fetch_batch), host<->device copies inside the timed region.
-`per_kernel` times the plain form (one pipeline run per kernel) on a sample of
-the same kernels; `serve` drives the job service with open-loop Poisson
-arrivals at 1k, 10k and 100k requests/s and reports p50/p99 latency.
+Default workload: the large batch, 1,000,000 seeded synthetic kernels with
+log-uniform lengths 50..2000 (about 5.46e8 instructions and 20 GB of text),
+decompiled in chunks of 100,000 kernels, one pipeline pass (every stage
+S1..S13 of the method) per chunk.  One step is one pass over all chunks.
+
+* ``value``: instructions per second with every chunk's text already in HBM
+  when the timed region starts (gcn_decomp_run_device), timed with CUDA events;
+  the chunks are spread over several handles, each with its own stream and
+  host thread, so that the passes of different chunks overlap on the device.
+* ``e2e``: the same stream through the job service's host-buffer entry points
+  (gcn_decomp_submit_batch with the packed texts of each piece, then
+  gcn_decomp_fetch_batch), host->device and device->host copies inside the
+  timed region; the service's worker lanes overlap the copies of one batch
+  with the passes of others.
+* ``roofline``: the longest kernel of a pass, timed alone (one pass over all
+  chunks on one stream) by the library's CUDA events around that kernel.
+* extras: the 10,000-kernel batch in one pass (``batch``), the plain form, one
+  pipeline run per kernel (``per_kernel``), the large-CFG workload
+  (``large_cfg``), and the job service under open-loop Poisson arrivals at 1k,
+  10k and 100k requests/s (``serve``, p50/p99 latency).
 
 --impl reference times the CPU oracle (single-threaded) on bounded samples of
 the same workload, the comparison arm.  Multi-GPU (torchrun): every rank
-decompiles its own kernels (weak scaling); there is no collective.
+decompiles its own slice of the stream (weak scaling); there is no collective.
 """
 import argparse
 import json
@@ -23,6 +33,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -37,15 +48,41 @@ import gcngen  # noqa: E402
 WORKLOADS = {
     # name: (preset, kernels)
     "config1": (1, 10_000),
-    "config2": (2, 1_000_000),  # streamed in chunks (large_batch)
+    "config2": (2, 1_000_000),  # streamed in chunks
     "config3": (3, 64),
     "select": (5, 10_000),  # the batch mix with ternaries (v_cndmask_b32)
     "sysval": (6, 10_000),  # the batch mix with dispatch-packet system values and scalar bit fields
+    "flatmulhi": (7, 10_000),  # the batch mix with FLAT accesses and double-suffix high multiplies
 }
+METRIC = "GCN instrs decompiled/sec"
+# the library's event timing of single kernels (gcn_decomp_stage_times names)
+KERNEL_TIMINGS = ("k_line_scan (S1)", "k_decode (S4)", "k_nodes (S7)", "k_node_fwd (S9-S10)",
+                  "k_node_cache (S9-S10)", "k_items (S13 print)")
 
 
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def rank_first(rank, per_rank):
+    """First kernel of a rank's slice of the seeded stream: every rank decompiles its own
+    `per_rank` consecutive kernels (weak scaling), so the slices are disjoint and together are
+    the first world * per_rank kernels of the stream."""
+    return rank * per_rank
+
+
+def max_over_ranks(torch, value, device):
+    """The largest of every rank's value (the job's time is its slowest rank's); the value
+    itself with one rank.  The only collective of the benchmark: there is no data exchange."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def tuning_file():
+    return TUNING if os.path.exists(TUNING) else None
 
 
 def measured_peaks():
@@ -120,7 +157,8 @@ def make_workload(name, rank, kernels=None):
     if kernels:
         n = kernels
     params = gcngen.preset(cfg)
-    batch = gcngen.generate(params, n, seed=gcngen.SEED_BASE + cfg, first=rank * n)
+    batch = gcngen.generate(params, n, seed=gcngen.SEED_BASE + cfg, first=rank_first(rank, n),
+                            threads=os.cpu_count() or 4)
     return cfg, batch
 
 
@@ -144,7 +182,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cfg, batch = make_workload(args.workload, 0, args.kernels)
+    # a prefix of the same seeded stream: the oracle never gets past it within the bounded sample
+    name = args.workload
+    cfg, total = WORKLOADS[name]
+    cfg, batch = make_workload(name, 0, min(args.kernels or total, 20_000))
     per_step = 6.0
     for _ in range(args.warmup):
         oracle_rate(batch, 1.0)
@@ -157,12 +198,13 @@ def run_reference(args):
         instrs += ni
         kern += nk
     value = float(statistics.mean(rates))
-    sample = f"{kern} kernels ({instrs} instrs) over {args.steps} steps of ~{per_step:.0f} s, single thread"
+    sample = (f"{kern} kernels ({instrs} instrs) of the first {len(batch)} kernels of the stream, over "
+              f"{args.steps} steps of ~{per_step:.0f} s, single thread")
     line = {
-        "impl": "reference", "metric": "GCN instrs decompiled/sec", "value": value, "unit": "instr/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "instr/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {len(batch)} seeded synthetic kernels (preset {cfg})"},
+        "config": {"workload": f"{name}: {total} seeded synthetic kernels (preset {cfg})"},
         "cpu_baseline": {"value": value, "unit": "instr/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "instr/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -194,6 +236,7 @@ def per_kernel_form(pkg, torch, batch, local, n_sample):
     for i in range(min(n, 8)):
         one(i)
     torch.cuda.synchronize()
+    launches = dec.launches()
     t0 = time.perf_counter()
     for i in range(n):
         one(i)
@@ -202,29 +245,29 @@ def per_kernel_form(pkg, torch, batch, local, n_sample):
     dec.close()
     ni = int(batch.ninstr[:n].sum())
     return {"value": ni / dt, "unit": "instr/s", "kernels": n, "instrs": ni, "ms_per_kernel": dt * 1e3 / n,
-            "form": "one pipeline run per kernel, text in HBM"}
+            "launches_per_kernel": launches, "form": "one pipeline run per kernel, text in HBM",
+            "kernels_from": "the first kernels of the 10,000-kernel batch"}
 
 
-def serve(pkg, local, rates, n_pool=1000, max_requests=20000, max_seconds=5.0, budget=20 << 30):
+def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0, budget=20 << 30):
     """Open-loop Poisson arrivals of single-kernel requests (lengths 100..50,000,
     the batch mix) through submit_batch / poll / fetch_batch; latency is from
-    the scheduled arrival to the job's finish time."""
-    import threading
-
+    the scheduled arrival to the job's finish time.  Each rate runs for
+    min_seconds of arrivals or min_requests requests, whichever is fewer
+    requests: 10 s at 1k/s and 10k/s, 100,000 requests (1 s) at 100k/s."""
     params = gcngen.preset(4)
     pool = gcngen.generate(params, n_pool, seed=gcngen.SEED_BASE + 4, threads=os.cpu_count() or 4)
     texts = [pool.kernel(i) for i in range(n_pool)]
     ninstr = pool.ninstr.astype(np.int64)
     out = {"budget_bytes": budget, "pool": f"{n_pool} seeded requests (lengths 100..50000), cycled",
            "latency": "scheduled arrival -> job finished (CLOCK_MONOTONIC)", "rates": []}
-    with pkg.Decompiler(local, mem_budget_bytes=budget,
-                        tuning_file=TUNING if os.path.exists(TUNING) else None) as dec:
+    with pkg.Decompiler(local, mem_budget_bytes=budget, tuning_file=tuning_file()) as dec:
         ids = dec.submit_batch(texts)
         raw, offs, _ = dec.fetch_batch_raw(ids)
         ref = [raw[offs[i]:offs[i + 1]].tobytes() for i in range(n_pool)]
         for rate in rates:
             rng = np.random.default_rng(2107078090 + rate)
-            n = int(min(max_requests, rate * max_seconds))
+            n = int(min(min_requests, rate * min_seconds))
             arr = np.cumsum(rng.exponential(1.0 / rate, n))
             which = rng.integers(0, n_pool, n)
             id_to_req = {}
@@ -288,85 +331,11 @@ def serve(pkg, local, rates, n_pool=1000, max_requests=20000, max_seconds=5.0, b
             served = int(ninstr[which].sum())
             span = (done_ns.max() - arr_ns[0]) / 1e9
             out["rates"].append({
-                "rate_rps": rate, "requests": n, "offered_instr_s": float(rate * ninstr[which].mean()),
+                "rate_rps": rate, "requests": n, "arrival_window_s": float(arr[-1]),
+                "offered_instr_s": float(rate * ninstr[which].mean()),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "throughput_instr_s": served / span, "mismatches": mism[0]})
     return out
-
-
-# the library's event timing of the statement-printing kernel alone (not a stage)
-KERNEL_TIMING = "k_items (S13 print)"
-# ncu counters of one k_items launch (4,000 kernels of the batch distribution)
-K_ITEMS_TRAFFIC = {"instrs": 2201608, "bytes": 0.579754240e9 + 0.252110336e9}
-
-
-def large_batch(args, pkg, torch, rank, world, local):
-    """The 1,000,000-kernel stream (the batch distribution), decompiled in chunks of
-    --chunk kernels: each chunk is generated and copied to HBM outside the timed
-    region, then one pipeline pass decompiles it; value = all instructions / the
-    summed CUDA-event time of the passes.  A sample of every chunk is checked
-    against the oracle."""
-    import oracle
-
-    cfg, total = WORKLOADS["config2"]
-    total = args.kernels or total
-    chunk = min(args.chunk, total)
-    params = gcngen.preset(cfg)
-    dec = pkg.Decompiler(local, tuning_file=TUNING if os.path.exists(TUNING) else None)
-    stream = torch.cuda.current_stream()
-    ms_total, instr_total, bytes_total, kern_ms, parity = 0.0, 0, 0, 0.0, {"checked": 0, "mismatches": 0}
-    first0 = rank * total
-    warm = False
-    with Clocks(local) as clk:
-        for c0 in range(0, total, chunk):
-            n = min(chunk, total - c0)
-            b = gcngen.generate(params, n, seed=gcngen.SEED_BASE + cfg, first=first0 + c0,
-                                threads=os.cpu_count() or 4)
-            d_text = torch.from_numpy(b.text).to(f"cuda:{local}")
-            d_off = torch.from_numpy(b.offsets.view(np.int64)).to(f"cuda:{local}")
-            if not warm:  # grow the workspace once
-                for _ in range(max(args.warmup, 3)):
-                    dec.run_device(d_text.data_ptr(), int(b.text.nbytes), d_off.data_ptr(), n, stream.cuda_stream)
-                warm = True
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            dec.run_device(d_text.data_ptr(), int(b.text.nbytes), d_off.data_ptr(), n, stream.cuda_stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            dec.result_device()
-            ms_total += e0.elapsed_time(e1)
-            kern_ms += dec.stage_times().get(KERNEL_TIMING, 0.0)
-            instr_total += int(b.total_instr)
-            bytes_total += int(b.text.nbytes)
-            if rank == 0:
-                k = min(20, n)
-                texts, sts = dec.result_copy(0, k)
-                for f in range(k):
-                    want = oracle.decompile(b.kernel(f))
-                    parity["checked"] += 1
-                    parity["mismatches"] += int(texts[f] != want.text or sts[f] != want.worst)
-            del d_text, d_off, b
-    if world > 1:
-        t = torch.tensor([ms_total], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = instr_total * world / (ms_total / 1e3)
-    if rank == 0:
-        line = {
-            "metric": "GCN instrs decompiled/sec", "value": value, "unit": "instr/s", "n_gpus": world,
-            "steps": (total + chunk - 1) // chunk, "warmup": max(args.warmup, 3),
-            "ms_per_step": ms_total / ((total + chunk - 1) // chunk), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"config2: {total} seeded synthetic kernels (preset {cfg}) in chunks of {chunk}, "
-                                   f"{instr_total} instrs, {bytes_total} text bytes per GPU",
-                       "kernels": total, "chunk": chunk, "instrs": instr_total, "text_bytes": bytes_total,
-                       "l2": "every chunk's text exceeds L2; no flush",
-                       "form": "batched: one pipeline pass per chunk, text in HBM"},
-            "kernel_ms_total": kern_ms, "e2e": None, "clocks": clk.summary(), "parity": parity,
-        }
-        print(json.dumps(line), flush=True)
-    dec.close()
 
 
 def algorithmic_bytes(st):
@@ -380,19 +349,400 @@ def algorithmic_bytes(st):
     }
 
 
+def check_parity(dec, batch, files):
+    """Byte-exact comparison of files of the handle's last device-resident run with the oracle."""
+    import oracle
+
+    bad = 0
+    for f in files:
+        texts, sts = dec.result_copy(f, f + 1)
+        want = oracle.decompile(batch.kernel(f))
+        bad += int(texts[0] != want.text or sts[0] != want.worst)
+    return len(files), bad
+
+
+def device_batch(torch, batch, local):
+    d_text = torch.from_numpy(batch.text).to(f"cuda:{local}")
+    d_off = torch.from_numpy(batch.offsets.view(np.int64)).to(f"cuda:{local}")
+    return d_text, d_off
+
+
+def single_batch_value(pkg, torch, dec, batch, local, steps, warmup, check=50):
+    """One pipeline pass over a whole batch per step, text in HBM: instr/s, ms per pass, parity."""
+    d_text, d_off = device_batch(torch, batch, local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dec.run_device(d_text.data_ptr(), int(batch.text.nbytes), d_off.data_ptr(), len(batch), stream.cuda_stream)
+
+    for _ in range(max(warmup, 1)):
+        step()
+    dec.result_device()
+    n = len(batch)
+    checked, bad = check_parity(dec, batch, sorted(set(int(x) for x in np.linspace(0, n - 1, min(check, n)))))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": batch.total_instr / (ms / 1e3), "unit": "instr/s", "ms_per_pass": ms,
+            "kernels": n, "instrs": batch.total_instr, "text_bytes": int(batch.text.nbytes),
+            "parity": {"checked": checked, "mismatches": bad}}
+
+
+def e2e_stream(pkg, dec, chunks, piece, window):
+    """The stream through the job service: a submitting thread hands the packed
+    texts of `piece` kernels at a time to gcn_decomp_submit_batch while at most
+    `window` pieces are unfetched; a fetching thread takes each piece's results
+    with gcn_decomp_fetch_batch (waiting for them).  Returns wall seconds and
+    bytes copied each way."""
+    import queue
+
+    q = queue.Queue(maxsize=window)
+    d2h = [0]
+    err = []
+
+    def fetcher():
+        try:
+            while True:
+                ids = q.get()
+                if ids is None:
+                    break
+                raw, offs, st = dec.fetch_batch_raw(ids)
+                d2h[0] += len(raw) + 12 * len(ids)
+        except Exception as e:  # noqa: BLE001 - reported by the caller
+            err.append(e)
+
+    th = threading.Thread(target=fetcher)
+    t0 = time.perf_counter()
+    th.start()
+    h2d = 0
+    for b in chunks:
+        n = len(b)
+        for p0 in range(0, n, piece):
+            p1 = min(p0 + piece, n)
+            ids = []
+            while len(ids) < p1 - p0:
+                got = dec.submit_packed(b.text, b.offsets[p0 + len(ids):p1 + 1])
+                if not got:
+                    time.sleep(0.0005)
+                ids += got
+            h2d += int(b.offsets[p1] - b.offsets[p0]) + 8 * (p1 - p0 + 1)
+            q.put(ids)
+            if err:
+                break
+    q.put(None)
+    th.join()
+    if err:
+        raise err[0]
+    return time.perf_counter() - t0, h2d, d2h[0]
+
+
+def stream_main(args, pkg, torch, rank, world, local):
+    """The default measurement: the 1,000,000-kernel stream in chunks."""
+    cfg, total = WORKLOADS["config2"]
+    total = args.kernels or total
+    chunk = min(args.chunk, total)
+    params = gcngen.preset(cfg)
+    first0 = rank_first(rank, total)
+    threads = os.cpu_count() or 4
+    t_gen = time.perf_counter()
+    chunks = [gcngen.generate(params, min(chunk, total - c0), seed=gcngen.SEED_BASE + cfg, first=first0 + c0,
+                              threads=threads) for c0 in range(0, total, chunk)]
+    t_gen = time.perf_counter() - t_gen
+    instr_total = sum(b.total_instr for b in chunks)
+    bytes_total = sum(int(b.text.nbytes) for b in chunks)
+    dev = [device_batch(torch, b, local) for b in chunks]
+    S = max(1, args.streams)
+    decs = [pkg.Decompiler(local, tuning_file=tuning_file()) for _ in range(S)]
+    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream(device=local) for _ in range(S - 1)]
+
+    def run_chunk(h, c):
+        d_text, d_off = dev[c]
+        decs[h].run_device(d_text.data_ptr(), int(chunks[c].text.nbytes), d_off.data_ptr(), len(chunks[c]),
+                           streams[h].cuda_stream)
+
+    def steps_over_handles(nsteps):
+        """nsteps passes over every chunk; chunk c goes to handle c % S, each handle driven by its own
+        host thread (the library releases the interpreter lock while it runs)."""
+        errs = []
+
+        def drive(h):
+            try:
+                with torch.cuda.stream(streams[h]):
+                    for _ in range(nsteps):
+                        for c in range(h, len(chunks), S):
+                            run_chunk(h, c)
+            except Exception as e:  # noqa: BLE001
+                errs.append(e)
+
+        ths = [threading.Thread(target=drive, args=(h,)) for h in range(S)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        if errs:
+            raise errs[0]
+
+    # warm-up: grows every handle's workspace to the largest chunk
+    steps_over_handles(max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    # parity on every chunk (outside the timed region) and the pass statistics
+    stats_sum = {k: 0 for k in ("text_bytes", "out_bytes", "instrs", "pblocks", "lblocks", "kernels")}
+    parity = {"checked": 0, "mismatches": 0}
+    launches_per_step = 0
+    for c, b in enumerate(chunks):
+        run_chunk(0, c)
+        decs[0].result_device()
+        st = decs[0].run_stats()
+        st["text_bytes"] = int(b.text.nbytes)
+        for k in stats_sum:
+            stats_sum[k] += st[k]
+        launches_per_step += decs[0].launches()
+        if rank == 0:
+            n = len(b)
+            files = sorted(set(int(x) for x in np.linspace(0, n - 1, min(args.check, n))))
+            k_, bad = check_parity(decs[0], b, files)
+            parity["checked"] += k_
+            parity["mismatches"] += bad
+    torch.cuda.synchronize()
+    for d in decs:
+        d.stage_totals(reset=True)
+
+    # the timed region: K passes over every chunk, text in HBM
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    main = streams[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(main)
+        for s in streams[1:]:
+            s.wait_event(e0)
+        steps_over_handles(args.steps)
+        for s in streams[1:]:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            main.wait_event(ev)
+        e1.record(main)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(torch, ms, f"cuda:{local}")
+    value = instr_total * world / (ms / 1e3)
+    # stage and kernel times summed over the timed passes of every handle (overlapping on the device)
+    timed_stage_ms = {}
+    timed_runs = 0
+    for d in decs:
+        tot, runs = d.stage_totals(reset=True)
+        timed_runs += runs
+        for k, v in tot.items():
+            timed_stage_ms[k] = timed_stage_ms.get(k, 0.0) + v / args.steps
+
+    # the longest kernels timed alone: one pass over every chunk on one stream
+    for c in range(len(chunks)):
+        run_chunk(0, c)
+    alone, _ = decs[0].stage_totals(reset=True)
+    for d in decs[1:]:
+        d.close()
+    decs = decs[:1]
+    torch.cuda.synchronize()
+
+    # end to end through the job service (host buffers)
+    e2e = None
+    if args.e2e_steps > 0:
+        with pkg.Decompiler(local, tuning_file=tuning_file()) as jd:
+            e2e_stream(pkg, jd, chunks[:1], args.piece, args.window)  # warm-up: pinned slabs, engines
+            runs = [e2e_stream(pkg, jd, chunks, args.piece, args.window) for _ in range(args.e2e_steps)]
+        secs = statistics.median(r[0] for r in runs)
+        secs = max_over_ranks(torch, secs, f"cuda:{local}")
+        e2e = {"value": instr_total * world / secs, "unit": "instr/s", "h2d_bytes_per_step": runs[-1][1],
+               "d2h_bytes_per_step": runs[-1][2], "ms_per_step": secs * 1e3,
+               "path": "gcn_decomp_submit_batch (packed host texts, pieces of "
+                       f"{args.piece} kernels, at most {args.window} pieces unfetched) + gcn_decomp_fetch_batch",
+               "copies_declared": True}
+
+    peaks, src = measured_peaks()
+    ab = algorithmic_bytes(stats_sum)
+    bytes_per_step = ab["text_in"] + ab["text_out"] + ab["ir"]
+    stage_alone = {k: v for k, v in alone.items() if k not in KERNEL_TIMINGS}
+    kern_alone = {k: alone.get(k, 0.0) for k in KERNEL_TIMINGS}
+    dom = max(kern_alone, key=kern_alone.get)
+    dom_ms = kern_alone[dom]
+    achieved = bytes_per_step / (dom_ms / 1e3) / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": f"{dom}: the longest kernel of a pass",
+        "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+        "peak_source": src, "bytes_per_instr": bytes_per_step / instr_total,
+        "kernel_ms_per_step": dom_ms,
+        "timing": "CUDA events around each launch inside the library, summed over one pass of every chunk on "
+                  "one stream (kernel timed alone)",
+        "traffic": None,
+        "traffic_note": "DRAM bytes of this kernel: profiles/ (ncu captures on a smaller batch of the same "
+                        "distribution); not re-taken for this run",
+        "path_frac": bytes_per_step / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+        "path_note": "the whole pass: algorithmic bytes / ms_per_step against the same peak",
+        "kernels_ms_per_step_alone": kern_alone,
+    }
+
+    extras = {}
+    cpu = None
+    if rank == 0 and not args.no_extras:
+        c1cfg, c1 = make_workload("config1", 0)
+        extras["batch"] = dict(single_batch_value(pkg, torch, decs[0], c1, local, 10, 3),
+                               workload=f"config1: 10,000 seeded synthetic kernels (preset {c1cfg}) in one pass")
+        if args.per_kernel > 0:
+            extras["per_kernel"] = per_kernel_form(pkg, torch, c1, local, args.per_kernel)
+        c3cfg, c3 = make_workload("config3", 0)
+        extras["large_cfg"] = dict(single_batch_value(pkg, torch, decs[0], c3, local, 3, 1, check=2),
+                                   workload=f"config3: 64 seeded synthetic kernels of 200,000 instrs (preset {c3cfg})")
+        del c3
+        if not args.no_serve:
+            decs[0].close()
+            decs = []
+            extras["serve"] = serve(pkg, local, [1000, 10000, 100000])
+    if rank == 0 and not args.no_cpu_baseline:
+        r, ni, nk, dt = oracle_rate(chunks[0], 12.0)
+        cpu = {"value": r, "unit": "instr/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {nk} kernels of the stream ({ni} instrs, {dt:.1f} s), single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "instr/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"config2: {total} seeded synthetic kernels (preset {cfg}) per GPU in chunks of "
+                                   f"{chunk}, {instr_total} instrs, {bytes_total} text bytes",
+                       "kernels": total, "chunk": chunk, "instrs": instr_total, "text_bytes": bytes_total,
+                       "handles": S,
+                       "l2": "inputs larger than L2 (every chunk's text > 129 MB); no flush between steps",
+                       "form": f"batched: one pipeline pass per chunk, chunks spread over {S} handles "
+                               f"(streams and host threads), text in HBM"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "launches_per_pass": launches_per_step / len(chunks),
+            "clocks": clk.summary(), "parity": parity,
+            "stage_ms_per_step_alone": stage_alone, "stage_ms_per_step_timed": timed_stage_ms,
+            "run_stats_per_step": stats_sum, "generate_s": t_gen,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    for d in decs:
+        d.close()
+
+
+def batch_main(args, pkg, torch, rank, world, local):
+    """A single-batch workload (--workload config1/config3/select/sysval): one pass per step."""
+    cfg, batch = make_workload(args.workload, rank, args.kernels)
+    dec = pkg.Decompiler(local, tuning_file=tuning_file())
+    d_text, d_off = device_batch(torch, batch, local)
+    stream = torch.cuda.current_stream()
+    n_files = len(batch)
+
+    def step():
+        dec.run_device(d_text.data_ptr(), int(batch.text.nbytes), d_off.data_ptr(), n_files, stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    dec.result_device()
+    parity = {"checked": 0, "mismatches": 0}
+    if rank == 0:
+        files = sorted(set(int(x) for x in np.linspace(0, n_files - 1, min(args.check, n_files))))
+        parity["checked"], parity["mismatches"] = check_parity(dec, batch, files)
+    stats = dec.run_stats()
+    stats["text_bytes"] = int(batch.text.nbytes)
+    launches = dec.launches()
+    dec.stage_totals(reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tot, runs = dec.stage_totals(reset=True)
+    per = {k: v / max(runs, 1) for k, v in tot.items()}
+    ms = max_over_ranks(torch, ms, f"cuda:{local}")
+    value = batch.total_instr * world / (ms / 1e3)
+
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e_ms, d2h = [], 0
+        for _ in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ids = dec.submit_packed(batch.text, batch.offsets)
+            raw, offs, sts = dec.fetch_batch_raw(ids)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            d2h = len(raw) + 12 * n_files
+        e2e_ms = e2e_ms[1:]
+        e2e = {"value": batch.total_instr * world / (statistics.median(e2e_ms) / 1e3), "unit": "instr/s",
+               "h2d_bytes_per_step": int(batch.text.nbytes) + 8 * (n_files + 1), "d2h_bytes_per_step": d2h,
+               "ms_per_step": statistics.median(e2e_ms), "copies_declared": True}
+
+    peaks, src = measured_peaks()
+    ab = algorithmic_bytes(stats)
+    bytes_per_pass = ab["text_in"] + ab["text_out"] + ab["ir"]
+    kern = {k: per.get(k, 0.0) for k in KERNEL_TIMINGS}
+    dom = max(kern, key=kern.get)
+    achieved = bytes_per_pass / (kern[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"{dom}: the longest kernel of a pass", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": src,
+                "bytes_per_instr": bytes_per_pass / batch.total_instr, "kernel_ms": kern[dom], "traffic": None,
+                "path_frac": bytes_per_pass / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], "kernels_ms": kern}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, ni, nk, dt = oracle_rate(batch, 12.0)
+        cpu = {"value": r, "unit": "instr/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {nk} kernels of the workload ({ni} instrs, {dt:.1f} s), single thread"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "instr/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {n_files} seeded synthetic kernels (preset {cfg}), "
+                                   f"{batch.total_instr} instrs, {stats['text_bytes']} text bytes per GPU",
+                       "kernels": n_files, "instrs": batch.total_instr, "text_bytes": stats["text_bytes"],
+                       "l2": ("inputs larger than L2 (text > 129 MB); no flush between steps"
+                              if stats["text_bytes"] > 129e6 else
+                              "text smaller than L2 but the IR arrays of a pass exceed it; no flush"),
+                       "form": "batched: one pipeline pass over all kernels per step"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches * args.steps, "clocks": clk.summary(),
+            "stage_ms": {k: v for k, v in per.items() if k not in KERNEL_TIMINGS},
+            "parity": parity, "run_stats": stats,
+        }
+        if args.per_kernel > 0:
+            line["per_kernel"] = per_kernel_form(pkg, torch, batch, local, args.per_kernel)
+        print(json.dumps(line), flush=True)
+    dec.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config1", choices=sorted(WORKLOADS))
-    ap.add_argument("--kernels", type=int, default=None)
-    ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--per-kernel", type=int, default=300, help="kernels timed in the one-run-per-kernel form")
-    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
+    ap.add_argument("--kernels", type=int, default=None, help="kernels per GPU (default: the workload's)")
     ap.add_argument("--chunk", type=int, default=100_000, help="kernels per pass of the config2 stream")
+    ap.add_argument("--streams", type=int, default=1, help="handles (streams, host threads) the chunks spread over")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--piece", type=int, default=8192, help="kernels per submit_batch call of the e2e stream")
+    ap.add_argument("--window", type=int, default=6, help="pieces submitted and not yet fetched in the e2e stream")
+    ap.add_argument("--check", type=int, default=20, help="files per chunk compared with the oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-kernel", type=int, default=2000, help="kernels timed in the one-run-per-kernel form")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch, plain-form, large-CFG and serving lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -407,122 +757,9 @@ def main():
         dist.init_process_group("nccl")
     pkg.build()
     if args.workload == "config2":
-        return large_batch(args, pkg, torch, rank, world, local)
-    cfg, batch = make_workload(args.workload, rank, args.kernels)
-    n_files = len(batch)
-    total_instr = batch.total_instr
-    d_text = torch.from_numpy(batch.text).to(f"cuda:{local}")
-    d_off = torch.from_numpy(batch.offsets.view(np.int64)).to(f"cuda:{local}")
-    dec = pkg.Decompiler(local, tuning_file=TUNING if os.path.exists(TUNING) else None)
-    stream = torch.cuda.current_stream()
-
-    def step():
-        dec.run_device(d_text.data_ptr(), int(batch.text.nbytes), d_off.data_ptr(), n_files, stream.cuda_stream)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    out_ptr, off_ptr, st_ptr, out_bytes = dec.result_device()
-
-    # byte-exact parity on a sample of the benchmarked batch (outside the timed region)
-    parity = {"checked": 0, "mismatches": 0}
-    if rank == 0:
-        import oracle
-
-        n_check = min(200, n_files)
-        texts, statuses = dec.result_copy(0, n_check)
-        for f in range(n_check):
-            want = oracle.decompile(batch.kernel(f))
-            parity["checked"] += 1
-            parity["mismatches"] += int(texts[f] != want.text or statuses[f] != want.worst)
-
-    stats = dec.run_stats()
-    stats["text_bytes"] = int(batch.text.nbytes)
-    launches = dec.launches()
-
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    stage_ms = dec.stage_times()
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = total_instr * world / (ms / 1e3)
-
-    # end to end through the host-buffer API
-    h2d = int(batch.text.nbytes) + 8 * (n_files + 1)
-    e2e_ms = []
-    d2h = 0
-    for _ in range(args.e2e_steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ids = dec.submit_packed(batch.text, batch.offsets)
-        raw, offs, sts = dec.fetch_batch_raw(ids)
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        d2h = len(raw) + 12 * n_files
-    e2e_val = total_instr * world / (statistics.median(e2e_ms) / 1e3) if e2e_ms else None
-
-    plain = per_kernel_form(pkg, torch, batch, local, args.per_kernel) if args.per_kernel > 0 else None
-    served = None
-    if rank == 0 and not args.no_serve:
-        served = serve(pkg, local, [1000, 10000, 100000])
-
-    peaks, src = measured_peaks()
-    ab = algorithmic_bytes(stats)
-    bytes_per_pass = ab["text_in"] + ab["text_out"] + ab["ir"]
-    kern_ms = stage_ms.pop(KERNEL_TIMING, None)
-    dom = max(stage_ms, key=stage_ms.get)
-    roofline = {"bound": "hbm", "kernel": "k_items (S13 statement printing, the longest kernel of a pass)",
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src,
-                "bytes_per_instr": bytes_per_pass / total_instr,
-                "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_items launch on "
-                                  f"{K_ITEMS_TRAFFIC['instrs']} instructions, scaled by instructions "
-                                  f"(profiles/k_items_config1_4000.md)",
-                "dominant_stage": {"name": dom, "ms": stage_ms[dom],
-                                   "achieved": bytes_per_pass / (stage_ms[dom] / 1e3) / 1e9},
-                "path_frac": bytes_per_pass / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
-    if kern_ms:
-        achieved = bytes_per_pass / (kern_ms / 1e3) / 1e9
-        roofline.update({"achieved": achieved, "frac": achieved / peaks["hbm_gbs"], "kernel_ms": kern_ms,
-                         "traffic": K_ITEMS_TRAFFIC["bytes"] / K_ITEMS_TRAFFIC["instrs"] * total_instr})
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        r, ni, nk, dt = oracle_rate(batch, 12.0)
-        cpu = {"value": r, "unit": "instr/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {nk} kernels of the workload ({ni} instrs, {dt:.1f} s), single thread"}
-
-    if rank == 0:
-        line = {
-            "metric": "GCN instrs decompiled/sec", "value": value, "unit": "instr/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {n_files} seeded synthetic kernels (preset {cfg}), "
-                                   f"{total_instr} instrs, {stats['text_bytes']} text bytes per GPU",
-                       "kernels": n_files, "instrs": total_instr, "text_bytes": stats["text_bytes"],
-                       "l2": ("inputs larger than L2 (text > 129 MB); no flush between steps"
-                              if stats["text_bytes"] > 129e6 else
-                              "text smaller than L2 but the IR arrays of a pass exceed it; no flush"),
-                       "form": "batched: one pipeline pass over all kernels per step"},
-            "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "instr/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": statistics.median(e2e_ms) if e2e_ms else None},
-            "per_kernel": plain, "serve": served,
-            "gpu_launches": launches * args.steps, "clocks": clk.summary(), "stage_ms": stage_ms,
-            "parity": parity, "run_stats": stats,
-        }
-        print(json.dumps(line), flush=True)
-    dec.close()
+        stream_main(args, pkg, torch, rank, world, local)
+    else:
+        batch_main(args, pkg, torch, rank, world, local)
     if world > 1:
         torch.distributed.destroy_process_group()
 

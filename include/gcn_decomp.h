@@ -28,6 +28,15 @@
  * others are on the GPU start as soon as a lane frees up, and the batches of
  * different lanes overlap on the device.  A job's result does not depend on
  * which jobs share its batch.
+ *
+ * Which calls follow a passage of the paper: submit_batch, fetch_opencl,
+ * fetch_batch and run_device/result_* carry the operation the paper states
+ * (disassembly in, OpenCL out; Listing 2's split of a file into kernels;
+ * inline assembly for unsupported instructions).  create, destroy, poll,
+ * job_info, fetch_ir, stage_times, stage_totals, run_stats, launches,
+ * line_starts_noalloc and last_error are infrastructure of this library
+ * (handles, serving, parity access, measurement) with no counterpart in the
+ * paper.
  */
 #ifndef GCN_DECOMP_H
 #define GCN_DECOMP_H
@@ -66,7 +75,13 @@ typedef struct {
                                  lanes (worker lanes, 1..8; default 2), batch_mib (text one lane
                                  takes at once; default 64), big_kernel (instructions from which
                                  a kernel is analysed by a thread block instead of a warp;
-                                 default 4096); a malformed file makes create fail (GCN_EINVAL) */
+                                 default 4096); a malformed file makes create fail (GCN_EINVAL).
+                                 Test hooks: fail_alloc_jobs=M makes every workspace allocation
+                                 of a job batch of more than M jobs fail as if cudaMalloc had
+                                 (GCN_ENOMEM inside a lane, which then frees idle memory, retries
+                                 and splits the batch); fixpoint_sweeps=S caps the type fixed
+                                 point at S sweeps (a kernel still changing in sweep S gets
+                                 GCN_ST_FIXPOINT_CAP) */
   uint32_t flags;             /* reserved (0) */
 } gcn_decomp_config;
 
@@ -165,16 +180,30 @@ int gcn_decomp_result_device(gcn_decomp_t *h, const uint8_t **d_out, const uint6
 int gcn_decomp_result_copy(gcn_decomp_t *h, uint64_t f0, uint64_t f1, void *buf, size_t cap, uint64_t *off_out,
                            int32_t *status_out);
 
-/* Per-stage device times of the last run of either form (milliseconds, CUDA
- * events on the run's stream), stage names in *names (static strings): the
- * ten stages S1..S13, then the statement-printing kernel of S13 alone.  Returns the number
+/* Per-stage device times of the last finished run of either form
+ * (milliseconds, CUDA events on the run's stream), stage names in *names
+ * (static strings): the ten stages S1..S13, then six kernels alone (the S1
+ * newline scan, S4 decoding, S7 node building, the two S9-S10 node-cache
+ * passes, S13 statement printing; 0 when a run did not launch one).  A
+ * device-resident run counts as finished once result_device was called or
+ * the next run_device passed its first synchronisation.  Returns the number
  * of stages (<= cap) or a negative code. */
 int gcn_decomp_stage_times(gcn_decomp_t *h, float *ms, const char **names, int cap);
 
+/* The times of gcn_decomp_stage_times summed over every device-resident run
+ * (run_device) since the handle was created or the sums were last reset;
+ * *runs (may be NULL) receives the number of runs summed.  The call waits for
+ * the runs still in flight on the device.  reset != 0 clears the sums after
+ * they are read.  Returns the number of stages (<= cap) or a negative code. */
+int gcn_decomp_stage_totals(gcn_decomp_t *h, double *ms, const char **names, int cap, uint64_t *runs, int reset);
+
 /* Sizes of the last pipeline run (either form): out[0..8] = lines, kernels,
  * instructions, labels, physical blocks, logical blocks, register-state
- * words, output bytes, device bytes held by the engine that ran it.
- * Returns the number of values written (<= cap) or a negative code. */
+ * words, output bytes, device bytes held by the engine that ran it; then two
+ * values of the handle: out[9] = the most device bytes its workspaces have
+ * held at once (never above mem_budget_bytes when that is set), out[10] = job
+ * batches split after an allocation failure.  Returns the number of values
+ * written (<= cap) or a negative code. */
 int gcn_decomp_run_stats(gcn_decomp_t *h, uint64_t *out, int cap);
 
 /* Number of CUDA kernels the library launched for the last pipeline run
@@ -189,7 +218,7 @@ uint64_t gcn_decomp_launches(gcn_decomp_t *h);
  * allowed; a process whose memory pool owns all device memory; a real-time
  * path that must not block on the allocator).  It runs the S1 newline scan of
  * the batch pipeline on a text already in device memory, with its scratch in
- * a fixed 512 KiB array compiled into the library instead of handle memory.
+ * a fixed 256 KiB array compiled into the library instead of handle memory.
  * No handle is needed; nothing is allocated by the CUDA runtime or any
  * library.
  *
@@ -197,13 +226,9 @@ uint64_t gcn_decomp_launches(gcn_decomp_t *h);
  *                        16-byte aligned is faster), at most 1 GiB.
  *  d_line_start[0..line_cap)  device u32, receives the byte offset of every
  *                        line start: [0] = 0, [k] = 1 + offset of the k-th
- *                        '
-' (so a text ending with '
-' yields lines+1
- *                        entries).  Needs line_cap >= 1 + number of '
-'.
- *  d_result[0..2)        device u32: [0] = number of '
-' bytes, [1] = error
+ *                        '\n' (so a text ending with '\n' yields lines+1
+ *                        entries).  Needs line_cap >= 1 + number of '\n'.
+ *  d_result[0..2)        device u32: [0] = number of '\n' bytes, [1] = error
  *                        bits (0 = ok; 4 = line_cap too small, the offsets
  *                        past it were not written; 1 or 2 = a bounded
  *                        device-side wait gave up, the output is invalid).
@@ -215,7 +240,9 @@ uint64_t gcn_decomp_launches(gcn_decomp_t *h);
  * once (that may load the module): make it before any stream capture starts.
  * The scratch is shared by all calls on a device, so calls whose device work
  * could overlap (other streams, other threads) must be serialised by the
- * caller; overlapping calls race and give wrong results.
+ * caller; overlapping calls race and give wrong results.  The cached address
+ * belongs to the device's primary context: do not call this across a
+ * cudaDeviceReset of the device (the cache would point into the old context).
  * Errors: GCN_EINVAL (NULL pointer, line_cap 0), GCN_ENOMEM (text longer
  * than 1 GiB: rejected before anything is queued), GCN_ECUDA. */
 int gcn_decomp_line_starts_noalloc(const uint8_t *d_text, uint64_t text_len, uint32_t *d_line_start,

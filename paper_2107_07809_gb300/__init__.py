@@ -103,6 +103,8 @@ def lib():
             L.gcn_decomp_last_error.restype = ctypes.c_char_p
             L.gcn_decomp_result_copy.argtypes = [vp, u64, u64, vp, sz, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_int32)]
             L.gcn_decomp_run_stats.argtypes = [vp, ctypes.POINTER(u64), i32]
+            L.gcn_decomp_stage_totals.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_char_p), i32, ctypes.POINTER(u64), i32]
             L.gcn_decomp_launches.argtypes = [vp]
             L.gcn_decomp_launches.restype = u64
             L.gcn_decomp_line_starts_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
@@ -267,11 +269,11 @@ class Decompiler:
 
     def run_stats(self) -> dict[str, int]:
         """Sizes of the last run (lines, kernels, instructions, labels, blocks, state words, output and
-        device bytes)."""
-        v = (ctypes.c_uint64 * 9)()
-        n = lib().gcn_decomp_run_stats(self._h, v, 9)
+        device bytes), the handle's peak workspace bytes and its batches split after allocation failures."""
+        v = (ctypes.c_uint64 * 11)()
+        n = lib().gcn_decomp_run_stats(self._h, v, 11)
         keys = ["lines", "kernels", "instrs", "labels", "pblocks", "lblocks", "state_words", "out_bytes",
-                "device_bytes"]
+                "device_bytes", "peak_device_bytes", "splits"]
         return {keys[i]: int(v[i]) for i in range(max(n, 0))}
 
     def launches(self) -> int:
@@ -289,10 +291,21 @@ class Decompiler:
         raw = buf.raw
         return [raw[offs[i]:offs[i + 1]].decode() for i in range(n)], [int(st[i]) for i in range(n)]
 
+    def stage_totals(self, reset: bool = False) -> tuple[dict[str, float], int]:
+        """Stage and kernel times summed over the device-resident runs since the last reset, and the
+        number of runs."""
+        ms = (ctypes.c_double * 32)()
+        nm = (ctypes.c_char_p * 32)()
+        runs = ctypes.c_uint64()
+        n = lib().gcn_decomp_stage_totals(self._h, ms, nm, 32, ctypes.byref(runs), 1 if reset else 0)
+        if n < 0:
+            raise GcnDecompError(n, "gcn_decomp_stage_totals")
+        return {nm[i].decode(): float(ms[i]) for i in range(n)}, int(runs.value)
+
     def stage_times(self) -> dict[str, float]:
-        ms = (ctypes.c_float * 16)()
-        nm = (ctypes.c_char_p * 16)()
-        n = lib().gcn_decomp_stage_times(self._h, ms, nm, 16)
+        ms = (ctypes.c_float * 32)()
+        nm = (ctypes.c_char_p * 32)()
+        n = lib().gcn_decomp_stage_times(self._h, ms, nm, 32)
         return {nm[i].decode(): float(ms[i]) for i in range(max(n, 0))}
 
 

@@ -66,6 +66,9 @@ struct Workspace {
   size_t total = 0;
   uint64_t budget = 0;                         // device bytes all workspaces of a handle may hold (0 = no limit)
   std::atomic<uint64_t>* pool = nullptr;       // bytes held by all workspaces of the handle
+  std::atomic<uint64_t>* peak = nullptr;       // the most *pool has ever been
+  uint32_t fail_jobs = 0;   // test hook: with more jobs than this in the batch, allocations fail (0 = off)
+  uint32_t cur_jobs = 0;    // jobs of the batch being run (0: a device-resident run)
   template <class T>
   T* get(const char* name, size_t n) {
     size_t bytes = std::max<size_t>(n * sizeof(T), 256);
@@ -78,19 +81,35 @@ struct Workspace {
         b.p = nullptr;
         b.cap = 0;
       }
-      size_t want = bytes + bytes / 8;
-      if (budget && pool && *pool + want > budget) {
-        set_err(std::string("memory budget exceeded allocating ") + name);
-        throw GCN_ENOMEM;
+      const uint64_t want = bytes + bytes / 8;
+      // reserve the bytes against the budget before allocating: the lanes of a
+      // handle allocate concurrently, and a separate check and add would let
+      // two of them pass the check together and overshoot the budget
+      if (pool) {
+        uint64_t cur = pool->load();
+        do {
+          if (budget && cur + want > budget) {
+            set_err(std::string("memory budget exceeded allocating ") + name);
+            throw GCN_ENOMEM;
+          }
+        } while (!pool->compare_exchange_weak(cur, cur + want));
+        if (peak) {
+          uint64_t pk = peak->load();
+          while (cur + want > pk && !peak->compare_exchange_weak(pk, cur + want)) {
+          }
+        }
       }
-      if (cudaMalloc(&b.p, want) != cudaSuccess) {
-        cudaGetLastError();
-        set_err(std::string("cudaMalloc failed for ") + name);
+      const bool fake_fail = fail_jobs && cur_jobs > fail_jobs;
+      if (fake_fail || cudaMalloc(&b.p, want) != cudaSuccess) {
+        if (!fake_fail) cudaGetLastError();
+        if (pool) *pool -= want;
+        b.p = nullptr;
+        set_err(std::string(fake_fail ? "allocation refused by the fail_alloc_jobs test hook for "
+                                      : "cudaMalloc failed for ") + name);
         throw GCN_ENOMEM;
       }
       b.cap = want;
       total += want;
-      if (pool) *pool += want;
     }
     return (T*)b.p;
   }
@@ -105,9 +124,28 @@ struct Workspace {
 
 const char* kStageNames[] = {"S1 tokenise", "S2 segment", "S3 config", "S4 decode", "S5 cfg", "S6 logical cfg",
                              "S7-S8 dataflow", "S9-S11 analysis", "S12 regions", "S13 emit",
-                             "k_items (S13 print)"};
+                             // the longest kernels alone (KTimed order)
+                             "k_line_scan (S1)", "k_decode (S4)", "k_nodes (S7)", "k_node_fwd (S9-S10)",
+                             "k_node_cache (S9-S10)", "k_items (S13 print)"};
 constexpr int kStages = 10;
-constexpr int kTimings = kStages + 1;  // the stages, then the emission kernel alone
+constexpr int kTimings = kStages + KT_COUNT;  // the stages, then the timed kernels
+static_assert(sizeof(kStageNames) / sizeof(kStageNames[0]) == kTimings, "one name per timing");
+
+// The events of one pass: stage boundaries, the region reduction's own stream,
+// the timed kernels.  An engine alternates between two sets, so that the times
+// of a pass are read (at the first synchronisation of the next pass) without
+// stalling the device between passes.
+struct PassEvents {
+  cudaEvent_t st[kStages + 1] = {};
+  cudaEvent_t rs[2] = {};
+  KernelTimer kt{};
+  bool pending = false;  // recorded by a finished pass whose times are not yet read
+};
+
+// The type lattice is finite and every sweep of the fixed point that changes
+// something raises a type, so this limit is never reached by a real kernel; a
+// smaller one (the tuning file's fixpoint_sweeps, a test hook) caps kernels.
+constexpr uint32_t kTypeSweeps = 100000;
 
 struct Run {
   bool valid = false;
@@ -121,14 +159,17 @@ struct Run {
 struct Engine {
   Workspace ws;
   Run run;
-  cudaEvent_t ev[kStages + 3] = {};  // stage boundaries, then around the k_items print launch
-  float stage_ms[kTimings] = {0};
+  PassEvents pe[2];
+  int cur = 0;                 // the set of the latest pass
+  float stage_ms[kTimings] = {0};  // the latest pass whose events were read
+  double sum_ms[kTimings] = {0};   // summed over the passes read since the last reset
+  uint64_t sum_runs = 0;
   uint64_t launches = 0;
   uint32_t* h_tot = nullptr;  // pinned counters
   uint32_t big_kernel = 4096;  // size-bucket threshold
+  uint32_t type_sweeps = kTypeSweeps;  // sweep limit of the type fixed point
   SideStream fk{};             // second stream for launches that overlap the main one
   SideStream rs{};             // stream of the region reduction (S12), beside S7-S11
-  cudaEvent_t rs_ev[2] = {};   // around the region reduction
   // job service: the batch whose IR the workspace holds and its unfetched jobs
   uint64_t batch = 0;
   uint32_t live = 0;
@@ -178,6 +219,8 @@ struct Tuning {
   int lanes = 2;                     // worker lanes of the job service
   uint64_t batch_bytes = 64ull << 20;  // text bytes one lane takes at once
   uint32_t big_kernel = 4096;        // kernels of this many instructions or more get a thread block
+  uint32_t fail_alloc_jobs = 0;      // test hook: batches of more jobs fail every workspace allocation
+  uint32_t type_sweeps = kTypeSweeps;  // test hook (fixpoint_sweeps): sweep limit of the type fixed point
 };
 constexpr int kMaxLanes = 8;
 // Job texts are copied once, at submit, into pinned host slabs; a batch whose
@@ -218,6 +261,8 @@ bool read_tuning(const char* path, Tuning* t) {
     if (k == "lanes" && v >= 1 && v <= (unsigned long long)kMaxLanes) t->lanes = (int)v;
     else if (k == "batch_mib" && v >= 1 && v <= 4095) t->batch_bytes = v << 20;
     else if (k == "big_kernel" && v >= 32 && v <= (1ull << 26)) t->big_kernel = (uint32_t)v;
+    else if (k == "fail_alloc_jobs" && v <= (1ull << 31)) t->fail_alloc_jobs = (uint32_t)v;
+    else if (k == "fixpoint_sweeps" && v >= 1 && v <= kTypeSweeps) t->type_sweeps = (uint32_t)v;
     else ok = false;
   }
   fclose(f);
@@ -251,6 +296,8 @@ struct gcn_decomp {
   uint64_t admitted = 0;  // estimated device bytes of admitted, unfetched jobs
   std::vector<Slab> slabs;
   std::atomic<uint64_t> pool{0};
+  std::atomic<uint64_t> pool_peak{0};
+  std::atomic<uint64_t> splits{0};  // batches split after an allocation failure
   // most recent completed pipeline run (either form)
   std::mutex smu;
   float last_ms[kTimings] = {0};
@@ -260,6 +307,32 @@ struct gcn_decomp {
 
 namespace {
 
+// Read the times of the pass recorded in event set `set` (waiting for it) and
+// add them to the engine's sums; a set is read once.
+void fold_times(Engine* E, int set) {
+  PassEvents& p = E->pe[set];
+  if (!p.pending) return;
+  p.pending = false;
+  CK(cudaEventSynchronize(p.st[kStages]));
+  float ms[kTimings] = {0};
+  for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&ms[i], p.st[i], p.st[i + 1]);
+  cudaEventElapsedTime(&ms[8], p.rs[0], p.rs[1]);  // S12 ran on its own stream
+  for (int w = 0; w < KT_COUNT; ++w)
+    if (cudaEventElapsedTime(&ms[kStages + w], p.kt.ev[2 * w], p.kt.ev[2 * w + 1]) != cudaSuccess) ms[kStages + w] = 0;
+  cudaGetLastError();
+  for (int i = 0; i < kTimings; ++i) {
+    E->stage_ms[i] = ms[i];
+    E->sum_ms[i] += ms[i];
+  }
+  ++E->sum_runs;
+}
+
+// points the launchers' kernel timer at a pass's events for the scope of the pass
+struct TimerScope {
+  explicit TimerScope(KernelTimer* t) { kernel_timer() = t; }
+  ~TimerScope() { kernel_timer() = nullptr; }
+};
+
 // the whole pipeline on a device-resident batch
 void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* file_off, uint32_t F,
                   cudaStream_t s) {
@@ -267,6 +340,17 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   Run& R = h->run;
   R.valid = false;
   const uint64_t launches0 = launch_counter();
+  // this pass records into the other event set; the set's previous pass (two
+  // passes ago) is read first, and the last pass's after the first read-back
+  h->cur ^= 1;
+  fold_times(h, h->cur);
+  PassEvents& pe = h->pe[h->cur];
+  cudaEvent_t* ev = pe.st;
+  TimerScope timer_scope(&pe.kt);
+  for (int w = 0; w < KT_COUNT; ++w) {  // a kernel a pass does not launch reads 0 ms
+    CK(cudaEventRecord(pe.kt.ev[2 * w], s));
+    CK(cudaEventRecord(pe.kt.ev[2 * w + 1], s));
+  }
   Batch& b = R.b;
   b = Batch{};
   b.text = text;
@@ -274,6 +358,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.file_off = file_off;
   b.F = F;
   b.big_kernel = h->big_kernel;
+  b.type_sweeps = h->type_sweeps;
   uint32_t* tot = W.get<uint32_t>("totals", 16);
   uint32_t* err = W.get<uint32_t>("err", 4);
   b.err = err;
@@ -283,19 +368,20 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
     CK(cudaMemcpyAsync(h->h_tot, tot, 64, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   };
-  CK(cudaEventRecord(h->ev[0], s));
+  CK(cudaEventRecord(ev[0], s));
   // S1
   uint32_t* line_start = W.get<uint32_t>("line_start", n + 2);
   uint64_t* tstat = W.get<uint64_t>("tile_status", std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)) + 64);
   uint32_t* counters = W.get<uint32_t>("counters", 4);
   launch_line_scan(text, n, line_start, tstat, counters, err, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[1], s));
+  CK(cudaEventRecord(ev[1], s));
   uint32_t L = 0;
   CK(cudaMemcpyAsync(&h->h_tot[8], counters + 1, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   L = h->h_tot[8];
   b.L = L;
+  fold_times(h, h->cur ^ 1);  // the previous pass (complete: read-backs wait for the stream)
   b.line_start = line_start;
   ScanScratch sc{tstat, W.get<uint32_t>("scan_counter", 4)};
   // S2
@@ -334,11 +420,11 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.label_tab = W.get<uint32_t>("label_tab", (size_t)b.label_tab_mask + 1);
   b.cfg_line = W.get<uint32_t>("cfg_line", b.NC + 1);
   if (L) launch_scatter_rows(L, ra, b.instr_line, b.label_line, b.label_instr, b.cfg_line, b.kh, s);
-  CK(cudaEventRecord(h->ev[2], s));
+  CK(cudaEventRecord(ev[2], s));
   // S3
   launch_config(b, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[3], s));
+  CK(cudaEventRecord(ev[3], s));
   // S4 + S5
   b.ikern = W.get<uint32_t>("ikern", b.I + 1);
   b.blen = W.get<uint32_t>("blen", b.I + 1);
@@ -350,14 +436,14 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.pblock_of = W.get<uint32_t>("pblock_of", b.I + 1);
   launch_decode(b, sc, tot, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[4], s));
+  CK(cudaEventRecord(ev[4], s));
   sync_totals();
   b.NPB = h->h_tot[3];
   b.pblocks = W.get<BlockRec>("pblocks", b.NPB + 1);
   uint32_t* blk_kern = W.get<uint32_t>("blk_kern", std::max(b.NPB, b.I) + 1);
   launch_pblocks(b, blk_kern, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[5], s));
+  CK(cudaEventRecord(ev[5], s));
   // S6
   b.ctl = W.get<uint8_t>("ctl", b.I + 1);
   b.sense = W.get<uint8_t>("sense", b.I + 1);
@@ -372,7 +458,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.lterm = W.get<uint32_t>("lterm", b.NLB + 1);
   launch_lblocks(b, blk_kern, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[6], s));
+  CK(cudaEventRecord(ev[6], s));
   // S7 + S8
   DfScratch d{};
   d.kstate = W.get<uint32_t>("kstate", b.K + 1);
@@ -398,10 +484,10 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   uint8_t* cond = W.get<uint8_t>("rg_cond", b.NLB + 1);
   CK(cudaEventRecord(h->rs.fork, s));
   CK(cudaStreamWaitEvent(h->rs.side, h->rs.fork, 0));
-  CK(cudaEventRecord(h->rs_ev[0], h->rs.side));
+  CK(cudaEventRecord(pe.rs[0], h->rs.side));
   launch_regions(b, rwork, rstk, alive, cond, h->rs.side);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->rs_ev[1], h->rs.side));
+  CK(cudaEventRecord(pe.rs[1], h->rs.side));
   CK(cudaEventRecord(h->rs.join, h->rs.side));
   b.NS = h->h_tot[5];
   d.NW = h->h_tot[6];
@@ -422,7 +508,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.nodes = W.get<Node>("nodes", 4ull * b.I + 4);
   launch_df_main(b, d, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[7], s));
+  CK(cudaEventRecord(ev[7], s));
   // S9 - S11
   b.ncls = W.get<uint8_t>("ncls", 4ull * b.I + 4);
   b.nclsk = W.get<uint8_t>("nclsk", 4ull * b.I + 4);
@@ -455,10 +541,10 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
     scv.status = W.get<uint64_t>("tile_status_var", scan_tiles((uint32_t)nvc) + 64);
   launch_analysis(b, wl, bits, nbw, blk_kern, vflag, vpos, scv, h->fk, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[8], s));
+  CK(cudaEventRecord(ev[8], s));
   // S12, launched beside S7-S11, joined here
   CK(cudaStreamWaitEvent(s, h->rs.join, 0));
-  CK(cudaEventRecord(h->ev[9], s));
+  CK(cudaEventRecord(ev[9], s));
   // S13: layout (count, scan, write), item sizes, scan, item text
   b.kout_off = W.get<uint32_t>("kout_off", b.K + 1);
   uint32_t* icnt = W.get<uint32_t>("item_cnt", b.K + 1);
@@ -523,9 +609,9 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.prec = reinterpret_cast<PRec*>(W.get<uint4>("print_rec", 4ull * b.I + 4));
   static_assert(sizeof(uint4) == kPRecBytes, "one uint4 per print record");
   launch_print_records(b, s);
-  CK(cudaEventRecord(h->ev[kStages + 1], s));
+  ktime(KT_ITEMS, 0, s);
   launch_items(b, items, sitem, sub0, prank, plist, NS2, sorder, ilen, ioff, stage, ovl, &tot[13], 0, s);
-  CK(cudaEventRecord(h->ev[kStages + 2], s));
+  ktime(KT_ITEMS, 1, s);
   if (NS2) launch_scan(ilen, ioff, NS2, 0, false, sc2, &tot[11], b.err, s);
   CK(cudaGetLastError());
   sync_totals();
@@ -538,9 +624,10 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   launch_items(b, items, sitem, sub0, prank, plist, novf, ovl, ilen, ioff, nullptr, nullptr, nullptr, 5, s);
   launch_finish(b, ibase, sub0, ioff, total, s);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[10], s));
+  CK(cudaEventRecord(ev[10], s));
   R.out_bytes = total;
   R.valid = true;
+  pe.pending = true;
   h->launches = launch_counter() - launches0;
 }
 
@@ -551,9 +638,7 @@ void finish_run(Engine* h, cudaStream_t s) {
   R.kh.resize(b.K);
   if (b.K) CK(cudaMemcpyAsync(R.kh.data(), b.kh, sizeof(KHdr) * b.K, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&h->stage_ms[i], h->ev[i], h->ev[i + 1]);
-  cudaEventElapsedTime(&h->stage_ms[8], h->rs_ev[0], h->rs_ev[1]);  // S12 ran on its own stream
-  cudaEventElapsedTime(&h->stage_ms[kStages], h->ev[kStages + 1], h->ev[kStages + 2]);
+  fold_times(h, h->cur);
   if (uint32_t e = h->h_tot[15]) {
     set_err("device error flags " + std::to_string(e));
     throw GCN_ECUDA;
@@ -569,31 +654,40 @@ void finish_run(Engine* h, cudaStream_t s) {
 
 void engine_init(gcn_decomp* h, Engine* E) {
   E->big_kernel = h->tune.big_kernel;
+  E->type_sweeps = h->tune.type_sweeps;
   E->ws.budget = h->budget;
   E->ws.pool = &h->pool;
-  for (auto& e : E->ev) CK(cudaEventCreate(&e));
+  E->ws.peak = &h->pool_peak;
+  E->ws.fail_jobs = h->tune.fail_alloc_jobs;
+  for (PassEvents& p : E->pe) {
+    for (auto& e : p.st) CK(cudaEventCreate(&e));
+    for (auto& e : p.rs) CK(cudaEventCreate(&e));
+    for (auto& e : p.kt.ev) CK(cudaEventCreate(&e));
+  }
   for (SideStream* q : {&E->fk, &E->rs}) {
     CK(cudaStreamCreateWithFlags(&q->side, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&q->fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&q->join, cudaEventDisableTiming));
   }
-  for (auto& e : E->rs_ev) CK(cudaEventCreate(&e));
   CK(cudaMallocHost(&E->h_tot, 64));
 }
 
 void engine_free(Engine* E) {
   E->ws.release();
-  for (auto& e : E->ev)
-    if (e) cudaEventDestroy(e);
+  for (PassEvents& p : E->pe) {
+    for (auto& e : p.st)
+      if (e) cudaEventDestroy(e);
+    for (auto& e : p.rs)
+      if (e) cudaEventDestroy(e);
+    for (auto& e : p.kt.ev)
+      if (e) cudaEventDestroy(e);
+    p = PassEvents{};
+  }
   for (SideStream* q : {&E->fk, &E->rs}) {
     if (q->side) cudaStreamDestroy(q->side);
     if (q->fork) cudaEventDestroy(q->fork);
     if (q->join) cudaEventDestroy(q->join);
     *q = SideStream{};
-  }
-  for (auto& e : E->rs_ev) {
-    if (e) cudaEventDestroy(e);
-    e = nullptr;
   }
   if (E->h_tot) cudaFreeHost(E->h_tot);
   E->h_tot = nullptr;
@@ -681,6 +775,7 @@ void run_jobs(gcn_decomp* h, Lane* L, Engine* E, const std::vector<JobRec*>& js)
     for (size_t i = 0; i < n; ++i) memcpy(L->h_in + L->h_off[i], js[i]->in, js[i]->in_len);
     src = L->h_in;
   }
+  E->ws.cur_jobs = (uint32_t)n;
   uint8_t* d_text = E->ws.get<uint8_t>("in_text", N + 16);
   uint64_t* d_off = E->ws.get<uint64_t>("in_off", n + 1);
   if (N) CK(cudaMemcpyAsync(d_text, src, N, cudaMemcpyHostToDevice, s));
@@ -771,6 +866,7 @@ void lane_main(gcn_decomp* h, Lane* L) {
       shrink_pool(h);
       E->ws.release();
       if (shrunk) {
+        h->splits.fetch_add(1);
         const size_t keep = js.size() / 2;
         for (size_t q = js.size(); q-- > keep;) {
           js[q]->state = JOB_PENDING;
@@ -921,6 +1017,7 @@ int gcn_decomp_run_device(gcn_decomp_t* h, const uint8_t* d_text, uint64_t text_
     CK(cudaSetDevice(h->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
     h->direct_stream = s;
+    h->direct.ws.cur_jobs = 0;
     run_pipeline(&h->direct, d_text, text_len, d_file_off, (uint32_t)n_files, s);
     ++h->run_id;
     note_run(h, &h->direct);
@@ -1254,8 +1351,35 @@ uint64_t gcn_decomp_launches(gcn_decomp_t* h) {
 int gcn_decomp_run_stats(gcn_decomp_t* h, uint64_t* out, int cap) {
   if (!h || !out || cap < 0) return GCN_EINVAL;
   std::lock_guard<std::mutex> g(h->smu);
-  int n = cap < 9 ? cap : 9;
-  for (int i = 0; i < n; ++i) out[i] = h->last_stats[i];
+  const uint64_t v[11] = {h->last_stats[0], h->last_stats[1], h->last_stats[2], h->last_stats[3],
+                          h->last_stats[4], h->last_stats[5], h->last_stats[6], h->last_stats[7],
+                          h->last_stats[8], h->pool_peak.load(), h->splits.load()};
+  int n = cap < 11 ? cap : 11;
+  for (int i = 0; i < n; ++i) out[i] = v[i];
+  return n;
+}
+
+int gcn_decomp_stage_totals(gcn_decomp_t* h, double* ms, const char** names, int cap, uint64_t* runs, int reset) {
+  if (!h || cap < 0) return GCN_EINVAL;
+  std::lock_guard<std::mutex> lk(h->dmu);
+  Engine& E = h->direct;
+  try {
+    CK(cudaSetDevice(h->device));
+    fold_times(&E, E.cur ^ 1);  // the older pass first: sums in pass order
+    fold_times(&E, E.cur);
+  } catch (int rc) {
+    return rc;
+  }
+  int n = std::min(cap, kTimings);
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = E.sum_ms[i];
+    if (names) names[i] = kStageNames[i];
+  }
+  if (runs) *runs = E.sum_runs;
+  if (reset) {
+    for (double& x : E.sum_ms) x = 0;
+    E.sum_runs = 0;
+  }
   return n;
 }
 

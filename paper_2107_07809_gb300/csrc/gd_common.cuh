@@ -50,7 +50,11 @@ enum : uint16_t {
   O_BUFFER_LOAD_DWORD = 81, O_BUFFER_STORE_DWORD = 82,
   O_V_CNDMASK_B32 = 83,  // the ternary ("Search for control structures"): vD = vcc ? src1 : src0
   O_S_LSHR_B32 = 84, O_S_BFE_U32 = 85,  // scalar shift right, bit-field extract (get_num_groups, get_work_dim)
-  O_COUNT = 86
+  // FLAT memory instructions ("The body extraction": prefix flat, a VGPR pair holds the address)
+  // and the double-suffix high multiplies (result type, then operand type)
+  O_FLAT_LOAD_DWORD = 86, O_FLAT_LOAD_DWORDX2 = 87, O_FLAT_STORE_DWORD = 88, O_FLAT_STORE_DWORDX2 = 89,
+  O_V_MUL_HI_U32_U24 = 90, O_V_MUL_HI_I32_I24 = 91,
+  O_COUNT = 92
 };
 
 // ---- operand word: tag<<28 | count<<24 | payload -----------------------------------
@@ -77,7 +81,8 @@ static __device__ char c_sig[O_COUNT][12] = {
     "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S",
     "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S",
     "V,c,S,S", "V,c,S,S,c", "V,c,S,S", "V,c,S,S,c", "W,S,W", "W,W,W", "W,W,W", "W,W,W,W",
-    "V,W,o", "W,W,o", "W,V,o", "W,W,o", "V,o,q,s", "V,o,q,s", "V,S,S,c", "s,S,S", "s,S,S"};
+    "V,W,o", "W,W,o", "W,V,o", "W,W,o", "V,o,q,s", "V,o,q,s", "V,S,S,c", "s,S,S", "s,S,S",
+    "V,W", "W,W", "W,V", "W,W", "V,S,S", "V,S,S"};
 __device__ __forceinline__ int sig_count(uint16_t op) {
   const char* s = c_sig[op];
   int n = 0;
@@ -94,6 +99,24 @@ struct __align__(4) InstrRec {
   uint32_t opnd[5];
 };
 static_assert(sizeof(InstrRec) == 32, "InstrRec is 32 bytes");
+
+// global and FLAT accesses are the same access in this dialect (a FLAT address is always formed
+// from a __global buffer argument)
+__host__ __device__ __forceinline__ bool op_store(uint16_t op) {
+  return op == O_GLOBAL_STORE_DWORD || op == O_GLOBAL_STORE_DWORDX2 || op == O_FLAT_STORE_DWORD ||
+         op == O_FLAT_STORE_DWORDX2;
+}
+__host__ __device__ __forceinline__ bool op_gload(uint16_t op) {
+  return op == O_GLOBAL_LOAD_DWORD || op == O_GLOBAL_LOAD_DWORDX2 || op == O_FLAT_LOAD_DWORD ||
+         op == O_FLAT_LOAD_DWORDX2;
+}
+// bytes one load or store moves
+__host__ __device__ __forceinline__ uint32_t op_mem_width(uint16_t op) {
+  return (op == O_GLOBAL_LOAD_DWORDX2 || op == O_GLOBAL_STORE_DWORDX2 || op == O_FLAT_LOAD_DWORDX2 ||
+          op == O_FLAT_STORE_DWORDX2)
+             ? 8u
+             : 4u;
+}
 
 struct BlockRec {
   uint32_t first, end, succ0, succ1;
@@ -128,6 +151,7 @@ struct KHdr {
   uint32_t n_phis;                // used join versions (listed by the reachability walk)
   uint32_t out_len;
   uint32_t root;                  // root region (kernel-relative) or kNone
+  uint32_t capped;                // the type fixed point hit its sweep limit (status FIXPOINT_CAP)
 };
 
 // ---- control kinds of the logical CFG ------------------------------------------------

@@ -13,6 +13,22 @@ inline uint64_t& launch_counter() {
   return c;
 }
 
+// Device-time events around the pipeline's longest kernels, for the per-kernel
+// figures of gcn_decomp_stage_times: the engine running a pass points
+// kernel_timer() at its events (per host thread, like the launch counter).
+enum KTimed : int { KT_LINE_SCAN = 0, KT_DECODE, KT_NODES, KT_NODE_FWD, KT_NODE_CACHE, KT_ITEMS, KT_COUNT };
+struct KernelTimer {
+  cudaEvent_t ev[2 * KT_COUNT];
+};
+inline KernelTimer*& kernel_timer() {
+  thread_local KernelTimer* t = nullptr;
+  return t;
+}
+// edge 0 before the launch, 1 after it
+inline void ktime(int which, int edge, cudaStream_t s) {
+  if (KernelTimer* t = kernel_timer()) cudaEventRecord(t->ev[2 * which + edge], s);
+}
+
 // line kinds and row types
 enum : uint8_t { LK_BLANK = 0, LK_KERNEL = 1, LK_CONFIG = 2, LK_TEXT = 3, LK_LABEL = 4, LK_ROW = 5 };
 enum : uint8_t { RT_NONE = 0, RT_CFG = 1, RT_LABEL = 2, RT_INSTR = 3, RT_KERNEL = 4 };
@@ -37,6 +53,7 @@ struct Batch {
   const uint64_t* file_off;
   uint32_t F, L, K, I, NL, NC;   // files, lines, kernels, instructions, labels, configuration rows
   uint32_t big_kernel;           // size buckets: kernels this long or longer get a thread block
+  uint32_t type_sweeps;          // sweep limit of the type fixed point (a kernel that reaches it is capped)
   uint32_t NPB, NLB;             // physical / logical blocks
   uint64_t NS;                   // block x register state words
   const uint32_t* line_start;

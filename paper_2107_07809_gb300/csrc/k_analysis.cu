@@ -179,10 +179,12 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
     case O_V_ADD_CO_U32: case O_V_SUB_CO_U32: return TY_UINT;
     case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused ? tjoin(st(0), st(1)) : TY_UINT;
     case O_V_LSHLREV_B64: return st(1);
-    case O_GLOBAL_LOAD_DWORD: case O_GLOBAL_LOAD_DWORDX2: {
+    case O_V_MUL_HI_U32_U24: return TY_UINT;
+    case O_V_MUL_HI_I32_I24: return TY_INT;
+    case O_GLOBAL_LOAD_DWORD: case O_GLOBAL_LOAD_DWORDX2: case O_FLAT_LOAD_DWORD: case O_FLAT_LOAD_DWORDX2: {
       Mem m = mem_of(v, id);
       if (m.ok) return v.A[m.arg].elem;
-      return n.op == O_GLOBAL_LOAD_DWORDX2 ? TY_ULONG : TY_UINT;
+      return op_mem_width(n.op) == 8 ? TY_ULONG : TY_UINT;
     }
     case O_S_LOAD_DWORD: return TY_UINT;
     case O_S_LOAD_DWORDX2: case O_S_LOAD_DWORDX4: return TY_ULONG;
@@ -257,8 +259,8 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_co
   T::sync();
   const uint32_t nd = b.dyn_count[k];  // listed by k_types_static
   bool changed = true;
-  int guard = 0;
-  while (changed && guard++ < 100000) {
+  uint32_t sweeps = 0;
+  while (changed && sweeps++ < b.type_sweeps) {
     bool ch = false;
     for (uint32_t q = lane; q < nd; q += TS) {
       const uint32_t id = dyn[q];
@@ -284,7 +286,8 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_co
     T::sync();
     changed = T::any(ch);
   }
-  if (changed && lane == 0) atomicOr(b.err, ERR_CAPACITY);
+  // still changing in the last allowed sweep: this kernel is not decompiled (FIXPOINT_CAP)
+  if (lane == 0) K.capped = changed ? 1u : 0u;
 }
 
 __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses, const uint8_t* fl, uint32_t id) {
@@ -500,8 +503,7 @@ __global__ void __launch_bounds__(128)
   uint32_t a = kNone, x = kTop;
   const Node& n = v.node(id0);
   if (!bad && n.kind == N_OP && (op_gload(n.op) || op_store(n.op))) {
-    uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
-    Mem m = match_addr(v, nsrc(v, n, 0), w);
+    Mem m = match_addr(v, nsrc(v, n, 0), op_mem_width(n.op));
     if (m.ok) {
       a = m.arg;
       x = m.idx;
@@ -515,8 +517,12 @@ void launch_node_cache(Batch& b, cudaStream_t s) {
   if (!b.I) return;
   Batch raw = b;
   raw.ncls = nullptr;
+  ktime(KT_NODE_FWD, 0, s);
   k_node_fwd<<<(b.I + 127) / 128, 128, 0, s>>>(raw, b.nsrcf);
+  ktime(KT_NODE_FWD, 1, s);
+  ktime(KT_NODE_CACHE, 0, s);
   k_node_cache<<<(b.I + 127) / 128, 128, 0, s>>>(raw, b.ncls, b.nclsk, b.nsrcf, b.mem_arg, b.mem_idx);
+  ktime(KT_NODE_CACHE, 1, s);
   ++launch_counter();
   ++launch_counter();
 }

@@ -316,13 +316,12 @@ static __device__ GD_MATCH_INLINE Mem match_addr(const KView& v, uint32_t addr, 
   return m;
 }
 
-__device__ __forceinline__ bool op_store(uint16_t op) { return op == O_GLOBAL_STORE_DWORD || op == O_GLOBAL_STORE_DWORDX2; }
-__device__ __forceinline__ bool op_gload(uint16_t op) { return op == O_GLOBAL_LOAD_DWORD || op == O_GLOBAL_LOAD_DWORDX2; }
 __device__ __forceinline__ bool op_vcmp(uint16_t op) { return op >= O_V_CMP0 && op < O_V_CMP0 + 18; }
 __device__ __forceinline__ bool op_scmp(uint16_t op) { return op >= O_S_CMP0 && op < O_S_CMP0 + 12; }
 __device__ __forceinline__ bool op_wide(uint16_t op) {
   return op == O_S_LOAD_DWORDX2 || op == O_V_CVT_F64_F32 || op == O_V_CVT_F64_I32 || op == O_V_LSHLREV_B64 ||
-         op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2;
+         op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2 ||
+         op == O_FLAT_LOAD_DWORDX2;
 }
 
 __device__ __forceinline__ int node_width(const KView& v, uint32_t id) {
@@ -353,8 +352,7 @@ __device__ __forceinline__ uint8_t tresolve(uint8_t t, int width) {
 __device__ __forceinline__ Mem mem_of(const KView& v, uint32_t id) {
   if (v.marg) return Mem{v.marg[id / 4] != kNone, v.marg[id / 4], v.midx[id / 4]};
   const Node& n = v.node(id);
-  uint32_t w = (n.op == O_GLOBAL_LOAD_DWORDX2 || n.op == O_GLOBAL_STORE_DWORDX2) ? 8 : 4;
-  return match_addr(v, nsrc(v, n, 0), w);
+  return match_addr(v, nsrc(v, n, 0), op_mem_width(n.op));
 }
 
 static __device__ int node_children(const KView& v, uint32_t id, uint32_t* ch) {

@@ -37,7 +37,8 @@ __device__ __forceinline__ bool vcmp(uint16_t op) { return op >= O_V_CMP0 && op 
 __device__ __forceinline__ bool scmp(uint16_t op) { return op >= O_S_CMP0 && op < O_S_CMP0 + 12; }
 __device__ __forceinline__ bool wide_result(uint16_t op) {
   return op == O_S_LOAD_DWORDX2 || op == O_V_CVT_F64_F32 || op == O_V_CVT_F64_I32 || op == O_V_LSHLREV_B64 ||
-         op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2;
+         op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2 ||
+         op == O_FLAT_LOAD_DWORDX2;
 }
 
 // register index of the first register of an operand word (v/s/vcc)
@@ -56,7 +57,8 @@ __device__ int idefs(const Batch& b, const KHdr& K, const RegMap& M, uint32_t i,
   uint32_t base = 4 * i;
   int n = 0;
   switch (r.op) {
-    case O_S_WAITCNT: case O_GLOBAL_STORE_DWORD: case O_GLOBAL_STORE_DWORDX2: return 0;
+    case O_S_WAITCNT: case O_GLOBAL_STORE_DWORD: case O_GLOBAL_STORE_DWORDX2: case O_FLAT_STORE_DWORD:
+    case O_FLAT_STORE_DWORDX2: return 0;
     case O_S_LOAD_DWORD: d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)}; return n;
     case O_S_LOAD_DWORDX4:
       d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_LO)};
@@ -587,7 +589,7 @@ __device__ void build_instr_nodes(const Batch& b, const KHdr& K, NodeCtx& c, Nod
         char sc = sig[2 * q];
         bool dst = (q == 0 && (sc == 'V' || sc == 'W' || sc == 's' || sc == 'p' || sc == 'q' || sc == 'c')) ||
                    (q == 1 && sc == 'c' && (r.op == O_V_ADD_CO_U32 || r.op == O_V_SUB_CO_U32));
-        if (r.op == O_GLOBAL_STORE_DWORD || r.op == O_GLOBAL_STORE_DWORDX2 || scmp(r.op)) dst = false;
+        if (op_store(r.op) || scmp(r.op)) dst = false;
         if (dst || sc == 'o') continue;
         uint32_t slot = 1 + ns;
         if (sc == 'W' || sc == 'p') s[ns] = src64(c, nodes, r.opnd[q], slot);
@@ -758,7 +760,9 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s) {
     ++launch_counter();
   }
   if (b.NLB) {
+    ktime(KT_NODES, 0, s);
     k_nodes<<<(b.NLB + kNodeWarps - 1) / kNodeWarps, 32 * kNodeWarps, 0, s>>>(b, d.rows, d.blk_kern);
+    ktime(KT_NODES, 1, s);
     ++launch_counter();
   }
 }

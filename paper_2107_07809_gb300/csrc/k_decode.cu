@@ -52,6 +52,8 @@ static const OpName kOps[O_COUNT] = {
     {"global_store_dword", "W,V,o"}, {"global_store_dwordx2", "W,W,o"}, {"buffer_load_dword", "V,o,q,s"},
     {"buffer_store_dword", "V,o,q,s"}, {"v_cndmask_b32", "V,S,S,c"}, {"s_lshr_b32", "s,S,S"},
     {"s_bfe_u32", "s,S,S"},
+    {"flat_load_dword", "V,W"}, {"flat_load_dwordx2", "W,W"}, {"flat_store_dword", "W,V"},
+    {"flat_store_dwordx2", "W,W"}, {"v_mul_hi_u32_u24", "V,S,S"}, {"v_mul_hi_i32_i24", "V,S,S"},
 };
 
 constexpr int kHash = 512;
@@ -171,6 +173,7 @@ __global__ void k_config(const __grid_constant__ Batch b) {
   K.nuser = 0;
   K.bad = 0;
   K.partial = 0;
+  K.capped = 0;
   K.nspill = 0;
   K.entry_target = 0;
   K.status = 0;
@@ -346,14 +349,46 @@ __device__ bool sig_ok(char s, uint32_t o) {
   return false;
 }
 
-__global__ void k_decode(const __grid_constant__ Batch b) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b.I) return;
-  uint32_t line = b.instr_line[i];
+// A warp decodes 32 consecutive instructions, one per lane.  Their lines lie
+// close together in the text, so the warp first copies the span they cover
+// into shared memory with coalesced 16-byte loads, and each lane then parses
+// its line from there: the byte-by-byte reads of the parser no longer touch 32
+// different cache lines per warp access.  A line beyond the staged span (a
+// kernel's configuration block between two instructions can make the span
+// long) is parsed straight from global memory.
+constexpr int DEC_THREADS = 256;
+constexpr uint32_t DEC_STAGE = 2048;  // staged text bytes per warp
+
+__global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ Batch b) {
+  __shared__ __align__(16) uint8_t stage[DEC_THREADS / 32][DEC_STAGE];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t w0 = i - lane;  // the warp's first instruction
+  if (w0 >= b.I) return;         // the whole warp
+  const uint32_t wl = b.I - w0 < 32u ? b.I - w0 : 32u;
+  const uint32_t line = lane < wl ? b.instr_line[i] : 0;
+  const uint32_t l_first = __shfl_sync(0xFFFFFFFFu, line, 0), l_last = __shfl_sync(0xFFFFFFFFu, line, wl - 1);
+  const uint64_t a0 = b.line_start[l_first] & ~15ull;
+  const uint64_t s1 = b.line_start[l_last + 1];
+  const uint32_t span = (uint32_t)(s1 - a0 < DEC_STAGE ? s1 - a0 : DEC_STAGE);  // within the text
+  uint8_t* st = stage[threadIdx.x >> 5];
+  if ((reinterpret_cast<uintptr_t>(b.text) & 15u) == 0) {
+    const uint32_t nv = span / 16;
+    for (uint32_t q = lane; q < nv; q += 32)
+      reinterpret_cast<uint4*>(st)[q] = reinterpret_cast<const uint4*>(b.text + a0)[q];
+    for (uint32_t j = nv * 16 + lane; j < span; j += 32) st[j] = b.text[a0 + j];
+  } else {
+    for (uint32_t j = lane; j < span; j += 32) st[j] = b.text[a0 + j];
+  }
+  __syncwarp();
+  if (lane >= wl) return;
   uint32_t k = b.kcnt[line] - 1;
   const KHdr& K = b.kh[k];
-  const uint8_t* p = b.text + b.line_start[line];
-  const uint8_t* e = b.text + b.line_start[line + 1] - 1;
+  const uint64_t ls = b.line_start[line], le = b.line_start[line + 1] - 1;  // the line without its '\n'
+  const bool staged = le <= a0 + span;
+  const uint8_t* lp = staged ? st + (ls - a0) : b.text + ls;  // the line's first byte
+  const uint8_t* p = lp;
+  const uint8_t* e = lp + (le - ls);
   trim(p, e);
   const uint8_t* me = p;
   while (me < e && !is_space(*me)) ++me;
@@ -399,7 +434,7 @@ __global__ void k_decode(const __grid_constant__ Batch b) {
         uint32_t word = 0, lit = 0;
         bool is_lit = false, ok = true;
         if (sig[0] == 'L') {
-          lbl_pos = (uint32_t)(a - b.text);
+          lbl_pos = (uint32_t)(ls + (uint64_t)(a - lp));
           lbl_len = (uint32_t)(s0 - a);
           word = opw(TG_LABEL, 0, 0);
         } else if (!parse_operand(a, s0, &word, &is_lit, &lit)) {
@@ -431,6 +466,12 @@ __global__ void k_decode(const __grid_constant__ Batch b) {
       r.imm = (pay & 0x800000u) ? (pay | 0xFF000000u) : pay;
     }
     if ((r.op == O_BUFFER_LOAD_DWORD || r.op == O_BUFFER_STORE_DWORD) && (r.imm & 3u)) r.flags |= FL_BAD;
+    // a global or FLAT access with a constant byte offset: not folded into the address, so the
+    // instruction stays inline assembly
+    if ((op_gload(r.op) || op_store(r.op)) && r.imm) {
+      r.op = O_UNKNOWN;
+      r.flags |= FL_UNSUPPORTED;
+    }
   }
   if (r.op == O_S_WAITCNT) r.nops = 0;
   for (int q = 0; q < r.nops; ++q) {
@@ -439,7 +480,7 @@ __global__ void k_decode(const __grid_constant__ Batch b) {
     if (tg == TG_SGPR && opay(o) + ocnt(o) > K.sgprs) r.flags |= FL_REGRANGE;
   }
   b.ins[i] = r;
-  b.branch_hash[i] = lbl_len ? fnv1a(b.text + lbl_pos, lbl_len) : 0;
+  b.branch_hash[i] = lbl_len ? fnv1a(lp + (lbl_pos - ls), lbl_len) : 0;
   b.branch_pos[i] = lbl_len ? lbl_pos : kNone;
   b.blen[i] = lbl_len;
   b.ikern[i] = k;
@@ -559,7 +600,9 @@ __global__ void k_pblock_edges(const __grid_constant__ Batch b, const uint32_t* 
 void launch_decode(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
   const int T = 256;
   if (!b.I) return;
-  k_decode<<<(b.I + T - 1) / T, T, 0, s>>>(b);
+  ktime(KT_DECODE, 0, s);
+  k_decode<<<(b.I + DEC_THREADS - 1) / DEC_THREADS, DEC_THREADS, 0, s>>>(b);
+  ktime(KT_DECODE, 1, s);
   ++launch_counter();
   if (b.NL) {
     cudaMemsetAsync(b.label_tab, 0xFF, sizeof(uint32_t) * ((size_t)b.label_tab_mask + 1), s);

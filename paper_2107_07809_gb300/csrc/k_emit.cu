@@ -206,7 +206,7 @@ __device__ __noinline__ void lit64(Wr& w, uint64_t bits, uint8_t want) {
 enum : uint8_t { F_NONE = 0, F_TPL, F_CARRY, F_LOAD4, F_LOAD8, F_BFE };
 constexpr uint8_t kSelf = 0xFE;
 struct Fmt {
-  char tpl[24];
+  char tpl[64];
   uint8_t ty[3];
   uint8_t mask;
   uint8_t kind;
@@ -298,6 +298,14 @@ __device__ const Fmt g_fmt[O_COUNT + 1] = {
     {"(\3 ? \2 : \1)", {kSelf, kSelf, TY_NONE}, 0, F_TPL},
     {"(\1 >> \5)", {TY_UINT, TY_NONE, TY_NONE}, 31, F_TPL},
     {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_BFE},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_LOAD4},  // flat_load_dword
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_LOAD8},  // flat_load_dwordx2
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},   // flat_store_dword (a statement, not a value)
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},   // flat_store_dwordx2
+    // the high half of the 48-bit product of the operands' low 24 bits, zero- / sign-extended:
+    // OpenCL's mul_hi of the operands reduced to 24 bits
+    {"mul_hi((\1 & 16777215u), (\2 & 16777215u))", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"mul_hi(((int)(\1 << 8) >> 8), ((int)(\2 << 8) >> 8))", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
     {"upsample(\2, \1)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
 };
 
@@ -382,8 +390,10 @@ __device__ __noinline__ uint8_t node_expr_type_of(const KView& v, const uint8_t*
     case O_V_CVT_F32_U32: case O_V_CVT_F32_F64: return TY_FLOAT;
     case O_V_CVT_F64_F32: case O_V_CVT_F64_I32: case O_V_ADD_F64: case O_V_MUL_F64: case O_V_FMA_F64: return TY_DOUBLE;
     case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused ? T : TY_UINT;
-    case O_GLOBAL_LOAD_DWORD: return mem_elem_of(v, id, 4);
-    case O_GLOBAL_LOAD_DWORDX2: return mem_elem_of(v, id, 8);
+    case O_GLOBAL_LOAD_DWORD: case O_GLOBAL_LOAD_DWORDX2: case O_FLAT_LOAD_DWORD: case O_FLAT_LOAD_DWORDX2:
+      return mem_elem_of(v, id, op_mem_width(op));
+    case O_V_MUL_HI_U32_U24: return TY_UINT;
+    case O_V_MUL_HI_I32_I24: return TY_INT;
   }
   return T == TY_ULONG ? TY_ULONG : TY_UINT;
 }
@@ -711,7 +721,7 @@ struct Em {
           continue;
         }
         if (n.kind == N_OP && order[q] == 0 && op_store(n.op) && (fl[id] & 1)) {
-          uint32_t width = n.op == O_GLOBAL_STORE_DWORDX2 ? 8 : 4;
+          uint32_t width = op_mem_width(n.op);
           uint8_t elem = mem_elem(n, width);
           w.indent(lvl);
           memref(n, width, 0);
@@ -970,6 +980,9 @@ __global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ sta
   if (K.bad) {
     L.put(IT_FAIL, 0, 0, 0);
     L.put(IT_TAIL, 0, 1, 0);
+  } else if (K.capped) {
+    L.put(IT_FAIL, 0, 1, 0);
+    L.put(IT_TAIL, 0, 1, 0);
   } else if (K.n_lblock && K.root == kNone) {
     L.put(IT_FAIL, 0, 1, 0);
     L.put(IT_TAIL, 0, 1, 0);
@@ -1206,7 +1219,7 @@ __global__ void __launch_bounds__(128, 12)
       w.s(")\n{\n");
       if (kind == IT_FAIL) {
         w.s("    /* not decompiled: ");
-        w.s(K.bad ? "parse error" : "unstructured control flow");
+        w.s(K.bad ? "parse error" : K.capped ? "fixed-point limit" : "unstructured control flow");
         w.s(" */\n}\n");
       }
       break;
@@ -1262,6 +1275,7 @@ __global__ void k_kernel_status(const __grid_constant__ Batch b, const uint32_t*
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad) K.status = ST_PARSE_ERROR;
+  else if (K.capped) K.status = ST_FIXPOINT_CAP;
   else if (K.n_lblock && K.root == kNone) K.status = ST_PARTIAL;
   else K.status = K.partial ? ST_PARTIAL : ST_OK;
   b.kout_off[k] = item_off[sub0[item_base[k]]];

@@ -12,7 +12,7 @@
 // through any library.
 //
 // Scratch: kNaMaxTiles look-back words (8 bytes each) plus one tile counter,
-// 512 KiB in all, enough for texts up to kNaMaxTiles * 16 KiB = 1 GiB.  Longer
+// 256 KiB in all, enough for texts up to kNaMaxTiles * 32 KiB = 1 GiB.  Longer
 // texts are rejected on the host before anything is queued.  The look-back
 // words of the tiles a call uses and the tile counter must start at zero; the
 // call clears them on its stream before the scan kernel.
@@ -31,15 +31,14 @@
 
 #include "../../include/gcn_decomp.h"
 #include "gd_kernels.h"
+#include "k_linescan.cuh"
 
 namespace gd {
 namespace {
 
-constexpr int NA_THREADS = 256;
-constexpr int NA_PER_THREAD = 64;
-constexpr int NA_TILE = NA_THREADS * NA_PER_THREAD;  // 16 KiB of text per block
-constexpr uint32_t kNaMaxTiles = 65536;               // 1 GiB of text
+constexpr uint32_t kNaMaxTiles = 32768;  // look-back words: 1 GiB of text in 32 KiB tiles
 constexpr int kNaMaxDevices = 64;
+static_assert((uint64_t)kNaMaxTiles * LS_TILE == (1ull << 30), "the scratch covers 1 GiB of text");
 
 // [0, kNaMaxTiles): look-back status per tile; [kNaMaxTiles]: tile counter
 static __device__ __align__(256) uint64_t g_na_scratch[kNaMaxTiles + 1];
@@ -47,96 +46,13 @@ static __device__ __align__(256) uint64_t g_na_scratch[kNaMaxTiles + 1];
 std::mutex g_na_mu;
 uint64_t* g_na_ptr[kNaMaxDevices];  // scratch address per device, set once
 
-// The S1 scan with three differences from the batch kernel: the tile counter
-// and look-back words come from the static scratch, a text pointer that is not
-// 16-byte aligned is read with plain loads instead of the bulk copy, and the
-// line-start writes are bounded by the caller's capacity (ERR_CAPACITY when the
-// text has more lines than fit).
-__global__ void __launch_bounds__(NA_THREADS)
-    k_line_scan_static(const uint8_t* __restrict__ text, uint64_t n, int use_bulk, uint32_t* __restrict__ line_start,
-                       uint64_t cap, uint64_t* __restrict__ status, uint32_t* result) {
-  __shared__ __align__(128) uint8_t buf[NA_TILE];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t s_tile, s_prefix, s_warp[32];
-  uint32_t* err = result + 1;
-  uint32_t* counter = reinterpret_cast<uint32_t*>(status + kNaMaxTiles);
-  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * NA_TILE;
-  const uint64_t rem = n > base ? n - base : 0;
-  const uint32_t nbytes = rem < (uint64_t)NA_TILE ? (uint32_t)rem : (uint32_t)NA_TILE;
-  const uint32_t bulk = use_bulk ? (nbytes & ~15u) : 0u;
-  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
-  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
-  if (threadIdx.x == 0 && bulk) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bulk) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(text + base), "r"(bulk), "r"(mb)
-        : "memory");
-  }
-  for (uint32_t j = bulk + threadIdx.x; j < (uint32_t)NA_TILE; j += blockDim.x) buf[j] = j < nbytes ? text[base + j] : 0;
-  __syncthreads();
-  if (bulk) {
-    uint32_t done = 0, spins = 0;
-    while (!done) {
-      asm volatile(
-          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-          : "=r"(done)
-          : "r"(mb)
-          : "memory");
-      if (!done && ++spins > (1u << 22)) {
-        atomicOr(err, ERR_MBAR);
-        break;
-      }
-    }
-  }
-  const uint4* mine = reinterpret_cast<const uint4*>(buf + threadIdx.x * NA_PER_THREAD);
-  uint4 w[4];
-  uint32_t cnt = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    w[k] = mine[k];
-    cnt += __popc(__vcmpeq4(w[k].x, 0x0A0A0A0Au)) + __popc(__vcmpeq4(w[k].y, 0x0A0A0A0Au)) +
-           __popc(__vcmpeq4(w[k].z, 0x0A0A0A0Au)) + __popc(__vcmpeq4(w[k].w, 0x0A0A0A0Au));
-  }
-  cnt >>= 3;
-  uint32_t total;
-  uint32_t incl = block_incl_scan<ScanSum>(cnt, s_warp, &total);
-  if (threadIdx.x < 32) {
-    uint32_t p = lookback<ScanSum>(status, tile, total, err);
-    if (threadIdx.x == 0) {
-      s_prefix = p;
-      if (tile == gridDim.x - 1) result[0] = p + total;  // number of lines
-    }
-  }
-  __syncthreads();
-  uint64_t rank = (uint64_t)s_prefix + incl - cnt;
-  if (tile == 0 && threadIdx.x == 0) line_start[0] = 0;
-  const uint64_t my0 = base + (uint64_t)threadIdx.x * NA_PER_THREAD;
-  bool over = false;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    uint32_t ws[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t m = __vcmpeq4(ws[q], 0x0A0A0A0Au);
-      while (m) {
-        int bit = __ffs(m) - 1;
-        uint32_t byte = (uint32_t)bit >> 3;
-        uint64_t slot = 1 + rank++;
-        if (slot < cap)
-          line_start[slot] = (uint32_t)(my0 + k * 16 + q * 4 + byte + 1);
-        else
-          over = true;
-        m &= ~(0xFFu << (byte * 8));
-      }
-    }
-  }
-  if (over) atomicOr(err, ERR_CAPACITY);
+// The S1 scan of the batch pipeline (the same tile routine), with the tile
+// counter and look-back words in the static scratch and the line-start writes
+// bounded by the caller's capacity (ERR_CAPACITY when the text has more lines
+// than fit).
+__global__ void __launch_bounds__(LS_THREADS) k_line_scan_static(const __grid_constant__ LineScanArgs a) {
+  __shared__ LineScanSmem sm;
+  line_scan_tile(sm, a);
 }
 
 uint64_t* scratch_for_current_device(int* dev_out) {
@@ -174,7 +90,7 @@ extern "C" int gcn_decomp_line_starts_noalloc(const uint8_t* d_text, uint64_t te
     set_api_error("bad argument");
     return GCN_EINVAL;
   }
-  const uint64_t tiles64 = text_len ? (text_len + NA_TILE - 1) / NA_TILE : 1;
+  const uint64_t tiles64 = text_len ? (text_len + LS_TILE - 1) / LS_TILE : 1;
   if (tiles64 > kNaMaxTiles) {
     set_api_error("text longer than the static scratch allows (1 GiB)");
     return GCN_ENOMEM;
@@ -188,9 +104,18 @@ extern "C" int gcn_decomp_line_starts_noalloc(const uint8_t* d_text, uint64_t te
   if (e == cudaSuccess) e = cudaMemsetAsync(scratch + kNaMaxTiles, 0, sizeof(uint64_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_result, 0, 2 * sizeof(uint32_t), s);
   if (e == cudaSuccess) {
-    const int use_bulk = (reinterpret_cast<uintptr_t>(d_text) & 15u) == 0;
-    k_line_scan_static<<<tiles, NA_THREADS, 0, s>>>(d_text, text_len, use_bulk, d_line_start, line_cap, scratch,
-                                                     d_result);
+    LineScanArgs a;
+    a.text = d_text;
+    a.n = text_len;
+    a.use_bulk = (reinterpret_cast<uintptr_t>(d_text) & 15u) == 0;
+    a.line_start = d_line_start;
+    a.cap = line_cap;
+    a.status = scratch;
+    a.counter = reinterpret_cast<uint32_t*>(scratch + kNaMaxTiles);
+    a.ntiles = tiles;
+    a.lines_out = d_result;
+    a.err = d_result + 1;
+    k_line_scan_static<<<tiles, LS_THREADS, 0, s>>>(a);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

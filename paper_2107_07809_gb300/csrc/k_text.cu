@@ -1,107 +1,25 @@
 // k_text.cu — tokenisation and body extraction on the GPU.
 //
-// S1 (line tokenisation): every byte of the batch text is read once.  A tile
-// of 16 KiB is moved into shared memory with one bulk TMA copy
-// (cp.async.bulk + mbarrier), each thread counts the '\n' bytes of 64
-// contiguous bytes, a block scan plus a single-pass decoupled look-back gives
-// each newline its global rank, and the line starts are written.
+// S1 (line tokenisation): every byte of the batch text is read once, a 16 KiB
+// tile per block moved into shared memory by one bulk copy (k_linescan.cuh);
+// a block scan plus a single-pass decoupled look-back (the whole block looking
+// back 256 tiles at a time) gives each newline its global rank, and the line
+// starts are written.
 // S2 (body extraction, Listing 2 of the paper): the row state machine
 // (.kernel / .config / .text) becomes three scans over the rows — the last
 // state marker, the last file start and the running count of .kernel rows —
 // after which every row knows its kernel and its section independently.
 #include "gd_kernels.h"
+#include "k_linescan.cuh"
 
 namespace gd {
 
 // ---------------------------------------------------------------------------
 // S1: newline scan
 // ---------------------------------------------------------------------------
-constexpr int LS_THREADS = 256;
-constexpr int LS_PER_THREAD = 64;
-constexpr int LS_TILE = LS_THREADS * LS_PER_THREAD;
-
-__global__ void __launch_bounds__(LS_THREADS) k_line_scan(const uint8_t* __restrict__ text, uint64_t n, int use_bulk,
-                                                          uint32_t* __restrict__ line_start,
-                                                          uint64_t* __restrict__ status, uint32_t* counters,
-                                                          uint32_t* err) {
-  __shared__ __align__(128) uint8_t buf[LS_TILE];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t s_tile, s_prefix, s_warp[32];
-  if (threadIdx.x == 0) s_tile = atomicAdd(&counters[0], 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * LS_TILE;
-  const uint64_t rem = n > base ? n - base : 0;
-  const uint32_t nbytes = rem < (uint64_t)LS_TILE ? (uint32_t)rem : (uint32_t)LS_TILE;
-  // bulk-copy part: a 16-byte multiple from a 16-byte aligned source (a text
-  // that does not start 16-byte aligned is read with plain loads)
-  const uint32_t bulk = use_bulk ? (nbytes & ~15u) : 0u;
-  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
-  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
-  if (threadIdx.x == 0 && bulk) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bulk) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(text + base), "r"(bulk), "r"(mb)
-        : "memory");
-  }
-  for (uint32_t j = bulk + threadIdx.x; j < (uint32_t)LS_TILE; j += blockDim.x)
-    buf[j] = j < nbytes ? text[base + j] : 0;
-  __syncthreads();
-  if (bulk) {
-    uint32_t done = 0, spins = 0;
-    while (!done) {
-      asm volatile(
-          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-          : "=r"(done)
-          : "r"(mb)
-          : "memory");
-      if (!done && ++spins > (1u << 22)) {
-        atomicOr(err, ERR_MBAR);
-        break;
-      }
-    }
-  }
-  // count newlines in this thread's 64 contiguous bytes
-  const uint4* mine = reinterpret_cast<const uint4*>(buf + threadIdx.x * LS_PER_THREAD);
-  uint4 w[4];
-  uint32_t cnt = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    w[k] = mine[k];
-    cnt += __popc(__vcmpeq4(w[k].x, 0x0A0A0A0Au)) + __popc(__vcmpeq4(w[k].y, 0x0A0A0A0Au)) +
-           __popc(__vcmpeq4(w[k].z, 0x0A0A0A0Au)) + __popc(__vcmpeq4(w[k].w, 0x0A0A0A0Au));
-  }
-  cnt >>= 3;
-  uint32_t total;
-  uint32_t incl = block_incl_scan<ScanSum>(cnt, s_warp, &total);
-  if (threadIdx.x < 32) {
-    uint32_t p = lookback<ScanSum>(status, tile, total, err);
-    if (threadIdx.x == 0) {
-      s_prefix = p;
-      if (tile == gridDim.x - 1) counters[1] = p + total;  // number of lines
-    }
-  }
-  __syncthreads();
-  uint32_t rank = s_prefix + incl - cnt;
-  if (tile == 0 && threadIdx.x == 0) line_start[0] = 0;
-  const uint64_t my0 = base + (uint64_t)threadIdx.x * LS_PER_THREAD;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    uint32_t ws[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t m = __vcmpeq4(ws[q], 0x0A0A0A0Au);
-      while (m) {
-        int bit = __ffs(m) - 1;  // lowest byte first = text order (little endian)
-        uint32_t byte = (uint32_t)bit >> 3;
-        line_start[1 + rank++] = (uint32_t)(my0 + k * 16 + q * 4 + byte + 1);
-        m &= ~(0xFFu << (byte * 8));
-      }
-    }
-  }
+__global__ void __launch_bounds__(LS_THREADS) k_line_scan(const __grid_constant__ LineScanArgs a) {
+  __shared__ LineScanSmem sm;
+  line_scan_tile(sm, a);
 }
 
 void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uint64_t* tile_status,
@@ -110,8 +28,20 @@ void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uin
   if (!tiles) tiles = 1;
   cudaMemsetAsync(tile_status, 0, sizeof(uint64_t) * tiles, s);
   cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), s);
-  const int use_bulk = (reinterpret_cast<uintptr_t>(text) & 15u) == 0;
-  k_line_scan<<<tiles, LS_THREADS, 0, s>>>(text, n, use_bulk, line_start, tile_status, counters, err);
+  LineScanArgs a;
+  a.text = text;
+  a.n = n;
+  a.use_bulk = (reinterpret_cast<uintptr_t>(text) & 15u) == 0;
+  a.line_start = line_start;
+  a.cap = n + 2;  // the array holds n + 2 entries: never more newlines than bytes
+  a.status = tile_status;
+  a.counter = &counters[0];
+  a.ntiles = tiles;
+  a.lines_out = &counters[1];
+  a.err = err;
+  ktime(KT_LINE_SCAN, 0, s);
+  k_line_scan<<<tiles, LS_THREADS, 0, s>>>(a);
+  ktime(KT_LINE_SCAN, 1, s);
   ++launch_counter();
 }
 uint32_t line_scan_tiles(uint64_t n) { return (uint32_t)((n + LS_TILE - 1) / LS_TILE) + 1; }

@@ -48,3 +48,10 @@ def test_noalloc_rejects_on_the_host():
     assert L.gcn_decomp_line_starts_noalloc(fake, 100, fake, 0, fake, None) == pkg.GCN_EINVAL
     assert L.gcn_decomp_line_starts_noalloc(None, 100, fake, 16, fake, None) == pkg.GCN_EINVAL
     assert L.gcn_decomp_line_starts_noalloc(fake, 100, None, 16, fake, None) == pkg.GCN_EINVAL
+
+
+def test_header_comments_are_intact():
+    """No line of the header starts with a stray quote (a '\\n' that became a
+    real line break inside a comment)."""
+    lines = open(os.path.join(ROOT, "include", "gcn_decomp.h")).read().split("\n")
+    assert not [i for i, l in enumerate(lines, 1) if l.startswith("'")]

@@ -54,6 +54,10 @@ def test_ir_parity_sysval_mix(dec):
     _check_ir(dec, _files(6, 150))
 
 
+def test_ir_parity_flat_mulhi_mix(dec):
+    _check_ir(dec, _files(7, 150))
+
+
 def test_ir_parity_multi_kernel_files(dec):
     ks = _files(1, 12, max_len=400)
     files = [b"".join(ks[0:4]), b"leading junk\n" + b"".join(ks[4:9]), ks[9], b"", b"".join(ks[10:12])]
@@ -90,6 +94,31 @@ def test_text_parity_ternary_mix(dec):
 def test_text_parity_sysval_mix(dec):
     """the batch mix with dispatch-packet system values and scalar bit fields in 10% of integer leaves"""
     _check_text(dec, _files(6, 600))
+
+
+def test_text_parity_flat_mulhi_mix(dec):
+    """the batch mix with FLAT loads/stores (30% of accesses) and double-suffix high multiplies
+    (10% of 32-bit integer operations)"""
+    _check_text(dec, _files(7, 600))
+
+
+def test_text_parity_flat_mulhi_edge_cases(dec):
+    """FLAT accesses whose address is not a buffer element (raw pointer arithmetic), a FLAT
+    64-bit access, high multiplies of registers and of two literals"""
+    import os
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    base = open(os.path.join(g, "flat_mulhi.s"), "rb").read()
+    files = [
+        base.replace(b"v_lshlrev_b64 v[4:5], 2, v[2:3]\n    v_mov_b32 v6, s9",
+                     b"v_lshlrev_b64 v[4:5], 3, v[2:3]\n    v_mov_b32 v6, s9"),
+        base.replace(b"v_mul_hi_u32_u24 v8, 0xfedcba, v7", b"v_mul_hi_u32_u24 v8, v7, v7"),
+        base.replace(b"v_mul_hi_i32_i24 v9, 0x800001, v7", b"v_mul_hi_i32_i24 v9, v0, v7"),
+        base.replace(b"flat_store_dword v[4:5], v8", b"flat_store_dwordx2 v[4:5], v[8:9]"),
+        base.replace(b"flat_load_dword v7, v[4:5]", b"global_load_dword v7, v[4:5], off"),
+        base.replace(b"flat_load_dword v7, v[4:5]", b"flat_load_dword v7, v[4:5] offset:8"),
+    ]
+    assert len(set(files)) == len(files)
+    _check_text(dec, files)
 
 
 def test_text_parity_sysval_edge_cases(dec):
