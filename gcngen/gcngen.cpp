@@ -83,6 +83,8 @@ struct gcngen_params {
                                // (flat_load_dword[x2] / flat_store_dword[x2]); 0 = never
   int32_t p_mulhi;             // percent chance that a 32-bit integer operation is a double-suffix
                                // high multiply (v_mul_hi_u32_u24 / v_mul_hi_i32_i24); 0 = never
+  int32_t p_break;             // percent chance that a loop body has an early exit: a uniform
+                               // test that jumps past the loop (break) or to its latch (continue)
 };
 }
 
@@ -789,6 +791,24 @@ struct Gen {
     ins(f("s_mov_b32 s%d, 0", c));
     int l = label();
     put_label(l);
+    // an early exit sits at the top level of the body, outside any divergent region, so that a
+    // scalar branch leaves the loop (or skips to its latch) without touching the exec mask
+    const bool early = P.p_break > 0 && rng.chance(P.p_break);
+    if (early) {
+      block(depth + 1, share(stop, rng.range(8, 25)), 1);
+      const bool brk = rng.chance(50);
+      if (rng.chance(50)) ins(f("s_cmp_eq_u32 s%d, %s", c, I(rng.range(0, trip)).s().c_str()));
+      else ins(f("s_cmp_gt_u32 s%d, %s", s_n, I(rng.range(0, 40)).s().c_str()));
+      const int lx = label();
+      ins(f("s_cbranch_scc1 %s", lname(lx).c_str()));
+      block(depth + 1, share(stop, rng.range(8, 25)), 1);
+      if (!brk) put_label(lx);  // continue: to the latch
+      ins(f("s_add_u32 s%d, s%d, 1", c, c));
+      ins(f("s_cmp_lt_u32 s%d, %s", c, I(trip).s().c_str()));
+      ins(f("s_cbranch_scc1 %s", lname(l).c_str()));
+      if (brk) put_label(lx);  // break: past the loop
+      return;
+    }
     block(depth + 1, share(stop, rng.range(15, 45)), 1);
     ins(f("s_add_u32 s%d, s%d, 1", c, c));
     ins(f("s_cmp_lt_u32 s%d, %s", c, I(trip).s().c_str()));
@@ -996,7 +1016,9 @@ gcngen_params preset(int cfg) {
       p.p_mulhi = 10;
       break;
     case 8:  // mixed uniform and divergent nesting: divergent if / if-else (forms 1-3), uniform
-             // if / if-else and loops interleaved, nesting <= 4
+             // if / if-else and loops interleaved, nesting <= 4; a third of the loops exit early
+             // (break or continue)
+      p.p_break = 35;
       p.min_len = 50;
       p.max_len = 2000;
       p.w_if = 30;

@@ -2183,8 +2183,9 @@ struct Reducer {
   int entry = 0;
   std::vector<std::vector<int>> log;  // merged member lists, in order
   // block-level info for the tail / conditional checks
-  std::vector<char> cond_block;       // block ends with a two-way branch
+  std::vector<char> cond_block;       // block ends with a two-way branch (not counting a cut break edge)
   std::vector<std::vector<int>> bsucc;
+  std::vector<int> brk_latch;         // per block: the latch of the loop it breaks out of, or -1
 
   int head(int r) const { return reg[r].kind == R_BLOCK ? (int)reg[r].block : head(reg[r].ch[0]); }
   int tail(int r) const {
@@ -2311,12 +2312,32 @@ struct Reducer {
     return false;
   }
 
+  // Every break block must print inside the do-while of its own loop: the nearest loop region
+  // above it in the region tree is the loop whose latch the break rule found.  Otherwise the
+  // `break` would leave another loop, and the kernel counts as unstructured.
+  bool breaks_in_place(int root) const {
+    std::vector<int> parent(reg.size(), -1);
+    for (size_t r = 0; r < reg.size(); ++r)
+      for (int c : reg[r].ch) parent[c] = (int)r;
+    for (size_t b = 0; b < brk_latch.size(); ++b) {
+      if (brk_latch[b] < 0 || !is_in_tree(root, (int)b, parent)) continue;
+      int r = parent[b];
+      while (r >= 0 && reg[r].kind != R_LOOP) r = parent[r];
+      if (r < 0 || tail(reg[r].ch.back()) != brk_latch[b]) return false;
+    }
+    return true;
+  }
+  static bool is_in_tree(int root, int x, const std::vector<int>& parent) {
+    while (x >= 0 && x != root) x = parent[x];
+    return x == root;
+  }
+
   // returns the root region, or -1 when the graph does not reduce to one region
   int run() {
     for (;;) {
       int n_alive = 0;
       for (char a : alive) n_alive += a;
-      if (n_alive <= 1) return n_alive == 1 ? entry : -1;
+      if (n_alive <= 1) return n_alive == 1 && breaks_in_place(entry) ? entry : -1;
       std::vector<char> seen(reg.size(), 0);
       std::vector<int> stack{entry};
       bool merged = false;
@@ -2333,6 +2354,38 @@ struct Reducer {
     }
   }
 };
+
+// Early exits from counted loops (a project extension: the paper restores no loops).  A latch
+// is a two-way block with exactly one successor at or before it (the header H, the back edge)
+// and the other after it (the exit E).  A two-way block b that is not a latch breaks out of the
+// loop whose body holds it when one of its successors is that loop's exit and the other stays
+// in the loop; the loop that holds b is the first latch l after b whose header is at or before
+// b (for nested loops laid out in program order, the innermost one).  The edge b -> E is left
+// out of the graph the regions are reduced on, and b prints `if (c) { break; }` after its
+// statements.  A jump to the latch (continue) needs no rule: it is an if.
+std::vector<int> break_latches(const LogicalCfg& L, const std::vector<char>& cond) {
+  const uint32_t n = (uint32_t)L.blocks.size();
+  std::vector<int> hdr(n, -1), out(n, -1);
+  for (uint32_t l = 0; l < n; ++l) {
+    if (!cond[l]) continue;
+    const uint32_t s0 = L.blocks[l].succ0, s1 = L.blocks[l].succ1;
+    if ((s0 <= l) != (s1 <= l)) hdr[l] = (int)(s0 <= l ? s0 : s1);
+  }
+  for (uint32_t b = 0; b < n; ++b) {
+    if (!cond[b] || hdr[b] >= 0) continue;
+    for (uint32_t l = b + 1; l < n; ++l) {
+      if (hdr[l] < 0 || hdr[l] > (int)b) continue;
+      const uint32_t E = L.blocks[l].succ0 == (uint32_t)hdr[l] ? L.blocks[l].succ1 : L.blocks[l].succ0;
+      const uint32_t s0 = L.blocks[b].succ0, s1 = L.blocks[b].succ1;
+      if ((s0 == E) != (s1 == E)) {
+        const uint32_t x = s0 == E ? s1 : s0;
+        if ((int)x >= hdr[l] && x <= l) out[b] = (int)l;
+      }
+      break;  // only the loop that holds b
+    }
+  }
+  return out;
+}
 
 Reducer make_reducer(const Kernel& K, std::vector<char>* reachable) {
   Reducer rd;
@@ -2353,13 +2406,24 @@ Reducer make_reducer(const Kernel& K, std::vector<char>* reachable) {
   rd.alive.assign(nb, 0);
   rd.cond_block.assign(nb, 0);
   rd.bsucc.resize(nb);
+  for (uint32_t b = 0; b < nb; ++b) rd.cond_block[b] = L.ctl[L.term[b]] == C_CBR && L.blocks[b].succ1 != NONE;
+  rd.brk_latch = break_latches(L, rd.cond_block);
   for (uint32_t b = 0; b < nb; ++b) {
     rd.reg[b] = Region{R_BLOCK, {}, b};
-    if (!live[b]) continue;
+    if (!live[b]) { rd.brk_latch[b] = -1; continue; }
     rd.alive[b] = 1;
+    int cut = -1;  // a break edge is not part of the reduced graph
+    if (rd.brk_latch[b] >= 0) {
+      const uint32_t l = (uint32_t)rd.brk_latch[b];
+      const uint32_t h = L.blocks[l].succ0 <= l ? L.blocks[l].succ0 : L.blocks[l].succ1;
+      cut = (int)(L.blocks[l].succ0 == h ? L.blocks[l].succ1 : L.blocks[l].succ0);
+      rd.cond_block[b] = 0;
+    }
     for (uint32_t s : {L.blocks[b].succ0, L.blocks[b].succ1})
-      if (s != NONE) { rd.succ[b].push_back((int)s); rd.bsucc[b].push_back((int)s); }
-    rd.cond_block[b] = L.ctl[L.term[b]] == C_CBR && L.blocks[b].succ1 != NONE;
+      if (s != NONE) {
+        if ((int)s != cut) rd.succ[b].push_back((int)s);
+        rd.bsucc[b].push_back((int)s);
+      }
   }
   for (uint32_t b = 0; b < nb; ++b)
     for (int s : rd.succ[b]) rd.pred[s].insert((int)b);
@@ -2401,7 +2465,19 @@ struct RegionPrinter {
       case R_BLOCK: {
         uint32_t b = R.block;
         em.block_stmts(b, lvl);
-        if (!rd.cond_block[b] && K.lcfg.blocks[b].succ0 != NONE) em.copies(b, K.lcfg.blocks[b].succ0, lvl);
+        if (rd.brk_latch[b] >= 0) {  // an early exit: the join copies of each edge on its own path
+          const uint32_t l = (uint32_t)rd.brk_latch[b];
+          const uint32_t h = K.lcfg.blocks[l].succ0 <= l ? K.lcfg.blocks[l].succ0 : K.lcfg.blocks[l].succ1;
+          const uint32_t E = K.lcfg.blocks[l].succ0 == h ? K.lcfg.blocks[l].succ1 : K.lcfg.blocks[l].succ0;
+          const uint32_t x = K.lcfg.blocks[b].succ0 == E ? K.lcfg.blocks[b].succ1 : K.lcfg.blocks[b].succ0;
+          em.line(lvl, "if (" + cond_to(b, E) + ") {");
+          em.copies(b, E, lvl + 1);
+          em.line(lvl + 1, "break;");
+          em.line(lvl, "}");
+          em.copies(b, x, lvl);
+        } else if (!rd.cond_block[b] && K.lcfg.blocks[b].succ0 != NONE) {
+          em.copies(b, K.lcfg.blocks[b].succ0, lvl);
+        }
         break;
       }
       case R_SEQ:
@@ -2440,11 +2516,18 @@ struct RegionPrinter {
         uint32_t h = (uint32_t)rd.head(R.ch[0]);
         uint32_t t = (uint32_t)rd.tail(R.ch.back());
         uint32_t exitb = K.lcfg.blocks[t].succ0 == h ? K.lcfg.blocks[t].succ1 : K.lcfg.blocks[t].succ0;
+        // With an early exit, the exit block's join versions are also assigned before the
+        // `break`, so the latch's exit copies cannot follow the loop (they would overwrite
+        // those): they go at the end of every iteration, before the loop-carried copies.  They
+        // assign only versions of the exit block, which the loop does not read.
+        bool has_break = false;
+        for (int l : rd.brk_latch) has_break |= l == (int)t;
         em.line(lvl, "do {");
         for (int c : R.ch) emit(c, lvl + 1);
+        if (has_break && exitb != NONE) em.copies(t, exitb, lvl + 1);
         em.copies(t, h, lvl + 1);
         em.line(lvl, "} while (" + cond_to(t, h) + ");");
-        if (exitb != NONE) em.copies(t, exitb, lvl);
+        if (!has_break && exitb != NONE) em.copies(t, exitb, lvl);
         break;
       }
     }

@@ -45,10 +45,12 @@ def random_buffers(prog: gcn_interp.KernelText, seed: int, wide: bool = False):
     return bufs, scal
 
 
-def check(asm_text: str, ocl_text: str, seed: int = 0, groups=(2, 1), wide: bool = False):
-    """Returns None when both executions agree, else a description."""
+def check(asm_text: str, ocl_text: str, seed: int = 0, groups=(2, 1), wide: bool = False, scalars=None):
+    """Returns None when both executions agree, else a description.  `scalars` overrides
+    the seeded values of scalar arguments."""
     prog = gcn_interp.KernelText(asm_text)
     bufs, scal = random_buffers(prog, seed, wide)
+    scal.update(scalars or {})
     b_asm = {k: v.copy() for k, v in bufs.items()}
     b_ocl = {k: v.copy() for k, v in bufs.items()}
     gcn_interp.run_ndrange(asm_text, b_asm, scal, groups=groups, gofs=GOFS)

@@ -62,6 +62,7 @@ class Parser:
     def __init__(self, toks):
         self.t = toks
         self.i = 0
+        self.loops = 0  # do-while bodies being parsed (a break needs one)
 
     def peek(self, k=0):
         return self.t[self.i + k][1] if self.i + k < len(self.t) else None
@@ -147,7 +148,9 @@ class Parser:
         if p == "do":
             self.eat()
             self.eat("{")
+            self.loops += 1
             b = self.block_items()
+            self.loops -= 1
             self.eat("}")
             self.eat("while")
             self.eat("(")
@@ -155,6 +158,12 @@ class Parser:
             self.eat(")")
             self.eat(";")
             return ("do", b, c)
+        if p == "break":
+            if not self.loops:
+                raise ParseError("break outside a loop")
+            self.eat()
+            self.eat(";")
+            return ("break",)
         if p == "__asm__":
             raise ParseError("inline asm")
         lhs = self.unary()
@@ -445,8 +454,14 @@ def call(nm, args, env: Env):
     raise EvalError(f"unknown function {nm}")
 
 
+class _Break(Exception):
+    """`break;`: leaves the innermost do-while."""
+
+
 def run_block(items, env):
     for s in items:
+        if s[0] == "break":
+            raise _Break()
         if s[0] == "assign":
             lhs, rhs = s[1], s[2]
             rty, rv = ev(rhs, env)
@@ -471,7 +486,10 @@ def run_block(items, env):
         elif s[0] == "do":
             n = 0
             while True:
-                run_block(s[1], env)
+                try:
+                    run_block(s[1], env)
+                except _Break:
+                    break
                 n += 1
                 if n > 100000:
                     raise EvalError("loop limit")

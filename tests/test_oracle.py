@@ -172,7 +172,7 @@ def test_join_versions_are_minimal():
     assert used > 0
 
 
-@pytest.mark.parametrize("cfg", [1, 5, 6, 7])
+@pytest.mark.parametrize("cfg", [1, 5, 6, 7, 8])
 def test_output_is_wellformed_opencl(cfg):
     b = _batch(cfg, 60, max_len=900)
     out, oo, st = oracle.decompile_batch(b.text, b.offsets)
@@ -364,3 +364,60 @@ def test_brute_force_flat_and_mul_hi_preset():
         assert r.status == [0]
         assert brute.check(txt, r.text, seed=i, wide=True) is None, f"kernel {i}"
     assert all(seen.values()), seen
+
+
+# ---- early exits from counted loops (loops are a project extension; "Search for control
+# structures" gives the templates they build on) ------------------------------------------------
+@pytest.mark.parametrize("name", ["loop_break", "loop_continue"])
+def test_early_exit_goldens(name):
+    """A uniform test that leaves the loop prints `if (c) { <join copies> break; }` inside the
+    do-while; one that skips to the latch is an if around the rest of the body.  The expected
+    texts are derived by hand."""
+    r = oracle.decompile(gold(name + ".s"))
+    assert r.status == [0]
+    assert r.text == gold(name + ".cl")
+
+
+@pytest.mark.parametrize("name", ["loop_break", "loop_continue"])
+def test_brute_force_early_exit_goldens(name):
+    """The assembly and the text agree for an exit at every iteration (n = 0..3) and none (n = 4)."""
+    for n in range(5):
+        assert brute.check(gold(name + ".s"), gold(name + ".cl"), seed=n, scalars={"n": n}) is None
+
+
+def test_brute_force_catches_misplaced_break_copy():
+    good = gold("loop_break.cl")
+    planted = [good.replace("            var5 = var2;\n", ""),               # the exit value not passed
+               good.replace("        if (var1 == n) {", "        if (var1 != n) {"),  # the test inverted
+               good.replace("            break;\n", "")]                      # no exit at all
+    for bad in planted:
+        assert bad != good
+        assert any(brute.check(gold("loop_break.s"), bad, seed=n, scalars={"n": n}) is not None for n in range(4))
+
+
+def test_exit_from_an_outer_loop_stays_unstructured():
+    """A jump from an inner loop's body to the outer loop's exit would need a two-level break:
+    the rule only cuts an exit of the innermost loop, so the graph does not reduce and the kernel
+    is not decompiled (PARTIAL)."""
+    src = gold("loop_break.s")
+    nested = src.replace("LOOP:\n", "OUTER:\n    s_mov_b32 s13, 0\nLOOP:\n").replace(
+        "    s_cbranch_scc1 LOOP\n", "    s_cbranch_scc1 LOOP\n    s_add_u32 s13, s13, 1\n"
+        "    s_cmp_lt_u32 s13, 3\n    s_cbranch_scc1 OUTER\n")
+    assert nested != src
+    r = oracle.decompile(nested)
+    assert r.status == [1]
+    assert "/* not decompiled: unstructured control flow */" in r.text
+
+
+def test_brute_force_mixed_nesting_and_early_exits():
+    """Preset 8: divergent and uniform ifs of every form nested with loops, a third of the loops
+    with a break or continue; the decompiled text computes the assembly's buffers."""
+    b = _batch(8, 40, max_len=600, cws0=8, cws1=4)
+    breaks = 0
+    for i in range(len(b)):
+        txt = b.kernel(i).decode()
+        r = oracle.decompile(txt)
+        assert r.status == [0]
+        breaks += r.text.count("break;")
+        assert brute.check(txt, r.text, seed=i, scalars={"n": i % 5}) is None, f"kernel {i}"
+    assert breaks > 0
