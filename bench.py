@@ -53,6 +53,7 @@ WORKLOADS = {
     "select": (5, 10_000),  # the batch mix with ternaries (v_cndmask_b32)
     "sysval": (6, 10_000),  # the batch mix with dispatch-packet system values and scalar bit fields
     "flatmulhi": (7, 10_000),  # the batch mix with FLAT accesses and double-suffix high multiplies
+    "mixed": (8, 10_000),  # mixed uniform/divergent nesting, loops with early exits
 }
 METRIC = "GCN instrs decompiled/sec"
 # the library's event timing of single kernels (gcn_decomp_stage_times names)

@@ -477,6 +477,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   // S12 needs the logical CFG and the parse flags only, final once the sizes above are taken:
   // it runs on its own stream beside S7-S11
   b.rg = W.get<uint32_t>("regions", 12ull * kRegionsPerBlock * b.NLB + 24);
+  b.brk = W.get<uint32_t>("break_of", b.NLB + 1);
   // region reduction work: 64 words per block + 128 per kernel (red_work_words)
   uint32_t* rwork = W.get<uint32_t>("rg_work", 64ull * b.NLB + 128ull * b.K + 64);
   uint32_t* rstk = W.get<uint32_t>("rg_stack", (size_t)kStackPerBlock * b.NLB + 4);

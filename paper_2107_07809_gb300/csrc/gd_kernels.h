@@ -124,6 +124,7 @@ struct Batch {
   uint64_t* wl;                  // reachability work lists
   // regions
   uint32_t* rg;                  // region records, 12 words per region
+  uint32_t* brk;                 // NLB: per block, the latch an early exit leaves by, kBrkLatch or kNone
   // emission
   uint32_t* kout_len;            // K (text length of each kernel incl. separator)
   uint32_t* kout_off;            // K (exclusive scan)

@@ -822,7 +822,7 @@ __device__ void print_args(Wr& w, const Batch& b, const KHdr& K, const ArgRec* A
 // writes it
 // ---------------------------------------------------------------------------
 enum : uint32_t { IT_NONE = 0, IT_HEAD, IT_DECLS, IT_BLOCK, IT_COPYSET, IT_IF, IT_ELSE, IT_CLOSE, IT_DO, IT_WHILE,
-                  IT_TAIL, IT_FAIL };
+                  IT_TAIL, IT_FAIL, IT_BREAK };
 // declarations per item: ten lines of at most 22 bytes ("    double var800000;") fit a
 // staging slot, so declaration items are never printed twice
 constexpr uint32_t kDeclChunk = 10;
@@ -929,8 +929,10 @@ __global__ void k_copy_sets(const __grid_constant__ Batch b, const uint32_t* __r
 // kernel's items into its slice of a staging array (size bounded by
 // layout_bound), counting them; a scan places the kernels and a copy compacts.
 // ---------------------------------------------------------------------------
+// items of a kernel: at most 4 per region (fewer than 3 per block) and 4 more per block for
+// an early exit (if, copies, break, close)
 __device__ __forceinline__ uint32_t layout_bound(const KHdr& K) {
-  return 4 + (K.n_vars + kDeclChunk - 1) / kDeclChunk + 4 * kRegionsPerBlock * K.n_lblock;
+  return 4 + (K.n_vars + kDeclChunk - 1) / kDeclChunk + (4 * kRegionsPerBlock + 4) * K.n_lblock;
 }
 
 __global__ void k_layout_bound(const __grid_constant__ Batch b, uint32_t* __restrict__ bound) {
@@ -1015,7 +1017,18 @@ __global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ sta
             L.put(IT_BLOCK, lvl, bl, 0);
             uint32_t term = b.lterm[K.first_lblock + bl];
             bool cb = b.ctl[K.first_instr + term] == C_CBR && B.succ1 != kNone;
-            if (!cb && B.succ0 != kNone) L.copies(bl, B.succ0, lvl);
+            const uint32_t lb = b.brk[K.first_lblock + bl];
+            if (lb != kNone && lb != kBrkLatch) {  // an early exit: the join copies of each edge on its own path
+              const uint32_t lh = BL[lb].succ0 <= lb ? BL[lb].succ0 : BL[lb].succ1;
+              const uint32_t E = latch_exit(BL, lb, lh), xin = B.succ0 == E ? B.succ1 : B.succ0;
+              L.put(IT_IF, lvl, bl, E);
+              L.copies(bl, E, lvl + 1);
+              L.put(IT_BREAK, lvl + 1, 0, 0);
+              L.put(IT_CLOSE, lvl, 0, 0);
+              L.copies(bl, xin, lvl);
+            } else if (!cb && B.succ0 != kNone) {
+              L.copies(bl, B.succ0, lvl);
+            }
             break;
           }
           case R_SEQ:
@@ -1077,9 +1090,14 @@ __global__ void k_layout(const __grid_constant__ Batch b, Item* __restrict__ sta
               for (int q = (int)nch - 1; q >= 0; --q) push(X[RG_CH + q], lvl + 1, 0);
             } else {
               uint32_t exitb = BL[t].succ0 == h ? BL[t].succ1 : BL[t].succ0;
+              // with an early exit the exit block's join versions are assigned before each
+              // `break` too: the latch's exit copies go at the end of every iteration, before
+              // the loop-carried ones (they assign only versions the loop does not read)
+              const bool has_break = b.brk[K.first_lblock + t] == kBrkLatch;
+              if (has_break && exitb != kNone) L.copies(t, exitb, lvl + 1);
               L.copies(t, h, lvl + 1);
               L.put(IT_WHILE, lvl, t, h);
-              if (exitb != kNone) L.copies(t, exitb, lvl);
+              if (!has_break && exitb != kNone) L.copies(t, exitb, lvl);
             }
             break;
           }
@@ -1247,6 +1265,7 @@ __global__ void __launch_bounds__(128, 12)
       break;
     case IT_ELSE: w.indent((int)lvl); w.s("} else {\n"); break;
     case IT_CLOSE: w.indent((int)lvl); w.s("}\n"); break;
+    case IT_BREAK: w.indent((int)lvl); w.s("break;\n"); break;
     case IT_DO: w.indent((int)lvl); w.s("do {\n"); break;
     case IT_WHILE:
       w.indent((int)lvl);

@@ -1,7 +1,8 @@
 // k_region.cu — S12: region graph and structural analysis ("Search for
 // control structures", Fig. 3).  One thread per kernel marks the blocks
-// reached from the entry and runs the reduction of region_red.cuh (the
-// restarting pre-order search, resumed incrementally after each merge).
+// reached from the entry, finds the early exits of loops (a project
+// extension), and runs the reduction of region_red.cuh (the restarting
+// pre-order search, resumed incrementally after each merge).
 #include "gd_kernels.h"
 #include "region_red.cuh"
 
@@ -41,10 +42,18 @@ __global__ void k_regions(const __grid_constant__ Batch b, uint32_t* __restrict_
       }
     }
   }
+  // early exits from loops: find them on the blocks as they are, then take the break blocks'
+  // exit edges out of the graph (they print as `break`)
+  uint32_t* brk = b.brk + base;
+  find_breaks(rd.B, cnd, rd.alive, n, brk);
+  for (uint32_t x = 0; x < n; ++x)
+    if (brk[x] != kNone && brk[x] != kBrkLatch) cnd[x] = 0;
+  rd.brk = brk;
   rd.init(work_all + 128 * (size_t)k + 64 * (size_t)base);  // red_work_words of the kernels before
   bool capacity = false;
-  const uint32_t root = rd.run(&capacity);
+  uint32_t root = rd.run(&capacity);
   if (capacity) atomicOr(b.err, ERR_CAPACITY);
+  if (root != kNone && !rd.breaks_in_place()) root = kNone;  // a break that would leave another loop
   K.root = root;
 }
 

@@ -41,12 +41,50 @@ constexpr int RGW = 12;
 // work words the reducer needs for a kernel of n blocks
 GD_HD inline size_t red_work_words(uint32_t n) { return 64ull * n + 128; }
 
+// Early exits from counted loops (a project extension: the paper restores no loops).  A latch
+// is a two-way block with exactly one successor at or before it (the header, the back edge) and
+// the other after it (the exit).  A two-way block b that is not a latch breaks out of the loop
+// that holds it -- the first latch l after b whose header is at or before b (for nested loops in
+// program order, the innermost) -- when one of its successors is that loop's exit and the other
+// stays in [header, l].  brk[b] = l for such a block; brk[l] = kBrkLatch for a latch with at least
+// one; kNone otherwise.  The reduction leaves the edge b -> exit out.
+constexpr uint32_t kBrkLatch = 0xFFFFFFFEu;
+GD_HD inline uint32_t latch_header(const BlockRec* B, const uint8_t* cond, uint32_t l) {
+  if (!cond[l]) return kNone;
+  const uint32_t s0 = B[l].succ0, s1 = B[l].succ1;
+  if ((s0 <= l) == (s1 <= l)) return kNone;
+  return s0 <= l ? s0 : s1;
+}
+GD_HD inline uint32_t latch_exit(const BlockRec* B, uint32_t l, uint32_t h) {
+  return B[l].succ0 == h ? B[l].succ1 : B[l].succ0;
+}
+// live[x]: block x is reached from the entry (an unreached block breaks out of nothing)
+GD_HD inline void find_breaks(const BlockRec* B, const uint8_t* cond, const uint8_t* live, uint32_t n, uint32_t* brk) {
+  for (uint32_t x = 0; x < n; ++x) brk[x] = kNone;
+  for (uint32_t b = 0; b < n; ++b) {
+    if (!live[b] || !cond[b] || latch_header(B, cond, b) != kNone) continue;
+    for (uint32_t l = b + 1; l < n; ++l) {
+      const uint32_t h = latch_header(B, cond, l);
+      if (h == kNone || h > b) continue;
+      const uint32_t E = latch_exit(B, l, h), s0 = B[b].succ0, s1 = B[b].succ1;
+      if ((s0 == E) != (s1 == E)) {
+        const uint32_t x = s0 == E ? s1 : s0;
+        if (x >= h && x <= l) brk[b] = l;
+      }
+      break;  // only the loop that holds b
+    }
+  }
+  for (uint32_t b = 0; b < n; ++b)
+    if (brk[b] != kNone && brk[b] != kBrkLatch) brk[brk[b]] = kBrkLatch;
+}
+
 struct RedInc {
   // inputs
   uint32_t* rg;         // 3n region records (RGW words each)
   uint8_t* alive;       // 3n
   const BlockRec* B;    // the kernel's logical blocks (succ0/succ1 kernel-relative, kNone = none)
-  const uint8_t* cond;  // block ends with a two-way branch
+  const uint8_t* cond;  // block ends with a two-way branch (not counting a cut edge)
+  const uint32_t* brk = nullptr;  // find_breaks() of the blocks (null: no early exits)
   uint32_t n;
   // state
   uint32_t nreg, entry, nalive;
@@ -334,6 +372,11 @@ struct RedInc {
       ++nalive;
       X[RG_S0] = B[x].succ0;
       X[RG_S1] = B[x].succ1;
+      if (brk && brk[x] != kNone && brk[x] != kBrkLatch) {  // leave the exit edge out
+        const uint32_t l = brk[x], E = latch_exit(B, l, latch_header(B, cond, l));
+        if (X[RG_S0] == E) X[RG_S0] = kNone;
+        else if (X[RG_S1] == E) X[RG_S1] = kNone;
+      }
       if (X[RG_S0] == kNone) {
         X[RG_S0] = X[RG_S1];
         X[RG_S1] = kNone;
@@ -353,6 +396,27 @@ struct RedInc {
     L = 0;
     Q = 0;
     push(entry);
+  }
+
+  // Every break block (brk[b] a latch) must sit inside the do-while of its own loop: the
+  // nearest loop region above it in the tree has that latch as its tail.  Uses mark[] (free
+  // once the reduction is over) for the parents.
+  GD_HD bool breaks_in_place() {
+    uint32_t* parent = mark;
+    for (uint32_t r = 0; r < nreg; ++r) parent[r] = kNone;
+    for (uint32_t r = n; r < nreg; ++r) {
+      const uint32_t* X = R(r);
+      for (uint32_t q = 0; q < X[RG_NCH]; ++q) parent[X[RG_CH + q]] = r;
+    }
+    for (uint32_t b = 0; brk && b < n; ++b) {
+      if (brk[b] == kNone || brk[b] == kBrkLatch) continue;
+      uint32_t r = parent[b];
+      while (r != kNone && R(r)[RG_KIND] != R_LOOP) r = parent[r];
+      if (r == kNone) return false;
+      const uint32_t* X = R(r);
+      if (R(X[RG_CH + X[RG_NCH] - 1])[RG_TAIL] != brk[b]) return false;
+    }
+    return true;
   }
 
   // Reduce until one region is left.  Returns the root region, or kNone when

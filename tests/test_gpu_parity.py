@@ -58,6 +58,10 @@ def test_ir_parity_flat_mulhi_mix(dec):
     _check_ir(dec, _files(7, 150))
 
 
+def test_ir_parity_mixed_nesting(dec):
+    _check_ir(dec, _files(8, 150))
+
+
 def test_ir_parity_multi_kernel_files(dec):
     ks = _files(1, 12, max_len=400)
     files = [b"".join(ks[0:4]), b"leading junk\n" + b"".join(ks[4:9]), ks[9], b"", b"".join(ks[10:12])]
@@ -116,6 +120,34 @@ def test_text_parity_flat_mulhi_edge_cases(dec):
         base.replace(b"flat_store_dword v[4:5], v8", b"flat_store_dwordx2 v[4:5], v[8:9]"),
         base.replace(b"flat_load_dword v7, v[4:5]", b"global_load_dword v7, v[4:5], off"),
         base.replace(b"flat_load_dword v7, v[4:5]", b"flat_load_dword v7, v[4:5] offset:8"),
+    ]
+    assert len(set(files)) == len(files)
+    _check_text(dec, files)
+
+
+def test_text_parity_mixed_nesting_and_early_exits(dec):
+    """divergent if / if-else (three forms), uniform ifs and loops nested to depth 4, a third of
+    the loops with a break or continue"""
+    files = _files(8, 600)
+    _check_text(dec, files)
+    assert sum(oracle.decompile(f).text.count("break;") for f in files[:200]) > 0
+
+
+def test_text_parity_early_exit_edge_cases(dec):
+    """an exit from an inner loop to the outer loop's exit (unstructured), an exit whose other
+    branch leaves the loop too, an exit at the loop's first block, and two exits of one loop"""
+    import os
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    base = open(os.path.join(g, "loop_break.s"), "rb").read()
+    files = [
+        base.replace(b"LOOP:\n", b"OUTER:\n    s_mov_b32 s13, 0\nLOOP:\n").replace(
+            b"    s_cbranch_scc1 LOOP\n", b"    s_cbranch_scc1 LOOP\n    s_add_u32 s13, s13, 1\n"
+            b"    s_cmp_lt_u32 s13, 3\n    s_cbranch_scc1 OUTER\n"),
+        base.replace(b"    s_cbranch_scc1 DONE\n    v_add_u32 v7, v7, 5\n",
+                     b"    s_cbranch_scc1 DONE\n    s_branch DONE\n    v_add_u32 v7, v7, 5\n"),
+        base.replace(b"LOOP:\n    v_add_u32 v7, v7, 3\n", b"LOOP:\n"),
+        base.replace(b"    v_add_u32 v7, v7, 5\n", b"    v_add_u32 v7, v7, 5\n    s_cmp_eq_u32 s12, 2\n"
+                     b"    s_cbranch_scc1 DONE\n    v_add_u32 v7, v7, 1\n"),
     ]
     assert len(set(files)) == len(files)
     _check_text(dec, files)
