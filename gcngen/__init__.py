@@ -20,6 +20,8 @@ Workload presets (``preset(i)``) follow the five synthetic workloads:
      multiplies v_mul_hi_u32_u24 / v_mul_hi_i32_i24 (10% of 32-bit integer operations)
   8  mixed uniform and divergent nesting (divergent if / if-else in all three forms, uniform
      if / if-else, loops; depth <= 4), 35% of loops with an early exit (break or continue)
+  9  the mix of 1 (1-D) with a __local buffer argument and exchanges through it (write the
+     work-item's element, barrier, read a neighbour's) in 15% of top-level statements
 Seeds: ``SEED_BASE + workload index``; kernel k of a stream uses mix(seed, k).
 """
 from __future__ import annotations
@@ -45,7 +47,7 @@ class Params(ctypes.Structure):
         for n in (
             "w_if", "w_ifelse", "w_loop", "w_uif", "p_ctrl", "max_depth", "min_bufs", "max_bufs",
             "vgpr_budget", "sgpr_budget", "spills", "max_locals", "expr_depth", "trip_max", "dims",
-            "cws0", "cws1", "fixed_args", "one_ifelse", "form_mask", "p_select", "p_sysval", "p_flat", "p_mulhi", "p_break",
+            "cws0", "cws1", "fixed_args", "one_ifelse", "form_mask", "p_select", "p_sysval", "p_flat", "p_mulhi", "p_break", "p_lds",
         )
     ]
 

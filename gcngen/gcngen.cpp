@@ -85,6 +85,9 @@ struct gcngen_params {
                                // high multiply (v_mul_hi_u32_u24 / v_mul_hi_i32_i24); 0 = never
   int32_t p_break;             // percent chance that a loop body has an early exit: a uniform
                                // test that jumps past the loop (break) or to its latch (continue)
+  int32_t p_lds;               // percent chance that a top-level statement is an exchange through
+                               // a __local buffer (ds_write_b32, s_barrier, ds_read_b32); 0 = never,
+                               // and above 0 the kernel gets a __local argument and is 1-D
 };
 }
 
@@ -166,6 +169,7 @@ struct Gen {
   bool buf_out[8];
   int s_buf[8];
   int s_n = 0;
+  int s_lds = -1, lds_ty = TI;  // SGPR with the __local buffer's LDS address, its element type
   int vloc = 6, vtop = 6, vmax = 5, smax = 13;
   int label_ctr = 0, spill_next = 0;
   int ifelse_left = 0;
@@ -673,6 +677,44 @@ struct Gen {
     }
   }
 
+  // An exchange through the __local buffer (top level only: every work-item of the group reaches
+  // both barriers): each work-item writes its element, and after the barrier reads a neighbour's,
+  // which becomes a local.  The first barrier keeps this write from overtaking the reads of the
+  // previous exchange.
+  void stmt_lds() {
+    int t = lds_ty;
+    int d = stmt_depth();
+    vtop = vloc + (vloc & 1) + 2;
+    ins("s_barrier");
+    Opd v = vgpr(gen32(t, d));
+    int a = tmp32();
+    ins(f("v_lshlrev_b32 v%d, 2, v0", a));
+    ins(f("v_add_u32 v%d, s%d, v%d", a, s_lds, a));
+    ins(f("ds_write_b32 v%d, %s", a, v.s().c_str()));
+    ins("s_waitcnt lgkmcnt(0)");
+    ins("s_barrier");
+    int j = tmp32();
+    const int c = cws[0];
+    if ((c & (c - 1)) == 0) {
+      ins(f("v_add_u32 v%d, %d, v0", j, rng.range(1, 7)));
+      ins(f("v_and_b32 v%d, %s, v%d", j, I(c - 1).s().c_str(), j));
+    } else {
+      ins(f("v_xor_b32 v%d, 1, v0", j));
+    }
+    ins(f("v_lshlrev_b32 v%d, 2, v%d", j, j));
+    ins(f("v_add_u32 v%d, s%d, v%d", j, s_lds, j));
+    int r = tmp32();
+    ins(f("ds_read_b32 v%d, v%d", r, j));
+    ins("s_waitcnt lgkmcnt(0)");
+    int base = vloc;
+    if (base + 1 + 24 > P.vgpr_budget) return;  // no room for a new local: the value is dropped
+    Local L{t, base, -1};
+    vloc = base + 1;
+    touchv(base);
+    locals.push_back(L);
+    ins(f("v_mov_b32 v%d, v%d", base, r));
+  }
+
   void divergent_cond() { divergent_cond_depth(-1); }
 
   // a comparison into vcc (operand depth d, or a random shallow depth when d < 0)
@@ -703,6 +745,10 @@ struct Gen {
       if (P.one_ifelse && ifelse_left && depth == 0 && ninstr * 5 >= target * 2) {
         ifelse_left = 0;
         stmt_ifelse(depth, stop, 1);
+        continue;
+      }
+      if (s_lds >= 0 && depth == 0 && P.p_lds > 0 && rng.chance(P.p_lds)) {
+        stmt_lds();
         continue;
       }
       if (ctrl && !P.one_ifelse) {
@@ -830,6 +876,7 @@ struct Gen {
       if (target > P.max_len) target = P.max_len;
     }
     dims = P.dims ? P.dims : (rng.chance(50) ? 1 : 2);
+    if (P.p_lds > 0) dims = 1;  // the exchange indexes the buffer by get_local_id(0)
     if (P.cws0) {
       cws[0] = P.cws0;
       cws[1] = dims == 2 ? P.cws1 : 1;
@@ -877,6 +924,15 @@ struct Gen {
       }
     }
     ins(f("s_load_dword s%d, s[4:5], 0x%x", s_n, 0x30 + 8 * nbufs));
+    if (P.p_lds > 0) {  // the __local buffer's LDS address: the low dword of the slot after n
+      s_lds = s_n + 1;
+      touchs(s_lds);
+      int tys[3], nt = 0;
+      for (int q = TI; q <= TF; ++q)
+        if (allowed(q)) tys[nt++] = q;
+      lds_ty = nt ? tys[rng.below(nt)] : TI;
+      ins(f("s_load_dword s%d, s[4:5], 0x%x", s_lds, 0x30 + 8 * (nbufs + 1)));
+    }
     ins("s_waitcnt lgkmcnt(0)");
     for (int d = 0; d < dims; ++d) {
       int g = 6 + d, l = d, dst = 3 + d, o = 10 + 2 * d, c = cws[d];
@@ -940,6 +996,10 @@ struct Gen {
       h += b;
     }
     h += "        .arg n, \"uint\", uint\n";
+    if (s_lds >= 0) {
+      snprintf(b, sizeof b, "        .arg tmp, \"%s*\", %s*, local,\n", kTyName[lds_ty], kTyName[lds_ty]);
+      h += b;
+    }
     h += "    .text\n";
     return h + body;
   }
@@ -1015,6 +1075,11 @@ gcngen_params preset(int cfg) {
       p.p_flat = 30;
       p.p_mulhi = 10;
       break;
+    case 9:  // the batch mix (1-D) with exchanges through a __local buffer in 15% of top-level statements
+      p.min_len = 50;
+      p.max_len = 2000;
+      p.p_lds = 15;
+      break;
     case 8:  // mixed uniform and divergent nesting: divergent if / if-else (forms 1-3), uniform
              // if / if-else and loops interleaved, nesting <= 4; a third of the loops exit early
              // (break or continue)
@@ -1042,9 +1107,9 @@ struct Result {
 
 extern "C" {
 
-// Default knobs of workload `cfg` (0..8).  Returns 0, or -1 for an unknown index.
+// Default knobs of workload `cfg` (0..9).  Returns 0, or -1 for an unknown index.
 int gcngen_preset(int cfg, gcngen_params* out) {
-  if (cfg < 0 || cfg > 8 || !out) return -1;
+  if (cfg < 0 || cfg > 9 || !out) return -1;
   *out = preset(cfg);
   return 0;
 }

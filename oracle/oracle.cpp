@@ -262,7 +262,10 @@ enum Op : uint16_t {
   // address) and the double-suffix V_MUL_HI family (result type, then operand type)
   FLAT_LOAD_DWORD = 86, FLAT_LOAD_DWORDX2 = 87, FLAT_STORE_DWORD = 88, FLAT_STORE_DWORDX2 = 89,
   V_MUL_HI_U32_U24 = 90, V_MUL_HI_I32_I24 = 91,
-  OP_COUNT = 92
+  // "The body extraction": data share operations (prefix "ds") on the LDS, the equivalent of
+  // OpenCL local memory ("The AMD GCN architecture"), and the work-group barrier
+  DS_READ_B32 = 92, DS_READ_B64 = 93, DS_WRITE_B32 = 94, DS_WRITE_B64 = 95, S_BARRIER = 96,
+  OP_COUNT = 97
 };
 
 // comparison codes shared by s_cmp and v_cmp: eq, ne(lg/neq), gt, lt, ge, le
@@ -358,6 +361,11 @@ std::vector<OpInfo> build_table() {
   set(FLAT_STORE_DWORDX2, "flat_store_dwordx2", "W,W");
   set(V_MUL_HI_U32_U24, "v_mul_hi_u32_u24", "V,S,S");
   set(V_MUL_HI_I32_I24, "v_mul_hi_i32_i24", "V,S,S");
+  set(DS_READ_B32, "ds_read_b32", "V,V");
+  set(DS_READ_B64, "ds_read_b64", "W,V");
+  set(DS_WRITE_B32, "ds_write_b32", "V,V");
+  set(DS_WRITE_B64, "ds_write_b64", "V,W");
+  set(S_BARRIER, "s_barrier", "");
   return t;
 }
 
@@ -543,6 +551,7 @@ Decoded decode(const std::vector<std::string>& rows, const Config& cfg) {
       // stays inline assembly
       if (rec.op >= GLOBAL_LOAD_DWORD && rec.op <= GLOBAL_STORE_DWORDX2 && rec.imm) rec.op = OP_UNKNOWN;
       if (rec.op >= FLAT_LOAD_DWORD && rec.op <= FLAT_STORE_DWORDX2 && rec.imm) rec.op = OP_UNKNOWN;
+      if (rec.op >= DS_READ_B32 && rec.op <= DS_WRITE_B64 && rec.imm) rec.op = OP_UNKNOWN;
       if (rec.op == OP_UNKNOWN) rec.flags |= F_UNSUPPORTED;
     }
     if (rec.op == S_WAITCNT) rec.nops = 0;
@@ -857,7 +866,7 @@ std::vector<uint32_t> regs_of(const Regs& R, uint32_t o) {
 bool is64_result(int op) {
   return op == S_LOAD_DWORDX2 || op == V_CVT_F64_F32 || op == V_CVT_F64_I32 || op == V_LSHLREV_B64 ||
          op == V_ADD_F64 || op == V_MUL_F64 || op == V_FMA_F64 || op == GLOBAL_LOAD_DWORDX2 ||
-         op == FLAT_LOAD_DWORDX2;
+         op == FLAT_LOAD_DWORDX2 || op == DS_READ_B64;
 }
 bool is_scmp(int op) { return op >= S_CMP_FIRST && op < S_CMP_FIRST + 12; }
 bool is_vcmp(int op) { return op >= V_CMP_FIRST && op < V_CMP_FIRST + 18; }
@@ -903,7 +912,8 @@ std::vector<Def> defs_of(const Decoded& d, const LogicalCfg& L, const Regs& R, u
       }
       out.push_back({R.vcc(), UNDEF});
       break;
-    case GLOBAL_STORE_DWORD: case GLOBAL_STORE_DWORDX2: case FLAT_STORE_DWORD: case FLAT_STORE_DWORDX2: break;
+    case GLOBAL_STORE_DWORD: case GLOBAL_STORE_DWORDX2: case FLAT_STORE_DWORD: case FLAT_STORE_DWORDX2:
+    case DS_WRITE_B32: case DS_WRITE_B64: case S_BARRIER: break;
     case BUFFER_STORE_DWORD: out.push_back({R.spill(r.imm / 4), node_ref(i, 0, P_ENTIRE)}); break;
     case OP_UNKNOWN: {
       if (r.nops == 0) break;
@@ -1243,7 +1253,7 @@ void build_nodes(Kernel& K) {
               bool is_dst = (k == 0 && (s == 'V' || s == 'W' || s == 's' || s == 'p' || s == 'q' || s == 'c')) ||
                             (k == 1 && s == 'c' && (op == V_ADD_CO_U32 || op == V_SUB_CO_U32));
               if (op == GLOBAL_STORE_DWORD || op == GLOBAL_STORE_DWORDX2 || op == FLAT_STORE_DWORD ||
-                  op == FLAT_STORE_DWORDX2)
+                  op == FLAT_STORE_DWORDX2 || op == DS_WRITE_B32 || op == DS_WRITE_B64)
                 is_dst = false;
               if (is_scmp(op)) is_dst = false;
               if (is_dst || s == 'o') continue;
@@ -1330,7 +1340,8 @@ enum Cls { K_NONE, K_LID, K_GRP, K_KARG, K_UNDEF, K_GOFS64, K_GOFSLO, K_MULGRP, 
            K_DISP0,   // its first dword (header and setup; an intermediate, like K_MULGRP)
            K_GSIZE,   // get_global_size(d)
            K_NGRP,    // get_num_groups(d)
-           K_WDIM };  // get_work_dim()
+           K_WDIM,    // get_work_dim()
+           K_LPTR };  // the LDS address of a __local pointer argument (the low dword of its slot)
 struct ClsV {
   int c = K_NONE;
   int k = 0;
@@ -1374,6 +1385,8 @@ ClsV settings_load(const Kernel& K, const Node& n, uint32_t part, bool wide) {
     if (is_64type(a.elem)) return ClsV{K_ARG64, (int)slot};
     return v;
   }
+  // a __local pointer argument: the low dword of its slot is the buffer's LDS address
+  if (!a.hidden && a.pointer && a.space == 2 && part == P_ENTIRE) return ClsV{K_LPTR, (int)slot};
   if (a.hidden || a.pointer || is_64type(a.elem) || part != P_ENTIRE) return v;
   return ClsV{K_ARG32, (int)slot};
 }
@@ -1518,6 +1531,41 @@ MemRef match_addr(const Kernel& K, uint32_t addr, int width) {
   return m;
 }
 
+// An LDS access (ds_read / ds_write): the address is 32 bits, the __local buffer's LDS address
+// plus the index shifted by log2 of the element size (v_lshlrev_b32 then v_add_u32, either
+// operand order), or the buffer's address alone (element 0).
+MemRef match_lds(const Kernel& K, uint32_t addr, int width) {
+  MemRef m;
+  ClsV c = classify(K, addr);
+  if (c.c == K_LPTR) {
+    if (elem_size(K.cfg.args[c.k].elem) != width) return m;
+    m.ok = true;
+    m.arg = c.k;
+    return m;
+  }
+  if (!is_node(addr) || rpart(addr) != P_ENTIRE) return m;
+  const Node& n = K.nodes[rid(addr)];
+  if (n.kind != N_OP || n.op != V_ADD_U32) return m;
+  for (int o = 0; o < 2; ++o) {
+    uint32_t X = fwd(K, n.src[o]), Y = fwd(K, n.src[1 - o]);
+    ClsV cx = classify(K, X);
+    if (cx.c != K_LPTR) continue;
+    int es = elem_size(K.cfg.args[cx.k].elem);
+    if (es != width) continue;
+    if (!is_node(Y) || rpart(Y) != P_ENTIRE) continue;
+    const Node& sh = K.nodes[rid(Y)];
+    if (sh.kind != N_OP || sh.op != V_LSHLREV_B32) continue;
+    uint32_t s0 = fwd(K, sh.src[0]);
+    if (!is_node(s0) || K.nodes[rid(s0)].kind != N_CONST || K.nodes[rid(s0)].cval != (uint32_t)log2_exact(es))
+      continue;
+    m.ok = true;
+    m.arg = cx.k;
+    m.idx = fwd(K, sh.src[1]);
+    return m;
+  }
+  return m;
+}
+
 // ============================================================================
 // Emission state: reachability, variables, types ("Data type recovery")
 // ============================================================================
@@ -1549,18 +1597,27 @@ int resolve_type(int t, int width) {
 // Memory accesses.  FLAT instructions may address global memory, LDS or scratch
 // ("The body extraction"); in this dialect their address is always formed from
 // a __global buffer argument, exactly as for the GLOBAL instructions, so both
-// are the same access: the same dataflow, address match and output.
+// are the same access: the same dataflow, address match and output.  The LDS
+// accesses are loads and stores of a __local buffer, with their own address
+// match (match_lds).
+bool is_lds(int op) { return op >= DS_READ_B32 && op <= DS_WRITE_B64; }
 bool is_store(int op) {
-  return op == GLOBAL_STORE_DWORD || op == GLOBAL_STORE_DWORDX2 || op == FLAT_STORE_DWORD || op == FLAT_STORE_DWORDX2;
+  return op == GLOBAL_STORE_DWORD || op == GLOBAL_STORE_DWORDX2 || op == FLAT_STORE_DWORD || op == FLAT_STORE_DWORDX2 ||
+         op == DS_WRITE_B32 || op == DS_WRITE_B64;
 }
 bool is_gload(int op) {
-  return op == GLOBAL_LOAD_DWORD || op == GLOBAL_LOAD_DWORDX2 || op == FLAT_LOAD_DWORD || op == FLAT_LOAD_DWORDX2;
+  return op == GLOBAL_LOAD_DWORD || op == GLOBAL_LOAD_DWORDX2 || op == FLAT_LOAD_DWORD || op == FLAT_LOAD_DWORDX2 ||
+         op == DS_READ_B32 || op == DS_READ_B64;
 }
 // bytes one access moves
 int mem_width(int op) {
-  return op == GLOBAL_LOAD_DWORDX2 || op == GLOBAL_STORE_DWORDX2 || op == FLAT_LOAD_DWORDX2 || op == FLAT_STORE_DWORDX2
+  return op == GLOBAL_LOAD_DWORDX2 || op == GLOBAL_STORE_DWORDX2 || op == FLAT_LOAD_DWORDX2 ||
+                 op == FLAT_STORE_DWORDX2 || op == DS_READ_B64 || op == DS_WRITE_B64
              ? 8
              : 4;
+}
+MemRef match_mem(const Kernel& K, int op, uint32_t addr) {
+  return is_lds(op) ? match_lds(K, addr, mem_width(op)) : match_addr(K, addr, mem_width(op));
 }
 
 // Sweep limit of the type fixed point.  The lattice is finite and a sweep that
@@ -1615,7 +1672,7 @@ struct Emitter {
     }
     if (n.kind != N_OP) return ch;
     if (is_gload(n.op) || is_store(n.op)) {
-      MemRef m = match_addr(K, fwd(K, n.src[0]), mem_width(n.op));
+      MemRef m = match_mem(K, n.op, fwd(K, n.src[0]));
       if (m.ok) {
         if (m.idx != TOP) ch.push_back(m.idx);
       } else {
@@ -1723,6 +1780,7 @@ struct Emitter {
     ClsV c = cls(r);
     switch (c.c) {
       case K_GID: case K_GIDNO: case K_LID: case K_GRP: case K_GOFSLO: case K_GSIZE: case K_NGRP: case K_WDIM:
+      case K_LPTR:
         return T_UINT;
       case K_GOFS64: case K_ARGPTR: case K_KARG: return T_ULONG;
       case K_ARG32: case K_ARG64: return K.cfg.args[c.k].elem;
@@ -1751,9 +1809,10 @@ struct Emitter {
       case V_LSHLREV_B64: return st(1);
       case V_MUL_HI_U32_U24: return T_UINT;
       case V_MUL_HI_I32_I24: return T_INT;
-      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: case FLAT_LOAD_DWORD: case FLAT_LOAD_DWORDX2: {
+      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: case FLAT_LOAD_DWORD: case FLAT_LOAD_DWORDX2:
+      case DS_READ_B32: case DS_READ_B64: {
         int w = mem_width(n.op);
-        MemRef m = match_addr(K, fwd(K, n.src[0]), w);
+        MemRef m = match_mem(K, n.op, fwd(K, n.src[0]));
         if (m.ok) return K.cfg.args[m.arg].elem;
         return w == 8 ? T_ULONG : T_UINT;
       }
@@ -1928,13 +1987,17 @@ struct Emitter {
   }
 
   std::string memref(const Node& n, int width, int* elem) {
-    MemRef m = match_addr(K, fwd(K, n.src[0]), width);
+    MemRef m = match_mem(K, n.op, fwd(K, n.src[0]));
     if (m.ok) {
       *elem = K.cfg.args[m.arg].elem;
       std::string idx = m.idx == TOP ? std::string("0") : E(m.idx, T_NONE);
       return K.cfg.args[m.arg].name + "[" + idx + "]";
     }
     *elem = width == 8 ? T_ULONG : T_UINT;
+    if (is_lds(n.op)) {  // an LDS address that is no buffer element: pseudo-code
+      partial = true;
+      return std::string("*((__local ") + type_name(*elem) + " *)(" + E(fwd(K, n.src[0]), T_UINT) + "))";
+    }
     return std::string("*((__global ") + type_name(*elem) + " *)(" + E(fwd(K, n.src[0]), T_ULONG) + "))";
   }
 
@@ -2016,7 +2079,8 @@ struct Emitter {
       case V_FMA_F64: return Ex{"fma(" + S(0, T_DOUBLE) + ", " + S(1, T_DOUBLE) + ", " + S(2, T_DOUBLE) + ")", T_DOUBLE};
       case V_CNDMASK_B32:  // "Search for control structures": the ternary operator, one instruction
         return Ex{"(" + S(2, T_NONE) + " ? " + S(1, NT) + " : " + S(0, NT) + ")", NT};
-      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: case FLAT_LOAD_DWORD: case FLAT_LOAD_DWORDX2: {
+      case GLOBAL_LOAD_DWORD: case GLOBAL_LOAD_DWORDX2: case FLAT_LOAD_DWORD: case FLAT_LOAD_DWORDX2:
+      case DS_READ_B32: case DS_READ_B64: {
         int elem;
         std::string m = memref(n, mem_width(op), &elem);
         return Ex{m, elem};
@@ -2045,6 +2109,7 @@ struct Emitter {
       case K_GOFS64: return Ex{"get_global_offset(" + std::to_string(c.k) + ")", T_ULONG};
       case K_ARG32: case K_ARG64: return Ex{K.cfg.args[c.k].name, K.cfg.args[c.k].elem};
       case K_ARGPTR: return Ex{"(ulong)" + K.cfg.args[c.k].name, T_ULONG};
+      case K_LPTR: partial = true; return Ex{"(uint)(ulong)" + K.cfg.args[c.k].name, T_UINT};
       case K_KARG: case K_DISP: partial = true; return Ex{"0UL", T_ULONG};
       case K_GSIZE: return Ex{"get_global_size(" + std::to_string(c.k) + ")", T_UINT};
       case K_NGRP: return Ex{"get_num_groups(" + std::to_string(c.k) + ")", T_UINT};
@@ -2109,6 +2174,10 @@ struct Emitter {
           int elem;
           std::string m = memref(n, mem_width(n.op), &elem);
           line(lvl, m + " = " + E(fwd(K, n.src[1]), elem) + ";");
+          continue;
+        }
+        if (n.kind == N_OP && order[q] == 0 && n.op == S_BARRIER) {  // at its program point
+          line(lvl, "barrier(CLK_LOCAL_MEM_FENCE);");
           continue;
         }
         if (var_of[id] >= 0) {

@@ -24,7 +24,7 @@ def random_buffers(prog: gcn_interp.KernelText, seed: int, wide: bool = False):
     rng = np.random.default_rng(seed)
     bufs, scal = {}, {}
     for name, hidden, ptr, elem in prog.args:
-        if hidden:
+        if hidden or name in prog.local_args:  # a __local buffer lives in each work-group's LDS
             continue
         if not ptr:
             scal[name] = int(rng.integers(0, 40))

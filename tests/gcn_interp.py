@@ -42,6 +42,7 @@ class KernelText:
         self.dims = 1
         self.cws = [1, 1, 1]
         self.args = []        # (name, hidden, pointer, elem)
+        self.local_args = set()  # pointer arguments in the local address space (LDS)
         self.useargs = False
         self.instrs = []      # (mnemonic, [operand strings], modifiers dict)
         self.labels = {}
@@ -73,6 +74,8 @@ class KernelText:
                     ty = f[2]
                     ptr = ty.endswith("*")
                     self.args.append((f[0], f[0].startswith("_."), ptr, ty[:-1] if ptr else ty))
+                    if ptr and len(f) > 3 and f[3] == "local":
+                        self.local_args.add(f[0])
             elif state == "t":
                 if len(w) == 1 and row.endswith(":"):
                     self.labels[row[:-1]] = len(self.instrs)
@@ -95,9 +98,10 @@ _one = re.compile(r"^([vs])(\d+)$")
 
 
 class Wave:
-    def __init__(self, prog: KernelText, mem, kargs: bytes, lid, grp, active, disp: bytes = b""):
+    def __init__(self, prog: KernelText, mem, kargs: bytes, lid, grp, active, disp: bytes = b"", lds=None):
         self.p = prog
         self.mem = mem                    # dict base -> numpy array (buffers)
+        self.lds = lds                    # the work-group's LDS bytes (uint8 array)
         self.karg = kargs
         self.disp = disp
         self.v = np.zeros((256, W), dtype=np.uint32)
@@ -402,6 +406,30 @@ class Wave:
                     arr, off = self.gaddr(int(addr[i]))
                     arr.view(np.uint8)[off:off + nb] = np.frombuffer(int(val[i]).to_bytes(nb, "little"), np.uint8)
             return None
+        if m in ("ds_read_b32", "ds_read_b64"):
+            addr = self.rd32(o[1]).astype(np.int64) + mods.get("offset", 0)
+            nb = 4 if m == "ds_read_b32" else 8
+            val = np.zeros(W, dtype=np.uint64)
+            for i in range(W):
+                if ex[i]:
+                    a = int(addr[i])
+                    val[i] = int.from_bytes(self.lds[a:a + nb].tobytes(), "little")
+            if nb == 4:
+                self.wr32(o[0], val)
+            else:
+                self.wr64(o[0], val)
+            return None
+        if m in ("ds_write_b32", "ds_write_b64"):
+            addr = self.rd32(o[0]).astype(np.int64) + mods.get("offset", 0)
+            nb = 4 if m == "ds_write_b32" else 8
+            val = self.rd32(o[1]).astype(np.uint64) if nb == 4 else self.rd64(o[1])
+            for i in range(W):
+                if ex[i]:
+                    a = int(addr[i])
+                    self.lds[a:a + nb] = np.frombuffer(int(val[i]).to_bytes(nb, "little"), np.uint8)
+            return None
+        if m == "s_barrier":  # the group is one wave (run_ndrange checks): its lanes are in step
+            return None
         if m == "buffer_store_dword":
             slot = mods.get("offset", 0)
             cur = self.scratch.get(slot, np.zeros(W, dtype=np.uint32))
@@ -462,13 +490,22 @@ _VOP2_INT = {
 }
 
 
+LDS_BYTES = 65536
+LDS_SLICE = 16384  # LDS bytes given to each __local argument
+
+
 def make_kargs(prog: KernelText, buf_base: dict, scalars: dict, gofs) -> bytes:
     b = bytearray(8 * len(prog.args) + 64)
+    nloc = 0
     for i, (name, hidden, ptr, elem) in enumerate(prog.args):
         off = 8 * i
         if hidden:
             if name.startswith("_.global_offset_"):
                 struct.pack_into("<Q", b, off, gofs[int(name[-1])])
+            continue
+        if name in prog.local_args:  # the low dword holds the buffer's LDS address
+            struct.pack_into("<Q", b, off, LDS_SLICE * nloc)
+            nloc += 1
             continue
         if ptr:
             struct.pack_into("<Q", b, off, buf_base[name])
@@ -496,7 +533,7 @@ def run_ndrange(text: str, buffers: dict, scalars: dict, groups=(2, 1), gofs=(0,
     mem = {}
     addr = 0x10_0000_0000
     for name, hidden, ptr, elem in prog.args:
-        if ptr and not hidden:
+        if ptr and not hidden and name not in prog.local_args:
             base[name] = addr
             mem[addr] = buffers[name]
             addr += 0x1_0000_0000
@@ -504,14 +541,19 @@ def run_ndrange(text: str, buffers: dict, scalars: dict, groups=(2, 1), gofs=(0,
     c0, c1 = prog.cws[0], prog.cws[1] if prog.dims > 1 else 1
     g1n = groups[1] if prog.dims > 1 else 1
     disp = make_dispatch(prog.dims, (c0, c1, 1), (groups[0] * c0, g1n * c1, 1))
+    has_barrier = any(m == "s_barrier" for m, _, _ in prog.instrs)
+    if has_barrier and c0 * c1 > W:
+        raise NotImplementedError("barriers in a work-group of more than one wave")
     for g1 in range(g1n):
         for g0 in range(groups[0]):
             n = c0 * c1
+            lds = np.zeros(LDS_BYTES, dtype=np.uint8)  # a fresh LDS per work-group
             for w0 in range(0, n, W):
                 lanes = np.arange(w0, w0 + W)
                 active = lanes < n
                 lid0 = np.where(active, lanes % c0, 0).astype(np.uint32)
                 lid1 = np.where(active, lanes // c0, 0).astype(np.uint32)
-                wave = Wave(prog, mem, kargs, (lid0, lid1, np.zeros(W, np.uint32)), (g0, g1, 0), active, disp)
+                wave = Wave(prog, mem, kargs, (lid0, lid1, np.zeros(W, np.uint32)), (g0, g1, 0), active, disp,
+                            lds)
                 wave.run()
     return prog

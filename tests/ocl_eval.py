@@ -93,12 +93,12 @@ class Parser:
         else:
             while True:
                 if self.peek() in ("__global", "__constant", "__local"):
-                    self.eat()
+                    space = self.eat()
                     if self.peek() == "const":
                         self.eat()
                     ty = self.eat()
                     self.eat("*")
-                    params.append(("ptr", ty, self.eat()))
+                    params.append(("ptr", ty, self.eat(), space))
                 else:
                     ty = self.eat()
                     params.append(("val", ty, self.eat()))
@@ -158,6 +158,14 @@ class Parser:
             self.eat(")")
             self.eat(";")
             return ("do", b, c)
+        if p == "barrier":  # barrier(CLK_LOCAL_MEM_FENCE);
+            self.eat()
+            self.eat("(")
+            if self.eat() != "CLK_LOCAL_MEM_FENCE":
+                raise ParseError("barrier flags")
+            self.eat(")")
+            self.eat(";")
+            return ("barrier",)
         if p == "break":
             if not self.loops:
                 raise ParseError("break outside a loop")
@@ -459,7 +467,11 @@ class _Break(Exception):
 
 
 def run_block(items, env):
+    """Runs the statements of one work-item; a generator that yields at every barrier."""
     for s in items:
+        if s[0] == "barrier":
+            yield
+            continue
         if s[0] == "break":
             raise _Break()
         if s[0] == "assign":
@@ -482,12 +494,12 @@ def run_block(items, env):
                 raise EvalError("raw pointer store")
         elif s[0] == "if":
             _, c = ev(s[1], env)
-            run_block(s[2] if c != 0 else s[3], env)
+            yield from run_block(s[2] if c != 0 else s[3], env)
         elif s[0] == "do":
             n = 0
             while True:
                 try:
-                    run_block(s[1], env)
+                    yield from run_block(s[1], env)
                 except _Break:
                     break
                 n += 1
@@ -498,16 +510,37 @@ def run_block(items, env):
                     break
 
 
+LOCAL_ELEMS = 4096  # elements of each __local buffer, per work-group
+
+
 def run_ndrange(k: Kernel, buffers, scalars, cws, dims, groups=(2, 1), gofs=(0, 0, 0)):
+    """Every work-group of the NDRange; inside a group the work-items run in turn up to the next
+    barrier, and every work-item must reach the same barrier (or the end) before any goes on.
+    Each group has fresh __local buffers."""
     c0, c1 = cws[0], (cws[1] if dims > 1 else 1)
     g1n = groups[1] if dims > 1 else 1
+    local = [p for p in k.params if p[0] == "ptr" and len(p) > 3 and p[3] == "__local"]
     for g1 in range(g1n):
         for g0 in range(groups[0]):
+            bufs = dict(buffers)
+            for p in local:
+                bufs[p[2]] = np.zeros(LOCAL_ELEMS, dtype=T[p[1]])
+            items = []
             for l1 in range(c1):
                 for l0 in range(c0):
                     ids = {"lid": (l0, l1, 0), "grp": (g0, g1, 0), "gofs": gofs,
                            "gid": ((g0 * c0 + l0 + gofs[0]) & 0xFFFFFFFF, (g1 * c1 + l1 + gofs[1]) & 0xFFFFFFFF, 0),
                            "gsize": (groups[0] * c0, g1n * c1, 1), "ngrp": (groups[0], g1n, 1), "wdim": dims}
-                    env = Env(k, buffers, scalars, ids)
-                    with np.errstate(all="ignore"):
-                        run_block(k.body, env)
+                    items.append(run_block(k.body, Env(k, bufs, scalars, ids)))
+            with np.errstate(all="ignore"):
+                while items:
+                    at_barrier = []
+                    for g in items:
+                        try:
+                            next(g)
+                            at_barrier.append(g)
+                        except StopIteration:
+                            pass
+                    if at_barrier and len(at_barrier) != len(items):
+                        raise EvalError("work-items of a group disagree on a barrier")
+                    items = at_barrier

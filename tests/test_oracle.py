@@ -172,7 +172,7 @@ def test_join_versions_are_minimal():
     assert used > 0
 
 
-@pytest.mark.parametrize("cfg", [1, 5, 6, 7, 8])
+@pytest.mark.parametrize("cfg", [1, 5, 6, 7, 8, 9])
 def test_output_is_wellformed_opencl(cfg):
     b = _batch(cfg, 60, max_len=900)
     out, oo, st = oracle.decompile_batch(b.text, b.offsets)
@@ -421,3 +421,49 @@ def test_brute_force_mixed_nesting_and_early_exits():
         breaks += r.text.count("break;")
         assert brute.check(txt, r.text, seed=i, scalars={"n": i % 5}) is None, f"kernel {i}"
     assert breaks > 0
+
+
+# ---- LDS ("The AMD GCN architecture": LDS is OpenCL local memory; "The body extraction":
+# data share operations, prefix ds) ------------------------------------------------------------
+def test_lds_golden():
+    """A __local argument's slot holds its LDS address; ds_write / ds_read at that address plus
+    the index shifted by the element size are elements of the buffer; s_barrier is the work-group
+    barrier.  The expected text is derived by hand."""
+    r = oracle.decompile(gold("lds_exchange.s"))
+    assert r.status == [0]
+    assert r.text == gold("lds_exchange.cl")
+
+
+def test_brute_force_lds_golden_and_planted_mistakes():
+    asm, good = gold("lds_exchange.s"), gold("lds_exchange.cl")
+    for seed in range(3):
+        assert brute.check(asm, good, seed=seed) is None
+    planted = [good.replace("    barrier(CLK_LOCAL_MEM_FENCE);\n", ""),          # no barrier
+               good.replace("(1u + get_local_id(0))", "(2u + get_local_id(0))"),   # another neighbour
+               good.replace("tmp[get_local_id(0)] = var0;", "tmp[0] = var0;")]     # another element
+    for bad in planted:
+        assert bad != good
+        assert brute.check(asm, bad, seed=0) is not None
+
+
+def test_lds_address_that_is_no_element_is_partial():
+    """An LDS address scaled by 8 for a buffer of 4-byte elements names no element: the access is
+    printed as pseudo-code through a __local pointer and the kernel is PARTIAL."""
+    src = gold("lds_exchange.s").replace("v_lshlrev_b32 v8, 2, v0", "v_lshlrev_b32 v8, 3, v0")
+    r = oracle.decompile(src)
+    assert r.status == [1]
+    assert "*((__local uint *)(" in r.text
+
+
+def test_brute_force_lds_preset():
+    """Preset 9: exchanges through a __local buffer (write, barrier, read a neighbour) among the
+    batch mix; the decompiled text computes the assembly's buffers."""
+    b = _batch(9, 30, max_len=500, cws0=8)
+    barriers = 0
+    for i in range(len(b)):
+        txt = b.kernel(i).decode()
+        r = oracle.decompile(txt)
+        assert r.status == [0]
+        barriers += r.text.count("barrier(CLK_LOCAL_MEM_FENCE);")
+        assert brute.check(txt, r.text, seed=i) is None, f"kernel {i}"
+    assert barriers > 0
