@@ -54,6 +54,7 @@ WORKLOADS = {
     "sysval": (6, 10_000),  # the batch mix with dispatch-packet system values and scalar bit fields
     "flatmulhi": (7, 10_000),  # the batch mix with FLAT accesses and double-suffix high multiplies
     "mixed": (8, 10_000),  # mixed uniform/divergent nesting, loops with early exits
+    "lds": (9, 10_000),  # 1-D kernels exchanging values through a __local buffer around a barrier
 }
 METRIC = "GCN instrs decompiled/sec"
 # the library's event timing of single kernels (gcn_decomp_stage_times names)

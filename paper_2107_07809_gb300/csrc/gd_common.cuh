@@ -54,7 +54,9 @@ enum : uint16_t {
   // and the double-suffix high multiplies (result type, then operand type)
   O_FLAT_LOAD_DWORD = 86, O_FLAT_LOAD_DWORDX2 = 87, O_FLAT_STORE_DWORD = 88, O_FLAT_STORE_DWORDX2 = 89,
   O_V_MUL_HI_U32_U24 = 90, O_V_MUL_HI_I32_I24 = 91,
-  O_COUNT = 92
+  // data share operations on the LDS (OpenCL local memory; prefix ds) and the work-group barrier
+  O_DS_READ_B32 = 92, O_DS_READ_B64 = 93, O_DS_WRITE_B32 = 94, O_DS_WRITE_B64 = 95, O_S_BARRIER = 96,
+  O_COUNT = 97
 };
 
 // ---- operand word: tag<<28 | count<<24 | payload -----------------------------------
@@ -82,7 +84,7 @@ static __device__ char c_sig[O_COUNT][12] = {
     "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S", "c,S,S",
     "V,c,S,S", "V,c,S,S,c", "V,c,S,S", "V,c,S,S,c", "W,S,W", "W,W,W", "W,W,W", "W,W,W,W",
     "V,W,o", "W,W,o", "W,V,o", "W,W,o", "V,o,q,s", "V,o,q,s", "V,S,S,c", "s,S,S", "s,S,S",
-    "V,W", "W,W", "W,V", "W,W", "V,S,S", "V,S,S"};
+    "V,W", "W,W", "W,V", "W,W", "V,S,S", "V,S,S", "V,V", "W,V", "V,V", "V,W", ""};
 __device__ __forceinline__ int sig_count(uint16_t op) {
   const char* s = c_sig[op];
   int n = 0;
@@ -100,20 +102,22 @@ struct __align__(4) InstrRec {
 };
 static_assert(sizeof(InstrRec) == 32, "InstrRec is 32 bytes");
 
-// global and FLAT accesses are the same access in this dialect (a FLAT address is always formed
-// from a __global buffer argument)
+// Memory accesses: global and FLAT accesses are the same access in this dialect (a FLAT address
+// is always formed from a __global buffer argument); the LDS accesses (ds_) are loads and stores
+// of a __local buffer, with their own address match.
+__host__ __device__ __forceinline__ bool op_lds(uint16_t op) { return op >= O_DS_READ_B32 && op <= O_DS_WRITE_B64; }
 __host__ __device__ __forceinline__ bool op_store(uint16_t op) {
   return op == O_GLOBAL_STORE_DWORD || op == O_GLOBAL_STORE_DWORDX2 || op == O_FLAT_STORE_DWORD ||
-         op == O_FLAT_STORE_DWORDX2;
+         op == O_FLAT_STORE_DWORDX2 || op == O_DS_WRITE_B32 || op == O_DS_WRITE_B64;
 }
 __host__ __device__ __forceinline__ bool op_gload(uint16_t op) {
   return op == O_GLOBAL_LOAD_DWORD || op == O_GLOBAL_LOAD_DWORDX2 || op == O_FLAT_LOAD_DWORD ||
-         op == O_FLAT_LOAD_DWORDX2;
+         op == O_FLAT_LOAD_DWORDX2 || op == O_DS_READ_B32 || op == O_DS_READ_B64;
 }
 // bytes one load or store moves
 __host__ __device__ __forceinline__ uint32_t op_mem_width(uint16_t op) {
   return (op == O_GLOBAL_LOAD_DWORDX2 || op == O_GLOBAL_STORE_DWORDX2 || op == O_FLAT_LOAD_DWORDX2 ||
-          op == O_FLAT_STORE_DWORDX2)
+          op == O_FLAT_STORE_DWORDX2 || op == O_DS_READ_B64 || op == O_DS_WRITE_B64)
              ? 8u
              : 4u;
 }

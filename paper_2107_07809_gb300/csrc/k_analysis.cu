@@ -154,6 +154,7 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
   Cls c = classify(v, mkref(id, PART_ENTIRE));
   switch (c.c) {
     case K_GID: case K_GIDNO: case K_LID: case K_GRP: case K_GOFSLO: case K_GSIZE: case K_NGRP: case K_WDIM:
+    case K_LPTR:
       return TY_UINT;
     case K_GOFS64: case K_ARGPTR: case K_KARG: return TY_ULONG;
     case K_ARG32: case K_ARG64: return v.A[c.k].elem;
@@ -181,7 +182,8 @@ __device__ uint8_t node_type(const KView& v, const uint8_t* nt, const uint8_t* p
     case O_V_LSHLREV_B64: return st(1);
     case O_V_MUL_HI_U32_U24: return TY_UINT;
     case O_V_MUL_HI_I32_I24: return TY_INT;
-    case O_GLOBAL_LOAD_DWORD: case O_GLOBAL_LOAD_DWORDX2: case O_FLAT_LOAD_DWORD: case O_FLAT_LOAD_DWORDX2: {
+    case O_GLOBAL_LOAD_DWORD: case O_GLOBAL_LOAD_DWORDX2: case O_FLAT_LOAD_DWORD: case O_FLAT_LOAD_DWORDX2:
+    case O_DS_READ_B32: case O_DS_READ_B64: {
       Mem m = mem_of(v, id);
       if (m.ok) return v.A[m.arg].elem;
       return op_mem_width(n.op) == 8 ? TY_ULONG : TY_UINT;
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(128)
   uint32_t a = kNone, x = kTop;
   const Node& n = v.node(id0);
   if (!bad && n.kind == N_OP && (op_gload(n.op) || op_store(n.op))) {
-    Mem m = match_addr(v, nsrc(v, n, 0), op_mem_width(n.op));
+    Mem m = match_mem(v, n);
     if (m.ok) {
       a = m.arg;
       x = m.idx;

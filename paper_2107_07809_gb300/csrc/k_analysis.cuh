@@ -85,7 +85,8 @@ enum : uint8_t { K_NONE = 0, K_LID, K_GRP, K_KARG, K_UNDEF, K_GOFS64, K_GOFSLO, 
                  K_DISP0,   // the packet's first dword (header, setup): an intermediate like K_MULGRP
                  K_GSIZE,   // get_global_size(d): the dword at 0xc + 4d
                  K_NGRP,    // get_num_groups(d): global size >> log2(work-group size)
-                 K_WDIM };  // get_work_dim(): field 0x20010 (offset 16, width 2) of the first dword
+                 K_WDIM,    // get_work_dim(): field 0x20010 (offset 16, width 2) of the first dword
+                 K_LPTR };  // the LDS address of a __local pointer argument (the low dword of its slot)
 struct Cls {
   uint8_t c, k;
 };
@@ -129,6 +130,8 @@ static __device__ GD_MATCH_INLINE Cls settings_load(const KView& v, const Node& 
     if (ty64(a.elem)) return Cls{K_ARG64, (uint8_t)slot};
     return none;
   }
+  // a __local pointer argument: the low dword of its slot is the buffer's LDS address
+  if (!a.hidden && a.pointer && a.space == 2 && part == PART_ENTIRE) return Cls{K_LPTR, (uint8_t)slot};
   if (a.hidden || a.pointer || ty64(a.elem) || part != PART_ENTIRE) return none;
   return Cls{K_ARG32, (uint8_t)slot};
 }
@@ -316,12 +319,48 @@ static __device__ GD_MATCH_INLINE Mem match_addr(const KView& v, uint32_t addr, 
   return m;
 }
 
+// LDS access: the __local buffer's 32-bit LDS address plus the index shifted by log2 of the
+// element size (v_lshlrev_b32 then v_add_u32, either operand order), or the address alone
+static __device__ GD_MATCH_INLINE Mem match_lds(const KView& v, uint32_t addr, uint32_t width) {
+  Mem m{false, kNone, kTop};
+  Cls c = classify(v, addr);
+  if (c.c == K_LPTR) {
+    if ((ty64(v.A[c.k].elem) ? 8u : 4u) != width) return m;
+    m.ok = true;
+    m.arg = c.k;
+    return m;
+  }
+  if (!r_node(addr) || rpart(addr) != PART_ENTIRE) return m;
+  const Node& n = v.node(rid(addr));
+  if (n.kind != N_OP || n.op != O_V_ADD_U32) return m;
+  for (int o = 0; o < 2; ++o) {
+    uint32_t X = nsrc(v, n, o), Y = nsrc(v, n, 1 - o);
+    Cls cx = classify(v, X);
+    if (cx.c != K_LPTR) continue;
+    uint32_t es = ty64(v.A[cx.k].elem) ? 8u : 4u;
+    if (es != width) continue;
+    if (!r_node(Y) || rpart(Y) != PART_ENTIRE) continue;
+    const Node& sh = v.node(rid(Y));
+    if (sh.kind != N_OP || sh.op != O_V_LSHLREV_B32) continue;
+    if (const_src(v, sh, 0) != ilog2_exact(es)) continue;
+    m.ok = true;
+    m.arg = cx.k;
+    m.idx = nsrc(v, sh, 1);
+    return m;
+  }
+  return m;
+}
+// the match of load / store node n's address, by its kind of access
+__device__ __forceinline__ Mem match_mem(const KView& v, const Node& n) {
+  return op_lds(n.op) ? match_lds(v, nsrc(v, n, 0), op_mem_width(n.op)) : match_addr(v, nsrc(v, n, 0), op_mem_width(n.op));
+}
+
 __device__ __forceinline__ bool op_vcmp(uint16_t op) { return op >= O_V_CMP0 && op < O_V_CMP0 + 18; }
 __device__ __forceinline__ bool op_scmp(uint16_t op) { return op >= O_S_CMP0 && op < O_S_CMP0 + 12; }
 __device__ __forceinline__ bool op_wide(uint16_t op) {
   return op == O_S_LOAD_DWORDX2 || op == O_V_CVT_F64_F32 || op == O_V_CVT_F64_I32 || op == O_V_LSHLREV_B64 ||
          op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2 ||
-         op == O_FLAT_LOAD_DWORDX2;
+         op == O_FLAT_LOAD_DWORDX2 || op == O_DS_READ_B64;
 }
 
 __device__ __forceinline__ int node_width(const KView& v, uint32_t id) {
@@ -351,8 +390,7 @@ __device__ __forceinline__ uint8_t tresolve(uint8_t t, int width) {
 // memory match of load/store node `id` (slot 0 of its instruction)
 __device__ __forceinline__ Mem mem_of(const KView& v, uint32_t id) {
   if (v.marg) return Mem{v.marg[id / 4] != kNone, v.marg[id / 4], v.midx[id / 4]};
-  const Node& n = v.node(id);
-  return match_addr(v, nsrc(v, n, 0), op_mem_width(n.op));
+  return match_mem(v, v.node(id));
 }
 
 static __device__ int node_children(const KView& v, uint32_t id, uint32_t* ch) {

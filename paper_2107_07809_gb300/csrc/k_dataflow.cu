@@ -38,7 +38,7 @@ __device__ __forceinline__ bool scmp(uint16_t op) { return op >= O_S_CMP0 && op 
 __device__ __forceinline__ bool wide_result(uint16_t op) {
   return op == O_S_LOAD_DWORDX2 || op == O_V_CVT_F64_F32 || op == O_V_CVT_F64_I32 || op == O_V_LSHLREV_B64 ||
          op == O_V_ADD_F64 || op == O_V_MUL_F64 || op == O_V_FMA_F64 || op == O_GLOBAL_LOAD_DWORDX2 ||
-         op == O_FLAT_LOAD_DWORDX2;
+         op == O_FLAT_LOAD_DWORDX2 || op == O_DS_READ_B64;
 }
 
 // register index of the first register of an operand word (v/s/vcc)
@@ -58,7 +58,7 @@ __device__ int idefs(const Batch& b, const KHdr& K, const RegMap& M, uint32_t i,
   int n = 0;
   switch (r.op) {
     case O_S_WAITCNT: case O_GLOBAL_STORE_DWORD: case O_GLOBAL_STORE_DWORDX2: case O_FLAT_STORE_DWORD:
-    case O_FLAT_STORE_DWORDX2: return 0;
+    case O_FLAT_STORE_DWORDX2: case O_DS_WRITE_B32: case O_DS_WRITE_B64: case O_S_BARRIER: return 0;
     case O_S_LOAD_DWORD: d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_ENTIRE)}; return n;
     case O_S_LOAD_DWORDX4:
       d[n++] = {reg_of(M, r.opnd[0], 0), mkref(base, PART_LO)};

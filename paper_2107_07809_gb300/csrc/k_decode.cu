@@ -54,6 +54,8 @@ static const OpName kOps[O_COUNT] = {
     {"s_bfe_u32", "s,S,S"},
     {"flat_load_dword", "V,W"}, {"flat_load_dwordx2", "W,W"}, {"flat_store_dword", "W,V"},
     {"flat_store_dwordx2", "W,W"}, {"v_mul_hi_u32_u24", "V,S,S"}, {"v_mul_hi_i32_i24", "V,S,S"},
+    {"ds_read_b32", "V,V"}, {"ds_read_b64", "W,V"}, {"ds_write_b32", "V,V"}, {"ds_write_b64", "V,W"},
+    {"s_barrier", ""},
 };
 
 constexpr int kHash = 512;
@@ -466,8 +468,8 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ 
       r.imm = (pay & 0x800000u) ? (pay | 0xFF000000u) : pay;
     }
     if ((r.op == O_BUFFER_LOAD_DWORD || r.op == O_BUFFER_STORE_DWORD) && (r.imm & 3u)) r.flags |= FL_BAD;
-    // a global or FLAT access with a constant byte offset: not folded into the address, so the
-    // instruction stays inline assembly
+    // a global, FLAT or LDS access with a constant byte offset: not folded into the address, so
+    // the instruction stays inline assembly
     if ((op_gload(r.op) || op_store(r.op)) && r.imm) {
       r.op = O_UNKNOWN;
       r.flags |= FL_UNSUPPORTED;

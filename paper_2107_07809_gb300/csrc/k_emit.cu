@@ -306,6 +306,11 @@ __device__ const Fmt g_fmt[O_COUNT + 1] = {
     // OpenCL's mul_hi of the operands reduced to 24 bits
     {"mul_hi((\1 & 16777215u), (\2 & 16777215u))", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
     {"mul_hi(((int)(\1 << 8) >> 8), ((int)(\2 << 8) >> 8))", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_LOAD4},  // ds_read_b32 (an element of a __local buffer)
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_LOAD8},  // ds_read_b64
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},   // ds_write_b32 (a statement)
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},   // ds_write_b64
+    {"", {TY_NONE, TY_NONE, TY_NONE}, 0, F_NONE},   // s_barrier (a statement)
     {"upsample(\2, \1)", {TY_UINT, TY_UINT, TY_NONE}, 0, F_TPL},
 };
 
@@ -313,7 +318,7 @@ __device__ const Fmt g_fmt[O_COUNT + 1] = {
 // number is printed: pre, the number (or argument name, or literal), mid, the
 // number again (NUM2), suf.  Every leaf goes through the same code.
 enum : uint8_t { LF_F_NUM = 1, LF_F_NUM2 = 2, LF_F_NAME = 4, LF_F_LIT32 = 8, LF_F_LIT64 = 16, LF_F_PARTIAL = 32 };
-constexpr uint8_t LF_VAR = 20, LF_EXPR = 21, LF_PART = 22;
+constexpr uint8_t LF_VAR = 21, LF_EXPR = 22, LF_PART = 23;
 struct LeafFmt {
   char pre[20];
   char mid[24];
@@ -321,7 +326,7 @@ struct LeafFmt {
   uint8_t flags;
 };
 static_assert(K_LID == 1 && K_UNDEF == 4 && K_GIDNO == 8 && K_ARGPTR == 10 && K_CONST64 == 14 && K_DISP == 15 &&
-                  K_WDIM == 19, "leaf table order");
+                  K_WDIM == 19 && K_LPTR == 20, "leaf table order");
 __device__ const LeafFmt g_leaf[LF_VAR + 1] = {
     {"", "", "", 0},                                                   // K_NONE
     {"get_local_id(", "", ")", LF_F_NUM},                              // K_LID
@@ -343,6 +348,7 @@ __device__ const LeafFmt g_leaf[LF_VAR + 1] = {
     {"get_global_size(", "", ")", LF_F_NUM},                           // K_GSIZE
     {"get_num_groups(", "", ")", LF_F_NUM},                            // K_NGRP
     {"get_work_dim()", "", "", 0},                                     // K_WDIM
+    {"(uint)(ulong)", "", "", LF_F_NAME | LF_F_PARTIAL},               // K_LPTR (an LDS address, no element)
     {"var", "", "", LF_F_NUM},                                         // LF_VAR
 };
 
@@ -391,6 +397,7 @@ __device__ __noinline__ uint8_t node_expr_type_of(const KView& v, const uint8_t*
     case O_V_CVT_F64_F32: case O_V_CVT_F64_I32: case O_V_ADD_F64: case O_V_MUL_F64: case O_V_FMA_F64: return TY_DOUBLE;
     case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: return n.fused ? T : TY_UINT;
     case O_GLOBAL_LOAD_DWORD: case O_GLOBAL_LOAD_DWORDX2: case O_FLAT_LOAD_DWORD: case O_FLAT_LOAD_DWORDX2:
+    case O_DS_READ_B32: case O_DS_READ_B64:
       return mem_elem_of(v, id, op_mem_width(op));
     case O_V_MUL_HI_U32_U24: return TY_UINT;
     case O_V_MUL_HI_I32_I24: return TY_INT;
@@ -472,7 +479,7 @@ struct Em {
     Cls c = classify(v, r);
     switch (c.c) {
       case K_UNDEF: case K_LID: case K_GRP: case K_GID: case K_GIDNO: case K_GOFSLO: case K_GSIZE: case K_NGRP:
-      case K_WDIM: return TY_UINT;
+      case K_WDIM: case K_LPTR: return TY_UINT;
       case K_GOFS64: case K_ARGPTR: case K_KARG: case K_DISP: return TY_ULONG;
       case K_ARG32: case K_ARG64: return v.A[c.k].elem;
       case K_CONST32: {
@@ -529,7 +536,7 @@ struct Em {
       num = c.k;
       switch (c.c) {
         case K_UNDEF: case K_LID: case K_GRP: case K_GID: case K_GIDNO: case K_GOFSLO: case K_GSIZE: case K_NGRP:
-        case K_WDIM: t = TY_UINT; break;
+        case K_WDIM: case K_LPTR: t = TY_UINT; break;
         case K_GOFS64: case K_ARGPTR: case K_KARG: case K_DISP: t = TY_ULONG; break;
         case K_ARG32: case K_ARG64: t = v.A[c.k].elem; break;
         case K_CONST32: {
@@ -631,6 +638,15 @@ struct Em {
       w.c(']');
       return;
     }
+    if (op_lds(n.op)) {  // an LDS address that is no buffer element: pseudo-code
+      partial = true;
+      w.s("*((__local ");
+      w.s(width == 8 ? "ulong" : "uint");
+      w.s(" *)(");
+      P(nsrc(v, n, 0), TY_UINT, d, false);
+      w.s("))");
+      return;
+    }
     w.s("*((__global ");
     w.s(width == 8 ? "ulong" : "uint");
     w.s(" *)(");
@@ -728,6 +744,11 @@ struct Em {
           w.s(" = ");
           P(nsrc(v, n, 1), elem, 0, false);
           w.s(";\n");
+          continue;
+        }
+        if (n.kind == N_OP && order[q] == 0 && n.op == O_S_BARRIER) {  // at its program point
+          w.indent(lvl);
+          w.s("barrier(CLK_LOCAL_MEM_FENCE);\n");
           continue;
         }
         if (vo[id] >= 0) {
@@ -1139,6 +1160,7 @@ __global__ void k_print_flag(const __grid_constant__ Batch b, uint32_t* __restri
     const size_t id = 4 * (size_t)gi;
     const Node& n = b.nodes[id];
     if (n.kind == N_OP && (n.op == O_UNKNOWN || op_store(n.op)) && (b.nflag[id] & 1)) f = 1;
+    if (n.kind == N_OP && n.op == O_S_BARRIER) f = 1;
     for (int q = 0; q < 4; ++q)
       if (b.var_of[id + q] >= 0) f = 1;
   }

@@ -62,6 +62,10 @@ def test_ir_parity_mixed_nesting(dec):
     _check_ir(dec, _files(8, 150))
 
 
+def test_ir_parity_lds_mix(dec):
+    _check_ir(dec, _files(9, 150))
+
+
 def test_ir_parity_multi_kernel_files(dec):
     ks = _files(1, 12, max_len=400)
     files = [b"".join(ks[0:4]), b"leading junk\n" + b"".join(ks[4:9]), ks[9], b"", b"".join(ks[10:12])]
@@ -148,6 +152,39 @@ def test_text_parity_early_exit_edge_cases(dec):
         base.replace(b"LOOP:\n    v_add_u32 v7, v7, 3\n", b"LOOP:\n"),
         base.replace(b"    v_add_u32 v7, v7, 5\n", b"    v_add_u32 v7, v7, 5\n    s_cmp_eq_u32 s12, 2\n"
                      b"    s_cbranch_scc1 DONE\n    v_add_u32 v7, v7, 1\n"),
+    ]
+    assert len(set(files)) == len(files)
+    _check_text(dec, files)
+
+
+def test_text_parity_lds_mix(dec):
+    """1-D kernels with a __local argument: ds writes of the own slot, a barrier, ds reads of
+    a neighbour's slot (40% of kernels), among global accesses"""
+    files = _files(9, 600)
+    _check_text(dec, files)
+    assert sum(oracle.decompile(f).text.count("barrier(") for f in files[:200]) > 0
+
+
+def test_text_parity_lds_edge_cases(dec):
+    """LDS addresses that are no element of the __local buffer (no base, a literal base, 64-bit
+    accesses at a 4-byte stride), 64-bit accesses at their own stride, ds offsets (unsupported),
+    no barrier and two barriers"""
+    import os
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    base = open(os.path.join(g, "lds_exchange.s"), "rb").read()
+    files = [
+        base.replace(b"    v_add_u32 v9, s10, v9\n    ds_read_b32", b"    ds_read_b32"),
+        base.replace(b"ds_read_b32 v9, v9\n", b"ds_read_b32 v9, v9 offset:4\n"),
+        base.replace(b"ds_write_b32 v8, v7\n", b"ds_write_b32 v8, v7 offset:8\n"),
+        base.replace(b"    s_waitcnt lgkmcnt(0)\n    s_barrier\n", b""),
+        base.replace(b"ds_write_b32 v8, v7", b"ds_write_b64 v8, v[6:7]").replace(
+            b"ds_read_b32 v9, v9", b"ds_read_b64 v[8:9], v9"),
+        base.replace(b"ds_write_b32 v8, v7", b"ds_write_b64 v8, v[6:7]").replace(
+            b"ds_read_b32 v9, v9", b"ds_read_b64 v[8:9], v9").replace(
+            b"v_lshlrev_b32 v8, 2, v0", b"v_lshlrev_b32 v8, 3, v0").replace(
+            b"v_lshlrev_b32 v9, 2, v9", b"v_lshlrev_b32 v9, 3, v9"),
+        base.replace(b"    v_add_u32 v8, s10, v8\n", b"    v_add_u32 v8, 0x100, v8\n"),
+        base.replace(b"    s_barrier\n", b"    s_barrier\n    s_barrier\n"),
     ]
     assert len(set(files)) == len(files)
     _check_text(dec, files)
