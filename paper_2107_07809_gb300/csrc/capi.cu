@@ -602,7 +602,8 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   uint32_t* ovl = W.get<uint32_t>("emit_overflow", (size_t)NS2 + 1);
   CK(cudaMemsetAsync(&tot[13], 0, 4, s));
   // one thread per statement while staging (measured faster than a warp per
-  // statement); one warp per statement for the few long ones redone in place
+  // statement on large batches; a small batch takes a warp per statement, for
+  // latency); one warp per statement for the few long ones redone in place
   uint32_t* skey = W.get<uint32_t>("sub_key", (size_t)NS2 + 1);
   uint32_t* sorder = W.get<uint32_t>("sub_order", (size_t)NS2 + 1);
   uint32_t* shist = W.get<uint32_t>("sub_hist", shape_buckets() + 1);
@@ -611,7 +612,8 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   static_assert(sizeof(uint4) == kPRecBytes, "one uint4 per print record");
   launch_print_records(b, s);
   ktime(KT_ITEMS, 0, s);
-  launch_items(b, items, sitem, sub0, prank, plist, NS2, sorder, ilen, ioff, stage, ovl, &tot[13], 0, s);
+  launch_items(b, items, sitem, sub0, prank, plist, NS2, sorder, ilen, ioff, stage, ovl, &tot[13],
+               NS2 <= kSmallBatchStmts ? 5u : 0u, s);
   ktime(KT_ITEMS, 1, s);
   if (NS2) launch_scan(ilen, ioff, NS2, 0, false, sc2, &tot[11], b.err, s);
   CK(cudaGetLastError());

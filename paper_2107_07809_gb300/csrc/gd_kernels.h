@@ -238,6 +238,11 @@ void launch_items_place(const Item* stage, const uint32_t* stage_off, uint32_t K
                         const uint32_t* item_cnt, const uint32_t* item_base, Item* items, cudaStream_t s);
 constexpr uint32_t kPRecBytes = 16;  // size of a print record (k_emit.cu)
 constexpr uint32_t kEmitSlot = 1024;  // staging bytes per emission sub-item
+// A batch of at most this many statements prints one statement per warp (lane 0
+// works) instead of one per thread: the warps then fit on the GPU at once, and a
+// warp no longer runs the printing paths of 32 different statements one after
+// another, which sets the latency of a small batch.
+constexpr uint32_t kSmallBatchStmts = 4096;
 void launch_print_list(Batch& b, uint32_t* flag, const uint32_t* rank, uint32_t* list, int phase, cudaStream_t s);
 void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* prank, uint32_t* weight,
                      const uint32_t* sub0, uint32_t* sub_item, uint32_t NS2, int phase, cudaStream_t s);

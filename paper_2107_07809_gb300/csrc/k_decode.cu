@@ -1,11 +1,11 @@
 // k_decode.cu — configuration, instruction decoding and control-flow graphs.
 //
-// S3 (configuration, Listings 1 and 3): one thread per kernel reads its
-//    .config rows: dims, .cws, register counts, .useargs and the .arg table
-//    (8-byte settings slots in declaration order; "_."-names are hidden).
+// S3 (configuration, Listings 1 and 3): a warp per kernel reads its .config
+//    rows, one row per lane: dims, .cws, register counts, .useargs and the .arg
+//    table (8-byte settings slots in declaration order; "_."-names are hidden).
 // S4 (decoding, prefix_root_suffix names of "The body extraction"): one thread
 //    per instruction row produces a fixed 32-byte record; mnemonics are found
-//    through an FNV-1a hash table held in constant memory.
+//    through an FNV-1a hash table in global memory.
 // S5 (CFG, "Search for control structures"): leaders by flags, block ids by a
 //    device-wide scan, block table by one thread per block.
 // S6 (logical CFG, Fig. 4/5): the exec-mask if / if-else forms are matched by
@@ -133,149 +133,209 @@ __device__ __forceinline__ void trim(const uint8_t*& p, const uint8_t*& e) {
   while (e > p && is_space(e[-1])) --e;
 }
 
-__global__ void k_config(const __grid_constant__ Batch b) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+// What one configuration row sets: flags of the fields it assigns, their
+// values, and an argument record for an .arg row with at least three fields.
+enum : uint32_t {
+  CF_DIMS = 1, CF_CWS0 = 2, CF_SGPRS = 16, CF_VGPRS = 32, CF_USEARGS = 64, CF_ARG = 128, CF_BAD = 256
+};
+struct CfgRow {
+  uint32_t set;  // CF_* bits (CF_CWS0 << d for .cws component d)
+  uint32_t dims, cws[3], regs;
+  ArgRec a;
+};
+
+__device__ void config_row(const Batch& b, uint32_t l, CfgRow& r) {
+  const uint8_t* T = b.text;
+  r.set = 0;
+  const uint8_t* p = T + b.line_start[l];
+  const uint8_t* e = T + b.line_start[l + 1] - 1;
+  trim(p, e);
+  const uint8_t* t = p;
+  while (t < e && !is_space(*t)) ++t;
+  const uint8_t* w1 = t;
+  while (w1 < e && is_space(*w1)) ++w1;
+  const uint8_t* w1e = w1;
+  while (w1e < e && !is_space(*w1e)) ++w1e;
+  if (tok_eq(p, t, ".dims") || tok_eq(p, t, "dims")) {
+    if (w1 == w1e) { r.set = CF_BAD; return; }
+    r.set = CF_DIMS;
+    r.dims = (uint32_t)(w1e - w1);
+    if (r.dims < 1 || r.dims > 3) r.set |= CF_BAD;
+  } else if (tok_eq(p, t, ".cws")) {
+    const uint8_t* q = p + 4;  // the row after ".cws"
+    for (int idx = 0; idx < 3; ++idx) {
+      const uint8_t* fe = q;
+      while (fe < e && *fe != ',') ++fe;
+      const uint8_t *a = q, *z = fe;
+      trim(a, z);
+      int64_t v;
+      bool hx;
+      if (!dparse_int(a, z, &v, &hx) || v < 1 || v > 1024) {
+        r.set |= CF_BAD;
+      } else {
+        r.set |= CF_CWS0 << idx;
+        r.cws[idx] = (uint32_t)v;
+      }
+      if (fe >= e) break;
+      q = fe + 1;
+    }
+  } else if (tok_eq(p, t, ".sgprsnum") || tok_eq(p, t, ".vgprsnum")) {
+    int64_t v;
+    bool hx;
+    if (w1 == w1e || !dparse_int(w1, w1e, &v, &hx) || v < 0 || v > 1024) { r.set = CF_BAD; return; }
+    r.set = p[1] == 's' ? CF_SGPRS : CF_VGPRS;
+    r.regs = (uint32_t)v;
+  } else if (tok_eq(p, t, ".useargs")) {
+    r.set = CF_USEARGS;
+  } else if (tok_eq(p, t, ".arg")) {
+    // fields of the row after ".arg", split at commas and trimmed
+    const uint8_t* fs[6];
+    const uint8_t* fe[6];
+    int nf = 0;
+    const uint8_t* q = p + 4;
+    while (true) {
+      const uint8_t* z = q;
+      while (z < e && *z != ',') ++z;
+      const uint8_t *a = q, *y = z;
+      trim(a, y);
+      if (nf < 6) { fs[nf] = a; fe[nf] = y; }
+      ++nf;
+      if (z >= e) break;
+      q = z + 1;
+    }
+    if (nf < 3) { r.set = CF_BAD; return; }
+    ArgRec& a = r.a;
+    a.name_off = (uint32_t)(fs[0] - T);
+    a.name_len = (uint16_t)(fe[0] - fs[0]);
+    a.hidden = (fe[0] - fs[0]) >= 2 && fs[0][0] == '_' && fs[0][1] == '.';
+    a.gofs = 0;
+    if (a.hidden && fe[0] - fs[0] == 17) {
+      const char* g = "_.global_offset_";
+      bool m = true;
+      for (int i = 0; i < 16 && m; ++i) m = fs[0][i] == (uint8_t)g[i];
+      if (m && fs[0][16] >= '0' && fs[0][16] <= '2') a.gofs = (uint8_t)(1 + fs[0][16] - '0');
+    }
+    a.pointer = 0;
+    a.is_const = 0;
+    a.space = 0;
+    if (fe[2] > fs[2] && fe[2][-1] == '*') {
+      a.pointer = 1;
+      a.elem = type_code(fs[2], fe[2] - 1);
+      if (nf > 3) {
+        if (tok_eq(fs[3], fe[3], "constant")) a.space = 1;
+        else if (tok_eq(fs[3], fe[3], "local")) a.space = 2;
+      }
+      a.is_const = nf > 4 && tok_eq(fs[4], fe[4], "const");
+    } else {
+      a.elem = type_code(fs[2], fe[2]);
+    }
+    r.set = CF_ARG;
+  }
+}
+
+// S3, a warp per kernel.  Lane 0 reads the .kernel row (the name), finds the
+// file and the kernel's counts; the lanes then parse the configuration rows 32
+// at a time, one row each, and the rows' effects are combined in row order: a
+// field takes the value of the last row that sets it, an argument is appended
+// at its rank among the .arg rows before it (rows beyond kMaxArgs arguments
+// are errors), and any error marks the kernel bad.
+__global__ void __launch_bounds__(128) k_config(const __grid_constant__ Batch b) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   const uint8_t* T = b.text;
-  // name: second word of the .kernel row
-  {
-    const uint8_t* p = T + b.line_start[K.line];
-    const uint8_t* e = T + b.line_start[K.line + 1] - 1;
-    trim(p, e);
-    while (p < e && !is_space(*p)) ++p;
-    while (p < e && is_space(*p)) ++p;
-    const uint8_t* q = p;
-    while (q < e && !is_space(*q)) ++q;
-    K.name_off = (uint32_t)(p - T);
-    K.name_len = (uint32_t)(q - p);
-  }
-  // file
-  {
-    // last f with file_off[f] <= pos: empty files share their start with the next
-    // file, so this is the (non-empty) file that holds the row
-    uint64_t pos = b.line_start[K.line];
-    uint32_t lo = 0, hi = b.F;
-    while (lo + 1 < hi) {
-      uint32_t mid = (lo + hi) >> 1;
-      if (b.file_off[mid] <= pos) lo = mid;
-      else hi = mid;
+  if (lane == 0) {
+    // name: second word of the .kernel row
+    {
+      const uint8_t* p = T + b.line_start[K.line];
+      const uint8_t* e = T + b.line_start[K.line + 1] - 1;
+      trim(p, e);
+      while (p < e && !is_space(*p)) ++p;
+      while (p < e && is_space(*p)) ++p;
+      const uint8_t* q = p;
+      while (q < e && !is_space(*q)) ++q;
+      K.name_off = (uint32_t)(p - T);
+      K.name_len = (uint32_t)(q - p);
     }
-    K.file = lo;
+    // file: last f with file_off[f] <= pos; empty files share their start with
+    // the next file, so this is the (non-empty) file that holds the row
+    {
+      uint64_t pos = b.line_start[K.line];
+      uint32_t lo = 0, hi = b.F;
+      while (lo + 1 < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (b.file_off[mid] <= pos) lo = mid;
+        else hi = mid;
+      }
+      K.file = lo;
+    }
+    K.n_instr = (k + 1 < b.K ? b.kh[k + 1].first_instr : b.I) - K.first_instr;
+    K.n_label = (k + 1 < b.K ? b.kh[k + 1].first_label : b.NL) - K.first_label;
+    K.first_pblock = K.n_pblock = K.first_lblock = K.n_lblock = 0;
+    K.partial = 0;
+    K.capped = 0;
+    K.nspill = 0;
+    K.entry_target = 0;
+    K.status = 0;
+    K.n_cfg = (k + 1 < b.K ? b.kh[k + 1].first_cfg : b.NC) - K.first_cfg;
   }
-  K.n_instr = (k + 1 < b.K ? b.kh[k + 1].first_instr : b.I) - K.first_instr;
-  K.n_label = (k + 1 < b.K ? b.kh[k + 1].first_label : b.NL) - K.first_label;
-  K.first_pblock = K.n_pblock = K.first_lblock = K.n_lblock = 0;
-  K.dims = 1;
-  K.cws[0] = K.cws[1] = K.cws[2] = 1;
-  K.sgprs = 104;
-  K.vgprs = 256;
-  K.useargs = 0;
-  K.nargs = 0;
-  K.nuser = 0;
-  K.bad = 0;
-  K.partial = 0;
-  K.capped = 0;
-  K.nspill = 0;
-  K.entry_target = 0;
-  K.status = 0;
+  const uint32_t first_cfg = K.first_cfg;
+  const uint32_t n_cfg = (k + 1 < b.K ? b.kh[k + 1].first_cfg : b.NC) - first_cfg;
   ArgRec* A = b.args + (size_t)k * kMaxArgs;
-  K.n_cfg = (k + 1 < b.K ? b.kh[k + 1].first_cfg : b.NC) - K.first_cfg;
-  // the configuration rows of this kernel, in line order
-  for (uint32_t c = K.first_cfg; c < K.first_cfg + K.n_cfg; ++c) {
-    const uint32_t l = b.cfg_line[c];
-    const uint8_t* p = T + b.line_start[l];
-    const uint8_t* e = T + b.line_start[l + 1] - 1;
-    trim(p, e);
-    const uint8_t* t = p;
-    while (t < e && !is_space(*t)) ++t;
-    const uint8_t* w1 = t;
-    while (w1 < e && is_space(*w1)) ++w1;
-    const uint8_t* w1e = w1;
-    while (w1e < e && !is_space(*w1e)) ++w1e;
-    if (tok_eq(p, t, ".dims") || tok_eq(p, t, "dims")) {
-      if (w1 == w1e) { K.bad = 1; continue; }
-      K.dims = (uint32_t)(w1e - w1);
-      if (K.dims < 1 || K.dims > 3) K.bad = 1;
-    } else if (tok_eq(p, t, ".cws")) {
-      const uint8_t* q = p + 4;  // the row after ".cws"
-      int idx = 0;
-      while (idx < 3) {
-        const uint8_t* fe = q;
-        while (fe < e && *fe != ',') ++fe;
-        const uint8_t *a = q, *z = fe;
-        trim(a, z);
-        int64_t v;
-        bool hx;
-        if (!dparse_int(a, z, &v, &hx) || v < 1 || v > 1024) K.bad = 1;
-        else K.cws[idx] = (uint32_t)v;
-        ++idx;
-        if (fe >= e) break;
-        q = fe + 1;
-      }
-    } else if (tok_eq(p, t, ".sgprsnum") || tok_eq(p, t, ".vgprsnum")) {
-      int64_t v;
-      bool hx;
-      if (w1 == w1e || !dparse_int(w1, w1e, &v, &hx) || v < 0 || v > 1024) { K.bad = 1; continue; }
-      if (p[1] == 's') K.sgprs = (uint32_t)v;
-      else K.vgprs = (uint32_t)v;
-    } else if (tok_eq(p, t, ".useargs")) {
-      K.useargs = 1;
-    } else if (tok_eq(p, t, ".arg")) {
-      // fields of the row after ".arg", split at commas and trimmed
-      const uint8_t* fs[6];
-      const uint8_t* fe[6];
-      int nf = 0;
-      const uint8_t* q = p + 4;
-      while (true) {
-        const uint8_t* z = q;
-        while (z < e && *z != ',') ++z;
-        const uint8_t *a = q, *y = z;
-        trim(a, y);
-        if (nf < 6) { fs[nf] = a; fe[nf] = y; }
-        ++nf;
-        if (z >= e) break;
-        q = z + 1;
-      }
-      if (nf < 3) { K.bad = 1; continue; }
-      if (K.nargs >= (uint32_t)kMaxArgs) { K.bad = 1; continue; }
-      ArgRec a;
-      a.name_off = (uint32_t)(fs[0] - T);
-      a.name_len = (uint16_t)(fe[0] - fs[0]);
-      a.hidden = (fe[0] - fs[0]) >= 2 && fs[0][0] == '_' && fs[0][1] == '.';
-      a.gofs = 0;
-      if (a.hidden && fe[0] - fs[0] == 17) {
-        const char* g = "_.global_offset_";
-        bool m = true;
-        for (int i = 0; i < 16 && m; ++i) m = fs[0][i] == (uint8_t)g[i];
-        if (m && fs[0][16] >= '0' && fs[0][16] <= '2') a.gofs = (uint8_t)(1 + fs[0][16] - '0');
-      }
-      a.pointer = 0;
-      a.is_const = 0;
-      a.space = 0;
-      if (fe[2] > fs[2] && fe[2][-1] == '*') {
-        a.pointer = 1;
-        a.elem = type_code(fs[2], fe[2] - 1);
-        if (nf > 3) {
-          if (tok_eq(fs[3], fe[3], "constant")) a.space = 1;
-          else if (tok_eq(fs[3], fe[3], "local")) a.space = 2;
-        }
-        a.is_const = nf > 4 && tok_eq(fs[4], fe[4], "const");
+  uint32_t dims = 1, cws[3] = {1, 1, 1}, sgprs = 104, vgprs = 256, useargs = 0, nargs = 0, nuser = 0, bad = 0;
+  for (uint32_t c0 = 0; c0 < n_cfg; c0 += 32) {
+    CfgRow r;
+    r.set = 0;
+    if (c0 + lane < n_cfg) config_row(b, b.cfg_line[first_cfg + c0 + lane], r);
+    // last row (highest lane) that sets each field
+    const auto last = [&](uint32_t flag, uint32_t val, uint32_t& field) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, (r.set & flag) != 0);
+      if (m) field = __shfl_sync(0xFFFFFFFFu, val, 31 - __clz(m));
+    };
+    last(CF_DIMS, r.dims, dims);
+    last(CF_CWS0, r.cws[0], cws[0]);
+    last(CF_CWS0 << 1, r.cws[1], cws[1]);
+    last(CF_CWS0 << 2, r.cws[2], cws[2]);
+    last(CF_SGPRS, r.regs, sgprs);
+    last(CF_VGPRS, r.regs, vgprs);
+    if (__any_sync(0xFFFFFFFFu, (r.set & CF_USEARGS) != 0)) useargs = 1;
+    bool my_bad = (r.set & CF_BAD) != 0;
+    const unsigned am = __ballot_sync(0xFFFFFFFFu, (r.set & CF_ARG) != 0);
+    bool user = false;
+    if (r.set & CF_ARG) {
+      const uint32_t at = nargs + __popc(am & ((1u << lane) - 1u));
+      if (at >= (uint32_t)kMaxArgs) {
+        my_bad = true;
       } else {
-        a.elem = type_code(fs[2], fe[2]);
+        A[at] = r.a;
+        if (!r.a.hidden) {
+          user = true;
+          if (r.a.elem == TY_NONE) my_bad = true;
+        }
       }
-      if (!a.hidden) {
-        if (a.elem == TY_NONE) K.bad = 1;
-        ++K.nuser;
-      }
-      A[K.nargs++] = a;
     }
+    nuser += __popc(__ballot_sync(0xFFFFFFFFu, user));
+    nargs = min(nargs + (uint32_t)__popc(am), (uint32_t)kMaxArgs);
+    if (__any_sync(0xFFFFFFFFu, my_bad)) bad = 1;
+  }
+  if (lane == 0) {
+    K.dims = dims;
+    K.cws[0] = cws[0];
+    K.cws[1] = cws[1];
+    K.cws[2] = cws[2];
+    K.sgprs = sgprs;
+    K.vgprs = vgprs;
+    K.useargs = useargs;
+    K.nargs = nargs;
+    K.nuser = nuser;
+    K.bad = bad;
   }
 }
 
 void launch_config(Batch& b, cudaStream_t s) {
   if (!b.K) return;
-  k_config<<<(b.K + 127) / 128, 128, 0, s>>>(b);
+  k_config<<<(uint32_t)(((uint64_t)b.K * 32 + 127) / 128), 128, 0, s>>>(b);
   ++launch_counter();
 }
 
@@ -351,23 +411,26 @@ __device__ bool sig_ok(char s, uint32_t o) {
   return false;
 }
 
-// A warp decodes 32 consecutive instructions, one per lane.  Their lines lie
-// close together in the text, so the warp first copies the span they cover
+// A warp decodes `per` consecutive instructions, one per lane: 32, or 1 for a
+// small batch, where the lanes of a warp would otherwise run the parsing paths
+// of 32 different lines one after another on the critical path.  The lines
+// lie close together in the text, so the warp first copies the span they cover
 // into shared memory with coalesced 16-byte loads, and each lane then parses
 // its line from there: the byte-by-byte reads of the parser no longer touch 32
 // different cache lines per warp access.  A line beyond the staged span (a
 // kernel's configuration block between two instructions can make the span
 // long) is parsed straight from global memory.
 constexpr int DEC_THREADS = 256;
-constexpr uint32_t DEC_STAGE = 2048;  // staged text bytes per warp
+constexpr uint32_t DEC_STAGE = 2048;     // staged text bytes per warp
+constexpr uint32_t DEC_SMALL = 8192;     // at most this many instructions: one per warp
 
-__global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ Batch b) {
+__global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ Batch b, uint32_t per) {
   __shared__ __align__(16) uint8_t stage[DEC_THREADS / 32][DEC_STAGE];
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t w0 = i - lane;  // the warp's first instruction
-  if (w0 >= b.I) return;         // the whole warp
-  const uint32_t wl = b.I - w0 < 32u ? b.I - w0 : 32u;
+  const uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;  // the warp's first instruction
+  if (w0 >= b.I) return;  // the whole warp
+  const uint32_t i = w0 + lane;
+  const uint32_t wl = b.I - w0 < per ? b.I - w0 : per;
   const uint32_t line = lane < wl ? b.instr_line[i] : 0;
   const uint32_t l_first = __shfl_sync(0xFFFFFFFFu, line, 0), l_last = __shfl_sync(0xFFFFFFFFu, line, wl - 1);
   const uint64_t a0 = b.line_start[l_first] & ~15ull;
@@ -603,7 +666,9 @@ void launch_decode(Batch& b, ScanScratch sc, uint32_t* totals, cudaStream_t s) {
   const int T = 256;
   if (!b.I) return;
   ktime(KT_DECODE, 0, s);
-  k_decode<<<(b.I + DEC_THREADS - 1) / DEC_THREADS, DEC_THREADS, 0, s>>>(b);
+  const uint32_t per = b.I <= DEC_SMALL ? 1u : 32u;
+  const uint64_t warps = (b.I + per - 1) / per;
+  k_decode<<<(uint32_t)((warps * 32 + DEC_THREADS - 1) / DEC_THREADS), DEC_THREADS, 0, s>>>(b, per);
   ktime(KT_DECODE, 1, s);
   ++launch_counter();
   if (b.NL) {

@@ -1386,17 +1386,20 @@ void launch_subitems(Batch& b, const Item* items, uint32_t NI, const uint32_t* p
   }
 }
 
-// staged sub-item texts that fit their slot -> final place; a warp moves 32
-// consecutive sub-items, its lanes copying the bytes of one sub-item at a time
+// staged sub-item texts that fit their slot -> final place; a warp moves `per`
+// consecutive sub-items (32, or 1 for a small batch, where the copies of one
+// warp would be the critical path), its lanes copying the bytes of one
+// sub-item at a time
 __global__ void __launch_bounds__(256)
     k_compact(const uint8_t* __restrict__ stage, const uint32_t* __restrict__ item_len,
-              const uint32_t* __restrict__ item_off, uint32_t N, uint8_t* __restrict__ out) {
+              const uint32_t* __restrict__ item_off, uint32_t N, uint8_t* __restrict__ out, uint32_t per) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t s0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+  const uint32_t s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
   if (s0 >= N) return;
   const uint32_t mine = s0 + lane;
-  const uint32_t len = mine < N ? item_len[mine] : 0;
-  const uint32_t off = mine < N ? item_off[mine] : 0;
+  const bool own = lane < per && mine < N;
+  const uint32_t len = own ? item_len[mine] : 0;
+  const uint32_t off = own ? item_off[mine] : 0;
   unsigned todo = __ballot_sync(0xFFFFFFFFu, len > 0 && len <= kEmitSlot);
   while (todo) {
     const int src = __ffs(todo) - 1;
@@ -1554,7 +1557,9 @@ void launch_items(Batch& b, const Item* items, const uint32_t* sub_item, const u
 void launch_compact(const uint8_t* stage, const uint32_t* item_len, const uint32_t* item_off, uint32_t N,
                     uint8_t* out, cudaStream_t s) {
   if (!N) return;
-  k_compact<<<(N + 255) / 256, 256, 0, s>>>(stage, item_len, item_off, N, out);
+  const uint32_t per = N <= kSmallBatchStmts ? 1u : 32u;
+  const uint64_t warps = (N + per - 1) / per;
+  k_compact<<<(uint32_t)((warps * 32 + 255) / 256), 256, 0, s>>>(stage, item_len, item_off, N, out, per);
   ++launch_counter();
 }
 
