@@ -373,7 +373,13 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   uint32_t* line_start = W.get<uint32_t>("line_start", n + 2);
   uint64_t* tstat = W.get<uint64_t>("tile_status", std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)) + 64);
   uint32_t* counters = W.get<uint32_t>("counters", 4);
-  launch_line_scan(text, n, line_start, tstat, counters, err, s);
+  LineScan2 two{};
+  if (const uint32_t lt = line_scan_tiles(n) - 1; lt > kLsOnePass) {
+    two.masks = W.get<uint16_t>("ls_masks", (size_t)lt * (kLsTileBytes / 16));
+    two.counts = W.get<uint32_t>("ls_counts", lt);
+    two.prefix = W.get<uint32_t>("ls_prefix", lt);
+  }
+  launch_line_scan(text, n, line_start, tstat, counters, err, two, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ev[1], s));
   uint32_t L = 0;

@@ -179,8 +179,17 @@ struct Team {
 // k_text.cu
 uint32_t line_scan_tiles(uint64_t n);
 uint32_t scan_tiles(uint32_t n);
+// scratch of the two-pass S1 (texts of more than kLsOnePass 32 KiB tiles): per tile its newline
+// count, the exclusive scan of the counts, and 2048 16-bit newline masks
+constexpr uint32_t kLsOnePass = 256;
+constexpr uint32_t kLsTileBytes = 32768;  // the S1 tile (LS_TILE)
+struct LineScan2 {
+  uint16_t* masks;   // tiles * 2048
+  uint32_t* counts;  // tiles
+  uint32_t* prefix;  // tiles
+};
 void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uint64_t* tile_status,
-                      uint32_t* counters, uint32_t* err, cudaStream_t s);
+                      uint32_t* counters, uint32_t* err, const LineScan2& two, cudaStream_t s);
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t n, int op, bool inclusive, ScanScratch sc,
                  uint32_t* total_out, uint32_t* err, cudaStream_t s);
 void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, const uint64_t* file_off, uint32_t F,

@@ -1,6 +1,7 @@
-// k_linescan.cuh — the S1 newline scan (line tokenisation of Listing 2's
-// `for current_row in file`), shared by the batch pipeline (k_text.cu) and the
-// allocation-free entry point (k_noalloc.cu).
+// k_linescan.cuh — the single-pass S1 newline scan (line tokenisation of
+// Listing 2's `for current_row in file`): used by the batch pipeline for small
+// texts (k_text.cu, which takes a two-pass count/scan/write form for large
+// ones) and by the allocation-free entry point (k_noalloc.cu).
 //
 // One 512-thread block per 32 KiB tile, four blocks resident per SM: the tile
 // comes into shared memory with one bulk copy (cp.async.bulk + mbarrier).
@@ -8,12 +9,10 @@
 // single-pass decoupled look-back (warp 0) that gives each tile the number of
 // newlines before it only waits for tiles whose blocks already run.
 //
-// The look-back bounds a single-pass scan: a tile sums the aggregates of its
-// predecessors back to the nearest one with an inclusive prefix, so the
-// inclusive frontier moves one window (32 tiles) per round trip to L2.  The
-// tile is 32 KiB, not 16, to double the text that frontier covers per round
-// trip (a look-back by the whole block, 256 tiles per window, measured slower:
-// it waits for the slowest of 256 predecessors instead of 32).
+// The look-back bounds this form: every block waits until its predecessors
+// publish, so on large texts it reaches about a fifth of the copy bandwidth.
+// Widening the look-back window (256 predecessors per round trip) measured
+// slower, not faster; the two-pass form avoids the wait altogether.
 //
 // Within a tile each thread reads four 16-byte chunks at stride 8 KiB (thread
 // t, chunk k: bytes (k*512 + t)*16 ..+16), so the reads of a warp from shared
