@@ -59,12 +59,11 @@ static const OpName kOps[O_COUNT] = {
 };
 
 constexpr int kHash = 512;
+constexpr uint32_t kNameWords = 6;  // a mnemonic of at most 23 bytes, packed little-endian
 struct DecodeTables {
-  char names[O_COUNT][24];
-  char sigs[O_COUNT][12];
+  uint32_t namew[O_COUNT][kNameWords];  // the name's bytes, zero beyond its length
   uint8_t name_len[O_COUNT];
-  uint8_t nsig[O_COUNT];   // operand count of the signature
-  uint16_t ht[kHash];      // hash slot -> op + 1 (0 = empty)
+  uint16_t ht[kHash];  // hash slot -> op + 1 (0 = empty)
 };
 // in global memory, not the constant bank: lanes look up different mnemonics,
 // and the constant cache serves one address per access
@@ -73,7 +72,14 @@ __device__ DecodeTables c_tab;
 static const uint32_t kInlineFloatBits[8] = {0x3f000000u, 0xbf000000u, 0x3f800000u, 0xbf800000u,
                                              0x40000000u, 0xc0000000u, 0x40800000u, 0xc0800000u};
 __constant__ uint32_t c_fbits[8];
-__constant__ char c_ftext[8][5];
+
+// hash of a packed mnemonic (the same on host and device)
+__host__ __device__ __forceinline__ uint32_t name_hash(const uint32_t (&w)[kNameWords], uint32_t n) {
+  uint32_t h = n * 0x9E3779B1u;
+#pragma unroll
+  for (uint32_t k = 0; k < kNameWords; ++k) h = (h ^ w[k]) * 0x85EBCA77u;
+  return (h ^ (h >> 15)) & (kHash - 1);
+}
 
 void init_decode_tables() {
   static bool done = false;
@@ -81,33 +87,35 @@ void init_decode_tables() {
   DecodeTables t;
   memset(&t, 0, sizeof t);
   for (int i = 1; i < O_COUNT; ++i) {
-    size_t n = strlen(kOps[i].n);
-    memcpy(t.names[i], kOps[i].n, n);
+    const size_t n = strlen(kOps[i].n);
+    uint32_t w[kNameWords] = {0, 0, 0, 0, 0, 0};
+    for (size_t j = 0; j < n; ++j) w[j / 4] |= (uint32_t)(uint8_t)kOps[i].n[j] << (8 * (j % 4));
+    memcpy(t.namew[i], w, sizeof w);
     t.name_len[i] = (uint8_t)n;
-    memcpy(t.sigs[i], kOps[i].sig, strlen(kOps[i].sig));
-    size_t sl = strlen(kOps[i].sig);
-    t.nsig[i] = (uint8_t)(sl ? (sl + 1) / 2 : 0);
-    uint32_t h = fnv1a((const uint8_t*)kOps[i].n, (uint32_t)n) & (kHash - 1);
+    uint32_t h = name_hash(w, (uint32_t)n);
     while (t.ht[h]) h = (h + 1) & (kHash - 1);
     t.ht[h] = (uint16_t)(i + 1);
   }
   cudaMemcpyToSymbol(c_tab, &t, sizeof t);
-  const char ft[8][5] = {"0.5", "-0.5", "1.0", "-1.0", "2.0", "-2.0", "4.0", "-4.0"};
   cudaMemcpyToSymbol(c_fbits, kInlineFloatBits, sizeof kInlineFloatBits);
-  cudaMemcpyToSymbol(c_ftext, ft, sizeof ft);
   done = true;
 }
 
-__device__ int find_op(const uint8_t* p, const uint8_t* e) {
-  uint32_t n = (uint32_t)(e - p);
-  uint32_t h = fnv1a(p, n) & (kHash - 1);
+// the opcode whose mnemonic is exactly [p, p + n), or O_UNKNOWN
+__device__ int find_op(const uint8_t* p, uint32_t n) {
+  if (n == 0 || n >= 4 * kNameWords) return O_UNKNOWN;
+  uint32_t w[kNameWords] = {0, 0, 0, 0, 0, 0};
+  for (uint32_t j = 0; j < n; ++j) w[j >> 2] |= (uint32_t)p[j] << (8 * (j & 3));
+  uint32_t h = name_hash(w, n);
   for (int probe = 0; probe < kHash; ++probe) {
-    uint16_t v = c_tab.ht[h];
+    const uint16_t v = c_tab.ht[h];
     if (!v) return O_UNKNOWN;
-    int op = v - 1;
+    const int op = v - 1;
     if (c_tab.name_len[op] == n) {
+      const uint32_t* q = c_tab.namew[op];
       bool eq = true;
-      for (uint32_t i = 0; i < n && eq; ++i) eq = c_tab.names[op][i] == (char)p[i];
+#pragma unroll
+      for (uint32_t k = 0; k < kNameWords; ++k) eq &= q[k] == w[k];
       if (eq) return op;
     }
     h = (h + 1) & (kHash - 1);
@@ -344,12 +352,13 @@ void launch_config(Batch& b, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 __device__ bool parse_operand(const uint8_t* p, const uint8_t* e, uint32_t* word, bool* is_lit, uint32_t* lit) {
   *is_lit = false;
-  uint32_t n = (uint32_t)(e - p);
-  if (tok_eq(p, e, "vcc")) { *word = opw(TG_VCC, 2, 0); return true; }
-  if (tok_eq(p, e, "exec")) { *word = opw(TG_EXEC, 2, 0); return true; }
-  if (tok_eq(p, e, "off")) { *word = opw(TG_OFF, 0, 0); return true; }
-  if ((p[0] == 'v' || p[0] == 's') && n >= 2) {
-    uint32_t tag = p[0] == 'v' ? TG_VGPR : TG_SGPR;
+  const uint32_t n = (uint32_t)(e - p);
+  const uint8_t c0 = p[0];
+  if (n == 3 && c0 == 'v' && p[1] == 'c' && p[2] == 'c') { *word = opw(TG_VCC, 2, 0); return true; }
+  if (n == 4 && c0 == 'e' && p[1] == 'x' && p[2] == 'e' && p[3] == 'c') { *word = opw(TG_EXEC, 2, 0); return true; }
+  if (n == 3 && c0 == 'o' && p[1] == 'f' && p[2] == 'f') { *word = opw(TG_OFF, 0, 0); return true; }
+  if ((c0 == 'v' || c0 == 's') && n >= 2) {
+    const uint32_t tag = c0 == 'v' ? TG_VGPR : TG_SGPR;
     if (p[1] == '[') {
       const uint8_t *colon = nullptr, *close = nullptr;
       for (const uint8_t* q = p; q < e; ++q) {
@@ -365,24 +374,33 @@ __device__ bool parse_operand(const uint8_t* p, const uint8_t* e, uint32_t* word
       *word = opw(tag, (uint32_t)(bb - a + 1), (uint32_t)a);
       return true;
     }
-    for (const uint8_t* q = p + 1; q < e; ++q)
+    // a register number: decimal digits only (a '-' or hex prefix is no register)
+    uint32_t a = 0;
+    for (const uint8_t* q = p + 1; q < e; ++q) {
       if (*q < '0' || *q > '9') return false;
-    int64_t a;
-    bool hx;
-    if (!dparse_int(p + 1, e, &a, &hx) || a > 1023) return false;
-    *word = opw(tag, 1, (uint32_t)a);
+      a = a * 10 + (*q - '0');
+      if (a > 1023) return false;
+    }
+    *word = opw(tag, 1, a);
     return true;
   }
-  for (int i = 0; i < 8; ++i) {
-    const char* f = c_ftext[i];
-    if (tok_eq(p, e, f)) { *word = opw(TG_FCONST, 1, (uint32_t)i); return true; }
+  // the inline float constants 0.5, 1.0, 2.0, 4.0 and their negations (table order: value, then
+  // its negation)
+  if ((n == 3 || n == 4) && p[n - 2] == '.') {
+    const bool neg = c0 == '-';
+    if (n == 3 + (uint32_t)neg) {
+      const uint8_t d = p[neg], f = p[neg + 2];
+      int k = -1;
+      if (d == '0' && f == '5') k = 0;
+      else if (f == '0') k = d == '1' ? 1 : d == '2' ? 2 : d == '4' ? 3 : -1;
+      if (k >= 0) { *word = opw(TG_FCONST, 1, (uint32_t)(2 * k + neg)); return true; }
+    }
   }
   int64_t v;
   bool hex;
   if (dparse_int(p, e, &v, &hex)) {
-    bool anyx = false;
-    for (const uint8_t* q = p; q < e; ++q) anyx |= (*q == 'x' || *q == 'X');
-    if (!anyx && v >= -16 && v <= 64) {
+    // a parsed integer holds an 'x' only as its hex prefix
+    if (!hex && v >= -16 && v <= 64) {
       *word = opw(TG_ICONST, 1, (uint32_t)v & 0xFFFFFFu);
       return true;
     }
@@ -411,87 +429,106 @@ __device__ bool sig_ok(char s, uint32_t o) {
   return false;
 }
 
-// A warp decodes `per` consecutive instructions, one per lane: 32, or 1 for a
-// small batch, where the lanes of a warp would otherwise run the parsing paths
-// of 32 different lines one after another on the critical path.  The lines
-// lie close together in the text, so the warp first copies the span they cover
-// into shared memory with coalesced 16-byte loads, and each lane then parses
-// its line from there: the byte-by-byte reads of the parser no longer touch 32
-// different cache lines per warp access.  A line beyond the staged span (a
-// kernel's configuration block between two instructions can make the span
-// long) is parsed straight from global memory.
-constexpr int DEC_THREADS = 256;
-constexpr uint32_t DEC_STAGE = 2048;     // staged text bytes per warp
-constexpr uint32_t DEC_SMALL = 8192;     // at most this many instructions: one per warp
-
-__global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ Batch b, uint32_t per) {
-  __shared__ __align__(16) uint8_t stage[DEC_THREADS / 32][DEC_STAGE];
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;  // the warp's first instruction
-  if (w0 >= b.I) return;  // the whole warp
-  const uint32_t i = w0 + lane;
-  const uint32_t wl = b.I - w0 < per ? b.I - w0 : per;
-  const uint32_t line = lane < wl ? b.instr_line[i] : 0;
-  const uint32_t l_first = __shfl_sync(0xFFFFFFFFu, line, 0), l_last = __shfl_sync(0xFFFFFFFFu, line, wl - 1);
-  const uint64_t a0 = b.line_start[l_first] & ~15ull;
-  const uint64_t s1 = b.line_start[l_last + 1];
-  const uint32_t span = (uint32_t)(s1 - a0 < DEC_STAGE ? s1 - a0 : DEC_STAGE);  // within the text
-  uint8_t* st = stage[threadIdx.x >> 5];
-  if ((reinterpret_cast<uintptr_t>(b.text) & 15u) == 0) {
-    const uint32_t nv = span / 16;
-    for (uint32_t q = lane; q < nv; q += 32)
-      reinterpret_cast<uint4*>(st)[q] = reinterpret_cast<const uint4*>(b.text + a0)[q];
-    for (uint32_t j = nv * 16 + lane; j < span; j += 32) st[j] = b.text[a0 + j];
-  } else {
-    for (uint32_t j = lane; j < span; j += 32) st[j] = b.text[a0 + j];
+// Scanners over the bytes of one line; positions are offsets from a base.
+// BitScan serves a line staged in shared memory, through the warp's bitmaps of
+// space (' ', '\t', '\r') and comma bytes: a scan to the next token boundary
+// is a few word operations instead of a loop over bytes.  ByteScan is the same
+// over plain bytes, for a line the stage does not hold.
+struct BitScan {
+  const uint32_t* sp;  // bit j: byte j is a space
+  const uint32_t* cm;  // bit j: byte j is a comma
+  // first j in [from, to) whose bit in B (inverted by inv) is set, else to
+  __device__ __forceinline__ static uint32_t first(const uint32_t* B, uint32_t inv, uint32_t from, uint32_t to) {
+    if (from >= to) return to;
+    uint32_t w = from >> 5;
+    uint32_t x = (B[w] ^ inv) & (0xFFFFFFFFu << (from & 31));
+    while (!x) {
+      if ((++w << 5) >= to) return to;
+      x = B[w] ^ inv;
+    }
+    const uint32_t j = (w << 5) + (uint32_t)(__ffs(x) - 1);
+    return j < to ? j : to;
   }
-  __syncwarp();
-  if (lane >= wl) return;
-  uint32_t k = b.kcnt[line] - 1;
-  const KHdr& K = b.kh[k];
-  const uint64_t ls = b.line_start[line], le = b.line_start[line + 1] - 1;  // the line without its '\n'
-  const bool staged = le <= a0 + span;
-  const uint8_t* lp = staged ? st + (ls - a0) : b.text + ls;  // the line's first byte
-  const uint8_t* p = lp;
-  const uint8_t* e = lp + (le - ls);
-  trim(p, e);
-  const uint8_t* me = p;
-  while (me < e && !is_space(*me)) ++me;
+  __device__ __forceinline__ uint32_t space(uint32_t from, uint32_t to) const { return first(sp, 0u, from, to); }
+  __device__ __forceinline__ uint32_t nonspace(uint32_t from, uint32_t to) const { return first(sp, ~0u, from, to); }
+  __device__ __forceinline__ uint32_t comma(uint32_t from, uint32_t to) const { return first(cm, 0u, from, to); }
+  // one past the last non-space of [from, to), else from
+  __device__ __forceinline__ uint32_t trim_end(uint32_t from, uint32_t to) const {
+    if (from >= to) return from;
+    uint32_t w = (to - 1) >> 5;
+    uint32_t x = ~sp[w] & (0xFFFFFFFFu >> (31 - ((to - 1) & 31)));
+    while (!x) {
+      if ((w << 5) <= from) return from;
+      x = ~sp[--w];
+    }
+    const uint32_t j = (w << 5) + 31 - (uint32_t)__clz(x);
+    return j >= from ? j + 1 : from;
+  }
+};
+struct ByteScan {
+  const uint8_t* t;
+  __device__ __forceinline__ uint32_t space(uint32_t from, uint32_t to) const {
+    while (from < to && !is_space(t[from])) ++from;
+    return from;
+  }
+  __device__ __forceinline__ uint32_t nonspace(uint32_t from, uint32_t to) const {
+    while (from < to && is_space(t[from])) ++from;
+    return from;
+  }
+  __device__ __forceinline__ uint32_t comma(uint32_t from, uint32_t to) const {
+    while (from < to && t[from] != ',') ++from;
+    return from;
+  }
+  __device__ __forceinline__ uint32_t trim_end(uint32_t from, uint32_t to) const {
+    while (to > from && is_space(t[to - 1])) --to;
+    return to;
+  }
+};
+
+// The record of the instruction row [P0, E0) (positions of scanner S over the
+// bytes at t; the row without its '\n'): the mnemonic (first word), then the
+// operand fields split at commas, each trimmed; a field's first word is the
+// operand, its further words modifiers, of which offset:K is read.  A branch's
+// label operand is returned as its text position (ls = the text offset of P0)
+// and length.
+template <class S>
+__device__ __forceinline__ InstrRec decode_row(const S& sc, const uint8_t* t, uint32_t P0, uint32_t E0, uint64_t ls,
+                                               uint32_t* lbl_pos, uint32_t* lbl_len) {
+  const uint32_t p = sc.nonspace(P0, E0);
+  const uint32_t e = sc.trim_end(p, E0);
+  const uint32_t me = sc.space(p, e);  // the mnemonic
   InstrRec r;
-  r.op = (uint16_t)find_op(p, me);
+  r.op = (uint16_t)find_op(t + p, me - p);
   r.nops = 0;
   r.flags = r.op == O_UNKNOWN ? FL_UNSUPPORTED : 0;
   r.imm = 0;
   r.target = kNone;
   for (int q = 0; q < 5; ++q) r.opnd[q] = 0;
-  uint32_t lbl_pos = 0, lbl_len = 0;
+  *lbl_pos = 0;
+  *lbl_len = 0;
   const char* sig = c_sig[r.op];
-  const uint8_t* rp = me;
-  while (rp < e && is_space(*rp)) ++rp;
+  const uint32_t rp = sc.nonspace(me, e);
   if (r.op != O_S_WAITCNT && rp < e) {
     int nlit = 0;
-    const uint8_t* q = rp;
+    uint32_t q = rp;
     while (true) {
-      const uint8_t* z = q;
-      while (z < e && *z != ',') ++z;
-      const uint8_t *a = q, *y = z;
-      trim(a, y);
-      // sub-tokens: operand then modifiers
-      const uint8_t* s0 = a;
-      while (s0 < y && !is_space(*s0)) ++s0;
+      const uint32_t z = sc.comma(q, e);
+      const uint32_t a = sc.nonspace(q, z);
+      const uint32_t y = sc.trim_end(a, z);
+      const uint32_t s0 = sc.space(a, y);  // the operand is [a, s0), modifiers follow
       if (a == y) {
         r.flags |= FL_BAD;
       } else {
-        const uint8_t* m = s0;
+        uint32_t m = s0;
         while (m < y) {
-          while (m < y && is_space(*m)) ++m;
-          const uint8_t* me2 = m;
-          while (me2 < y && !is_space(*me2)) ++me2;
-          if (me2 - m >= 7 && m[0] == 'o' && m[1] == 'f' && m[2] == 'f' && m[3] == 's' && m[4] == 'e' &&
-              m[5] == 't' && m[6] == ':') {
+          m = sc.nonspace(m, y);
+          const uint32_t me2 = sc.space(m, y);
+          const uint8_t* w = t + m;
+          if (me2 - m >= 7 && w[0] == 'o' && w[1] == 'f' && w[2] == 'f' && w[3] == 's' && w[4] == 'e' && w[5] == 't' &&
+              w[6] == ':') {
             int64_t v;
             bool hx;
-            if (!dparse_int(m + 7, me2, &v, &hx) || v < 0) r.flags |= FL_BAD;
+            if (!dparse_int(w + 7, t + me2, &v, &hx) || v < 0) r.flags |= FL_BAD;
             else r.imm = (uint32_t)v;
           }
           m = me2;
@@ -499,10 +536,10 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ 
         uint32_t word = 0, lit = 0;
         bool is_lit = false, ok = true;
         if (sig[0] == 'L') {
-          lbl_pos = (uint32_t)(ls + (uint64_t)(a - lp));
-          lbl_len = (uint32_t)(s0 - a);
+          *lbl_pos = (uint32_t)(ls + (a - P0));
+          *lbl_len = s0 - a;
           word = opw(TG_LABEL, 0, 0);
-        } else if (!parse_operand(a, s0, &word, &is_lit, &lit)) {
+        } else if (!parse_operand(t + a, t + s0, &word, &is_lit, &lit)) {
           r.flags |= FL_BAD;
           ok = false;
         }
@@ -519,6 +556,66 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ 
       q = z + 1;
     }
   }
+  return r;
+}
+
+// A warp decodes `per` consecutive instructions, one per lane: 32, or 1 for a
+// small batch, where the lanes of a warp would otherwise run the parsing paths
+// of 32 different lines one after another on the critical path.  The lines
+// lie close together in the text, so the warp first copies the span they cover
+// into shared memory with coalesced 16-byte loads and marks its space and
+// comma bytes in two bitmaps (a ballot per 32 bytes); each lane then parses
+// its line from there.  A line beyond the staged span (a kernel's
+// configuration block between two instructions can make the span long) is
+// parsed straight from global memory.
+constexpr int DEC_THREADS = 256;
+constexpr uint32_t DEC_STAGE = 2048;     // staged text bytes per warp
+constexpr uint32_t DEC_SMALL = 8192;     // at most this many instructions: one per warp
+
+__global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ Batch b, uint32_t per) {
+  __shared__ __align__(16) uint8_t stage[DEC_THREADS / 32][DEC_STAGE];
+  __shared__ uint32_t s_sp[DEC_THREADS / 32][DEC_STAGE / 32], s_cm[DEC_THREADS / 32][DEC_STAGE / 32];
+  const uint32_t lane = threadIdx.x & 31u, wp = threadIdx.x >> 5;
+  const uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;  // the warp's first instruction
+  if (w0 >= b.I) return;  // the whole warp
+  const uint32_t i = w0 + lane;
+  const uint32_t wl = b.I - w0 < per ? b.I - w0 : per;
+  const uint32_t line = lane < wl ? b.instr_line[i] : 0;
+  const uint32_t l_first = __shfl_sync(0xFFFFFFFFu, line, 0), l_last = __shfl_sync(0xFFFFFFFFu, line, wl - 1);
+  const uint64_t a0 = b.line_start[l_first] & ~15ull;
+  const uint64_t s1 = b.line_start[l_last + 1];
+  const uint32_t span = (uint32_t)(s1 - a0 < DEC_STAGE ? s1 - a0 : DEC_STAGE);  // within the text
+  uint8_t* st = stage[wp];
+  if ((reinterpret_cast<uintptr_t>(b.text) & 15u) == 0) {
+    const uint32_t nv = span / 16;
+    for (uint32_t q = lane; q < nv; q += 32)
+      reinterpret_cast<uint4*>(st)[q] = reinterpret_cast<const uint4*>(b.text + a0)[q];
+    for (uint32_t j = nv * 16 + lane; j < span; j += 32) st[j] = b.text[a0 + j];
+  } else {
+    for (uint32_t j = lane; j < span; j += 32) st[j] = b.text[a0 + j];
+  }
+  __syncwarp();
+  for (uint32_t j0 = 0; j0 < span; j0 += 32) {
+    const uint8_t c = j0 + lane < span ? st[j0 + lane] : (uint8_t)'\n';
+    const unsigned sp = __ballot_sync(0xFFFFFFFFu, is_space(c)), cm = __ballot_sync(0xFFFFFFFFu, c == ',');
+    if (lane == 0) {
+      s_sp[wp][j0 >> 5] = sp;
+      s_cm[wp][j0 >> 5] = cm;
+    }
+  }
+  __syncwarp();
+  if (lane >= wl) return;
+  uint32_t k = b.kcnt[line] - 1;
+  const KHdr& K = b.kh[k];
+  const uint64_t ls = b.line_start[line], le = b.line_start[line + 1] - 1;  // the line without its '\n'
+  const bool staged = le <= a0 + span;
+  uint32_t lbl_pos, lbl_len;
+  InstrRec r;
+  if (staged)
+    r = decode_row(BitScan{s_sp[wp], s_cm[wp]}, st, (uint32_t)(ls - a0), (uint32_t)(le - a0), ls, &lbl_pos, &lbl_len);
+  else
+    r = decode_row(ByteScan{b.text + ls}, b.text + ls, 0u, (uint32_t)(le - ls), ls, &lbl_pos, &lbl_len);
+  const char* sig = c_sig[r.op];
   if (r.op && r.op != O_S_WAITCNT) {
     int want = sig_count(r.op);
     if (r.nops != want) r.flags |= FL_BAD;
@@ -545,7 +642,7 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ 
     if (tg == TG_SGPR && opay(o) + ocnt(o) > K.sgprs) r.flags |= FL_REGRANGE;
   }
   b.ins[i] = r;
-  b.branch_hash[i] = lbl_len ? fnv1a(lp + (lbl_pos - ls), lbl_len) : 0;
+  b.branch_hash[i] = lbl_len ? fnv1a(b.text + lbl_pos, lbl_len) : 0;
   b.branch_pos[i] = lbl_len ? lbl_pos : kNone;
   b.blen[i] = lbl_len;
   b.ikern[i] = k;
