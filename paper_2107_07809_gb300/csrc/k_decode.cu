@@ -101,11 +101,10 @@ void init_decode_tables() {
   done = true;
 }
 
-// the opcode whose mnemonic is exactly [p, p + n), or O_UNKNOWN
-__device__ int find_op(const uint8_t* p, uint32_t n) {
+// the opcode whose mnemonic, packed into w (zero beyond its n bytes), is that of a table entry,
+// or O_UNKNOWN
+__device__ int find_op(const uint32_t (&w)[kNameWords], uint32_t n) {
   if (n == 0 || n >= 4 * kNameWords) return O_UNKNOWN;
-  uint32_t w[kNameWords] = {0, 0, 0, 0, 0, 0};
-  for (uint32_t j = 0; j < n; ++j) w[j >> 2] |= (uint32_t)p[j] << (8 * (j & 3));
   uint32_t h = name_hash(w, n);
   for (int probe = 0; probe < kHash; ++probe) {
     const uint16_t v = c_tab.ht[h];
@@ -434,6 +433,8 @@ __device__ bool sig_ok(char s, uint32_t o) {
 // space (' ', '\t', '\r') and comma bytes: a scan to the next token boundary
 // is a few word operations instead of a loop over bytes.  ByteScan is the same
 // over plain bytes, for a line the stage does not hold.
+constexpr uint32_t DEC_STAGE = 2048;  // staged text bytes per warp
+constexpr uint32_t kStageWords = DEC_STAGE / 4;
 struct BitScan {
   const uint32_t* sp;  // bit j: byte j is a space
   const uint32_t* cm;  // bit j: byte j is a comma
@@ -452,6 +453,21 @@ struct BitScan {
   __device__ __forceinline__ uint32_t space(uint32_t from, uint32_t to) const { return first(sp, 0u, from, to); }
   __device__ __forceinline__ uint32_t nonspace(uint32_t from, uint32_t to) const { return first(sp, ~0u, from, to); }
   __device__ __forceinline__ uint32_t comma(uint32_t from, uint32_t to) const { return first(cm, 0u, from, to); }
+  // bytes [p, p + n) of the 16-byte aligned stage t, packed into words (n < 24): seven aligned
+  // word loads and funnel shifts, the same for every lane (no loop over the bytes)
+  __device__ __forceinline__ static void pack(const uint8_t* t, uint32_t p, uint32_t n, uint32_t (&w)[kNameWords]) {
+    const uint32_t* t32 = reinterpret_cast<const uint32_t*>(t);
+    const uint32_t w0 = p >> 2, sh = 8 * (p & 3);
+    uint32_t x[kNameWords + 1];
+#pragma unroll
+    for (uint32_t k = 0; k <= kNameWords; ++k) x[k] = w0 + k < kStageWords ? t32[w0 + k] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kNameWords; ++k) {
+      const uint32_t v = __funnelshift_r(x[k], x[k + 1], sh);
+      const uint32_t lo = 4 * k;  // bytes lo..lo+3 of the name
+      w[k] = n >= lo + 4 ? v : n <= lo ? 0u : v & (0xFFFFFFFFu >> (8 * (lo + 4 - n)));
+    }
+  }
   // one past the last non-space of [from, to), else from
   __device__ __forceinline__ uint32_t trim_end(uint32_t from, uint32_t to) const {
     if (from >= to) return from;
@@ -483,6 +499,11 @@ struct ByteScan {
     while (to > from && is_space(t[to - 1])) --to;
     return to;
   }
+  __device__ __forceinline__ static void pack(const uint8_t* t, uint32_t p, uint32_t n, uint32_t (&w)[kNameWords]) {
+#pragma unroll
+    for (uint32_t k = 0; k < kNameWords; ++k) w[k] = 0;
+    for (uint32_t j = 0; j < n; ++j) w[j >> 2] |= (uint32_t)t[p + j] << (8 * (j & 3));
+  }
 };
 
 // The record of the instruction row [P0, E0) (positions of scanner S over the
@@ -498,7 +519,12 @@ __device__ __forceinline__ InstrRec decode_row(const S& sc, const uint8_t* t, ui
   const uint32_t e = sc.trim_end(p, E0);
   const uint32_t me = sc.space(p, e);  // the mnemonic
   InstrRec r;
-  r.op = (uint16_t)find_op(t + p, me - p);
+  {
+    uint32_t w[kNameWords];
+    const uint32_t n = me - p < 4 * kNameWords ? me - p : 0u;  // longer: no mnemonic, O_UNKNOWN
+    S::pack(t, p, n, w);
+    r.op = (uint16_t)find_op(w, n);
+  }
   r.nops = 0;
   r.flags = r.op == O_UNKNOWN ? FL_UNSUPPORTED : 0;
   r.imm = 0;
@@ -569,7 +595,6 @@ __device__ __forceinline__ InstrRec decode_row(const S& sc, const uint8_t* t, ui
 // configuration block between two instructions can make the span long) is
 // parsed straight from global memory.
 constexpr int DEC_THREADS = 256;
-constexpr uint32_t DEC_STAGE = 2048;     // staged text bytes per warp
 constexpr uint32_t DEC_SMALL = 8192;     // at most this many instructions: one per warp
 
 __global__ void __launch_bounds__(DEC_THREADS) k_decode(const __grid_constant__ Batch b, uint32_t per) {
