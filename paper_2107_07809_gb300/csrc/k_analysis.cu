@@ -426,7 +426,7 @@ void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint3
 // slots (most instructions define one value, so a thread per slot left three
 // lanes in four idle).  First the forwarded sources of every node, then the
 // classes and memory matches, whose pattern walks read those sources.
-// fwd_d(v, r, 0) with its loop in line: only a whole pair (its two halves
+// fwd_n(v.N, r, 0) with its loop in line: only a whole pair (its two halves
 // forwarded separately) makes a recursive call
 __device__ __forceinline__ uint32_t fwd_inline(const KView& v, uint32_t r) {
   for (int step = 0; step < 512; ++step) {
@@ -441,7 +441,7 @@ __device__ __forceinline__ uint32_t fwd_inline(const KView& v, uint32_t r) {
     if (n.kind == N_PAIR) {
       if (part == PART_LO) { r = n.src[0]; continue; }
       if (part == PART_HI) { r = n.src[1]; continue; }
-      return fwd_d(v, r, 0);
+      return fwd_n(v.N, r, 0);
     }
     return r;
   }

@@ -51,11 +51,13 @@ __device__ __forceinline__ bool is_copy_node(const Node& n) {
 
 // a copy is the value it copies; the halves of a split pair are its sources;
 // a pair of the low and high part of one 64-bit value is that value
-static __device__ GD_MATCH_INLINE uint32_t fwd_d(const KView& v, uint32_t r, int depth) {
+// (a function of the kernel's node array alone, so that a caller's view need not be kept in local
+// memory for the call)
+static __device__ GD_MATCH_INLINE uint32_t fwd_n(const Node* N, uint32_t r, int depth) {
   for (int step = 0; step < 512 && depth < 64; ++step) {
     if (r == kTop) return kUndef;
     if (!r_node(r)) return r;
-    const Node& n = v.node(rid(r));
+    const Node& n = N[rid(r)];
     uint32_t part = rpart(r);
     if (is_copy_node(n) && part == PART_ENTIRE) {
       r = n.src[0];
@@ -64,7 +66,7 @@ static __device__ GD_MATCH_INLINE uint32_t fwd_d(const KView& v, uint32_t r, int
     if (n.kind == N_PAIR) {
       if (part == PART_LO) { r = n.src[0]; continue; }
       if (part == PART_HI) { r = n.src[1]; continue; }
-      uint32_t lo = fwd_d(v, n.src[0], depth + 1), hi = fwd_d(v, n.src[1], depth + 1);
+      uint32_t lo = fwd_n(N, n.src[0], depth + 1), hi = fwd_n(N, n.src[1], depth + 1);
       if ((r_node(lo) || r_leaf(lo)) && rpart(lo) == PART_LO && hi == ((lo & ~3u) | PART_HI)) return lo & ~3u;
       return r;
     }
@@ -72,6 +74,7 @@ static __device__ GD_MATCH_INLINE uint32_t fwd_d(const KView& v, uint32_t r, int
   }
   return r;
 }
+__device__ __forceinline__ uint32_t fwd_d(const KView& v, uint32_t r, int depth) { return fwd_n(v.N, r, depth); }
 __device__ __forceinline__ uint32_t fwd(const KView& v, uint32_t r) { return fwd_d(v, r, 0); }
 // forwarded source q of node n (n must live in v.N)
 __device__ __forceinline__ uint32_t nsrc(const KView& v, const Node& n, int q) {
