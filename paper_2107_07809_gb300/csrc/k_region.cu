@@ -45,7 +45,7 @@ __global__ void k_regions(const __grid_constant__ Batch b, uint32_t* __restrict_
   // early exits from loops: find them on the blocks as they are, then take the break blocks'
   // exit edges out of the graph (they print as `break`)
   uint32_t* brk = b.brk + base;
-  find_breaks(rd.B, cnd, rd.alive, n, brk);
+  find_breaks(rd.B, cnd, rd.alive, n, brk, stk);  // the search stack is free again: its scratch
   for (uint32_t x = 0; x < n; ++x)
     if (brk[x] != kNone && brk[x] != kBrkLatch) cnd[x] = 0;
   rd.brk = brk;

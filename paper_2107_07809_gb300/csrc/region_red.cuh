@@ -58,20 +58,33 @@ GD_HD inline uint32_t latch_header(const BlockRec* B, const uint8_t* cond, uint3
 GD_HD inline uint32_t latch_exit(const BlockRec* B, uint32_t l, uint32_t h) {
   return B[l].succ0 == h ? B[l].succ1 : B[l].succ0;
 }
-// live[x]: block x is reached from the entry (an unreached block breaks out of nothing)
-GD_HD inline void find_breaks(const BlockRec* B, const uint8_t* cond, const uint8_t* live, uint32_t n, uint32_t* brk) {
+// live[x]: block x is reached from the entry (an unreached block breaks out of nothing).
+// The loop that holds b is found for every b in one backward sweep (linear time; a forward search
+// from each block was quadratic on large CFGs): stk (n words of scratch) holds the latches after
+// b that can still be the first one whose header is at or before b.  Entering b, latch b + 1
+// joins and removes every latch whose header is at or after its own (b + 1 qualifies whenever
+// they do, and comes first); then the latches whose header lies after b leave for good (no
+// earlier block is inside them).  The top is the answer: the stack holds latches in increasing
+// order from the top and headers in decreasing order.
+GD_HD inline void find_breaks(const BlockRec* B, const uint8_t* cond, const uint8_t* live, uint32_t n, uint32_t* brk,
+                              uint32_t* stk) {
   for (uint32_t x = 0; x < n; ++x) brk[x] = kNone;
-  for (uint32_t b = 0; b < n; ++b) {
-    if (!live[b] || !cond[b] || latch_header(B, cond, b) != kNone) continue;
-    for (uint32_t l = b + 1; l < n; ++l) {
-      const uint32_t h = latch_header(B, cond, l);
-      if (h == kNone || h > b) continue;
-      const uint32_t E = latch_exit(B, l, h), s0 = B[b].succ0, s1 = B[b].succ1;
-      if ((s0 == E) != (s1 == E)) {
-        const uint32_t x = s0 == E ? s1 : s0;
-        if (x >= h && x <= l) brk[b] = l;
+  uint32_t sp = 0;
+  for (uint32_t b = n; b-- > 0;) {
+    if (b + 1 < n) {
+      const uint32_t h = latch_header(B, cond, b + 1);
+      if (h != kNone) {
+        while (sp && latch_header(B, cond, stk[sp - 1]) >= h) --sp;
+        stk[sp++] = b + 1;
       }
-      break;  // only the loop that holds b
+    }
+    while (sp && latch_header(B, cond, stk[sp - 1]) > b) --sp;
+    if (!sp || !live[b] || !cond[b] || latch_header(B, cond, b) != kNone) continue;
+    const uint32_t l = stk[sp - 1], h = latch_header(B, cond, l);  // only the loop that holds b
+    const uint32_t E = latch_exit(B, l, h), s0 = B[b].succ0, s1 = B[b].succ1;
+    if ((s0 == E) != (s1 == E)) {
+      const uint32_t x = s0 == E ? s1 : s0;
+      if (x >= h && x <= l) brk[b] = l;
     }
   }
   for (uint32_t b = 0; b < n; ++b)

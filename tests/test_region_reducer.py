@@ -156,3 +156,78 @@ def test_incremental_reducer_equals_restarting_search(reducer):
             reducible += 1
             assert root >= 0 and got == want, f"graph {g}: merge sequences differ"
     assert reducible > 500
+
+
+# ---- early exits: the linear-time finder against the rule written out ----------------------
+def _breaks_definition(s0, s1, live):
+    """The rule as stated: a two-way block b that is not a latch breaks out of the loop that holds
+    it (the first latch l after b whose header is at or before b) when one successor is that
+    loop's exit and the other stays in [header, l]; a latch with such a block is marked."""
+    n = len(s0)
+    cond = [s0[i] >= 0 and s1[i] >= 0 for i in range(n)]
+
+    def header(l):
+        if not cond[l] or (s0[l] <= l) == (s1[l] <= l):
+            return None
+        return s0[l] if s0[l] <= l else s1[l]
+
+    brk = [-1] * n
+    for b in range(n):
+        if not live[b] or not cond[b] or header(b) is not None:
+            continue
+        for l in range(b + 1, n):
+            h = header(l)
+            if h is None or h > b:
+                continue
+            e = s1[l] if s0[l] == h else s0[l]
+            if (s0[b] == e) != (s1[b] == e):
+                x = s1[b] if s0[b] == e else s0[b]
+                if h <= x <= l:
+                    brk[b] = l
+            break
+    for b in range(n):
+        if brk[b] >= 0:
+            brk[brk[b]] = -2
+    return brk
+
+
+def test_find_breaks_equals_the_forward_search(tmp_path):
+    if not shutil.which("nvcc"):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "breaks_host")
+    subprocess.check_call(["nvcc", "-O2", "-std=c++17", "--expt-relaxed-constexpr", "-x", "cu",
+                           os.path.join(HERE, "breaks_host.cu"), "-o", exe])
+    rng = random.Random(2107)
+    graphs = []
+    for g in range(400):
+        n = rng.randint(1, 70)
+        s0, s1, live = [], [], []
+        for b in range(n):
+            def target():
+                r = rng.random()
+                if r < 0.35:
+                    return b + 1 if b + 1 < n else -1
+                if r < 0.6:
+                    return rng.randint(0, b)  # at or before: a back edge
+                return rng.randint(b, n - 1) if b < n - 1 else -1
+            a, c = target(), (target() if rng.random() < 0.7 else -1)
+            if a == c:
+                c = -1
+            s0.append(a)
+            s1.append(c)
+            live.append(1 if rng.random() < 0.9 else 0)
+        graphs.append((s0, s1, live))
+    text = [str(len(graphs))]
+    for s0, s1, live in graphs:
+        text.append(str(len(s0)))
+        text += [f"{a} {c} {l}" for a, c, l in zip(s0, s1, live)]
+    out = subprocess.run([exe], input="\n".join(text) + "\n", capture_output=True, text=True, check=True).stdout
+    lines = out.strip().split("\n")
+    assert len(lines) == len(graphs)
+    breaks = 0
+    for (s0, s1, live), line in zip(graphs, lines):
+        got = [int(x) for x in line.split()]
+        want = _breaks_definition(s0, s1, live)
+        assert got == want
+        breaks += sum(1 for x in want if x >= 0)
+    assert breaks > 50  # the graphs do exercise the rule
