@@ -55,6 +55,7 @@ WORKLOADS = {
     "flatmulhi": (7, 10_000),  # the batch mix with FLAT accesses and double-suffix high multiplies
     "mixed": (8, 10_000),  # mixed uniform/divergent nesting, loops with early exits
     "lds": (9, 10_000),  # 1-D kernels exchanging values through a __local buffer around a barrier
+    "serving": (4, 1_000),  # the serving length mix (100..50,000 instructions) as one batch
 }
 METRIC = "GCN instrs decompiled/sec"
 # the library's event timing of single kernels (gcn_decomp_stage_times names)
@@ -315,13 +316,13 @@ def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0
                         continue
                     rs = set(ready)
                     waiting = [j for j in waiting if j not in rs]
-                    infos = [dec.job_info(j)["t_done"] for j in ready]
+                    t_done = dec.job_info_batch(ready)[:, 3].astype(np.int64)
                     raw, offs, _ = dec.fetch_batch_raw(ready)
-                    for q, j in enumerate(ready):
-                        r = id_to_req[j]
-                        done_ns[r] = infos[q]
-                        lat[r] = (infos[q] - arr_ns[r]) / 1e6
-                        if raw[offs[q]:offs[q + 1]].tobytes() != ref[which[r]]:
+                    rq = np.fromiter((id_to_req[j] for j in ready), np.int64, len(ready))
+                    done_ns[rq] = t_done
+                    lat[rq] = (t_done - arr_ns[rq]) / 1e6
+                    for q in range(len(ready)):
+                        if raw[offs[q]:offs[q + 1]].tobytes() != ref[which[rq[q]]]:
                             mism[0] += 1
                     seen += len(ready)
 

@@ -136,6 +136,14 @@ int gcn_decomp_poll(gcn_decomp_t *h, uint64_t *job_ids, size_t cap, size_t *n_ou
  * Errors: GCN_ENOJOB, GCN_EINVAL. */
 int gcn_decomp_job_info(gcn_decomp_t *h, uint64_t job_id, uint64_t *info, int cap);
 
+/* gcn_decomp_job_info for n jobs under one lock (infrastructure: a client
+ * that fetches thousands of jobs a second reads their times in one call):
+ * info[i * per .. i * per + per) receives the first per (1..5) values for
+ * job_ids[i], all zero for a job that is not known (never submitted, or
+ * already fetched).  Errors: GCN_EINVAL (h or a pointer NULL with n > 0, per
+ * outside 1..5); nothing is written then. */
+int gcn_decomp_job_info_batch(gcn_decomp_t *h, const uint64_t *job_ids, size_t n, uint64_t *info, int per);
+
 /* Intermediate arrays of a job, for parity checks: `which` selects
  *   0 instruction records (32 bytes each: u16 op, u8 nops, u8 flags, u32 imm,
  *     u32 target, u32 operand[5]),

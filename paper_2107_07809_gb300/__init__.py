@@ -112,6 +112,7 @@ def lib():
                                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32]
             L.gcn_decomp_poll.argtypes = [vp, ctypes.POINTER(u64), sz, ctypes.POINTER(sz), i32]
             L.gcn_decomp_job_info.argtypes = [vp, u64, ctypes.POINTER(u64), i32]
+            L.gcn_decomp_job_info_batch.argtypes = [vp, ctypes.POINTER(u64), sz, ctypes.POINTER(u64), i32]
             _lib = L
     return _lib
 
@@ -249,6 +250,18 @@ class Decompiler:
             raise GcnDecompError(n, "gcn_decomp_job_info")
         keys = ["state", "t_submit", "t_start", "t_done", "ir_resident"]
         return {keys[i]: int(v[i]) for i in range(n)}
+
+    def job_info_batch(self, jobs: list[int]):
+        """job_info for many jobs in one call: an (n, 5) uint64 numpy array (columns as job_info;
+        all zero for an unknown job)."""
+        import numpy as np
+
+        n = len(jobs)
+        ids = (ctypes.c_uint64 * max(n, 1))(*jobs)
+        out = np.zeros((n, 5), np.uint64)
+        _ck(lib().gcn_decomp_job_info_batch(self._h, ids, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 5),
+            "gcn_decomp_job_info_batch")
+        return out
 
     def decompile(self, texts: list[bytes]) -> list[tuple[str, int]]:
         ids = self.submit_batch(texts)

@@ -1301,6 +1301,26 @@ int gcn_decomp_job_info(gcn_decomp_t* h, uint64_t job_id, uint64_t* info, int ca
   return n;
 }
 
+int gcn_decomp_job_info_batch(gcn_decomp_t* h, const uint64_t* job_ids, size_t n, uint64_t* info, int per) {
+  if (!h || per < 1 || per > 5 || (n && (!job_ids || !info))) {
+    set_err("bad argument");
+    return GCN_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t* o = info + i * (size_t)per;
+    auto it = h->jobs.find(job_ids[i]);
+    if (it == h->jobs.end()) {
+      for (int q = 0; q < per; ++q) o[q] = 0;
+      continue;
+    }
+    const JobRec& j = it->second;
+    const uint64_t v[5] = {(uint64_t)j.state, j.t_submit, j.t_start, j.t_done, j.eng != nullptr};
+    for (int q = 0; q < per; ++q) o[q] = v[q];
+  }
+  return GCN_OK;
+}
+
 int gcn_decomp_fetch_ir(gcn_decomp_t* h, uint64_t job_id, int which, void* buf, size_t cap, size_t* len_out) {
   if (!h || which < 0 || which > 5) return GCN_EINVAL;
   std::unique_lock<std::mutex> lk(h->mu);
