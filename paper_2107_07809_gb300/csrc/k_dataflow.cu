@@ -532,7 +532,7 @@ __device__ __forceinline__ uint32_t src64(const NodeCtx& c, Node* nodes, uint32_
 }
 
 // nodes of instruction c.i (kernel-relative); `knodes` = the kernel's nodes
-__device__ void build_instr_nodes(const Batch& b, const KHdr& K, NodeCtx& c, Node* knodes) {
+__device__ __forceinline__ void build_instr_nodes(const Batch& b, const KHdr& K, NodeCtx& c, Node* knodes) {
   uint32_t gi = K.first_instr + c.i;
   Node* nodes = knodes + 4 * (size_t)c.i;
   const InstrRec& r = b.ins[gi];
@@ -673,9 +673,12 @@ __global__ void __launch_bounds__(32 * kNodeWarps)
     c.i = i;
     const uint32_t gi = K.first_instr + i;
     const bool late = mine && b.fused[gi];  // fused carry half
-    if (mine && !late) build_instr_nodes(b, K, c, knodes);
-    __syncwarp();
-    if (late) build_instr_nodes(b, K, c, knodes);
+    // two trips, one call site (in line: the context stays in registers): the other nodes, then the
+    // fused carry halves, which read their low half's node
+    for (int trip = 0; trip < 2; ++trip) {
+      if (mine && late == (trip == 1)) build_instr_nodes(b, K, c, knodes);
+      if (trip == 0) __syncwarp();
+    }
     // the row after the chunk: a register takes the chunk's last definition of it
     const uint32_t above = ~((2u << lane) - 1u);  // lanes after this one
     for (int t = 0; t < n; ++t) {
