@@ -522,7 +522,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   b.nsrcf = W.get<uint32_t>("nsrcf", 12ull * b.I + 12);
   b.mem_arg = W.get<uint32_t>("mem_arg", b.I + 1);
   b.mem_idx = W.get<uint32_t>("mem_idx", b.I + 1);
-  launch_node_cache(b, s);
+  launch_node_cache(b, W.get<uint8_t>("kviews", 2 * (size_t)b.K * kview_bytes() + 16), s);
   b.uses = W.get<uint32_t>("uses", 4ull * b.I + 4);
   b.nflag = W.get<uint8_t>("nflag", 4ull * b.I + 4);
   b.ntype = W.get<uint8_t>("ntype", 4ull * b.I + 4);

@@ -47,6 +47,8 @@ struct RowArrays {    // per line
 };
 
 // everything the per-kernel stages read and write (device pointers)
+struct KView;  // a kernel's view of the batch arrays (k_analysis.cuh)
+
 struct Batch {
   const uint8_t* text;
   uint64_t text_len;
@@ -125,6 +127,11 @@ struct Batch {
   // regions
   uint32_t* rg;                  // region records, 12 words per region
   uint32_t* brk;                 // NLB: per block, the latch an early exit leaves by, kBrkLatch or kNone
+  // per kernel, its view built once (k_make_views): with the forwarded sources only (for the class
+  // pass), and with every cache; threads take references into them instead of each building its
+  // own view in local memory
+  const KView* kview_sf;
+  const KView* kview;
   // emission
   uint32_t* kout_len;            // K (text length of each kernel incl. separator)
   uint32_t* kout_off;            // K (exclusive scan)
@@ -220,7 +227,8 @@ void launch_df_main(Batch& b, DfScratch& d, cudaStream_t s);
 
 // k_analysis.cu
 void launch_wl_size(Batch& b, uint32_t* sz, uint32_t* off, ScanScratch sc, uint32_t* total, cudaStream_t s);
-void launch_node_cache(Batch& b, cudaStream_t s);
+size_t kview_bytes();
+void launch_node_cache(Batch& b, void* views, cudaStream_t s);  // views: 2 * K * kview_bytes() bytes
 // a second stream for launches that may overlap those of the main stream, with
 // the events that fork work onto it and join it back
 struct SideStream {

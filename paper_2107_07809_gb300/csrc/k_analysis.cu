@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_co
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad || !T::mine(K, b.big_kernel)) return;
-  KView v = make_view(b, K, k);
+  const KView& v = b.kview[k];
   const size_t nb = 4 * (size_t)K.first_instr;
   uint32_t* uses = b.uses + nb;
   uint8_t* pu = b.phi_used + K.state_off;
@@ -222,7 +222,7 @@ __global__ void k_types_static(const __grid_constant__ Batch b, uint32_t* __rest
   const uint32_t k = b.ikern[gi];
   const KHdr& K = b.kh[k];
   if (K.bad) return;
-  const KView v = make_view(b, K, k);
+  const KView& v = b.kview[k];
   const size_t nb = 4 * (size_t)K.first_instr;
   uint8_t* nt = b.ntype + nb;
   const uint8_t* pt = b.phi_type + K.state_off;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_co
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad || !T::mine(K, b.big_kernel)) return;
-  KView v = make_view(b, K, k);
+  const KView& v = b.kview[k];
   const size_t nb = 4 * (size_t)K.first_instr;
   uint8_t* nt = b.ntype + nb;
   uint8_t* pt = b.phi_type + K.state_off;
@@ -321,7 +321,7 @@ __global__ void k_var_flag_nodes(const __grid_constant__ Batch b, uint32_t* __re
   const uint32_t k = b.ikern[gi];
   const KHdr& K = b.kh[k];
   if (K.bad) return;
-  const KView v = make_view(b, K, k);
+  const KView& v = b.kview[k];
   const size_t nb = 4 * (size_t)K.first_instr;
   const uint32_t id0 = 4 * (gi - K.first_instr);
   uint32_t* f = vflag + vbase(K) + (size_t)(bl + 1) * K.R;
@@ -481,6 +481,19 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// the views of every kernel, once: with the forwarded sources only, and with every cache
+__global__ void k_make_views(const __grid_constant__ Batch b, KView* __restrict__ vsf, KView* __restrict__ vall) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.K) return;
+  KView v = make_view(b, b.kh[k], k);  // b carries the caches' arrays here
+  vall[k] = v;
+  v.cc = nullptr;
+  v.ck = nullptr;
+  v.marg = nullptr;
+  v.midx = nullptr;
+  vsf[k] = v;
+}
+
 __global__ void __launch_bounds__(128)
     k_node_cache(const __grid_constant__ Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck,
                  const uint32_t* __restrict__ sf, uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
@@ -488,8 +501,7 @@ __global__ void __launch_bounds__(128)
   if (gi >= b.I) return;
   const uint32_t k = b.ikern[gi];
   const KHdr& K = b.kh[k];
-  KView v = make_view(b, K, k);  // b carries no caches here: only the forwarded sources
-  v.sf = sf + 12 * (size_t)K.first_instr;
+  const KView& v = b.kview_sf[k];  // the forwarded sources, no class caches yet
   const bool bad = K.bad;
   const uint32_t id0 = 4 * (gi - K.first_instr);
   uint32_t cls = 0, clk = 0;
@@ -515,8 +527,15 @@ __global__ void __launch_bounds__(128)
   midx[gi] = x;
 }
 
-void launch_node_cache(Batch& b, cudaStream_t s) {
+size_t kview_bytes() { return sizeof(KView); }
+
+void launch_node_cache(Batch& b, void* views, cudaStream_t s) {
   if (!b.I) return;
+  KView* vsf = static_cast<KView*>(views);
+  b.kview_sf = vsf;
+  b.kview = vsf + b.K;
+  k_make_views<<<(b.K + 127) / 128, 128, 0, s>>>(b, vsf, vsf + b.K);
+  ++launch_counter();
   Batch raw = b;
   raw.ncls = nullptr;
   ktime(KT_NODE_FWD, 0, s);

@@ -15,7 +15,6 @@ namespace gd {
 #endif
 
 struct KView {
-  const Batch* b;
   const KHdr* K;
   const Node* N;      // b.nodes + 4 * first_instr
   const ArgRec* A;    // b.args + k * kMaxArgs
@@ -33,7 +32,7 @@ struct KView {
 // a kernel view with the caches of the batch
 __device__ __forceinline__ KView make_view(const Batch& b, const KHdr& K, uint32_t k) {
   const size_t nb = 4 * (size_t)K.first_instr;
-  KView v{&b, &K, b.nodes + nb, b.args + (size_t)k * kMaxArgs, k, nullptr, nullptr, nullptr, nullptr, nullptr};
+  KView v{&K, b.nodes + nb, b.args + (size_t)k * kMaxArgs, k, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (b.ncls) {
     v.cc = b.ncls + nb;
     v.ck = b.nclsk + nb;

@@ -902,7 +902,7 @@ __global__ void k_copy_sets(const __grid_constant__ Batch b, const uint32_t* __r
   uint32_t m = 0;
   uint8_t cyc = 0;
   if (!K.bad && s != kNone) {
-    const KView v = make_view(b, K, k);
+    const KView& v = b.kview[k];
     const uint32_t p = g - K.first_lblock, R = K.R, off = b.cs_off[e];
     uint32_t* reg_of = b.cs_reg + off;  // candidates, then the printing order
     uint32_t* src_of = src_tmp + off;
@@ -1422,7 +1422,7 @@ __global__ void __launch_bounds__(128, 8) k_print_records(const __grid_constant_
   const KHdr& K = b.kh[k];
   if (K.bad) return;
   const size_t nb = 4 * (size_t)K.first_instr;
-  const KView v = make_view(b, K, k);
+  const KView& v = b.kview[k];
   const uint8_t* nt = b.ntype + nb;
   const int32_t* vo = b.var_of + nb;
   const uint8_t* vt = b.var_type + nb + K.state_off;
@@ -1493,7 +1493,7 @@ __global__ void __launch_bounds__(256)
       const BlockRec& B = b.lblocks[K.first_lblock + it.a];
       const uint32_t gi = pinstr[prank[K.first_instr + B.first] + (t - sub0[i])];
       if (b.lblock_of[gi] == it.a) {
-        const KView v = make_view(b, K, it.k);
+        const KView& v = b.kview[it.k];
         const int32_t* vo = b.var_of + 4 * (size_t)K.first_instr;
         const uint32_t id = 4 * (gi - K.first_instr);
         const Node& n = v.node(id);
