@@ -97,3 +97,24 @@ def test_million_kernel_stream_spread_sample():
     got, gst = _device_texts(v)
     assert len(got) == 10_000
     assert _mismatches(got, want) == [] and gst == wst
+
+
+def test_million_kernel_stream_every_kernel():
+    """Every one of the 1,000,000 kernels of the large-batch stream (5.46e8 instructions), in ten
+    chunks of 100,000 through the job service (packed submit, raw fetch), against the oracle in
+    parallel on the host cores: each chunk's whole output, its offsets and its statuses must be
+    identical."""
+    pkg.build()
+    p = gcngen.preset(2)
+    chunk = 100_000
+    with pkg.Decompiler(0, max_slots=chunk + 1024) as dec:  # a chunk's jobs all admitted at once
+        for c0 in range(0, 1_000_000, chunk):
+            b = gcngen.generate(p, chunk, seed=gcngen.SEED_BASE + 2, first=c0, threads=THREADS)
+            ids = dec.submit_packed(b.text, b.offsets)
+            assert len(ids) == chunk
+            want, woff, wst = oracle.decompile_batch(b.text, b.offsets, THREADS)  # while the GPU runs
+            raw, off, st = dec.fetch_batch_raw(ids)
+            assert len(off) == chunk + 1, f"chunk at {c0}"
+            assert np.array_equal(np.asarray(st, dtype=np.int64), np.asarray(wst, dtype=np.int64)), f"statuses, chunk at {c0}"
+            assert np.array_equal(np.asarray(off, dtype=np.uint64), np.asarray(woff, dtype=np.uint64)), f"offsets, chunk at {c0}"
+            assert np.array_equal(raw[: int(off[-1])], want[: int(woff[-1])]), f"text, chunk at {c0}"
