@@ -546,7 +546,11 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   ScanScratch scv = sc;
   if (scan_tiles((uint32_t)nvc) + 64 > std::max<uint64_t>(line_scan_tiles(n), scan_tiles((uint32_t)n + 1)) + 64)
     scv.status = W.get<uint64_t>("tile_status_var", scan_tiles((uint32_t)nvc) + 64);
-  launch_analysis(b, wl, bits, nbw, blk_kern, vflag, vpos, scv, h->fk, s);
+  // the kernels longest first, for the work queues of the per-kernel stages
+  KernelOrder ko{W.get<uint32_t>("kernel_order", (size_t)b.K + 1), W.get<uint32_t>("kernel_order_info", 4),
+                 W.get<uint32_t>("work_queue_heads", 8)};
+  launch_kernel_order(b, ko, s);
+  launch_analysis(b, wl, bits, nbw, blk_kern, vflag, vpos, scv, h->fk, ko, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ev[8], s));
   // S12, launched beside S7-S11, joined here

@@ -181,7 +181,34 @@ struct Team {
     return __syncthreads_or(p) != 0;
   }
   static __device__ __forceinline__ bool mine(const KHdr& K, uint32_t big) { return (K.n_instr >= big) != WARP; }
+  // the next kernel of a device work queue: entry *head (then advanced) of list[0..n), kNone when
+  // the list is exhausted; every thread of the team gets the same answer
+  static __device__ __forceinline__ uint32_t next(uint32_t* head, const uint32_t* list, uint32_t n) {
+    if (WARP) {
+      uint32_t i = 0;
+      if ((threadIdx.x & 31u) == 0) i = atomicAdd(head, 1u);
+      i = __shfl_sync(0xFFFFFFFFu, i, 0);
+      return i < n ? list[i] : kNone;
+    }
+    __shared__ uint32_t s_i;
+    if (threadIdx.x == 0) s_i = atomicAdd(head, 1u);
+    __syncthreads();
+    const uint32_t i = s_i;
+    __syncthreads();  // read by every thread before thread 0 takes the next one
+    return i < n ? list[i] : kNone;
+  }
 };
+
+// The kernels of a batch in the order the per-kernel work queues hand them out: those of the block
+// bucket (big_kernel instructions or more) first, then the rest, each by decreasing size (a
+// counting sort by the size's binary logarithm), so that the longest start first.  order[K],
+// info[0] = the number in the block bucket.
+struct KernelOrder {
+  uint32_t* order;
+  uint32_t* info;
+  uint32_t* heads;  // work-queue heads, zeroed before the launches that use them
+};
+void launch_kernel_order(const Batch& b, const KernelOrder& ko, cudaStream_t s);
 
 // k_text.cu
 uint32_t line_scan_tiles(uint64_t n);
@@ -236,7 +263,7 @@ struct SideStream {
   cudaEvent_t fork, join;
 };
 void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, const uint32_t* blk_kern,
-                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, SideStream fk, cudaStream_t s);
+                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, SideStream fk, const KernelOrder& ko, cudaStream_t s);
 
 // k_region.cu
 void launch_regions(Batch& b, uint32_t* work, uint32_t* stk, uint8_t* alive, uint8_t* cond, cudaStream_t s);

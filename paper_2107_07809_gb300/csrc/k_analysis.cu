@@ -10,6 +10,7 @@
 // the least fixed point.  A warp (short kernels) or a thread block (long
 // kernels) walks a kernel's nodes.
 #include "k_analysis.cuh"
+#include <algorithm>
 
 namespace gd {
 
@@ -30,12 +31,11 @@ __device__ __forceinline__ bool claim(uint32_t* bits, uint64_t g) {
 }
 
 template <bool WARP>
-__global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
-                        uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits) {
+__device__ __forceinline__ void reach_one(const Batch& b, uint32_t k, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
+                                          uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits) {
   using T = Team<WARP>;
   __shared__ uint32_t s_top[4], s_npl[4];
   const uint32_t wid = T::slot(), lane = T::tid(), TS = T::size();
-  uint32_t k = T::kid();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad || !T::mine(K, b.big_kernel)) return;
@@ -119,6 +119,20 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_reach(const __grid_co
   }
   T::sync();
   if (lane == 0) K.n_phis = s_npl[wid];
+}
+
+// a persistent team (a warp, or a block for the block bucket) per slot of the GPU, taking kernels
+// from the work queue of its bucket, longest first
+template <bool WARP>
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam)
+    k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
+            uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits,
+            const __grid_constant__ KernelOrder ko) {
+  const uint32_t nbig = ko.info[0];
+  const uint32_t* list = WARP ? ko.order + nbig : ko.order;
+  const uint32_t n = WARP ? b.K - nbig : nbig;
+  for (uint32_t k; (k = Team<WARP>::next(&ko.heads[WARP ? 1 : 0], list, n)) != kNone;)
+    reach_one<WARP>(b, k, wl_all, rbits, cbits, ibits, pbits);
 }
 
 // node flags from the reachability bitmaps (reached, used in another block,
@@ -241,10 +255,9 @@ __global__ void k_types_static(const __grid_constant__ Batch b, uint32_t* __rest
 }
 
 template <bool WARP>
-__global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_constant__ Batch b,
-                                                                 uint32_t* __restrict__ wl_all) {
+__device__ __forceinline__ void types_one(const Batch& b, uint32_t k, uint32_t* __restrict__ wl_all) {
   using T = Team<WARP>;
-  const uint32_t k = T::kid(), lane = T::tid(), TS = T::size();
+  const uint32_t lane = T::tid(), TS = T::size();
   if (k >= b.K) return;
   KHdr& K = b.kh[k];
   if (K.bad || !T::mine(K, b.big_kernel)) return;
@@ -290,6 +303,15 @@ __global__ void __launch_bounds__(WARP ? 128 : kBigTeam) k_types(const __grid_co
   }
   // still changing in the last allowed sweep: this kernel is not decompiled (FIXPOINT_CAP)
   if (lane == 0) K.capped = changed ? 1u : 0u;
+}
+
+template <bool WARP>
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam)
+    k_types(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, const __grid_constant__ KernelOrder ko) {
+  const uint32_t nbig = ko.info[0];
+  const uint32_t* list = WARP ? ko.order + nbig : ko.order;
+  const uint32_t n = WARP ? b.K - nbig : nbig;
+  for (uint32_t k; (k = Team<WARP>::next(&ko.heads[WARP ? 3 : 2], list, n)) != kNone;) types_one<WARP>(b, k, wl_all);
 }
 
 __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses, const uint8_t* fl, uint32_t id) {
@@ -548,8 +570,59 @@ void launch_node_cache(Batch& b, void* views, cudaStream_t s) {
   ++launch_counter();
 }
 
+// One block: a histogram of the kernels by (bucket, size class) in shared memory, its exclusive
+// scan (the class of the largest kernels first), then every kernel placed at its class's cursor.
+constexpr int kOrderClasses = 64;  // 32 size classes (binary logarithm) per bucket
+__global__ void __launch_bounds__(1024) k_kernel_order(const __grid_constant__ Batch b, const __grid_constant__ KernelOrder ko) {
+  __shared__ uint32_t cnt[kOrderClasses];
+  const uint32_t t = threadIdx.x;
+  if (t < kOrderClasses) cnt[t] = 0;
+  __syncthreads();
+  auto cls = [&](uint32_t k) {
+    const uint32_t n = b.kh[k].n_instr;
+    const uint32_t lg = 31u - (uint32_t)__clz(n | 1u);
+    return (n >= b.big_kernel ? 0u : 32u) + (31u - lg);
+  };
+  for (uint32_t k = t; k < b.K; k += blockDim.x) atomicAdd(&cnt[cls(k)], 1u);
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0, big = 0;
+    for (int c = 0; c < kOrderClasses; ++c) {
+      const uint32_t x = cnt[c];
+      cnt[c] = run;
+      run += x;
+      if (c == 31) big = run;
+    }
+    ko.info[0] = big;
+  }
+  __syncthreads();
+  for (uint32_t k = t; k < b.K; k += blockDim.x) ko.order[atomicAdd(&cnt[cls(k)], 1u)] = k;
+}
+
+void launch_kernel_order(const Batch& b, const KernelOrder& ko, cudaStream_t s) {
+  if (!b.K) return;
+  k_kernel_order<<<1, 1024, 0, s>>>(b, ko);
+  ++launch_counter();
+}
+
+// blocks of a team kernel resident on the whole GPU at once (the persistent grid), per device
+template <class F>
+static uint32_t resident_blocks(F kernel, int threads, int* cache) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = per_sm > 0 && sms > 0 ? per_sm * sms : 1;
+  }
+  return (uint32_t)cache[dev];
+}
+
 void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_words, const uint32_t* blk_kern,
-                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, SideStream fk, cudaStream_t s) {
+                     uint32_t* vflag, uint32_t* vpos, ScanScratch sc, SideStream fk, const KernelOrder& ko,
+                     cudaStream_t s) {
   if (!b.K) return;
   // four bitmaps: reached nodes, cross-block uses, join inputs (4I bits each), used joins (NS bits)
   uint64_t wn = (4ull * b.I + 63) / 32;
@@ -560,10 +633,14 @@ void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_word
   cudaMemsetAsync(b.uses, 0, sizeof(uint32_t) * 4ull * b.I, s);
   if (b.NS) cudaMemsetAsync(b.phi_used, 0, b.NS, s);
   cudaMemsetAsync(b.dyn_count, 0, sizeof(uint32_t) * b.K, s);
+  static int res_reach[2][64], res_types[2][64];
+  const uint32_t gw = std::min<uint32_t>((b.K + 3) / 4, resident_blocks(k_reach<true>, 128, res_reach[1]));
+  const uint32_t gb = std::min<uint32_t>(b.K, resident_blocks(k_reach<false>, kBigTeam, res_reach[0]));
+  cudaMemsetAsync(ko.heads, 0, 4 * sizeof(uint32_t), s);
   cudaEventRecord(fk.fork, s);
   cudaStreamWaitEvent(fk.side, fk.fork, 0);
-  k_reach<false><<<b.K, kBigTeam, 0, fk.side>>>(b, wl, rb, cb, ib, pb);
-  k_reach<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl, rb, cb, ib, pb);
+  k_reach<false><<<gb, kBigTeam, 0, fk.side>>>(b, wl, rb, cb, ib, pb, ko);
+  k_reach<true><<<gw, 128, 0, s>>>(b, wl, rb, cb, ib, pb, ko);
   cudaEventRecord(fk.join, fk.side);
   cudaStreamWaitEvent(s, fk.join, 0);
   if (b.I) {
@@ -573,8 +650,10 @@ void launch_analysis(Batch& b, uint32_t* wl, uint32_t* bits, uint64_t nbits_word
   }
   cudaEventRecord(fk.fork, s);
   cudaStreamWaitEvent(fk.side, fk.fork, 0);
-  k_types<false><<<b.K, kBigTeam, 0, fk.side>>>(b, wl);
-  k_types<true><<<(b.K + 3) / 4, 128, 0, s>>>(b, wl);
+  const uint32_t tw = std::min<uint32_t>((b.K + 3) / 4, resident_blocks(k_types<true>, 128, res_types[1]));
+  const uint32_t tb = std::min<uint32_t>(b.K, resident_blocks(k_types<false>, kBigTeam, res_types[0]));
+  k_types<false><<<tb, kBigTeam, 0, fk.side>>>(b, wl, ko);
+  k_types<true><<<tw, 128, 0, s>>>(b, wl, ko);
   cudaEventRecord(fk.join, fk.side);
   cudaStreamWaitEvent(s, fk.join, 0);
   launch_counter() += 4;
