@@ -80,6 +80,7 @@ def lib():
             L.gcngen_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                       ctypes.c_void_p, ctypes.c_void_p]
             L.gcngen_free.argtypes = [ctypes.c_void_p]
+            L.gcngen_truth.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             _lib = L
     return _lib
 
@@ -96,10 +97,12 @@ def preset(cfg: int, **over) -> Params:
 class Batch:
     """Concatenated kernel text plus per-kernel byte offsets and instruction counts."""
 
-    def __init__(self, text: np.ndarray, offsets: np.ndarray, ninstr: np.ndarray):
+    def __init__(self, text: np.ndarray, offsets: np.ndarray, ninstr: np.ndarray, truth: np.ndarray | None = None):
         self.text = text          # uint8[N]
         self.offsets = offsets    # uint64[n+1]
         self.ninstr = ninstr      # uint64[n]
+        # uint32[n]: dims (bits 0-1), and bit 2 + d set when get_global_id(d) adds the global offset
+        self.truth = truth
 
     def __len__(self):
         return len(self.ninstr)
@@ -142,6 +145,9 @@ def generate(params: Params | int, n: int, seed: int | None = None, first: int =
         rc = L.gcngen_copy(h, out.ctypes.data, out.nbytes, offs.ctypes.data, ni.ctypes.data)
         if rc != 0:
             raise RuntimeError(f"gcngen_copy failed: {rc}")
+        truth = np.empty(n, dtype=np.uint32)
+        if L.gcngen_truth(h, truth.ctypes.data) != 0:
+            raise RuntimeError("gcngen_truth failed")
     finally:
         L.gcngen_free(h)
-    return Batch(out[:size], offs, ni)
+    return Batch(out[:size], offs, ni, truth)

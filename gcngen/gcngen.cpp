@@ -1101,6 +1101,7 @@ struct Result {
   std::string text;
   std::vector<uint64_t> off;
   std::vector<uint64_t> ninstr;
+  std::vector<uint32_t> truth;  // per kernel: dims | gid_ofs[0] << 2 | gid_ofs[1] << 3
 };
 
 }  // namespace
@@ -1124,6 +1125,7 @@ void* gcngen_generate(const gcngen_params* p, uint64_t seed, uint64_t first, uin
   Result* R = new Result;
   std::vector<std::string> part(threads);
   std::vector<std::vector<uint64_t>> lens(threads), ni(threads);
+  std::vector<std::vector<uint32_t>> tr(threads);
   auto work = [&](int t) {
     uint64_t a = n * t / threads, b = n * (t + 1) / threads;
     for (uint64_t k = a; k < b; ++k) {
@@ -1131,6 +1133,7 @@ void* gcngen_generate(const gcngen_params* p, uint64_t seed, uint64_t first, uin
       std::string s = g.run();
       lens[t].push_back(s.size());
       ni[t].push_back(g.ninstr);
+      tr[t].push_back((uint32_t)g.dims | ((uint32_t)g.gid_ofs[0] << 2) | ((uint32_t)g.gid_ofs[1] << 3));
       part[t] += s;
     }
   };
@@ -1148,6 +1151,7 @@ void* gcngen_generate(const gcngen_params* p, uint64_t seed, uint64_t first, uin
     for (size_t i = 0; i < lens[t].size(); ++i) {
       R->off.push_back(R->off.back() + lens[t][i]);
       R->ninstr.push_back(ni[t][i]);
+      R->truth.push_back(tr[t][i]);
     }
   }
   return R;
@@ -1164,6 +1168,15 @@ int gcngen_copy(void* r, char* buf, uint64_t cap, uint64_t* offsets, uint64_t* n
   }
   if (offsets) memcpy(offsets, R->off.data(), R->off.size() * 8);
   if (ninstr) memcpy(ninstr, R->ninstr.data(), R->ninstr.size() * 8);
+  return 0;
+}
+// what the generator decided for each kernel, for ground-truth checks of the decompiled text:
+// bits 0-1 the number of NDRange dimensions, bit 2 + d set when the get_global_id(d) chain adds the
+// global offset (clear: the offset-free idiom)
+int gcngen_truth(void* r, uint32_t* out) {
+  Result* R = (Result*)r;
+  if (!R || !out) return -1;
+  memcpy(out, R->truth.data(), R->truth.size() * 4);
   return 0;
 }
 void gcngen_free(void* r) { delete (Result*)r; }

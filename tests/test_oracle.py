@@ -467,3 +467,32 @@ def test_brute_force_lds_preset():
         barriers += r.text.count("barrier(CLK_LOCAL_MEM_FENCE);")
         assert brute.check(txt, r.text, seed=i) is None, f"kernel {i}"
     assert barriers > 0
+
+
+# ---- generator ground truth: the system values the generator built ("Search for memory
+# accesses": the get_global_id chain with and without the global offset) -----------------------
+@pytest.mark.parametrize("cfg", [0, 1, 2, 5, 6, 7, 8])
+def test_global_ids_recovered_as_the_generator_built_them(cfg):
+    """Every kernel computes get_global_id(d) once per dimension (group id times work-group size
+    plus local id, the global offset added or not) and uses that register as an expression leaf.
+    The decompiled text must show each use as exactly that value: get_global_id(d) when the chain
+    adds the offset, the idiom (get_global_id(d) - get_global_offset(d)) when it does not, no
+    get_global_id of a dimension the kernel does not have, and no raw group or local id."""
+    b = gcngen.generate(cfg, 120, seed=gcngen.SEED_BASE + 300 + cfg)
+    uses = 0
+    for i in range(len(b)):
+        t = oracle.decompile(b.kernel(i)).text
+        truth = int(b.truth[i])
+        dims = truth & 3
+        assert "get_group_id(" not in t and "get_local_id(" not in t, f"kernel {i}"
+        for d in range(2):
+            gid, idiom = f"get_global_id({d})", f"(get_global_id({d}) - get_global_offset({d}))"
+            if d >= dims:
+                assert gid not in t, f"kernel {i}: dimension {d} of a {dims}-D kernel"
+                continue
+            if truth & (4 << d):
+                assert idiom not in t, f"kernel {i}: dimension {d} adds the offset"
+            else:
+                assert t.count(gid) == t.count(idiom), f"kernel {i}: dimension {d} is offset-free"
+            uses += t.count(gid)
+    assert uses >= 4 * len(b)  # the property is exercised (about 8 to 50 uses per kernel)
