@@ -101,7 +101,8 @@ class Batch:
         self.text = text          # uint8[N]
         self.offsets = offsets    # uint64[n+1]
         self.ninstr = ninstr      # uint64[n]
-        # uint32[n]: dims (bits 0-1), and bit 2 + d set when get_global_id(d) adds the global offset
+        # uint32[n, 4]: dims (bits 0-1) and bit 2 + d set when get_global_id(d) adds the global offset;
+        # the numbers of ifs, else parts and counted loops the generator emitted
         self.truth = truth
 
     def __len__(self):
@@ -145,7 +146,7 @@ def generate(params: Params | int, n: int, seed: int | None = None, first: int =
         rc = L.gcngen_copy(h, out.ctypes.data, out.nbytes, offs.ctypes.data, ni.ctypes.data)
         if rc != 0:
             raise RuntimeError(f"gcngen_copy failed: {rc}")
-        truth = np.empty(n, dtype=np.uint32)
+        truth = np.empty((n, 4), dtype=np.uint32)
         if L.gcngen_truth(h, truth.ctypes.data) != 0:
             raise RuntimeError("gcngen_truth failed")
     finally:

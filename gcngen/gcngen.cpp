@@ -175,6 +175,7 @@ struct Gen {
   int ifelse_left = 0;
   std::vector<Local> locals;
   bool gid_ofs[2] = {true, true};
+  uint32_t n_if = 0, n_else = 0, n_loop = 0;  // control statements emitted (ground truth)
 
   Gen(const gcngen_params& p, uint64_t seed, uint64_t k) : rng{mix(seed, k)}, P(p), kid(k) {}
 
@@ -777,6 +778,7 @@ struct Gen {
   }
 
   void stmt_if(int depth, uint32_t stop) {
+    ++n_if;
     divergent_cond();
     int e = exec_pair(depth);
     touchs(e, 2);
@@ -789,6 +791,8 @@ struct Gen {
   }
 
   void stmt_ifelse(int depth, uint32_t stop, int form) {
+    ++n_if;
+    ++n_else;
     divergent_cond();
     int e = exec_pair(depth);
     touchs(e, 2);
@@ -813,12 +817,14 @@ struct Gen {
   }
 
   void stmt_uif(int depth, uint32_t stop) {  // uniform if / if-else on the scalar argument
+    ++n_if;
     static const char* cc[4] = {"gt", "lt", "eq", "lg"};
     ins(f("s_cmp_%s_u32 s%d, %s", cc[rng.below(4)], s_n, I(rng.range(0, 40)).s().c_str()));
     int l = label();
     ins(f("s_cbranch_scc0 %s", lname(l).c_str()));
     block(depth + 1, share(stop, rng.range(10, 35)), 1);
     if (rng.chance(40)) {
+      ++n_else;
       int le = label();
       ins(f("s_branch %s", lname(le).c_str()));
       put_label(l);
@@ -831,6 +837,7 @@ struct Gen {
   }
 
   void stmt_loop(int depth, uint32_t stop) {
+    ++n_loop;
     int c = loop_sreg(depth);
     touchs(c);
     int trip = rng.range(1, P.trip_max);
@@ -841,6 +848,7 @@ struct Gen {
     // scalar branch leaves the loop (or skips to its latch) without touching the exec mask
     const bool early = P.p_break > 0 && rng.chance(P.p_break);
     if (early) {
+      ++n_if;  // the exit's test
       block(depth + 1, share(stop, rng.range(8, 25)), 1);
       const bool brk = rng.chance(50);
       if (rng.chance(50)) ins(f("s_cmp_eq_u32 s%d, %s", c, I(rng.range(0, trip)).s().c_str()));
@@ -1101,7 +1109,7 @@ struct Result {
   std::string text;
   std::vector<uint64_t> off;
   std::vector<uint64_t> ninstr;
-  std::vector<uint32_t> truth;  // per kernel: dims | gid_ofs[0] << 2 | gid_ofs[1] << 3
+  std::vector<uint32_t> truth;  // per kernel 4 words: dims | gid_ofs[0] << 2 | gid_ofs[1] << 3, ifs, elses, loops
 };
 
 }  // namespace
@@ -1134,6 +1142,9 @@ void* gcngen_generate(const gcngen_params* p, uint64_t seed, uint64_t first, uin
       lens[t].push_back(s.size());
       ni[t].push_back(g.ninstr);
       tr[t].push_back((uint32_t)g.dims | ((uint32_t)g.gid_ofs[0] << 2) | ((uint32_t)g.gid_ofs[1] << 3));
+      tr[t].push_back(g.n_if);
+      tr[t].push_back(g.n_else);
+      tr[t].push_back(g.n_loop);
       part[t] += s;
     }
   };
@@ -1151,7 +1162,7 @@ void* gcngen_generate(const gcngen_params* p, uint64_t seed, uint64_t first, uin
     for (size_t i = 0; i < lens[t].size(); ++i) {
       R->off.push_back(R->off.back() + lens[t][i]);
       R->ninstr.push_back(ni[t][i]);
-      R->truth.push_back(tr[t][i]);
+      for (int q = 0; q < 4; ++q) R->truth.push_back(tr[t][4 * i + q]);
     }
   }
   return R;
@@ -1170,9 +1181,10 @@ int gcngen_copy(void* r, char* buf, uint64_t cap, uint64_t* offsets, uint64_t* n
   if (ninstr) memcpy(ninstr, R->ninstr.data(), R->ninstr.size() * 8);
   return 0;
 }
-// what the generator decided for each kernel, for ground-truth checks of the decompiled text:
-// bits 0-1 the number of NDRange dimensions, bit 2 + d set when the get_global_id(d) chain adds the
-// global offset (clear: the offset-free idiom)
+// what the generator decided for each kernel, for ground-truth checks of the decompiled text, four
+// words per kernel: bits 0-1 the number of NDRange dimensions and bit 2 + d set when the
+// get_global_id(d) chain adds the global offset (clear: the offset-free idiom); then the numbers of
+// ifs (divergent, uniform, and the tests of early exits), of else parts, and of counted loops
 int gcngen_truth(void* r, uint32_t* out) {
   Result* R = (Result*)r;
   if (!R || !out) return -1;

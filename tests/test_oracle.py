@@ -482,7 +482,7 @@ def test_global_ids_recovered_as_the_generator_built_them(cfg):
     uses = 0
     for i in range(len(b)):
         t = oracle.decompile(b.kernel(i)).text
-        truth = int(b.truth[i])
+        truth = int(b.truth[i, 0])
         dims = truth & 3
         assert "get_group_id(" not in t and "get_local_id(" not in t, f"kernel {i}"
         for d in range(2):
@@ -496,3 +496,23 @@ def test_global_ids_recovered_as_the_generator_built_them(cfg):
                 assert t.count(gid) == t.count(idiom), f"kernel {i}: dimension {d} is offset-free"
             uses += t.count(gid)
     assert uses >= 4 * len(b)  # the property is exercised (about 8 to 50 uses per kernel)
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2, 5, 6, 7, 8, 9])
+def test_control_structure_as_the_generator_built_it(cfg):
+    """"Search for control structures" and the loop template, against what the generator emitted:
+    every divergent if / if-else (in all three exec-mask forms), uniform if / if-else and
+    early-exit test prints as exactly one `if (`, every counted loop as one `do {`; an else part
+    the program has prints as `} else {`, and an if without one may still print an else part
+    holding the join copies of its skip edge, so the generated else parts are a lower bound."""
+    b = gcngen.generate(cfg, 120, seed=gcngen.SEED_BASE + 500 + cfg)
+    stats = [0, 0, 0]
+    for i in range(len(b)):
+        r = oracle.decompile(b.kernel(i))
+        assert r.status == [0], f"kernel {i}"
+        n_if, n_else, n_loop = (int(x) for x in b.truth[i, 1:])
+        assert r.text.count("if (") == n_if, f"kernel {i}: ifs"
+        assert r.text.count("do {") == n_loop, f"kernel {i}: loops"
+        assert r.text.count("} else {") >= n_else, f"kernel {i}: else parts"
+        stats = [stats[0] + n_if, stats[1] + n_else, stats[2] + n_loop]
+    assert stats[0] > 0 and (cfg == 0 or stats[2] > 0)
