@@ -50,7 +50,7 @@ __device__ __forceinline__ uint32_t reg_of(const RegMap& M, uint32_t o, uint32_t
 }
 
 // definitions of kernel-relative instruction i (at most 4)
-__device__ int idefs(const Batch& b, const KHdr& K, const RegMap& M, uint32_t i, Def* d) {
+__device__ __forceinline__ int idefs(const Batch& b, const KHdr& K, const RegMap& M, uint32_t i, Def* d) {
   uint32_t gi = K.first_instr + i;
   if (b.ctl[gi] != C_NORMAL) return 0;
   const InstrRec& r = b.ins[gi];
@@ -361,14 +361,20 @@ __global__ void __launch_bounds__(32 * kDefWarps)
     for (int t = 0; t < 4; ++t) s_reg[wp][lane][t] = t < n ? d[t].reg : kNone;
     for (uint32_t q = lane; q < kDefBuckets; q += 32) s_mask[wp][q] = 0;
     __syncwarp();
-    for (int t = 0; t < n; ++t) atomicOr(&s_mask[wp][d[t].reg % kDefBuckets], 1u << lane);
+    // (loops of constant trip count over d, so that it stays in registers)
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < n) atomicOr(&s_mask[wp][d[t].reg % kDefBuckets], 1u << lane);
     __syncwarp();
     const uint32_t above = ~((2u << lane) - 1u);  // lanes after this one
-    for (int t = 0; t < n; ++t) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t >= n) continue;
       const uint32_t reg = d[t].reg;
       atomicOr(&db[reg >> 5], 1u << (reg & 31));
       bool last = true;
-      for (int u = t + 1; u < n; ++u) last = last && d[u].reg != reg;
+#pragma unroll
+      for (int u = t + 1; u < 4; ++u) last = last && (u >= n || d[u].reg != reg);
       int u;
       if (last && last_def(s_reg[wp], s_mask[wp], reg, above, &u) < 0) out[reg] = d[t].val;
     }
@@ -668,7 +674,9 @@ __global__ void __launch_bounds__(32 * kNodeWarps)
     }
     for (uint32_t q = lane; q < kDefBuckets; q += 32) s_mask[wp][q] = 0;
     __syncwarp();
-    for (int t = 0; t < n; ++t) atomicOr(&s_mask[wp][d[t].reg % kDefBuckets], 1u << lane);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < n) atomicOr(&s_mask[wp][d[t].reg % kDefBuckets], 1u << lane);
     __syncwarp();
     c.i = i;
     const uint32_t gi = K.first_instr + i;
@@ -681,10 +689,13 @@ __global__ void __launch_bounds__(32 * kNodeWarps)
     }
     // the row after the chunk: a register takes the chunk's last definition of it
     const uint32_t above = ~((2u << lane) - 1u);  // lanes after this one
-    for (int t = 0; t < n; ++t) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t >= n) continue;
       const uint32_t reg = d[t].reg;
       bool last = true;
-      for (int u = t + 1; u < n; ++u) last = last && d[u].reg != reg;
+#pragma unroll
+      for (int u = t + 1; u < 4; ++u) last = last && (u >= n || d[u].reg != reg);
       int u;
       if (last && last_def(s_reg[wp], s_mask[wp], reg, above, &u) < 0) row[reg] = d[t].val;
     }
