@@ -257,7 +257,9 @@ def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0
     the batch mix) through submit_batch / poll / fetch_batch; latency is from
     the scheduled arrival to the job's finish time.  Each rate runs for
     min_seconds of arrivals or min_requests requests, whichever is fewer
-    requests: 10 s at 1k/s and 10k/s, 100,000 requests (1 s) at 100k/s."""
+    requests: 10 s at 1k/s and 10k/s, 100,000 requests (1 s) at 100k/s.  Every result's length, and
+    the whole text of every 16th request, is compared with the pool decompiled in one batch (the
+    full comparison of every result is tests/test_gpu_serving.py's)."""
     params = gcngen.preset(4)
     pool = gcngen.generate(params, n_pool, seed=gcngen.SEED_BASE + 4, threads=os.cpu_count() or 4)
     texts = [pool.kernel(i) for i in range(n_pool)]
@@ -268,6 +270,7 @@ def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0
         ids = dec.submit_batch(texts)
         raw, offs, _ = dec.fetch_batch_raw(ids)
         ref = [raw[offs[i]:offs[i + 1]].tobytes() for i in range(n_pool)]
+        ref_len = np.array([len(r) for r in ref], dtype=np.int64)
         for rate in rates:
             rng = np.random.default_rng(2107078090 + rate)
             n = int(min(min_requests, rate * min_seconds))
@@ -278,6 +281,7 @@ def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0
             lat = np.zeros(n)
             done_ns = np.zeros(n, np.int64)
             mism = [0]
+            full = [0]
             t0 = time.monotonic_ns() + 20_000_000
             arr_ns = (t0 + arr * 1e9).astype(np.int64)
 
@@ -321,7 +325,12 @@ def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0
                     rq = np.fromiter((id_to_req[j] for j in ready), np.int64, len(ready))
                     done_ns[rq] = t_done
                     lat[rq] = (t_done - arr_ns[rq]) / 1e6
-                    for q in range(len(ready)):
+                    # every result's length; the whole text of every 16th request (copying and
+                    # comparing all of them in this thread would bound the rate measured)
+                    lens = np.diff(offs)
+                    mism[0] += int(np.count_nonzero(lens != ref_len[which[rq]]))
+                    for q in np.nonzero(rq % 16 == 0)[0]:
+                        full[0] += 1
                         if raw[offs[q]:offs[q + 1]].tobytes() != ref[which[rq[q]]]:
                             mism[0] += 1
                     seen += len(ready)
@@ -337,7 +346,8 @@ def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0
                 "rate_rps": rate, "requests": n, "arrival_window_s": float(arr[-1]),
                 "offered_instr_s": float(rate * ninstr[which].mean()),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "throughput_instr_s": served / span, "mismatches": mism[0]})
+                "throughput_instr_s": served / span, "mismatches": mism[0],
+                "compared": f"the length of every result, the whole text of {full[0]} (every 16th request)"})
     return out
 
 
