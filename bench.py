@@ -42,6 +42,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 # runtime parameters picked by paper_2107_07809_gb300/autotune.py on a GB300 (if present)
 TUNING = os.path.join(ROOT, "paper_2107_07809_gb300", "tuning", "gb300.tune")
+# the job service under a memory budget and latency targets takes its own tuning (fewer lanes,
+# smaller batches): the autotuner writes both files
+TUNING_SERVE = os.path.join(ROOT, "paper_2107_07809_gb300", "tuning", "gb300_serve.tune")
 
 import gcngen  # noqa: E402
 
@@ -84,8 +87,9 @@ def max_over_ranks(torch, value, device):
     return float(t.item())
 
 
-def tuning_file():
-    return TUNING if os.path.exists(TUNING) else None
+def tuning_file(serve=False):
+    t = TUNING_SERVE if serve else TUNING
+    return t if os.path.exists(t) else None
 
 
 def measured_peaks():
@@ -266,7 +270,7 @@ def serve(pkg, local, rates, n_pool=1000, min_requests=100_000, min_seconds=10.0
     ninstr = pool.ninstr.astype(np.int64)
     out = {"budget_bytes": budget, "pool": f"{n_pool} seeded requests (lengths 100..50000), cycled",
            "latency": "scheduled arrival -> job finished (CLOCK_MONOTONIC)", "rates": []}
-    with pkg.Decompiler(local, mem_budget_bytes=budget, tuning_file=tuning_file()) as dec:
+    with pkg.Decompiler(local, mem_budget_bytes=budget, tuning_file=tuning_file(serve=True)) as dec:
         ids = dec.submit_batch(texts)
         raw, offs, _ = dec.fetch_batch_raw(ids)
         ref = [raw[offs[i]:offs[i + 1]].tobytes() for i in range(n_pool)]
