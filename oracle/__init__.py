@@ -66,6 +66,7 @@ def lib():
             L.oracle_reduce_graph.argtypes = [i32, vp, vp, vp, i32]
             L.oracle_type_join.argtypes = [i32, i32]
             L.oracle_set_type_sweep_limit.argtypes = [ctypes.c_uint32]
+            L.oracle_set_class_depth.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -113,6 +114,13 @@ def set_type_sweep_limit(n: int = 0) -> None:
     kernel whose types still change in the last allowed sweep is not decompiled: status 3 and the
     text `/* not decompiled: fixed-point limit */` (a test hook for the capped path)."""
     lib().oracle_set_type_sweep_limit(n)
+
+
+def set_class_depth(d: int = -1) -> None:
+    """Depth below which a node gets no class in later calls (negative = the default, 4).  A test
+    hook: a class comes from operands at most three levels down, so any larger depth gives the
+    same output."""
+    lib().oracle_set_class_depth(d)
 
 
 def decompile_batch(text: np.ndarray, offsets: np.ndarray, threads: int = 1):

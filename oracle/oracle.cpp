@@ -1008,6 +1008,13 @@ void find_fusions(Kernel& K) {
     }
     int want = op == V_ADDC_CO_U32 ? V_ADD_CO_U32 : V_SUB_CO_U32;
     if (j < 0 || d.ins[j].op != want) continue;
+    // the two 64-bit operands take the instruction's slots 1 and 2, which leaves one
+    // slot (3) for a constant high source: two constants are left unfused
+    auto is_reg = [&](uint32_t o) {
+      uint32_t tg = tag_of(o);
+      return tg == TG_VGPR || tg == TG_SGPR || tg == TG_VCC;
+    };
+    if (!is_reg(d.ins[i].opnd[2]) && !is_reg(d.ins[i].opnd[3])) continue;
     uint32_t lo = K.R.v(pay_of(d.ins[j].opnd[0]));
     uint32_t hi = K.R.v(pay_of(d.ins[i].opnd[0]));
     if (lo == hi) continue;
@@ -1222,8 +1229,11 @@ void build_nodes(Kernel& K) {
           case BUFFER_STORE_DWORD: srcs.push_back(read32(r.opnd[0], 1)); break;
           case BUFFER_LOAD_DWORD: srcs.push_back(st[K.R.spill(r.imm / 4)]); break;
           case V_ADDC_CO_U32: case V_SUBB_CO_U32: {
-            uint32_t a = read32(r.opnd[2], 1), bsrc = read32(r.opnd[3], 2);
-            if (K.fusedv[i]) {
+            // fused: slots 1 and 2 hold the operand pairs, so the (at most one) constant
+            // high source sits in slot 3
+            bool f = K.fusedv[i] != 0;
+            uint32_t a = read32(r.opnd[2], f ? 3 : 1), bsrc = read32(r.opnd[3], f ? 3 : 2);
+            if (f) {
               const Node& lo = K.nodes[4 * (size_t)K.co_idx[i]];
               srcs.push_back(pair_of(lo.src[0], a, 1));
               srcs.push_back(pair_of(lo.src[1], bsrc, 2));
@@ -1355,11 +1365,19 @@ int log2_exact(int v) {
 
 bool is_64type(int t) { return t == T_LONG || t == T_ULONG || t == T_DOUBLE || t == T_TOP64; }
 
-ClsV classify(const Kernel& K, uint32_t r);
+// A class other than none comes from operands at most three levels below the value (the deepest
+// is get_global_id: group id * size + local id, the product, the group id), and an operand without
+// a class only keeps a pattern from matching; so a node reached more than g_class_depth levels
+// down has no class, which changes no class and bounds the recursion on long chains (a damaged
+// file can hold thousands of nested 64-bit pairs).  Leaves are classified at any depth.  The
+// bound is a test hook (oracle_set_class_depth) so that a test can show it changes nothing.
+int g_class_depth = 4;
 
-ClsV settings_load(const Kernel& K, const Node& n, uint32_t part, bool wide) {
+ClsV classify(const Kernel& K, uint32_t r, int d = 0);
+
+ClsV settings_load(const Kernel& K, const Node& n, uint32_t part, bool wide, int d) {
   ClsV v;
-  ClsV base = classify(K, fwd(K, n.src[0]));
+  ClsV base = classify(K, fwd(K, n.src[0]), d + 1);
   if (base.c == K_DISP) {
     // the dispatch packet: the dword at 0x0 holds the dimension count in its setup
     // field, the dwords at 0xc/0x10/0x14 the global size of dimension 0/1/2
@@ -1391,9 +1409,10 @@ ClsV settings_load(const Kernel& K, const Node& n, uint32_t part, bool wide) {
   return ClsV{K_ARG32, (int)slot};
 }
 
-ClsV classify(const Kernel& K, uint32_t r) {
+ClsV classify(const Kernel& K, uint32_t r, int d) {
   ClsV v;
   if (r == UNDEF || r == TOP) return ClsV{K_UNDEF, 0};
+  if (d > g_class_depth && is_node(r)) return v;
   if (is_leaf(r)) {
     uint32_t id = rid(r) & 0x0FFFFFFFu;
     uint32_t kind = id >> 8, k = id & 0xFF;
@@ -1408,19 +1427,19 @@ ClsV classify(const Kernel& K, uint32_t r) {
   uint32_t part = rpart(r);
   if (n.kind == N_CONST) return ClsV{K_CONST32, 0};
   if (n.kind == N_PAIR && part == P_ENTIRE) {
-    ClsV a = classify(K, fwd(K, n.src[0])), b = classify(K, fwd(K, n.src[1]));
+    ClsV a = classify(K, fwd(K, n.src[0]), d + 1), b = classify(K, fwd(K, n.src[1]), d + 1);
     if (a.c == K_CONST32 && b.c == K_CONST32) return ClsV{K_CONST64, 0};
     return v;
   }
-  if (n.kind == N_SLOAD64B) return settings_load(K, n, part, true);
+  if (n.kind == N_SLOAD64B) return settings_load(K, n, part, true, d);
   if (n.kind != N_OP) return v;
   switch (n.op) {
-    case S_LOAD_DWORDX2: case S_LOAD_DWORDX4: return settings_load(K, n, part, true);
-    case S_LOAD_DWORD: return settings_load(K, n, part, false);
+    case S_LOAD_DWORDX2: case S_LOAD_DWORDX4: return settings_load(K, n, part, true, d);
+    case S_LOAD_DWORD: return settings_load(K, n, part, false, d);
     default: break;
   }
   if (part != P_ENTIRE) return v;
-  auto cl = [&](int k) { return classify(K, fwd(K, n.src[k])); };
+  auto cl = [&](int k) { return classify(K, fwd(K, n.src[k]), d + 1); };
   auto cval = [&](int k) -> int64_t {
     uint32_t s = fwd(K, n.src[k]);
     if (!is_node(s) || K.nodes[rid(s)].kind != N_CONST || rpart(s) != P_ENTIRE) return -1;
@@ -2703,6 +2722,9 @@ void run_file(FileResult& F, const char* text, size_t len) {
 // C ABI of the oracle (used by tests and the benchmark's CPU baseline)
 // ============================================================================
 extern "C" {
+
+// test hook: the depth below which classify gives no class (the default 4 changes no class)
+void oracle_set_class_depth(int d) { g_class_depth = d < 0 ? 4 : d; }
 
 void* oracle_decompile(const char* text, uint64_t len) {
   FileResult* F = new FileResult;

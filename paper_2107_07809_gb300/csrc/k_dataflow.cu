@@ -176,6 +176,9 @@ __global__ void k_fusion(const __grid_constant__ Batch b) {
   }
   uint16_t want = r.op == O_V_ADDC_CO_U32 ? O_V_ADD_CO_U32 : O_V_SUB_CO_U32;
   if (j < 0 || b.ins[K.first_instr + j].op != want) return;
+  // the operand pairs take slots 1 and 2 and a constant high source slot 3: at most one constant
+  uint32_t t2 = otag(r.opnd[2]), t3 = otag(r.opnd[3]);
+  if (!(t2 == TG_VGPR || t2 == TG_SGPR || t2 == TG_VCC) && !(t3 == TG_VGPR || t3 == TG_SGPR || t3 == TG_VCC)) return;
   RegMap M{K.vgprs, K.sgprs};
   uint32_t lo = M.v(opay(b.ins[K.first_instr + j].opnd[0]));
   uint32_t hi = M.v(opay(r.opnd[0]));
@@ -563,8 +566,9 @@ __device__ __forceinline__ void build_instr_nodes(const Batch& b, const KHdr& K,
     case O_BUFFER_STORE_DWORD: s[ns++] = src32(c, nodes, r, r.opnd[0], 1); break;
     case O_BUFFER_LOAD_DWORD: s[ns++] = reg_now(c, c.M.spill(r.imm / 4)); break;
     case O_V_ADDC_CO_U32: case O_V_SUBB_CO_U32: {
-      uint32_t a = src32(c, nodes, r, r.opnd[2], 1), bb = src32(c, nodes, r, r.opnd[3], 2);
-      if (b.fused[gi]) {
+      const bool f = b.fused[gi] != 0;  // fused: a constant high source sits in slot 3
+      uint32_t a = src32(c, nodes, r, r.opnd[2], f ? 3 : 1), bb = src32(c, nodes, r, r.opnd[3], f ? 3 : 2);
+      if (f) {
         // the low half's sources, as its node (built earlier in this walk) holds them
         const Node& lo = knodes[4 * (size_t)b.co_idx[gi]];
         s[ns++] = make_pair(c, nodes, lo.src[0], a, 1);

@@ -268,3 +268,34 @@ def test_text_parity_label_cases(dec):
     only_long = t.replace(b".L1:", b".L10:")
     cross = t + t.replace(b".kernel k0", b".kernel k1").replace(b".L0:", b".M0:")
     _check_text(dec, [dup, pre, only_long, cross])
+
+
+def test_parity_fused_add_constant_high_sources(dec):
+    """64-bit adds whose carry half adds a constant: one constant high source fuses (the
+    constant takes the instruction's last operand slot), two stay split; and a damaged file
+    whose fused add reads unwritten registers."""
+    files = []
+    for hi in (b"0, v3", b"v3, 5", b"s4, v3", b"0, 1", b"-4.0, v3", b"0x12345, v3"):
+        files.append(b""".kernel k
+    .text
+        v_mov_b32 v2, 7
+        s_mov_b32 s4, 9
+        v_mov_b32 v3, 11
+        v_add_co_u32 v0, vcc, v2, s4
+        v_addc_co_u32 v1, vcc, """ + hi + b""", vcc
+        global_load_dword v5, v[0:1], off
+        global_store_dword v[0:1], v5, off
+        s_endpgm
+""")
+    files.append(b""".kernel k37
+    .text
+        v_add_co_u32 v14, vcc, v14, s16
+        v_addc_co_u32 v15, vcc, -4.0, v16, vcc
+        global_load_dwordx2 v[12:13], v[14:15], off
+        s_and_saveexec_b64 s[30:31], vcc
+        s_xor_b64 s[30:31], exec, s[30:31]
+        s_or_saveexec_b64 s[30:31], s[30:31]
+        s_xor_b64 exec, exec, s[30:31]
+        s_or_b64 exec, exec, s[30:31]""")
+    _check_ir(dec, files)
+    _check_text(dec, files)

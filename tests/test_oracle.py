@@ -516,3 +516,134 @@ def test_control_structure_as_the_generator_built_it(cfg):
         assert r.text.count("} else {") >= n_else, f"kernel {i}: else parts"
         stats = [stats[0] + n_if, stats[1] + n_else, stats[2] + n_loop]
     assert stats[0] > 0 and (cfg == 0 or stats[2] > 0)
+
+
+# ---- damaged input: the decompiler takes arbitrary disassembly text ---------------------------
+def _damaged(n, seed, cws=False):
+    import mutate
+
+    texts = []
+    for cfg in (0, 1, 5, 7, 8, 9):
+        over = dict(max_len=400)
+        if cws and cfg != 9:
+            over.update(cws0=8, cws1=4)
+        b = _batch(cfg, 30, **over)
+        texts += [b.kernel(i) for i in range(len(b))]
+    return mutate.mutants(texts, n, seed)
+
+
+def test_damaged_files_decompile_to_balanced_text():
+    """Generated files with lines missing, repeated or swapped, misspelled mnemonics and operands,
+    registers out of range, undefined and doubled labels, bad configuration values, CRLF endings,
+    comments and truncation: every file decompiles; a file whose worst kernel is a parse error says
+    so; every output has balanced braces and parentheses, and every OK one parses as OpenCL."""
+    st = [0, 0, 0]
+    for k, m in enumerate(_damaged(800, 2107)):
+        r = oracle.decompile(m)
+        assert r.worst in (0, 1, 2), f"file {k}"
+        st[r.worst] += 1
+        assert r.text.count("{") == r.text.count("}") and r.text.count("(") == r.text.count(")"), f"file {k}"
+        if r.worst == 2:
+            assert "not decompiled: parse error" in r.text, f"file {k}"
+    assert min(st) > 50  # every outcome is exercised
+
+
+def test_brute_force_on_damaged_files():
+    """Damaged files the oracle decompiles without inline assembly still compute what their
+    (damaged) assembly computes, on every file the interpreter and the evaluator can run (the
+    interpreter takes no comment rows and stops a program whose damaged address leaves every
+    buffer, the evaluator takes no pointer arithmetic on buffer arguments)."""
+    checked = 0
+    for k, m in enumerate(_damaged(300, 99, cws=True)):
+        r = oracle.decompile(m)
+        if r.worst != 0:
+            continue
+        try:
+            ocl_eval.parse(r.text)
+        except ocl_eval.ParseError:
+            continue
+        try:
+            err = brute.check(m.decode(errors="replace"), r.text, seed=k)
+        except (AssertionError, NotImplementedError, IndexError):
+            continue
+        if err is not None and "vacuous" in err:
+            continue
+        assert err is None, f"file {k}: {err}"
+        checked += 1
+    assert checked >= 40
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 3, 5, 6, 7, 8, 9])
+def test_class_depth_bound_changes_nothing(cfg):
+    """Classification stops four levels below a value (a class comes from operands at most three
+    levels down, and below that an operand can only keep a pattern from matching): with the bound
+    raised to 1,000 levels every generated kernel decompiles to the same text."""
+    b = _batch(cfg, 4 if cfg == 3 else 40, **({"max_len": 20000} if cfg == 3 else {}))
+    texts = [b.kernel(i) for i in range(len(b))]
+    want = [oracle.decompile(t).text for t in texts]
+    oracle.set_class_depth(1000)
+    try:
+        got = [oracle.decompile(t).text for t in texts]
+    finally:
+        oracle.set_class_depth()
+    assert got == want
+
+
+def _fused_add(hi_sources):
+    return f""".kernel k
+    .text
+        v_mov_b32 v2, 7
+        s_mov_b32 s4, 9
+        v_mov_b32 v3, 11
+        v_add_co_u32 v0, vcc, v2, s4
+        v_addc_co_u32 v1, vcc, {hi_sources}, vcc
+        global_load_dword v5, v[0:1], off
+        global_store_dword v[0:1], v5, off
+        s_endpgm
+"""
+
+
+@pytest.mark.parametrize("hi,want", [
+    # low halves 7 and 9 (v2, s4); high halves as written: the two 64-bit operands are
+    # hi << 32 | lo, folded to their values
+    ("0, v3", "(7UL + 47244640265UL)"),             # 0 << 32 | 7,  11 << 32 | 9
+    ("v3, 5", "(47244640263UL + 21474836489UL)"),   # 11 << 32 | 7,  5 << 32 | 9
+    ("s4, v3", "(38654705671UL + 47244640265UL)"),  # 9 << 32 | 7,  11 << 32 | 9
+])
+def test_fused_add_with_a_constant_high_source(hi, want):
+    """A 64-bit add whose high half adds an inline constant (as compilers write for a 32-bit
+    offset added to a pointer) fuses into one 64-bit add of the two register pairs; the value
+    of each operand is fixed by its halves."""
+    r = oracle.decompile(_fused_add(hi))
+    assert r.worst == 0
+    assert f"var0 = {want};" in r.text
+
+
+def test_fused_add_with_two_constant_high_sources_stays_split():
+    """Two constant high sources leave the carry half on its own (no slot is left for the second
+    constant); the low half is still the 32-bit sum."""
+    r = oracle.decompile(_fused_add("0, 1"))
+    assert "(7u + 9u)" in r.text and "UL" not in r.text
+
+
+def test_damaged_fused_add_is_not_self_referential():
+    """A damaged file whose carry half adds an inline float constant to a low half that reads a
+    register nothing wrote: every value is built from earlier ones (no variable is defined from
+    itself), so the decompilation is finite."""
+    asm = b""".kernel k37
+    .text
+        v_add_co_u32 v14, vcc, v14, s16
+        v_addc_co_u32 v15, vcc, -4.0, v16, vcc
+        global_load_dwordx2 v[12:13], v[14:15], off
+        s_and_saveexec_b64 s[30:31], vcc
+        s_xor_b64 s[30:31], exec, s[30:31]
+        s_or_saveexec_b64 s[30:31], s[30:31]
+        s_xor_b64 exec, exec, s[30:31]
+        s_or_b64 exec, exec, s[30:31]"""
+    oracle.set_class_depth(1000)
+    try:
+        r = oracle.decompile(asm)
+    finally:
+        oracle.set_class_depth()
+    # -4.0 is 0xc0800000 = 3229614080; the unwritten registers read as 0
+    assert "var0 = *((__global ulong *)((upsample(3229614080u, 0u) + upsample(0u, 0u))));" in r.text
