@@ -409,6 +409,7 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   sync_totals();
   b.K = h->h_tot[0];
   b.I = h->h_tot[1];
+  if (b.K <= kBlockPerKernelBatch) b.big_kernel = 0;  // every kernel its own thread block
   b.NL = h->h_tot[2];
   b.NC = h->h_tot[14];
   b.rowtype = ra.rowtype;

@@ -163,6 +163,9 @@ inline uint32_t walk_threads(uint32_t K) { return 32 * walk_warps(K); }
 // thread block (Team<false>); both launches cover every kernel and a team
 // leaves the kernels of the other bucket alone.
 constexpr int kBigTeam = 512;
+// A batch of at most this many kernels (one per SM) puts every kernel in the block bucket: the
+// teams then occupy no more than the GPU's SMs, and a block finishes a kernel's walks sooner.
+constexpr uint32_t kBlockPerKernelBatch = 152;
 
 template <bool WARP>
 struct Team {

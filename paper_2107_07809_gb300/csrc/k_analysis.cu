@@ -124,7 +124,7 @@ __device__ __forceinline__ void reach_one(const Batch& b, uint32_t k, uint32_t* 
 // a persistent team (a warp, or a block for the block bucket) per slot of the GPU, taking kernels
 // from the work queue of its bucket, longest first
 template <bool WARP>
-__global__ void __launch_bounds__(WARP ? 128 : kBigTeam)
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam, WARP ? 8 : 1)
     k_reach(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, uint32_t* __restrict__ rbits,
             uint32_t* __restrict__ cbits, uint32_t* __restrict__ ibits, uint32_t* __restrict__ pbits,
             const __grid_constant__ KernelOrder ko) {
@@ -230,7 +230,7 @@ __device__ __forceinline__ bool type_from_operands(const Node& n) {
 // equation has no unknowns): one thread per instruction types those of its four
 // slots and lists the others, whose type comes from their operands, in its
 // kernel's list for the iteration (the reachability work list, free again).
-__global__ void k_types_static(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all) {
+__global__ void __launch_bounds__(128, 12) k_types_static(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= b.I) return;
   const uint32_t k = b.ikern[gi];
@@ -306,7 +306,7 @@ __device__ __forceinline__ void types_one(const Batch& b, uint32_t k, uint32_t* 
 }
 
 template <bool WARP>
-__global__ void __launch_bounds__(WARP ? 128 : kBigTeam)
+__global__ void __launch_bounds__(WARP ? 128 : kBigTeam, WARP ? 8 : 1)
     k_types(const __grid_constant__ Batch b, uint32_t* __restrict__ wl_all, const __grid_constant__ KernelOrder ko) {
   const uint32_t nbig = ko.info[0];
   const uint32_t* list = WARP ? ko.order + nbig : ko.order;
@@ -333,7 +333,7 @@ __device__ __forceinline__ bool is_var_node(const KView& v, const uint32_t* uses
 __device__ __forceinline__ size_t vbase(const KHdr& K) { return (size_t)K.state_off + 4 * (size_t)K.first_instr; }
 
 // one thread per instruction over its four node slots
-__global__ void k_var_flag_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ vflag) {
+__global__ void __launch_bounds__(128, 12) k_var_flag_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ vflag) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= b.I) return;
   const uint32_t bl = b.lblock_of[gi];
@@ -475,19 +475,11 @@ __device__ __forceinline__ uint32_t fwd_inline(const KView& v, uint32_t r) {
 __device__ __forceinline__ Cls classify_node(const KView& v, uint32_t id) {
   const Node& n = v.node(id);
   if (n.kind == N_CONST) return Cls{K_CONST32, 0};
-  if (n.kind == N_OP) {
-    switch (n.op) {
-      case O_S_LOAD_DWORD: case O_S_LOAD_DWORDX2: case O_S_LOAD_DWORDX4: case O_S_MUL_I32: case O_S_LSHL_B32:
-      case O_S_LSHR_B32: case O_S_BFE_U32: case O_V_ADD_U32: case O_V_MAD_U32_U24: break;
-      default: return Cls{K_NONE, 0};
-    }
-  } else if (n.kind != N_PAIR && n.kind != N_SLOAD64B) {
-    return Cls{K_NONE, 0};
-  }
-  return classify(v, mkref(id, PART_ENTIRE));
+  if (n.kind == N_OP ? !class_op(n.op) : (n.kind != N_PAIR && n.kind != N_SLOAD64B)) return Cls{K_NONE, 0};
+  return classify_d(v, mkref(id, PART_ENTIRE), 0);
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 12)
     k_node_fwd(const __grid_constant__ Batch b, uint32_t* __restrict__ sf) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= b.I) return;
@@ -516,7 +508,7 @@ __global__ void k_make_views(const __grid_constant__ Batch b, KView* __restrict_
   vsf[k] = v;
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 12)
     k_node_cache(const __grid_constant__ Batch b, uint8_t* __restrict__ cc, uint8_t* __restrict__ ck,
                  const uint32_t* __restrict__ sf, uint32_t* __restrict__ marg, uint32_t* __restrict__ midx) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;

@@ -108,6 +108,40 @@ __device__ __forceinline__ int ilog2_exact(uint32_t x) {
 constexpr int kClassDepth = 4;
 static __device__ Cls classify_d(const KView& v, uint32_t r, int d);
 
+// the operations whose class depends on their operands (every other operation has none)
+__device__ __forceinline__ bool class_op(uint16_t op) {
+  switch (op) {
+    case O_S_LOAD_DWORD: case O_S_LOAD_DWORDX2: case O_S_LOAD_DWORDX4: case O_S_MUL_I32: case O_S_LSHL_B32:
+    case O_S_LSHR_B32: case O_S_BFE_U32: case O_V_ADD_U32: case O_V_MAD_U32_U24: return true;
+  }
+  return false;
+}
+__device__ __forceinline__ Cls leaf_class(uint32_t r) {
+  const uint32_t id = rid(r) & 0x0FFFFFFFu;
+  const uint32_t kind = id >> 8, k = id & 0xFF;
+  if (rpart(r) != PART_ENTIRE) return Cls{K_NONE, 0};
+  if (kind == LEAF_LID) return Cls{K_LID, (uint8_t)k};
+  if (kind == LEAF_GRP) return Cls{K_GRP, (uint8_t)k};
+  if (kind == LEAF_KARG) return Cls{K_KARG, 0};
+  if (kind == LEAF_DISP) return Cls{K_DISP, 0};
+  return Cls{K_NONE, 0};
+}
+// classify_d(v, r, d), answered in line wherever no operand needs a look (undefined values,
+// cached classes, leaves, constants, operations without a class): only a node whose class
+// depends on its operands costs a call.  Used at the top of a classification; the recursion
+// itself stays in classify_d (screening its operands in line there made the class pass slower).
+__device__ __forceinline__ Cls classify_q(const KView& v, uint32_t r, int d) {
+  if (r == kUndef || r == kTop) return Cls{K_UNDEF, 0};
+  if (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) return Cls{v.cc[rid(r)], v.ck[rid(r)]};
+  if (d > kClassDepth && r_node(r)) return Cls{K_NONE, 0};
+  if (r_leaf(r)) return leaf_class(r);
+  if (!r_node(r)) return Cls{K_NONE, 0};
+  const Node& n = v.node(rid(r));
+  if (n.kind == N_CONST) return Cls{K_CONST32, 0};
+  if (n.kind == N_OP ? !class_op(n.op) : (n.kind != N_PAIR && n.kind != N_SLOAD64B)) return Cls{K_NONE, 0};
+  return classify_d(v, r, d);
+}
+
 static __device__ GD_MATCH_INLINE Cls settings_load(const KView& v, const Node& n, uint32_t part, bool wide, int d) {
   Cls none{K_NONE, 0};
   Cls base = classify_d(v, nsrc(v, n, 0), d + 1);
@@ -175,16 +209,7 @@ static __device__ GD_MATCH_INLINE Cls classify_d(const KView& v, uint32_t r, int
   if (r == kUndef || r == kTop) return Cls{K_UNDEF, 0};
   if (v.cc && r_node(r) && rpart(r) == PART_ENTIRE) return Cls{v.cc[rid(r)], v.ck[rid(r)]};
   if (d > kClassDepth && r_node(r)) return none;
-  if (r_leaf(r)) {
-    uint32_t id = rid(r) & 0x0FFFFFFFu;
-    uint32_t kind = id >> 8, k = id & 0xFF;
-    if (rpart(r) != PART_ENTIRE) return none;
-    if (kind == LEAF_LID) return Cls{K_LID, (uint8_t)k};
-    if (kind == LEAF_GRP) return Cls{K_GRP, (uint8_t)k};
-    if (kind == LEAF_KARG) return Cls{K_KARG, 0};
-    if (kind == LEAF_DISP) return Cls{K_DISP, 0};
-    return none;
-  }
+  if (r_leaf(r)) return leaf_class(r);
   if (!r_node(r)) return none;
   const Node& n = v.node(rid(r));
   uint32_t part = rpart(r);
@@ -269,7 +294,7 @@ static __device__ GD_MATCH_INLINE Cls classify_d(const KView& v, uint32_t r, int
 }
 
 // the class of value r
-__device__ __forceinline__ Cls classify(const KView& v, uint32_t r) { return classify_d(v, r, 0); }
+__device__ __forceinline__ Cls classify(const KView& v, uint32_t r) { return classify_q(v, r, 0); }
 
 // memory access: argument pointer + (32-bit index, extended) << log2(element size)
 struct Mem {

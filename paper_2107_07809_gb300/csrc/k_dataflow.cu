@@ -341,7 +341,7 @@ __device__ __forceinline__ int last_def(const uint32_t (*dreg)[4], const uint32_
 // chunk's last definition of each register is written (later chunks overwrite
 // earlier ones, so the row ends as the block's last definitions).
 constexpr int kDefWarps = 4;
-__global__ void __launch_bounds__(32 * kDefWarps)
+__global__ void __launch_bounds__(32 * kDefWarps, 16)
     k_local_defs(const __grid_constant__ Batch b, uint32_t* __restrict__ defbits, const uint32_t* __restrict__ bits_off,
                  const uint32_t* __restrict__ blk_kern) {
   __shared__ uint32_t s_reg[kDefWarps][32][4], s_mask[kDefWarps][kDefBuckets];
@@ -642,7 +642,7 @@ __global__ void k_clear_nodes(const __grid_constant__ Batch b) {
 // Carry halves fused with a low half of the same chunk are built after the
 // other nodes, as they read the low half's node.
 constexpr int kNodeWarps = 4;
-__global__ void __launch_bounds__(32 * kNodeWarps)
+__global__ void __launch_bounds__(32 * kNodeWarps, 16)
     k_nodes(const __grid_constant__ Batch b, uint32_t* __restrict__ rows, const uint32_t* __restrict__ blk_kern) {
   __shared__ uint32_t s_reg[kNodeWarps][32][4], s_val[kNodeWarps][32][4], s_mask[kNodeWarps][kDefBuckets];
   const uint32_t wp = threadIdx.x / 32, lane = threadIdx.x & 31u;

@@ -246,7 +246,7 @@ __device__ void config_row(const Batch& b, uint32_t l, CfgRow& r) {
 // field takes the value of the last row that sets it, an argument is appended
 // at its rank among the .arg rows before it (rows beyond kMaxArgs arguments
 // are errors), and any error marks the kernel bad.
-__global__ void __launch_bounds__(128) k_config(const __grid_constant__ Batch b) {
+__global__ void __launch_bounds__(128, 12) k_config(const __grid_constant__ Batch b) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (k >= b.K) return;

@@ -1412,7 +1412,7 @@ __global__ void __launch_bounds__(256)
 }
 
 // Print records: one thread per instruction, its four node slots.
-__global__ void __launch_bounds__(128, 8) k_print_records(const __grid_constant__ Batch b) {
+__global__ void __launch_bounds__(128, 12) k_print_records(const __grid_constant__ Batch b) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= b.I) return;
   // only reached nodes are ever printed (the reachability walk follows the printed operands)
