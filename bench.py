@@ -62,6 +62,10 @@ WORKLOADS = {
 }
 METRIC = "GCN instrs decompiled/sec"
 # the library's event timing of single kernels (gcn_decomp_stage_times names)
+# DRAM bytes (read + write) per instruction of one k_items launch: ncu on the first 4,000 kernels of
+# the batch distribution (the k_items capture under profiles/: 814.1 MB over 2,201,608 instructions);
+# it holds for the code captured there, and is scaled by the instructions of a launch
+K_ITEMS_DRAM_PER_INSTR = (573.546240e6 + 240.553216e6) / 2_201_608
 KERNEL_TIMINGS = ("k_line_scan (S1)", "k_decode (S4)", "k_nodes (S7)", "k_node_fwd (S9-S10)",
                   "k_node_cache (S9-S10)", "k_items (S13 print)")
 
@@ -597,9 +601,10 @@ def stream_main(args, pkg, torch, rank, world, local):
         "kernel_ms_per_step": dom_ms,
         "timing": "CUDA events around each launch inside the library, summed over one pass of every chunk on "
                   "one stream (kernel timed alone)",
-        "traffic": None,
-        "traffic_note": "DRAM bytes of this kernel: profiles/ (ncu captures on a smaller batch of the same "
-                        "distribution); not re-taken for this run",
+        "traffic": (K_ITEMS_DRAM_PER_INSTR * instr_total / len(chunks)) if dom.startswith("k_items") else None,
+        "traffic_note": "DRAM bytes per launch (one chunk): the ncu capture of k_items on 4,000 kernels of the "
+                        "same distribution (under profiles/), 370 B per instruction, times "
+                        "the instructions of a launch; not re-taken in this run",
         "path_frac": bytes_per_step / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
         "path_note": "the whole pass: algorithmic bytes / ms_per_step against the same peak",
         "kernels_ms_per_step_alone": kern_alone,
