@@ -171,34 +171,52 @@ uint32_t line_scan_tiles(uint64_t n) { return (uint32_t)((n + LS_TILE - 1) / LS_
 // ---------------------------------------------------------------------------
 // generic single-pass scan of u32 arrays
 // ---------------------------------------------------------------------------
-constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
+// A tile of 4096 elements per 256-thread block.  The tile moves between global and shared memory
+// in 16-byte pieces (four consecutive elements per thread and row, when both arrays are 16-byte
+// aligned) and sits in shared memory with a pad word after every 32, so that a thread's run of 16
+// consecutive elements (the sequential part of the scan) and the rows of 16-byte pieces both read
+// and write without bank conflicts.
+constexpr int SC_THREADS = 256, SC_ITEMS = 16, SC_TILE = SC_THREADS * SC_ITEMS;
+constexpr int SC_ROWS = SC_ITEMS / 4;  // rows of 4 * SC_THREADS elements
+__device__ __forceinline__ uint32_t sc_at(uint32_t e) { return e + (e >> 5); }
 
 template <class Op, bool Incl>
 __global__ void __launch_bounds__(SC_THREADS) k_scan(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                                                      uint32_t n, uint64_t* status, uint32_t* counter,
                                                      uint32_t* total_out, uint32_t* err) {
-  __shared__ uint32_t sm[SC_TILE];
+  __shared__ uint32_t sm[SC_TILE + SC_TILE / 32];
   __shared__ uint32_t s_tile, s_prefix, s_warp[32];
   if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
   const uint64_t base = (uint64_t)tile * SC_TILE;
-  for (int k = 0; k < SC_ITEMS; ++k) {
-    uint64_t i = base + (uint64_t)k * SC_THREADS + threadIdx.x;
-    sm[k * SC_THREADS + threadIdx.x] = i < n ? in[i] : Op::id;
+  const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+#pragma unroll
+  for (int r = 0; r < SC_ROWS; ++r) {
+    const uint32_t e = 4 * (threadIdx.x + r * SC_THREADS);  // the first of four consecutive elements
+    const uint64_t i = base + e;
+    uint32_t x[4];
+    if (vec && i + 3 < n) {
+      const uint4 q = *reinterpret_cast<const uint4*>(in + i);
+      x[0] = q.x, x[1] = q.y, x[2] = q.z, x[3] = q.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x[c] = i + c < n ? in[i + c] : Op::id;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm[sc_at(e + c)] = x[c];
   }
   __syncthreads();
   uint32_t v[SC_ITEMS];
   uint32_t acc = Op::id;
 #pragma unroll
   for (int k = 0; k < SC_ITEMS; ++k) {
-    acc = Op::op(acc, sm[threadIdx.x * SC_ITEMS + k]);
+    acc = Op::op(acc, sm[sc_at(threadIdx.x * SC_ITEMS + k)]);
     v[k] = acc;
   }
   uint32_t total;
   uint32_t incl = block_incl_scan<Op>(acc, s_warp, &total);
-  // exclusive prefix of this thread inside the tile: inclusive minus own (for sum),
-  // or the previous thread's inclusive value (general)
+  // exclusive prefix of this thread inside the tile: the previous thread's inclusive value
   uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   __syncthreads();
@@ -218,13 +236,24 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan(const uint32_t* __restrict_
 #pragma unroll
   for (int k = 0; k < SC_ITEMS; ++k) {
     uint32_t r = Op::op(pre, v[k]);
-    sm[threadIdx.x * SC_ITEMS + k] = Incl ? r : run;
+    sm[sc_at(threadIdx.x * SC_ITEMS + k)] = Incl ? r : run;
     run = r;
   }
   __syncthreads();
-  for (int k = 0; k < SC_ITEMS; ++k) {
-    uint64_t i = base + (uint64_t)k * SC_THREADS + threadIdx.x;
-    if (i < n) out[i] = sm[k * SC_THREADS + threadIdx.x];
+#pragma unroll
+  for (int r = 0; r < SC_ROWS; ++r) {
+    const uint32_t e = 4 * (threadIdx.x + r * SC_THREADS);
+    const uint64_t i = base + e;
+    uint32_t x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = sm[sc_at(e + c)];
+    if (vec && i + 3 < n) {
+      *reinterpret_cast<uint4*>(out + i) = make_uint4(x[0], x[1], x[2], x[3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (i + c < n) out[i + c] = x[c];
+    }
   }
 }
 
