@@ -481,17 +481,30 @@ __device__ __forceinline__ Cls classify_node(const KView& v, uint32_t id) {
 
 __global__ void __launch_bounds__(128, 12)
     k_node_fwd(const __grid_constant__ Batch b, uint32_t* __restrict__ sf) {
-  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= b.I) return;
-  const uint32_t k = b.ikern[gi];
-  const KHdr& K = b.kh[k];
-  const KView v = make_view(b, K, k);  // b carries no caches here
-  const bool bad = K.bad;
-  const uint32_t id0 = 4 * (gi - K.first_instr);
-  for (int s = 0; s < 4; ++s) {
-    const Node& n = v.node(id0 + s);
-    uint32_t* o = sf + 3 * (4ull * gi + s);
-    for (int q = 0; q < 3; ++q) o[q] = (!bad && q < n.nsrc) ? fwd_inline(v, n.src[q]) : kTop;
+  // a block's results (12 words per instruction, consecutive for consecutive instructions) are
+  // gathered in shared memory and stored as whole 16-byte pieces
+  __shared__ __align__(16) uint32_t s_sf[128 * 12];
+  const uint32_t g0 = blockIdx.x * blockDim.x, gi = g0 + threadIdx.x;
+  if (gi < b.I) {
+    const uint32_t k = b.ikern[gi];
+    const KHdr& K = b.kh[k];
+    const KView v = make_view(b, K, k);  // b carries no caches here
+    const bool bad = K.bad;
+    const uint32_t id0 = 4 * (gi - K.first_instr);
+    for (int s = 0; s < 4; ++s) {
+      const Node& n = v.node(id0 + s);
+      for (int q = 0; q < 3; ++q)
+        s_sf[12 * threadIdx.x + 3 * s + q] = (!bad && q < n.nsrc) ? fwd_inline(v, n.src[q]) : kTop;
+    }
+  }
+  __syncthreads();
+  const uint32_t nw = 12 * min(blockDim.x, b.I - g0);  // a multiple of 4
+  uint32_t* dst = sf + 12ull * g0;
+  if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+    for (uint32_t q = threadIdx.x; q < nw / 4; q += blockDim.x)
+      reinterpret_cast<uint4*>(dst)[q] = reinterpret_cast<const uint4*>(s_sf)[q];
+  } else {
+    for (uint32_t q = threadIdx.x; q < nw; q += blockDim.x) dst[q] = s_sf[q];
   }
 }
 
