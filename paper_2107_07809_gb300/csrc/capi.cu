@@ -404,7 +404,8 @@ void run_pipeline(Engine* h, const uint8_t* text, uint64_t n, const uint64_t* fi
   ra.instr_excl = W.get<uint32_t>("instr_excl", L + 1);
   ra.label_excl = W.get<uint32_t>("label_excl", L + 1);
   ra.cfg_excl = W.get<uint32_t>("cfg_excl", L + 1);
-  if (L) launch_rows(text, line_start, L, file_off, F, ra, sc, tot, err, s);
+  uint64_t* status3 = W.get<uint64_t>("tile_status3", scan3_status_words(L) + 8);
+  if (L) launch_rows(text, line_start, L, file_off, F, ra, sc, status3, tot, err, s);
   CK(cudaGetLastError());
   sync_totals();
   b.K = h->h_tot[0];

@@ -229,8 +229,10 @@ void launch_line_scan(const uint8_t* text, uint64_t n, uint32_t* line_start, uin
                       uint32_t* counters, uint32_t* err, const LineScan2& two, cudaStream_t s);
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t n, int op, bool inclusive, ScanScratch sc,
                  uint32_t* total_out, uint32_t* err, cudaStream_t s);
+// status3: scan3_status_words(L) look-back words for the three-channel row scans
 void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, const uint64_t* file_off, uint32_t F,
-                 RowArrays& ra, ScanScratch sc, uint32_t* totals, uint32_t* err, cudaStream_t s);
+                 RowArrays& ra, ScanScratch sc, uint64_t* status3, uint32_t* totals, uint32_t* err, cudaStream_t s);
+uint32_t scan3_status_words(uint32_t n);
 void launch_scatter_rows(uint32_t L, RowArrays& ra, uint32_t* instr_line, uint32_t* label_line, uint32_t* label_instr,
                          uint32_t* cfg_line, KHdr* kh, cudaStream_t s);
 

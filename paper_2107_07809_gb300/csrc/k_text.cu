@@ -257,6 +257,151 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan(const uint32_t* __restrict_
   }
 }
 
+// Three scans of the same length in one pass (S2's row scans): each block stages a 2048-element
+// tile of every channel, scans the three locally, and warps 0, 1 and 2 run the three look-backs
+// side by side (channel c's status words at status + c * tiles).
+constexpr int S3_ITEMS = 8, S3_TILE = SC_THREADS * S3_ITEMS;
+
+template <class Op>
+__device__ __forceinline__ void s3_stage(const uint32_t* __restrict__ in, uint32_t* sm, uint64_t base, uint32_t n,
+                                         bool vec) {
+#pragma unroll
+  for (int r = 0; r < S3_ITEMS / 4; ++r) {
+    const uint32_t e = 4 * (threadIdx.x + r * SC_THREADS);
+    const uint64_t i = base + e;
+    uint32_t x[4];
+    if (vec && i + 3 < n) {
+      const uint4 q = *reinterpret_cast<const uint4*>(in + i);
+      x[0] = q.x, x[1] = q.y, x[2] = q.z, x[3] = q.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x[c] = i + c < n ? in[i + c] : Op::id;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm[sc_at(e + c)] = x[c];
+  }
+}
+
+// the thread's inclusive run over its S3_ITEMS elements (v), and the exclusive prefix of the run
+// inside the tile; *total = the tile's aggregate
+template <class Op>
+__device__ __forceinline__ uint32_t s3_local(const uint32_t* sm, uint32_t* v, uint32_t* s_warp, uint32_t* total) {
+  uint32_t acc = Op::id;
+#pragma unroll
+  for (int k = 0; k < S3_ITEMS; ++k) {
+    acc = Op::op(acc, sm[sc_at(threadIdx.x * S3_ITEMS + k)]);
+    v[k] = acc;
+  }
+  const uint32_t incl = block_incl_scan<Op>(acc, s_warp, total);
+  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  return lane ? prev : (warp ? s_warp[warp - 1] : Op::id);
+}
+
+template <class Op, bool Incl>
+__device__ __forceinline__ void s3_write(uint32_t* sm, const uint32_t* v, uint32_t pre) {
+  uint32_t run = pre;
+#pragma unroll
+  for (int k = 0; k < S3_ITEMS; ++k) {
+    const uint32_t r = Op::op(pre, v[k]);
+    sm[sc_at(threadIdx.x * S3_ITEMS + k)] = Incl ? r : run;
+    run = r;
+  }
+}
+
+__device__ __forceinline__ void s3_store(const uint32_t* sm, uint32_t* __restrict__ out, uint64_t base, uint32_t n,
+                                         bool vec) {
+#pragma unroll
+  for (int r = 0; r < S3_ITEMS / 4; ++r) {
+    const uint32_t e = 4 * (threadIdx.x + r * SC_THREADS);
+    const uint64_t i = base + e;
+    uint32_t x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = sm[sc_at(e + c)];
+    if (vec && i + 3 < n) {
+      *reinterpret_cast<uint4*>(out + i) = make_uint4(x[0], x[1], x[2], x[3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (i + c < n) out[i + c] = x[c];
+    }
+  }
+}
+
+struct Scan3 {
+  const uint32_t* in[3];
+  uint32_t* out[3];
+  uint32_t n;
+  uint64_t* status;  // 3 * tiles words, zeroed before the launch
+  uint32_t* counter;
+  uint32_t* total_out[3];  // null: not wanted
+  uint32_t* err;
+};
+
+template <class O0, class O1, class O2, bool Incl>
+__global__ void __launch_bounds__(SC_THREADS) k_scan3(const __grid_constant__ Scan3 a) {
+  __shared__ uint32_t sm[3][S3_TILE + S3_TILE / 32];
+  __shared__ uint32_t s_tile, s_prefix[3], s_warp[3][32];
+  if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * S3_TILE;
+  bool vec = true;
+  for (int c = 0; c < 3; ++c)
+    vec = vec && ((reinterpret_cast<uintptr_t>(a.in[c]) | reinterpret_cast<uintptr_t>(a.out[c])) & 15u) == 0;
+  s3_stage<O0>(a.in[0], sm[0], base, a.n, vec);
+  s3_stage<O1>(a.in[1], sm[1], base, a.n, vec);
+  s3_stage<O2>(a.in[2], sm[2], base, a.n, vec);
+  __syncthreads();
+  uint32_t v0[S3_ITEMS], v1[S3_ITEMS], v2[S3_ITEMS], t0, t1, t2;
+  const uint32_t x0 = s3_local<O0>(sm[0], v0, s_warp[0], &t0);
+  const uint32_t x1 = s3_local<O1>(sm[1], v1, s_warp[1], &t1);
+  const uint32_t x2 = s3_local<O2>(sm[2], v2, s_warp[2], &t2);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const bool last = tile == gridDim.x - 1;
+  if (warp == 0) {
+    const uint32_t p = lookback<O0>(a.status, tile, t0, a.err);
+    if (lane == 0) {
+      s_prefix[0] = p;
+      if (last && a.total_out[0]) *a.total_out[0] = O0::op(p, t0);
+    }
+  } else if (warp == 1) {
+    const uint32_t p = lookback<O1>(a.status + gridDim.x, tile, t1, a.err);
+    if (lane == 0) {
+      s_prefix[1] = p;
+      if (last && a.total_out[1]) *a.total_out[1] = O1::op(p, t1);
+    }
+  } else if (warp == 2) {
+    const uint32_t p = lookback<O2>(a.status + 2ull * gridDim.x, tile, t2, a.err);
+    if (lane == 0) {
+      s_prefix[2] = p;
+      if (last && a.total_out[2]) *a.total_out[2] = O2::op(p, t2);
+    }
+  }
+  __syncthreads();
+  s3_write<O0, Incl>(sm[0], v0, O0::op(s_prefix[0], x0));
+  s3_write<O1, Incl>(sm[1], v1, O1::op(s_prefix[1], x1));
+  s3_write<O2, Incl>(sm[2], v2, O2::op(s_prefix[2], x2));
+  __syncthreads();
+  s3_store(sm[0], a.out[0], base, a.n, vec);
+  s3_store(sm[1], a.out[1], base, a.n, vec);
+  s3_store(sm[2], a.out[2], base, a.n, vec);
+}
+
+template <class O0, class O1, class O2, bool Incl>
+static void launch_scan3(Scan3 a, cudaStream_t s) {
+  uint32_t tiles = (a.n + S3_TILE - 1) / S3_TILE;
+  if (!tiles) tiles = 1;
+  cudaMemsetAsync(a.status, 0, sizeof(uint64_t) * 3 * tiles, s);
+  cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), s);
+  k_scan3<O0, O1, O2, Incl><<<tiles, SC_THREADS, 0, s>>>(a);
+  ++launch_counter();
+}
+uint32_t scan3_status_words(uint32_t n) { return 3 * ((n + S3_TILE - 1) / S3_TILE + 1); }
+
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t n, int op, bool inclusive, ScanScratch sc,
                  uint32_t* total_out, uint32_t* err, cudaStream_t s) {
   uint32_t tiles = (n + SC_TILE - 1) / SC_TILE;
@@ -375,7 +520,7 @@ __global__ void k_scatter_rows(const uint8_t* __restrict__ rowtype, const uint32
 }
 
 void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, const uint64_t* file_off, uint32_t F,
-                 RowArrays& ra, ScanScratch sc, uint32_t* totals, uint32_t* err, cudaStream_t s) {
+                 RowArrays& ra, ScanScratch sc, uint64_t* status3, uint32_t* totals, uint32_t* err, cudaStream_t s) {
   const int T = 256;
   cudaMemsetAsync(ra.file_start, 0, L, s);
   if (F) {
@@ -384,14 +529,19 @@ void launch_rows(const uint8_t* text, const uint32_t* line_start, uint32_t L, co
   }
   k_classify<<<(L + T - 1) / T, T, 0, s>>>(text, line_start, L, ra.file_start, ra.kind, ra.t0, ra.t1, ra.t2);
   ++launch_counter();
-  launch_scan(ra.t0, ra.mkmax, L, 1, true, sc, nullptr, err, s);
-  launch_scan(ra.t1, ra.fsmax, L, 1, true, sc, nullptr, err, s);
-  launch_scan(ra.t2, ra.kcnt, L, 0, true, sc, &totals[0], err, s);  // totals[0] = kernels
+  // the last state marker, the last file start (inclusive maxima) and the running .kernel count
+  launch_scan3<ScanMax, ScanMax, ScanSum, true>(
+      Scan3{{ra.t0, ra.t1, ra.t2}, {ra.mkmax, ra.fsmax, ra.kcnt}, L, status3, sc.counter,
+            {nullptr, nullptr, &totals[0]}, err},  // totals[0] = kernels
+      s);
   k_assign<<<(L + T - 1) / T, T, 0, s>>>(ra.kind, ra.mkmax, ra.fsmax, ra.kcnt, L, ra.rowtype, ra.t0, ra.t1, ra.t2);
   ++launch_counter();
-  launch_scan(ra.t0, ra.instr_excl, L, 0, false, sc, &totals[1], err, s);  // totals[1] = instructions
-  launch_scan(ra.t1, ra.label_excl, L, 0, false, sc, &totals[2], err, s);  // totals[2] = labels
-  launch_scan(ra.t2, ra.cfg_excl, L, 0, false, sc, &totals[14], err, s);   // totals[14] = configuration rows
+  // ranks of the instruction, label and configuration rows; totals[1] = instructions, totals[2] =
+  // labels, totals[14] = configuration rows
+  launch_scan3<ScanSum, ScanSum, ScanSum, false>(
+      Scan3{{ra.t0, ra.t1, ra.t2}, {ra.instr_excl, ra.label_excl, ra.cfg_excl}, L, status3, sc.counter,
+            {&totals[1], &totals[2], &totals[14]}, err},
+      s);
 }
 
 void launch_scatter_rows(uint32_t L, RowArrays& ra, uint32_t* instr_line, uint32_t* label_line, uint32_t* label_instr,
