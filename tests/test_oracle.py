@@ -97,6 +97,78 @@ def test_suffix_u32_is_unsigned_addition():
     assert r.text == gold("suffix_uint_add.cl")
 
 
+_SUFFIX_HEAD = """.kernel t
+    .config
+        .dims x
+        .cws 64, 1, 1
+        .sgprsnum 16
+        .vgprsnum 12
+        .useargs
+        .arg _.global_offset_0, "size_t", long
+        .arg _.global_offset_1, "size_t", long
+        .arg _.global_offset_2, "size_t", long
+        .arg _.printf_buffer, "size_t", void*, global, , rdonly
+        .arg _.vqueue_pointer, "size_t", long
+        .arg _.aqlwrap_pointer, "size_t", long
+        .arg x, "int", int
+        .arg y, "int", int
+        .arg data, "int*", int*, global,
+    .text
+        s_load_dword s0, s[4:5], 0x30
+        s_load_dword s1, s[4:5], 0x38
+        s_load_dwordx2 s[8:9], s[4:5], 0x40
+        s_waitcnt lgkmcnt(0)
+        v_mov_b32 v2, v0
+        v_mov_b32 v3, 0
+        v_lshlrev_b64 v[4:5], 2, v[2:3]
+        v_add_co_u32 v4, vcc, s8, v4
+        v_addc_co_u32 v5, vcc, s9, v5, vcc
+        v_mov_b32 v7, s0
+        v_mov_b32 v8, s1
+"""
+
+
+def _suffix_kernel(op):
+    # the result of `op` (in v6) is stored twice, so it becomes the kernel's one variable
+    return (_SUFFIX_HEAD + "        " + op + "\n        global_store_dword v[4:5], v6, off\n"
+            "        global_store_dword v[4:5], v6, off\n        s_endpgm\n")
+
+
+@pytest.mark.parametrize("op,want", [
+    ("v_add_f32 v6, v7, v8", "float"), ("v_sub_f32 v6, v7, v8", "float"), ("v_mul_f32 v6, v7, v8", "float"),
+    ("v_fma_f32 v6, v7, v8, v7", "float"), ("v_cvt_f32_i32 v6, v7", "float"), ("v_cvt_f32_u32 v6, v7", "float"),
+    ("v_add_u32 v6, v7, v8", "uint"), ("v_sub_u32 v6, v7, v8", "uint"), ("v_mul_lo_u32 v6, v7, v8", "uint"),
+    ("v_mad_u32_u24 v6, v7, v8, v7", "uint"), ("v_mul_u32_u24 v6, v7, v8", "uint"),
+    ("v_mul_hi_u32_u24 v6, v7, v8", "uint"), ("v_ashrrev_i32 v6, v7, v8", "int"),
+    ("v_mul_hi_i32_i24 v6, v7, v8", "int"),
+    ("s_mul_i32 s2, s0, s1\n        v_mov_b32 v6, s2", "int"),
+    ("s_add_u32 s2, s0, s1\n        v_mov_b32 v6, s2", "uint"),
+])
+def test_result_type_follows_the_suffix(op, want):
+    """"Data type recovery": an instruction's suffix (the first one for a conversion or a
+    double-suffix operation) gives its result's type: f32 float, u32 uint, i32 int.  The result
+    here is used twice, so it is declared once, with that type."""
+    r = oracle.decompile(_suffix_kernel(op))
+    assert r.worst == 0
+    assert re.findall(r"^    (\w+) (var\d+);", r.text, re.M) == [(want, "var0")]
+
+
+@pytest.mark.parametrize("op,stmt", [
+    # int arguments under a float operation: the register's bits are read as a float
+    ("v_add_f32 v6, v7, v8", "var0 = (as_float(x) + as_float(y));"),
+    # the paper's _u32 example: the signed arguments are read as unsigned
+    ("v_add_u32 v6, v7, v8", "var0 = ((uint)x + (uint)y);"),
+    # a conversion instruction converts the value
+    ("v_cvt_f32_i32 v6, v7", "var0 = (float)x;"),
+])
+def test_operands_convert_to_the_suffix_type(op, stmt):
+    """"Data type recovery": the arguments' types are fixed by the signature, so an operand of
+    another type than the suffix asks for is converted: a cast between integers, a reinterpretation
+    of the bits between an integer and a float, and a value conversion for a cvt instruction."""
+    r = oracle.decompile(_suffix_kernel(op))
+    assert "    " + stmt + "\n" in r.text
+
+
 # ---- "Search for control structures", Fig. 3 --------------------------------
 def test_fig3_region_trace():
     lines = [l.split() for l in gold("fig3_trace.txt").split("\n") if l and not l.startswith("#")]
