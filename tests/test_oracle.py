@@ -153,6 +153,27 @@ def test_result_type_follows_the_suffix(op, want):
     assert re.findall(r"^    (\w+) (var\d+);", r.text, re.M) == [(want, "var0")]
 
 
+@pytest.mark.parametrize("op,want,stmt", [
+    # int and int join to int: no conversion
+    ("v_and_b32 v6, v7, v8", "int", "var0 = (x & y);"),
+    ("v_xor_b32 v6, v7, v8", "int", "var0 = (x ^ y);"),
+    # float and int join to the top of the 32-bit chain, printed as uint: the float's bits are read
+    # as an unsigned integer, the int is cast
+    ("v_add_f32 v9, v7, v8\n        v_and_b32 v6, v9, v7", "uint",
+     "var0 = (as_uint((as_float(x) + as_float(y))) & (uint)x);"),
+    # uint and int join to top32 as well
+    ("v_add_u32 v9, v7, v8\n        v_and_b32 v6, v9, v7", "uint", "var0 = (((uint)x + (uint)y) & (uint)x);"),
+])
+def test_bitwise_operations_take_the_join_of_their_operands(op, want, stmt):
+    """"Data type recovery": a bitwise operation has no type of its own; its result takes the join
+    of its operands' types in the lattice none < {int, uint, float} < top32, and top prints as
+    uint."""
+    r = oracle.decompile(_suffix_kernel(op))
+    assert r.worst == 0
+    assert re.findall(r"^    (\w+) (var\d+);", r.text, re.M) == [(want, "var0")]
+    assert "    " + stmt + "\n" in r.text
+
+
 @pytest.mark.parametrize("op,stmt", [
     # int arguments under a float operation: the register's bits are read as a float
     ("v_add_f32 v6, v7, v8", "var0 = (as_float(x) + as_float(y));"),
