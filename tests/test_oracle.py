@@ -7,6 +7,7 @@ interpreter running the assembly against an evaluator running the decompiled
 OpenCL on random buffers)."""
 import os
 import re
+import struct
 
 import numpy as np
 import pytest
@@ -151,6 +152,27 @@ def test_result_type_follows_the_suffix(op, want):
     r = oracle.decompile(_suffix_kernel(op))
     assert r.worst == 0
     assert re.findall(r"^    (\w+) (var\d+);", r.text, re.M) == [(want, "var0")]
+
+
+def _f32_bits(x):
+    return struct.unpack("<I", struct.pack("<f", x))[0]
+
+
+@pytest.mark.parametrize("lit,text", [
+    (f"{_f32_bits(0.25):#x}", "0.25f"),       # two fraction bits: the exact decimal
+    (f"{_f32_bits(1000.0):#x}", "1000.0f"),   # an integer value
+    ("-4.0", "-4.0f"),                        # an inline float constant
+    (f"{_f32_bits(0.1):#x}", f"as_float({_f32_bits(0.1)}u)"),              # 0.1 has no finite binary form
+    (f"{_f32_bits(1.0) + 1:#x}", f"as_float({_f32_bits(1.0) + 1}u)"),      # 23 fraction bits
+    ("0x7f800000", "as_float(2139095040u)"),  # infinity
+    ("0x80000000", "as_float(2147483648u)"),  # negative zero
+])
+def test_float_literals(lit, text):
+    """Output format of a float literal: its exact decimal when the value has at most 16 binary
+    fraction digits, else its bit pattern reinterpreted, so that every literal reads back to the
+    same bits."""
+    r = oracle.decompile(_suffix_kernel(f"v_add_f32 v6, {lit}, v8"))
+    assert f"    var0 = ({text} + as_float(y));\n" in r.text
 
 
 @pytest.mark.parametrize("op,want,stmt", [
