@@ -154,6 +154,27 @@ def test_result_type_follows_the_suffix(op, want):
     assert re.findall(r"^    (\w+) (var\d+);", r.text, re.M) == [(want, "var0")]
 
 
+@pytest.mark.parametrize("op,stmt", [
+    # an unsigned operation reads the inline constant -1 as 2^32 - 1
+    ("v_add_u32 v6, -1, v8", "var0 = (4294967295u + (uint)y);"),
+    ("v_add_u32 v6, 0xffffffff, v8", "var0 = (4294967295u + (uint)y);"),
+    # a signed one keeps it signed
+    ("s_mul_i32 s2, s0, -5\n        v_mov_b32 v6, s2", "var0 = (x * -5);"),
+    ("s_mul_i32 s2, s0, 0x7fffffff\n        v_mov_b32 v6, s2", "var0 = (x * 2147483647);"),
+    # a 32-bit shift uses the low five bits of its amount (33 & 31 = 1)
+    ("v_lshlrev_b32 v6, 33, v8", "var0 = (y << 1);"),
+    ("v_ashrrev_i32 v6, 3, v8", "var0 = (y >> 3);"),
+    # an inline float constant in an integer operation is its bit pattern (1.0f = 0x3f800000)
+    ("v_add_u32 v6, 1.0, v8", "var0 = (1065353216u + (uint)y);"),
+])
+def test_integer_literals(op, stmt):
+    """Output format of integer literals (decimal, `u` for unsigned), with the values the GCN
+    operation gives its constant operand."""
+    r = oracle.decompile(_suffix_kernel(op))
+    assert r.worst == 0
+    assert "    " + stmt + "\n" in r.text
+
+
 def _f32_bits(x):
     return struct.unpack("<I", struct.pack("<f", x))[0]
 
