@@ -175,6 +175,36 @@ def test_integer_literals(op, stmt):
     assert "    " + stmt + "\n" in r.text
 
 
+_SIG = "__kernel void t(int x, int y, __global int *data)\n{\n"
+
+
+@pytest.mark.parametrize("body,want", [
+    # used once: printed in place
+    ("        v_add_u32 v6, v7, v8\n        global_store_dword v[4:5], v6, off\n",
+     "    data[get_local_id(0)] = (int)((uint)x + (uint)y);\n"),
+    # used twice: a variable
+    ("        v_add_u32 v6, v7, v8\n        global_store_dword v[4:5], v6, off\n"
+     "        global_store_dword v[4:5], v6, off\n",
+     "    uint var0;\n    var0 = ((uint)x + (uint)y);\n    data[get_local_id(0)] = (int)var0;\n"
+     "    data[get_local_id(0)] = (int)var0;\n"),
+    # a global load: a variable at its program point, even when used once
+    ("        global_load_dword v6, v[4:5], off\n        s_waitcnt vmcnt(0)\n        v_add_u32 v9, v6, v7\n"
+     "        global_store_dword v[4:5], v9, off\n",
+     "    int var0;\n    var0 = data[get_local_id(0)];\n    data[get_local_id(0)] = (int)((uint)var0 + (uint)x);\n"),
+    # used in another block (the then-part of a uniform if): a variable
+    ("        v_add_u32 v6, v7, v8\n        s_cmp_eq_u32 s0, 0\n        s_cbranch_scc1 .L1\n"
+     "        global_store_dword v[4:5], v6, off\n.L1:\n",
+     "    uint var0;\n    var0 = ((uint)x + (uint)y);\n    if (!((uint)x == 0u)) {\n"
+     "        data[get_local_id(0)] = (int)var0;\n    }\n"),
+])
+def test_variables_by_the_materialisation_rule(body, want):
+    """Variables are introduced only when needed: a value becomes a variable when it is a global
+    load, is used twice or more, or is used in another block; otherwise it prints in place."""
+    r = oracle.decompile(_SUFFIX_HEAD + body + "        s_endpgm\n")
+    assert r.worst == 0
+    assert r.text == _SIG + want + "}\n"
+
+
 def _f32_bits(x):
     return struct.unpack("<I", struct.pack("<f", x))[0]
 
