@@ -175,6 +175,22 @@ def test_integer_literals(op, stmt):
     assert "    " + stmt + "\n" in r.text
 
 
+@pytest.mark.parametrize("op", [
+    "v_add_f32 v6, v7, v8", "v_fma_f32 v6, v7, v8, v7", "v_cvt_f32_i32 v6, v7", "v_cvt_f32_u32 v6, v7",
+    "v_sub_u32 v6, v7, v8", "v_mul_lo_u32 v6, v7, v8", "v_mad_u32_u24 v6, v7, v8, v7", "v_mul_hi_u32_u24 v6, v7, v8",
+    "v_mul_hi_i32_i24 v6, v7, v8", "v_ashrrev_i32 v6, v7, v8", "v_lshrrev_b32 v6, v7, v8",
+    "s_mul_i32 s2, s0, s1\n        v_mov_b32 v6, s2", "v_lshlrev_b32 v6, 33, v8", "v_add_u32 v6, 1.0, v8",
+    "v_add_u32 v6, -1, v8", "v_add_f32 v6, 0x3dcccccd, v8", "v_add_f32 v9, v7, v8\n        v_and_b32 v6, v9, v7",
+])
+def test_brute_force_pin_kernels(op):
+    """The hand-made kernels of the typing and literal pins compute, as decompiled, the same bits as
+    their assembly (three seeded runs of the interpreter against the evaluator)."""
+    src = _suffix_kernel(op)
+    r = oracle.decompile(src)
+    for seed in range(3):
+        assert brute.check(src, r.text, seed=seed) is None
+
+
 _SIG = "__kernel void t(int x, int y, __global int *data)\n{\n"
 
 
